@@ -1,0 +1,110 @@
+"""Each plausible mistake planted in the oracle must fail at least one pin.
+
+The mutations are applied with monkeypatch to the oracle module on the CPU
+only; they show the pins in test_oracle_pins.py are not vacuous.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dcflow_ref as ref
+import tests.test_oracle_pins as pins
+
+
+def _fails(fn, *args):
+    try:
+        fn(*args)
+    except AssertionError:
+        return True
+    except (ValueError, IndexError, np.linalg.LinAlgError, ZeroDivisionError):
+        return True
+    return False
+
+
+def _cw_wrong_sign(n_bus, f, t, b):
+    Cw = np.zeros((len(f), n_bus))
+    for l in range(len(f)):
+        Cw[l, f[l]] += b[l]
+        Cw[l, t[l]] += b[l]  # planted: + instead of -
+    return Cw
+
+
+def _lodf_no_override(ptdf_m, f, t, k):
+    num = ptdf_m[:, f[k]] - ptdf_m[:, t[k]]
+    return num / (1.0 - num[k])  # planted: LODF[k,k] = -1 dropped
+
+
+def _lodf_transposed(ptdf_m, f, t, k):
+    num = ptdf_m[k, f] - ptdf_m[k, t]  # planted: row instead of column
+    col = num / (1.0 - num[k])
+    col[k] = -1.0
+    return col
+
+
+def _modf_no_override(ptdf_m, f, t, outages):
+    O = list(outages)
+    rhs = ptdf_m[:, [f[k] for k in O]] - ptdf_m[:, [t[k] for k in O]]
+    A = np.eye(len(O)) - rhs[O, :]
+    return np.linalg.solve(A.T, rhs.T).T  # planted: rows O not set to -I
+
+
+def _bsdf_corr_on_all(ptdf_m, f, t, b, A, moved, new_bus):
+    _, bbc, ext = _orig_bsdf(ptdf_m, f, t, b, A, moved, new_bus)
+    E, V = ptdf_m.shape
+    inc = [l for l in range(E) if f[l] == A or t[l] == A]
+    S = [l for l in inc if l not in set(moved)]
+    bS = sum(b[l] for l in S)
+    shift = np.zeros(V + 1)
+    shift[new_bus] = -1.0
+    corr = np.zeros(E)
+    for l in S:
+        far = t[l] if f[l] == A else f[l]
+        shift[far] += b[l] / bS
+    for l in inc:  # planted: correction over every incident branch, moved ones too
+        corr[l] = b[l] / bS if f[l] == A else -b[l] / bS
+    return (ext @ shift + corr) / (1.0 - bbc @ shift), bbc, ext
+
+
+_orig_bsdf = ref.bsdf
+
+
+def _incident_descending(n_bus, f, t):
+    return [x[::-1] for x in _orig_inc(n_bus, f, t)]  # planted: mask bit order reversed
+
+
+_orig_inc = ref.incident_lists
+
+
+def _components_ignores_isolated(n, f, t, alive):
+    used = set(np.asarray(f)[alive].tolist()) | set(np.asarray(t)[alive].tolist())
+    c = _orig_comp(n, f, t, alive)
+    return c - (n - len(used))  # planted: isolated buses are not islands
+
+
+_orig_comp = ref.components
+
+
+MUTATIONS = [
+    ("weighted_connectivity", _cw_wrong_sign, [(pins.test_three_bus_golden, "golden")]),
+    ("lodf_column", _lodf_no_override, [(pins.test_lodf_diagonal_and_outaged_flow, 4)]),
+    ("lodf_column", _lodf_transposed, [(pins.test_lodf_equals_refactorisation, 12)]),
+    ("modf", _modf_no_override, [(pins.test_modf_equals_refactorisation, 15)]),
+    ("bsdf", _bsdf_corr_on_all, [(pins.test_bsdf_sequential_equals_refactorisation, 17)]),
+    ("incident_lists", _incident_descending, [(pins.test_split_examples_golden, "golden")]),
+    ("components", _components_ignores_isolated, [(pins.test_split_examples_golden, "golden")]),
+]
+
+
+@pytest.mark.parametrize("name,mut,checks", MUTATIONS, ids=[m[1].__name__ for m in MUTATIONS])
+def test_planted_mistake_is_caught(monkeypatch, golden_dir, name, mut, checks):
+    monkeypatch.setattr(ref, name, mut)
+    monkeypatch.setattr(oracle, name, mut, raising=False)
+    caught = False
+    for fn, arg in checks:
+        if arg == "golden":
+            caught |= _fails(fn, golden_dir)
+        elif arg is None:
+            caught |= _fails(fn)
+        else:
+            caught |= _fails(fn, arg)
+    assert caught, f"planted mistake in {name} not detected"
