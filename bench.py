@@ -1,0 +1,363 @@
+"""Benchmark: N-1 DC loadflows per second on the 500-bus / 700-branch study.
+
+Workload (synthetic, seeded): 500-bus, 700-branch grid, 50 split-capable
+substations, 10,000 topologies with 1-4 bus splits and 0-3 branch outages,
+24 timesteps of injections, full N-1 over all 700 branches with every branch
+monitored.  One step = one dcflow_solve_batch over the whole batch (N-0 flows,
+r x r updates, fused N-1 with max / arg-max / overload reduction), inputs
+resident in HBM.  A loadflow is one solved (topology, timestep, contingency)
+N-1 case (islanded topologies and islanding or outaged contingencies are not
+counted).
+
+The headline form is FP32 (mixed precision: FP64 factor, r x r systems and
+N-1 denominators); the plain FP64 form is measured beside it.  Under torchrun
+every rank solves its own 10,000-topology batch (weak scaling, no collective
+on the data path).  ``--impl reference`` times the CPU oracle on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "grid500_splits1-4_outages0-3_T24_fullN1"
+N_TOPO, T_STEPS = 10000, 24
+# dram bytes per launch of the dominant kernel from the ncu capture summarised in
+# profiles/k_n1_grid500.md, keyed by the sha1 of the kernel source it was taken on
+N1_TRAFFIC = {}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def _src_hash():
+    h = hashlib.sha1()
+    for f in ("solve.cu", "internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2501_17529_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _loadflows(topo, status, n_island_cont, cont, T):
+    """N-1 cases solved: valid contingencies of non-islanded topologies x T."""
+    cset = set(int(c) for c in cont)
+    n = 0
+    for i in range(topo.n_topo):
+        if status[i] != 0:
+            continue
+        a, b = topo.out_ptr[i], topo.out_ptr[i + 1]
+        n_out_cont = sum(1 for c in topo.out_branch[a:b] if int(c) in cset)
+        n += len(cont) - n_out_cont - int(n_island_cont[i])
+    return n * T
+
+
+def _cpu_worker(args):
+    idx, = args
+    import oracle
+    from paper_2501_17529_b300 import synth
+    w = synth.workload(2)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    t0 = time.perf_counter()
+    r = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, idx=idx)
+    dt = time.perf_counter() - t0
+    return oracle.loadflow_count(r, w.inj.shape[0]), dt
+
+
+def cpu_baseline(budget_s: float = 20.0):
+    """The oracle as it stands on the host cores, on a bounded topology sample."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    # probe the per-topology cost, then size the sample to the budget
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        probe = pool.map(_cpu_worker, [([i],) for i in range(cores)])
+        per_topo = max(1e-3, statistics.median(dt for _, dt in probe))
+        n_each = max(1, int(budget_s / per_topo))
+        chunks = [(list(range(cores + k * n_each, cores + (k + 1) * n_each)),) for k in range(cores)]
+        t0 = time.perf_counter()
+        res = pool.map(_cpu_worker, chunks)
+        wall = time.perf_counter() - t0
+    lf = sum(r[0] for r in res)
+    ntop = n_each * cores
+    return {"value": lf / wall, "unit": "loadflows/s", "cores": cores, "kind": "oracle",
+            "sample": f"{ntop} of the {N_TOPO} topologies (x{T_STEPS} timesteps, full N-1), "
+                      f"{cores} spawn workers, 1 BLAS thread each, {wall:.1f} s wall"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2501_17529_b300 import synth
+    w = synth.workload(2)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    per = max(1, int(os.environ.get("DCFLOW_REF_TOPO_PER_STEP", "8")))
+    times, lfs = [], []
+    for s in range(args.warmup + args.steps):
+        idx = list(range(s * per, (s + 1) * per))
+        t0 = time.perf_counter()
+        r = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, idx=idx)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            lfs.append(oracle.loadflow_count(r, T_STEPS))
+    value = sum(lfs) / sum(times)
+    line = {"impl": "reference", "metric": "N-1 DC loadflows/sec (oracle on host cores)", "value": value,
+            "unit": "loadflows/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "topologies_per_step": per, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": "loadflows/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per} topologies per step, single process"},
+            "e2e": {"value": value, "unit": "loadflows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2501_17529_b300 import synth
+    from paper_2501_17529_b300.csrc import build as cbuild
+    from paper_2501_17529_b300.dcflow import DeviceBatch, DeviceResults, Solver
+
+    if rank == 0 or ws == 1:
+        cbuild.build()
+    if ws > 1:
+        dist.barrier()
+    w = synth.workload(2)
+    if ws > 1 and rank > 0:  # each rank its own batch of the same shape
+        w.topo = synth.make_topologies(w.grid, w.subs, N_TOPO, 202 + 1000 * rank, (1, 4), (0, 3))
+    # limits from the unsplit grid's N-0 flows, computed on the device
+    base = Solver(w.grid, precision="fp64")
+    pt = base.base_ptdf(np.arange(w.grid.n_branch)).cpu().numpy()
+    base.close()
+    lim = 1.2 * np.abs(w.inj @ pt.T).max(axis=0) + 0.1
+
+    results = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
+    peaks, peak_kind = _peaks()
+    for form in (args.forms.split(",")):
+        solver = Solver(w.grid, precision=form)
+        solver.set_study(w.mon, w.cont, lim, split_bus=w.subs)
+        db = DeviceBatch(w.topo, w.inj)
+        res = DeviceResults(db.n_topo, db.n_time, len(w.mon))
+        stream = torch.cuda.current_stream()
+        steps = args.steps if form == "fp32" else max(1, min(args.steps, args.fp64_steps))
+        for _ in range(args.warmup):
+            solver.solve(db, results=res)
+        torch.cuda.synchronize()
+        host = res.to_host()
+        lf = _loadflows(w.topo, host["status"], host["n_island_cont"], w.cont, T_STEPS)
+        lib = __import__("paper_2501_17529_b300.dcflow", fromlist=["x"])
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        launches = 0
+        lib.dcflow_profile(solver.ctx, True)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(dev) as clk:
+            wall0 = time.perf_counter()
+            for k in range(steps):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+                solver.solve(db, results=res)
+                ev[k][1].record(stream)
+                launches += solver.last_launch_count()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - wall0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        t_dev = sum(ms) / 1e3
+        kern = lib.dcflow_profile_read(solver.ctx)
+        lib.dcflow_profile(solver.ctx, False)
+        n_ok = int((host["status"] == 0).sum())
+        kern["entries"] = float(n_ok) * len(w.mon) * len(w.cont) * T_STEPS * steps
+        if ws > 1:
+            tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_dev = float(tt.item())
+            lft = torch.tensor([lf], device="cuda", dtype=torch.float64)
+            dist.all_reduce(lft)
+            lf_all = float(lft.item())
+        else:
+            lf_all = lf
+        results[form] = {"value": lf_all * steps / t_dev, "ms_per_step": 1e3 * t_dev / steps,
+                         "loadflows_per_step": lf_all, "steps": steps, "launches": launches,
+                         "clocks": clk.summary(), "wall_s": wall, "kernel": kern}
+        # end to end through host buffers: H2D of the batch, solve, D2H of the results
+        if form == "fp32" and not args.no_e2e:
+            results[form]["e2e"] = _e2e(solver, w, lim, steps, args.warmup, lf)
+        solver.close()
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    head = results.get("fp32") or next(iter(results.values()))
+    roof = None
+    if head.get("kernel"):
+        k = head["kernel"]
+        # 4 FP32-pipe issue slots per N-1 entry (FFMA, FMNMX, FFMA.SAT, FADD); peak =
+        # 148 SMs x 128 lanes x max SM clock lane-instructions per second
+        peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        ach = k["entries"] * 4 / (k["n1_ms"] / 1e3) / 1e12
+        key = (_src_hash(), "fp32")
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s", "frac": ach / peak,
+                "traffic": N1_TRAFFIC.get(key), "kernel": "k_n1<float>",
+                "peak_note": f"FP32 issue slots at max SM clock ({peak_kind} sm_max_mhz)",
+                "n1_share_of_step": k["n1_ms"] / (head["ms_per_step"] * head["steps"])}
+    line = {"metric": "N-1 DC loadflows/sec on 1 B300, FP64 plain vs mixed-prec form at stated max err",
+            "value": head["value"], "unit": "loadflows/s", "n_gpus": ws, "steps": head["steps"],
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "topologies": N_TOPO, "timesteps": T_STEPS, "monitored": 700,
+                       "contingencies": 700, "l2": "flushed between steps (256 MB write)",
+                       "max_err_stated": {"fp32": 1e-4, "fp64": 1e-10}},
+            "gpu_launches": head["launches"], "clocks": head["clocks"],
+            "forms": {f: {k: v for k, v in r.items() if k not in ("clocks", "kernel")} for f, r in results.items()}}
+    if "fp64" in results and "fp32" in results:
+        line["forms"]["fp32_over_fp64_speedup"] = results["fp32"]["value"] / results["fp64"]["value"]
+    if "e2e" in head:
+        line["e2e"] = head["e2e"]
+    if roof:
+        line["roofline"] = roof
+    if ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _e2e(solver, w, lim, steps, warmup, lf):
+    import torch
+    from paper_2501_17529_b300.dcflow import DeviceBatch, DeviceResults
+
+    db = DeviceBatch(w.topo, w.inj)
+    res = DeviceResults(db.n_topo, db.n_time, len(w.mon))
+    names = ["split_ptr", "split_sub", "split_mask", "out_ptr", "out_branch", "inj"]
+    host_in = {n: getattr(db, n).cpu().pin_memory() for n in names}
+    outs = ["n1_max_loading", "overload_sum", "worst_cont", "worst_mon", "island_flag", "n_island_cont"]
+    host_out = {n: torch.empty_like(getattr(res, n), device="cpu").pin_memory() for n in outs}
+    h2d = sum(t.numel() * t.element_size() for t in host_in.values())
+    d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for n in names:
+            getattr(db, n).copy_(host_in[n], non_blocking=True)
+        solver.solve(db, results=res)
+        for n in outs:
+            host_out[n].copy_(getattr(res, n), non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = time.perf_counter() - t0
+    return {"value": lf * steps / dt, "unit": "loadflows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", default="fp32,fp64")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * dcflow: batched DC loadflow over many grid topologies on one NVIDIA B300.
+ *
+ * Method: "Accelerated DC loadflow solver for topology optimization"
+ * (arXiv 2501.17529).  The reduced susceptance matrix of the base grid is
+ * factored once (Sec. II, Def. 2, Eq. (1)); every topology (bus splits, the
+ * busbar assignment t_b of Sec. III-A, and branch outages t_d) is then a
+ * rank-r correction of the base branch-to-branch factors, solved with one
+ * r x r FP64 system (the simultaneous form of the BSDF of Def. 5-6 / Eq. (7)
+ * and of the MODF of Def. 4).  N-0 flows follow Eq. (2), the full N-1 follows
+ * the LODF of Def. 3 / Eq. (5) evaluated on the updated factors, and every
+ * N-1 case is reduced on the fly to the maximum relative loading (agg_m of
+ * Sec. III-A), its arg-max and the overload sum, so the monitored x
+ * contingency matrix is never stored.  Optional injection candidates T_i are
+ * brute-forced per topology and timestep (Eq. (8), metric-first mode of
+ * Sec. III-C).
+ *
+ * Conventions for every entry point:
+ *  - returns DCFLOW_OK (0) or a negative DCFLOW_ERR_* code; no C++ exception
+ *    crosses this interface; dcflow_last_error() gives a message for the
+ *    calling thread's last failure;
+ *  - "host" pointers are read during the call and may be freed afterwards;
+ *    "device" pointers are CUDA device memory owned by the caller, read or
+ *    written asynchronously on the given stream;
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *  - one context must not be used from two host threads at the same time.
+ */
+#ifndef DCFLOW_H
+#define DCFLOW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dcflow_ctx dcflow_ctx;
+
+enum {
+  DCFLOW_OK = 0,
+  DCFLOW_ERR_INVALID_ARG = -1,      /* bad size, index, pointer or option */
+  DCFLOW_ERR_GRID_DISCONNECTED = -2,/* base grid not connected (setup) */
+  DCFLOW_ERR_OOM = -3,              /* device allocation failed */
+  DCFLOW_ERR_CUDA = -4,             /* a CUDA call failed */
+  DCFLOW_ERR_TIMEOUT = -5,          /* a bounded device wait expired */
+  DCFLOW_ERR_NO_STUDY = -6,         /* dcflow_solve_batch before dcflow_set_study */
+  DCFLOW_ERR_SINGULAR = -7          /* base factorisation lost positive definiteness */
+};
+
+/* Arithmetic form of the per-topology contractions and the N-1 reduction.
+ * The base factorisation, the r x r update systems and the N-1 denominators
+ * 1 - Phi_f[c,c] are FP64 in every form. */
+enum {
+  DCFLOW_FP64 = 0, /* everything FP64 */
+  DCFLOW_FP32 = 1  /* N-0 / N-1 contractions and reductions in FP32 */
+};
+
+typedef struct {
+  int32_t precision;     /* DCFLOW_FP64 or DCFLOW_FP32 */
+  int32_t device;        /* CUDA device ordinal; -1 = the current device */
+  int32_t chunk_topo;    /* topologies per internal chunk; 0 = automatic */
+  double island_tol;     /* pivot / denominator threshold for islanding; 0 = 1e-9 */
+} dcflow_options;
+
+/* Fill `opt` with the defaults (FP32 form, current device, automatic chunk, 1e-9). */
+void dcflow_default_options(dcflow_options* opt);
+
+/*
+ * Build a context for one grid and factor its reduced susceptance matrix.
+ * Sec. II, Def. 1 (C_w, B = C^T diag(b) C, parallel branches add up) and
+ * Def. 2 / Eq. (1) (slack removed, slack column of the PTDF zero).
+ *
+ * n_bus >= 2, n_branch >= 1; from/to: host int32[n_branch] bus indices
+ * (from != to); b: host double[n_branch] susceptances (> 0); slack in
+ * [0, n_bus).  `opt` may be NULL (defaults).  The base grid must be
+ * connected (DCFLOW_ERR_GRID_DISCONNECTED otherwise).  On success *out owns
+ * all device state; release it with dcflow_destroy.  Synchronous.
+ */
+int dcflow_setup(dcflow_ctx** out, int32_t n_bus, int32_t n_branch,
+                 const int32_t* from, const int32_t* to, const double* b,
+                 int32_t slack, const dcflow_options* opt);
+
+/*
+ * Rows of the base PTDF, Def. 2 / Eq. (1): out[i * n_bus + n] = PTDF[rows[i], n].
+ * rows: host int32[n_rows] branch indices; out: device double[n_rows * n_bus],
+ * row-major, caller-owned.  The slack column is 0.  Runs on `stream` and
+ * returns after enqueueing.
+ */
+int dcflow_base_ptdf(dcflow_ctx* ctx, const int32_t* rows, int32_t n_rows,
+                     double* out, void* stream);
+
+/*
+ * Bind the study sets that every later batch uses (PTDF row restriction of
+ * Sec. II: only monitored, contingency and switching branches are needed).
+ *
+ * mon: host int32[n_mon] monitored branches (distinct); cont: host
+ * int32[n_cont] N-1 contingency branches (distinct); limit: host
+ * double[n_branch] thermal limits (> 0 on monitored branches), loading
+ * rho = |flow| / limit.  split_bus: host int32[n_split_bus] substations that
+ * batches may split (NULL = every bus); outage_cand: host
+ * int32[n_outage_cand] branches batches may outage (NULL = every branch).
+ * Synchronous; may be called again to change the study.
+ */
+typedef struct {
+  const int32_t* mon;  int32_t n_mon;
+  const int32_t* cont; int32_t n_cont;
+  const double* limit;
+  const int32_t* split_bus;   int32_t n_split_bus;
+  const int32_t* outage_cand; int32_t n_outage_cand;
+} dcflow_study;
+
+int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* study);
+
+/*
+ * One batch of topologies (t_b, t_d of Sec. III-A) evaluated for every
+ * timestep, and optionally for every injection candidate (T_i, Eq. (8)).
+ * All arrays are device memory, caller-owned, read on `stream`.
+ *
+ *  split_ptr  int32[n_topo+1]   CSR offsets into split_sub / split_mask
+ *  split_sub  int32[]           substation (bus) split by each entry; at most
+ *                               once per topology; must be a split bus of the study
+ *  split_mask uint64[]          bit j = 1 moves the j-th incident branch of the
+ *                               substation (ascending branch id) to the new
+ *                               busbar B; a mask with an empty side is a no-op
+ *  out_ptr    int32[n_topo+1]   CSR offsets into out_branch
+ *  out_branch int32[]           outaged branches (t_d), distinct per topology
+ *  inj        double[n_time * n_bus]  nodal injections per timestep; the slack
+ *                               balances them (its PTDF column is zero)
+ *  var_*      optional (n_var = 0 disables): candidate u adds
+ *             var_delta[k] at bus var_bus[k] for k in [var_ptr[u], var_ptr[u+1])
+ *
+ * Per topology, effective splits + outages <= 16 and moved + outaged branches
+ * <= 256.  A topology that breaks a rule is flagged 2 (invalid) in
+ * island_flag, never faulted.
+ */
+typedef struct {
+  int32_t n_topo;
+  const int32_t* split_ptr;
+  const int32_t* split_sub;
+  const uint64_t* split_mask;
+  const int32_t* out_ptr;
+  const int32_t* out_branch;
+  int32_t n_time;
+  const double* inj;
+  int32_t n_var;
+  const int32_t* var_ptr;
+  const int32_t* var_bus;
+  const double* var_delta;
+} dcflow_batch;
+
+/*
+ * Caller-owned device outputs ([n_topo * n_time] arrays are topology-major).
+ *  n0_flow        double[n_topo * n_time * n_mon] N-0 flows (Eq. (2)), or NULL
+ *  n0_max_loading double[n_topo * n_time] max_l |p_n0| / limit, or NULL
+ *  n1_max_loading double[n_topo * n_time] max over monitored l and valid
+ *                 contingencies c of |p_n1[c][l]| / limit (agg_m)
+ *  overload_sum   double[n_topo * n_time] sum of max(0, rho - 1) over the same cases
+ *  worst_cont     int32[n_topo * n_time]  position in `cont` of the arg-max (ties:
+ *                 lowest position), -1 if no valid contingency
+ *  worst_mon      int32[n_topo * n_time]  position in `mon` of the arg-max (ties:
+ *                 lowest), -1 if none, or NULL
+ *  best_var       int32[n_topo * n_time]  chosen candidate (argmin of n1_max_loading,
+ *                 ties to the lowest index), or NULL; -1 without candidates
+ *  island_flag    uint8[n_topo]  0 ok, 1 the topology islands (outputs zero / -1),
+ *                 2 invalid topology input
+ *  n_island_cont  int32[n_topo]  contingencies skipped because they island
+ * Outaged monitored branches load 0; outaged contingencies are skipped.
+ */
+typedef struct {
+  double* n0_flow;
+  double* n0_max_loading;
+  double* n1_max_loading;
+  double* overload_sum;
+  int32_t* worst_cont;
+  int32_t* worst_mon;
+  int32_t* best_var;
+  uint8_t* island_flag;
+  int32_t* n_island_cont;
+} dcflow_results;
+
+/*
+ * Evaluate a batch.  Enqueues all work on `stream`; blocks the host only for
+ * one small device-to-host read of the per-rank topology histogram used to
+ * group topologies by rank (Sec. III-C batching without dummy padding).
+ * Scratch memory is allocated on first use and kept in the context.
+ */
+int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* batch,
+                       const dcflow_results* res, void* stream);
+
+/* Number of kernel launches issued by the last dcflow_solve_batch call. */
+int64_t dcflow_last_launch_count(const dcflow_ctx* ctx);
+
+/*
+ * Kernel timing.  dcflow_profile(ctx, 1) resets the counters and makes every
+ * later dcflow_solve_batch bracket each launch of the fused N-1 kernel with
+ * CUDA events recorded on the call's stream; dcflow_profile(ctx, 0) stops.
+ * dcflow_profile_read synchronises on the recorded events and returns the
+ * summed N-1 kernel time in milliseconds and the number of such launches.
+ */
+int dcflow_profile(dcflow_ctx* ctx, int32_t enable);
+int dcflow_profile_read(dcflow_ctx* ctx, double* n1_ms, int64_t* n1_launches);
+
+void dcflow_destroy(dcflow_ctx* ctx);
+const char* dcflow_strerror(int code);
+const char* dcflow_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCFLOW_H */

@@ -333,7 +333,7 @@ def _flows_from_angles(th, f2, t2, b, alive):
 # ---------------------------------------------------------------------------
 
 def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
-                      var=None, mode="lodf", want_flows=False):
+                      var=None, mode="lodf", want_flows=False, want_cmax=False):
     """Outputs of one topology for every timestep (and variation).
 
     P: [T, V] injections.  var: (var_ptr, var_bus, var_delta) or None.
@@ -349,6 +349,8 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
                best_var=-np.ones(T, np.int64), n_valid_cont=0)
     if want_flows:
         res["n0_flow"] = np.zeros((T, M))
+    if want_cmax:
+        res["cmax"] = -np.ones((T, C))  # per contingency: max_l rho (-1 if skipped)
     st, n, f2, t2, alive, k_eff = build_topology(V, f, t, inc, splits, outages)
     if st != OK:
         res["status"] = st
@@ -412,7 +414,7 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
         n0r = np.abs(p[mon]) / lim_mon
         n0m = float(n0r.max()) if M else 0.0
         if vc.size == 0:
-            return n0m, 0.0, 0.0, -1, -1
+            return n0m, 0.0, 0.0, -1, -1, None
         n1 = n1_block(p, pinj)
         rho = np.abs(n1) / lim_mon[:, None]
         rho[diag_mask] = 0.0
@@ -422,7 +424,7 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
         k = int(np.argmax(flat))
         jc, im = divmod(k, M)
         ovl = float(np.maximum(rho - 1.0, 0.0).sum())
-        return n0m, float(flat[k]), ovl, int(vj[jc]), int(im)
+        return n0m, float(flat[k]), ovl, int(vj[jc]), int(im), rho.max(axis=0)
 
     for ti in range(T):
         if not nvar:
@@ -443,11 +445,13 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
                 res["n0_flow"][ti] = p[mon]
         res["n0_max"][ti], res["n1_max"][ti], res["ovl"][ti] = r[0], r[1], r[2]
         res["worst_cont"][ti], res["worst_mon"][ti] = r[3], r[4]
+        if want_cmax and r[5] is not None:
+            res["cmax"][ti, vj] = r[5]
     return res
 
 
 def evaluate(grid, topo, P, mon, cont, limit, var=None, mode="lodf", idx=None,
-             want_flows=False):
+             want_flows=False, want_cmax=False):
     """Evaluate a batch of topologies (or the subset ``idx``); arrays per topology."""
     inc = incident_lists(grid.n_bus, grid.f, grid.t)
     P = np.atleast_2d(np.asarray(P, np.float64))
@@ -462,7 +466,7 @@ def evaluate(grid, topo, P, mon, cont, limit, var=None, mode="lodf", idx=None,
         a, c = topo.out_ptr[i], topo.out_ptr[i + 1]
         outages = list(topo.out_branch[a:c])
         outs.append(evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
-                                      vtuple, mode, want_flows))
+                                      vtuple, mode, want_flows, want_cmax))
     keys = ["n0_max", "n1_max", "ovl", "worst_cont", "worst_mon", "best_var"]
     r = {k: np.stack([o[k] for o in outs]) if outs else np.zeros((0, P.shape[0])) for k in keys}
     r["status"] = np.array([o["status"] for o in outs], np.int64)
@@ -470,7 +474,18 @@ def evaluate(grid, topo, P, mon, cont, limit, var=None, mode="lodf", idx=None,
     r["n_valid_cont"] = np.array([o["n_valid_cont"] for o in outs], np.int64)
     if want_flows:
         r["n0_flow"] = np.stack([o["n0_flow"] for o in outs]) if outs else np.zeros((0, P.shape[0], len(mon)))
+    if want_cmax:
+        r["cmax"] = np.stack([o["cmax"] for o in outs]) if outs else np.zeros((0, P.shape[0], len(cont)))
     return r
+
+
+def n1_loading_column(grid, splits, outages, P_t, mon, c_branch, limit):
+    """|p_n1| / limit over the monitored branches for one contingency branch, by
+    refactorisation of the topology without it (None if it islands)."""
+    fl, info = topology_flows(grid, splits, list(outages) + [int(c_branch)], P_t)
+    if fl is None:
+        return None
+    return np.abs(fl[np.asarray(mon)]) / np.asarray(limit)[np.asarray(mon)]
 
 
 def base_flows(grid, P):

@@ -1,0 +1,65 @@
+// Context lifetime, error strings and device-buffer helpers of the C ABI.
+#include <string>
+
+#include "internal.cuh"
+
+namespace dcf {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int DevBuf::ensure(size_t need) {
+  if (need <= bytes && p) return 0;
+  release();
+  if (need == 0) need = 1;
+  if (cudaMalloc(&p, need) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    bytes = 0;
+    set_error("device allocation of " + std::to_string(need) + " bytes failed");
+    return DCFLOW_ERR_OOM;
+  }
+  bytes = need;
+  return 0;
+}
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+}  // namespace dcf
+
+extern "C" void dcflow_destroy(dcflow_ctx* ctx) {
+  if (!ctx) return;
+  dcf::DevBuf* bufs[] = {&ctx->f, &ctx->t, &ctx->b, &ctx->inc_ptr, &ctx->inc_list, &ctx->rid, &ctx->L, &ctx->info,
+                         &ctx->nidx, &ctx->split_ok, &ctx->monN, &ctx->contN, &ctx->cpos_of_mon, &ctx->mpos_of_cont,
+                         &ctx->inv_lim, &ctx->PhiN, &ctx->PtdfN, &ctx->PhiMC, &ctx->Y, &ctx->p0, &ctx->dp,
+                         &ctx->rank, &ctx->status, &ctx->perm, &ctx->hist, &ctx->hist_host, &ctx->ent_n, &ctx->ent_s,
+                         &ctx->ent_w, &ctx->mod_ptr, &ctx->q_info, &ctx->Kinv, &ctx->alpha, &ctx->Vt64, &ctx->VtR,
+                         &ctx->Zs, &ctx->ptil, &ctx->rowmul, &ctx->diagv, &ctx->s, &ctx->valid, &ctx->nisl,
+                         &ctx->pmax, &ctx->parg, &ctx->povl, &ctx->vmax, &ctx->Gs, &ctx->Gc};
+  for (auto* b : bufs) b->release();
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+  delete ctx;
+}
+
+extern "C" int64_t dcflow_last_launch_count(const dcflow_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" const char* dcflow_strerror(int code) {
+  switch (code) {
+    case DCFLOW_OK: return "ok";
+    case DCFLOW_ERR_INVALID_ARG: return "invalid argument";
+    case DCFLOW_ERR_GRID_DISCONNECTED: return "base grid is not connected";
+    case DCFLOW_ERR_OOM: return "device memory exhausted";
+    case DCFLOW_ERR_CUDA: return "CUDA error";
+    case DCFLOW_ERR_TIMEOUT: return "bounded device wait expired";
+    case DCFLOW_ERR_NO_STUDY: return "no study bound to the context";
+    case DCFLOW_ERR_SINGULAR: return "base susceptance matrix is not positive definite";
+    default: return "unknown error";
+  }
+}
+
+extern "C" const char* dcflow_last_error(void) { return dcf::g_last_error.c_str(); }

@@ -1,0 +1,89 @@
+// Internal declarations shared by the dcflow translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dcflow.h"
+
+namespace dcf {
+
+constexpr int kNB = 64;          // dense FP64 block size (factor and solves)
+constexpr int kRMax = 16;        // largest rank r = effective splits + outages
+constexpr int kEntMax = 256;     // moved + outaged branches per topology
+constexpr int kTMaxPass = 32;    // timesteps handled by one N-1 pass
+
+void set_error(const std::string& msg);
+
+#define DCF_CUDA(call)                                                          \
+  do {                                                                          \
+    cudaError_t e__ = (call);                                                   \
+    if (e__ != cudaSuccess) {                                                   \
+      ::dcf::set_error(std::string(#call) + ": " + cudaGetErrorString(e__));    \
+      return DCFLOW_ERR_CUDA;                                                   \
+    }                                                                           \
+  } while (0)
+
+#define DCF_CHECK_LAUNCH()                                                      \
+  do {                                                                          \
+    cudaError_t e__ = cudaGetLastError();                                       \
+    if (e__ != cudaSuccess) {                                                   \
+      ::dcf::set_error(std::string("kernel launch: ") + cudaGetErrorString(e__)); \
+      return DCFLOW_ERR_CUDA;                                                   \
+    }                                                                           \
+  } while (0)
+
+// Device buffer that grows on demand and is freed with the context.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need);  // 0 or DCFLOW_ERR_OOM
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace dcf
+
+struct dcflow_ctx {
+  dcflow_options opt{};
+  int dev = 0;
+  // grid
+  int V = 0, E = 0, slack = 0;
+  int n = 0, npad = 0;  // reduced size V-1 and its padding to the block size
+  std::vector<int> hf, ht;
+  std::vector<double> hb;
+  std::vector<int> h_inc_ptr, h_inc_list;
+  dcf::DevBuf f, t, b, inc_ptr, inc_list, rid, L, info;
+  // study
+  bool has_study = false;
+  int M = 0, C = 0, NN = 0;  // monitored, contingencies, needed rows
+  std::vector<int> h_mon, h_cont, h_N, h_nidx;
+  dcf::DevBuf nidx;        // int[E]: branch -> needed-row index or -1
+  dcf::DevBuf split_ok;    // uint8[V]
+  dcf::DevBuf monN, contN; // int[M], int[C]: needed-row index of mon / cont
+  dcf::DevBuf cpos_of_mon; // int[M]: position in cont of the same branch or -1
+  dcf::DevBuf mpos_of_cont;// int[C]: position in mon of the same branch or -1
+  dcf::DevBuf inv_lim;     // double[M]
+  dcf::DevBuf PhiN;        // double[NN*NN] base branch-to-branch factors
+  dcf::DevBuf PtdfN;       // double[NN*V] base PTDF rows of the needed branches
+  dcf::DevBuf PhiMC;       // Real[M*C] Phi[mon, cont] / limit[mon]
+  dcf::DevBuf Y;           // solve workspace
+  // batch scratch
+  dcf::DevBuf p0;          // double[NN*T]
+  dcf::DevBuf dp;          // double[NN*U] base flow change of each candidate
+  dcf::DevBuf rank, status, perm, hist, hist_host;
+  dcf::DevBuf ent_n, ent_s, ent_w, mod_ptr, q_info;
+  dcf::DevBuf Kinv, alpha, Vt64, VtR, Zs, ptil, rowmul, diagv, s, valid, nisl;
+  dcf::DevBuf pmax, parg, povl, vmax, Gs, Gc;
+  int64_t launches = 0;
+  int64_t chunk_cap = 0;
+  // kernel timing (dcflow_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop) per N-1 launch
+  size_t prof_used = 0;
+};

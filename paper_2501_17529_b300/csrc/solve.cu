@@ -1,0 +1,955 @@
+// Per-batch path of dcflow_solve_batch.
+//
+// Every topology tau (splits t_b and outages t_d, Sec. III-A) is expressed as
+// r = k_s + k_o modifications of the base grid.  Modification j injects a
+// fictitious transfer into the base network:
+//   split j  (substation A, moved set M_j, beta_j = sum_{M_j} b):
+//            W[:, j] = sigma_m b_m / beta_j on the moved branches m, Sigma[:, j] = sigma_m
+//            (sigma_m = +1 if the from end of m moves to the new busbar, else -1);
+//   outage c: W[:, j] = Sigma[:, j] = e_c.
+// With the base branch-to-branch factors Phi[l, c] = PTDF[l, f_c] - PTDF[l, t_c]
+// (the LODF numerator of Def. 3):
+//   Z = (I - Phi) W,  K = Sigma^T Z   (r x r, FP64),
+//   p_f = p0 - Z K^{-1} Sigma^T p0                      (N-0 flows, Eq. (2)),
+//   Phi_f[:, c] = Phi[:, c] - Z K^{-1} (Sigma^T Phi[:, c] - s_c)
+// where s_c[j] = sigma of c in split j (0 for outage rows).  This is the
+// simultaneous form of the BSDF update (Def. 5-6, Eq. (7)) and of the MODF
+// (Def. 4): K = Sigma^T (I - Phi) W generalises both denominators, its
+// natural-order LU pivots are the sequential BSDF / LODF denominators
+// (in [0, 1], zero exactly when the topology islands), and the outaged rows
+// of p_f vanish (the MODF rows O := -I).  The N-1 of the updated topology then
+// follows Def. 3 / Eq. (5):
+//   p_n1[c][l] = p_f[l] + Phi_f[l, c] p_f[c] / (1 - Phi_f[c, c]),  LODF[c, c] = -1,
+// reduced on the fly to max |p_n1| / limit (agg_m), its arg-max and the
+// overload sum.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace dcf {
+
+enum : int { ST_OK = 0, ST_ISLAND = 1, ST_INVALID = 2 };
+
+struct QInfo {
+  int tau, r, ks, status;
+};
+
+struct GridDev {
+  const int *f, *t;
+  const double* b;
+  const int *inc_ptr, *inc_list, *nidx;
+  const uint8_t* split_ok;
+  int V, E;
+};
+
+struct BatchDev {
+  const int *split_ptr, *split_sub;
+  const uint64_t* split_mask;
+  const int *out_ptr, *out_branch;
+};
+
+struct Args {
+  // study
+  int M, C, NN, T, U;
+  const int *monN, *contN, *cpos, *mpos;
+  const double *inv_lim, *PhiN;
+  const void* PhiMC;
+  const double* p0;  // [NN][T]
+  double tol;
+  // chunk
+  int nq;
+  QInfo* qi;
+  int* ent_n;
+  int8_t* ent_s;
+  double* ent_w;
+  int16_t* mod_ptr;
+  double *Kinv, *alpha, *Vt64;
+  void *VtR, *Zs, *ptil, *rowmul, *diagv, *s;
+  uint8_t* valid;
+  int* nisl;
+  void* pmax;
+  int* parg;
+  double* povl;
+  int ncb;
+  // outputs
+  dcflow_results out;
+};
+
+// ---------------------------------------------------------------------------
+// decode: topology vectors -> modification list
+// ---------------------------------------------------------------------------
+template <bool WRITE>
+__device__ int decode_topology(const GridDev& g, const BatchDev& in, int tau, int* r_out, int* ks_out, int* en,
+                               int8_t* es, double* ew, int16_t* mp) {
+  const int s0 = in.split_ptr[tau], s1 = in.split_ptr[tau + 1];
+  const int o0 = in.out_ptr[tau], o1 = in.out_ptr[tau + 1];
+  *r_out = 0;
+  *ks_out = 0;
+  if (s1 < s0 || o1 < o0) return ST_INVALID;
+  int r = 0, ne = 0;
+  for (int k = s0; k < s1; ++k) {
+    const int A = in.split_sub[k];
+    if (A < 0 || A >= g.V || !g.split_ok[A]) return ST_INVALID;
+    for (int k2 = s0; k2 < k; ++k2)
+      if (in.split_sub[k2] == A) return ST_INVALID;
+    const uint64_t m = in.split_mask[k];
+    const int p0 = g.inc_ptr[A], deg = g.inc_ptr[A + 1] - p0;
+    if (deg > 64 || (deg < 64 && (m >> deg) != 0)) return ST_INVALID;
+    const int nb = __popcll(m);
+    if (nb == 0 || nb == deg) continue;  // one busbar empty: no split
+    if (r >= kRMax || ne + nb > kEntMax) return ST_INVALID;
+    double beta = 0.0;
+    for (int j = 0; j < deg; ++j)
+      if ((m >> j) & 1ull) {
+        const int l = g.inc_list[p0 + j];
+        if (g.nidx[l] < 0) return ST_INVALID;
+        beta += g.b[l];
+      }
+    if (WRITE) mp[r] = (int16_t)ne;
+    for (int j = 0; j < deg; ++j)
+      if ((m >> j) & 1ull) {
+        const int l = g.inc_list[p0 + j];
+        const int sg = (g.f[l] == A) ? 1 : -1;
+        if (WRITE) {
+          en[ne] = g.nidx[l];
+          es[ne] = (int8_t)sg;
+          ew[ne] = sg * g.b[l] / beta;
+        }
+        ++ne;
+      }
+    ++r;
+  }
+  const int ks = r;
+  for (int k = o0; k < o1; ++k) {
+    const int c = in.out_branch[k];
+    if (c < 0 || c >= g.E || g.nidx[c] < 0) return ST_INVALID;
+    for (int k2 = o0; k2 < k; ++k2)
+      if (in.out_branch[k2] == c) return ST_INVALID;
+    if (r >= kRMax || ne >= kEntMax) return ST_INVALID;
+    if (WRITE) {
+      mp[r] = (int16_t)ne;
+      en[ne] = g.nidx[c];
+      es[ne] = 1;
+      ew[ne] = 1.0;
+    }
+    ++ne;
+    ++r;
+  }
+  if (WRITE) mp[r] = (int16_t)ne;
+  *r_out = r;
+  *ks_out = ks;
+  return ST_OK;
+}
+
+__global__ void k_rank(GridDev g, BatchDev in, int n_topo, int8_t* rank) {
+  const int tau = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tau >= n_topo) return;
+  int r, ks;
+  int st = decode_topology<false>(g, in, tau, &r, &ks, nullptr, nullptr, nullptr, nullptr);
+  rank[tau] = (int8_t)(st == ST_OK ? r : -1);
+}
+
+__global__ void k_decode(GridDev g, BatchDev in, const int* perm, Args a) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.nq) return;
+  const int tau = perm[q];
+  int r, ks;
+  int st = decode_topology<true>(g, in, tau, &r, &ks, a.ent_n + (size_t)q * kEntMax, a.ent_s + (size_t)q * kEntMax,
+                                 a.ent_w + (size_t)q * kEntMax, a.mod_ptr + (size_t)q * (kRMax + 1));
+  QInfo qi;
+  qi.tau = tau;
+  qi.r = r;
+  qi.ks = ks;
+  qi.status = st;
+  a.qi[q] = qi;
+}
+
+// ---------------------------------------------------------------------------
+// base flows p0 = PTDF[N, :] P_t (Eq. (2)), one warp per needed branch
+// ---------------------------------------------------------------------------
+__global__ void k_p0(int NN, int V, int T, const double* __restrict__ ptdf, const double* __restrict__ inj,
+                     double* __restrict__ p0) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= NN) return;
+  const double* row = ptdf + (size_t)warp * V;
+  for (int t0 = 0; t0 < T; t0 += 8) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int n = lane; n < V; n += 32) {
+      const double pv = row[n];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (t0 + k < T) acc[k] = fma(pv, inj[(size_t)(t0 + k) * V + n], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      double v = acc[k];
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && t0 + k < T) p0[(size_t)warp * T + t0 + k] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// r x r system per topology: K, natural-order LU (pivot test), K^{-1},
+// alpha = K^{-1} Sigma^T p0, Vt = K^{-1} (Sigma^T Phi[:, cont] - s)
+// ---------------------------------------------------------------------------
+struct EntSmem {
+  int en[kEntMax];
+  double ew[kEntMax];
+  int8_t es[kEntMax];
+  int mp[kRMax + 1];
+};
+
+__device__ void load_entries(EntSmem& S, const Args& a, int q, int r) {
+  for (int i = threadIdx.x; i <= r; i += blockDim.x) S.mp[i] = a.mod_ptr[(size_t)q * (kRMax + 1) + i];
+  __syncthreads();
+  const int ne = S.mp[r];
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    S.en[e] = a.ent_n[(size_t)q * kEntMax + e];
+    S.ew[e] = a.ent_w[(size_t)q * kEntMax + e];
+    S.es[e] = a.ent_s[(size_t)q * kEntMax + e];
+  }
+  __syncthreads();
+}
+
+// Z[row, j] = W[row, j] - sum_{q in mod j} w_q Phi[row, m_q]  (FP64)
+__device__ __forceinline__ double z_entry(const EntSmem& S, const double* PhiRow, int row, int j) {
+  double z = 0.0;
+  for (int e = S.mp[j]; e < S.mp[j + 1]; ++e) {
+    const int m = S.en[e];
+    const double w = S.ew[e];
+    z = fma(-w, PhiRow[m], z);
+    if (m == row) z += w;
+  }
+  return z;
+}
+
+template <class Real>
+__global__ __launch_bounds__(128) void k_small(Args a) {
+  const int q = blockIdx.x;
+  __shared__ EntSmem S;
+  __shared__ double K[kRMax][kRMax + 1];
+  __shared__ double Ki[kRMax][kRMax + 1];
+  __shared__ int bad;
+  const QInfo qi = a.qi[q];
+  if (qi.status != ST_OK) return;
+  const int r = qi.r, ks = qi.ks, tid = threadIdx.x;
+  load_entries(S, a, q, r);
+  for (int p = tid; p < r * r; p += blockDim.x) {
+    const int i = p / r, j = p % r;
+    double acc = 0.0;
+    for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
+      const int m = S.en[e];
+      acc = fma((double)S.es[e], z_entry(S, a.PhiN + (size_t)m * a.NN, m, j), acc);
+    }
+    K[i][j] = acc;
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  if (tid < 32) {
+    int isl = 0;
+    for (int k = 0; k < r; ++k) {
+      const double piv = K[k][k];
+      if (!(fabs(piv) > a.tol)) {
+        isl = 1;
+        break;
+      }
+      __syncwarp();
+      const int i = tid;
+      if (i > k && i < r) {
+        const double fct = K[i][k] / piv;
+        K[i][k] = fct;
+        for (int j = k + 1; j < r; ++j) K[i][j] = fma(-fct, K[k][j], K[i][j]);
+      }
+      __syncwarp();
+    }
+    if (!isl && tid < r) {
+      const int j = tid;
+      double y[kRMax];
+#pragma unroll
+      for (int i = 0; i < kRMax; ++i) {
+        if (i < r) {
+          double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+          for (int p = 0; p < kRMax; ++p)
+            if (p < i) s = fma(-K[i][p], y[p], s);
+          y[i] = s;
+        }
+      }
+#pragma unroll
+      for (int i = kRMax - 1; i >= 0; --i) {
+        if (i < r) {
+          double s = y[i];
+#pragma unroll
+          for (int p = 0; p < kRMax; ++p)
+            if (p > i && p < r) s = fma(-K[i][p], y[p], s);
+          y[i] = s / K[i][i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kRMax; ++i)
+        if (i < r) Ki[i][j] = y[i];
+    }
+    if (tid == 0) bad = isl;
+  }
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) a.qi[q].status = ST_ISLAND;
+    return;
+  }
+  double* Kinv = a.Kinv + (size_t)q * kRMax * kRMax;
+  for (int p = tid; p < kRMax * kRMax; p += blockDim.x) {
+    const int i = p / kRMax, j = p % kRMax;
+    Kinv[p] = (i < r && j < r) ? Ki[i][j] : 0.0;
+  }
+  // alpha[j][t]
+  const int T = a.T;
+  for (int t = tid; t < T; t += blockDim.x) {
+    double bv[kRMax];
+#pragma unroll
+    for (int i = 0; i < kRMax; ++i) {
+      double acc = 0.0;
+      if (i < r)
+        for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) acc = fma((double)S.es[e], a.p0[(size_t)S.en[e] * T + t], acc);
+      bv[i] = acc;
+    }
+#pragma unroll
+    for (int j = 0; j < kRMax; ++j) {
+      double x = 0.0;
+#pragma unroll
+      for (int i = 0; i < kRMax; ++i)
+        if (i < r && j < r) x = fma(Ki[j][i], bv[i], x);
+      a.alpha[((size_t)q * kRMax + j) * T + t] = x;
+    }
+  }
+  // Vt[j][c]
+  const int C = a.C;
+  Real* VtR = static_cast<Real*>(a.VtR);
+  for (int c = tid; c < C; c += blockDim.x) {
+    const int nc = a.contN[c];
+    double v[kRMax];
+#pragma unroll
+    for (int i = 0; i < kRMax; ++i) {
+      double acc = 0.0;
+      if (i < r)
+        for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
+          const int m = S.en[e];
+          acc = fma((double)S.es[e], a.PhiN[(size_t)m * a.NN + nc], acc);
+          if (i < ks && m == nc) acc -= (double)S.es[e];
+        }
+      v[i] = acc;
+    }
+#pragma unroll
+    for (int j = 0; j < kRMax; ++j) {
+      double x = 0.0;
+#pragma unroll
+      for (int i = 0; i < kRMax; ++i)
+        if (i < r && j < r) x = fma(Ki[j][i], v[i], x);
+      const size_t o = ((size_t)q * kRMax + j) * C + c;
+      a.Vt64[o] = x;
+      VtR[o] = (Real)x;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// rows: Z, N-0 flows, scaled operands of the N-1 kernel, FP64 denominators
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ __launch_bounds__(128) void k_rows(Args a) {
+  const int q = blockIdx.x;
+  __shared__ EntSmem S;
+  __shared__ int outN[kRMax];
+  __shared__ int nout;
+  __shared__ int nisl;
+  extern __shared__ unsigned char dyn[];
+  Real* alph = reinterpret_cast<Real*>(dyn);  // [kRMax][T]
+  const QInfo qi = a.qi[q];
+  if (qi.status != ST_OK) return;
+  const int r = qi.r, ks = qi.ks, tid = threadIdx.x, T = a.T, M = a.M, C = a.C, NN = a.NN;
+  load_entries(S, a, q, r);
+  if (tid == 0) {
+    nout = r - ks;
+    nisl = 0;
+  }
+  for (int i = tid; i < r - ks; i += blockDim.x) outN[i] = S.en[S.mp[ks + i]];
+  for (int p = tid; p < kRMax * T; p += blockDim.x) alph[p] = (Real)a.alpha[(size_t)q * kRMax * T + p];
+  __syncthreads();
+  Real* Zs = static_cast<Real*>(a.Zs) + (size_t)q * M * kRMax;
+  Real* ptil = static_cast<Real*>(a.ptil) + (size_t)q * M * T;
+  Real* rowmul = static_cast<Real*>(a.rowmul) + (size_t)q * M;
+  Real* diagv = static_cast<Real*>(a.diagv) + (size_t)q * M;
+  Real* sv = static_cast<Real*>(a.s) + (size_t)q * T * C;
+  const int tau = qi.tau;
+  for (int l = tid; l < M; l += blockDim.x) {
+    const int nl = a.monN[l];
+    bool outd = false;
+    for (int k = 0; k < nout; ++k) outd |= (outN[k] == nl);
+    const double* prow = a.PhiN + (size_t)nl * NN;
+    Real z[kRMax];
+#pragma unroll
+    for (int j = 0; j < kRMax; ++j) z[j] = (j < r) ? (Real)z_entry(S, prow, nl, j) : (Real)0;
+    const Real il = (Real)a.inv_lim[l];
+#pragma unroll
+    for (int j = 0; j < kRMax; ++j) Zs[(size_t)l * kRMax + j] = outd ? (Real)0 : z[j] * il;
+    rowmul[l] = outd ? (Real)0 : (Real)1;
+    diagv[l] = (Real)0;
+    for (int t = 0; t < T; ++t) {
+      Real pf = (Real)a.p0[(size_t)nl * T + t];
+#pragma unroll
+      for (int j = 0; j < kRMax; ++j) pf = fma(-z[j], alph[j * T + t], pf);
+      ptil[(size_t)l * T + t] = outd ? (Real)0 : pf * il;
+      if (a.out.n0_flow) a.out.n0_flow[((size_t)tau * T + t) * M + l] = outd ? 0.0 : (double)pf;
+    }
+  }
+  __syncthreads();
+  const double* Vt64 = a.Vt64 + (size_t)q * kRMax * C;
+  int my_isl = 0;
+  for (int c = tid; c < C; c += blockDim.x) {
+    const int nc = a.contN[c];
+    bool outd = false;
+    for (int k = 0; k < nout; ++k) outd |= (outN[k] == nc);
+    const double* prow = a.PhiN + (size_t)nc * NN;
+    double z[kRMax];
+#pragma unroll
+    for (int j = 0; j < kRMax; ++j) z[j] = (j < r) ? z_entry(S, prow, nc, j) : 0.0;
+    double phicc = prow[nc];
+#pragma unroll
+    for (int j = 0; j < kRMax; ++j) phicc = fma(-z[j], Vt64[(size_t)j * C + c], phicc);
+    const double den = 1.0 - phicc;
+    const bool ok = !outd && den > a.tol;
+    my_isl += (!outd && !ok);
+    a.valid[(size_t)q * C + c] = ok;
+    const int mp = a.mpos[c];
+    if (mp >= 0) diagv[mp] = (Real)(-den * a.inv_lim[mp]);
+    const double invd = ok ? 1.0 / den : 0.0;
+    for (int t = 0; t < T; ++t) {
+      Real pf = (Real)a.p0[(size_t)nc * T + t];
+#pragma unroll
+      for (int j = 0; j < kRMax; ++j) pf = fma(-(Real)z[j], alph[j * T + t], pf);
+      sv[(size_t)t * C + c] = (Real)((double)pf * invd);
+    }
+  }
+  if (my_isl) atomicAdd(&nisl, my_isl);
+  __syncthreads();
+  if (tid == 0) a.nisl[q] = nisl;
+  // N-0 maximum loading per timestep
+  if (a.out.n0_max_loading) {
+    __shared__ double red[4];
+    for (int t = 0; t < T; ++t) {
+      double m = 0.0;
+      for (int l = tid; l < M; l += blockDim.x) m = fmax(m, (double)fabs((double)ptil[(size_t)l * T + t]));
+      for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if ((tid & 31) == 0) red[tid >> 5] = m;
+      __syncthreads();
+      if (tid == 0) {
+        double x = red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = fmax(x, red[w]);
+        a.out.n0_max_loading[(size_t)tau * T + t] = x;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused N-1 (Def. 3, Eq. (5)) with in-register max / overload reduction
+// ---------------------------------------------------------------------------
+template <class Real>
+struct Acc;
+
+template <>
+struct Acc<float> {
+  // overload term via a saturating FMA: sat((|v| - 1) 2^-20) = max(0, |v| - 1) 2^-20 for |v| < 2^20 + 1
+  static __device__ __forceinline__ void add(float& mx, float& ov, float v) {
+    const float av = fabsf(v);
+    mx = fmaxf(mx, av);
+    ov += __saturatef(fmaf(av, 0x1p-20f, -0x1p-20f));
+  }
+  static __device__ __forceinline__ double ovl_scale() { return 1048576.0; }
+};
+
+template <>
+struct Acc<double> {
+  static __device__ __forceinline__ void add(double& mx, double& ov, double v) {
+    const double av = fabs(v);
+    mx = fmax(mx, av);
+    ov += fmax(av - 1.0, 0.0);
+  }
+  static __device__ __forceinline__ double ovl_scale() { return 1.0; }
+};
+
+// Phi_f[l, c] / limit_l for one (l, c): shared by the N-1 kernel and the
+// final arg-max pass so both see bit-identical values.
+template <class Real, int RMAX>
+__device__ __forceinline__ Real phi_entry(Real base, const Real* zrow, const Real* vt, Real rm, int cp, int c, Real dg) {
+  Real p = base;
+#pragma unroll
+  for (int j = 0; j < RMAX; ++j) p = fma(-zrow[j], vt[j], p);
+  p = p * rm;
+  return (cp == c) ? dg : p;
+}
+
+template <class Real, int TT, int RMAX, int LT>
+__global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
+  const int q = blockIdx.y;
+  const QInfo qi = a.qi[q];
+  if (qi.status != ST_OK) return;
+  const int tid = threadIdx.x, M = a.M, C = a.C, T = a.T;
+  const int c = blockIdx.x * 64 + tid;
+  const bool cin = c < C;
+  const int cc = cin ? c : C - 1;
+  __shared__ Real zs[LT][RMAX];
+  __shared__ Real pt[LT][TT];
+  __shared__ Real dg[LT], rm[LT];
+  __shared__ int cp[LT];
+  const Real* PhiMC = static_cast<const Real*>(a.PhiMC);
+  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * M * kRMax;
+  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * M * T;
+  const Real* rowmul = static_cast<const Real*>(a.rowmul) + (size_t)q * M;
+  const Real* diagv = static_cast<const Real*>(a.diagv) + (size_t)q * M;
+  const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
+  const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
+  Real vt[RMAX];
+#pragma unroll
+  for (int j = 0; j < RMAX; ++j) vt[j] = VtR[(size_t)j * C + cc];
+  Real s[TT], mx[TT], ov[TT];
+#pragma unroll
+  for (int t = 0; t < TT; ++t) {
+    s[t] = (cin && t0 + t < T) ? sv[(size_t)(t0 + t) * C + cc] : (Real)0;
+    mx[t] = 0;
+    ov[t] = 0;
+  }
+  for (int l0 = 0; l0 < M; l0 += LT) {
+    __syncthreads();
+    for (int idx = tid; idx < LT * RMAX; idx += 64) {
+      const int i = idx / RMAX, j = idx % RMAX, l = l0 + i;
+      zs[i][j] = (l < M) ? Zs[(size_t)l * kRMax + j] : (Real)0;
+    }
+    for (int idx = tid; idx < LT * TT; idx += 64) {
+      const int i = idx / TT, t = idx % TT, l = l0 + i;
+      pt[i][t] = (l < M && t0 + t < T) ? ptil[(size_t)l * T + t0 + t] : (Real)0;
+    }
+    for (int i = tid; i < LT; i += 64) {
+      const int l = l0 + i;
+      dg[i] = (l < M) ? diagv[l] : (Real)0;
+      rm[i] = (l < M) ? rowmul[l] : (Real)0;
+      cp[i] = (l < M) ? a.cpos[l] : -1;
+    }
+    __syncthreads();
+    Real phi[LT];
+#pragma unroll
+    for (int i = 0; i < LT; ++i) {
+      const int l = l0 + i;
+      const Real base = (l < M) ? PhiMC[(size_t)l * C + cc] : (Real)0;
+      phi[i] = phi_entry<Real, RMAX>(base, zs[i], vt, rm[i], cp[i], c, dg[i]);
+    }
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+      const Real st = s[t];
+#pragma unroll
+      for (int i = 0; i < LT; ++i) Acc<Real>::add(mx[t], ov[t], fma(phi[i], st, pt[i][t]));
+    }
+  }
+  // reduce the 64 contingencies of this block: max (ties: lowest c) and overload sum
+  const bool ok = cin && a.valid[(size_t)q * C + c];
+  __shared__ double rv[2], ro[2];
+  __shared__ int ra[2];
+  const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+  for (int t = 0; t < TT; ++t) {
+    if (t0 + t < T) {  // uniform over the block
+      double v = ok ? (double)mx[t] : -1.0;
+      int arg = ok ? c : 0x7fffffff;
+      double o = ok ? (double)ov[t] * Acc<Real>::ovl_scale() : 0.0;
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+        const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
+        o += __shfl_xor_sync(0xffffffffu, o, off);
+        if (v2 > v || (v2 == v && a2 < arg)) {
+          v = v2;
+          arg = a2;
+        }
+      }
+      if (lane == 0) {
+        rv[w] = v;
+        ra[w] = arg;
+        ro[w] = o;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double bv = rv[0];
+        int ba = ra[0];
+        if (rv[1] > bv || (rv[1] == bv && ra[1] < ba)) {
+          bv = rv[1];
+          ba = ra[1];
+        }
+        const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + blockIdx.x;
+        static_cast<Real*>(a.pmax)[o2] = (Real)bv;
+        a.parg[o2] = (bv < 0.0) ? -1 : ba;
+        a.povl[o2] = ro[0] + ro[1];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// final: combine the contingency blocks, locate the worst monitored branch,
+// write the outputs of every topology of the chunk
+// ---------------------------------------------------------------------------
+template <class Real, int RMAX>
+__global__ __launch_bounds__(128) void k_final(Args a) {
+  const int q = blockIdx.x;
+  const QInfo qi = a.qi[q];
+  const int tau = qi.tau, T = a.T, M = a.M, C = a.C, tid = threadIdx.x;
+  const dcflow_results& o = a.out;
+  if (tid == 0) {
+    o.island_flag[tau] = (uint8_t)qi.status;
+    o.n_island_cont[tau] = (qi.status == ST_OK) ? a.nisl[q] : 0;
+  }
+  if (qi.status != ST_OK) {
+    for (int t = tid; t < T; t += blockDim.x) {
+      const size_t k = (size_t)tau * T + t;
+      o.n1_max_loading[k] = 0.0;
+      o.overload_sum[k] = 0.0;
+      o.worst_cont[k] = -1;
+      if (o.worst_mon) o.worst_mon[k] = -1;
+      if (o.best_var) o.best_var[k] = -1;
+      if (o.n0_max_loading) o.n0_max_loading[k] = 0.0;
+    }
+    if (o.n0_flow)
+      for (size_t k = tid; k < (size_t)T * M; k += blockDim.x) o.n0_flow[(size_t)tau * T * M + k] = 0.0;
+    return;
+  }
+  const Real* PhiMC = static_cast<const Real*>(a.PhiMC);
+  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * M * kRMax;
+  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * M * T;
+  const Real* rowmul = static_cast<const Real*>(a.rowmul) + (size_t)q * M;
+  const Real* diagv = static_cast<const Real*>(a.diagv) + (size_t)q * M;
+  const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
+  const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
+  __shared__ double bestv;
+  __shared__ int besta;
+  __shared__ double rv[4];
+  __shared__ int ra[4];
+  for (int t = 0; t < T; ++t) {
+    if (tid == 0) {
+      double bv = -1.0, ovl = 0.0;
+      int ba = -1;
+      for (int b = 0; b < a.ncb; ++b) {
+        const size_t k = ((size_t)q * T + t) * a.ncb + b;
+        const double v = (double)static_cast<const Real*>(a.pmax)[k];
+        const int ar = a.parg[k];
+        if (ar >= 0 && v > bv) {
+          bv = v;
+          ba = ar;
+        }
+        ovl += a.povl[k];
+      }
+      const size_t k = (size_t)tau * T + t;
+      o.n1_max_loading[k] = ba >= 0 ? bv : 0.0;
+      o.overload_sum[k] = ovl;
+      o.worst_cont[k] = ba;
+      if (o.best_var) o.best_var[k] = -1;
+      bestv = bv;
+      besta = ba;
+    }
+    __syncthreads();
+    const int c = besta;
+    if (o.worst_mon) {
+      int arg = 0x7fffffff;
+      double v = -1.0;
+      if (c >= 0) {
+        Real vt[RMAX];
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) vt[j] = VtR[(size_t)j * C + c];
+        const Real st = sv[(size_t)t * C + c];
+        for (int l = tid; l < M; l += blockDim.x) {
+          Real zr[RMAX];
+#pragma unroll
+          for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)l * kRMax + j];
+          const Real ph = phi_entry<Real, RMAX>(PhiMC[(size_t)l * C + c], zr, vt, rowmul[l], a.cpos[l], c, diagv[l]);
+          const double x = (double)fabs(fma(ph, st, ptil[(size_t)l * T + t]));
+          if (x > v) {
+            v = x;
+            arg = l;
+          }
+        }
+      }
+      for (int off = 16; off; off >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+        const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
+        if (v2 > v || (v2 == v && a2 < arg)) {
+          v = v2;
+          arg = a2;
+        }
+      }
+      if ((tid & 31) == 0) {
+        rv[tid >> 5] = v;
+        ra[tid >> 5] = arg;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double bv = rv[0];
+        int ba = ra[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+          if (rv[w] > bv || (rv[w] == bv && ra[w] < ba)) {
+            bv = rv[w];
+            ba = ra[w];
+          }
+        o.worst_mon[(size_t)tau * T + t] = (c >= 0) ? ba : -1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace dcf
+
+using namespace dcf;
+
+namespace {
+
+struct Plan {
+  int TT, RMAX, LT;
+};
+
+int pick_tt(int T, bool fp64) {
+  const int opts32[] = {1, 4, 8, 16, 24, 32};
+  const int opts64[] = {1, 4, 8};
+  const int* o = fp64 ? opts64 : opts32;
+  const int n = fp64 ? 3 : 6;
+  for (int i = 0; i < n; ++i)
+    if (T <= o[i]) return o[i];
+  return o[n - 1];
+}
+
+template <class Real, int TT, int RMAX>
+void launch_n1_t(const Args& a, dim3 grid, cudaStream_t st, int t0) {
+  constexpr int LT = sizeof(Real) == 8 ? 8 : 16;
+  k_n1<Real, TT, RMAX, LT><<<grid, 64, 0, st>>>(a, t0);
+}
+
+template <class Real, int RMAX>
+int launch_n1_r(const Args& a, int TT, dim3 grid, cudaStream_t st, int t0) {
+  switch (TT) {
+    case 1: launch_n1_t<Real, 1, RMAX>(a, grid, st, t0); break;
+    case 4: launch_n1_t<Real, 4, RMAX>(a, grid, st, t0); break;
+    case 8: launch_n1_t<Real, 8, RMAX>(a, grid, st, t0); break;
+    default:
+      if constexpr (sizeof(Real) == 4) {
+        if (TT == 16) launch_n1_t<Real, 16, RMAX>(a, grid, st, t0);
+        else if (TT == 24) launch_n1_t<Real, 24, RMAX>(a, grid, st, t0);
+        else launch_n1_t<Real, 32, RMAX>(a, grid, st, t0);
+      } else {
+        return DCFLOW_ERR_INVALID_ARG;
+      }
+  }
+  return 0;
+}
+
+template <class Real>
+int launch_n1(const Args& a, int RMAX, int TT, dim3 grid, cudaStream_t st, int t0) {
+  if (RMAX == 4) return launch_n1_r<Real, 4>(a, TT, grid, st, t0);
+  if (RMAX == 8) return launch_n1_r<Real, 8>(a, TT, grid, st, t0);
+  return launch_n1_r<Real, 16>(a, TT, grid, st, t0);
+}
+
+template <class Real>
+void launch_final(const Args& a, int RMAX, cudaStream_t st) {
+  if (RMAX == 4) k_final<Real, 4><<<a.nq, 128, 0, st>>>(a);
+  else if (RMAX == 8) k_final<Real, 8><<<a.nq, 128, 0, st>>>(a);
+  else k_final<Real, 16><<<a.nq, 128, 0, st>>>(a);
+}
+
+int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
+
+}  // namespace
+
+extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_results* res, void* stream) {
+  if (!ctx || !bt || !res) {
+    set_error("dcflow_solve_batch: null argument");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  if (!ctx->has_study) {
+    set_error("dcflow_solve_batch: no study bound (dcflow_set_study)");
+    return DCFLOW_ERR_NO_STUDY;
+  }
+  const int N = bt->n_topo, T = bt->n_time;
+  if (N < 0 || T < 1 || T > 256 || bt->n_var != 0) {
+    set_error("dcflow_solve_batch: n_topo >= 0, 1 <= n_time <= 256 (candidates: see dcflow_solve_batch_var)");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  ctx->launches = 0;
+  if (N == 0) return DCFLOW_OK;
+  if (!bt->split_ptr || !bt->out_ptr || !bt->inj || !res->n1_max_loading || !res->overload_sum ||
+      !res->worst_cont || !res->island_flag || !res->n_island_cont) {
+    set_error("dcflow_solve_batch: missing required pointer");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool fp64 = ctx->opt.precision == DCFLOW_FP64;
+  const size_t rs = fp64 ? sizeof(double) : sizeof(float);
+  const int M = ctx->M, C = ctx->C, NN = ctx->NN;
+  // p0 = PTDF[N, :] inj^T
+  if (ctx->p0.ensure((size_t)NN * T * sizeof(double))) return DCFLOW_ERR_OOM;
+  k_p0<<<(NN * 32 + 255) / 256, 256, 0, st>>>(NN, ctx->V, T, ctx->PtdfN.as<double>(), bt->inj, ctx->p0.as<double>());
+  ++ctx->launches;
+  DCF_CHECK_LAUNCH();
+  GridDev g{ctx->f.as<int>(), ctx->t.as<int>(), ctx->b.as<double>(), ctx->inc_ptr.as<int>(), ctx->inc_list.as<int>(),
+            ctx->nidx.as<int>(), ctx->split_ok.as<uint8_t>(), ctx->V, ctx->E};
+  BatchDev in{bt->split_ptr, bt->split_sub, bt->split_mask, bt->out_ptr, bt->out_branch};
+  // rank of every topology -> group by rank class (no dummy padding of uneven k)
+  if (ctx->rank.ensure(N)) return DCFLOW_ERR_OOM;
+  k_rank<<<(N + 127) / 128, 128, 0, st>>>(g, in, N, ctx->rank.as<int8_t>());
+  ++ctx->launches;
+  DCF_CHECK_LAUNCH();
+  std::vector<int8_t> hr(N);
+  DCF_CUDA(cudaMemcpyAsync(hr.data(), ctx->rank.p, N, cudaMemcpyDeviceToHost, st));
+  DCF_CUDA(cudaStreamSynchronize(st));
+  std::vector<int> perm;
+  perm.reserve(N);
+  std::vector<int> cls_start(4, 0);
+  const int classes[3] = {4, 8, 16};
+  for (int ci = 0; ci < 3; ++ci) {
+    cls_start[ci] = (int)perm.size();
+    for (int i = 0; i < N; ++i) {
+      const int r = hr[i] < 0 ? 0 : hr[i];
+      if (rank_class(r) == classes[ci]) perm.push_back(i);
+    }
+  }
+  cls_start[3] = N;
+  if (ctx->perm.ensure(sizeof(int) * N)) return DCFLOW_ERR_OOM;
+  DCF_CUDA(cudaMemcpyAsync(ctx->perm.p, perm.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  // chunk capacity from a scratch budget
+  const int ncb = (C + 63) / 64;
+  const size_t per_slot = (size_t)kEntMax * (sizeof(int) + sizeof(double) + 1) + (kRMax + 1) * 2 + sizeof(QInfo) +
+                          (size_t)kRMax * kRMax * 8 + (size_t)kRMax * T * 8 + (size_t)kRMax * C * (8 + rs) +
+                          (size_t)M * (kRMax + T + 2) * rs + (size_t)T * C * rs + C + 4 +
+                          (size_t)T * ncb * (rs + 4 + 8) + 64;
+  int64_t cap = ctx->opt.chunk_topo > 0 ? ctx->opt.chunk_topo : (int64_t)((size_t)2 << 30) / (int64_t)per_slot;
+  cap = std::max<int64_t>(1, std::min<int64_t>({cap, 8192, (int64_t)N}));
+  {
+    const size_t c = (size_t)cap;
+    if (ctx->q_info.ensure(c * sizeof(QInfo)) || ctx->ent_n.ensure(c * kEntMax * sizeof(int)) ||
+        ctx->ent_s.ensure(c * kEntMax) || ctx->ent_w.ensure(c * kEntMax * sizeof(double)) ||
+        ctx->mod_ptr.ensure(c * (kRMax + 1) * sizeof(int16_t)) || ctx->Kinv.ensure(c * kRMax * kRMax * 8) ||
+        ctx->alpha.ensure(c * kRMax * T * 8) || ctx->Vt64.ensure(c * kRMax * std::max(C, 1) * 8) ||
+        (!fp64 && ctx->VtR.ensure(c * kRMax * std::max(C, 1) * rs)) || ctx->Zs.ensure(c * M * kRMax * rs) ||
+        ctx->ptil.ensure(c * M * T * rs) || ctx->rowmul.ensure(c * M * rs) || ctx->diagv.ensure(c * M * rs) ||
+        ctx->s.ensure(c * T * std::max(C, 1) * rs) || ctx->valid.ensure(c * std::max(C, 1)) ||
+        ctx->nisl.ensure(c * sizeof(int)) || ctx->pmax.ensure(c * T * std::max(ncb, 1) * rs) ||
+        ctx->parg.ensure(c * T * std::max(ncb, 1) * sizeof(int)) ||
+        ctx->povl.ensure(c * T * std::max(ncb, 1) * sizeof(double)))
+      return DCFLOW_ERR_OOM;
+    ctx->chunk_cap = cap;
+  }
+  Args a{};
+  a.M = M;
+  a.C = C;
+  a.NN = NN;
+  a.T = T;
+  a.U = 0;
+  a.monN = ctx->monN.as<int>();
+  a.contN = ctx->contN.as<int>();
+  a.cpos = ctx->cpos_of_mon.as<int>();
+  a.mpos = ctx->mpos_of_cont.as<int>();
+  a.inv_lim = ctx->inv_lim.as<double>();
+  a.PhiN = ctx->PhiN.as<double>();
+  a.PhiMC = ctx->PhiMC.p;
+  a.p0 = ctx->p0.as<double>();
+  a.tol = ctx->opt.island_tol;
+  a.qi = ctx->q_info.as<QInfo>();
+  a.ent_n = ctx->ent_n.as<int>();
+  a.ent_s = ctx->ent_s.as<int8_t>();
+  a.ent_w = ctx->ent_w.as<double>();
+  a.mod_ptr = ctx->mod_ptr.as<int16_t>();
+  a.Kinv = ctx->Kinv.as<double>();
+  a.alpha = ctx->alpha.as<double>();
+  a.Vt64 = ctx->Vt64.as<double>();
+  a.VtR = fp64 ? ctx->Vt64.p : ctx->VtR.p;
+  a.Zs = ctx->Zs.p;
+  a.ptil = ctx->ptil.p;
+  a.rowmul = ctx->rowmul.p;
+  a.diagv = ctx->diagv.p;
+  a.s = ctx->s.p;
+  a.valid = ctx->valid.as<uint8_t>();
+  a.nisl = ctx->nisl.as<int>();
+  a.pmax = ctx->pmax.p;
+  a.parg = ctx->parg.as<int>();
+  a.povl = ctx->povl.as<double>();
+  a.ncb = ncb;
+  a.out = *res;
+  const int TT = pick_tt(T, fp64);
+  const size_t dyn = (size_t)kRMax * T * rs;
+  for (int ci = 0; ci < 3; ++ci) {
+    for (int c0 = cls_start[ci]; c0 < cls_start[ci + 1]; c0 += (int)cap) {
+      const int nq = std::min<int>((int)cap, cls_start[ci + 1] - c0);
+      a.nq = nq;
+      const int* dperm = ctx->perm.as<int>() + c0;
+      k_decode<<<(nq + 127) / 128, 128, 0, st>>>(g, in, dperm, a);
+      if (fp64) {
+        k_small<double><<<nq, 128, 0, st>>>(a);
+        k_rows<double><<<nq, 128, dyn, st>>>(a);
+      } else {
+        k_small<float><<<nq, 128, 0, st>>>(a);
+        k_rows<float><<<nq, 128, dyn, st>>>(a);
+      }
+      ctx->launches += 3;
+      DCF_CHECK_LAUNCH();
+      if (C > 0) {
+        for (int t0 = 0; t0 < T; t0 += TT) {
+          const dim3 grid(ncb, nq);
+          cudaEvent_t e0 = nullptr, e1 = nullptr;
+          if (ctx->prof_on) {
+            while (ctx->prof_ev.size() < ctx->prof_used + 2) {
+              cudaEvent_t e;
+              DCF_CUDA(cudaEventCreate(&e));
+              ctx->prof_ev.push_back(e);
+            }
+            e0 = ctx->prof_ev[ctx->prof_used];
+            e1 = ctx->prof_ev[ctx->prof_used + 1];
+            ctx->prof_used += 2;
+            DCF_CUDA(cudaEventRecord(e0, st));
+          }
+          int rc = fp64 ? launch_n1<double>(a, classes[ci], TT, grid, st, t0)
+                        : launch_n1<float>(a, classes[ci], TT, grid, st, t0);
+          if (rc) return rc;
+          ++ctx->launches;
+          DCF_CHECK_LAUNCH();
+          if (ctx->prof_on) DCF_CUDA(cudaEventRecord(e1, st));
+        }
+      }
+      if (fp64) launch_final<double>(a, classes[ci], st);
+      else launch_final<float>(a, classes[ci], st);
+      ++ctx->launches;
+      DCF_CHECK_LAUNCH();
+    }
+  }
+  return DCFLOW_OK;
+}
+
+extern "C" int dcflow_profile(dcflow_ctx* ctx, int32_t enable) {
+  if (!ctx) return DCFLOW_ERR_INVALID_ARG;
+  ctx->prof_on = enable != 0;
+  ctx->prof_used = 0;
+  return DCFLOW_OK;
+}
+
+extern "C" int dcflow_profile_read(dcflow_ctx* ctx, double* n1_ms, int64_t* n1_launches) {
+  if (!ctx || !n1_ms || !n1_launches) return DCFLOW_ERR_INVALID_ARG;
+  double ms = 0.0;
+  for (size_t i = 0; i + 1 < ctx->prof_used; i += 2) {
+    DCF_CUDA(cudaEventSynchronize(ctx->prof_ev[i + 1]));
+    float x = 0.f;
+    DCF_CUDA(cudaEventElapsedTime(&x, ctx->prof_ev[i], ctx->prof_ev[i + 1]));
+    ms += x;
+  }
+  *n1_ms = ms;
+  *n1_launches = (int64_t)(ctx->prof_used / 2);
+  return DCFLOW_OK;
+}

@@ -1,0 +1,74 @@
+"""Comparison of CUDA-path outputs with the oracle (shared by the GPU tests).
+
+Error metric: flows |x - x_ref| / max(|x_ref|, limit_l); loadings
+|rho - rho_ref| / max(rho_ref, 1); overload sums |s - s_ref| / max(s_ref, 1).
+Integer outputs: island flags and islanding-contingency counts bit-exact; the
+arg-max contingency (and monitored branch) exact wherever the oracle's best
+value beats the runner-up by more than twice the tolerance, otherwise the
+CUDA pick must reach the maximum within the tolerance (near-tie rule).
+"""
+import numpy as np
+
+import oracle
+
+TOL = {"fp64": 1e-10, "fp32": 1e-4}
+
+
+def _topo_lists(topo, i):
+    a, c = topo.split_ptr[i], topo.split_ptr[i + 1]
+    splits = list(zip(topo.split_sub[a:c], topo.split_mask[a:c]))
+    a, c = topo.out_ptr[i], topo.out_ptr[i + 1]
+    return splits, list(topo.out_branch[a:c])
+
+
+def compare(gpu, ref, w, topo, lim, tol, report=None):
+    """gpu/ref: dicts of per-topology arrays for the same topologies (ref from
+    oracle.evaluate(..., want_flows=True, want_cmax=True)).  Raises AssertionError."""
+    rep = {"max_err_flow": 0.0, "max_err_n1": 0.0, "max_err_n0": 0.0, "max_err_ovl": 0.0,
+           "near_ties": 0, "exact_argmax": 0}
+    np.testing.assert_array_equal(gpu["status"], ref["status"], err_msg="island flags")
+    ok = ref["status"] == 0
+    np.testing.assert_array_equal(gpu["n_island_cont"][ok], ref["n_island_cont"][ok], err_msg="islanding contingencies")
+    mon = np.asarray(w.mon)
+    lim_mon = np.asarray(lim)[mon]
+    if not ok.any():
+        return rep
+    if "n0_flow" in gpu and "n0_flow" in ref:
+        d = np.abs(gpu["n0_flow"][ok] - ref["n0_flow"][ok]) / np.maximum(np.abs(ref["n0_flow"][ok]), lim_mon)
+        rep["max_err_flow"] = float(d.max())
+        assert d.max() <= tol, f"N-0 flow error {d.max():.3e}"
+    for key, rk in (("n0_max", "max_err_n0"), ("n1_max", "max_err_n1")):
+        d = np.abs(gpu[key][ok] - ref[key][ok]) / np.maximum(ref[key][ok], 1.0)
+        rep[rk] = float(d.max())
+        assert d.max() <= tol, f"{key} error {d.max():.3e}"
+    d = np.abs(gpu["ovl"][ok] - ref["ovl"][ok]) / np.maximum(ref["ovl"][ok], 1.0)
+    rep["max_err_ovl"] = float(d.max())
+    assert d.max() <= tol, f"overload-sum error {d.max():.3e}"
+    cmax = ref["cmax"]
+    for i in np.nonzero(ok)[0]:
+        for t in range(ref["n1_max"].shape[1]):
+            go, ro = int(gpu["worst_cont"][i, t]), int(ref["worst_cont"][i, t])
+            vals = cmax[i, t]
+            if ro < 0:
+                assert go == -1
+                continue
+            srt = np.sort(vals[vals >= 0])[::-1]
+            gap = srt[0] - srt[1] if srt.size > 1 else np.inf
+            if gap > 2 * tol * max(1.0, srt[0]):
+                assert go == ro, f"topology {i} t {t}: worst contingency {go} != {ro}"
+                rep["exact_argmax"] += 1
+            else:
+                assert go >= 0 and vals[go] >= srt[0] - 2 * tol * max(1.0, srt[0]), \
+                    f"topology {i} t {t}: near-tie pick {go} value {vals[go]} vs {srt[0]}"
+                rep["near_ties"] += 1
+            gm, rm = int(gpu["worst_mon"][i, t]), int(ref["worst_mon"][i, t])
+            if go == ro and gm != rm:
+                splits, outs = _topo_lists(topo, i)
+                col = oracle.n1_loading_column(w.grid, splits, outs, w.inj[t], mon, w.cont[go], lim)
+                best = col.max()
+                assert col[gm] >= best - 2 * tol * max(1.0, best), \
+                    f"topology {i} t {t}: worst monitored {gm} != {rm} beyond tolerance"
+                rep["near_ties"] += 1
+    if report is not None:
+        report.update(rep)
+    return rep

@@ -1,0 +1,182 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_17529_b300 import synth
+
+from .parity import TOL, compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2501_17529_b300.csrc import build
+    build.build()
+
+
+def _solver(w, lim, precision, chunk=0, split_bus="subs"):
+    from paper_2501_17529_b300.dcflow import Solver
+    s = Solver(w.grid, precision=precision, chunk_topo=chunk)
+    s.set_study(w.mon, w.cont, lim, split_bus=(w.subs if split_bus == "subs" else split_bus))
+    return s
+
+
+def _gpu(w, lim, precision, topo=None, chunk=0, want_flows=True):
+    from paper_2501_17529_b300.dcflow import DeviceBatch
+    s = _solver(w, lim, precision, chunk)
+    topo = w.topo if topo is None else topo
+    res = s.solve(DeviceBatch(topo, w.inj), want_flows=want_flows)
+    torch.cuda.synchronize()
+    out = res.to_host()
+    s.close()
+    return out
+
+
+def _ref(w, lim, topo=None):
+    topo = w.topo if topo is None else topo
+    return oracle.evaluate(w.grid, topo, w.inj, w.mon, w.cont, lim, want_flows=True, want_cmax=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tiny_grid_all_topologies(precision):
+    """14-bus grid, 64 single splits (slack included), full N-1: every output."""
+    w = synth.workload(1)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    compare(_gpu(w, lim, precision), _ref(w, lim), w, w.topo, lim, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tiny_grid_every_mask(precision):
+    """Every busbar assignment of every substation (islanding ones included)."""
+    w = synth.workload(1)
+    g = w.grid
+    inc = oracle.incident_lists(g.n_bus, g.f, g.t)
+    sp, ss, sm = [0], [], []
+    for A in range(g.n_bus):
+        for m in range(1, 2 ** len(inc[A]) - 1):
+            ss.append(A)
+            sm.append(m)
+            sp.append(len(ss))
+    topo = synth.Topologies(np.array(sp, np.int32), np.array(ss, np.int32), np.array(sm, np.uint64),
+                            np.zeros(len(ss) + 1, np.int32), np.zeros(0, np.int32))
+    w.subs = np.arange(g.n_bus, dtype=np.int32)
+    lim = oracle.thermal_limits(g, w.inj)
+    ref = _ref(w, lim, topo)
+    assert (ref["status"] == 1).sum() > 0
+    compare(_gpu(w, lim, precision, topo), ref, w, topo, lim, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_grid500_sample(precision):
+    """500-bus grid, 1-4 splits + 0-3 outages, 24 timesteps: 48 topologies."""
+    w = synth.workload(2, n_topo=48)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    compare(_gpu(w, lim, precision), _ref(w, lim), w, w.topo, lim, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ragged_chunks_times_and_sets(precision):
+    """Small chunks across rank classes, T beyond one pass, ragged mon / cont subsets."""
+    g = synth.make_grid(120, 170, 31)
+    subs = synth.split_capable(g, 30, 31)
+    rng = np.random.default_rng(32)
+    topo = synth.make_topologies(g, subs, 40, 33, (0, 9), (0, 7))
+    T = 37 if precision == "fp32" else 19
+    inj = synth.make_injections(g, T, 34, daily=True)
+    mon = np.sort(rng.choice(g.n_branch, 101, replace=False)).astype(np.int32)
+    cont = np.sort(rng.choice(g.n_branch, 77, replace=False)).astype(np.int32)
+    w = synth.Workload("ragged", g, topo, inj, mon, cont, subs)
+    lim = oracle.thermal_limits(g, inj)
+    compare(_gpu(w, lim, precision, chunk=7), _ref(w, lim), w, topo, lim, TOL[precision])
+
+
+def test_edge_cases_and_invalid_inputs():
+    """Empty batch, no-op masks, base topology, outaged monitored / contingency branches,
+    islanding outages, rank 16 and invalid topology inputs (flag 2, never a fault)."""
+    g = synth.make_grid(40, 60, 41)
+    subs = synth.split_capable(g, None, 41, min_degree=2)
+    inc = oracle.incident_lists(g.n_bus, g.f, g.t)
+    deg = np.array([len(x) for x in inc])
+    A = int(subs[0])
+    full = (1 << int(deg[A])) - 1
+    br = oracle.bridges(g.n_bus, g.f, g.t, np.ones(g.n_branch, bool))
+    bridge = int(np.nonzero(br)[0][0]) if br.any() else -1
+    many = [int(x) for x in subs[:16]]
+    cases = [
+        ([], []),                                   # base topology
+        ([(A, 0)], []),                             # empty busbar B: no-op
+        ([(A, full)], []),                          # empty busbar A: no-op
+        ([(A, 1)], [5]),                            # split + outage
+        ([], [3, 4]),                               # outages of monitored and contingency branches
+        ([], [bridge] if bridge >= 0 else [0]),     # islanding outage
+        ([(s, 1) for s in many[:10]], [7, 8, 9, 10, 11, 12]),  # rank 16
+        ([(A, 1), (A, 2)], []),                     # invalid: same substation twice
+        ([(A, 1 << int(deg[A]))], []),              # invalid: mask bit beyond the degree
+        ([], [g.n_branch]),                         # invalid: outage out of range
+        ([], [2, 2]),                               # invalid: duplicate outage
+        ([(s, 1) for s in many[:12]], [7, 8, 9, 10, 11]),  # invalid: rank 17
+    ]
+    sp, ss, sm, op, ob = [0], [], [], [0], []
+    for splits, outs in cases:
+        for s, m in splits:
+            ss.append(s)
+            sm.append(m)
+        sp.append(len(ss))
+        ob.extend(outs)
+        op.append(len(ob))
+    topo = synth.Topologies(np.array(sp, np.int32), np.array(ss, np.int32), np.array(sm, np.uint64),
+                            np.array(op, np.int32), np.array(ob, np.int32))
+    inj = synth.make_injections(g, 3, 42, daily=False)
+    mon = np.arange(g.n_branch, dtype=np.int32)
+    w = synth.Workload("edge", g, topo, inj, mon, mon.copy(), subs)
+    lim = oracle.thermal_limits(g, inj)
+    for precision in ("fp64", "fp32"):
+        gpu = _gpu(w, lim, precision)
+        ref = _ref(w, lim)
+        assert list(ref["status"][7:]) == [2, 2, 2, 2, 2]
+        compare(gpu, ref, w, topo, lim, TOL[precision])
+    # empty batch is a no-op
+    from paper_2501_17529_b300.dcflow import DeviceBatch
+    s = _solver(w, lim, "fp32")
+    empty = topo.subset([])
+    s.solve(DeviceBatch(empty, inj))
+    torch.cuda.synchronize()
+    s.close()
+
+
+def test_base_ptdf_matches_oracle():
+    g = synth.make_grid(300, 420, 51)
+    from paper_2501_17529_b300.dcflow import Solver
+    s = Solver(g, precision="fp64")
+    rows = np.array([0, 5, 17, 419, 200], np.int32)
+    out = s.base_ptdf(rows).cpu().numpy()
+    torch.cuda.synchronize()
+    ref = oracle.ptdf(g.n_bus, g.f, g.t, g.b, g.slack)[rows]
+    assert np.abs(out - ref).max() < 1e-11
+    assert np.all(out[:, g.slack] == 0.0)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_grid500_full_batch_sampled(precision):
+    """The 10,000-topology batch in the benchmark's launch configuration; 24
+    sampled topologies checked against the oracle, invariants on all."""
+    w = synth.workload(2)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    gpu = _gpu(w, lim, precision, want_flows=False)
+    N = w.topo.n_topo
+    assert gpu["status"].shape == (N,)
+    ok = gpu["status"] == 0
+    assert np.all(gpu["n1_max"][ok] > 0) and np.all(gpu["ovl"][ok] >= 0)
+    assert np.all(gpu["worst_cont"][ok] >= 0) and np.all(gpu["worst_cont"][~ok] == -1)
+    idx = np.random.default_rng(7).choice(N, 24, replace=False)
+    sub = w.topo.subset(idx)
+    ref = _ref(w, lim, sub)
+    g2 = {k: v[idx] for k, v in gpu.items()}
+    compare(g2, ref, w, sub, lim, TOL[precision])
