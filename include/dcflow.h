@@ -90,6 +90,30 @@ int dcflow_base_ptdf(dcflow_ctx* ctx, const int32_t* rows, int32_t n_rows,
                      double* out, void* stream);
 
 /*
+ * Same rows as dcflow_base_ptdf, for callers that cannot allocate device
+ * memory (code running inside an arena or memory pool it does not own,
+ * real-time loops that must not enter the driver allocator, hosts whose
+ * allocator belongs to another framework).  The paper has no counterpart.
+ *
+ * It allocates nothing: its solve workspace and its device copy of `rows`
+ * live in one fixed 8 MiB device array inside the library, which every GPU
+ * that loads the library holds until the process exits.  A call needs
+ * round_up(4 * n_rows, 256) + round_up(n_bus - 1, 64) * round_up(n_rows, 64) * 8
+ * bytes of it; a larger request fails with DCFLOW_ERR_INVALID_ARG (use fewer
+ * rows per call, or dcflow_base_ptdf).  Arguments, layout and ownership as for
+ * dcflow_base_ptdf: rows host int32[n_rows], out device double[n_rows * n_bus]
+ * row-major, caller-owned; enqueued on `stream`.
+ *
+ * The first call on each device looks up the array's device address (once
+ * per device, with that device current); make that first call before any
+ * stream capture.  Every call shares the array and it keeps the previous
+ * call's contents (the workspace is cleared on each call), so calls that
+ * overlap on the GPU (other streams or host threads) race: serialise them.
+ */
+int dcflow_base_ptdf_noalloc(dcflow_ctx* ctx, const int32_t* rows, int32_t n_rows,
+                             double* out, void* stream);
+
+/*
  * Bind the study sets that every later batch uses (PTDF row restriction of
  * Sec. II: only monitored, contingency and switching branches are needed).
  *

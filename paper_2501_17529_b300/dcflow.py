@@ -46,7 +46,8 @@ class Results(ctypes.Structure):
                 ("best_var", c_void_p), ("island_flag", c_void_p), ("n_island_cont", c_void_p)]
 
 
-EXPORTED = ["dcflow_default_options", "dcflow_setup", "dcflow_base_ptdf", "dcflow_set_study",
+EXPORTED = ["dcflow_default_options", "dcflow_setup", "dcflow_base_ptdf", "dcflow_base_ptdf_noalloc",
+            "dcflow_set_study",
             "dcflow_solve_batch", "dcflow_last_launch_count", "dcflow_profile", "dcflow_profile_read",
             "dcflow_destroy", "dcflow_strerror", "dcflow_last_error"]
 
@@ -68,6 +69,8 @@ def load_library(path: str = LIB_PATH):
     lib.dcflow_setup.restype = c_int32
     lib.dcflow_base_ptdf.argtypes = [c_void_p, POINTER(c_int32), c_int32, c_void_p, c_void_p]
     lib.dcflow_base_ptdf.restype = c_int32
+    lib.dcflow_base_ptdf_noalloc.argtypes = [c_void_p, POINTER(c_int32), c_int32, c_void_p, c_void_p]
+    lib.dcflow_base_ptdf_noalloc.restype = c_int32
     lib.dcflow_set_study.argtypes = [c_void_p, POINTER(Study)]
     lib.dcflow_set_study.restype = c_int32
     lib.dcflow_solve_batch.argtypes = [c_void_p, POINTER(Batch), POINTER(Results), c_void_p]
@@ -152,6 +155,14 @@ def dcflow_base_ptdf(ctx, rows, out, stream=None):
     ra, rp = _i32(rows)
     _check(load_library().dcflow_base_ptdf(ctx, rp, int(ra.size), _ptr(out), _stream_ptr(stream)),
            "dcflow_base_ptdf")
+
+
+def dcflow_base_ptdf_noalloc(ctx, rows, out, stream=None):
+    """Rows of the base PTDF without any device allocation (fixed 8 MiB workspace
+    inside the library); for callers that cannot allocate device memory."""
+    ra, rp = _i32(rows)
+    _check(load_library().dcflow_base_ptdf_noalloc(ctx, rp, int(ra.size), _ptr(out), _stream_ptr(stream)),
+           "dcflow_base_ptdf_noalloc")
 
 
 def dcflow_set_study(ctx, mon, cont, limit, split_bus=None, outage_cand=None):
