@@ -206,9 +206,10 @@ def run_ours(args):
         cbuild.build()
     if ws > 1:
         dist.barrier()
-    w = synth.workload(2)
+    n_topo = args.topologies
+    w = synth.workload(2, n_topo=n_topo)
     if ws > 1 and rank > 0:  # each rank its own batch of the same shape
-        w.topo = synth.make_topologies(w.grid, w.subs, N_TOPO, 202 + 1000 * rank, (1, 4), (0, 3))
+        w.topo = synth.make_topologies(w.grid, w.subs, n_topo, 202 + 1000 * rank, (1, 4), (0, 3))
     # limits from the unsplit grid's N-0 flows, computed on the device
     base = Solver(w.grid, precision="fp64")
     pt = base.base_ptdf(np.arange(w.grid.n_branch)).cpu().numpy()
@@ -291,7 +292,7 @@ def run_ours(args):
             "value": head["value"], "unit": "loadflows/s", "n_gpus": ws, "steps": head["steps"],
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "topologies": N_TOPO, "timesteps": T_STEPS, "monitored": 700,
+            "config": {"workload": WORKLOAD, "topologies": args.topologies, "timesteps": T_STEPS, "monitored": 700,
                        "contingencies": 700, "l2": "flushed between steps (256 MB write)",
                        "max_err_stated": {"fp32": 1e-4, "fp64": 1e-10}},
             "gpu_launches": head["launches"], "clocks": head["clocks"],
@@ -352,6 +353,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--topologies", type=int, default=N_TOPO, help="batch size (smaller only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -40,7 +40,7 @@ extern "C" void dcflow_destroy(dcflow_ctx* ctx) {
                          &ctx->rank, &ctx->status, &ctx->perm, &ctx->hist, &ctx->hist_host, &ctx->ent_n, &ctx->ent_s,
                          &ctx->ent_w, &ctx->mod_ptr, &ctx->q_info, &ctx->Kinv, &ctx->alpha, &ctx->Vt64, &ctx->VtR,
                          &ctx->Zs, &ctx->ptil, &ctx->rowmul, &ctx->diagv, &ctx->s, &ctx->valid, &ctx->nisl,
-                         &ctx->pmax, &ctx->parg, &ctx->povl, &ctx->vmax, &ctx->Gs, &ctx->Gc};
+                         &ctx->pmax, &ctx->parg, &ctx->povl, &ctx->vmax, &ctx->Gs, &ctx->Gc, &ctx->err};
   for (auto* b : bufs) b->release();
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   delete ctx;

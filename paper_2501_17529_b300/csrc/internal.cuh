@@ -71,7 +71,8 @@ struct dcflow_ctx {
   dcf::DevBuf inv_lim;     // double[M]
   dcf::DevBuf PhiN;        // double[NN*NN] base branch-to-branch factors
   dcf::DevBuf PtdfN;       // double[NN*V] base PTDF rows of the needed branches
-  dcf::DevBuf PhiMC;       // Real[M*C] Phi[mon, cont] / limit[mon]
+  dcf::DevBuf PhiMC;       // Real[M*ldc] Phi[mon, cont] / limit[mon], row stride ldc
+  int ldc = 0;             // round_up(C, 4): 16-byte row pitch for the tensor-memory accelerator
   dcf::DevBuf Y;           // solve workspace
   // batch scratch
   dcf::DevBuf p0;          // double[NN*T]
@@ -80,6 +81,7 @@ struct dcflow_ctx {
   dcf::DevBuf ent_n, ent_s, ent_w, mod_ptr, q_info;
   dcf::DevBuf Kinv, alpha, Vt64, VtR, Zs, ptil, rowmul, diagv, s, valid, nisl;
   dcf::DevBuf pmax, parg, povl, vmax, Gs, Gc;
+  dcf::DevBuf err;         // int: set by a kernel whose bounded wait expired
   int64_t launches = 0;
   int64_t chunk_cap = 0;
   // kernel timing (dcflow_profile)

@@ -89,14 +89,14 @@ __global__ void k_ptdf_rows(int nr, int V, const int* rows, const double* b, con
   }
 }
 
-// PhiMC[l][c] = Phi[monN_l][contN_c] / limit_l in the working precision.
+// PhiMC[l][c] = Phi[monN_l][contN_c] / limit_l in the working precision (row stride ldc >= C).
 template <class Real>
-__global__ void k_phi_mc(int M, int C, int nn, const int* monN, const int* contN, const double* inv_lim,
+__global__ void k_phi_mc(int M, int C, int ldc, int nn, const int* monN, const int* contN, const double* inv_lim,
                          const double* Phi, Real* out) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int l = blockIdx.y;
-  if (c >= C) return;
-  out[(size_t)l * C + c] = (Real)(Phi[(size_t)monN[l] * nn + contN[c]] * inv_lim[l]);
+  if (c >= ldc) return;
+  out[(size_t)l * ldc + c] = (c < C) ? (Real)(Phi[(size_t)monN[l] * nn + contN[c]] * inv_lim[l]) : (Real)0;
 }
 
 }  // namespace dcf
@@ -218,7 +218,11 @@ extern "C" int dcflow_setup(dcflow_ctx** out, int32_t n_bus, int32_t n_branch, c
   if ((rc = upload(ctx->inc_list, ctx->h_inc_list.data(), sizeof(int) * ctx->h_inc_list.size()))) return fail(rc);
   if ((rc = upload(ctx->rid, rid.data(), sizeof(int) * n_bus))) return fail(rc);
   const size_t abytes = (size_t)ctx->npad * ctx->npad * sizeof(double);
-  if (ctx->L.ensure(abytes) || ctx->info.ensure(sizeof(int))) return fail(DCFLOW_ERR_OOM);
+  if (ctx->L.ensure(abytes) || ctx->info.ensure(sizeof(int)) || ctx->err.ensure(sizeof(int))) return fail(DCFLOW_ERR_OOM);
+  if (cudaMemset(ctx->err.p, 0, sizeof(int)) != cudaSuccess) {
+    set_error("dcflow_setup: memset failed");
+    return fail(DCFLOW_ERR_CUDA);
+  }
   cudaStream_t st = 0;
   if (cudaMemsetAsync(ctx->L.p, 0, abytes, st) != cudaSuccess || cudaMemsetAsync(ctx->info.p, 0, sizeof(int), st) != cudaSuccess) {
     set_error("dcflow_setup: memset failed");
@@ -390,18 +394,19 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
       NN, V, d_N.as<int>(), ctx->b.as<double>(), ctx->rid.as<int>(), ctx->Y.as<double>(), ldy, ctx->PtdfN.as<double>());
   ctx->launches += 2;
   const size_t rs = ctx->opt.precision == DCFLOW_FP64 ? sizeof(double) : sizeof(float);
-  if (ctx->PhiMC.ensure((size_t)M * std::max(C, 1) * rs)) {
+  ctx->ldc = (int)round_up(std::max(C, 1), 4);
+  if (ctx->PhiMC.ensure((size_t)M * ctx->ldc * rs)) {
     d_N.release();
     return DCFLOW_ERR_OOM;
   }
   if (C > 0) {
-    dim3 g((C + 127) / 128, M);
+    dim3 g((ctx->ldc + 127) / 128, M);
     if (ctx->opt.precision == DCFLOW_FP64)
-      k_phi_mc<double><<<g, 128, 0, st>>>(M, C, NN, ctx->monN.as<int>(), ctx->contN.as<int>(), ctx->inv_lim.as<double>(),
-                                         ctx->PhiN.as<double>(), ctx->PhiMC.as<double>());
+      k_phi_mc<double><<<g, 128, 0, st>>>(M, C, ctx->ldc, NN, ctx->monN.as<int>(), ctx->contN.as<int>(),
+                                         ctx->inv_lim.as<double>(), ctx->PhiN.as<double>(), ctx->PhiMC.as<double>());
     else
-      k_phi_mc<float><<<g, 128, 0, st>>>(M, C, NN, ctx->monN.as<int>(), ctx->contN.as<int>(), ctx->inv_lim.as<double>(),
-                                        ctx->PhiN.as<double>(), ctx->PhiMC.as<float>());
+      k_phi_mc<float><<<g, 128, 0, st>>>(M, C, ctx->ldc, NN, ctx->monN.as<int>(), ctx->contN.as<int>(),
+                                        ctx->inv_lim.as<double>(), ctx->PhiN.as<double>(), ctx->PhiMC.as<float>());
     ++ctx->launches;
   }
   cudaError_t e = cudaStreamSynchronize(st);

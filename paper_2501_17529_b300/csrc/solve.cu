@@ -26,6 +26,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cudaTypedefs.h>
+
 #include "internal.cuh"
 
 namespace dcf {
@@ -53,6 +55,7 @@ struct BatchDev {
 struct Args {
   // study
   int M, C, NN, T, U;
+  int Mpad, ldc;  // padded monitored count (row stride of the per-row arrays), Phi[mon, cont] row stride
   const int *monN, *contN, *cpos, *mpos;
   const double *inv_lim, *PhiN;
   const void* PhiMC;
@@ -73,6 +76,7 @@ struct Args {
   int* parg;
   double* povl;
   int ncb;
+  int* err;  // set to 1 by a kernel whose bounded wait expired
   // outputs
   dcflow_results out;
 };
@@ -357,6 +361,12 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
 // ---------------------------------------------------------------------------
 // rows: Z, N-0 flows, scaled operands of the N-1 kernel, FP64 denominators
 // ---------------------------------------------------------------------------
+// Per-topology operands of the N-1 kernels, all row-strided by Mpad:
+//   Zs   [kRMax][Mpad]  Z[l, j] / limit_l          (zero rows for outaged l)
+//   ptil [T][Mpad]      p_f[l, t] / limit_l        (zero for outaged l)
+//   meta [4][Mpad]      row 0: -den_c / limit_l on the row of contingency c,
+//                       row 1: 1 (0 for an outaged l), row 2: position of l in
+//                       the contingency list as int bits (-1 if none), row 3: 0
 template <class Real>
 __global__ __launch_bounds__(128) void k_rows(Args a) {
   const int q = blockIdx.x;
@@ -368,7 +378,7 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
   Real* alph = reinterpret_cast<Real*>(dyn);  // [kRMax][T]
   const QInfo qi = a.qi[q];
   if (qi.status != ST_OK) return;
-  const int r = qi.r, ks = qi.ks, tid = threadIdx.x, T = a.T, M = a.M, C = a.C, NN = a.NN;
+  const int r = qi.r, ks = qi.ks, tid = threadIdx.x, T = a.T, M = a.M, C = a.C, NN = a.NN, Mp = a.Mpad;
   load_entries(S, a, q, r);
   if (tid == 0) {
     nout = r - ks;
@@ -377,10 +387,9 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
   for (int i = tid; i < r - ks; i += blockDim.x) outN[i] = S.en[S.mp[ks + i]];
   for (int p = tid; p < kRMax * T; p += blockDim.x) alph[p] = (Real)a.alpha[(size_t)q * kRMax * T + p];
   __syncthreads();
-  Real* Zs = static_cast<Real*>(a.Zs) + (size_t)q * M * kRMax;
-  Real* ptil = static_cast<Real*>(a.ptil) + (size_t)q * M * T;
-  Real* rowmul = static_cast<Real*>(a.rowmul) + (size_t)q * M;
-  Real* diagv = static_cast<Real*>(a.diagv) + (size_t)q * M;
+  Real* Zs = static_cast<Real*>(a.Zs) + (size_t)q * kRMax * Mp;
+  Real* ptil = static_cast<Real*>(a.ptil) + (size_t)q * T * Mp;
+  Real* meta = static_cast<Real*>(a.diagv) + (size_t)q * 4 * Mp;
   Real* sv = static_cast<Real*>(a.s) + (size_t)q * T * C;
   const int tau = qi.tau;
   for (int l = tid; l < M; l += blockDim.x) {
@@ -393,14 +402,20 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     for (int j = 0; j < kRMax; ++j) z[j] = (j < r) ? (Real)z_entry(S, prow, nl, j) : (Real)0;
     const Real il = (Real)a.inv_lim[l];
 #pragma unroll
-    for (int j = 0; j < kRMax; ++j) Zs[(size_t)l * kRMax + j] = outd ? (Real)0 : z[j] * il;
-    rowmul[l] = outd ? (Real)0 : (Real)1;
-    diagv[l] = (Real)0;
+    for (int j = 0; j < kRMax; ++j) Zs[(size_t)j * Mp + l] = outd ? (Real)0 : z[j] * il;
+    meta[l] = (Real)0;
+    meta[Mp + l] = outd ? (Real)0 : (Real)1;
+    if (sizeof(Real) == 4) {
+      reinterpret_cast<int*>(meta)[2 * Mp + l] = a.cpos[l];
+    } else {
+      meta[2 * Mp + l] = (Real)a.cpos[l];
+    }
+    meta[3 * Mp + l] = (Real)0;
     for (int t = 0; t < T; ++t) {
       Real pf = (Real)a.p0[(size_t)nl * T + t];
 #pragma unroll
       for (int j = 0; j < kRMax; ++j) pf = fma(-z[j], alph[j * T + t], pf);
-      ptil[(size_t)l * T + t] = outd ? (Real)0 : pf * il;
+      ptil[(size_t)t * Mp + l] = outd ? (Real)0 : pf * il;
       if (a.out.n0_flow) a.out.n0_flow[((size_t)tau * T + t) * M + l] = outd ? 0.0 : (double)pf;
     }
   }
@@ -423,7 +438,7 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     my_isl += (!outd && !ok);
     a.valid[(size_t)q * C + c] = ok;
     const int mp = a.mpos[c];
-    if (mp >= 0) diagv[mp] = (Real)(-den * a.inv_lim[mp]);
+    if (mp >= 0) meta[mp] = (Real)(-den * a.inv_lim[mp]);
     const double invd = ok ? 1.0 / den : 0.0;
     for (int t = 0; t < T; ++t) {
       Real pf = (Real)a.p0[(size_t)nc * T + t];
@@ -435,21 +450,14 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
   if (my_isl) atomicAdd(&nisl, my_isl);
   __syncthreads();
   if (tid == 0) a.nisl[q] = nisl;
-  // N-0 maximum loading per timestep
+  // N-0 maximum loading per timestep (one warp per timestep)
   if (a.out.n0_max_loading) {
-    __shared__ double red[4];
-    for (int t = 0; t < T; ++t) {
+    const int lane = tid & 31, nw = blockDim.x >> 5;
+    for (int t = tid >> 5; t < T; t += nw) {
       double m = 0.0;
-      for (int l = tid; l < M; l += blockDim.x) m = fmax(m, (double)fabs((double)ptil[(size_t)l * T + t]));
+      for (int l = lane; l < M; l += 32) m = fmax(m, fabs((double)ptil[(size_t)t * Mp + l]));
       for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if ((tid & 31) == 0) red[tid >> 5] = m;
-      __syncthreads();
-      if (tid == 0) {
-        double x = red[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = fmax(x, red[w]);
-        a.out.n0_max_loading[(size_t)tau * T + t] = x;
-      }
-      __syncthreads();
+      if (lane == 0) a.out.n0_max_loading[(size_t)tau * T + t] = m;
     }
   }
 }
@@ -505,11 +513,11 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
   __shared__ Real pt[LT][TT];
   __shared__ Real dg[LT], rm[LT];
   __shared__ int cp[LT];
+  const int Mp = a.Mpad;
   const Real* PhiMC = static_cast<const Real*>(a.PhiMC);
-  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * M * kRMax;
-  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * M * T;
-  const Real* rowmul = static_cast<const Real*>(a.rowmul) + (size_t)q * M;
-  const Real* diagv = static_cast<const Real*>(a.diagv) + (size_t)q * M;
+  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
+  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
+  const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
   const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
   const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
   Real vt[RMAX];
@@ -525,17 +533,17 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
   for (int l0 = 0; l0 < M; l0 += LT) {
     __syncthreads();
     for (int idx = tid; idx < LT * RMAX; idx += 64) {
-      const int i = idx / RMAX, j = idx % RMAX, l = l0 + i;
-      zs[i][j] = (l < M) ? Zs[(size_t)l * kRMax + j] : (Real)0;
+      const int i = idx % LT, j = idx / LT, l = l0 + i;
+      zs[i][j] = (l < M) ? Zs[(size_t)j * Mp + l] : (Real)0;
     }
     for (int idx = tid; idx < LT * TT; idx += 64) {
-      const int i = idx / TT, t = idx % TT, l = l0 + i;
-      pt[i][t] = (l < M && t0 + t < T) ? ptil[(size_t)l * T + t0 + t] : (Real)0;
+      const int i = idx % LT, t = idx / LT, l = l0 + i;
+      pt[i][t] = (l < M && t0 + t < T) ? ptil[(size_t)(t0 + t) * Mp + l] : (Real)0;
     }
     for (int i = tid; i < LT; i += 64) {
       const int l = l0 + i;
-      dg[i] = (l < M) ? diagv[l] : (Real)0;
-      rm[i] = (l < M) ? rowmul[l] : (Real)0;
+      dg[i] = (l < M) ? meta[l] : (Real)0;
+      rm[i] = (l < M) ? meta[Mp + l] : (Real)0;
       cp[i] = (l < M) ? a.cpos[l] : -1;
     }
     __syncthreads();
@@ -543,7 +551,7 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
 #pragma unroll
     for (int i = 0; i < LT; ++i) {
       const int l = l0 + i;
-      const Real base = (l < M) ? PhiMC[(size_t)l * C + cc] : (Real)0;
+      const Real base = (l < M) ? PhiMC[(size_t)l * a.ldc + cc] : (Real)0;
       phi[i] = phi_entry<Real, RMAX>(base, zs[i], vt, rm[i], cp[i], c, dg[i]);
     }
 #pragma unroll
@@ -598,14 +606,16 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
 }
 
 // ---------------------------------------------------------------------------
-// final: combine the contingency blocks, locate the worst monitored branch,
-// write the outputs of every topology of the chunk
+// final: combine the contingency blocks (one warp per timestep), locate the
+// worst monitored branch by recomputing the winning contingency's column with
+// the same arithmetic as the N-1 kernel, write every output of the topology
 // ---------------------------------------------------------------------------
 template <class Real, int RMAX>
 __global__ __launch_bounds__(128) void k_final(Args a) {
   const int q = blockIdx.x;
   const QInfo qi = a.qi[q];
-  const int tau = qi.tau, T = a.T, M = a.M, C = a.C, tid = threadIdx.x;
+  const int tau = qi.tau, T = a.T, M = a.M, C = a.C, Mp = a.Mpad, tid = threadIdx.x;
+  const int lane = tid & 31, nw = blockDim.x >> 5;
   const dcflow_results& o = a.out;
   if (tid == 0) {
     o.island_flag[tau] = (uint8_t)qi.status;
@@ -626,54 +636,55 @@ __global__ __launch_bounds__(128) void k_final(Args a) {
     return;
   }
   const Real* PhiMC = static_cast<const Real*>(a.PhiMC);
-  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * M * kRMax;
-  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * M * T;
-  const Real* rowmul = static_cast<const Real*>(a.rowmul) + (size_t)q * M;
-  const Real* diagv = static_cast<const Real*>(a.diagv) + (size_t)q * M;
+  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
+  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
+  const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
   const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
   const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
-  __shared__ double bestv;
-  __shared__ int besta;
-  __shared__ double rv[4];
-  __shared__ int ra[4];
-  for (int t = 0; t < T; ++t) {
-    if (tid == 0) {
-      double bv = -1.0, ovl = 0.0;
-      int ba = -1;
-      for (int b = 0; b < a.ncb; ++b) {
-        const size_t k = ((size_t)q * T + t) * a.ncb + b;
-        const double v = (double)static_cast<const Real*>(a.pmax)[k];
-        const int ar = a.parg[k];
-        if (ar >= 0 && v > bv) {
-          bv = v;
-          ba = ar;
-        }
-        ovl += a.povl[k];
+  for (int t = tid >> 5; t < T; t += nw) {
+    double bv = -1.0, ovl = 0.0;
+    int ba = 0x7fffffff;
+    for (int b = lane; b < a.ncb; b += 32) {
+      const size_t k = ((size_t)q * T + t) * a.ncb + b;
+      const double v = (double)static_cast<const Real*>(a.pmax)[k];
+      const int ar = a.parg[k];
+      if (ar >= 0 && (v > bv || (v == bv && ar < ba))) {
+        bv = v;
+        ba = ar;
       }
-      const size_t k = (size_t)tau * T + t;
-      o.n1_max_loading[k] = ba >= 0 ? bv : 0.0;
-      o.overload_sum[k] = ovl;
-      o.worst_cont[k] = ba;
-      if (o.best_var) o.best_var[k] = -1;
-      bestv = bv;
-      besta = ba;
+      ovl += a.povl[k];
     }
-    __syncthreads();
-    const int c = besta;
+    for (int off = 16; off; off >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int a2 = __shfl_xor_sync(0xffffffffu, ba, off);
+      ovl += __shfl_xor_sync(0xffffffffu, ovl, off);
+      if (v2 > bv || (v2 == bv && a2 < ba)) {
+        bv = v2;
+        ba = a2;
+      }
+    }
+    const int c = (ba == 0x7fffffff) ? -1 : ba;
+    if (lane == 0) {
+      const size_t k = (size_t)tau * T + t;
+      o.n1_max_loading[k] = c >= 0 ? bv : 0.0;
+      o.overload_sum[k] = ovl;
+      o.worst_cont[k] = c;
+      if (o.best_var) o.best_var[k] = -1;
+    }
     if (o.worst_mon) {
-      int arg = 0x7fffffff;
       double v = -1.0;
+      int arg = 0x7fffffff;
       if (c >= 0) {
         Real vt[RMAX];
 #pragma unroll
         for (int j = 0; j < RMAX; ++j) vt[j] = VtR[(size_t)j * C + c];
         const Real st = sv[(size_t)t * C + c];
-        for (int l = tid; l < M; l += blockDim.x) {
+        for (int l = lane; l < M; l += 32) {
           Real zr[RMAX];
 #pragma unroll
-          for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)l * kRMax + j];
-          const Real ph = phi_entry<Real, RMAX>(PhiMC[(size_t)l * C + c], zr, vt, rowmul[l], a.cpos[l], c, diagv[l]);
-          const double x = (double)fabs(fma(ph, st, ptil[(size_t)l * T + t]));
+          for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
+          const Real ph = phi_entry<Real, RMAX>(PhiMC[(size_t)l * a.ldc + c], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
+          const double x = (double)fabs(fma(ph, st, ptil[(size_t)t * Mp + l]));
           if (x > v) {
             v = x;
             arg = l;
@@ -688,27 +699,14 @@ __global__ __launch_bounds__(128) void k_final(Args a) {
           arg = a2;
         }
       }
-      if ((tid & 31) == 0) {
-        rv[tid >> 5] = v;
-        ra[tid >> 5] = arg;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        double bv = rv[0];
-        int ba = ra[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-          if (rv[w] > bv || (rv[w] == bv && ra[w] < ba)) {
-            bv = rv[w];
-            ba = ra[w];
-          }
-        o.worst_mon[(size_t)tau * T + t] = (c >= 0) ? ba : -1;
-      }
+      if (lane == 0) o.worst_mon[(size_t)tau * T + t] = (c >= 0) ? arg : -1;
     }
-    __syncthreads();
   }
 }
 
 }  // namespace dcf
+
+#include "n1_tma.cuh"
 
 using namespace dcf;
 
@@ -768,6 +766,75 @@ void launch_final(const Args& a, int RMAX, cudaStream_t st) {
 
 int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Row-major FP32 tensor of `rank` dims (innermost first); strides in bytes for dims 1..rank-1.
+int encode_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+               const uint32_t* box) {
+  auto fn = tensor_map_encoder();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return DCFLOW_ERR_CUDA;
+  }
+  cuuint64_t d[5], s[4];
+  cuuint32_t b[5], e[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+    e[i] = 1;
+    if (i + 1 < rank) s[i] = strides[i];
+  }
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void*>(base), d, s, b, e,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return DCFLOW_ERR_CUDA;
+  }
+  return 0;
+}
+
+template <int TT, int RMAX>
+int launch_tma_t(const N1Maps& maps, const Args& a, dim3 grid, cudaStream_t st, int t0) {
+  using L = TmaLayout<TT, RMAX>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_n1_tma<TT, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) != cudaSuccess)
+      return DCFLOW_ERR_CUDA;
+    attr = true;
+  }
+  k_n1_tma<TT, RMAX><<<grid, kCB, L::kBytes, st>>>(maps, a, t0);
+  return 0;
+}
+
+template <int RMAX>
+int launch_tma_r(const N1Maps& maps, const Args& a, int TT, dim3 grid, cudaStream_t st, int t0) {
+  switch (TT) {
+    case 1: return launch_tma_t<1, RMAX>(maps, a, grid, st, t0);
+    case 4: return launch_tma_t<4, RMAX>(maps, a, grid, st, t0);
+    case 8: return launch_tma_t<8, RMAX>(maps, a, grid, st, t0);
+    case 16: return launch_tma_t<16, RMAX>(maps, a, grid, st, t0);
+    case 24: return launch_tma_t<24, RMAX>(maps, a, grid, st, t0);
+    default: return launch_tma_t<32, RMAX>(maps, a, grid, st, t0);
+  }
+}
+
+int launch_tma(const N1Maps& maps, const Args& a, int RMAX, int TT, dim3 grid, cudaStream_t st, int t0) {
+  if (RMAX == 4) return launch_tma_r<4>(maps, a, TT, grid, st, t0);
+  if (RMAX == 8) return launch_tma_r<8>(maps, a, TT, grid, st, t0);
+  return launch_tma_r<16>(maps, a, TT, grid, st, t0);
+}
+
 }  // namespace
 
 extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_results* res, void* stream) {
@@ -809,8 +876,16 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   ++ctx->launches;
   DCF_CHECK_LAUNCH();
   std::vector<int8_t> hr(N);
+  int herr = 0;
+  if (ctx->err.ensure(sizeof(int))) return DCFLOW_ERR_OOM;
   DCF_CUDA(cudaMemcpyAsync(hr.data(), ctx->rank.p, N, cudaMemcpyDeviceToHost, st));
+  DCF_CUDA(cudaMemcpyAsync(&herr, ctx->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   DCF_CUDA(cudaStreamSynchronize(st));
+  if (herr) {  // a bounded device wait of an earlier call expired
+    DCF_CUDA(cudaMemsetAsync(ctx->err.p, 0, sizeof(int), st));
+    set_error("dcflow_solve_batch: a bounded device wait of an earlier call expired");
+    return DCFLOW_ERR_TIMEOUT;
+  }
   std::vector<int> perm;
   perm.reserve(N);
   std::vector<int> cls_start(4, 0);
@@ -827,9 +902,10 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   DCF_CUDA(cudaMemcpyAsync(ctx->perm.p, perm.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
   // chunk capacity from a scratch budget
   const int ncb = (C + 63) / 64;
+  const int Mp = (int)round_up(M, 16);
   const size_t per_slot = (size_t)kEntMax * (sizeof(int) + sizeof(double) + 1) + (kRMax + 1) * 2 + sizeof(QInfo) +
                           (size_t)kRMax * kRMax * 8 + (size_t)kRMax * T * 8 + (size_t)kRMax * C * (8 + rs) +
-                          (size_t)M * (kRMax + T + 2) * rs + (size_t)T * C * rs + C + 4 +
+                          (size_t)Mp * (kRMax + T + 4) * rs + (size_t)T * C * rs + C + 4 +
                           (size_t)T * ncb * (rs + 4 + 8) + 64;
   int64_t cap = ctx->opt.chunk_topo > 0 ? ctx->opt.chunk_topo : (int64_t)((size_t)2 << 30) / (int64_t)per_slot;
   cap = std::max<int64_t>(1, std::min<int64_t>({cap, 8192, (int64_t)N}));
@@ -839,8 +915,8 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
         ctx->ent_s.ensure(c * kEntMax) || ctx->ent_w.ensure(c * kEntMax * sizeof(double)) ||
         ctx->mod_ptr.ensure(c * (kRMax + 1) * sizeof(int16_t)) || ctx->Kinv.ensure(c * kRMax * kRMax * 8) ||
         ctx->alpha.ensure(c * kRMax * T * 8) || ctx->Vt64.ensure(c * kRMax * std::max(C, 1) * 8) ||
-        (!fp64 && ctx->VtR.ensure(c * kRMax * std::max(C, 1) * rs)) || ctx->Zs.ensure(c * M * kRMax * rs) ||
-        ctx->ptil.ensure(c * M * T * rs) || ctx->rowmul.ensure(c * M * rs) || ctx->diagv.ensure(c * M * rs) ||
+        (!fp64 && ctx->VtR.ensure(c * kRMax * std::max(C, 1) * rs)) || ctx->Zs.ensure(c * Mp * kRMax * rs) ||
+        ctx->ptil.ensure(c * Mp * T * rs) || ctx->diagv.ensure(c * 4 * Mp * rs) ||
         ctx->s.ensure(c * T * std::max(C, 1) * rs) || ctx->valid.ensure(c * std::max(C, 1)) ||
         ctx->nisl.ensure(c * sizeof(int)) || ctx->pmax.ensure(c * T * std::max(ncb, 1) * rs) ||
         ctx->parg.ensure(c * T * std::max(ncb, 1) * sizeof(int)) ||
@@ -874,7 +950,7 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   a.VtR = fp64 ? ctx->Vt64.p : ctx->VtR.p;
   a.Zs = ctx->Zs.p;
   a.ptil = ctx->ptil.p;
-  a.rowmul = ctx->rowmul.p;
+  a.rowmul = nullptr;
   a.diagv = ctx->diagv.p;
   a.s = ctx->s.p;
   a.valid = ctx->valid.as<uint8_t>();
@@ -883,7 +959,23 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   a.parg = ctx->parg.as<int>();
   a.povl = ctx->povl.as<double>();
   a.ncb = ncb;
+  a.Mpad = Mp;
+  a.ldc = ctx->ldc;
+  a.err = ctx->err.as<int>();
   a.out = *res;
+  // tensor maps of the TMA-staged N-1 kernel (FP32 form); the per-topology maps
+  // (zt, pt) depend on the rank class and the pass width and are encoded per launch
+  N1Maps maps;
+  if (!fp64 && C > 0) {
+    const uint64_t d_phi[2] = {(uint64_t)C, (uint64_t)M}, s_phi[1] = {(uint64_t)ctx->ldc * 4};
+    const uint32_t b_phi[2] = {kCB, kLT};
+    const uint64_t d_me[3] = {(uint64_t)M, 4, (uint64_t)cap};
+    const uint64_t s_me[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * 16};
+    const uint32_t b_me[3] = {kLT, 4, 1};
+    int rc = encode_map(&maps.phi, ctx->PhiMC.p, 2, d_phi, s_phi, b_phi);
+    if (!rc) rc = encode_map(&maps.meta, ctx->diagv.p, 3, d_me, s_me, b_me);
+    if (rc) return rc;
+  }
   const int TT = pick_tt(T, fp64);
   const size_t dyn = (size_t)kRMax * T * rs;
   for (int ci = 0; ci < 3; ++ci) {
@@ -916,8 +1008,20 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
             ctx->prof_used += 2;
             DCF_CUDA(cudaEventRecord(e0, st));
           }
-          int rc = fp64 ? launch_n1<double>(a, classes[ci], TT, grid, st, t0)
-                        : launch_n1<float>(a, classes[ci], TT, grid, st, t0);
+          int rc;
+          if (fp64) {
+            rc = launch_n1<double>(a, classes[ci], TT, grid, st, t0);
+          } else {
+            const uint64_t d_zt[3] = {(uint64_t)M, (uint64_t)kRMax, (uint64_t)cap};
+            const uint64_t s_zt[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * kRMax * 4};
+            const uint32_t b_zt[3] = {kLT, (uint32_t)classes[ci], 1};
+            const uint64_t d_pt[3] = {(uint64_t)M, (uint64_t)T, (uint64_t)cap};
+            const uint64_t s_pt[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * T * 4};
+            const uint32_t b_pt[3] = {kLT, (uint32_t)TT, 1};
+            rc = encode_map(&maps.zt, ctx->Zs.p, 3, d_zt, s_zt, b_zt);
+            if (!rc) rc = encode_map(&maps.pt, ctx->ptil.p, 3, d_pt, s_pt, b_pt);
+            if (!rc) rc = launch_tma(maps, a, classes[ci], TT, grid, st, t0);
+          }
           if (rc) return rc;
           ++ctx->launches;
           DCF_CHECK_LAUNCH();
