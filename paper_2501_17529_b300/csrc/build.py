@@ -12,7 +12,6 @@ PKG = os.path.dirname(HERE)
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libdcflow.so")
 SOURCES = ["api.cu", "dense64.cu", "setup.cu", "solve.cu", "noalloc.cu"]
-HEADERS = ["internal.cuh", "dense64.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -27,7 +26,8 @@ def needs_build() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(HERE, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "dcflow.h")]
+    deps = [os.path.join(HERE, f) for f in os.listdir(HERE) if f.endswith((".cu", ".cuh"))]
+    deps.append(os.path.join(ROOT, "include", "dcflow.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
 

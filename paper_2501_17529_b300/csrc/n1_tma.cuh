@@ -21,7 +21,7 @@ namespace dcf {
 
 constexpr int kLT = 16;     // monitored rows per tile
 constexpr int kCB = 64;     // contingencies per block
-constexpr int kStages = 2;  // TMA ring depth
+constexpr int kStages = 3;  // TMA ring depth
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier wait
 
 template <int TT, int RMAX>
@@ -36,10 +36,13 @@ struct TmaLayout {
   static constexpr int kOffPt = kOffZt + a128(kZt);
   static constexpr int kOffMeta = kOffPt + a128(kPt);
   static constexpr int kStage = kOffMeta + a128(kMeta);
-  static constexpr int kOffS = kStages * kStage;             // float s[TT][kCB]
+  static constexpr int kOffPh = kStages * kStage;             // float2 ph[kLT/2][kCB]: the built Phi_f tile
+  static constexpr int kOffS = kOffPh + kLT * kCB * 4;        // float s[TT][kCB]
   static constexpr int kOffOv = kOffS + a128(TT * kCB * 4);   // float ov[TT][kCB]
   static constexpr int kOffBar = kOffOv + a128(TT * kCB * 4); // uint64 bar[kStages]
-  static constexpr int kBytes = kOffBar + 64 + 128;           // + alignment slack
+  static constexpr int kOffOk = kOffBar + 64;                 // uint8 ok[kCB]
+  static constexpr int kOffQ = kOffOk + 128;                  // uint16 queue[warps][32 * TT]
+  static constexpr int kBytes = kOffQ + (kCB / 32) * 2 * 32 * TT * 2;  // one queue per warp (up to 4 warps)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -93,23 +96,39 @@ struct N1Maps {
   CUtensorMap phi, zt, pt, meta;
 };
 
-template <int TT, int RMAX>
-__global__ __launch_bounds__(kCB) void k_n1_tma(const __grid_constant__ N1Maps maps, Args a, int t0) {
+// NTH threads per contingency, each owning TT / NTH timesteps; the block
+// builds each tile's Phi_f [16 rows x 64 contingencies] once into shared memory
+// (thread group th builds rows th*16/NTH ...), then every thread reads its
+// contingency's 16 values back.
+template <int TT, int RMAX, int NTH>
+__global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1Maps maps, Args a, int t0) {
   using L = TmaLayout<TT, RMAX>;
+  constexpr int TH = TT / NTH;    // timesteps per thread
+  constexpr int RB = kLT / NTH;   // tile rows built per thread
+  static_assert(TT % NTH == 0 && RB % 4 == 0, "tile split");
   const int q = blockIdx.y;
   const QInfo qi = a.qi[q];
   if (qi.status != ST_OK) return;  // whole block: before any barrier
-  extern __shared__ unsigned char smraw[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
+  // the dynamic shared block starts 128-byte aligned (no static shared memory in
+  // this kernel); indexing it directly keeps every access in the shared space
+  extern __shared__ __align__(128) unsigned char sm[];
+  if (smem_u32(sm) & 127u) {  // the TMA destinations need the alignment: refuse, never fault
+    if (threadIdx.x == 0) atomicExch(a.err, 2);
+    return;
+  }
+  float2* s_ph = reinterpret_cast<float2*>(sm + L::kOffPh);
   float* s_s = reinterpret_cast<float*>(sm + L::kOffS);
   float* s_ov = reinterpret_cast<float*>(sm + L::kOffOv);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kOffBar);
-  const int tid = threadIdx.x, M = a.M, C = a.C, T = a.T;
-  const int c0 = blockIdx.x * kCB, c = c0 + tid;
+  const int tid = threadIdx.x, cl = tid % kCB, th = tid / kCB;
+  const int M = a.M, C = a.C, T = a.T;
+  const int c0 = blockIdx.x * kCB, c = c0 + cl;
   const bool cin = c < C;
   const int cc = cin ? c : C - 1;
   const float* VtR = static_cast<const float*>(a.VtR) + (size_t)q * kRMax * C;
   const float* sv = static_cast<const float*>(a.s) + (size_t)q * T * C;
+  // monitored row of this contingency's own branch (LODF[c, c] = -1 override), or -1
+  const int drow = cin ? a.mpos[c] : -1;
   float2 nvt[RMAX];
 #pragma unroll
   for (int j = 0; j < RMAX; ++j) {
@@ -117,9 +136,10 @@ __global__ __launch_bounds__(kCB) void k_n1_tma(const __grid_constant__ N1Maps m
     nvt[j] = make_float2(v, v);
   }
 #pragma unroll
-  for (int t = 0; t < TT; ++t) {
-    s_s[t * kCB + tid] = (cin && t0 + t < T) ? sv[(size_t)(t0 + t) * C + cc] : 0.f;
-    s_ov[t * kCB + tid] = 0.f;
+  for (int tt = 0; tt < TH; ++tt) {
+    const int t = th * TH + tt;
+    s_s[t * kCB + cl] = (cin && t0 + t < T) ? sv[(size_t)(t0 + t) * C + cc] : 0.f;
+    s_ov[t * kCB + cl] = 0.f;  // overload partial sums, scaled by 2^-20
   }
   if (tid == 0) {
     for (int st = 0; st < kStages; ++st) mbar_init(smem_u32(&bars[st]), 1);
@@ -140,48 +160,70 @@ __global__ __launch_bounds__(kCB) void k_n1_tma(const __grid_constant__ N1Maps m
   };
   if (tid == 0)
     for (int k = 0; k < kStages - 1 && k < ntiles; ++k) issue(k);
-  float mx[TT];
+  float mx[TH];
 #pragma unroll
-  for (int t = 0; t < TT; ++t) mx[t] = 0.f;
+  for (int tt = 0; tt < TH; ++tt) mx[tt] = 0.f;
   bool failed = false;
   for (int k = 0; k < ntiles; ++k) {
-    if (tid == 0 && k + kStages - 1 < ntiles) issue(k + kStages - 1);
     const int st = k % kStages;
     const bool got = mbar_wait(smem_u32(&bars[st]), (uint32_t)((k / kStages) & 1));
-    if (__syncthreads_or(!got)) {  // block-uniform decision
+    // one barrier: the block-uniform failure decision, and proof that every
+    // thread is done with tile k-1 (its stage is refilled next, its Phi_f rebuilt)
+    if (__syncthreads_or(!got)) {
       failed = true;
-      // wait (bounded) for this block's copies still in flight before leaving
-      const int last = min(ntiles - 1, k + kStages - 1);
+      const int last = min(ntiles - 1, k + kStages - 2);
       for (int k2 = k; k2 <= last; ++k2) mbar_wait(smem_u32(&bars[k2 % kStages]), (uint32_t)((k2 / kStages) & 1));
       break;
     }
+    if (tid == 0 && k + kStages - 1 < ntiles) issue(k + kStages - 1);
     const unsigned char* base = sm + st * L::kStage;
     const float* phi_t = reinterpret_cast<const float*>(base);
     const float* zt_t = reinterpret_cast<const float*>(base + L::kOffZt);
     const float* pt_t = reinterpret_cast<const float*>(base + L::kOffPt);
     const float* meta_t = reinterpret_cast<const float*>(base + L::kOffMeta);
-    // Phi_f / limit for this thread's contingency and the tile's 16 rows
-    float2 ph[kLT / 2];
+    {  // build rows [th*RB, th*RB + RB) of Phi_f / limit for contingency cl
+      const int r0 = th * RB;
+      float2 p[RB / 2];
 #pragma unroll
-    for (int i2 = 0; i2 < kLT / 2; ++i2) {
-      float2 p = make_float2(phi_t[(2 * i2) * kCB + tid], phi_t[(2 * i2 + 1) * kCB + tid]);
+      for (int i2 = 0; i2 < RB / 2; ++i2)
+        p[i2] = make_float2(phi_t[(r0 + 2 * i2) * kCB + cl], phi_t[(r0 + 2 * i2 + 1) * kCB + cl]);
 #pragma unroll
       for (int j = 0; j < RMAX; ++j) {
-        const float2 z = *reinterpret_cast<const float2*>(&zt_t[j * kLT + 2 * i2]);
-        p = __ffma2_rn(z, nvt[j], p);
-      }
-      const float2 rm = *reinterpret_cast<const float2*>(&meta_t[1 * kLT + 2 * i2]);
-      p = __fmul2_rn(p, rm);
-      const float2 dg = *reinterpret_cast<const float2*>(&meta_t[0 * kLT + 2 * i2]);
-      const int2 cp = *reinterpret_cast<const int2*>(&meta_t[2 * kLT + 2 * i2]);
-      if (cp.x == c) p.x = dg.x;
-      if (cp.y == c) p.y = dg.y;
-      ph[i2] = p;
-    }
 #pragma unroll
-    for (int t = 0; t < TT; ++t) {
-      const float s = s_s[t * kCB + tid];
-      const float2 s2 = make_float2(s, s);
+        for (int i4 = 0; i4 < RB / 4; ++i4) {
+          const float4 z = *reinterpret_cast<const float4*>(&zt_t[j * kLT + r0 + 4 * i4]);
+          p[2 * i4] = __ffma2_rn(make_float2(z.x, z.y), nvt[j], p[2 * i4]);
+          p[2 * i4 + 1] = __ffma2_rn(make_float2(z.z, z.w), nvt[j], p[2 * i4 + 1]);
+        }
+      }
+#pragma unroll
+      for (int i4 = 0; i4 < RB / 4; ++i4) {
+        const float4 rm = *reinterpret_cast<const float4*>(&meta_t[1 * kLT + r0 + 4 * i4]);
+        p[2 * i4] = __fmul2_rn(p[2 * i4], make_float2(rm.x, rm.y));
+        p[2 * i4 + 1] = __fmul2_rn(p[2 * i4 + 1], make_float2(rm.z, rm.w));
+      }
+      const int dr = drow - k * kLT - r0;
+      if ((unsigned)dr < (unsigned)RB) {  // LODF[c, c] = -1: Phi_f entry := -den_c / limit
+        const float dg = meta_t[r0 + dr];
+#pragma unroll
+        for (int i2 = 0; i2 < RB / 2; ++i2) {
+          if (2 * i2 == dr) p[i2].x = dg;
+          if (2 * i2 + 1 == dr) p[i2].y = dg;
+        }
+      }
+#pragma unroll
+      for (int i2 = 0; i2 < RB / 2; ++i2) s_ph[(r0 / 2 + i2) * kCB + cl] = p[i2];
+    }
+    __syncthreads();
+    float2 ph[kLT / 2];
+#pragma unroll
+    for (int i2 = 0; i2 < kLT / 2; ++i2) ph[i2] = s_ph[i2 * kCB + cl];
+    float mt[TH];
+#pragma unroll
+    for (int tt = 0; tt < TH; ++tt) {
+      const int t = th * TH + tt;
+      const float stv = s_s[t * kCB + cl];
+      const float2 s2 = make_float2(stv, stv);
       float2 v[kLT / 2];
 #pragma unroll
       for (int i4 = 0; i4 < kLT / 4; ++i4) {
@@ -189,72 +231,86 @@ __global__ __launch_bounds__(kCB) void k_n1_tma(const __grid_constant__ N1Maps m
         v[2 * i4] = __ffma2_rn(ph[2 * i4], s2, make_float2(p4.x, p4.y));
         v[2 * i4 + 1] = __ffma2_rn(ph[2 * i4 + 1], s2, make_float2(p4.z, p4.w));
       }
-      float m = max3abs(v[0].x, v[0].y, v[1].x);
-      m = max3abs(m, v[1].y, v[2].x);
-      m = max3abs(m, v[2].y, v[3].x);
-      m = max3abs(m, v[3].y, v[4].x);
-      m = max3abs(m, v[4].y, v[5].x);
-      m = max3abs(m, v[5].y, v[6].x);
-      m = max3abs(m, v[6].y, v[7].x);
-      m = max3abs(m, v[7].y, v[7].y);
-      mx[t] = fmaxf(mx[t], m);
-      if (m > 1.0f) {
-        float o = 0.f;
+      const float m0 = max3abs(v[0].x, v[0].y, v[1].x);
+      const float m1 = max3abs(v[1].y, v[2].x, v[2].y);
+      const float m2 = max3abs(v[3].x, v[3].y, v[4].x);
+      const float m3 = max3abs(v[4].y, v[5].x, v[5].y);
+      const float m4 = max3abs(v[6].x, v[6].y, v[7].x);
+      const float m = fmaxf(fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)), max3abs(m4, v[7].y, v[7].y));
+      mt[tt] = m;
+      mx[tt] = fmaxf(mx[tt], m);
+    }
+    // overload sum only for (tile, timestep, contingency) items whose tile max
+    // exceeds 1 (a few percent): the warp queues them timestep by timestep
+    // (one ballot per timestep) and serves the queue with all lanes; items of
+    // one timestep read the same p_f row (broadcast) and the built tile in s_ph
+    {
+      const int lane = tid & 31, cb = (tid & (kCB - 1)) & ~31;  // first contingency of this warp
+      uint16_t* queue = reinterpret_cast<uint16_t*>(sm + L::kOffQ) + (tid >> 5) * 32 * TT;
+      const uint32_t lt = (1u << lane) - 1u;
+      int n = 0;
 #pragma unroll
-        for (int i2 = 0; i2 < kLT / 2; ++i2) {
-          o += __saturatef(fmaf(fabsf(v[i2].x), 0x1p-20f, -0x1p-20f));
-          o += __saturatef(fmaf(fabsf(v[i2].y), 0x1p-20f, -0x1p-20f));
+      for (int tt = 0; tt < TH; ++tt) {
+        const bool hit = mt[tt] > 1.0f;
+        const uint32_t msk = __ballot_sync(0xffffffffu, hit);
+        if (hit) queue[n + __popc(msk & lt)] = (uint16_t)(tt * 32 + lane);
+        n += __popc(msk);
+      }
+      if (n) {
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+          const int item = queue[j];
+          const int t = th * TH + (item >> 5), cj = cb + (item & 31);
+          const float stv = s_s[t * kCB + cj];
+          const float2 s2 = make_float2(stv, stv);
+          float2 o2 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int i4 = 0; i4 < kLT / 4; ++i4) {
+            const float4 p4 = *reinterpret_cast<const float4*>(&pt_t[t * kLT + 4 * i4]);
+            const float2 va = __ffma2_rn(s_ph[(2 * i4) * kCB + cj], s2, make_float2(p4.x, p4.y));
+            const float2 vb = __ffma2_rn(s_ph[(2 * i4 + 1) * kCB + cj], s2, make_float2(p4.z, p4.w));
+            o2 = __fadd2_rn(o2, make_float2(__saturatef(fmaf(fabsf(va.x), 0x1p-20f, -0x1p-20f)),
+                                            __saturatef(fmaf(fabsf(va.y), 0x1p-20f, -0x1p-20f))));
+            o2 = __fadd2_rn(o2, make_float2(__saturatef(fmaf(fabsf(vb.x), 0x1p-20f, -0x1p-20f)),
+                                            __saturatef(fmaf(fabsf(vb.y), 0x1p-20f, -0x1p-20f))));
+          }
+          s_ov[t * kCB + cj] += o2.x + o2.y;  // items of one tile are distinct (t, contingency) pairs
         }
-        s_ov[t * kCB + tid] += o;
+        __syncwarp();
       }
     }
-    __syncthreads();  // every thread is done with this stage before it is refilled
   }
   if (failed) {
     if (tid == 0) atomicExch(a.err, 1);
     return;
   }
-  // reduce the 64 contingencies of this block: max (ties: lowest c) and overload sum
-  const bool ok = cin && a.valid[(size_t)q * C + c];
-  __shared__ double rv[2], ro[2];
-  __shared__ int ra[2];
-  const int lane = tid & 31, w = tid >> 5;
+  // per-timestep maxima to shared memory (the s array is no longer needed), then
+  // one thread per timestep scans the 64 contingencies in order: max with the
+  // lowest contingency on ties, and the overload sum in a fixed order
+  __syncthreads();
 #pragma unroll
-  for (int t = 0; t < TT; ++t) {
-    if (t0 + t < T) {
-      double v = ok ? (double)mx[t] : -1.0;
-      int arg = ok ? c : 0x7fffffff;
-      double o = ok ? (double)s_ov[t * kCB + tid] * 1048576.0 : 0.0;
-#pragma unroll
-      for (int off = 16; off; off >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
-        const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
-        o += __shfl_xor_sync(0xffffffffu, o, off);
-        if (v2 > v || (v2 == v && a2 < arg)) {
-          v = v2;
-          arg = a2;
-        }
+  for (int tt = 0; tt < TH; ++tt) s_s[(th * TH + tt) * kCB + cl] = mx[tt];
+  uint8_t* okc = sm + L::kOffOk;
+  if (th == 0) okc[cl] = cin && a.valid[(size_t)q * C + c];
+  __syncthreads();
+  for (int t = tid; t < TT; t += kCB * NTH) {
+    if (t0 + t >= T) continue;
+    float bv = -1.f;
+    int ba = -1;
+    double o = 0.0;
+    for (int k2 = 0; k2 < kCB; ++k2) {
+      if (!okc[k2]) continue;
+      const float v = s_s[t * kCB + k2];
+      if (v > bv) {
+        bv = v;
+        ba = c0 + k2;
       }
-      if (lane == 0) {
-        rv[w] = v;
-        ra[w] = arg;
-        ro[w] = o;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        double bv = rv[0];
-        int ba = ra[0];
-        if (rv[1] > bv || (rv[1] == bv && ra[1] < ba)) {
-          bv = rv[1];
-          ba = ra[1];
-        }
-        const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + blockIdx.x;
-        static_cast<float*>(a.pmax)[o2] = (float)bv;
-        a.parg[o2] = (bv < 0.0) ? -1 : ba;
-        a.povl[o2] = ro[0] + ro[1];
-      }
-      __syncthreads();
+      o += (double)s_ov[t * kCB + k2] * 1048576.0;
     }
+    const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + blockIdx.x;
+    static_cast<float*>(a.pmax)[o2] = bv;
+    a.parg[o2] = ba;
+    a.povl[o2] = o;
   }
 }
 

@@ -807,13 +807,15 @@ int encode_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
 template <int TT, int RMAX>
 int launch_tma_t(const N1Maps& maps, const Args& a, dim3 grid, cudaStream_t st, int t0) {
   using L = TmaLayout<TT, RMAX>;
+  constexpr int NTH = TT >= 16 ? 2 : 1;  // threads per contingency
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_n1_tma<TT, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_n1_tma<TT, RMAX, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) !=
+        cudaSuccess)
       return DCFLOW_ERR_CUDA;
     attr = true;
   }
-  k_n1_tma<TT, RMAX><<<grid, kCB, L::kBytes, st>>>(maps, a, t0);
+  k_n1_tma<TT, RMAX, NTH><<<grid, kCB * NTH, L::kBytes, st>>>(maps, a, t0);
   return 0;
 }
 
@@ -881,10 +883,11 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   DCF_CUDA(cudaMemcpyAsync(hr.data(), ctx->rank.p, N, cudaMemcpyDeviceToHost, st));
   DCF_CUDA(cudaMemcpyAsync(&herr, ctx->err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   DCF_CUDA(cudaStreamSynchronize(st));
-  if (herr) {  // a bounded device wait of an earlier call expired
+  if (herr) {  // a kernel of an earlier call gave up: bounded wait expired (1) or misaligned staging (2)
     DCF_CUDA(cudaMemsetAsync(ctx->err.p, 0, sizeof(int), st));
-    set_error("dcflow_solve_batch: a bounded device wait of an earlier call expired");
-    return DCFLOW_ERR_TIMEOUT;
+    set_error(herr == 1 ? "dcflow_solve_batch: a bounded device wait of an earlier call expired"
+                        : "dcflow_solve_batch: an earlier call found its shared staging buffer misaligned");
+    return herr == 1 ? DCFLOW_ERR_TIMEOUT : DCFLOW_ERR_CUDA;
   }
   std::vector<int> perm;
   perm.reserve(N);
