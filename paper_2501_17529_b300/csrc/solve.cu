@@ -230,7 +230,7 @@ __device__ __forceinline__ double z_entry(const EntSmem& S, const double* PhiRow
   return z;
 }
 
-template <class Real>
+template <class Real, int RMAX>
 __global__ __launch_bounds__(128) void k_small(Args a) {
   const int q = blockIdx.x;
   __shared__ EntSmem S;
@@ -251,6 +251,7 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
     K[i][j] = acc;
   }
   if (tid == 0) bad = 0;
+  for (int p = tid; p < kRMax * (kRMax + 1); p += blockDim.x) (&Ki[0][0])[p] = 0.0;
   __syncthreads();
   if (tid < 32) {
     int isl = 0;
@@ -271,29 +272,28 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
     }
     if (!isl && tid < r) {
       const int j = tid;
-      double y[kRMax];
+      double y[RMAX];
 #pragma unroll
-      for (int i = 0; i < kRMax; ++i) {
+      for (int i = 0; i < RMAX; ++i) {
         if (i < r) {
           double s = (i == j) ? 1.0 : 0.0;
 #pragma unroll
-          for (int p = 0; p < kRMax; ++p)
-            if (p < i) s = fma(-K[i][p], y[p], s);
+          for (int p = 0; p < i; ++p) s = fma(-K[i][p], y[p], s);
           y[i] = s;
         }
       }
 #pragma unroll
-      for (int i = kRMax - 1; i >= 0; --i) {
+      for (int i = RMAX - 1; i >= 0; --i) {
         if (i < r) {
           double s = y[i];
 #pragma unroll
-          for (int p = 0; p < kRMax; ++p)
-            if (p > i && p < r) s = fma(-K[i][p], y[p], s);
+          for (int p = i + 1; p < RMAX; ++p)
+            if (p < r) s = fma(-K[i][p], y[p], s);
           y[i] = s / K[i][i];
         }
       }
 #pragma unroll
-      for (int i = 0; i < kRMax; ++i)
+      for (int i = 0; i < RMAX; ++i)
         if (i < r) Ki[i][j] = y[i];
     }
     if (tid == 0) bad = isl;
@@ -311,20 +311,19 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
   // alpha[j][t]
   const int T = a.T;
   for (int t = tid; t < T; t += blockDim.x) {
-    double bv[kRMax];
+    double bv[RMAX];
 #pragma unroll
-    for (int i = 0; i < kRMax; ++i) {
+    for (int i = 0; i < RMAX; ++i) {
       double acc = 0.0;
       if (i < r)
         for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) acc = fma((double)S.es[e], a.p0[(size_t)S.en[e] * T + t], acc);
       bv[i] = acc;
     }
 #pragma unroll
-    for (int j = 0; j < kRMax; ++j) {
+    for (int j = 0; j < RMAX; ++j) {
       double x = 0.0;
 #pragma unroll
-      for (int i = 0; i < kRMax; ++i)
-        if (i < r && j < r) x = fma(Ki[j][i], bv[i], x);
+      for (int i = 0; i < RMAX; ++i) x = fma(Ki[j][i], bv[i], x);  // Ki is zero outside r x r
       a.alpha[((size_t)q * kRMax + j) * T + t] = x;
     }
   }
@@ -333,9 +332,9 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
   Real* VtR = static_cast<Real*>(a.VtR);
   for (int c = tid; c < C; c += blockDim.x) {
     const int nc = a.contN[c];
-    double v[kRMax];
+    double v[RMAX];
 #pragma unroll
-    for (int i = 0; i < kRMax; ++i) {
+    for (int i = 0; i < RMAX; ++i) {
       double acc = 0.0;
       if (i < r)
         for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
@@ -346,11 +345,10 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
       v[i] = acc;
     }
 #pragma unroll
-    for (int j = 0; j < kRMax; ++j) {
+    for (int j = 0; j < RMAX; ++j) {
       double x = 0.0;
 #pragma unroll
-      for (int i = 0; i < kRMax; ++i)
-        if (i < r && j < r) x = fma(Ki[j][i], v[i], x);
+      for (int i = 0; i < RMAX; ++i) x = fma(Ki[j][i], v[i], x);  // Ki is zero outside r x r
       const size_t o = ((size_t)q * kRMax + j) * C + c;
       a.Vt64[o] = x;
       VtR[o] = (Real)x;
@@ -367,7 +365,7 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
 //   meta [4][Mpad]      row 0: -den_c / limit_l on the row of contingency c,
 //                       row 1: 1 (0 for an outaged l), row 2: position of l in
 //                       the contingency list as int bits (-1 if none), row 3: 0
-template <class Real>
+template <class Real, int RMAX>
 __global__ __launch_bounds__(128) void k_rows(Args a) {
   const int q = blockIdx.x;
   __shared__ EntSmem S;
@@ -385,7 +383,7 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     nisl = 0;
   }
   for (int i = tid; i < r - ks; i += blockDim.x) outN[i] = S.en[S.mp[ks + i]];
-  for (int p = tid; p < kRMax * T; p += blockDim.x) alph[p] = (Real)a.alpha[(size_t)q * kRMax * T + p];
+  for (int p = tid; p < RMAX * T; p += blockDim.x) alph[p] = (Real)a.alpha[(size_t)q * kRMax * T + p];
   __syncthreads();
   Real* Zs = static_cast<Real*>(a.Zs) + (size_t)q * kRMax * Mp;
   Real* ptil = static_cast<Real*>(a.ptil) + (size_t)q * T * Mp;
@@ -397,12 +395,12 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     bool outd = false;
     for (int k = 0; k < nout; ++k) outd |= (outN[k] == nl);
     const double* prow = a.PhiN + (size_t)nl * NN;
-    Real z[kRMax];
+    Real z[RMAX];
 #pragma unroll
-    for (int j = 0; j < kRMax; ++j) z[j] = (j < r) ? (Real)z_entry(S, prow, nl, j) : (Real)0;
+    for (int j = 0; j < RMAX; ++j) z[j] = (j < r) ? (Real)z_entry(S, prow, nl, j) : (Real)0;
     const Real il = (Real)a.inv_lim[l];
 #pragma unroll
-    for (int j = 0; j < kRMax; ++j) Zs[(size_t)j * Mp + l] = outd ? (Real)0 : z[j] * il;
+    for (int j = 0; j < RMAX; ++j) Zs[(size_t)j * Mp + l] = outd ? (Real)0 : z[j] * il;
     meta[l] = (Real)0;
     meta[Mp + l] = outd ? (Real)0 : (Real)1;
     if (sizeof(Real) == 4) {
@@ -414,7 +412,7 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     for (int t = 0; t < T; ++t) {
       Real pf = (Real)a.p0[(size_t)nl * T + t];
 #pragma unroll
-      for (int j = 0; j < kRMax; ++j) pf = fma(-z[j], alph[j * T + t], pf);
+      for (int j = 0; j < RMAX; ++j) pf = fma(-z[j], alph[j * T + t], pf);
       ptil[(size_t)t * Mp + l] = outd ? (Real)0 : pf * il;
       if (a.out.n0_flow) a.out.n0_flow[((size_t)tau * T + t) * M + l] = outd ? 0.0 : (double)pf;
     }
@@ -427,12 +425,12 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     bool outd = false;
     for (int k = 0; k < nout; ++k) outd |= (outN[k] == nc);
     const double* prow = a.PhiN + (size_t)nc * NN;
-    double z[kRMax];
+    double z[RMAX];
 #pragma unroll
-    for (int j = 0; j < kRMax; ++j) z[j] = (j < r) ? z_entry(S, prow, nc, j) : 0.0;
+    for (int j = 0; j < RMAX; ++j) z[j] = (j < r) ? z_entry(S, prow, nc, j) : 0.0;
     double phicc = prow[nc];
 #pragma unroll
-    for (int j = 0; j < kRMax; ++j) phicc = fma(-z[j], Vt64[(size_t)j * C + c], phicc);
+    for (int j = 0; j < RMAX; ++j) phicc = fma(-z[j], Vt64[(size_t)j * C + c], phicc);
     const double den = 1.0 - phicc;
     const bool ok = !outd && den > a.tol;
     my_isl += (!outd && !ok);
@@ -443,7 +441,7 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     for (int t = 0; t < T; ++t) {
       Real pf = (Real)a.p0[(size_t)nc * T + t];
 #pragma unroll
-      for (int j = 0; j < kRMax; ++j) pf = fma(-(Real)z[j], alph[j * T + t], pf);
+      for (int j = 0; j < RMAX; ++j) pf = fma(-(Real)z[j], alph[j * T + t], pf);
       sv[(size_t)t * C + c] = (Real)((double)pf * invd);
     }
   }
@@ -766,6 +764,21 @@ void launch_final(const Args& a, int RMAX, cudaStream_t st) {
 
 int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
 
+// per-topology r x r systems and row operands of one chunk
+template <class Real>
+void launch_prep(const Args& a, int RMAX, int nq, size_t dyn, cudaStream_t st) {
+  if (RMAX == 4) {
+    k_small<Real, 4><<<nq, 128, 0, st>>>(a);
+    k_rows<Real, 4><<<nq, 128, dyn, st>>>(a);
+  } else if (RMAX == 8) {
+    k_small<Real, 8><<<nq, 128, 0, st>>>(a);
+    k_rows<Real, 8><<<nq, 128, dyn, st>>>(a);
+  } else {
+    k_small<Real, 16><<<nq, 128, 0, st>>>(a);
+    k_rows<Real, 16><<<nq, 128, dyn, st>>>(a);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -987,13 +1000,8 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
       a.nq = nq;
       const int* dperm = ctx->perm.as<int>() + c0;
       k_decode<<<(nq + 127) / 128, 128, 0, st>>>(g, in, dperm, a);
-      if (fp64) {
-        k_small<double><<<nq, 128, 0, st>>>(a);
-        k_rows<double><<<nq, 128, dyn, st>>>(a);
-      } else {
-        k_small<float><<<nq, 128, 0, st>>>(a);
-        k_rows<float><<<nq, 128, dyn, st>>>(a);
-      }
+      if (fp64) launch_prep<double>(a, classes[ci], nq, dyn, st);
+      else launch_prep<float>(a, classes[ci], nq, dyn, st);
       ctx->launches += 3;
       DCF_CHECK_LAUNCH();
       if (C > 0) {
