@@ -37,11 +37,14 @@ extern "C" void dcflow_destroy(dcflow_ctx* ctx) {
   dcf::DevBuf* bufs[] = {&ctx->f, &ctx->t, &ctx->b, &ctx->inc_ptr, &ctx->inc_list, &ctx->rid, &ctx->L, &ctx->info,
                          &ctx->nidx, &ctx->split_ok, &ctx->monN, &ctx->contN, &ctx->cpos_of_mon, &ctx->mpos_of_cont,
                          &ctx->inv_lim, &ctx->PhiN, &ctx->PtdfN, &ctx->PhiMC, &ctx->Y, &ctx->p0, &ctx->dp,
-                         &ctx->rank, &ctx->status, &ctx->perm, &ctx->hist, &ctx->hist_host, &ctx->ent_n, &ctx->ent_s,
-                         &ctx->ent_w, &ctx->mod_ptr, &ctx->q_info, &ctx->Kinv, &ctx->alpha, &ctx->Vt64, &ctx->VtR,
-                         &ctx->Zs, &ctx->ptil, &ctx->rowmul, &ctx->diagv, &ctx->s, &ctx->valid, &ctx->nisl,
-                         &ctx->pmax, &ctx->parg, &ctx->povl, &ctx->vmax, &ctx->Gs, &ctx->Gc, &ctx->err};
+                         &ctx->rank, &ctx->status, &ctx->perm, &ctx->hist, &ctx->hist_host, &ctx->err};
   for (auto* b : bufs) b->release();
+  ctx->bufs[0].release_all();
+  ctx->bufs[1].release_all();
+  cudaEvent_t evs[] = {ctx->ev_ready, ctx->ev_prep[0], ctx->ev_prep[1], ctx->ev_free[0], ctx->ev_free[1]};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   delete ctx;
 }

@@ -45,6 +45,19 @@ struct DevBuf {
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Per-chunk scratch of dcflow_solve_batch; two sets alternate so that one
+// chunk's preparation overlaps the previous chunk's N-1 kernel.
+struct ChunkBufs {
+  DevBuf ent_n, ent_s, ent_w, mod_ptr, q_info;
+  DevBuf Kinv, alpha, Vt64, VtR, Zs, ptil, meta, s, valid, nisl;
+  DevBuf pmax, parg, povl;
+  void release_all() {
+    DevBuf* b[] = {&ent_n, &ent_s, &ent_w, &mod_ptr, &q_info, &Kinv, &alpha, &Vt64, &VtR, &Zs,
+                   &ptil, &meta, &s, &valid, &nisl, &pmax, &parg, &povl};
+    for (auto* x : b) x->release();
+  }
+};
+
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace dcf
@@ -78,9 +91,9 @@ struct dcflow_ctx {
   dcf::DevBuf p0;          // double[NN*T]
   dcf::DevBuf dp;          // double[NN*U] base flow change of each candidate
   dcf::DevBuf rank, status, perm, hist, hist_host;
-  dcf::DevBuf ent_n, ent_s, ent_w, mod_ptr, q_info;
-  dcf::DevBuf Kinv, alpha, Vt64, VtR, Zs, ptil, rowmul, diagv, s, valid, nisl;
-  dcf::DevBuf pmax, parg, povl, vmax, Gs, Gc;
+  dcf::ChunkBufs bufs[2];
+  cudaStream_t side = nullptr;           // preparation stream (created on first use)
+  cudaEvent_t ev_ready = nullptr, ev_prep[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   dcf::DevBuf err;         // int: set by a kernel whose bounded wait expired
   int64_t launches = 0;
   int64_t chunk_cap = 0;

@@ -916,7 +916,10 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   cls_start[3] = N;
   if (ctx->perm.ensure(sizeof(int) * N)) return DCFLOW_ERR_OOM;
   DCF_CUDA(cudaMemcpyAsync(ctx->perm.p, perm.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-  // chunk capacity from a scratch budget
+  // chunk capacity from a scratch budget per buffer set (two sets alternate);
+  // large chunks keep the N-1 launches wide (measured better than many small
+  // overlapping chunks: the N-1 kernel fills the SMs' registers and shared
+  // memory, so preparation kernels of the next chunk only run in its tail)
   const int ncb = (C + 63) / 64;
   const int Mp = (int)round_up(M, 16);
   const size_t per_slot = (size_t)kEntMax * (sizeof(int) + sizeof(double) + 1) + (kRMax + 1) * 2 + sizeof(QInfo) +
@@ -925,125 +928,148 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
                           (size_t)T * ncb * (rs + 4 + 8) + 64;
   int64_t cap = ctx->opt.chunk_topo > 0 ? ctx->opt.chunk_topo : (int64_t)((size_t)2 << 30) / (int64_t)per_slot;
   cap = std::max<int64_t>(1, std::min<int64_t>({cap, 8192, (int64_t)N}));
-  {
+  for (int bi = 0; bi < 2; ++bi) {
     const size_t c = (size_t)cap;
-    if (ctx->q_info.ensure(c * sizeof(QInfo)) || ctx->ent_n.ensure(c * kEntMax * sizeof(int)) ||
-        ctx->ent_s.ensure(c * kEntMax) || ctx->ent_w.ensure(c * kEntMax * sizeof(double)) ||
-        ctx->mod_ptr.ensure(c * (kRMax + 1) * sizeof(int16_t)) || ctx->Kinv.ensure(c * kRMax * kRMax * 8) ||
-        ctx->alpha.ensure(c * kRMax * T * 8) || ctx->Vt64.ensure(c * kRMax * std::max(C, 1) * 8) ||
-        (!fp64 && ctx->VtR.ensure(c * kRMax * std::max(C, 1) * rs)) || ctx->Zs.ensure(c * Mp * kRMax * rs) ||
-        ctx->ptil.ensure(c * Mp * T * rs) || ctx->diagv.ensure(c * 4 * Mp * rs) ||
-        ctx->s.ensure(c * T * std::max(C, 1) * rs) || ctx->valid.ensure(c * std::max(C, 1)) ||
-        ctx->nisl.ensure(c * sizeof(int)) || ctx->pmax.ensure(c * T * std::max(ncb, 1) * rs) ||
-        ctx->parg.ensure(c * T * std::max(ncb, 1) * sizeof(int)) ||
-        ctx->povl.ensure(c * T * std::max(ncb, 1) * sizeof(double)))
+    ChunkBufs& B = ctx->bufs[bi];
+    if (B.q_info.ensure(c * sizeof(QInfo)) || B.ent_n.ensure(c * kEntMax * sizeof(int)) ||
+        B.ent_s.ensure(c * kEntMax) || B.ent_w.ensure(c * kEntMax * sizeof(double)) ||
+        B.mod_ptr.ensure(c * (kRMax + 1) * sizeof(int16_t)) || B.Kinv.ensure(c * kRMax * kRMax * 8) ||
+        B.alpha.ensure(c * kRMax * T * 8) || B.Vt64.ensure(c * kRMax * std::max(C, 1) * 8) ||
+        (!fp64 && B.VtR.ensure(c * kRMax * std::max(C, 1) * rs)) || B.Zs.ensure(c * Mp * kRMax * rs) ||
+        B.ptil.ensure(c * Mp * T * rs) || B.meta.ensure(c * 4 * Mp * rs) ||
+        B.s.ensure(c * T * std::max(C, 1) * rs) || B.valid.ensure(c * std::max(C, 1)) ||
+        B.nisl.ensure(c * sizeof(int)) || B.pmax.ensure(c * T * std::max(ncb, 1) * rs) ||
+        B.parg.ensure(c * T * std::max(ncb, 1) * sizeof(int)) ||
+        B.povl.ensure(c * T * std::max(ncb, 1) * sizeof(double)))
       return DCFLOW_ERR_OOM;
-    ctx->chunk_cap = cap;
   }
-  Args a{};
-  a.M = M;
-  a.C = C;
-  a.NN = NN;
-  a.T = T;
-  a.U = 0;
-  a.monN = ctx->monN.as<int>();
-  a.contN = ctx->contN.as<int>();
-  a.cpos = ctx->cpos_of_mon.as<int>();
-  a.mpos = ctx->mpos_of_cont.as<int>();
-  a.inv_lim = ctx->inv_lim.as<double>();
-  a.PhiN = ctx->PhiN.as<double>();
-  a.PhiMC = ctx->PhiMC.p;
-  a.p0 = ctx->p0.as<double>();
-  a.tol = ctx->opt.island_tol;
-  a.qi = ctx->q_info.as<QInfo>();
-  a.ent_n = ctx->ent_n.as<int>();
-  a.ent_s = ctx->ent_s.as<int8_t>();
-  a.ent_w = ctx->ent_w.as<double>();
-  a.mod_ptr = ctx->mod_ptr.as<int16_t>();
-  a.Kinv = ctx->Kinv.as<double>();
-  a.alpha = ctx->alpha.as<double>();
-  a.Vt64 = ctx->Vt64.as<double>();
-  a.VtR = fp64 ? ctx->Vt64.p : ctx->VtR.p;
-  a.Zs = ctx->Zs.p;
-  a.ptil = ctx->ptil.p;
-  a.rowmul = nullptr;
-  a.diagv = ctx->diagv.p;
-  a.s = ctx->s.p;
-  a.valid = ctx->valid.as<uint8_t>();
-  a.nisl = ctx->nisl.as<int>();
-  a.pmax = ctx->pmax.p;
-  a.parg = ctx->parg.as<int>();
-  a.povl = ctx->povl.as<double>();
-  a.ncb = ncb;
-  a.Mpad = Mp;
-  a.ldc = ctx->ldc;
-  a.err = ctx->err.as<int>();
-  a.out = *res;
-  // tensor maps of the TMA-staged N-1 kernel (FP32 form); the per-topology maps
-  // (zt, pt) depend on the rank class and the pass width and are encoded per launch
-  N1Maps maps;
-  if (!fp64 && C > 0) {
-    const uint64_t d_phi[2] = {(uint64_t)C, (uint64_t)M}, s_phi[1] = {(uint64_t)ctx->ldc * 4};
-    const uint32_t b_phi[2] = {kCB, kLT};
-    const uint64_t d_me[3] = {(uint64_t)M, 4, (uint64_t)cap};
-    const uint64_t s_me[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * 16};
-    const uint32_t b_me[3] = {kLT, 4, 1};
-    int rc = encode_map(&maps.phi, ctx->PhiMC.p, 2, d_phi, s_phi, b_phi);
-    if (!rc) rc = encode_map(&maps.meta, ctx->diagv.p, 3, d_me, s_me, b_me);
-    if (rc) return rc;
+  ctx->chunk_cap = cap;
+  if (!ctx->side) {
+    DCF_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    cudaEvent_t* evs[] = {&ctx->ev_ready, &ctx->ev_prep[0], &ctx->ev_prep[1], &ctx->ev_free[0], &ctx->ev_free[1]};
+    for (cudaEvent_t* e : evs) DCF_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   }
+  Args base{};
+  base.M = M;
+  base.C = C;
+  base.NN = NN;
+  base.T = T;
+  base.U = 0;
+  base.monN = ctx->monN.as<int>();
+  base.contN = ctx->contN.as<int>();
+  base.cpos = ctx->cpos_of_mon.as<int>();
+  base.mpos = ctx->mpos_of_cont.as<int>();
+  base.inv_lim = ctx->inv_lim.as<double>();
+  base.PhiN = ctx->PhiN.as<double>();
+  base.PhiMC = ctx->PhiMC.p;
+  base.p0 = ctx->p0.as<double>();
+  base.tol = ctx->opt.island_tol;
+  base.ncb = ncb;
+  base.Mpad = Mp;
+  base.ldc = ctx->ldc;
+  base.err = ctx->err.as<int>();
+  base.out = *res;
+  auto chunk_args = [&](int bi) {
+    Args a = base;
+    ChunkBufs& B = ctx->bufs[bi];
+    a.qi = B.q_info.as<QInfo>();
+    a.ent_n = B.ent_n.as<int>();
+    a.ent_s = B.ent_s.as<int8_t>();
+    a.ent_w = B.ent_w.as<double>();
+    a.mod_ptr = B.mod_ptr.as<int16_t>();
+    a.Kinv = B.Kinv.as<double>();
+    a.alpha = B.alpha.as<double>();
+    a.Vt64 = B.Vt64.as<double>();
+    a.VtR = fp64 ? B.Vt64.p : B.VtR.p;
+    a.Zs = B.Zs.p;
+    a.ptil = B.ptil.p;
+    a.rowmul = nullptr;
+    a.diagv = B.meta.p;
+    a.s = B.s.p;
+    a.valid = B.valid.as<uint8_t>();
+    a.nisl = B.nisl.as<int>();
+    a.pmax = B.pmax.p;
+    a.parg = B.parg.as<int>();
+    a.povl = B.povl.as<double>();
+    return a;
+  };
   const int TT = pick_tt(T, fp64);
   const size_t dyn = (size_t)kRMax * T * rs;
-  for (int ci = 0; ci < 3; ++ci) {
-    for (int c0 = cls_start[ci]; c0 < cls_start[ci + 1]; c0 += (int)cap) {
-      const int nq = std::min<int>((int)cap, cls_start[ci + 1] - c0);
-      a.nq = nq;
-      const int* dperm = ctx->perm.as<int>() + c0;
-      k_decode<<<(nq + 127) / 128, 128, 0, st>>>(g, in, dperm, a);
-      if (fp64) launch_prep<double>(a, classes[ci], nq, dyn, st);
-      else launch_prep<float>(a, classes[ci], nq, dyn, st);
-      ctx->launches += 3;
-      DCF_CHECK_LAUNCH();
-      if (C > 0) {
-        for (int t0 = 0; t0 < T; t0 += TT) {
-          const dim3 grid(ncb, nq);
-          cudaEvent_t e0 = nullptr, e1 = nullptr;
-          if (ctx->prof_on) {
-            while (ctx->prof_ev.size() < ctx->prof_used + 2) {
-              cudaEvent_t e;
-              DCF_CUDA(cudaEventCreate(&e));
-              ctx->prof_ev.push_back(e);
-            }
-            e0 = ctx->prof_ev[ctx->prof_used];
-            e1 = ctx->prof_ev[ctx->prof_used + 1];
-            ctx->prof_used += 2;
-            DCF_CUDA(cudaEventRecord(e0, st));
-          }
-          int rc;
-          if (fp64) {
-            rc = launch_n1<double>(a, classes[ci], TT, grid, st, t0);
-          } else {
-            const uint64_t d_zt[3] = {(uint64_t)M, (uint64_t)kRMax, (uint64_t)cap};
-            const uint64_t s_zt[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * kRMax * 4};
-            const uint32_t b_zt[3] = {kLT, (uint32_t)classes[ci], 1};
-            const uint64_t d_pt[3] = {(uint64_t)M, (uint64_t)T, (uint64_t)cap};
-            const uint64_t s_pt[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * T * 4};
-            const uint32_t b_pt[3] = {kLT, (uint32_t)TT, 1};
-            rc = encode_map(&maps.zt, ctx->Zs.p, 3, d_zt, s_zt, b_zt);
-            if (!rc) rc = encode_map(&maps.pt, ctx->ptil.p, 3, d_pt, s_pt, b_pt);
-            if (!rc) rc = launch_tma(maps, a, classes[ci], TT, grid, st, t0);
-          }
-          if (rc) return rc;
-          ++ctx->launches;
-          DCF_CHECK_LAUNCH();
-          if (ctx->prof_on) DCF_CUDA(cudaEventRecord(e1, st));
-        }
+  // chunk plan: rank class by rank class
+  struct Chunk {
+    int cls, c0, nq;
+  };
+  std::vector<Chunk> plan;
+  for (int ci = 0; ci < 3; ++ci)
+    for (int c0 = cls_start[ci]; c0 < cls_start[ci + 1]; c0 += (int)cap)
+      plan.push_back({ci, c0, std::min<int>((int)cap, cls_start[ci + 1] - c0)});
+  // two-stream pipeline: preparation of chunk i (decode, r x r systems, row
+  // operands; FP64-heavy) on the side stream overlaps the N-1 and final
+  // kernels of chunk i-1 (FP32) on the caller's stream
+  cudaStream_t side = ctx->side;
+  DCF_CUDA(cudaEventRecord(ctx->ev_ready, st));
+  DCF_CUDA(cudaStreamWaitEvent(side, ctx->ev_ready, 0));
+  for (size_t i = 0; i < plan.size(); ++i) {
+    const Chunk& ch = plan[i];
+    const int bi = (int)(i & 1);
+    Args a = chunk_args(bi);
+    a.nq = ch.nq;
+    const int RMAX = classes[ch.cls];
+    if (i >= 2) DCF_CUDA(cudaStreamWaitEvent(side, ctx->ev_free[bi], 0));
+    const int* dperm = ctx->perm.as<int>() + ch.c0;
+    k_decode<<<(ch.nq + 127) / 128, 128, 0, side>>>(g, in, dperm, a);
+    if (fp64) launch_prep<double>(a, RMAX, ch.nq, dyn, side);
+    else launch_prep<float>(a, RMAX, ch.nq, dyn, side);
+    ctx->launches += 3;
+    DCF_CHECK_LAUNCH();
+    DCF_CUDA(cudaEventRecord(ctx->ev_prep[bi], side));
+    DCF_CUDA(cudaStreamWaitEvent(st, ctx->ev_prep[bi], 0));
+    if (C > 0) {
+      N1Maps maps;
+      if (!fp64) {
+        const uint64_t d_phi[2] = {(uint64_t)C, (uint64_t)M}, s_phi[1] = {(uint64_t)ctx->ldc * 4};
+        const uint32_t b_phi[2] = {kCB, kLT};
+        const uint64_t d_me[3] = {(uint64_t)M, 4, (uint64_t)cap};
+        const uint64_t s_me[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * 16};
+        const uint32_t b_me[3] = {kLT, 4, 1};
+        const uint64_t d_zt[3] = {(uint64_t)M, (uint64_t)kRMax, (uint64_t)cap};
+        const uint64_t s_zt[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * kRMax * 4};
+        const uint32_t b_zt[3] = {kLT, (uint32_t)RMAX, 1};
+        const uint64_t d_pt[3] = {(uint64_t)M, (uint64_t)T, (uint64_t)cap};
+        const uint64_t s_pt[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * T * 4};
+        const uint32_t b_pt[3] = {kLT, (uint32_t)TT, 1};
+        int rc = encode_map(&maps.phi, ctx->PhiMC.p, 2, d_phi, s_phi, b_phi);
+        if (!rc) rc = encode_map(&maps.meta, a.diagv, 3, d_me, s_me, b_me);
+        if (!rc) rc = encode_map(&maps.zt, a.Zs, 3, d_zt, s_zt, b_zt);
+        if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt);
+        if (rc) return rc;
       }
-      if (fp64) launch_final<double>(a, classes[ci], st);
-      else launch_final<float>(a, classes[ci], st);
-      ++ctx->launches;
-      DCF_CHECK_LAUNCH();
+      for (int t0 = 0; t0 < T; t0 += TT) {
+        const dim3 grid(ncb, ch.nq);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (ctx->prof_on) {
+          while (ctx->prof_ev.size() < ctx->prof_used + 2) {
+            cudaEvent_t e;
+            DCF_CUDA(cudaEventCreate(&e));
+            ctx->prof_ev.push_back(e);
+          }
+          e0 = ctx->prof_ev[ctx->prof_used];
+          e1 = ctx->prof_ev[ctx->prof_used + 1];
+          ctx->prof_used += 2;
+          DCF_CUDA(cudaEventRecord(e0, st));
+        }
+        int rc = fp64 ? launch_n1<double>(a, RMAX, TT, grid, st, t0) : launch_tma(maps, a, RMAX, TT, grid, st, t0);
+        if (rc) return rc;
+        ++ctx->launches;
+        DCF_CHECK_LAUNCH();
+        if (ctx->prof_on) DCF_CUDA(cudaEventRecord(e1, st));
+      }
     }
+    if (fp64) launch_final<double>(a, RMAX, st);
+    else launch_final<float>(a, RMAX, st);
+    ++ctx->launches;
+    DCF_CHECK_LAUNCH();
+    DCF_CUDA(cudaEventRecord(ctx->ev_free[bi], st));
   }
   return DCFLOW_OK;
 }
