@@ -51,9 +51,12 @@ struct ChunkBufs {
   DevBuf ent_n, ent_s, ent_w, mod_ptr, q_info;
   DevBuf Kinv, alpha, Vt64, VtR, Zs, ptil, meta, s, valid, nisl;
   DevBuf pmax, parg, povl;
+  // injection candidates: per (timestep, candidate) operands and screening maxima,
+  // the chosen candidate per timestep and its operands
+  DevBuf ptv, svv, pmaxv, pargv, povlv, bestu, ptb, sb;
   void release_all() {
-    DevBuf* b[] = {&ent_n, &ent_s, &ent_w, &mod_ptr, &q_info, &Kinv, &alpha, &Vt64, &VtR, &Zs,
-                   &ptil, &meta, &s, &valid, &nisl, &pmax, &parg, &povl};
+    DevBuf* b[] = {&ent_n, &ent_s, &ent_w, &mod_ptr, &q_info, &Kinv, &alpha, &Vt64, &VtR, &Zs, &ptil, &meta,
+                   &s, &valid, &nisl, &pmax, &parg, &povl, &ptv, &svv, &pmaxv, &pargv, &povlv, &bestu, &ptb, &sb};
     for (auto* x : b) x->release();
   }
 };
@@ -88,7 +91,8 @@ struct dcflow_ctx {
   int ldc = 0;             // round_up(C, 4): 16-byte row pitch for the tensor-memory accelerator
   dcf::DevBuf Y;           // solve workspace
   // batch scratch
-  dcf::DevBuf p0;          // double[NN*T]
+  dcf::DevBuf p0;          // double[NN*(T+R)]: base flows, then R pool columns
+  dcf::DevBuf pool, var_k;  // candidate pool buses; pool index of every candidate entry
   dcf::DevBuf dp;          // double[NN*U] base flow change of each candidate
   dcf::DevBuf rank, status, perm, hist, hist_host;
   dcf::ChunkBufs bufs[2];

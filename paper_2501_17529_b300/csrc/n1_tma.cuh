@@ -100,7 +100,9 @@ struct N1Maps {
 // builds each tile's Phi_f [16 rows x 64 contingencies] once into shared memory
 // (thread group th builds rows th*16/NTH ...), then every thread reads its
 // contingency's 16 values back.
-template <int TT, int RMAX, int NTH>
+// OVL = false drops the overload sum (metric-first screening of injection
+// candidates needs only the maximum loading).
+template <int TT, int RMAX, int NTH, bool OVL>
 __global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1Maps maps, Args a, int t0) {
   using L = TmaLayout<TT, RMAX>;
   constexpr int TH = TT / NTH;    // timesteps per thread
@@ -244,7 +246,7 @@ __global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1
     // exceeds 1 (a few percent): the warp queues them timestep by timestep
     // (one ballot per timestep) and serves the queue with all lanes; items of
     // one timestep read the same p_f row (broadcast) and the built tile in s_ph
-    {
+    if (OVL) {
       const int lane = tid & 31, cb = (tid & (kCB - 1)) & ~31;  // first contingency of this warp
       uint16_t* queue = reinterpret_cast<uint16_t*>(sm + L::kOffQ) + (tid >> 5) * 32 * TT;
       const uint32_t lt = (1u << lane) - 1u;

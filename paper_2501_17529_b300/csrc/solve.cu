@@ -76,6 +76,7 @@ struct Args {
   int* parg;
   double* povl;
   int ncb;
+  const int* best_u;  // chosen injection candidate per (slot, timestep), or null
   int* err;  // set to 1 by a kernel whose bounded wait expired
   // outputs
   dcflow_results out;
@@ -173,7 +174,7 @@ __global__ void k_decode(GridDev g, BatchDev in, const int* perm, Args a) {
 // ---------------------------------------------------------------------------
 // base flows p0 = PTDF[N, :] P_t (Eq. (2)), one warp per needed branch
 // ---------------------------------------------------------------------------
-__global__ void k_p0(int NN, int V, int T, const double* __restrict__ ptdf, const double* __restrict__ inj,
+__global__ void k_p0(int NN, int V, int T, int ldp, const double* __restrict__ ptdf, const double* __restrict__ inj,
                      double* __restrict__ p0) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= NN) return;
@@ -190,9 +191,19 @@ __global__ void k_p0(int NN, int V, int T, const double* __restrict__ ptdf, cons
     for (int k = 0; k < 8; ++k) {
       double v = acc[k];
       for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0 && t0 + k < T) p0[(size_t)warp * T + t0 + k] = v;
+      if (lane == 0 && t0 + k < T) p0[(size_t)warp * ldp + t0 + k] = v;
     }
   }
+}
+
+// Columns T.. of p0 for the injection-candidate pool: the base flow change of
+// one unit injected at each pool bus (a PTDF column, Eq. (3)); the rank-r
+// update then turns them into the topology's own PTDF columns.
+__global__ void k_p0_pool(int NN, int V, int T, int R, int ldp, const int* __restrict__ pool,
+                          const double* __restrict__ ptdf, double* __restrict__ p0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NN) return;
+  for (int k = 0; k < R; ++k) p0[(size_t)i * ldp + T + k] = ptdf[(size_t)i * V + pool[k]];
 }
 
 // ---------------------------------------------------------------------------
@@ -667,7 +678,7 @@ __global__ __launch_bounds__(128) void k_final(Args a) {
       o.n1_max_loading[k] = c >= 0 ? bv : 0.0;
       o.overload_sum[k] = ovl;
       o.worst_cont[k] = c;
-      if (o.best_var) o.best_var[k] = -1;
+      if (o.best_var) o.best_var[k] = a.best_u ? a.best_u[(size_t)q * T + t] : -1;
     }
     if (o.worst_mon) {
       double v = -1.0;
@@ -698,6 +709,107 @@ __global__ __launch_bounds__(128) void k_final(Args a) {
         }
       }
       if (lane == 0) o.worst_mon[(size_t)tau * T + t] = (c >= 0) ? arg : -1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// injection candidates T_i (Sec. III-A, Eq. (8)), metric-first (Sec. III-C):
+// expand every (timestep, candidate) into a virtual timestep, screen them with
+// the max-only N-1 kernel, keep the argmin, gather its operands
+// ---------------------------------------------------------------------------
+// Candidate u adds sum_k d_k e_{pool_k}; by linearity (Eq. (3)) its scaled N-0
+// flows are p~[t] + sum_k d_k p~[T + k] and its N-1 weights s[t] + sum_k d_k s[T + k]
+// (the pool columns went through the same rank-r update as the timesteps).
+template <class Real>
+__global__ void k_var_expand(Args ap, int T, int U, const int* __restrict__ var_ptr, const int* __restrict__ var_k,
+                             const double* __restrict__ var_delta, Real* __restrict__ ptv, Real* __restrict__ svv) {
+  const int q = blockIdx.y;
+  if (ap.qi[q].status != ST_OK) return;
+  const int vt = blockIdx.x, t = vt / U, u = vt % U;
+  const int Text = ap.T, Mp = ap.Mpad, M = ap.M, C = ap.C, TV = T * U;
+  const Real* pt = static_cast<const Real*>(ap.ptil) + (size_t)q * Text * Mp;
+  const Real* sv = static_cast<const Real*>(ap.s) + (size_t)q * Text * C;
+  Real* po = ptv + ((size_t)q * TV + vt) * Mp;
+  Real* so = svv + ((size_t)q * TV + vt) * C;
+  const int k0 = var_ptr[u], k1 = var_ptr[u + 1];
+  for (int l = threadIdx.x; l < M; l += blockDim.x) {
+    Real v = pt[(size_t)t * Mp + l];
+    for (int k = k0; k < k1; ++k) v = fma((Real)var_delta[k], pt[(size_t)(T + var_k[k]) * Mp + l], v);
+    po[l] = v;
+  }
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    Real v = sv[(size_t)t * C + c];
+    for (int k = k0; k < k1; ++k) v = fma((Real)var_delta[k], sv[(size_t)(T + var_k[k]) * C + c], v);
+    so[c] = v;
+  }
+}
+
+// argmin over candidates of the screened maximum loading (ties: lowest index);
+// one warp per (slot, timestep)
+template <class Real>
+__global__ void k_var_select(Args av, int T, int U, int* __restrict__ best_u) {
+  const int q = blockIdx.x, t = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (t >= T) return;
+  if (av.qi[q].status != ST_OK) {
+    if (lane == 0) best_u[(size_t)q * T + t] = -1;
+    return;
+  }
+  const int TV = T * U;
+  double bv = 1e300;
+  int bu = 0x7fffffff;
+  for (int u = lane; u < U; u += 32) {
+    double v = -1.0;
+    for (int b = 0; b < av.ncb; ++b) {
+      const size_t k = ((size_t)q * TV + (size_t)t * U + u) * av.ncb + b;
+      if (av.parg[k] >= 0) v = fmax(v, (double)static_cast<const Real*>(av.pmax)[k]);
+    }
+    if (v < 0.0) v = 0.0;  // no valid contingency: loading 0
+    if (v < bv || (v == bv && u < bu)) {
+      bv = v;
+      bu = u;
+    }
+  }
+  for (int off = 16; off; off >>= 1) {
+    const double v2 = __shfl_xor_sync(0xffffffffu, bv, off);
+    const int u2 = __shfl_xor_sync(0xffffffffu, bu, off);
+    if (v2 < bv || (v2 == bv && u2 < bu)) {
+      bv = v2;
+      bu = u2;
+    }
+  }
+  if (lane == 0) best_u[(size_t)q * T + t] = bu;
+}
+
+// operands of the chosen candidate for the full N-1 pass, and its N-0 outputs
+template <class Real>
+__global__ void k_var_gather(Args af, int U, const Real* __restrict__ ptv, const Real* __restrict__ svv) {
+  const int q = blockIdx.y, t = blockIdx.x;
+  const QInfo qi = af.qi[q];
+  if (qi.status != ST_OK) return;
+  const int T = af.T, Mp = af.Mpad, M = af.M, C = af.C, TV = T * U;
+  const int u = af.best_u[(size_t)q * T + t];
+  const Real* pi = ptv + ((size_t)q * TV + (size_t)t * U + u) * Mp;
+  const Real* si = svv + ((size_t)q * TV + (size_t)t * U + u) * C;
+  Real* po = static_cast<Real*>(af.ptil) + ((size_t)q * T + t) * Mp;
+  Real* so = static_cast<Real*>(af.s) + ((size_t)q * T + t) * C;
+  double m = 0.0;
+  for (int l = threadIdx.x; l < M; l += blockDim.x) {
+    const Real v = pi[l];
+    po[l] = v;
+    m = fmax(m, fabs((double)v));
+    if (af.out.n0_flow) af.out.n0_flow[((size_t)qi.tau * T + t) * M + l] = (double)v / af.inv_lim[l];
+  }
+  for (int c = threadIdx.x; c < C; c += blockDim.x) so[c] = si[c];
+  if (af.out.n0_max_loading) {
+    __shared__ double red[32];
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double x = red[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = fmax(x, red[w]);
+      af.out.n0_max_loading[(size_t)qi.tau * T + t] = x;
     }
   }
 }
@@ -817,19 +929,26 @@ int encode_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
   return 0;
 }
 
-template <int TT, int RMAX>
+template <int TT, int RMAX, bool OVL = true>
 int launch_tma_t(const N1Maps& maps, const Args& a, dim3 grid, cudaStream_t st, int t0) {
   using L = TmaLayout<TT, RMAX>;
   constexpr int NTH = TT >= 16 ? 2 : 1;  // threads per contingency
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_n1_tma<TT, RMAX, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) !=
+    if (cudaFuncSetAttribute(k_n1_tma<TT, RMAX, NTH, OVL>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) !=
         cudaSuccess)
       return DCFLOW_ERR_CUDA;
     attr = true;
   }
-  k_n1_tma<TT, RMAX, NTH><<<grid, kCB * NTH, L::kBytes, st>>>(maps, a, t0);
+  k_n1_tma<TT, RMAX, NTH, OVL><<<grid, kCB * NTH, L::kBytes, st>>>(maps, a, t0);
   return 0;
+}
+
+// max-only pass over 32 virtual timesteps (injection candidates)
+int launch_tma_screen(const N1Maps& maps, const Args& a, int RMAX, dim3 grid, cudaStream_t st, int t0) {
+  if (RMAX == 4) return launch_tma_t<32, 4, false>(maps, a, grid, st, t0);
+  if (RMAX == 8) return launch_tma_t<32, 8, false>(maps, a, grid, st, t0);
+  return launch_tma_t<32, 16, false>(maps, a, grid, st, t0);
 }
 
 template <int RMAX>
@@ -862,8 +981,8 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
     return DCFLOW_ERR_NO_STUDY;
   }
   const int N = bt->n_topo, T = bt->n_time;
-  if (N < 0 || T < 1 || T > 256 || bt->n_var != 0) {
-    set_error("dcflow_solve_batch: n_topo >= 0, 1 <= n_time <= 256 (candidates: see dcflow_solve_batch_var)");
+  if (N < 0 || T < 1 || T > 256 || bt->n_var < 0) {
+    set_error("dcflow_solve_batch: need n_topo >= 0, 1 <= n_time <= 256, n_var >= 0");
     return DCFLOW_ERR_INVALID_ARG;
   }
   ctx->launches = 0;
@@ -877,9 +996,61 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   const bool fp64 = ctx->opt.precision == DCFLOW_FP64;
   const size_t rs = fp64 ? sizeof(double) : sizeof(float);
   const int M = ctx->M, C = ctx->C, NN = ctx->NN;
-  // p0 = PTDF[N, :] inj^T
-  if (ctx->p0.ensure((size_t)NN * T * sizeof(double))) return DCFLOW_ERR_OOM;
-  k_p0<<<(NN * 32 + 255) / 256, 256, 0, st>>>(NN, ctx->V, T, ctx->PtdfN.as<double>(), bt->inj, ctx->p0.as<double>());
+  // injection candidates T_i (Eq. (8)): read the small CSR to the host, validate
+  // it, and map every entry to a pool bus (a column of the extended base flows)
+  const int U = bt->n_var;
+  int R = 0;
+  if (U > 0) {
+    if (!bt->var_ptr || !bt->var_bus || !bt->var_delta || (int64_t)T * U > (1 << 20)) {
+      set_error("dcflow_solve_batch: candidate arrays missing or n_time * n_var > 2^20");
+      return DCFLOW_ERR_INVALID_ARG;
+    }
+    std::vector<int> vp(U + 1);
+    DCF_CUDA(cudaMemcpyAsync(vp.data(), bt->var_ptr, sizeof(int) * (U + 1), cudaMemcpyDeviceToHost, st));
+    DCF_CUDA(cudaStreamSynchronize(st));
+    if (vp[0] != 0) {
+      set_error("dcflow_solve_batch: var_ptr[0] must be 0");
+      return DCFLOW_ERR_INVALID_ARG;
+    }
+    for (int u = 0; u < U; ++u)
+      if (vp[u + 1] < vp[u]) {
+        set_error("dcflow_solve_batch: var_ptr must be non-decreasing");
+        return DCFLOW_ERR_INVALID_ARG;
+      }
+    const int nnz = vp[U];
+    std::vector<int> vb(std::max(nnz, 1));
+    if (nnz) {
+      DCF_CUDA(cudaMemcpyAsync(vb.data(), bt->var_bus, sizeof(int) * nnz, cudaMemcpyDeviceToHost, st));
+      DCF_CUDA(cudaStreamSynchronize(st));
+    }
+    std::vector<int> pool;
+    for (int k = 0; k < nnz; ++k) {
+      if (vb[k] < 0 || vb[k] >= ctx->V) {
+        set_error("dcflow_solve_batch: var_bus out of range");
+        return DCFLOW_ERR_INVALID_ARG;
+      }
+      pool.push_back(vb[k]);
+    }
+    std::sort(pool.begin(), pool.end());
+    pool.erase(std::unique(pool.begin(), pool.end()), pool.end());
+    R = (int)pool.size();
+    std::vector<int> vk(std::max(nnz, 1));
+    for (int k = 0; k < nnz; ++k) vk[k] = (int)(std::lower_bound(pool.begin(), pool.end(), vb[k]) - pool.begin());
+    if (ctx->pool.ensure(sizeof(int) * std::max(R, 1)) || ctx->var_k.ensure(sizeof(int) * std::max(nnz, 1)))
+      return DCFLOW_ERR_OOM;
+    if (R) DCF_CUDA(cudaMemcpyAsync(ctx->pool.p, pool.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+    if (nnz) DCF_CUDA(cudaMemcpyAsync(ctx->var_k.p, vk.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, st));
+  }
+  const int Text = T + R;  // timesteps plus pool columns through the preparation
+  // p0 = PTDF[N, :] inj^T (and the pool columns)
+  if (ctx->p0.ensure((size_t)NN * Text * sizeof(double))) return DCFLOW_ERR_OOM;
+  k_p0<<<(NN * 32 + 255) / 256, 256, 0, st>>>(NN, ctx->V, T, Text, ctx->PtdfN.as<double>(), bt->inj,
+                                               ctx->p0.as<double>());
+  if (R > 0) {
+    k_p0_pool<<<(NN + 127) / 128, 128, 0, st>>>(NN, ctx->V, T, R, Text, ctx->pool.as<int>(), ctx->PtdfN.as<double>(),
+                                                ctx->p0.as<double>());
+    ++ctx->launches;
+  }
   ++ctx->launches;
   DCF_CHECK_LAUNCH();
   GridDev g{ctx->f.as<int>(), ctx->t.as<int>(), ctx->b.as<double>(), ctx->inc_ptr.as<int>(), ctx->inc_list.as<int>(),
@@ -922,10 +1093,17 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   // memory, so preparation kernels of the next chunk only run in its tail)
   const int ncb = (C + 63) / 64;
   const int Mp = (int)round_up(M, 16);
-  const size_t per_slot = (size_t)kEntMax * (sizeof(int) + sizeof(double) + 1) + (kRMax + 1) * 2 + sizeof(QInfo) +
-                          (size_t)kRMax * kRMax * 8 + (size_t)kRMax * T * 8 + (size_t)kRMax * C * (8 + rs) +
-                          (size_t)Mp * (kRMax + T + 4) * rs + (size_t)T * C * rs + C + 4 +
-                          (size_t)T * ncb * (rs + 4 + 8) + 64;
+  const int TV = T * U;  // virtual timesteps: (timestep, candidate) pairs
+  if (R > 64) {
+    set_error("dcflow_solve_batch: at most 64 distinct candidate buses");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  size_t per_slot = (size_t)kEntMax * (sizeof(int) + sizeof(double) + 1) + (kRMax + 1) * 2 + sizeof(QInfo) +
+                    (size_t)kRMax * kRMax * 8 + (size_t)kRMax * Text * 8 + (size_t)kRMax * C * (8 + rs) +
+                    (size_t)Mp * (kRMax + Text + 4) * rs + (size_t)Text * C * rs + C + 4 +
+                    (size_t)T * ncb * (rs + 4 + 8) + 64;
+  if (U > 0)
+    per_slot += (size_t)TV * (Mp + C) * rs + (size_t)TV * ncb * (rs + 4 + 8) + (size_t)T * 4 + (size_t)T * (Mp + C) * rs;
   int64_t cap = ctx->opt.chunk_topo > 0 ? ctx->opt.chunk_topo : (int64_t)((size_t)2 << 30) / (int64_t)per_slot;
   cap = std::max<int64_t>(1, std::min<int64_t>({cap, 8192, (int64_t)N}));
   for (int bi = 0; bi < 2; ++bi) {
@@ -934,13 +1112,19 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
     if (B.q_info.ensure(c * sizeof(QInfo)) || B.ent_n.ensure(c * kEntMax * sizeof(int)) ||
         B.ent_s.ensure(c * kEntMax) || B.ent_w.ensure(c * kEntMax * sizeof(double)) ||
         B.mod_ptr.ensure(c * (kRMax + 1) * sizeof(int16_t)) || B.Kinv.ensure(c * kRMax * kRMax * 8) ||
-        B.alpha.ensure(c * kRMax * T * 8) || B.Vt64.ensure(c * kRMax * std::max(C, 1) * 8) ||
+        B.alpha.ensure(c * kRMax * Text * 8) || B.Vt64.ensure(c * kRMax * std::max(C, 1) * 8) ||
         (!fp64 && B.VtR.ensure(c * kRMax * std::max(C, 1) * rs)) || B.Zs.ensure(c * Mp * kRMax * rs) ||
-        B.ptil.ensure(c * Mp * T * rs) || B.meta.ensure(c * 4 * Mp * rs) ||
-        B.s.ensure(c * T * std::max(C, 1) * rs) || B.valid.ensure(c * std::max(C, 1)) ||
+        B.ptil.ensure(c * Mp * Text * rs) || B.meta.ensure(c * 4 * Mp * rs) ||
+        B.s.ensure(c * Text * std::max(C, 1) * rs) || B.valid.ensure(c * std::max(C, 1)) ||
         B.nisl.ensure(c * sizeof(int)) || B.pmax.ensure(c * T * std::max(ncb, 1) * rs) ||
         B.parg.ensure(c * T * std::max(ncb, 1) * sizeof(int)) ||
         B.povl.ensure(c * T * std::max(ncb, 1) * sizeof(double)))
+      return DCFLOW_ERR_OOM;
+    if (U > 0 && (B.ptv.ensure(c * TV * Mp * rs) || B.svv.ensure(c * TV * std::max(C, 1) * rs) ||
+                  B.pmaxv.ensure(c * TV * std::max(ncb, 1) * rs) ||
+                  B.pargv.ensure(c * TV * std::max(ncb, 1) * sizeof(int)) ||
+                  B.povlv.ensure(c * TV * std::max(ncb, 1) * sizeof(double)) || B.bestu.ensure(c * T * sizeof(int)) ||
+                  B.ptb.ensure(c * T * Mp * rs) || B.sb.ensure(c * T * std::max(C, 1) * rs)))
       return DCFLOW_ERR_OOM;
   }
   ctx->chunk_cap = cap;
@@ -954,7 +1138,7 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   base.C = C;
   base.NN = NN;
   base.T = T;
-  base.U = 0;
+  base.U = U;
   base.monN = ctx->monN.as<int>();
   base.contN = ctx->contN.as<int>();
   base.cpos = ctx->cpos_of_mon.as<int>();
@@ -968,6 +1152,7 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   base.Mpad = Mp;
   base.ldc = ctx->ldc;
   base.err = ctx->err.as<int>();
+  base.best_u = nullptr;
   base.out = *res;
   auto chunk_args = [&](int bi) {
     Args a = base;
@@ -994,7 +1179,56 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
     return a;
   };
   const int TT = pick_tt(T, fp64);
-  const size_t dyn = (size_t)kRMax * T * rs;
+  const size_t dyn = (size_t)kRMax * Text * rs;
+  // N-1 passes over Tn (virtual) timesteps whose operands are a.ptil / a.s;
+  // ovl = false screens the maximum only (FP32 form)
+  auto run_n1 = [&](const Args& a, int RMAX, int Tn, bool ovl) -> int {
+    const int TTn = ovl ? pick_tt(Tn, fp64) : (fp64 ? 8 : 32);
+    N1Maps maps;
+    if (!fp64) {
+      const uint64_t d_phi[2] = {(uint64_t)C, (uint64_t)M}, s_phi[1] = {(uint64_t)ctx->ldc * 4};
+      const uint32_t b_phi[2] = {kCB, kLT};
+      const uint64_t d_me[3] = {(uint64_t)M, 4, (uint64_t)cap};
+      const uint64_t s_me[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * 16};
+      const uint32_t b_me[3] = {kLT, 4, 1};
+      const uint64_t d_zt[3] = {(uint64_t)M, (uint64_t)kRMax, (uint64_t)cap};
+      const uint64_t s_zt[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * kRMax * 4};
+      const uint32_t b_zt[3] = {kLT, (uint32_t)RMAX, 1};
+      const uint64_t d_pt[3] = {(uint64_t)M, (uint64_t)Tn, (uint64_t)cap};
+      const uint64_t s_pt[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * Tn * 4};
+      const uint32_t b_pt[3] = {kLT, (uint32_t)TTn, 1};
+      int rc = encode_map(&maps.phi, ctx->PhiMC.p, 2, d_phi, s_phi, b_phi);
+      if (!rc) rc = encode_map(&maps.meta, a.diagv, 3, d_me, s_me, b_me);
+      if (!rc) rc = encode_map(&maps.zt, a.Zs, 3, d_zt, s_zt, b_zt);
+      if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt);
+      if (rc) return rc;
+    }
+    for (int t0 = 0; t0 < Tn; t0 += TTn) {
+      const dim3 grid(ncb, a.nq);
+      const bool prof = ctx->prof_on && ovl;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (prof) {
+        while (ctx->prof_ev.size() < ctx->prof_used + 2) {
+          cudaEvent_t e;
+          DCF_CUDA(cudaEventCreate(&e));
+          ctx->prof_ev.push_back(e);
+        }
+        e0 = ctx->prof_ev[ctx->prof_used];
+        e1 = ctx->prof_ev[ctx->prof_used + 1];
+        ctx->prof_used += 2;
+        DCF_CUDA(cudaEventRecord(e0, st));
+      }
+      int rc;
+      if (fp64) rc = launch_n1<double>(a, RMAX, TTn, grid, st, t0);
+      else rc = ovl ? launch_tma(maps, a, RMAX, TTn, grid, st, t0) : launch_tma_screen(maps, a, RMAX, grid, st, t0);
+      if (rc) return rc;
+      ++ctx->launches;
+      DCF_CHECK_LAUNCH();
+      if (prof) DCF_CUDA(cudaEventRecord(e1, st));
+    }
+    return 0;
+  };
+  (void)TT;
   // chunk plan: rank class by rank class
   struct Chunk {
     int cls, c0, nq;
@@ -1012,61 +1246,68 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   for (size_t i = 0; i < plan.size(); ++i) {
     const Chunk& ch = plan[i];
     const int bi = (int)(i & 1);
+    ChunkBufs& B = ctx->bufs[bi];
     Args a = chunk_args(bi);
     a.nq = ch.nq;
     const int RMAX = classes[ch.cls];
+    // preparation: with candidates it carries the pool columns (Text) and leaves
+    // the N-0 outputs to the gather of the chosen candidate
+    Args ap = a;
+    ap.T = Text;
+    if (U > 0) {
+      ap.out.n0_flow = nullptr;
+      ap.out.n0_max_loading = nullptr;
+    }
     if (i >= 2) DCF_CUDA(cudaStreamWaitEvent(side, ctx->ev_free[bi], 0));
     const int* dperm = ctx->perm.as<int>() + ch.c0;
-    k_decode<<<(ch.nq + 127) / 128, 128, 0, side>>>(g, in, dperm, a);
-    if (fp64) launch_prep<double>(a, RMAX, ch.nq, dyn, side);
-    else launch_prep<float>(a, RMAX, ch.nq, dyn, side);
+    k_decode<<<(ch.nq + 127) / 128, 128, 0, side>>>(g, in, dperm, ap);
+    if (fp64) launch_prep<double>(ap, RMAX, ch.nq, dyn, side);
+    else launch_prep<float>(ap, RMAX, ch.nq, dyn, side);
     ctx->launches += 3;
     DCF_CHECK_LAUNCH();
     DCF_CUDA(cudaEventRecord(ctx->ev_prep[bi], side));
     DCF_CUDA(cudaStreamWaitEvent(st, ctx->ev_prep[bi], 0));
-    if (C > 0) {
-      N1Maps maps;
-      if (!fp64) {
-        const uint64_t d_phi[2] = {(uint64_t)C, (uint64_t)M}, s_phi[1] = {(uint64_t)ctx->ldc * 4};
-        const uint32_t b_phi[2] = {kCB, kLT};
-        const uint64_t d_me[3] = {(uint64_t)M, 4, (uint64_t)cap};
-        const uint64_t s_me[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * 16};
-        const uint32_t b_me[3] = {kLT, 4, 1};
-        const uint64_t d_zt[3] = {(uint64_t)M, (uint64_t)kRMax, (uint64_t)cap};
-        const uint64_t s_zt[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * kRMax * 4};
-        const uint32_t b_zt[3] = {kLT, (uint32_t)RMAX, 1};
-        const uint64_t d_pt[3] = {(uint64_t)M, (uint64_t)T, (uint64_t)cap};
-        const uint64_t s_pt[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * T * 4};
-        const uint32_t b_pt[3] = {kLT, (uint32_t)TT, 1};
-        int rc = encode_map(&maps.phi, ctx->PhiMC.p, 2, d_phi, s_phi, b_phi);
-        if (!rc) rc = encode_map(&maps.meta, a.diagv, 3, d_me, s_me, b_me);
-        if (!rc) rc = encode_map(&maps.zt, a.Zs, 3, d_zt, s_zt, b_zt);
-        if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt);
+    Args af = a;  // final stage: T real timesteps
+    if (U > 0) {
+      // expand, screen (metric-first: maximum only), select, gather
+      if (fp64)
+        k_var_expand<double><<<dim3(TV, ch.nq), 128, 0, st>>>(ap, T, U, bt->var_ptr, ctx->var_k.as<int>(),
+                                                               bt->var_delta, B.ptv.as<double>(), B.svv.as<double>());
+      else
+        k_var_expand<float><<<dim3(TV, ch.nq), 128, 0, st>>>(ap, T, U, bt->var_ptr, ctx->var_k.as<int>(),
+                                                              bt->var_delta, B.ptv.as<float>(), B.svv.as<float>());
+      ++ctx->launches;
+      DCF_CHECK_LAUNCH();
+      Args av = a;
+      av.T = TV;
+      av.ptil = B.ptv.p;
+      av.s = B.svv.p;
+      av.pmax = B.pmaxv.p;
+      av.parg = B.pargv.as<int>();
+      av.povl = B.povlv.as<double>();
+      if (C > 0) {
+        int rc = run_n1(av, RMAX, TV, false);
         if (rc) return rc;
+      } else {
+        DCF_CUDA(cudaMemsetAsync(B.pargv.p, 0xff, (size_t)ch.nq * TV * sizeof(int), st));
       }
-      for (int t0 = 0; t0 < T; t0 += TT) {
-        const dim3 grid(ncb, ch.nq);
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (ctx->prof_on) {
-          while (ctx->prof_ev.size() < ctx->prof_used + 2) {
-            cudaEvent_t e;
-            DCF_CUDA(cudaEventCreate(&e));
-            ctx->prof_ev.push_back(e);
-          }
-          e0 = ctx->prof_ev[ctx->prof_used];
-          e1 = ctx->prof_ev[ctx->prof_used + 1];
-          ctx->prof_used += 2;
-          DCF_CUDA(cudaEventRecord(e0, st));
-        }
-        int rc = fp64 ? launch_n1<double>(a, RMAX, TT, grid, st, t0) : launch_tma(maps, a, RMAX, TT, grid, st, t0);
-        if (rc) return rc;
-        ++ctx->launches;
-        DCF_CHECK_LAUNCH();
-        if (ctx->prof_on) DCF_CUDA(cudaEventRecord(e1, st));
-      }
+      const dim3 gs(ch.nq, (T + 7) / 8);
+      if (fp64) k_var_select<double><<<gs, 256, 0, st>>>(av, T, U, B.bestu.as<int>());
+      else k_var_select<float><<<gs, 256, 0, st>>>(av, T, U, B.bestu.as<int>());
+      af.ptil = B.ptb.p;
+      af.s = B.sb.p;
+      af.best_u = B.bestu.as<int>();
+      if (fp64) k_var_gather<double><<<dim3(T, ch.nq), 128, 0, st>>>(af, U, B.ptv.as<double>(), B.svv.as<double>());
+      else k_var_gather<float><<<dim3(T, ch.nq), 128, 0, st>>>(af, U, B.ptv.as<float>(), B.svv.as<float>());
+      ctx->launches += 2;
+      DCF_CHECK_LAUNCH();
     }
-    if (fp64) launch_final<double>(a, RMAX, st);
-    else launch_final<float>(a, RMAX, st);
+    if (C > 0) {
+      int rc = run_n1(af, RMAX, T, true);
+      if (rc) return rc;
+    }
+    if (fp64) launch_final<double>(af, RMAX, st);
+    else launch_final<float>(af, RMAX, st);
     ++ctx->launches;
     DCF_CHECK_LAUNCH();
     DCF_CUDA(cudaEventRecord(ctx->ev_free[bi], st));
