@@ -33,8 +33,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "grid500_splits1-4_outages0-3_T24_fullN1"
-N_TOPO, T_STEPS = 10000, 24
+WORKLOADS = {
+    # name: (shape id, default topologies, description)
+    "grid500": (2, 10000, "grid500_splits1-4_outages0-3_T24_fullN1"),
+    "grid2000": (3, 1000, "grid2000_splits1-8_outages0-4_T8_cand256_mon3000_cont1000"),
+    "grid10000": (4, 50000, "grid10000_splits1-6_T16_mon5000_cont2000"),
+}
 # dram bytes per launch of the dominant kernel from the ncu capture summarised in
 # profiles/k_n1_grid500.md, keyed by the sha1 of the kernel source it was taken on
 N1_TRAFFIC = {}
@@ -123,19 +127,21 @@ def _loadflows(topo, status, n_island_cont, cont, T):
 
 
 def _cpu_worker(args):
-    idx, = args
+    shape, idx = args
     import oracle
     from paper_2501_17529_b300 import synth
-    w = synth.workload(2)
+    w = synth.workload(shape, n_topo=max(idx) + 1)
     lim = oracle.thermal_limits(w.grid, w.inj)
     t0 = time.perf_counter()
-    r = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, idx=idx)
+    r = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, var=w.var, idx=idx)
     dt = time.perf_counter() - t0
-    return oracle.loadflow_count(r, w.inj.shape[0]), dt
+    nv = 0 if w.var is None else w.var.n_var
+    return oracle.loadflow_count(r, w.inj.shape[0], nv), dt
 
 
-def cpu_baseline(budget_s: float = 20.0):
+def cpu_baseline(workload: str, budget_s: float = 20.0):
     """The oracle as it stands on the host cores, on a bounded topology sample."""
+    shape, n_all, _ = WORKLOADS[workload]
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -143,17 +149,18 @@ def cpu_baseline(budget_s: float = 20.0):
     # probe the per-topology cost, then size the sample to the budget
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
-        probe = pool.map(_cpu_worker, [([i],) for i in range(cores)])
+        probe = pool.map(_cpu_worker, [(shape, [i]) for i in range(cores)])
         per_topo = max(1e-3, statistics.median(dt for _, dt in probe))
         n_each = max(1, int(budget_s / per_topo))
-        chunks = [(list(range(cores + k * n_each, cores + (k + 1) * n_each)),) for k in range(cores)]
+        n_each = min(n_each, max(1, (n_all - cores) // cores))
+        chunks = [(shape, list(range(cores + k * n_each, cores + (k + 1) * n_each))) for k in range(cores)]
         t0 = time.perf_counter()
         res = pool.map(_cpu_worker, chunks)
         wall = time.perf_counter() - t0
     lf = sum(r[0] for r in res)
     ntop = n_each * cores
     return {"value": lf / wall, "unit": "loadflows/s", "cores": cores, "kind": "oracle",
-            "sample": f"{ntop} of the {N_TOPO} topologies (x{T_STEPS} timesteps, full N-1), "
+            "sample": f"{ntop} of the {n_all} topologies of {workload} (all timesteps, candidates and contingencies), "
                       f"{cores} spawn workers, 1 BLAS thread each, {wall:.1f} s wall"}
 
 
@@ -163,24 +170,26 @@ def run_reference(args):
         return
     import oracle
     from paper_2501_17529_b300 import synth
-    w = synth.workload(2)
+    shape, n_all, desc = WORKLOADS[args.workload]
+    per = max(1, int(os.environ.get("DCFLOW_REF_TOPO_PER_STEP", "8" if shape == 2 else "1")))
+    w = synth.workload(shape, n_topo=min(n_all, per * (args.warmup + args.steps)))
     lim = oracle.thermal_limits(w.grid, w.inj)
-    per = max(1, int(os.environ.get("DCFLOW_REF_TOPO_PER_STEP", "8")))
+    nv = 0 if w.var is None else w.var.n_var
     times, lfs = [], []
     for s in range(args.warmup + args.steps):
         idx = list(range(s * per, (s + 1) * per))
         t0 = time.perf_counter()
-        r = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, idx=idx)
+        r = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, var=w.var, idx=idx)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
-            lfs.append(oracle.loadflow_count(r, T_STEPS))
+            lfs.append(oracle.loadflow_count(r, w.inj.shape[0], nv))
     value = sum(lfs) / sum(times)
     line = {"impl": "reference", "metric": "N-1 DC loadflows/sec (oracle on host cores)", "value": value,
             "unit": "loadflows/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "topologies_per_step": per, "l2": "n/a (host)"},
+            "config": {"workload": desc, "topologies_per_step": per, "l2": "n/a (host)"},
             "cpu_baseline": {"value": value, "unit": "loadflows/s", "cores": 1, "kind": "oracle",
                              "sample": f"{per} topologies per step, single process"},
             "e2e": {"value": value, "unit": "loadflows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -206,31 +215,39 @@ def run_ours(args):
         cbuild.build()
     if ws > 1:
         dist.barrier()
-    n_topo = args.topologies
-    w = synth.workload(2, n_topo=n_topo)
+    shape, n_default, desc = WORKLOADS[args.workload]
+    n_topo = args.topologies or n_default
+    w = synth.workload(shape, n_topo=n_topo)
     if ws > 1 and rank > 0:  # each rank its own batch of the same shape
-        w.topo = synth.make_topologies(w.grid, w.subs, n_topo, 202 + 1000 * rank, (1, 4), (0, 3))
-    # limits from the unsplit grid's N-0 flows, computed on the device
+        w.topo = synth.make_topologies(w.grid, w.subs, n_topo, 1000 * rank + 200 + shape, (1, 4), (0, 3))
+    # limits from the unsplit grid's N-0 flows on the monitored branches, computed on the device
     base = Solver(w.grid, precision="fp64")
-    pt = base.base_ptdf(np.arange(w.grid.n_branch)).cpu().numpy()
+    pt = base.base_ptdf(w.mon).cpu().numpy()
     base.close()
-    lim = 1.2 * np.abs(w.inj @ pt.T).max(axis=0) + 0.1
+    lim = np.ones(w.grid.n_branch)
+    lim[w.mon] = 1.2 * np.abs(w.inj @ pt.T).max(axis=0) + 0.1
+    n_mon = len(w.mon)
+    T_STEPS = w.inj.shape[0]
 
     results = {}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
     peaks, peak_kind = _peaks()
     for form in (args.forms.split(",")):
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
         solver = Solver(w.grid, precision=form)
         solver.set_study(w.mon, w.cont, lim, split_bus=w.subs)
-        db = DeviceBatch(w.topo, w.inj)
-        res = DeviceResults(db.n_topo, db.n_time, len(w.mon))
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - ts
+        db = DeviceBatch(w.topo, w.inj, w.var)
+        res = DeviceResults(db.n_topo, db.n_time, len(w.mon), want_var=db.n_var > 0)
         stream = torch.cuda.current_stream()
         steps = args.steps if form == "fp32" else max(1, min(args.steps, args.fp64_steps))
         for _ in range(args.warmup):
             solver.solve(db, results=res)
         torch.cuda.synchronize()
         host = res.to_host()
-        lf = _loadflows(w.topo, host["status"], host["n_island_cont"], w.cont, T_STEPS)
+        lf = _loadflows(w.topo, host["status"], host["n_island_cont"], w.cont, T_STEPS) * max(1, db.n_var)
         lib = __import__("paper_2501_17529_b300.dcflow", fromlist=["x"])
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         launches = 0
@@ -267,6 +284,7 @@ def run_ours(args):
         # end to end through host buffers: H2D of the batch, solve, D2H of the results
         if form == "fp32" and not args.no_e2e:
             results[form]["e2e"] = _e2e(solver, w, lim, steps, args.warmup, lf)
+        results[form]["setup_s"] = setup_s
         solver.close()
     if rank != 0:
         if ws > 1:
@@ -282,7 +300,7 @@ def run_ours(args):
         # floor on the CUDA cores is one FP32 issue slot per entry (half a
         # packed FFMA2 for the flow, half a 3-input |max| for the reduction), so
         # the peak is 148 SMs x 128 lanes x the maximum SM clock.
-        entries = head["loadflows_per_step"] * 700 * head["steps"]
+        entries = head["loadflows_per_step"] * n_mon * head["steps"]
         peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
         ach = entries / (k["n1_ms"] / 1e3) / 1e12
         key = (_src_hash(), "fp32")
@@ -296,8 +314,9 @@ def run_ours(args):
             "value": head["value"], "unit": "loadflows/s", "n_gpus": ws, "steps": head["steps"],
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "topologies": args.topologies, "timesteps": T_STEPS, "monitored": 700,
-                       "contingencies": 700, "l2": "flushed between steps (256 MB write)",
+            "config": {"workload": desc, "topologies": n_topo, "timesteps": T_STEPS, "monitored": n_mon,
+                       "contingencies": len(w.cont), "candidates": 0 if w.var is None else w.var.n_var,
+                       "l2": "flushed between steps (256 MB write)",
                        "max_err_stated": {"fp32": 1e-4, "fp64": 1e-10}},
             "gpu_launches": head["launches"], "clocks": head["clocks"],
             "forms": {f: {k: v for k, v in r.items() if k not in ("clocks", "kernel")} for f, r in results.items()}}
@@ -308,7 +327,7 @@ def run_ours(args):
     if roof:
         line["roofline"] = roof
     if ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_budget)
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -319,9 +338,11 @@ def _e2e(solver, w, lim, steps, warmup, lf):
     import torch
     from paper_2501_17529_b300.dcflow import DeviceBatch, DeviceResults
 
-    db = DeviceBatch(w.topo, w.inj)
-    res = DeviceResults(db.n_topo, db.n_time, len(w.mon))
+    db = DeviceBatch(w.topo, w.inj, w.var)
+    res = DeviceResults(db.n_topo, db.n_time, len(w.mon), want_var=db.n_var > 0)
     names = ["split_ptr", "split_sub", "split_mask", "out_ptr", "out_branch", "inj"]
+    if db.n_var:
+        names += ["var_ptr", "var_bus", "var_delta"]
     host_in = {n: getattr(db, n).cpu().pin_memory() for n in names}
     outs = ["n1_max_loading", "overload_sum", "worst_cont", "worst_mon", "island_flag", "n_island_cont"]
     host_out = {n: torch.empty_like(getattr(res, n), device="cpu").pin_memory() for n in outs}
@@ -357,7 +378,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--topologies", type=int, default=N_TOPO, help="batch size (smaller only for profiling)")
+    ap.add_argument("--topologies", type=int, default=0, help="batch size (0 = the workload's own)")
+    ap.add_argument("--workload", default="grid500", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

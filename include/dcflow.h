@@ -216,8 +216,9 @@ int64_t dcflow_last_launch_count(const dcflow_ctx* ctx);
 
 /*
  * Kernel timing.  dcflow_profile(ctx, 1) resets the counters and makes every
- * later dcflow_solve_batch bracket each launch of the fused N-1 kernel with
- * CUDA events recorded on the call's stream; dcflow_profile(ctx, 0) stops.
+ * later dcflow_solve_batch bracket each launch of the fused N-1 kernel (the
+ * candidate screening passes included) with CUDA events recorded on the call's
+ * stream; dcflow_profile(ctx, 0) stops.
  * dcflow_profile_read synchronises on the recorded events and returns the
  * summed N-1 kernel time in milliseconds and the number of such launches.
  */

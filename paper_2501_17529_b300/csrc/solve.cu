@@ -1205,7 +1205,7 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
     }
     for (int t0 = 0; t0 < Tn; t0 += TTn) {
       const dim3 grid(ncb, a.nq);
-      const bool prof = ctx->prof_on && ovl;
+      const bool prof = ctx->prof_on;  // screening and full passes alike
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (prof) {
         while (ctx->prof_ev.size() < ctx->prof_used + 2) {

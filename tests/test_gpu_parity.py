@@ -182,6 +182,47 @@ def test_grid500_full_batch_sampled(precision):
     compare(g2, ref, w, sub, lim, TOL[precision])
 
 
+def _check_candidates(w, lim, precision):
+    """Run the candidate brute force on the GPU and check it against the oracle:
+    the pick must be the oracle's argmin (exact where the runner-up is clear,
+    within tolerance on near-ties), and every output must match the oracle
+    evaluated for the GPU's own pick."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch
+    g, var, inj = w.grid, w.var, w.inj
+    s = _solver(w, lim, precision)
+    out = s.solve(DeviceBatch(w.topo, inj, var), want_flows=True).to_host()
+    torch.cuda.synchronize()
+    s.close()
+    T, U = inj.shape[0], var.n_var
+    # every (timestep, candidate) as its own timestep of the oracle
+    per_u = oracle.evaluate(g, w.topo, np.repeat(inj, U, axis=0) + _cand_matrix(g, var, T), w.mon, w.cont, lim,
+                            want_flows=True, want_cmax=True)
+    tol = TOL[precision]
+    np.testing.assert_array_equal(out["status"], per_u["status"])
+    ok = per_u["status"] == 0
+    assert ok.sum() >= 2
+    assert np.all(out["best_var"][~ok] == -1)
+    ref = {k: per_u[k] for k in ("status", "n_island_cont", "n_valid_cont")}
+    cols = np.zeros((w.topo.n_topo, T), np.int64)
+    for i in range(w.topo.n_topo):
+        for t in range(T):
+            vals = per_u["n1_max"][i, t * U:(t + 1) * U]
+            gu = int(out["best_var"][i, t])
+            if not ok[i]:
+                continue
+            srt = np.sort(vals)
+            if srt.size > 1 and srt[1] - srt[0] > 2 * tol * max(1.0, srt[0]):
+                assert gu == int(np.argmin(vals)), (i, t, gu)
+            else:
+                assert vals[gu] <= srt[0] + 2 * tol * max(1.0, srt[0]), (i, t, gu)
+            cols[i, t] = t * U + gu
+    rows = np.arange(w.topo.n_topo)[:, None]
+    for k in ("n0_max", "n1_max", "ovl", "worst_cont", "worst_mon", "cmax", "n0_flow"):
+        ref[k] = per_u[k][rows, cols]
+    inj_pick = np.repeat(inj, U, axis=0) + _cand_matrix(g, var, T)
+    return out, ref, inj_pick, cols
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_injection_candidates_bruteforce(precision):
     """Injection candidates (Eq. (8), metric-first): argmin over candidates of the
@@ -196,34 +237,23 @@ def test_injection_candidates_bruteforce(precision):
     cont = np.sort(rng.choice(g.n_branch, 90, replace=False)).astype(np.int32)
     w = synth.Workload("cand", g, topo, inj, mon, cont, subs, var)
     lim = oracle.thermal_limits(g, inj)
-    from paper_2501_17529_b300.dcflow import DeviceBatch
-    s = _solver(w, lim, precision)
-    out = s.solve(DeviceBatch(topo, inj, var), want_flows=True).to_host()
-    torch.cuda.synchronize()
-    s.close()
-    ref = oracle.evaluate(g, topo, inj, mon, cont, lim, var=var, want_flows=True, want_cmax=True)
-    tol = TOL[precision]
-    np.testing.assert_array_equal(out["status"], ref["status"])
+    out, ref, inj_pick, cols = _check_candidates(w, lim, precision)
+    _compare_picked(out, ref, w, lim, precision, inj_pick, cols)
+
+
+def _compare_picked(out, ref, w, lim, precision, inj_pick, cols):
+    """compare() against the oracle rows of the picked candidates (the worst
+    monitored branch near-tie check needs the picked injections per timestep)."""
+    class _W:
+        pass
+    w2 = _W()
+    w2.grid, w2.mon, w2.cont = w.grid, w.mon, w.cont
     ok = ref["status"] == 0
-    assert ok.sum() > 5
-    # the chosen candidate: exact where the oracle's runner-up is clear, else within tolerance
-    U = var.n_var
-    per_u = oracle.evaluate(g, topo, np.repeat(inj, U, axis=0) + _cand_matrix(g, var, inj.shape[0]), mon, cont, lim)
     for i in np.nonzero(ok)[0]:
-        for t in range(inj.shape[0]):
-            vals = per_u["n1_max"][i, t * U:(t + 1) * U]
-            gu, ru = int(out["best_var"][i, t]), int(ref["best_var"][i, t])
-            srt = np.sort(vals)
-            if srt.size > 1 and srt[1] - srt[0] > 2 * tol * max(1.0, srt[0]):
-                assert gu == ru, (i, t, gu, ru)
-            else:
-                assert vals[gu] <= srt[0] + 2 * tol * max(1.0, srt[0])
-    # reported outputs of the chosen candidate (compare where the picks agree)
-    same = (out["best_var"] == ref["best_var"]).all(axis=1) & ok
-    sub = {k: v[same] for k, v in out.items()}
-    refs = {k: v[same] for k, v in ref.items()}
-    compare(sub, refs, w, topo.subset(np.nonzero(same)[0]), lim, tol)
-    assert np.all(out["best_var"][~ok] == -1)
+        w2.inj = inj_pick[cols[i]]
+        sub = {k: v[[i]] for k, v in out.items()}
+        r = {k: v[[i]] for k, v in ref.items()}
+        compare(sub, r, w2, w.topo.subset([i]), lim, TOL[precision])
 
 
 def _cand_matrix(g, var, T):
@@ -234,3 +264,22 @@ def _cand_matrix(g, var, T):
         for k in range(var.var_ptr[u], var.var_ptr[u + 1]):
             D[u, var.var_bus[k]] += var.var_delta[k]
     return np.tile(D, (T, 1))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_grid2000_candidates_sample(precision):
+    """Full 2000-bus / 3000-branch grid, 1000 random contingencies, uneven k
+    (geometric splits and outages), 8 injection candidates, 2 timesteps."""
+    w = synth.workload(3, n_topo=4, T=2, n_var=8)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    out, ref, inj_pick, cols = _check_candidates(w, lim, precision)
+    _compare_picked(out, ref, w, lim, precision, inj_pick, cols)
+
+
+@pytest.mark.parametrize("precision", ["fp32"])
+def test_grid10000_sample(precision):
+    """Full 10,000-bus / 15,000-branch grid, 5000 monitored x 2000 contingencies,
+    1-6 splits, 16 timesteps: three topologies."""
+    w = synth.workload(4, n_topo=3)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    compare(_gpu(w, lim, precision), _ref(w, lim), w, w.topo, lim, TOL[precision])
