@@ -85,6 +85,7 @@ struct dcflow_ctx {
   dcf::DevBuf cpos_of_mon; // int[M]: position in cont of the same branch or -1
   dcf::DevBuf mpos_of_cont;// int[C]: position in mon of the same branch or -1
   dcf::DevBuf inv_lim;     // double[M]
+  dcf::DevBuf bN;          // double[NN]: susceptance of the needed branches
   dcf::DevBuf PhiN;        // double[NN*NN] base branch-to-branch factors
   dcf::DevBuf PtdfN;       // double[NN*V] base PTDF rows of the needed branches
   dcf::DevBuf PhiMC;       // Real[M*ldc] Phi[mon, cont] / limit[mon], row stride ldc

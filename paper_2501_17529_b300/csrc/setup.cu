@@ -374,6 +374,11 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
   if ((rc = upload(ctx->cpos_of_mon, cpos.data(), sizeof(int) * M))) return rc;
   if ((rc = upload(ctx->mpos_of_cont, mpos.data(), sizeof(int) * mpos.size()))) return rc;
   if ((rc = upload(ctx->inv_lim, inv_lim.data(), sizeof(double) * M))) return rc;
+  {
+    std::vector<double> bN(NN);
+    for (int i = 0; i < NN; ++i) bN[i] = ctx->hb[ctx->h_N[i]];
+    if ((rc = upload(ctx->bN, bN.data(), sizeof(double) * NN))) return rc;
+  }
   DevBuf d_N;
   if ((rc = upload(d_N, ctx->h_N.data(), sizeof(int) * NN))) return rc;
   cudaStream_t st = 0;

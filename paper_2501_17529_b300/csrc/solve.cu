@@ -57,7 +57,7 @@ struct Args {
   int M, C, NN, T, U;
   int Mpad, ldc;  // padded monitored count (row stride of the per-row arrays), Phi[mon, cont] row stride
   const int *monN, *contN, *cpos, *mpos;
-  const double *inv_lim, *PhiN;
+  const double *inv_lim, *PhiN, *bN;  // bN: susceptance of every needed branch
   const void* PhiMC;
   const double* p0;  // [NN][T]
   double tol;
@@ -213,6 +213,7 @@ __global__ void k_p0_pool(int NN, int V, int T, int R, int ldp, const int* __res
 struct EntSmem {
   int en[kEntMax];
   double ew[kEntMax];
+  double ewb[kEntMax];  // ew / b of the entry's branch
   int8_t es[kEntMax];
   int mp[kRMax + 1];
 };
@@ -224,9 +225,39 @@ __device__ void load_entries(EntSmem& S, const Args& a, int q, int r) {
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     S.en[e] = a.ent_n[(size_t)q * kEntMax + e];
     S.ew[e] = a.ent_w[(size_t)q * kEntMax + e];
+    S.ewb[e] = S.ew[e] / a.bN[S.en[e]];
     S.es[e] = a.ent_s[(size_t)q * kEntMax + e];
   }
   __syncthreads();
+}
+
+// Z[row, j] = W[row, j] - sum_{q in mod j} w_q Phi[row, m_q], reading row m_q
+// of Phi instead of column m_q: by reciprocity Phi[l, m] b_m = Phi[m, l] b_l,
+// so threads with consecutive rows read consecutive addresses (FP64)
+__device__ __forceinline__ double z_entry_col(const EntSmem& S, const double* PhiN, int NN, const double* bN,
+                                              int row, int j) {
+  double z = 0.0, wdiag = 0.0;
+  for (int e = S.mp[j]; e < S.mp[j + 1]; ++e) {
+    const int m = S.en[e];
+    const double w = S.ew[e];
+    z = fma(S.ewb[e], PhiN[(size_t)m * NN + row], z);
+    if (m == row) wdiag += w;
+  }
+  return fma(-bN[row], z, wdiag);
+}
+
+// The same in the working precision (monitored rows of the FP32 form; the
+// denominators keep the FP64 version)
+template <class Real>
+__device__ __forceinline__ Real z_entry_col_r(const EntSmem& S, const double* PhiN, int NN, const double* bN,
+                                              int row, int j) {
+  Real z = 0, wdiag = 0;
+  for (int e = S.mp[j]; e < S.mp[j + 1]; ++e) {
+    const int m = S.en[e];
+    z = fma((Real)S.ewb[e], (Real)PhiN[(size_t)m * NN + row], z);
+    if (m == row) wdiag += (Real)S.ew[e];
+  }
+  return fma(-(Real)bN[row], z, wdiag);
 }
 
 // Z[row, j] = W[row, j] - sum_{q in mod j} w_q Phi[row, m_q]  (FP64)
@@ -405,10 +436,9 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     const int nl = a.monN[l];
     bool outd = false;
     for (int k = 0; k < nout; ++k) outd |= (outN[k] == nl);
-    const double* prow = a.PhiN + (size_t)nl * NN;
     Real z[RMAX];
 #pragma unroll
-    for (int j = 0; j < RMAX; ++j) z[j] = (j < r) ? (Real)z_entry(S, prow, nl, j) : (Real)0;
+    for (int j = 0; j < RMAX; ++j) z[j] = (j < r) ? z_entry_col_r<Real>(S, a.PhiN, NN, a.bN, nl, j) : (Real)0;
     const Real il = (Real)a.inv_lim[l];
 #pragma unroll
     for (int j = 0; j < RMAX; ++j) Zs[(size_t)j * Mp + l] = outd ? (Real)0 : z[j] * il;
@@ -438,7 +468,7 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     const double* prow = a.PhiN + (size_t)nc * NN;
     double z[RMAX];
 #pragma unroll
-    for (int j = 0; j < RMAX; ++j) z[j] = (j < r) ? z_entry(S, prow, nc, j) : 0.0;
+    for (int j = 0; j < RMAX; ++j) z[j] = (j < r) ? z_entry_col(S, a.PhiN, NN, a.bN, nc, j) : 0.0;
     double phicc = prow[nc];
 #pragma unroll
     for (int j = 0; j < RMAX; ++j) phicc = fma(-z[j], Vt64[(size_t)j * C + c], phicc);
@@ -448,12 +478,13 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     a.valid[(size_t)q * C + c] = ok;
     const int mp = a.mpos[c];
     if (mp >= 0) meta[mp] = (Real)(-den * a.inv_lim[mp]);
-    const double invd = ok ? 1.0 / den : 0.0;
+    // the denominator is FP64; its reciprocal only needs the working precision
+    const Real invd = ok ? (Real)1 / (Real)den : (Real)0;
     for (int t = 0; t < T; ++t) {
       Real pf = (Real)a.p0[(size_t)nc * T + t];
 #pragma unroll
       for (int j = 0; j < RMAX; ++j) pf = fma(-(Real)z[j], alph[j * T + t], pf);
-      sv[(size_t)t * C + c] = (Real)((double)pf * invd);
+      sv[(size_t)t * C + c] = pf * invd;
     }
   }
   if (my_isl) atomicAdd(&nisl, my_isl);
@@ -1145,6 +1176,7 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   base.mpos = ctx->mpos_of_cont.as<int>();
   base.inv_lim = ctx->inv_lim.as<double>();
   base.PhiN = ctx->PhiN.as<double>();
+  base.bN = ctx->bN.as<double>();
   base.PhiMC = ctx->PhiMC.p;
   base.p0 = ctx->p0.as<double>();
   base.tol = ctx->opt.island_tol;
