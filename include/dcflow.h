@@ -188,6 +188,10 @@ typedef struct {
  *  island_flag    uint8[n_topo]  0 ok, 1 the topology islands (outputs zero / -1),
  *                 2 invalid topology input
  *  n_island_cont  int32[n_topo]  contingencies skipped because they island
+ *  n1_cont_max    float[n_topo * n_time * n_cont] max over monitored l of |p_n1[c][l]| /
+ *                 limit for every contingency c (-1 where c is skipped or the topology
+ *                 islands), or NULL: the per-contingency summary that labels the
+ *                 learned screener
  * Outaged monitored branches load 0; outaged contingencies are skipped.
  */
 typedef struct {
@@ -200,6 +204,7 @@ typedef struct {
   int32_t* best_var;
   uint8_t* island_flag;
   int32_t* n_island_cont;
+  float* n1_cont_max;
 } dcflow_results;
 
 /*

@@ -293,7 +293,15 @@ __global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1
 #pragma unroll
   for (int tt = 0; tt < TH; ++tt) s_s[(th * TH + tt) * kCB + cl] = mx[tt];
   uint8_t* okc = sm + L::kOffOk;
-  if (th == 0) okc[cl] = cin && a.valid[(size_t)q * C + c];
+  const bool okv = cin && a.valid[(size_t)q * C + c];
+  if (th == 0) okc[cl] = okv;
+  if (a.out.n1_cont_max && cin) {  // per-contingency maxima (screener labels)
+#pragma unroll
+    for (int tt = 0; tt < TH; ++tt) {
+      const int t = t0 + th * TH + tt;
+      if (t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t) * C + c] = okv ? mx[tt] : -1.f;
+    }
+  }
   __syncthreads();
   for (int t = tid; t < TT; t += kCB * NTH) {
     if (t0 + t >= T) continue;

@@ -603,6 +603,11 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
   }
   // reduce the 64 contingencies of this block: max (ties: lowest c) and overload sum
   const bool ok = cin && a.valid[(size_t)q * C + c];
+  if (a.out.n1_cont_max && cin) {
+#pragma unroll
+    for (int t = 0; t < TT; ++t)
+      if (t0 + t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t0 + t) * C + c] = ok ? (float)mx[t] : -1.f;
+  }
   __shared__ double rv[2], ro[2];
   __shared__ int ra[2];
   const int lane = tid & 31, w = tid >> 5;
@@ -673,6 +678,8 @@ __global__ __launch_bounds__(128) void k_final(Args a) {
     }
     if (o.n0_flow)
       for (size_t k = tid; k < (size_t)T * M; k += blockDim.x) o.n0_flow[(size_t)tau * T * M + k] = 0.0;
+    if (o.n1_cont_max)
+      for (size_t k = tid; k < (size_t)T * C; k += blockDim.x) o.n1_cont_max[(size_t)tau * T * C + k] = -1.f;
     return;
   }
   const Real* PhiMC = static_cast<const Real*>(a.PhiMC);
@@ -1312,6 +1319,7 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
       DCF_CHECK_LAUNCH();
       Args av = a;
       av.T = TV;
+      av.out.n1_cont_max = nullptr;
       av.ptil = B.ptv.p;
       av.s = B.svv.p;
       av.pmax = B.pmaxv.p;

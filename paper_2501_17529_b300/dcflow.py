@@ -43,7 +43,8 @@ class Batch(ctypes.Structure):
 class Results(ctypes.Structure):
     _fields_ = [("n0_flow", c_void_p), ("n0_max_loading", c_void_p), ("n1_max_loading", c_void_p),
                 ("overload_sum", c_void_p), ("worst_cont", c_void_p), ("worst_mon", c_void_p),
-                ("best_var", c_void_p), ("island_flag", c_void_p), ("n_island_cont", c_void_p)]
+                ("best_var", c_void_p), ("island_flag", c_void_p), ("n_island_cont", c_void_p),
+                ("n1_cont_max", c_void_p)]
 
 
 EXPORTED = ["dcflow_default_options", "dcflow_setup", "dcflow_base_ptdf", "dcflow_base_ptdf_noalloc",
@@ -244,7 +245,8 @@ class DeviceBatch:
 class DeviceResults:
     """Caller-owned device outputs of one batch."""
 
-    def __init__(self, n_topo, n_time, n_mon, want_flows=False, want_var=False, device="cuda"):
+    def __init__(self, n_topo, n_time, n_mon, want_flows=False, want_var=False, device="cuda", n_cont=0,
+                 want_cont_max=False):
         import torch
         nt = max(1, n_topo * n_time)
         self.n0_flow = torch.empty(max(1, n_topo * n_time * n_mon), dtype=torch.float64, device=device) if want_flows else None
@@ -256,12 +258,16 @@ class DeviceResults:
         self.best_var = torch.empty(nt, dtype=torch.int32, device=device) if want_var else None
         self.island_flag = torch.empty(max(1, n_topo), dtype=torch.uint8, device=device)
         self.n_island_cont = torch.empty(max(1, n_topo), dtype=torch.int32, device=device)
+        self.n1_cont_max = (torch.empty(max(1, n_topo * n_time * n_cont), dtype=torch.float32, device=device)
+                            if want_cont_max else None)
         self.shape = (n_topo, n_time, n_mon)
+        self.n_cont = n_cont
 
     def cstruct(self) -> Results:
         return Results(_ptr(self.n0_flow), _ptr(self.n0_max_loading), _ptr(self.n1_max_loading),
                        _ptr(self.overload_sum), _ptr(self.worst_cont), _ptr(self.worst_mon),
-                       _ptr(self.best_var), _ptr(self.island_flag), _ptr(self.n_island_cont))
+                       _ptr(self.best_var), _ptr(self.island_flag), _ptr(self.n_island_cont),
+                       _ptr(self.n1_cont_max))
 
     def to_host(self) -> dict:
         N, T, M = self.shape
@@ -278,6 +284,8 @@ class DeviceResults:
             out["best_var"] = self.best_var[:N * T].cpu().numpy().reshape(N, T).astype(np.int64)
         if self.n0_flow is not None:
             out["n0_flow"] = self.n0_flow[:N * T * M].cpu().numpy().reshape(N, T, M)
+        if self.n1_cont_max is not None:
+            out["cont_max"] = self.n1_cont_max[:N * T * self.n_cont].cpu().numpy().reshape(N, T, self.n_cont)
         return out
 
 
@@ -289,10 +297,12 @@ class Solver:
         self.ctx = dcflow_setup(grid.n_bus, grid.f, grid.t, grid.b, grid.slack, precision=precision,
                                 device=device, chunk_topo=chunk_topo, island_tol=island_tol)
         self.n_mon = 0
+        self.n_cont = 0
 
     def set_study(self, mon, cont, limit, split_bus=None, outage_cand=None):
         dcflow_set_study(self.ctx, mon, cont, limit, split_bus, outage_cand)
         self.n_mon = int(np.asarray(mon).size)
+        self.n_cont = int(np.asarray(cont).size)
 
     def base_ptdf(self, rows, stream=None):
         import torch
@@ -301,8 +311,10 @@ class Solver:
         dcflow_base_ptdf(self.ctx, rows, out, stream)
         return out
 
-    def solve(self, dbatch: DeviceBatch, want_flows=False, results: DeviceResults | None = None, stream=None):
-        res = results or DeviceResults(dbatch.n_topo, dbatch.n_time, self.n_mon, want_flows, dbatch.n_var > 0)
+    def solve(self, dbatch: DeviceBatch, want_flows=False, results: DeviceResults | None = None, stream=None,
+              want_cont_max=False):
+        res = results or DeviceResults(dbatch.n_topo, dbatch.n_time, self.n_mon, want_flows, dbatch.n_var > 0,
+                                       n_cont=self.n_cont, want_cont_max=want_cont_max)
         dcflow_solve_batch(self.ctx, dbatch.cstruct(), res.cstruct(), stream)
         return res
 

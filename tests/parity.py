@@ -45,6 +45,14 @@ def compare(gpu, ref, w, topo, lim, tol, report=None):
     rep["max_err_ovl"] = float(d.max())
     assert d.max() <= tol, f"overload-sum error {d.max():.3e}"
     cmax = ref["cmax"]
+    if "cont_max" in gpu:  # per-contingency maxima (screener labels): -1 exactly where skipped
+        g = gpu["cont_max"][ok].astype(np.float64)
+        r = cmax[ok]
+        np.testing.assert_array_equal(g < 0, r < 0, err_msg="skipped contingencies")
+        v = r >= 0
+        d = np.abs(g[v] - r[v]) / np.maximum(r[v], 1.0)
+        rep["max_err_cont_max"] = float(d.max()) if d.size else 0.0
+        assert d.size == 0 or d.max() <= max(tol, 2e-7), f"per-contingency max error {d.max():.3e}"
     for i in np.nonzero(ok)[0]:
         for t in range(ref["n1_max"].shape[1]):
             go, ro = int(gpu["worst_cont"][i, t]), int(ref["worst_cont"][i, t])

@@ -31,7 +31,7 @@ def _gpu(w, lim, precision, topo=None, chunk=0, want_flows=True):
     from paper_2501_17529_b300.dcflow import DeviceBatch
     s = _solver(w, lim, precision, chunk)
     topo = w.topo if topo is None else topo
-    res = s.solve(DeviceBatch(topo, w.inj), want_flows=want_flows)
+    res = s.solve(DeviceBatch(topo, w.inj), want_flows=want_flows, want_cont_max=want_flows)
     torch.cuda.synchronize()
     out = res.to_host()
     s.close()
