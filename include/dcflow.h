@@ -230,6 +230,20 @@ int64_t dcflow_last_launch_count(const dcflow_ctx* ctx);
 int dcflow_profile(dcflow_ctx* ctx, int32_t enable);
 int dcflow_profile_read(dcflow_ctx* ctx, double* n1_ms, int64_t* n1_launches);
 
+/*
+ * Tensor-core BF16 GEMM used by the learned contingency screener (the paper
+ * has no learned part; this is the dense contraction of its MLP):
+ * D[M x N] = A[M x K] * B[N x K]^T (+ bias[N]) (ReLU if relu != 0).
+ * A, B: device bf16 (uint16 bit patterns), row-major, K-major, row pitch lda /
+ * ldb elements (multiples of 8), 16-byte aligned; D: device row-major FP32
+ * (out_bf16 = 0) or bf16, pitch ldd; bias: device float[N] or NULL.
+ * M and N multiples of 128, K a multiple of 64.  Accumulation is FP32 in
+ * tensor memory (tcgen05).  Synchronous: returns after the product is
+ * complete; DCFLOW_ERR_TIMEOUT if a bounded device wait expired.
+ */
+int dcflow_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda, const void* B, int32_t ldb,
+                     const float* bias, int32_t relu, void* D, int32_t ldd, int32_t out_bf16, void* stream);
+
 void dcflow_destroy(dcflow_ctx* ctx);
 const char* dcflow_strerror(int code);
 const char* dcflow_last_error(void);

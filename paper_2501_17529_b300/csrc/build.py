@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 PKG = os.path.dirname(HERE)
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libdcflow.so")
-SOURCES = ["api.cu", "dense64.cu", "setup.cu", "solve.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "dense64.cu", "setup.cu", "solve.cu", "noalloc.cu", "mlp.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

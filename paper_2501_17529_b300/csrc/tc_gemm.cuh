@@ -1,0 +1,217 @@
+// BF16 GEMM on the 5th-generation tensor cores (tcgen05) with FP32 accumulation
+// in tensor memory: D[M x N] = A[M x K] * B[N x K]^T (+ bias[N], optional ReLU),
+// both operands K-major bf16, D row-major in FP32 or BF16.
+//
+// One CTA per 128 x 128 output tile, 128 threads.  Thread 0 drives a 4-stage
+// ring: TMA loads 128 x 64 bf16 boxes of A and B with 128-byte swizzle into
+// shared memory (completion on a "full" mbarrier), issues four
+// tcgen05.mma.kind::f16 (K = 16 each) per stage into a 128 x 128 FP32
+// accumulator in tensor memory, and tcgen05.commit frees the stage on an
+// "empty" mbarrier.  After the last stage a commit signals the epilogue: each
+// warp reads its 32 accumulator lanes (rows) with tcgen05.ld.32x32b.
+// Every mbarrier wait is bounded; on expiry the CTA records an error, waits
+// (bounded) for its outstanding copies and MMAs, frees its tensor memory and
+// returns.  Shapes: M, N multiples of 128, K a multiple of 64.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace dcf {
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int kTileBytes = BM * BK * 2;          // 16 KB per operand tile
+constexpr int kStageBytes = 2 * kTileBytes;      // A + B
+constexpr int kSmemBytes = 1024 /*align*/ + STAGES * kStageBytes + 256 /*barriers, tmem slot*/;
+constexpr long long kWait = 4000000000LL;        // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint32_t b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint32_t b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWait) return false;
+  }
+}
+__device__ __forceinline__ void tma2d(uint32_t dst, const CUtensorMap* m, int x, int y, uint32_t b) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(m), "r"(x), "r"(y), "r"(b)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with
+// 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);         // start address
+  d |= (uint64_t)(16 >> 4) << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                         // descriptor version of this architecture
+  d |= (uint64_t)2 << 61;                         // layout: 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+struct GemmArgs {
+  int M, N, K;
+  const float* bias;  // [N] or null
+  int relu;
+  void* D;            // row-major
+  int ldd;
+  int out_bf16;
+  int* err;
+};
+
+__global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUtensorMap mA,
+                                                   const __grid_constant__ CUtensorMap mB, GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const uint32_t raw = su32(smem);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned tile area
+  const uint32_t bars = base + STAGES * kStageBytes;  // full[S], empty[S], done
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
+  const uint32_t done = bars + 8u * (2 * STAGES);
+  const uint32_t tslot = done + 8u;  // tensor-memory address written by tcgen05.alloc
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int KT = g.K / BK;
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      bar_init(full(s), 1);
+      bar_init(empty(s), 1);
+    }
+    bar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(128) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  uint32_t tmem;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(tslot) : "memory");
+  __shared__ int failed;
+  if (tid == 0) failed = 0;
+  __syncthreads();
+  if (tid == 0) {
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    auto load = [&](int kt) {
+      const int s = kt % STAGES;
+      const uint32_t a = base + s * kStageBytes, b = a + kTileBytes;
+      bar_expect(full(s), kStageBytes);
+      tma2d(a, &mA, kt * BK, m0, full(s));
+      tma2d(b, &mB, kt * BK, n0, full(s));
+    };
+    int issued = 0, landed = 0;  // loads issued / loads whose arrival was observed
+    for (int kt = 0; kt < KT && kt < STAGES; ++kt, ++issued) load(kt);
+    bool ok = true;
+    for (int kt = 0; kt < KT && ok; ++kt) {
+      const int s = kt % STAGES;
+      if (!bar_wait(full(s), (uint32_t)((kt / STAGES) & 1))) {
+        ok = false;
+        break;
+      }
+      ++landed;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a = base + s * kStageBytes, b = a + kTileBytes;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)  // 16 bf16 = 32 bytes per K step inside the swizzle atom
+        mma_bf16(tmem, sw128_desc(a + 32 * kk), sw128_desc(b + 32 * kk), idesc, (kt | kk) != 0);
+      mma_commit(empty(s));
+      if (kt + STAGES < KT) {
+        if (!bar_wait(empty(s), (uint32_t)((kt / STAGES) & 1))) {
+          ok = false;
+          break;
+        }
+        load(kt + STAGES);
+        ++issued;
+      }
+    }
+    mma_commit(done);
+    if (!ok) {
+      failed = 1;
+      for (int k = landed; k < issued; ++k) bar_wait(full(k % STAGES), (uint32_t)((k / STAGES) & 1));  // bounded drain
+    }
+  }
+  __syncthreads();
+  const bool fin = bar_wait(done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (failed || !fin) {
+    if (tid == 0) atomicExch(g.err, 1);
+  } else {
+    // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        float x = __uint_as_float(r[j]);
+        if (g.bias) x += g.bias[n0 + c0 + j];
+        if (g.relu) x = fmaxf(x, 0.f);
+        v[j] = x;
+      }
+      if (row < g.M) {
+        if (g.out_bf16) {
+          __nv_bfloat16* d = static_cast<__nv_bfloat16*>(g.D) + (size_t)row * g.ldd + n0 + c0;
+#pragma unroll
+          for (int j = 0; j < 16; j += 2)
+            *reinterpret_cast<__nv_bfloat162*>(d + j) = __floats2bfloat162_rn(v[j], v[j + 1]);
+        } else {
+          float* d = static_cast<float*>(g.D) + (size_t)row * g.ldd + n0 + c0;
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(d + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+}
+
+}  // namespace tc
+}  // namespace dcf

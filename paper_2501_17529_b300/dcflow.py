@@ -50,7 +50,7 @@ class Results(ctypes.Structure):
 EXPORTED = ["dcflow_default_options", "dcflow_setup", "dcflow_base_ptdf", "dcflow_base_ptdf_noalloc",
             "dcflow_set_study",
             "dcflow_solve_batch", "dcflow_last_launch_count", "dcflow_profile", "dcflow_profile_read",
-            "dcflow_destroy", "dcflow_strerror", "dcflow_last_error"]
+            "dcflow_gemm_bf16", "dcflow_destroy", "dcflow_strerror", "dcflow_last_error"]
 
 _lib = None
 
@@ -82,6 +82,9 @@ def load_library(path: str = LIB_PATH):
     lib.dcflow_profile.restype = c_int32
     lib.dcflow_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int64)]
     lib.dcflow_profile_read.restype = c_int32
+    lib.dcflow_gemm_bf16.argtypes = [c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
+                                     c_int32, c_void_p, c_int32, c_int32, c_void_p]
+    lib.dcflow_gemm_bf16.restype = c_int32
     lib.dcflow_destroy.argtypes = [c_void_p]
     lib.dcflow_destroy.restype = None
     lib.dcflow_strerror.argtypes = [c_int32]
@@ -200,6 +203,19 @@ def dcflow_profile_read(ctx):
     ms, n = c_double(), c_int64()
     _check(load_library().dcflow_profile_read(ctx, byref(ms), byref(n)), "dcflow_profile_read")
     return {"n1_ms": ms.value, "n1_launches": n.value}
+
+
+def dcflow_gemm_bf16(A, B, bias=None, relu=False, out=None, out_bf16=False, stream=None):
+    """D = A @ B^T (+ bias) (ReLU) on the tensor cores; A [M, K], B [N, K] bf16 torch tensors."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if out is None:
+        out = torch.empty((M, N), dtype=torch.bfloat16 if out_bf16 else torch.float32, device=A.device)
+    _check(load_library().dcflow_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(bias),
+                                           1 if relu else 0, _ptr(out), out.stride(0), 1 if out_bf16 else 0,
+                                           _stream_ptr(stream)), "dcflow_gemm_bf16")
+    return out
 
 
 def dcflow_destroy(ctx):
