@@ -40,8 +40,13 @@ WORKLOADS = {
     "grid10000": (4, 50000, "grid10000_splits1-6_T16_mon5000_cont2000"),
 }
 # dram bytes per launch of the dominant kernel from the ncu capture summarised in
-# profiles/k_n1_grid500.md, keyed by the sha1 of the kernel source it was taken on
-N1_TRAFFIC = {}
+# profiles/k_n1_tma_grid500.md, keyed by the sha1 of the kernel's source and of
+# its argument block at the time of the capture
+N1_TRAFFIC = {
+    ("25a28b617be9", "fp32"): {"bytes": 1.123e9, "per": "bench step of the 500-bus study (2 launches)",
+                               "how": "1,000-topology capture (626 + 374 topologies) scaled by topologies "
+                                      "per rank class to 6,233 + 3,767"},
+}
 
 
 def _peaks():
@@ -54,7 +59,7 @@ def _peaks():
 
 def _src_hash():
     h = hashlib.sha1()
-    for f in ("solve.cu", "internal.cuh"):
+    for f in ("n1_tma.cuh", "args.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2501_17529_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -305,7 +310,11 @@ def run_ours(args):
         ach = entries / (k["n1_ms"] / 1e3) / 1e12
         key = (_src_hash(), "fp32")
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T N-1 entries/s", "frac": ach / peak,
-                "traffic": N1_TRAFFIC.get(key), "kernel": "k_n1_tma (FP32 fused N-1)",
+                "traffic": (N1_TRAFFIC[key]["bytes"] if key in N1_TRAFFIC and args.workload == "grid500"
+                            and n_topo == 10000 else None),
+                "traffic_note": (N1_TRAFFIC[key] if key in N1_TRAFFIC and args.workload == "grid500"
+                                 and n_topo == 10000 else "no capture for this kernel source and workload"),
+                "kernel": "k_n1_tma (FP32 fused N-1)",
                 "peak_note": f"1 FP32 issue slot per entry at the {peak_kind} max SM clock "
                              f"({peaks.get('sm_max_mhz', 2032.0):.0f} MHz), 148 SMs x 128 lanes",
                 "n1_ms_per_step": k["n1_ms"] / head["steps"],

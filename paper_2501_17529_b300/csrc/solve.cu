@@ -28,59 +28,10 @@
 
 #include <cudaTypedefs.h>
 
+#include "args.cuh"
 #include "internal.cuh"
 
 namespace dcf {
-
-enum : int { ST_OK = 0, ST_ISLAND = 1, ST_INVALID = 2 };
-
-struct QInfo {
-  int tau, r, ks, status;
-};
-
-struct GridDev {
-  const int *f, *t;
-  const double* b;
-  const int *inc_ptr, *inc_list, *nidx;
-  const uint8_t* split_ok;
-  int V, E;
-};
-
-struct BatchDev {
-  const int *split_ptr, *split_sub;
-  const uint64_t* split_mask;
-  const int *out_ptr, *out_branch;
-};
-
-struct Args {
-  // study
-  int M, C, NN, T, U;
-  int Mpad, ldc;  // padded monitored count (row stride of the per-row arrays), Phi[mon, cont] row stride
-  const int *monN, *contN, *cpos, *mpos;
-  const double *inv_lim, *PhiN, *bN;  // bN: susceptance of every needed branch
-  const void* PhiMC;
-  const double* p0;  // [NN][T]
-  double tol;
-  // chunk
-  int nq;
-  QInfo* qi;
-  int* ent_n;
-  int8_t* ent_s;
-  double* ent_w;
-  int16_t* mod_ptr;
-  double *Kinv, *alpha, *Vt64;
-  void *VtR, *Zs, *ptil, *rowmul, *diagv, *s;
-  uint8_t* valid;
-  int* nisl;
-  void* pmax;
-  int* parg;
-  double* povl;
-  int ncb;
-  const int* best_u;  // chosen injection candidate per (slot, timestep), or null
-  int* err;  // set to 1 by a kernel whose bounded wait expired
-  // outputs
-  dcflow_results out;
-};
 
 // ---------------------------------------------------------------------------
 // decode: topology vectors -> modification list

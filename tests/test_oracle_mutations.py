@@ -108,3 +108,87 @@ def test_planted_mistake_is_caught(monkeypatch, golden_dir, name, mut, checks):
         else:
             caught |= _fails(fn, arg)
     assert caught, f"planted mistake in {name} not detected"
+
+
+# ---------------------------------------------------------------------------
+# screener reference
+# ---------------------------------------------------------------------------
+from oracle import screener_ref as sref  # noqa: E402
+import tests.test_oracle_screener as spins  # noqa: E402
+
+
+def _bwd_no_relu_mask(params, cache, z, Y, rounding=None):
+    Y = np.asarray(Y, np.float64)
+    B, C = z.shape
+    dz = (sref.sigmoid(z) - Y) / (B * C)
+    g = {"W3": dz.T @ cache["h2"], "b3": dz.sum(axis=0)}
+    dh2 = dz @ cache["W3"]  # planted: relu' dropped
+    g["W2"], g["b2"] = dh2.T @ cache["h1"], dh2.sum(axis=0)
+    dh1 = (dh2 @ cache["W2"]) * (cache["h1"] > 0)
+    g["W1"], g["b1"] = dh1.T @ cache["x"], dh1.sum(axis=0)
+    return g
+
+
+def _bwd_w2_transposed(params, cache, z, Y, rounding=None):
+    Y = np.asarray(Y, np.float64)
+    B, C = z.shape
+    dz = (sref.sigmoid(z) - Y) / (B * C)
+    g = {"W3": dz.T @ cache["h2"], "b3": dz.sum(axis=0)}
+    dh2 = (dz @ cache["W3"]) * (cache["h2"] > 0)
+    g["W2"], g["b2"] = dh2.T @ cache["h1"], dh2.sum(axis=0)
+    dh1 = (dh2 @ cache["W2"].T) * (cache["h1"] > 0)  # planted: W2^T instead of W2
+    g["W1"], g["b1"] = dh1.T @ cache["x"], dh1.sum(axis=0)
+    return g
+
+
+def _bwd_no_mean(params, cache, z, Y, rounding=None):
+    Y = np.asarray(Y, np.float64)
+    dz = sref.sigmoid(z) - Y  # planted: the 1 / (B C) of the mean dropped
+    g = {"W3": dz.T @ cache["h2"], "b3": dz.sum(axis=0)}
+    dh2 = (dz @ cache["W3"]) * (cache["h2"] > 0)
+    g["W2"], g["b2"] = dh2.T @ cache["h1"], dh2.sum(axis=0)
+    dh1 = (dh2 @ cache["W2"]) * (cache["h1"] > 0)
+    g["W1"], g["b1"] = dh1.T @ cache["x"], dh1.sum(axis=0)
+    return g
+
+
+def _adam_no_bias_correction(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    for k in sref.PARAM_NAMES:
+        m[k] = beta1 * m[k] + (1 - beta1) * grads[k]
+        v[k] = beta2 * v[k] + (1 - beta2) * grads[k] ** 2
+        params[k] = params[k] - lr * m[k] / (np.sqrt(v[k]) + eps)  # planted
+    return params
+
+
+def _labels_no_threshold(cmax, k):
+    cm = np.asarray(cmax, np.float64)
+    flat = cm.reshape(-1, cm.shape[-1])
+    Y = np.zeros(flat.shape, np.uint8)
+    for r in range(flat.shape[0]):
+        for c in sorted(range(flat.shape[1]), key=lambda c: (-flat[r, c], c))[:k]:
+            Y[r, c] = 1  # planted: max rho > 1 not required
+    return Y.reshape(cm.shape)
+
+
+def _bf16_truncate(x):
+    a = np.asarray(x, np.float64).astype(np.float32)
+    u = a.view(np.uint32) & np.uint32(0xFFFF0000)  # planted: truncation, not round-to-nearest-even
+    return u.view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("name,attr,fake,pin", [
+    ("relu mask dropped", "backward", _bwd_no_relu_mask, "fd"),
+    ("W2 transposed in backward", "backward", _bwd_w2_transposed, "hand"),
+    ("mean dropped", "backward", _bwd_no_mean, "fd"),
+    ("adam bias correction dropped", "adam_step", _adam_no_bias_correction, "adam"),
+    ("labels without overload test", "labels", _labels_no_threshold, "labels"),
+    ("bf16 truncation", "bf16_round", _bf16_truncate, "bf16"),
+])
+def test_screener_mutation_is_caught(monkeypatch, golden_dir, name, attr, fake, pin):
+    monkeypatch.setattr(sref, attr, fake)
+    fn = {"fd": lambda: spins.test_gradients_match_central_differences(None),
+          "hand": lambda: spins.test_hand_worked_network(golden_dir),
+          "adam": spins.test_adam_first_steps_closed_form,
+          "labels": spins.test_labels_characterisation,
+          "bf16": spins.test_bf16_round_known_values_and_torch}[pin]
+    assert _fails(fn), name
