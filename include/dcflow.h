@@ -244,6 +244,98 @@ int dcflow_profile_read(dcflow_ctx* ctx, double* n1_ms, int64_t* n1_launches);
 int dcflow_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda, const void* B, int32_t ldb,
                      const float* bias, int32_t relu, void* D, int32_t ldd, int32_t out_bf16, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned contingency screener.  The paper has no learned part: this is a
+ * filter in front of the exact N-1 of Def. 3 / Eq. (5).  A 3-layer perceptron
+ * (F -> 256 -> 256 -> C, ReLU, BF16 operands on the tensor cores, FP32
+ * accumulation, FP32 master weights) scores every contingency of the bound
+ * study for one (topology, timestep); the screened solve evaluates, per
+ * topology, only the union over its timesteps of the top_k scored
+ * contingencies.
+ *
+ * Features of one (topology, timestep), F = M + sum of the degrees of the
+ * split-capable buses: the M signed N-0 loadings p_f[l] / limit_l of the
+ * monitored branches (Eq. (2) on the modified topology), then one bit per
+ * incident branch of every split-capable bus (ascending bus id, then the
+ * incident branches in ascending branch id, the bit order of split_mask),
+ * 1 if the branch is on busbar B.  Rows are BF16 (uint16 bit patterns) with a
+ * row pitch ldx >= F_pad = round_up(F, 128), ldx % 8 == 0; columns F..F_pad
+ * are zero.  A topology that islands or is invalid has an all-zero row.
+ *
+ * Labels (dcflow_screen_labels): y[c] = 1 iff the per-contingency maximum
+ * loading (n1_cont_max of the exact solve) exceeds 1 and c is among the k
+ * largest of the row (ties to the lower contingency position).
+ *
+ * Tensors (dcflow_screen_get / _set, row-major FP32, logical shapes):
+ *   0 W1 [256 x F], 1 b1 [256], 2 W2 [256 x 256], 3 b2 [256],
+ *   4 W3 [C x 256], 5 b3 [C];  kind 0 parameters, 1 gradients (of the last
+ *   backward pass), 2 Adam first moments, 3 Adam second moments.
+ *
+ * Every call returns 0 or a negative error code; the screener belongs to the
+ * context (and study) it was created on and must be destroyed before it.
+ * Calls on one screener must not overlap (they share its work buffers).
+ * ------------------------------------------------------------------------ */
+typedef struct dcflow_screen dcflow_screen;
+
+/* New screener for ctx's current study: He-normal weights from a
+ * counter-based generator seeded by `seed`, b3 at the log-odds of 64/C.
+ * max_rows (multiple of 128): the largest training batch. */
+int dcflow_screen_create(dcflow_ctx* ctx, int32_t max_rows, uint64_t seed, dcflow_screen** out);
+void dcflow_screen_destroy(dcflow_screen* s);
+/* Feature count F and its padding, hidden width, contingencies C and padding. */
+int dcflow_screen_dims(const dcflow_screen* s, int32_t* F, int32_t* F_pad, int32_t* H, int32_t* C, int32_t* C_pad);
+/* Feature rows of a batch: row tau * n_time + t of X (device, caller-owned,
+ * n_topo * n_time rows of pitch ldx); status (device uint8[n_topo], optional):
+ * 0 ok, 1 islanded, 2 invalid.  The batch must carry no injection candidates. */
+int dcflow_screen_features(dcflow_ctx* ctx, const dcflow_screen* s, const dcflow_batch* batch, void* X, int64_t ldx,
+                           uint8_t* status, void* stream);
+/* Labels from n1_cont_max rows (device float[n_rows * C]) into Y (device
+ * uint8[n_rows * ldy], ldy >= C_pad for training; padding columns zero). */
+int dcflow_screen_labels(dcflow_screen* s, const float* cont_max, int64_t n_rows, int32_t k, uint8_t* Y, int64_t ldy,
+                         void* stream);
+/* Forward and backward pass over rows[0..n) of X / Y (device int32 indices;
+ * NULL: rows 0..n-1), n <= max_rows: the gradients of the mean binary
+ * cross-entropy with logits over the n rows and C contingencies replace the
+ * stored ones, and the loss is added to *loss (device float).  Synchronous. */
+int dcflow_screen_backward(dcflow_screen* s, const void* X, int64_t ldx, const uint8_t* Y, int64_t ldy,
+                           const int32_t* rows, int32_t n, float* loss, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) with the stored gradients. */
+int dcflow_screen_adam(dcflow_screen* s, float lr, void* stream);
+/* backward + adam without the synchronisation of dcflow_screen_backward;
+ * dcflow_screen_check reports a bounded wait that expired since the last check. */
+int dcflow_screen_train_step(dcflow_screen* s, const void* X, int64_t ldx, const uint8_t* Y, int64_t ldy,
+                             const int32_t* rows, int32_t n, float lr, float* loss, void* stream);
+int dcflow_screen_check(dcflow_screen* s, void* stream);
+/* Scores (logits) of n_rows feature rows into Z (device float, pitch ldz >= C). */
+int dcflow_screen_logits(dcflow_screen* s, const void* X, int64_t ldx, int64_t n_rows, float* Z, int64_t ldz,
+                         void* stream);
+int dcflow_screen_get(const dcflow_screen* s, int32_t tensor, int32_t kind, float* host);
+int dcflow_screen_set(dcflow_screen* s, int32_t tensor, int32_t kind, const float* host);
+/* Adam step counter: read (set = 0) or write (set != 0), for checkpoints. */
+int dcflow_screen_adam_step(dcflow_screen* s, int64_t* t, int32_t set);
+
+typedef struct dcflow_screen_options {
+  int32_t top_k;         /* contingencies kept per (topology, timestep) */
+  float fallback_logit;  /* the full N-1 of a topology runs when a k-th score exceeds this (INFINITY: never) */
+} dcflow_screen_options;
+
+typedef struct dcflow_screen_report {  /* device buffers, each optional */
+  int32_t* n_eval;   /* [n_topo] contingencies evaluated exactly */
+  uint8_t* fallback; /* [n_topo] 1 if the full N-1 ran */
+  int32_t* pred;     /* [n_topo * n_time * top_k] the top_k per row, ascending; -1 padding */
+} dcflow_screen_report;
+
+/* dcflow_solve_batch with the N-1 restricted, per topology, to the union over
+ * its timesteps of the top_k scored contingencies (all of them after a
+ * fallback).  Results as dcflow_solve_batch, over the evaluated contingencies:
+ * n1_max_loading / worst_cont / worst_mon are exact whenever the worst
+ * contingency is evaluated, overload_sum counts evaluated contingencies only,
+ * n1_cont_max (optional) is written for evaluated contingencies only.  No
+ * injection candidates. */
+int dcflow_solve_batch_screened(dcflow_ctx* ctx, const dcflow_batch* batch, const dcflow_results* results,
+                                dcflow_screen* s, const dcflow_screen_options* opt, const dcflow_screen_report* report,
+                                void* stream);
+
 void dcflow_destroy(dcflow_ctx* ctx);
 const char* dcflow_strerror(int code);
 const char* dcflow_last_error(void);

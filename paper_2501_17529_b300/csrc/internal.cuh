@@ -54,9 +54,13 @@ struct ChunkBufs {
   // injection candidates: per (timestep, candidate) operands and screening maxima,
   // the chosen candidate per timestep and its operands
   DevBuf ptv, svv, pmaxv, pargv, povlv, bestu, ptb, sb;
+  // learned screener: selected-contingency bit masks, fallback flags, the
+  // selected lists and their counts, the N-1 work list and its length
+  DevBuf selmask, sfb, csel, nsel, work, nwork;
   void release_all() {
     DevBuf* b[] = {&ent_n, &ent_s, &ent_w, &mod_ptr, &q_info, &Kinv, &alpha, &Vt64, &VtR, &Zs, &ptil, &meta,
-                   &s, &valid, &nisl, &pmax, &parg, &povl, &ptv, &svv, &pmaxv, &pargv, &povlv, &bestu, &ptb, &sb};
+                   &s, &valid, &nisl, &pmax, &parg, &povl, &ptv, &svv, &pmaxv, &pargv, &povlv, &bestu, &ptb, &sb,
+                   &selmask, &sfb, &csel, &nsel, &work, &nwork};
     for (auto* x : b) x->release();
   }
 };
@@ -90,6 +94,9 @@ struct dcflow_ctx {
   dcf::DevBuf PtdfN;       // double[NN*V] base PTDF rows of the needed branches
   dcf::DevBuf PhiMC;       // Real[M*ldc] Phi[mon, cont] / limit[mon], row stride ldc
   int ldc = 0;             // round_up(C, 4): 16-byte row pitch for the tensor-memory accelerator
+  std::vector<uint8_t> h_split_ok;  // split-capable buses of the study
+  dcf::DevBuf PhiCM;       // Real[C*Mpad] the same factors transposed (screened N-1; built on first use)
+  bool phicm_ready = false;
   dcf::DevBuf Y;           // solve workspace
   // batch scratch
   dcf::DevBuf p0;          // double[NN*(T+R)]: base flows, then R pool columns

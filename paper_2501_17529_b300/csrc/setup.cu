@@ -421,6 +421,8 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
     set_error(std::string("dcflow_set_study: ") + cudaGetErrorString(e));
     return DCFLOW_ERR_CUDA;
   }
+  ctx->h_split_ok = split_ok;
+  ctx->phicm_ready = false;
   ctx->has_study = true;
   return DCFLOW_OK;
 }

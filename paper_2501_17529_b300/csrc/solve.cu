@@ -30,6 +30,7 @@
 
 #include "args.cuh"
 #include "internal.cuh"
+#include "screen.cuh"
 
 namespace dcf {
 
@@ -607,7 +608,7 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
 // the same arithmetic as the N-1 kernel, write every output of the topology
 // ---------------------------------------------------------------------------
 template <class Real, int RMAX>
-__global__ __launch_bounds__(128) void k_final(Args a) {
+__global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ nsel) {
   const int q = blockIdx.x;
   const QInfo qi = a.qi[q];
   const int tau = qi.tau, T = a.T, M = a.M, C = a.C, Mp = a.Mpad, tid = threadIdx.x;
@@ -642,7 +643,8 @@ __global__ __launch_bounds__(128) void k_final(Args a) {
   for (int t = tid >> 5; t < T; t += nw) {
     double bv = -1.0, ovl = 0.0;
     int ba = 0x7fffffff;
-    for (int b = lane; b < a.ncb; b += 32) {
+    const int nb = nsel ? (nsel[q] + 63) / 64 : a.ncb;  // blocks of selected contingencies, or all
+    for (int b = lane; b < nb; b += 32) {
       const size_t k = ((size_t)q * T + t) * a.ncb + b;
       const double v = (double)static_cast<const Real*>(a.pmax)[k];
       const int ar = a.parg[k];
@@ -803,6 +805,284 @@ __global__ void k_var_gather(Args af, int U, const Real* __restrict__ ptv, const
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// learned screener in the loop (no counterpart in the paper): features of
+// every (topology, timestep), top-k of the network's scores, the union over a
+// topology's timesteps, then Eq. (5) over that union only
+// ---------------------------------------------------------------------------
+// Feature row (layout in screen.cuh): p_f / limit of the monitored branches,
+// then the busbar bits of the topology's splits; zero for a topology that
+// islands or is invalid.  Rows q T + t of the chunk, or tau T + t.
+template <class Real>
+__global__ void k_features(Args a, GridDev g, BatchDev in, const int* __restrict__ foff, int Fp,
+                           __nv_bfloat16* __restrict__ X, int64_t ldx, int by_tau, uint8_t* __restrict__ status) {
+  const int q = blockIdx.x;
+  const QInfo qi = a.qi[q];
+  const int T = a.T, M = a.M, Mp = a.Mpad;
+  const bool ok = qi.status == ST_OK;
+  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
+  if (status && threadIdx.x == 0) status[qi.tau] = (uint8_t)qi.status;
+  const int64_t r0 = by_tau ? (int64_t)qi.tau * T : (int64_t)q * T;
+  for (int t = 0; t < T; ++t) {
+    __nv_bfloat16* x = X + (r0 + t) * ldx;
+    for (int i = threadIdx.x; i < Fp; i += blockDim.x)
+      x[i] = __float2bfloat16_rn((ok && i < M) ? (float)ptil[(size_t)t * Mp + i] : 0.f);
+  }
+  __syncthreads();
+  if (!ok) return;
+  for (int k = in.split_ptr[qi.tau]; k < in.split_ptr[qi.tau + 1]; ++k) {
+    const int sub = in.split_sub[k];
+    const uint64_t mask = in.split_mask[k];
+    const int o = foff[sub];
+    if (o < 0) continue;
+    const int deg = g.inc_ptr[sub + 1] - g.inc_ptr[sub];
+    for (int idx = threadIdx.x; idx < deg * T; idx += blockDim.x) {
+      const int j = idx % deg, t = idx / deg;
+      X[(r0 + t) * ldx + o + j] = __float2bfloat16_rn((float)((mask >> j) & 1ull));
+    }
+  }
+}
+
+// Top k of the scores of every (topology, timestep) row (one warp per row,
+// ties to the lower contingency position); the union over the timesteps of a
+// topology goes to a bit mask, the request for the full N-1 to fb[q] when the
+// k-th score still exceeds the fallback threshold.
+template <int NPL>
+__global__ void k_select(const QInfo* __restrict__ qinfo, int nq, int T, int C, const float* __restrict__ Z,
+                         int ldz, int k, uint32_t fb_key, uint32_t* __restrict__ selmask, int W,
+                         uint8_t* __restrict__ fb, int32_t* __restrict__ pred) {
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= (int64_t)nq * T) return;
+  const int q = (int)(row / T), t = (int)(row % T);
+  const QInfo qi = qinfo[q];
+  int32_t* pr = pred ? pred + ((int64_t)qi.tau * T + t) * k : nullptr;
+  if (qi.status != ST_OK) {  // nothing is evaluated: an all -1 row
+    if (pr)
+      for (int j = lane; j < k; j += 32) pr[j] = -1;
+    return;
+  }
+  uint32_t key[NPL];
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {
+    const int c = lane + 32 * i;
+    key[i] = c < C ? float_key(Z[row * ldz + c]) : 0u;
+  }
+  const int kk = k < C ? k : C;
+  bool sel[NPL];
+  uint32_t thr;
+  warp_top_k<NPL>(key, kk, sel, thr);
+  int off = 0;
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {
+    const uint32_t b = __ballot_sync(0xffffffffu, sel[i]);
+    if (lane == 0 && b) atomicOr(&selmask[(size_t)q * W + i], b);
+    if (pr && sel[i]) pr[off + __popc(b & ((1u << lane) - 1u))] = lane + 32 * i;
+    off += __popc(b);
+  }
+  if (pr)
+    for (int j = kk + lane; j < k; j += 32) pr[j] = -1;
+  if (lane == 0 && thr > fb_key) fb[q] = 1;
+}
+
+// Per topology (one warp): the selected contingencies in ascending order
+// (all of them after a fallback), their count, and one work item per
+// 64 of them for the N-1 kernel.
+__global__ void k_compact(const QInfo* __restrict__ qinfo, int nq, int C, int W, const uint32_t* __restrict__ selmask,
+                          const uint8_t* __restrict__ fb, int* __restrict__ csel, int* __restrict__ nsel,
+                          int* __restrict__ work, int* __restrict__ nwork, int32_t* __restrict__ n_eval,
+                          uint8_t* __restrict__ fb_out) {
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  const QInfo qi = qinfo[q];
+  const bool ok = qi.status == ST_OK;
+  const bool full = ok && fb[q];
+  int base = 0;
+  if (ok) {
+    for (int w0 = 0; w0 < W; w0 += 32) {
+      const int w = w0 + lane;
+      uint32_t word = 0;
+      if (w < W) {
+        word = full ? 0xffffffffu : selmask[(size_t)q * W + w];
+        const int rem = C - 32 * w;
+        if (rem < 32) word &= (1u << rem) - 1u;
+      }
+      const int cnt = __popc(word);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      int pos = base + incl - cnt;
+      while (word) {
+        const int bit = __ffs(word) - 1;
+        word &= word - 1u;
+        csel[(size_t)q * C + pos++] = 32 * w + bit;
+      }
+      base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  if (lane == 0) {
+    nsel[q] = base;
+    const int nb = (base + 63) / 64;
+    if (nb) {
+      const int w = atomicAdd(nwork, nb);
+      for (int j = 0; j < nb; ++j) work[w + j] = q * 64 + j;
+    }
+    if (n_eval) n_eval[qi.tau] = base;
+    if (fb_out) fb_out[qi.tau] = full ? 1 : 0;
+  }
+}
+
+// Phi[mon, cont] / limit transposed to [cont][Mpad] (zero padding rows) for
+// the selected-contingency N-1: a contingency's column becomes contiguous.
+template <class Real>
+__global__ void k_phi_cm(const Real* __restrict__ PhiMC, int M, int C, int ldc, int Mp, Real* __restrict__ PhiCM) {
+  __shared__ Real tile[32][33];
+  const int l0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int l = l0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (l < M && c < C) ? PhiMC[(size_t)l * ldc + c] : (Real)0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, l = l0 + threadIdx.x;
+    if (c < C && l < Mp) PhiCM[(size_t)c * Mp + l] = tile[threadIdx.x][i];
+  }
+}
+
+// Eq. (5) over the selected contingencies of each work item (topology, 64 of
+// its selected contingencies), one contingency per thread; the same arithmetic
+// and partial-result layout as the all-contingency kernel, with Phi read as
+// contiguous rows of the transposed factors.  Blocks loop over the work list.
+template <class Real, int TT, int RMAX, int LT>
+__global__ __launch_bounds__(64) void k_n1_sel(Args a, const Real* __restrict__ PhiCM, const int* __restrict__ csel,
+                                               const int* __restrict__ nsel, const int* __restrict__ work,
+                                               const int* __restrict__ nwork, int t0) {
+  const int tid = threadIdx.x, M = a.M, C = a.C, T = a.T, Mp = a.Mpad;
+  __shared__ __align__(16) Real zs[LT][RMAX];
+  __shared__ __align__(16) Real pt[LT][TT];
+  __shared__ Real dg[LT], rm[LT];
+  __shared__ int cp[LT];
+  __shared__ double rv[2], ro[2];
+  __shared__ int ra[2];
+  const int total = *nwork;
+  for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
+    const int item = work[wi], q = item >> 6, cb = item & 63;
+    const QInfo qi = a.qi[q];
+    const int jj = cb * 64 + tid;
+    const bool cin = jj < nsel[q];
+    const int c = csel[(size_t)q * C + (cin ? jj : 0)];
+    const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
+    const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
+    const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
+    const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
+    const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
+    const Real* prow = PhiCM + (size_t)c * Mp;
+    Real vt[RMAX];
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) vt[j] = VtR[(size_t)j * C + c];
+    Real s[TT], mx[TT], ov[TT];
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+      s[t] = (cin && t0 + t < T) ? sv[(size_t)(t0 + t) * C + c] : (Real)0;
+      mx[t] = 0;
+      ov[t] = 0;
+    }
+    for (int l0 = 0; l0 < M; l0 += LT) {
+      __syncthreads();
+      for (int idx = tid; idx < LT * RMAX; idx += 64) {
+        const int i = idx % LT, j = idx / LT, l = l0 + i;
+        zs[i][j] = (l < M) ? Zs[(size_t)j * Mp + l] : (Real)0;
+      }
+      for (int idx = tid; idx < LT * TT; idx += 64) {
+        const int i = idx % LT, t = idx / LT, l = l0 + i;
+        pt[i][t] = (l < M && t0 + t < T) ? ptil[(size_t)(t0 + t) * Mp + l] : (Real)0;
+      }
+      for (int i = tid; i < LT; i += 64) {
+        const int l = l0 + i;
+        dg[i] = (l < M) ? meta[l] : (Real)0;
+        rm[i] = (l < M) ? meta[Mp + l] : (Real)0;
+        cp[i] = (l < M) ? a.cpos[l] : -1;
+      }
+      __syncthreads();
+      Real base[LT];  // l0 + LT <= Mp: the padded rows of PhiCM are zero
+      if constexpr (sizeof(Real) == 4) {
+#pragma unroll
+        for (int i = 0; i < LT; i += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(prow + l0 + i);
+          base[i] = v.x;
+          base[i + 1] = v.y;
+          base[i + 2] = v.z;
+          base[i + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < LT; i += 2) {
+          const double2 v = *reinterpret_cast<const double2*>(prow + l0 + i);
+          base[i] = v.x;
+          base[i + 1] = v.y;
+        }
+      }
+      Real phi[LT];
+#pragma unroll
+      for (int i = 0; i < LT; ++i) phi[i] = phi_entry<Real, RMAX>(base[i], zs[i], vt, rm[i], cp[i], c, dg[i]);
+#pragma unroll
+      for (int t = 0; t < TT; ++t) {
+        const Real st = s[t];
+#pragma unroll
+        for (int i = 0; i < LT; ++i) Acc<Real>::add(mx[t], ov[t], fma(phi[i], st, pt[i][t]));
+      }
+    }
+    const bool ok = cin && a.valid[(size_t)q * C + c];
+    if (a.out.n1_cont_max && cin) {
+#pragma unroll
+      for (int t = 0; t < TT; ++t)
+        if (t0 + t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t0 + t) * C + c] = ok ? (float)mx[t] : -1.f;
+    }
+    const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int t = 0; t < TT; ++t) {
+      if (t0 + t < T) {  // uniform over the block
+        double v = ok ? (double)mx[t] : -1.0;
+        int arg = ok ? c : 0x7fffffff;
+        double o = ok ? (double)ov[t] * Acc<Real>::ovl_scale() : 0.0;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+          const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+          const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
+          o += __shfl_xor_sync(0xffffffffu, o, off);
+          if (v2 > v || (v2 == v && a2 < arg)) {
+            v = v2;
+            arg = a2;
+          }
+        }
+        if (lane == 0) {
+          rv[w] = v;
+          ra[w] = arg;
+          ro[w] = o;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          double bv = rv[0];
+          int ba = ra[0];
+          if (rv[1] > bv || (rv[1] == bv && ra[1] < ba)) {
+            bv = rv[1];
+            ba = ra[1];
+          }
+          const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + cb;
+          static_cast<Real*>(a.pmax)[o2] = (Real)bv;
+          a.parg[o2] = (bv < 0.0) ? -1 : ba;
+          a.povl[o2] = ro[0] + ro[1];
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
 }  // namespace dcf
 
 #include "n1_tma.cuh"
@@ -857,10 +1137,10 @@ int launch_n1(const Args& a, int RMAX, int TT, dim3 grid, cudaStream_t st, int t
 }
 
 template <class Real>
-void launch_final(const Args& a, int RMAX, cudaStream_t st) {
-  if (RMAX == 4) k_final<Real, 4><<<a.nq, 128, 0, st>>>(a);
-  else if (RMAX == 8) k_final<Real, 8><<<a.nq, 128, 0, st>>>(a);
-  else k_final<Real, 16><<<a.nq, 128, 0, st>>>(a);
+void launch_final(const Args& a, int RMAX, cudaStream_t st, const int* nsel = nullptr) {
+  if (RMAX == 4) k_final<Real, 4><<<a.nq, 128, 0, st>>>(a, nsel);
+  else if (RMAX == 8) k_final<Real, 8><<<a.nq, 128, 0, st>>>(a, nsel);
+  else k_final<Real, 16><<<a.nq, 128, 0, st>>>(a, nsel);
 }
 
 int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
@@ -960,7 +1240,81 @@ int launch_tma(const N1Maps& maps, const Args& a, int RMAX, int TT, dim3 grid, c
 
 }  // namespace
 
-extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_results* res, void* stream) {
+namespace {
+
+// What a call of the per-batch path produces besides (or instead of) the
+// N-1 results: the screener's feature rows only, or the screened N-1.
+enum : int { kModeFull = 0, kModeFeatures = 1, kModeScreened = 2 };
+struct ScreenCall {
+  int mode = kModeFull;
+  dcflow_screen* scr = nullptr;
+  int top_k = 64;
+  float fallback_logit = 0.f;
+  const dcflow_screen_report* rep = nullptr;
+  void* X = nullptr;  // features mode: rows tau * T + t, pitch ldx
+  int64_t ldx = 0;
+  uint8_t* status = nullptr;
+};
+
+template <class Real, int TT, int RMAX>
+void launch_sel_t(const Args& a, const void* phicm, const ChunkBufs& B, int grid, cudaStream_t st, int t0) {
+  constexpr int LT = sizeof(Real) == 8 ? 8 : 16;
+  k_n1_sel<Real, TT, RMAX, LT><<<grid, 64, 0, st>>>(a, static_cast<const Real*>(phicm), B.csel.as<int>(),
+                                                      B.nsel.as<int>(), B.work.as<int>(), B.nwork.as<int>(), t0);
+}
+
+template <class Real, int RMAX>
+int launch_sel_r(const Args& a, const void* phicm, const ChunkBufs& B, int TT, int grid, cudaStream_t st, int t0) {
+  switch (TT) {
+    case 1: launch_sel_t<Real, 1, RMAX>(a, phicm, B, grid, st, t0); break;
+    case 4: launch_sel_t<Real, 4, RMAX>(a, phicm, B, grid, st, t0); break;
+    case 8: launch_sel_t<Real, 8, RMAX>(a, phicm, B, grid, st, t0); break;
+    default:
+      if constexpr (sizeof(Real) == 4) {
+        if (TT == 16) launch_sel_t<Real, 16, RMAX>(a, phicm, B, grid, st, t0);
+        else if (TT == 24) launch_sel_t<Real, 24, RMAX>(a, phicm, B, grid, st, t0);
+        else launch_sel_t<Real, 32, RMAX>(a, phicm, B, grid, st, t0);
+      } else {
+        return DCFLOW_ERR_INVALID_ARG;
+      }
+  }
+  return 0;
+}
+
+template <class Real>
+int launch_sel(const Args& a, const void* phicm, const ChunkBufs& B, int RMAX, int TT, int grid, cudaStream_t st,
+               int t0) {
+  if (RMAX == 4) return launch_sel_r<Real, 4>(a, phicm, B, TT, grid, st, t0);
+  if (RMAX == 8) return launch_sel_r<Real, 8>(a, phicm, B, TT, grid, st, t0);
+  return launch_sel_r<Real, 16>(a, phicm, B, TT, grid, st, t0);
+}
+
+int launch_select(const Args& a, int T, int C, const float* Z, int ldz, int k, uint32_t fb_key, const ChunkBufs& B,
+                  int W, int32_t* pred, cudaStream_t st) {
+  const int64_t rows = (int64_t)a.nq * T;
+  const unsigned grid = (unsigned)((rows * 32 + 255) / 256);
+  uint32_t* mk = B.selmask.as<uint32_t>();
+  uint8_t* fb = B.sfb.as<uint8_t>();
+  if (C <= 256) k_select<8><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, mk, W, fb, pred);
+  else if (C <= 512) k_select<16><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, mk, W, fb, pred);
+  else if (C <= 1024) k_select<32><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, mk, W, fb, pred);
+  else k_select<64><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, mk, W, fb, pred);
+  return 0;
+}
+
+uint32_t host_float_key(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+}  // namespace
+
+static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_results* res, void* stream,
+                      const ScreenCall* sc) {
+  const int mode = sc ? sc->mode : kModeFull;
+  dcflow_results none{};
+  if (mode == kModeFeatures) res = &none;
   if (!ctx || !bt || !res) {
     set_error("dcflow_solve_batch: null argument");
     return DCFLOW_ERR_INVALID_ARG;
@@ -976,8 +1330,9 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   }
   ctx->launches = 0;
   if (N == 0) return DCFLOW_OK;
-  if (!bt->split_ptr || !bt->out_ptr || !bt->inj || !res->n1_max_loading || !res->overload_sum ||
-      !res->worst_cont || !res->island_flag || !res->n_island_cont) {
+  if (!bt->split_ptr || !bt->out_ptr || !bt->inj ||
+      (mode != kModeFeatures && (!res->n1_max_loading || !res->overload_sum || !res->worst_cont ||
+                                 !res->island_flag || !res->n_island_cont))) {
     set_error("dcflow_solve_batch: missing required pointer");
     return DCFLOW_ERR_INVALID_ARG;
   }
@@ -988,6 +1343,10 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
   // injection candidates T_i (Eq. (8)): read the small CSR to the host, validate
   // it, and map every entry to a pool bus (a column of the extended base flows)
   const int U = bt->n_var;
+  if (mode != kModeFull && U > 0) {
+    set_error("dcflow_solve_batch: the screener runs without injection candidates");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
   int R = 0;
   if (U > 0) {
     if (!bt->var_ptr || !bt->var_bus || !bt->var_delta || (int64_t)T * U > (1 << 20)) {
@@ -1115,6 +1474,28 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
                   B.povlv.ensure(c * TV * std::max(ncb, 1) * sizeof(double)) || B.bestu.ensure(c * T * sizeof(int)) ||
                   B.ptb.ensure(c * T * Mp * rs) || B.sb.ensure(c * T * std::max(C, 1) * rs)))
       return DCFLOW_ERR_OOM;
+  }
+  dcflow_screen* scr = sc ? sc->scr : nullptr;
+  const int W = (C + 31) / 32;
+  const int64_t srows = round_up((int64_t)cap * T, 128);  // feature rows of a chunk
+  if (mode == kModeScreened) {
+    if (ctx->bufs[0].selmask.ensure((size_t)cap * std::max(W, 1) * 4) || ctx->bufs[0].sfb.ensure((size_t)cap) ||
+        ctx->bufs[0].csel.ensure((size_t)cap * std::max(C, 1) * 4) || ctx->bufs[0].nsel.ensure((size_t)cap * 4) ||
+        ctx->bufs[0].work.ensure((size_t)cap * std::max(ncb, 1) * 4) || ctx->bufs[0].nwork.ensure(4) ||
+        scr->iX.ensure((size_t)srows * scr->Fp * 2) || scr->iH1.ensure((size_t)srows * scr->H * 2) ||
+        scr->iH2.ensure((size_t)srows * scr->H * 2) || scr->iZ.ensure((size_t)srows * scr->Cp * 4))
+      return DCFLOW_ERR_OOM;
+    if (!ctx->phicm_ready) {
+      if (ctx->PhiCM.ensure((size_t)std::max(C, 1) * Mp * rs)) return DCFLOW_ERR_OOM;
+      const dim3 blk(32, 8), grd((Mp + 31) / 32, (C + 31) / 32);
+      if (fp64)
+        k_phi_cm<double><<<grd, blk, 0, st>>>(ctx->PhiMC.as<double>(), M, C, ctx->ldc, Mp, ctx->PhiCM.as<double>());
+      else
+        k_phi_cm<float><<<grd, blk, 0, st>>>(ctx->PhiMC.as<float>(), M, C, ctx->ldc, Mp, ctx->PhiCM.as<float>());
+      DCF_CHECK_LAUNCH();
+      ++ctx->launches;
+      ctx->phicm_ready = true;
+    }
   }
   ctx->chunk_cap = cap;
   if (!ctx->side) {
@@ -1293,17 +1674,142 @@ extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const
       ctx->launches += 2;
       DCF_CHECK_LAUNCH();
     }
-    if (C > 0) {
+    if (mode == kModeFeatures) {
+      if (fp64)
+        k_features<double><<<ch.nq, 256, 0, st>>>(a, g, in, scr->foff.as<int>(), scr->Fp,
+                                                   static_cast<__nv_bfloat16*>(sc->X), sc->ldx, 1, sc->status);
+      else
+        k_features<float><<<ch.nq, 256, 0, st>>>(a, g, in, scr->foff.as<int>(), scr->Fp,
+                                                  static_cast<__nv_bfloat16*>(sc->X), sc->ldx, 1, sc->status);
+      ++ctx->launches;
+      DCF_CHECK_LAUNCH();
+      DCF_CUDA(cudaEventRecord(ctx->ev_free[bi], st));
+      continue;
+    }
+    const int* nsel_dev = nullptr;
+    if (mode == kModeScreened) {
+      // features -> scores (tensor cores) -> top k per row -> union -> N-1 over the union
+      const int rows = ch.nq * T, Br = (int)round_up(rows, 128), Fp = scr->Fp, H = scr->H, Cp = scr->Cp;
+      if (fp64)
+        k_features<double><<<ch.nq, 256, 0, st>>>(a, g, in, scr->foff.as<int>(), Fp, scr->iX.as<__nv_bfloat16>(),
+                                                   Fp, 0, nullptr);
+      else
+        k_features<float><<<ch.nq, 256, 0, st>>>(a, g, in, scr->foff.as<int>(), Fp, scr->iX.as<__nv_bfloat16>(), Fp,
+                                                  0, nullptr);
+      DCF_CHECK_LAUNCH();
+      int* gerr = ctx->err.as<int>();
+      GemmSpec g1;
+      g1.A = scr->iX.p; g1.lda = Fp; g1.B = scr->wb[0].p; g1.ldb = Fp; g1.M = Br; g1.N = H; g1.K = Fp;
+      g1.bias = scr->prm[kB1].as<float>(); g1.relu = true; g1.D = scr->iH1.p; g1.ldd = H; g1.out_bf16 = true;
+      GemmSpec g2;
+      g2.A = scr->iH1.p; g2.lda = H; g2.B = scr->wb[1].p; g2.ldb = H; g2.M = Br; g2.N = H; g2.K = H;
+      g2.bias = scr->prm[kB2].as<float>(); g2.relu = true; g2.D = scr->iH2.p; g2.ldd = H; g2.out_bf16 = true;
+      GemmSpec g3;
+      g3.A = scr->iH2.p; g3.lda = H; g3.B = scr->wb[2].p; g3.ldb = H; g3.M = Br; g3.N = Cp; g3.K = H;
+      g3.bias = scr->prm[kB3].as<float>(); g3.D = scr->iZ.p; g3.ldd = Cp;
+      int rc = gemm_run(g1, gerr, st);
+      if (!rc) rc = gemm_run(g2, gerr, st);
+      if (!rc) rc = gemm_run(g3, gerr, st);
+      if (rc) return rc;
+      const ChunkBufs& SB = ctx->bufs[0];
+      DCF_CUDA(cudaMemsetAsync(SB.selmask.p, 0, (size_t)ch.nq * W * 4, st));
+      DCF_CUDA(cudaMemsetAsync(SB.sfb.p, 0, (size_t)ch.nq, st));
+      DCF_CUDA(cudaMemsetAsync(SB.nwork.p, 0, 4, st));
+      const dcflow_screen_report* rep = sc->rep;
+      launch_select(a, T, C, scr->iZ.as<float>(), Cp, sc->top_k, host_float_key(sc->fallback_logit), SB, W,
+                    rep ? rep->pred : nullptr, st);
+      DCF_CHECK_LAUNCH();
+      k_compact<<<(ch.nq * 32 + 255) / 256, 256, 0, st>>>(a.qi, ch.nq, C, W, SB.selmask.as<uint32_t>(),
+                                                         SB.sfb.as<uint8_t>(), SB.csel.as<int>(), SB.nsel.as<int>(),
+                                                         SB.work.as<int>(), SB.nwork.as<int>(),
+                                                         rep ? rep->n_eval : nullptr, rep ? rep->fallback : nullptr);
+      DCF_CHECK_LAUNCH();
+      ctx->launches += 6;
+      const int TTs = pick_tt(T, fp64);
+      const int sgrid = (int)std::min<int64_t>((int64_t)ch.nq * ncb, 148 * 16);
+      for (int t0 = 0; t0 < T; t0 += TTs) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (ctx->prof_on) {
+          while (ctx->prof_ev.size() < ctx->prof_used + 2) {
+            cudaEvent_t e;
+            DCF_CUDA(cudaEventCreate(&e));
+            ctx->prof_ev.push_back(e);
+          }
+          e0 = ctx->prof_ev[ctx->prof_used];
+          e1 = ctx->prof_ev[ctx->prof_used + 1];
+          ctx->prof_used += 2;
+          DCF_CUDA(cudaEventRecord(e0, st));
+        }
+        rc = fp64 ? launch_sel<double>(af, ctx->PhiCM.p, SB, RMAX, TTs, sgrid, st, t0)
+                  : launch_sel<float>(af, ctx->PhiCM.p, SB, RMAX, TTs, sgrid, st, t0);
+        if (rc) return rc;
+        ++ctx->launches;
+        DCF_CHECK_LAUNCH();
+        if (e1) DCF_CUDA(cudaEventRecord(e1, st));
+      }
+      nsel_dev = SB.nsel.as<int>();
+    } else if (C > 0) {
       int rc = run_n1(af, RMAX, T, true);
       if (rc) return rc;
     }
-    if (fp64) launch_final<double>(af, RMAX, st);
-    else launch_final<float>(af, RMAX, st);
+    if (fp64) launch_final<double>(af, RMAX, st, nsel_dev);
+    else launch_final<float>(af, RMAX, st, nsel_dev);
     ++ctx->launches;
     DCF_CHECK_LAUNCH();
     DCF_CUDA(cudaEventRecord(ctx->ev_free[bi], st));
   }
   return DCFLOW_OK;
+}
+
+extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_results* res, void* stream) {
+  return solve_impl(ctx, bt, res, stream, nullptr);
+}
+
+static int screen_matches(const dcflow_ctx* ctx, const dcflow_screen* s, const char* who) {
+  if (!ctx || !s) {
+    set_error(std::string(who) + ": null context or screener");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  if (s->ctx != ctx || s->M != ctx->M || s->C != ctx->C || s->V != ctx->V) {
+    set_error(std::string(who) + ": the screener was created for another context or study");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  return 0;
+}
+
+extern "C" int dcflow_screen_features(dcflow_ctx* ctx, const dcflow_screen* s, const dcflow_batch* bt, void* X,
+                                      int64_t ldx, uint8_t* status, void* stream) {
+  int rc = screen_matches(ctx, s, "dcflow_screen_features");
+  if (rc) return rc;
+  if (!X || ldx < s->Fp || ldx % 8) {
+    set_error("dcflow_screen_features: need X with ldx >= F_pad, ldx % 8 == 0");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  ScreenCall sc;
+  sc.mode = kModeFeatures;
+  sc.scr = const_cast<dcflow_screen*>(s);
+  sc.X = X;
+  sc.ldx = ldx;
+  sc.status = status;
+  return solve_impl(ctx, bt, nullptr, stream, &sc);
+}
+
+extern "C" int dcflow_solve_batch_screened(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_results* res,
+                                           dcflow_screen* s, const dcflow_screen_options* opt,
+                                           const dcflow_screen_report* rep, void* stream) {
+  int rc = screen_matches(ctx, s, "dcflow_solve_batch_screened");
+  if (rc) return rc;
+  if (!opt || opt->top_k < 1) {
+    set_error("dcflow_solve_batch_screened: need options with top_k >= 1");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  ScreenCall sc;
+  sc.mode = kModeScreened;
+  sc.scr = s;
+  sc.top_k = opt->top_k;
+  sc.fallback_logit = opt->fallback_logit;
+  sc.rep = rep;
+  return solve_impl(ctx, bt, res, stream, &sc);
 }
 
 extern "C" int dcflow_profile(dcflow_ctx* ctx, int32_t enable) {

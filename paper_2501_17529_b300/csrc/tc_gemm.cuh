@@ -9,9 +9,13 @@
 // accumulator in tensor memory, and tcgen05.commit frees the stage on an
 // "empty" mbarrier.  After the last stage a commit signals the epilogue: each
 // warp reads its 32 accumulator lanes (rows) with tcgen05.ld.32x32b.
+// Epilogue options: bias[N], ReLU, a ReLU-derivative mask (D := 0 where a
+// bf16 tensor of D's shape is <= 0), FP32 or BF16 output, an optional second
+// BF16 store of D transposed, and split-K: gridDim.z CTAs share the K range of
+// a tile and each stores its FP32 partial at D + z * split_stride.
 // Every mbarrier wait is bounded; on expiry the CTA records an error, waits
 // (bounded) for its outstanding copies and MMAs, frees its tensor memory and
-// returns.  Shapes: M, N multiples of 128, K a multiple of 64.
+// returns.  Shapes: M, N multiples of 128, K a multiple of 64 * gridDim.z.
 #pragma once
 
 #include <cuda.h>
@@ -85,11 +89,16 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 
 struct GemmArgs {
   int M, N, K;
-  const float* bias;  // [N] or null
+  const float* bias;             // [N] or null
   int relu;
-  void* D;            // row-major
+  const __nv_bfloat16* mask;     // [M x ldm] or null: D := 0 where mask <= 0
+  int ldm;
+  void* D;                       // row-major [M x ldd] or null
   int ldd;
   int out_bf16;
+  __nv_bfloat16* Dt;             // [N x lddt] transposed BF16 copy of D, or null
+  int lddt;
+  long long split_stride;        // elements between the FP32 partials of split-K
   int* err;
 };
 
@@ -105,7 +114,8 @@ __global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUten
   const uint32_t tslot = done + 8u;  // tensor-memory address written by tcgen05.alloc
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int KT = g.K / BK;
+  const int KT = g.K / BK / (int)gridDim.z;  // k-tiles of this CTA's share
+  const int kt0 = (int)blockIdx.z * KT;
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       bar_init(full(s), 1);
@@ -132,8 +142,8 @@ __global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUten
       const int s = kt % STAGES;
       const uint32_t a = base + s * kStageBytes, b = a + kTileBytes;
       bar_expect(full(s), kStageBytes);
-      tma2d(a, &mA, kt * BK, m0, full(s));
-      tma2d(b, &mB, kt * BK, n0, full(s));
+      tma2d(a, &mA, (kt0 + kt) * BK, m0, full(s));
+      tma2d(b, &mB, (kt0 + kt) * BK, n0, full(s));
     };
     int issued = 0, landed = 0;  // loads issued / loads whose arrival was observed
     for (int kt = 0; kt < KT && kt < STAGES; ++kt, ++issued) load(kt);
@@ -173,7 +183,7 @@ __global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUten
     if (tid == 0) atomicExch(g.err, 1);
   } else {
     // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
-    const int row = m0 + warp * 32 + lane;
+    const int row = m0 + warp * 32 + lane;  // < M: M is a multiple of 128
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t r[16];
@@ -194,17 +204,32 @@ __global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUten
         if (g.relu) x = fmaxf(x, 0.f);
         v[j] = x;
       }
-      if (row < g.M) {
+      if (g.mask) {
+        const __nv_bfloat16* mk = g.mask + (size_t)row * g.ldm + n0 + c0;
+#pragma unroll
+        for (int j = 0; j < 16; j += 8) {
+          const uint4 u = *reinterpret_cast<const uint4*>(mk + j);
+          const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (!(__bfloat162float(h[e]) > 0.f)) v[j + e] = 0.f;
+        }
+      }
+      if (g.D) {
         if (g.out_bf16) {
           __nv_bfloat16* d = static_cast<__nv_bfloat16*>(g.D) + (size_t)row * g.ldd + n0 + c0;
 #pragma unroll
           for (int j = 0; j < 16; j += 2)
             *reinterpret_cast<__nv_bfloat162*>(d + j) = __floats2bfloat162_rn(v[j], v[j + 1]);
         } else {
-          float* d = static_cast<float*>(g.D) + (size_t)row * g.ldd + n0 + c0;
+          float* d = static_cast<float*>(g.D) + (size_t)blockIdx.z * g.split_stride + (size_t)row * g.ldd + n0 + c0;
 #pragma unroll
           for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(d + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
+      }
+      if (g.Dt) {  // lanes hold consecutive rows: each column is a 64-byte run
+#pragma unroll
+        for (int j = 0; j < 16; ++j) g.Dt[(size_t)(n0 + c0 + j) * g.lddt + row] = __float2bfloat16_rn(v[j]);
       }
     }
   }

@@ -47,10 +47,26 @@ class Results(ctypes.Structure):
                 ("n1_cont_max", c_void_p)]
 
 
+class ScreenOptions(ctypes.Structure):
+    _fields_ = [("top_k", c_int32), ("fallback_logit", ctypes.c_float)]
+
+
+class ScreenReport(ctypes.Structure):
+    _fields_ = [("n_eval", c_void_p), ("fallback", c_void_p), ("pred", c_void_p)]
+
+
 EXPORTED = ["dcflow_default_options", "dcflow_setup", "dcflow_base_ptdf", "dcflow_base_ptdf_noalloc",
             "dcflow_set_study",
             "dcflow_solve_batch", "dcflow_last_launch_count", "dcflow_profile", "dcflow_profile_read",
-            "dcflow_gemm_bf16", "dcflow_destroy", "dcflow_strerror", "dcflow_last_error"]
+            "dcflow_gemm_bf16",
+            "dcflow_screen_create", "dcflow_screen_destroy", "dcflow_screen_dims", "dcflow_screen_features",
+            "dcflow_screen_labels", "dcflow_screen_backward", "dcflow_screen_adam", "dcflow_screen_train_step",
+            "dcflow_screen_check", "dcflow_screen_logits", "dcflow_screen_get", "dcflow_screen_set",
+            "dcflow_screen_adam_step", "dcflow_solve_batch_screened",
+            "dcflow_destroy", "dcflow_strerror", "dcflow_last_error"]
+
+SCREEN_TENSORS = ("W1", "b1", "W2", "b2", "W3", "b3")
+SCREEN_KINDS = ("param", "grad", "m", "v")
 
 _lib = None
 
@@ -85,6 +101,31 @@ def load_library(path: str = LIB_PATH):
     lib.dcflow_gemm_bf16.argtypes = [c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
                                      c_int32, c_void_p, c_int32, c_int32, c_void_p]
     lib.dcflow_gemm_bf16.restype = c_int32
+    f = ctypes.c_float
+    sigs = {
+        "dcflow_screen_create": ([c_void_p, c_int32, ctypes.c_uint64, POINTER(c_void_p)], c_int32),
+        "dcflow_screen_destroy": ([c_void_p], None),
+        "dcflow_screen_dims": ([c_void_p] + [POINTER(c_int32)] * 5, c_int32),
+        "dcflow_screen_features": ([c_void_p, c_void_p, POINTER(Batch), c_void_p, c_int64, c_void_p, c_void_p],
+                                   c_int32),
+        "dcflow_screen_labels": ([c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_int64, c_void_p], c_int32),
+        "dcflow_screen_backward": ([c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int32, c_void_p,
+                                    c_void_p], c_int32),
+        "dcflow_screen_adam": ([c_void_p, f, c_void_p], c_int32),
+        "dcflow_screen_train_step": ([c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_int32, f,
+                                      c_void_p, c_void_p], c_int32),
+        "dcflow_screen_check": ([c_void_p, c_void_p], c_int32),
+        "dcflow_screen_logits": ([c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_int64, c_void_p], c_int32),
+        "dcflow_screen_get": ([c_void_p, c_int32, c_int32, c_void_p], c_int32),
+        "dcflow_screen_set": ([c_void_p, c_int32, c_int32, c_void_p], c_int32),
+        "dcflow_screen_adam_step": ([c_void_p, POINTER(c_int64), c_int32], c_int32),
+        "dcflow_solve_batch_screened": ([c_void_p, POINTER(Batch), POINTER(Results), c_void_p,
+                                         POINTER(ScreenOptions), POINTER(ScreenReport), c_void_p], c_int32),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
     lib.dcflow_destroy.argtypes = [c_void_p]
     lib.dcflow_destroy.restype = None
     lib.dcflow_strerror.argtypes = [c_int32]
@@ -218,6 +259,82 @@ def dcflow_gemm_bf16(A, B, bias=None, relu=False, out=None, out_bf16=False, stre
     return out
 
 
+def dcflow_screen_create(ctx, max_rows, seed=0):
+    out = c_void_p()
+    _check(load_library().dcflow_screen_create(ctx, int(max_rows), int(seed), byref(out)), "dcflow_screen_create")
+    return out
+
+
+def dcflow_screen_destroy(scr):
+    load_library().dcflow_screen_destroy(scr)
+
+
+def dcflow_screen_dims(scr):
+    v = [c_int32() for _ in range(5)]
+    _check(load_library().dcflow_screen_dims(scr, *[byref(x) for x in v]), "dcflow_screen_dims")
+    return dict(zip(("F", "F_pad", "H", "C", "C_pad"), (x.value for x in v)))
+
+
+def dcflow_screen_features(ctx, scr, batch: Batch, X, ldx, status=None, stream=None):
+    _check(load_library().dcflow_screen_features(ctx, scr, byref(batch), _ptr(X), int(ldx), _ptr(status),
+                                                 _stream_ptr(stream)), "dcflow_screen_features")
+
+
+def dcflow_screen_labels(scr, cont_max, n_rows, k, Y, ldy, stream=None):
+    _check(load_library().dcflow_screen_labels(scr, _ptr(cont_max), int(n_rows), int(k), _ptr(Y), int(ldy),
+                                               _stream_ptr(stream)), "dcflow_screen_labels")
+
+
+def dcflow_screen_backward(scr, X, ldx, Y, ldy, rows, n, loss, stream=None):
+    _check(load_library().dcflow_screen_backward(scr, _ptr(X), int(ldx), _ptr(Y), int(ldy), _ptr(rows), int(n),
+                                                 _ptr(loss), _stream_ptr(stream)), "dcflow_screen_backward")
+
+
+def dcflow_screen_adam(scr, lr, stream=None):
+    _check(load_library().dcflow_screen_adam(scr, float(lr), _stream_ptr(stream)), "dcflow_screen_adam")
+
+
+def dcflow_screen_train_step(scr, X, ldx, Y, ldy, rows, n, lr, loss, stream=None):
+    _check(load_library().dcflow_screen_train_step(scr, _ptr(X), int(ldx), _ptr(Y), int(ldy), _ptr(rows), int(n),
+                                                   float(lr), _ptr(loss), _stream_ptr(stream)),
+           "dcflow_screen_train_step")
+
+
+def dcflow_screen_check(scr, stream=None):
+    _check(load_library().dcflow_screen_check(scr, _stream_ptr(stream)), "dcflow_screen_check")
+
+
+def dcflow_screen_logits(scr, X, ldx, n_rows, Z, ldz, stream=None):
+    _check(load_library().dcflow_screen_logits(scr, _ptr(X), int(ldx), int(n_rows), _ptr(Z), int(ldz),
+                                               _stream_ptr(stream)), "dcflow_screen_logits")
+
+
+def dcflow_screen_get(scr, tensor, kind, out: np.ndarray):
+    assert out.dtype == np.float32 and out.flags.c_contiguous
+    _check(load_library().dcflow_screen_get(scr, int(tensor), int(kind), out.ctypes.data_as(c_void_p)),
+           "dcflow_screen_get")
+    return out
+
+
+def dcflow_screen_set(scr, tensor, kind, values: np.ndarray):
+    v = np.ascontiguousarray(values, np.float32)
+    _check(load_library().dcflow_screen_set(scr, int(tensor), int(kind), v.ctypes.data_as(c_void_p)),
+           "dcflow_screen_set")
+
+
+def dcflow_screen_adam_step(scr, t=None):
+    v = c_int64(0 if t is None else int(t))
+    _check(load_library().dcflow_screen_adam_step(scr, byref(v), 0 if t is None else 1), "dcflow_screen_adam_step")
+    return v.value
+
+
+def dcflow_solve_batch_screened(ctx, batch: Batch, results: Results, scr, opt: ScreenOptions,
+                                report: ScreenReport, stream=None):
+    _check(load_library().dcflow_solve_batch_screened(ctx, byref(batch), byref(results), scr, byref(opt),
+                                                      byref(report), _stream_ptr(stream)),
+           "dcflow_solve_batch_screened")
+
+
 def dcflow_destroy(ctx):
     if ctx is not None and ctx.value:
         load_library().dcflow_destroy(ctx)
@@ -334,6 +451,21 @@ class Solver:
         dcflow_solve_batch(self.ctx, dbatch.cstruct(), res.cstruct(), stream)
         return res
 
+    def solve_screened(self, dbatch: DeviceBatch, screener: "Screener", top_k=64, fallback_logit=float("inf"),
+                       results: DeviceResults | None = None, want_pred=False, stream=None):
+        """Screened N-1 (the union of each topology's top_k scored contingencies); returns (results, report)."""
+        import torch
+        res = results or DeviceResults(dbatch.n_topo, dbatch.n_time, self.n_mon, n_cont=self.n_cont)
+        N, T = dbatch.n_topo, dbatch.n_time
+        rep = {"n_eval": torch.empty(max(1, N), dtype=torch.int32, device="cuda"),
+               "fallback": torch.empty(max(1, N), dtype=torch.uint8, device="cuda"),
+               "pred": (torch.empty(max(1, N * T * top_k), dtype=torch.int32, device="cuda") if want_pred else None)}
+        dcflow_solve_batch_screened(self.ctx, dbatch.cstruct(), res.cstruct(), screener.scr,
+                                    ScreenOptions(int(top_k), float(fallback_logit)),
+                                    ScreenReport(_ptr(rep["n_eval"]), _ptr(rep["fallback"]), _ptr(rep["pred"])),
+                                    stream)
+        return res, rep
+
     def last_launch_count(self) -> int:
         return dcflow_last_launch_count(self.ctx)
 
@@ -345,5 +477,99 @@ class Solver:
         try:
             if getattr(self, "ctx", None) is not None:
                 self.close()
+        except Exception:
+            pass
+
+
+class Screener:
+    """The learned contingency screener of one Solver's study (device state in libdcflow)."""
+
+    def __init__(self, solver: Solver, max_rows=8192, seed=0):
+        self.solver = solver
+        self.scr = dcflow_screen_create(solver.ctx, max_rows, seed)
+        self.max_rows = int(max_rows)
+        d = dcflow_screen_dims(self.scr)
+        self.F, self.F_pad, self.H, self.C, self.C_pad = d["F"], d["F_pad"], d["H"], d["C"], d["C_pad"]
+
+    def features(self, dbatch: DeviceBatch, stream=None):
+        """Feature rows [n_topo * n_time, F_pad] (bf16) and the topology status [n_topo] (uint8)."""
+        import torch
+        X = torch.empty((dbatch.n_topo * dbatch.n_time, self.F_pad), dtype=torch.bfloat16, device="cuda")
+        st = torch.empty(max(1, dbatch.n_topo), dtype=torch.uint8, device="cuda")
+        dcflow_screen_features(self.solver.ctx, self.scr, dbatch.cstruct(), X, self.F_pad, st, stream)
+        return X, st[:dbatch.n_topo]
+
+    def labels(self, cont_max, k=64, stream=None):
+        """uint8 labels [rows, C_pad] from per-contingency maximum loadings [rows * C] (float32)."""
+        import torch
+        rows = cont_max.numel() // self.C
+        Y = torch.empty((rows, self.C_pad), dtype=torch.uint8, device="cuda")
+        dcflow_screen_labels(self.scr, cont_max, rows, k, Y, self.C_pad, stream)
+        return Y
+
+    def backward(self, X, Y, rows=None, n=None, stream=None):
+        import torch
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        n = int(rows.numel() if rows is not None else (n or X.shape[0]))
+        dcflow_screen_backward(self.scr, X, X.stride(0), Y, Y.stride(0), rows, n, loss, stream)
+        return loss
+
+    def adam(self, lr, stream=None):
+        dcflow_screen_adam(self.scr, lr, stream)
+
+    def train_step(self, X, Y, rows, lr, loss, stream=None):
+        dcflow_screen_train_step(self.scr, X, X.stride(0), Y, Y.stride(0), rows, int(rows.numel()), lr, loss,
+                                 stream)
+
+    def check(self, stream=None):
+        dcflow_screen_check(self.scr, stream)
+
+    def logits(self, X, n_rows=None, stream=None):
+        import torch
+        n = int(X.shape[0] if n_rows is None else n_rows)
+        Z = torch.empty((max(1, n), self.C), dtype=torch.float32, device="cuda")
+        dcflow_screen_logits(self.scr, X, X.stride(0), n, Z, self.C, stream)
+        return Z[:n]
+
+    def shape(self, name):
+        return {"W1": (self.H, self.F), "b1": (self.H,), "W2": (self.H, self.H), "b2": (self.H,),
+                "W3": (self.C, self.H), "b3": (self.C,)}[name]
+
+    def get(self, name, kind="param"):
+        out = np.empty(self.shape(name), np.float32)
+        return dcflow_screen_get(self.scr, SCREEN_TENSORS.index(name), SCREEN_KINDS.index(kind), out)
+
+    def set(self, name, values, kind="param"):
+        v = np.asarray(values, np.float32)
+        assert v.shape == self.shape(name), (name, v.shape)
+        dcflow_screen_set(self.scr, SCREEN_TENSORS.index(name), SCREEN_KINDS.index(kind), v)
+
+    def state(self) -> dict:
+        """Parameters, Adam moments and step counter (a checkpoint)."""
+        st = {f"{k}.{n}": self.get(n, k) for n in SCREEN_TENSORS for k in ("param", "m", "v")}
+        st["adam_t"] = np.array(dcflow_screen_adam_step(self.scr), np.int64)
+        return st
+
+    def load_state(self, st: dict):
+        for n in SCREEN_TENSORS:
+            for k in ("param", "m", "v"):
+                self.set(n, st[f"{k}.{n}"], k)
+        dcflow_screen_adam_step(self.scr, int(st["adam_t"]))
+
+    def save(self, path):
+        np.savez(path, **self.state())
+
+    def load(self, path):
+        with np.load(path) as z:
+            self.load_state({k: z[k] for k in z.files})
+
+    def close(self):
+        if self.scr is not None:
+            dcflow_screen_destroy(self.scr)
+            self.scr = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

@@ -1,0 +1,207 @@
+"""Training and evaluation driver of the learned contingency screener.
+
+Orchestration only: features, labels, the forward/backward passes, Adam and
+the screened N-1 all run in libdcflow's kernels; PyTorch supplies device
+memory, index permutations and reductions of reported statistics.
+
+The exact full N-1 (``Solver.solve(want_cont_max=True)``) is both the source
+of the training labels and the judge of the screener: recall is measured
+against it, and the screened solve falls back to it per topology.
+
+    python -m paper_2501_17529_b300.screener --train 200000 --eval 100000
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from .dcflow import DeviceBatch, DeviceResults, Screener, Solver
+
+
+def exact(solver: Solver, topo, inj, chunk=20000):
+    """Full N-1 with per-contingency maxima, in batches: (cont_max [N*T*C] f32, n1_max [N, T], status [N])."""
+    import torch
+    N, T, C = topo.n_topo, inj.shape[0], solver.n_cont
+    cm = torch.empty(N * T * C, dtype=torch.float32, device="cuda")
+    n1 = torch.empty((N, T), dtype=torch.float64, device="cuda")
+    st = torch.empty(N, dtype=torch.uint8, device="cuda")
+    for a in range(0, N, chunk):
+        b = min(N, a + chunk)
+        db = DeviceBatch(topo.subset(np.arange(a, b)), inj)
+        r = solver.solve(db, want_cont_max=True)
+        cm[a * T * C:b * T * C] = r.n1_cont_max[:(b - a) * T * C]
+        n1[a:b] = r.n1_max_loading[:(b - a) * T].view(b - a, T)
+        st[a:b] = r.island_flag[:b - a]
+    return cm, n1, st
+
+
+def dataset(solver: Solver, screener: Screener, topo, inj, k=64, chunk=20000):
+    """Features X [N*T, F_pad] bf16, labels Y [N*T, C_pad] u8, cont_max, n1_max, status."""
+    import torch
+    N, T = topo.n_topo, inj.shape[0]
+    X = torch.empty((N * T, screener.F_pad), dtype=torch.bfloat16, device="cuda")
+    for a in range(0, N, chunk):
+        b = min(N, a + chunk)
+        db = DeviceBatch(topo.subset(np.arange(a, b)), inj)
+        Xa, _ = screener.features(db)
+        X[a * T:b * T] = Xa
+    cm, n1, st = exact(solver, topo, inj, chunk)
+    Y = screener.labels(cm, k)
+    return X, Y, cm, n1, st
+
+
+def train(screener: Screener, X, Y, status, T, epochs=4, batch=4096, lr=1e-3, seed=0, log=None):
+    """Minibatch Adam over the rows of non-islanded topologies; returns the mean loss per epoch."""
+    import torch
+    ok = torch.nonzero(status.repeat_interleave(T) == 0).flatten().to(torch.int32)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    for ep in range(epochs):
+        perm = ok[torch.randperm(ok.numel(), device="cuda", generator=g)]
+        loss.zero_()
+        nb = 0
+        for a in range(0, perm.numel() - batch + 1, batch):
+            screener.train_step(X, Y, perm[a:a + batch], lr, loss)
+            nb += 1
+        screener.check()
+        hist.append(float(loss.item()) / max(nb, 1))
+        if log:
+            log(f"epoch {ep}: mean loss {hist[-1]:.5f} over {nb} steps")
+    return hist
+
+
+def recall_at_k(pred, Y, C):
+    """sum |pred ∩ true| / sum |true| with pred [rows, k] (−1 padding) and labels Y [rows, C_pad]."""
+    import torch
+    p = pred.long()
+    valid = (p >= 0) & (p < C)
+    hit = torch.gather(Y[:, :C].to(torch.int64), 1, torch.where(valid, p, 0)) * valid
+    tot = Y[:, :C].sum()
+    return float(hit.sum().item()) / max(1, float(tot.item()))
+
+
+def evaluate(solver: Solver, screener: Screener, topo, inj, Y, cont_max, n1_exact, status, top_k=64,
+             fallback_logit=float("inf"), chunk=20000, repeats=3):
+    """Screened vs full N-1 on a held-out batch: recall, worst-contingency hits, error, timings."""
+    import torch
+    N, T, C = topo.n_topo, inj.shape[0], solver.n_cont
+    pred = torch.empty((N * T, top_k), dtype=torch.int32, device="cuda")
+    neval = torch.empty(N, dtype=torch.int32, device="cuda")
+    fb = torch.empty(N, dtype=torch.uint8, device="cuda")
+    n1s = torch.empty((N, T), dtype=torch.float64, device="cuda")
+    batches = [(a, min(N, a + chunk)) for a in range(0, N, chunk)]
+    dbs = [DeviceBatch(topo.subset(np.arange(a, b)), inj) for a, b in batches]
+    ress = [DeviceResults(b - a, T, solver.n_mon, n_cont=C) for a, b in batches]
+
+    def run_screened():
+        for (a, b), db, r in zip(batches, dbs, ress):
+            _, rep = solver.solve_screened(db, screener, top_k, fallback_logit, results=r, want_pred=True)
+            pred[a * T:b * T] = rep["pred"][:(b - a) * T * top_k].view(-1, top_k)
+            neval[a:b] = rep["n_eval"][:b - a]
+            fb[a:b] = rep["fallback"][:b - a]
+            n1s[a:b] = r.n1_max_loading[:(b - a) * T].view(b - a, T)
+
+    def run_full():
+        for db, r in zip(dbs, ress):
+            solver.solve(db, results=r)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return best
+
+    t_full = timed(run_full)
+    t_scr = timed(run_screened)
+    ok = (status == 0).repeat_interleave(T)
+    cm = cont_max.view(N * T, C)
+    worst = torch.where(cm.max(dim=1).values > 0, cm.argmax(dim=1), torch.full_like(cm[:, 0], -1, dtype=torch.int64))
+    # evaluated set per topology: the union of its rows' predictions (all contingencies after a fallback)
+    ev = torch.zeros((N, C + 1), dtype=torch.bool, device="cuda")  # column C collects the -1 padding
+    pv = pred.view(N, T * top_k).long()
+    ev.scatter_(1, torch.where((pv >= 0) & (pv < C), pv, C), True)
+    ev = ev[:, :C]
+    ev[fb.bool()] = True
+    ev_rows = ev.repeat_interleave(T, dim=0)
+    Yc = Y[:, :C].bool()
+    okr = ok.view(-1, 1)
+    rec64 = recall_at_k(pred[ok], Y[ok], C)
+    rec_ev = float((Yc & ev_rows & okr).sum().item()) / max(1, float((Yc & okr).sum().item()))
+    wv = worst[ok]
+    hit = ev_rows[ok].gather(1, wv.clamp(min=0).view(-1, 1)).flatten() | (wv < 0)
+    err = (n1s.flatten()[ok] - n1_exact.flatten()[ok]).abs()
+    rel = err / n1_exact.flatten()[ok].abs().clamp(min=1e-12)
+    lf_full = int(ok.sum().item()) * C
+    return {
+        "topologies": N, "timesteps": T, "contingencies": C, "top_k": top_k,
+        "recall_at_k": rec64, "recall_evaluated": rec_ev,
+        "worst_cont_hit_rate": float(hit.float().mean().item()),
+        "n1_max_rel_err_max": float(rel.max().item()) if rel.numel() else 0.0,
+        "n1_max_rel_err_mean": float(rel.mean().item()) if rel.numel() else 0.0,
+        "evaluated_fraction": float(neval[status == 0].float().mean().item()) / C,
+        "fallback_fraction": float(fb[status == 0].float().mean().item()),
+        "full_s": t_full, "screened_s": t_scr, "speedup": t_full / t_scr,
+        "full_loadflows_per_s": lf_full / t_full, "screened_equiv_loadflows_per_s": lf_full / t_scr,
+    }
+
+
+def main():
+    import torch
+    from . import synth
+    from .csrc import build
+
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--train", type=int, default=200000, help="training topologies")
+    ap.add_argument("--eval", type=int, default=100000, help="held-out topologies")
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--top-k", type=int, default=64)
+    ap.add_argument("--fallback-logit", type=float, default=float("inf"))
+    ap.add_argument("--save", default=None, help="checkpoint path (.npz)")
+    a = ap.parse_args()
+    build.build()
+    torch.cuda.set_device(0)
+    w = synth.workload(5, n_topo=a.train)
+    ev_topo = synth.make_topologies(w.grid, w.subs, a.eval, 605, (1, 8), (0, 0))
+    base = Solver(w.grid, precision="fp64")
+    pt = base.base_ptdf(w.mon).cpu().numpy()
+    base.close()
+    lim = np.ones(w.grid.n_branch)
+    lim[w.mon] = 1.2 * np.abs(w.inj @ pt.T).max(axis=0) + 0.1
+    solver = Solver(w.grid, precision="fp32")
+    solver.set_study(w.mon, w.cont, lim, split_bus=w.subs)
+    scr = Screener(solver, max_rows=a.batch, seed=1)
+    t0 = time.perf_counter()
+    Xtr, Ytr, _, _, st_tr = dataset(solver, scr, w.topo, w.inj, a.top_k)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = train(scr, Xtr, Ytr, st_tr, w.inj.shape[0], a.epochs, a.batch, a.lr, log=print)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del Xtr
+    Xev, Yev, cm_ev, n1_ev, st_ev = dataset(solver, scr, ev_topo, w.inj, a.top_k)
+    del Xev
+    rep = evaluate(solver, scr, ev_topo, w.inj, Yev, cm_ev, n1_ev, st_ev, a.top_k, a.fallback_logit)
+    rep.update({"train_topologies": a.train, "train_rows": a.train * w.inj.shape[0], "epochs": a.epochs,
+                "loss_per_epoch": hist, "data_s": t_data, "train_s": t_train,
+                "features": scr.F, "hidden": scr.H})
+    if a.save:
+        scr.save(a.save)
+    print(json.dumps(rep))
+
+
+if __name__ == "__main__":
+    main()
