@@ -53,20 +53,27 @@ def dataset(solver: Solver, screener: Screener, topo, inj, k=64, chunk=20000):
     return X, Y, cm, n1, st
 
 
-def train(screener: Screener, X, Y, status, T, epochs=4, batch=4096, lr=1e-3, seed=0, log=None):
-    """Minibatch Adam over the rows of non-islanded topologies; returns the mean loss per epoch."""
+def train(screener: Screener, X, Y, status, T, epochs=4, batch=4096, lr=1e-3, seed=0, log=None, cosine=False):
+    """Minibatch Adam over the rows of non-islanded topologies (optionally with a
+    cosine-decayed step size); returns the mean loss per epoch."""
+    import math
+
     import torch
     ok = torch.nonzero(status.repeat_interleave(T) == 0).flatten().to(torch.int32)
     g = torch.Generator(device="cuda").manual_seed(seed)
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     hist = []
+    per_epoch = max(1, ok.numel() // batch)
+    total, step = epochs * per_epoch, 0
     for ep in range(epochs):
         perm = ok[torch.randperm(ok.numel(), device="cuda", generator=g)]
         loss.zero_()
         nb = 0
         for a in range(0, perm.numel() - batch + 1, batch):
-            screener.train_step(X, Y, perm[a:a + batch], lr, loss)
+            lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * step / total)) if cosine else lr
+            screener.train_step(X, Y, perm[a:a + batch], lr_t, loss)
             nb += 1
+            step += 1
         screener.check()
         hist.append(float(loss.item()) / max(nb, 1))
         if log:
@@ -168,6 +175,8 @@ def main():
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--top-k", type=int, default=64)
+    ap.add_argument("--eval-top-k", default="", help="further k values to evaluate, comma separated")
+    ap.add_argument("--cosine", action="store_true", help="cosine-decayed step size")
     ap.add_argument("--fallback-logit", type=float, default=float("inf"))
     ap.add_argument("--save", default=None, help="checkpoint path (.npz)")
     a = ap.parse_args()
@@ -188,13 +197,17 @@ def main():
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    hist = train(scr, Xtr, Ytr, st_tr, w.inj.shape[0], a.epochs, a.batch, a.lr, log=print)
+    hist = train(scr, Xtr, Ytr, st_tr, w.inj.shape[0], a.epochs, a.batch, a.lr, log=print, cosine=a.cosine)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del Xtr
     Xev, Yev, cm_ev, n1_ev, st_ev = dataset(solver, scr, ev_topo, w.inj, a.top_k)
     del Xev
     rep = evaluate(solver, scr, ev_topo, w.inj, Yev, cm_ev, n1_ev, st_ev, a.top_k, a.fallback_logit)
+    for k in [int(x) for x in a.eval_top_k.split(",") if x]:
+        r = evaluate(solver, scr, ev_topo, w.inj, Yev, cm_ev, n1_ev, st_ev, k, a.fallback_logit)
+        rep[f"top_k_{k}"] = {x: r[x] for x in ("recall_at_k", "recall_evaluated", "worst_cont_hit_rate",
+                                               "evaluated_fraction", "speedup", "n1_max_rel_err_mean")}
     rep.update({"train_topologies": a.train, "train_rows": a.train * w.inj.shape[0], "epochs": a.epochs,
                 "loss_per_epoch": hist, "data_s": t_data, "train_s": t_train,
                 "features": scr.F, "hidden": scr.H})
