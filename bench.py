@@ -59,7 +59,7 @@ def _peaks():
 
 def _src_hash():
     h = hashlib.sha1()
-    for f in ("n1_tma.cuh", "args.cuh"):
+    for f in ("n1_reg.cuh", "n1_tma.cuh", "args.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2501_17529_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -314,7 +314,7 @@ def run_ours(args):
                             and n_topo == 10000 else None),
                 "traffic_note": (N1_TRAFFIC[key] if key in N1_TRAFFIC and args.workload == "grid500"
                                  and n_topo == 10000 else "no capture for this kernel source and workload"),
-                "kernel": "k_n1_tma (FP32 fused N-1)",
+                "kernel": "k_n1_reg (FP32 fused N-1)",
                 "peak_note": f"1 FP32 issue slot per entry at the {peak_kind} max SM clock "
                              f"({peaks.get('sm_max_mhz', 2032.0):.0f} MHz), 148 SMs x 128 lanes",
                 "n1_ms_per_step": k["n1_ms"] / head["steps"],

@@ -1,0 +1,311 @@
+// FP32 fused N-1 kernel, register-tiled (Def. 3 / Eq. (5), agg_m of Sec. III-A).
+//
+// One block = one topology x 64 contingencies x TT timesteps.  The operand
+// tiles arrive as in k_n1_tma (a TMA ring, here 2 stages, mbarrier completion,
+// bounded waits): per 16 monitored rows Phi/limit [16][64], Z^T/limit
+// [RMAX][16], p_f^T/limit [TT][16] and the metadata rows.  Per tile:
+//   build   every thread builds RB rows of one contingency's Phi_f column
+//           (FFMA2 over row pairs) into s_ph[row pair][contingency] and the
+//           block transposes p_f into s_pt[row pair][timestep] (float2 pairs);
+//   compute thread (cg, tg) owns contingencies cg + 16 i (i < 4) and
+//           timesteps TR tg .. TR tg + TR - 1: per row pair four LDS.64 of
+//           Phi_f pairs and the p_f pairs of its timesteps feed 4 TR packed
+//           FFMA2 (two rows each) and 4 TR three-input |max| (folding both
+//           rows), i.e. one FP32 issue slot per N-1 entry;
+//   overload the (contingency, timestep) items whose tile maximum exceeds 1
+//           are queued per warp, one ballot per item class (so the lanes of
+//           a serving round read consecutive contingencies: no bank
+//           conflicts), and their 16 entries recomputed with the
+//           saturating-FMA overload term.
+#pragma once
+
+#include <cuda.h>
+
+#include "n1_tma.cuh"
+
+namespace dcf {
+
+constexpr int kRegStages = 2;  // TMA ring depth of this kernel (shared memory sets its occupancy)
+
+template <int TT>
+struct RegTile {
+  static constexpr int NTH = TT >= 24 ? 2 : 1;  // 64 NTH threads
+  static constexpr int NT = kCB * NTH;
+  static constexpr int CR = 4;                  // contingencies per thread
+  static constexpr int CG = kCB / CR;           // 16 contingency groups
+  static constexpr int TG = NT / CG;            // timestep groups
+  static constexpr int TR = TT / TG;            // timesteps per thread
+  static constexpr int RB = kLT / NTH;          // tile rows built per thread
+  static_assert(TR * TG == TT && TR >= 1, "timestep split");
+  static_assert(RB % 4 == 0, "build split");
+};
+
+template <int TT, int RMAX>
+struct RegLayout {
+  using R = RegTile<TT>;
+  static constexpr int a128(int x) { return (x + 127) / 128 * 128; }
+  static constexpr int kPhi = kLT * kCB * 4;
+  static constexpr int kZt = RMAX * kLT * 4;
+  static constexpr int kPt = TT * kLT * 4;
+  static constexpr int kMeta = 4 * kLT * 4;
+  static constexpr int kTx = kPhi + kZt + kPt + kMeta;
+  static constexpr int kOffZt = a128(kPhi);
+  static constexpr int kOffPt = kOffZt + a128(kZt);
+  static constexpr int kOffMeta = kOffPt + a128(kPt);
+  static constexpr int kStage = kOffMeta + a128(kMeta);
+  static constexpr int kTP = TT + 2;   // row pitch (float2) of the transposed p_f: spreads the banks
+  static constexpr int kSP = kCB + 1;  // row pitch (float) of the per-timestep arrays: spreads the banks
+  static constexpr int kOffPh = kRegStages * kStage;              // float2 [kLT/2][kCB]
+  static constexpr int kOffPtT = kOffPh + kLT * kCB * 4;          // float2 [kLT/2][kTP]
+  static constexpr int kOffS = kOffPtT + a128(kLT / 2 * kTP * 8); // float [TT][kSP]
+  static constexpr int kOffOv = kOffS + a128(TT * kSP * 4);       // float [TT][kSP]
+  static constexpr int kOffVt = kOffOv + a128(TT * kSP * 4);      // float [RMAX][kCB]: -Vt
+  static constexpr int kOffBar = kOffVt + a128(RMAX * kCB * 4);   // uint64 [kRegStages]
+  static constexpr int kOffOk = kOffBar + 64;                     // uint8 [kCB]
+  static constexpr int kOffQ = kOffOk + 128;                      // uint16 [warps][32 CR TR]
+  static constexpr int kBytes = kOffQ + (R::NT / 32) * 32 * R::CR * R::TR * 2;
+};
+
+template <int TT, int RMAX, bool OVL>
+__global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constant__ N1Maps maps, Args a, int t0) {
+  using L = RegLayout<TT, RMAX>;
+  using R = RegTile<TT>;
+  constexpr int CR = R::CR, TR = R::TR, RB = R::RB;
+  const int q = blockIdx.y;
+  const QInfo qi = a.qi[q];
+  if (qi.status != ST_OK) return;  // whole block: before any barrier
+  extern __shared__ __align__(128) unsigned char sm[];
+  if (smem_u32(sm) & 127u) {  // the TMA destinations need the alignment: refuse, never fault
+    if (threadIdx.x == 0) atomicExch(a.err, 2);
+    return;
+  }
+  float2* s_ph = reinterpret_cast<float2*>(sm + L::kOffPh);
+  float2* s_pt = reinterpret_cast<float2*>(sm + L::kOffPtT);
+  float* s_s = reinterpret_cast<float*>(sm + L::kOffS);
+  float* s_ov = reinterpret_cast<float*>(sm + L::kOffOv);
+  float* s_vt = reinterpret_cast<float*>(sm + L::kOffVt);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kOffBar);
+  const int tid = threadIdx.x;
+  const int M = a.M, C = a.C, T = a.T;
+  const int c0 = blockIdx.x * kCB;
+  const float* VtR = static_cast<const float*>(a.VtR) + (size_t)q * kRMax * C;
+  const float* sv = static_cast<const float*>(a.s) + (size_t)q * T * C;
+  // builder role: contingency bl, rows [bth RB, bth RB + RB)
+  const int bl = tid % kCB, bth = tid / kCB;
+  const int bc = c0 + bl;
+  const int bdrow = bc < C ? a.mpos[bc] : -1;  // monitored row of its own branch (LODF[c, c] = -1)
+  // compute role: contingencies c0 + cg + 16 i, timesteps TR tg + j
+  constexpr int TP = L::kTP, SP = L::kSP;
+  const int cg = tid % R::CG, tg = tid / R::CG;
+  for (int i = tid; i < RMAX * kCB; i += R::NT) {
+    const int j = i / kCB, c = c0 + i % kCB;
+    s_vt[i] = c < C ? -VtR[(size_t)j * C + c] : 0.f;
+  }
+  for (int i = tid; i < TT * kCB; i += R::NT) {
+    const int t = i / kCB, cl = i % kCB, c = c0 + cl;
+    s_s[t * SP + cl] = (c < C && t0 + t < T) ? sv[(size_t)(t0 + t) * C + c] : 0.f;
+    s_ov[t * SP + cl] = 0.f;  // overload partial sums, scaled by 2^-20
+  }
+  if (tid == 0) {
+    for (int st = 0; st < kRegStages; ++st) mbar_init(smem_u32(&bars[st]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  float2 s2[CR][TR];  // N-1 weights s[c, t], duplicated for the row pairs
+#pragma unroll
+  for (int i = 0; i < CR; ++i)
+#pragma unroll
+    for (int j = 0; j < TR; ++j) {
+      const float v = s_s[(tg * TR + j) * SP + cg + R::CG * i];
+      s2[i][j] = make_float2(v, v);
+    }
+  const int ntiles = (M + kLT - 1) / kLT;
+  auto issue = [&](int k) {
+    const int st = k % kRegStages;
+    unsigned char* base = sm + st * L::kStage;
+    const uint32_t bar = smem_u32(&bars[st]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, L::kTx);
+    tma_load_2d(smem_u32(base), &maps.phi, c0, k * kLT, bar);
+    tma_load_3d(smem_u32(base + L::kOffZt), &maps.zt, k * kLT, 0, q, bar);
+    tma_load_3d(smem_u32(base + L::kOffPt), &maps.pt, k * kLT, t0, q, bar);
+    tma_load_3d(smem_u32(base + L::kOffMeta), &maps.meta, k * kLT, 0, q, bar);
+  };
+  if (tid == 0)
+    for (int k = 0; k < kRegStages - 1 && k < ntiles; ++k) issue(k);
+  float mx[CR][TR];
+#pragma unroll
+  for (int i = 0; i < CR; ++i)
+#pragma unroll
+    for (int j = 0; j < TR; ++j) mx[i][j] = 0.f;
+  bool failed = false;
+  for (int k = 0; k < ntiles; ++k) {
+    const int st = k % kRegStages;
+    const bool got = mbar_wait(smem_u32(&bars[st]), (uint32_t)((k / kRegStages) & 1));
+    // one barrier: the block-uniform failure decision, and proof that every
+    // thread is done with tile k-1 (its stage is refilled next, s_ph / s_pt rebuilt)
+    if (__syncthreads_or(!got)) {
+      failed = true;
+      const int last = min(ntiles - 1, k + kRegStages - 2);
+      for (int k2 = k; k2 <= last; ++k2) mbar_wait(smem_u32(&bars[k2 % kRegStages]), (uint32_t)((k2 / kRegStages) & 1));
+      break;
+    }
+    if (tid == 0 && k + kRegStages - 1 < ntiles) issue(k + kRegStages - 1);
+    const unsigned char* base = sm + st * L::kStage;
+    const float* phi_t = reinterpret_cast<const float*>(base);
+    const float* zt_t = reinterpret_cast<const float*>(base + L::kOffZt);
+    const float* pt_t = reinterpret_cast<const float*>(base + L::kOffPt);
+    const float* meta_t = reinterpret_cast<const float*>(base + L::kOffMeta);
+    {  // build rows [bth RB, bth RB + RB) of Phi_f / limit for contingency bl
+      const int r0 = bth * RB;
+      float2 p[RB / 2];
+#pragma unroll
+      for (int i2 = 0; i2 < RB / 2; ++i2)
+        p[i2] = make_float2(phi_t[(r0 + 2 * i2) * kCB + bl], phi_t[(r0 + 2 * i2 + 1) * kCB + bl]);
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) {
+        const float v = s_vt[j * kCB + bl];
+        const float2 v2 = make_float2(v, v);
+#pragma unroll
+        for (int i4 = 0; i4 < RB / 4; ++i4) {
+          const float4 z = *reinterpret_cast<const float4*>(&zt_t[j * kLT + r0 + 4 * i4]);
+          p[2 * i4] = __ffma2_rn(make_float2(z.x, z.y), v2, p[2 * i4]);
+          p[2 * i4 + 1] = __ffma2_rn(make_float2(z.z, z.w), v2, p[2 * i4 + 1]);
+        }
+      }
+#pragma unroll
+      for (int i4 = 0; i4 < RB / 4; ++i4) {
+        const float4 rm = *reinterpret_cast<const float4*>(&meta_t[1 * kLT + r0 + 4 * i4]);
+        p[2 * i4] = __fmul2_rn(p[2 * i4], make_float2(rm.x, rm.y));
+        p[2 * i4 + 1] = __fmul2_rn(p[2 * i4 + 1], make_float2(rm.z, rm.w));
+      }
+      const int dr = bdrow - k * kLT - r0;
+      if ((unsigned)dr < (unsigned)RB) {  // LODF[c, c] = -1: Phi_f entry := -den_c / limit
+        const float dg = meta_t[r0 + dr];
+#pragma unroll
+        for (int i2 = 0; i2 < RB / 2; ++i2) {
+          if (2 * i2 == dr) p[i2].x = dg;
+          if (2 * i2 + 1 == dr) p[i2].y = dg;
+        }
+      }
+#pragma unroll
+      for (int i2 = 0; i2 < RB / 2; ++i2) s_ph[(r0 / 2 + i2) * kCB + bl] = p[i2];
+    }
+    // p_f / limit as row pairs per timestep: s_pt[rp][t] = (pt[t][2 rp], pt[t][2 rp + 1])
+    for (int i = tid; i < (kLT / 2) * TT; i += R::NT) {
+      const int rp = i % (kLT / 2), t = i / (kLT / 2);
+      s_pt[rp * TP + t] = *reinterpret_cast<const float2*>(&pt_t[t * kLT + 2 * rp]);
+    }
+    __syncthreads();
+    float mt[CR][TR];  // maxima over this tile (the overload test), folded into mx
+#pragma unroll
+    for (int rp = 0; rp < kLT / 2; ++rp) {
+      float2 ph[CR];
+#pragma unroll
+      for (int i = 0; i < CR; ++i) ph[i] = s_ph[rp * kCB + cg + R::CG * i];
+      float2 pt[TR];
+      if constexpr (TR % 2 == 0) {
+#pragma unroll
+        for (int j2 = 0; j2 < TR / 2; ++j2) {
+          const float4 u = *reinterpret_cast<const float4*>(&s_pt[rp * TP + tg * TR + 2 * j2]);
+          pt[2 * j2] = make_float2(u.x, u.y);
+          pt[2 * j2 + 1] = make_float2(u.z, u.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < TR; ++j) pt[j] = s_pt[rp * TP + tg * TR + j];
+      }
+#pragma unroll
+      for (int i = 0; i < CR; ++i)
+#pragma unroll
+        for (int j = 0; j < TR; ++j) {
+          const float2 v = __ffma2_rn(ph[i], s2[i][j], pt[j]);  // rows 2 rp and 2 rp + 1
+          if (OVL) mt[i][j] = rp == 0 ? max3abs(v.x, v.y, v.y) : max3abs(mt[i][j], v.x, v.y);
+          else mx[i][j] = max3abs(mx[i][j], v.x, v.y);
+        }
+    }
+    if (OVL) {
+#pragma unroll
+      for (int i = 0; i < CR; ++i)
+#pragma unroll
+        for (int j = 0; j < TR; ++j) mx[i][j] = fmaxf(mx[i][j], mt[i][j]);
+      // overload sum only for the (contingency, timestep) items whose tile
+      // maximum exceeds 1: the warp queues them and serves the queue with all
+      // lanes (items of one tile are distinct (t, c) pairs: no write conflicts)
+      const int lane = tid & 31;
+      const uint32_t lt = (1u << lane) - 1u;
+      uint16_t* queue = reinterpret_cast<uint16_t*>(sm + L::kOffQ) + (tid >> 5) * 32 * CR * TR;
+      int n = 0;
+#pragma unroll
+      for (int i = 0; i < CR; ++i)
+#pragma unroll
+        for (int j = 0; j < TR; ++j) {
+          const bool hit = mt[i][j] > 1.0f;
+          const uint32_t m = __ballot_sync(0xffffffffu, hit);
+          if (hit) queue[n + __popc(m & lt)] = (uint16_t)((lane << 8) | (i * TR + j));
+          n += __popc(m);
+        }
+      if (n) {
+        __syncwarp();
+        for (int jq = lane; jq < n; jq += 32) {
+          const int item = queue[jq];
+          const int src = (tid & ~31) | (item >> 8), b = item & 255;
+          const int cl = src % R::CG + R::CG * (b / TR), t = (src / R::CG) * TR + b % TR;
+          const float stv = s_s[t * SP + cl];
+          const float2 s22 = make_float2(stv, stv);
+          float2 o2 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int rp = 0; rp < kLT / 2; ++rp) {
+            const float2 v = __ffma2_rn(s_ph[rp * kCB + cl], s22, s_pt[rp * TP + t]);
+            o2 = __fadd2_rn(o2, make_float2(__saturatef(fmaf(fabsf(v.x), 0x1p-20f, -0x1p-20f)),
+                                            __saturatef(fmaf(fabsf(v.y), 0x1p-20f, -0x1p-20f))));
+          }
+          s_ov[t * SP + cl] += o2.x + o2.y;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (failed) {
+    if (tid == 0) atomicExch(a.err, 1);
+    return;
+  }
+  // per-timestep maxima to shared memory (s is held in registers), then one
+  // thread per timestep scans the 64 contingencies in order: max with the
+  // lowest contingency on ties, and the overload sum in a fixed order
+  __syncthreads();
+  uint8_t* okc = sm + L::kOffOk;
+#pragma unroll
+  for (int i = 0; i < CR; ++i)
+#pragma unroll
+    for (int j = 0; j < TR; ++j) s_s[(tg * TR + j) * SP + cg + R::CG * i] = mx[i][j];
+  if (tid < kCB) okc[tid] = (c0 + tid < C) && a.valid[(size_t)q * C + c0 + tid];
+  __syncthreads();
+  if (a.out.n1_cont_max) {  // per-contingency maxima (screener labels)
+    for (int i = tid; i < TT * kCB; i += R::NT) {
+      const int t = t0 + i / kCB, cl = i % kCB, c = c0 + cl;
+      if (t < T && c < C) a.out.n1_cont_max[((size_t)qi.tau * T + t) * C + c] = okc[cl] ? s_s[(i / kCB) * SP + cl] : -1.f;
+    }
+  }
+  for (int t = tid; t < TT; t += R::NT) {
+    if (t0 + t >= T) continue;
+    float bv = -1.f;
+    int ba = -1;
+    double o = 0.0;
+    for (int k2 = 0; k2 < kCB; ++k2) {
+      if (!okc[k2]) continue;
+      const float v = s_s[t * SP + k2];
+      if (v > bv) {
+        bv = v;
+        ba = c0 + k2;
+      }
+      o += (double)s_ov[t * SP + k2] * 1048576.0;
+    }
+    const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + blockIdx.x;
+    static_cast<float*>(a.pmax)[o2] = bv;
+    a.parg[o2] = ba;
+    a.povl[o2] = o;
+  }
+}
+
+}  // namespace dcf

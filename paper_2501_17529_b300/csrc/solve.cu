@@ -1085,6 +1085,7 @@ __global__ __launch_bounds__(64) void k_n1_sel(Args a, const Real* __restrict__ 
 
 }  // namespace dcf
 
+#include "n1_reg.cuh"
 #include "n1_tma.cuh"
 
 using namespace dcf;
@@ -1200,20 +1201,29 @@ int encode_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
 
 template <int TT, int RMAX, bool OVL = true>
 int launch_tma_t(const N1Maps& maps, const Args& a, dim3 grid, cudaStream_t st, int t0) {
-  using L = TmaLayout<TT, RMAX>;
-  constexpr int NTH = TT >= 16 ? 2 : 1;  // threads per contingency
   static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_n1_tma<TT, RMAX, NTH, OVL>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) !=
-        cudaSuccess)
-      return DCFLOW_ERR_CUDA;
-    attr = true;
+  if constexpr (TT >= 4) {  // register-tiled kernel
+    using L = RegLayout<TT, RMAX>;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k_n1_reg<TT, RMAX, OVL>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) !=
+          cudaSuccess)
+        return DCFLOW_ERR_CUDA;
+      attr = true;
+    }
+    k_n1_reg<TT, RMAX, OVL><<<grid, RegTile<TT>::NT, L::kBytes, st>>>(maps, a, t0);
+  } else {  // one timestep: one thread per contingency
+    using L = TmaLayout<TT, RMAX>;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k_n1_tma<TT, RMAX, 1, OVL>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) !=
+          cudaSuccess)
+        return DCFLOW_ERR_CUDA;
+      attr = true;
+    }
+    k_n1_tma<TT, RMAX, 1, OVL><<<grid, kCB, L::kBytes, st>>>(maps, a, t0);
   }
-  k_n1_tma<TT, RMAX, NTH, OVL><<<grid, kCB * NTH, L::kBytes, st>>>(maps, a, t0);
   return 0;
 }
 
-// max-only pass over 32 virtual timesteps (injection candidates)
 int launch_tma_screen(const N1Maps& maps, const Args& a, int RMAX, dim3 grid, cudaStream_t st, int t0) {
   if (RMAX == 4) return launch_tma_t<32, 4, false>(maps, a, grid, st, t0);
   if (RMAX == 8) return launch_tma_t<32, 8, false>(maps, a, grid, st, t0);
