@@ -40,10 +40,10 @@ WORKLOADS = {
     "grid10000": (4, 50000, "grid10000_splits1-6_T16_mon5000_cont2000"),
 }
 # dram bytes per launch of the dominant kernel from the ncu capture summarised in
-# profiles/k_n1_tma_grid500.md, keyed by the sha1 of the kernel's source and of
+# profiles/k_n1_reg_grid500.md, keyed by the sha1 of the kernel's source and of
 # its argument block at the time of the capture
 N1_TRAFFIC = {
-    ("25a28b617be9", "fp32"): {"bytes": 1.123e9, "per": "bench step of the 500-bus study (2 launches)",
+    ("6655337741aa", "fp32"): {"bytes": 1.097e9, "per": "bench step of the 500-bus study (2 launches)",
                                "how": "1,000-topology capture (626 + 374 topologies) scaled by topologies "
                                       "per rank class to 6,233 + 3,767"},
 }

@@ -320,7 +320,8 @@ typedef struct dcflow_screen_options {
 } dcflow_screen_options;
 
 typedef struct dcflow_screen_report {  /* device buffers, each optional */
-  int32_t* n_eval;   /* [n_topo] contingencies evaluated exactly */
+  int32_t* n_eval;   /* [n_topo] contingencies evaluated exactly (bridges of the base grid, which
+                        island every topology, are never evaluated) */
   uint8_t* fallback; /* [n_topo] 1 if the full N-1 ran */
   int32_t* pred;     /* [n_topo * n_time * top_k] the top_k per row, ascending; -1 padding */
 } dcflow_screen_report;

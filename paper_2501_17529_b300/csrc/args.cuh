@@ -32,6 +32,7 @@ struct Args {
   int M, C, NN, T, U;
   int Mpad, ldc;  // padded monitored count (row stride of the per-row arrays), Phi[mon, cont] row stride
   const int *monN, *contN, *cpos, *mpos;
+  const int* cont_pos;  // internal contingency index -> caller's position (outputs)
   const double *inv_lim, *PhiN, *bN;  // bN: susceptance of every needed branch
   const void* PhiMC;
   const double* p0;  // [NN][T]
@@ -50,7 +51,8 @@ struct Args {
   void* pmax;
   int* parg;
   double* povl;
-  int ncb;
+  int ncb;    // 64-contingency blocks of the N-1 kernels: ceil(C_eff / 64)
+  int C_eff;  // contingencies before the base-grid bridges (internal order)
   const int* best_u;  // chosen injection candidate per (slot, timestep), or null
   int* err;  // set to 1 by a kernel whose bounded wait expired
   // outputs

@@ -95,6 +95,13 @@ struct dcflow_ctx {
   dcf::DevBuf PhiMC;       // Real[M*ldc] Phi[mon, cont] / limit[mon], row stride ldc
   int ldc = 0;             // round_up(C, 4): 16-byte row pitch for the tensor-memory accelerator
   std::vector<uint8_t> h_split_ok;  // split-capable buses of the study
+  // Internal contingency order: the contingencies that are not bridges of the
+  // base grid first (in the caller's order), then the bridges.  A split or an
+  // outage only removes paths, so a base-grid bridge islands every topology:
+  // the N-1 kernels cover the first C_eff only.
+  int C_eff = 0;
+  std::vector<int> h_cont_pos;  // internal index -> caller's position
+  dcf::DevBuf cont_pos, cont_inv;  // int[C]: internal -> caller position, caller position -> internal
   dcf::DevBuf PhiCM;       // Real[C*Mpad] the same factors transposed (screened N-1; built on first use)
   bool phicm_ready = false;
   dcf::DevBuf Y;           // solve workspace

@@ -284,7 +284,8 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
   if (a.out.n1_cont_max) {  // per-contingency maxima (screener labels)
     for (int i = tid; i < TT * kCB; i += R::NT) {
       const int t = t0 + i / kCB, cl = i % kCB, c = c0 + cl;
-      if (t < T && c < C) a.out.n1_cont_max[((size_t)qi.tau * T + t) * C + c] = okc[cl] ? s_s[(i / kCB) * SP + cl] : -1.f;
+      if (t < T && c < C)
+        a.out.n1_cont_max[((size_t)qi.tau * T + t) * C + a.cont_pos[c]] = okc[cl] ? s_s[(i / kCB) * SP + cl] : -1.f;
     }
   }
   for (int t = tid; t < TT; t += R::NT) {

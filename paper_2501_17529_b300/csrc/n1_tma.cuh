@@ -299,7 +299,7 @@ __global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1
 #pragma unroll
     for (int tt = 0; tt < TH; ++tt) {
       const int t = t0 + th * TH + tt;
-      if (t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t) * C + c] = okv ? mx[tt] : -1.f;
+      if (t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t) * C + a.cont_pos[c]] = okv ? mx[tt] : -1.f;
     }
   }
   __syncthreads();

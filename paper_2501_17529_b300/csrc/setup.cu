@@ -284,6 +284,46 @@ extern "C" int dcflow_base_ptdf(dcflow_ctx* ctx, const int32_t* rows, int32_t n_
   return rc;
 }
 
+// Bridges of the base multigraph (iterative Tarjan low-link over edge ids, so
+// that a parallel branch is never a bridge).
+static std::vector<char> base_bridges(int V, int E, const std::vector<int>& f, const std::vector<int>& t) {
+  std::vector<std::vector<std::pair<int, int>>> adj(V);
+  for (int l = 0; l < E; ++l) {
+    adj[f[l]].push_back({t[l], l});
+    adj[t[l]].push_back({f[l], l});
+  }
+  std::vector<int> disc(V, -1), low(V, 0), pedge(V, -1), it(V, 0);
+  std::vector<char> br(E, 0);
+  int timer = 0;
+  for (int r = 0; r < V; ++r) {
+    if (disc[r] >= 0) continue;
+    std::vector<int> stack{r};
+    disc[r] = low[r] = timer++;
+    while (!stack.empty()) {
+      const int u = stack.back();
+      if (it[u] < (int)adj[u].size()) {
+        const auto [w, l] = adj[u][it[u]++];
+        if (l == pedge[u]) continue;
+        if (disc[w] < 0) {
+          pedge[w] = l;
+          disc[w] = low[w] = timer++;
+          stack.push_back(w);
+        } else {
+          low[u] = std::min(low[u], disc[w]);
+        }
+      } else {
+        stack.pop_back();
+        if (pedge[u] >= 0) {
+          const int p = f[pedge[u]] == u ? t[pedge[u]] : f[pedge[u]];
+          low[p] = std::min(low[p], low[u]);
+          if (low[u] > disc[p]) br[pedge[u]] = 1;
+        }
+      }
+    }
+  }
+  return br;
+}
+
 extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
   if (!ctx || !s || s->n_mon < 1 || s->n_cont < 0 || !s->mon || (s->n_cont > 0 && !s->cont) || !s->limit) {
     set_error("dcflow_set_study: invalid arguments");
@@ -341,7 +381,19 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
   ctx->M = s->n_mon;
   ctx->C = s->n_cont;
   ctx->h_mon.assign(s->mon, s->mon + s->n_mon);
-  ctx->h_cont.assign(s->cont, s->cont + s->n_cont);
+  {  // internal order: base-grid bridges last (they island every topology)
+    const std::vector<char> br = base_bridges(V, E, ctx->hf, ctx->ht);
+    ctx->h_cont.clear();
+    ctx->h_cont_pos.clear();
+    for (int pass = 0; pass < 2; ++pass)
+      for (int i = 0; i < s->n_cont; ++i)
+        if ((br[s->cont[i]] != 0) == (pass == 1)) {
+          ctx->h_cont.push_back(s->cont[i]);
+          ctx->h_cont_pos.push_back(i);
+        }
+    ctx->C_eff = 0;
+    for (int i = 0; i < s->n_cont; ++i) ctx->C_eff += br[s->cont[i]] == 0;
+  }
   ctx->h_N.clear();
   ctx->h_nidx.assign(E, -1);
   for (int l = 0; l < E; ++l)
@@ -374,6 +426,15 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
   if ((rc = upload(ctx->cpos_of_mon, cpos.data(), sizeof(int) * M))) return rc;
   if ((rc = upload(ctx->mpos_of_cont, mpos.data(), sizeof(int) * mpos.size()))) return rc;
   if ((rc = upload(ctx->inv_lim, inv_lim.data(), sizeof(double) * M))) return rc;
+  {
+    std::vector<int> pos(std::max(C, 1), 0), inv(std::max(C, 1), 0);
+    for (int i = 0; i < C; ++i) {
+      pos[i] = ctx->h_cont_pos[i];
+      inv[ctx->h_cont_pos[i]] = i;
+    }
+    if ((rc = upload(ctx->cont_pos, pos.data(), sizeof(int) * pos.size()))) return rc;
+    if ((rc = upload(ctx->cont_inv, inv.data(), sizeof(int) * inv.size()))) return rc;
+  }
   {
     std::vector<double> bN(NN);
     for (int i = 0; i < NN; ++i) bN[i] = ctx->hb[ctx->h_N[i]];

@@ -558,7 +558,7 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
   if (a.out.n1_cont_max && cin) {
 #pragma unroll
     for (int t = 0; t < TT; ++t)
-      if (t0 + t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t0 + t) * C + c] = ok ? (float)mx[t] : -1.f;
+      if (t0 + t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t0 + t) * C + a.cont_pos[c]] = ok ? (float)mx[t] : -1.f;
   }
   __shared__ double rv[2], ro[2];
   __shared__ int ra[2];
@@ -634,6 +634,11 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       for (size_t k = tid; k < (size_t)T * C; k += blockDim.x) o.n1_cont_max[(size_t)tau * T * C + k] = -1.f;
     return;
   }
+  if (o.n1_cont_max && !nsel)  // contingencies beyond the N-1 range: base-grid bridges, never valid
+    for (int k = tid; k < (C - a.C_eff) * T; k += blockDim.x) {
+      const int t = k / (C - a.C_eff), c = a.C_eff + k % (C - a.C_eff);
+      o.n1_cont_max[((size_t)tau * T + t) * C + a.cont_pos[c]] = -1.f;
+    }
   const Real* PhiMC = static_cast<const Real*>(a.PhiMC);
   const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
   const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
@@ -668,7 +673,7 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       const size_t k = (size_t)tau * T + t;
       o.n1_max_loading[k] = c >= 0 ? bv : 0.0;
       o.overload_sum[k] = ovl;
-      o.worst_cont[k] = c;
+      o.worst_cont[k] = c >= 0 ? a.cont_pos[c] : -1;  // the caller's position
       if (o.best_var) o.best_var[k] = a.best_u ? a.best_u[(size_t)q * T + t] : -1;
     }
     if (o.worst_mon) {
@@ -889,10 +894,10 @@ __global__ void k_select(const QInfo* __restrict__ qinfo, int nq, int T, int C, 
 // Per topology (one warp): the selected contingencies in ascending order
 // (all of them after a fallback), their count, and one work item per
 // 64 of them for the N-1 kernel.
-__global__ void k_compact(const QInfo* __restrict__ qinfo, int nq, int C, int W, const uint32_t* __restrict__ selmask,
-                          const uint8_t* __restrict__ fb, int* __restrict__ csel, int* __restrict__ nsel,
-                          int* __restrict__ work, int* __restrict__ nwork, int32_t* __restrict__ n_eval,
-                          uint8_t* __restrict__ fb_out) {
+__global__ void k_compact(const QInfo* __restrict__ qinfo, int nq, int C, int C_eff, const int* __restrict__ cont_inv,
+                          int W, const uint32_t* __restrict__ selmask, const uint8_t* __restrict__ fb,
+                          int* __restrict__ csel, int* __restrict__ nsel, int* __restrict__ work,
+                          int* __restrict__ nwork, int32_t* __restrict__ n_eval, uint8_t* __restrict__ fb_out) {
   const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (q >= nq) return;
   const QInfo qi = qinfo[q];
@@ -907,6 +912,8 @@ __global__ void k_compact(const QInfo* __restrict__ qinfo, int nq, int C, int W,
         word = full ? 0xffffffffu : selmask[(size_t)q * W + w];
         const int rem = C - 32 * w;
         if (rem < 32) word &= (1u << rem) - 1u;
+        for (uint32_t x = word; x; x &= x - 1u)  // base-grid bridges are never evaluated
+          if (cont_inv[32 * w + __ffs(x) - 1] >= C_eff) word &= ~(1u << (__ffs(x) - 1));
       }
       const int cnt = __popc(word);
       int incl = cnt;
@@ -919,7 +926,7 @@ __global__ void k_compact(const QInfo* __restrict__ qinfo, int nq, int C, int W,
       while (word) {
         const int bit = __ffs(word) - 1;
         word &= word - 1u;
-        csel[(size_t)q * C + pos++] = 32 * w + bit;
+        csel[(size_t)q * C + pos++] = cont_inv[32 * w + bit];  // ascending: the order keeps the caller's
       }
       base += __shfl_sync(0xffffffffu, incl, 31);
     }
@@ -1040,7 +1047,7 @@ __global__ __launch_bounds__(64) void k_n1_sel(Args a, const Real* __restrict__ 
     if (a.out.n1_cont_max && cin) {
 #pragma unroll
       for (int t = 0; t < TT; ++t)
-        if (t0 + t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t0 + t) * C + c] = ok ? (float)mx[t] : -1.f;
+        if (t0 + t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t0 + t) * C + a.cont_pos[c]] = ok ? (float)mx[t] : -1.f;
     }
     const int lane = tid & 31, w = tid >> 5;
 #pragma unroll
@@ -1449,7 +1456,8 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   // large chunks keep the N-1 launches wide (measured better than many small
   // overlapping chunks: the N-1 kernel fills the SMs' registers and shared
   // memory, so preparation kernels of the next chunk only run in its tail)
-  const int ncb = (C + 63) / 64;
+  const int C_eff = ctx->C_eff;       // contingencies that can be valid (base-grid bridges excluded)
+  const int ncb = (C_eff + 63) / 64;  // 64-contingency blocks of the N-1 kernels
   const int Mp = (int)round_up(M, 16);
   const int TV = T * U;  // virtual timesteps: (timestep, candidate) pairs
   if (R > 64) {
@@ -1530,6 +1538,8 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   base.p0 = ctx->p0.as<double>();
   base.tol = ctx->opt.island_tol;
   base.ncb = ncb;
+  base.C_eff = C_eff;
+  base.cont_pos = ctx->cont_pos.as<int>();
   base.Mpad = Mp;
   base.ldc = ctx->ldc;
   base.err = ctx->err.as<int>();
@@ -1667,7 +1677,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       av.pmax = B.pmaxv.p;
       av.parg = B.pargv.as<int>();
       av.povl = B.povlv.as<double>();
-      if (C > 0) {
+      if (C_eff > 0) {
         int rc = run_n1(av, RMAX, TV, false);
         if (rc) return rc;
       } else {
@@ -1729,7 +1739,8 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       launch_select(a, T, C, scr->iZ.as<float>(), Cp, sc->top_k, host_float_key(sc->fallback_logit), SB, W,
                     rep ? rep->pred : nullptr, st);
       DCF_CHECK_LAUNCH();
-      k_compact<<<(ch.nq * 32 + 255) / 256, 256, 0, st>>>(a.qi, ch.nq, C, W, SB.selmask.as<uint32_t>(),
+      k_compact<<<(ch.nq * 32 + 255) / 256, 256, 0, st>>>(a.qi, ch.nq, C, C_eff, ctx->cont_inv.as<int>(), W,
+                                                         SB.selmask.as<uint32_t>(),
                                                          SB.sfb.as<uint8_t>(), SB.csel.as<int>(), SB.nsel.as<int>(),
                                                          SB.work.as<int>(), SB.nwork.as<int>(),
                                                          rep ? rep->n_eval : nullptr, rep ? rep->fallback : nullptr);
@@ -1758,7 +1769,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
         if (e1) DCF_CUDA(cudaEventRecord(e1, st));
       }
       nsel_dev = SB.nsel.as<int>();
-    } else if (C > 0) {
+    } else if (C_eff > 0) {
       int rc = run_n1(af, RMAX, T, true);
       if (rc) return rc;
     }
