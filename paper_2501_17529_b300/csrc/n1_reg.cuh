@@ -17,6 +17,11 @@
 //           a serving round read consecutive contingencies: no bank
 //           conflicts), and their 16 entries recomputed with the
 //           saturating-FMA overload term.
+// SEL (learned screener): a block is one work item (topology, 64 of its
+// selected contingencies) and its Phi tile is gathered from the transposed
+// factors [cont][Mpad]: each contingency's 16 rows are one 64-byte run,
+// copied with cp.async into a contingency-major tile (pitch 20 floats: the
+// builders' reads spread over all banks); the other operands arrive by TMA.
 #pragma once
 
 #include <cuda.h>
@@ -40,15 +45,25 @@ struct RegTile {
   static_assert(RB % 4 == 0, "build split");
 };
 
-template <int TT, int RMAX>
+// Selected-contingency mode: where the gathered Phi tile comes from.
+struct SelArgs {
+  const float* phicm;  // [C][mp] Phi[mon, cont] / limit transposed, zero rows mp > M
+  int mp;
+  const int* csel;     // [nq][C] selected internal contingencies, ascending
+  const int* nsel;     // [nq]
+  const int* work;     // [items] (topology << 6) | 64-contingency block
+};
+constexpr int kPP = 20;  // pitch (floats) of a gathered Phi column: 16 rows + bank spread
+
+template <int TT, int RMAX, bool SEL = false>
 struct RegLayout {
   using R = RegTile<TT>;
   static constexpr int a128(int x) { return (x + 127) / 128 * 128; }
-  static constexpr int kPhi = kLT * kCB * 4;
+  static constexpr int kPhi = SEL ? kCB * kPP * 4 : kLT * kCB * 4;
   static constexpr int kZt = RMAX * kLT * 4;
   static constexpr int kPt = TT * kLT * 4;
   static constexpr int kMeta = 4 * kLT * 4;
-  static constexpr int kTx = kPhi + kZt + kPt + kMeta;
+  static constexpr int kTx = (SEL ? 0 : kPhi) + kZt + kPt + kMeta;  // bytes landing by TMA
   static constexpr int kOffZt = a128(kPhi);
   static constexpr int kOffPt = kOffZt + a128(kZt);
   static constexpr int kOffMeta = kOffPt + a128(kPt);
@@ -62,16 +77,26 @@ struct RegLayout {
   static constexpr int kOffVt = kOffOv + a128(TT * kSP * 4);      // float [RMAX][kCB]: -Vt
   static constexpr int kOffBar = kOffVt + a128(RMAX * kCB * 4);   // uint64 [kRegStages]
   static constexpr int kOffOk = kOffBar + 64;                     // uint8 [kCB]
-  static constexpr int kOffQ = kOffOk + 128;                      // uint16 [warps][32 CR TR]
+  static constexpr int kOffCi = kOffOk + 128;                     // int [kCB]: contingency of each column
+  static constexpr int kOffQ = kOffCi + kCB * 4;                  // uint16 [warps][32 CR TR]
   static constexpr int kBytes = kOffQ + (R::NT / 32) * 32 * R::CR * R::TR * 2;
 };
 
-template <int TT, int RMAX, bool OVL>
-__global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constant__ N1Maps maps, Args a, int t0) {
-  using L = RegLayout<TT, RMAX>;
+template <int TT, int RMAX, bool OVL, bool SEL = false>
+__global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constant__ N1Maps maps, Args a, int t0,
+                                                            const SelArgs sel) {
+  using L = RegLayout<TT, RMAX, SEL>;
   using R = RegTile<TT>;
   constexpr int CR = R::CR, TR = R::TR, RB = R::RB;
-  const int q = blockIdx.y;
+  int q, cb;  // topology slot and 64-contingency block
+  if constexpr (SEL) {
+    const int item = sel.work[blockIdx.x];
+    q = item >> 6;
+    cb = item & 63;
+  } else {
+    q = blockIdx.y;
+    cb = blockIdx.x;
+  }
   const QInfo qi = a.qi[q];
   if (qi.status != ST_OK) return;  // whole block: before any barrier
   extern __shared__ __align__(128) unsigned char sm[];
@@ -87,23 +112,31 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kOffBar);
   const int tid = threadIdx.x;
   const int M = a.M, C = a.C, T = a.T;
-  const int c0 = blockIdx.x * kCB;
+  const int c0 = cb * kCB;  // first column: a contingency, or a position in the selected list
+  int* s_ci = reinterpret_cast<int*>(sm + L::kOffCi);
+  if constexpr (SEL) {
+    const int ns = sel.nsel[q];
+    for (int i = tid; i < kCB; i += R::NT) s_ci[i] = c0 + i < ns ? sel.csel[(size_t)q * C + c0 + i] : -1;
+  } else {
+    for (int i = tid; i < kCB; i += R::NT) s_ci[i] = c0 + i < C ? c0 + i : -1;
+  }
+  __syncthreads();
   const float* VtR = static_cast<const float*>(a.VtR) + (size_t)q * kRMax * C;
   const float* sv = static_cast<const float*>(a.s) + (size_t)q * T * C;
   // builder role: contingency bl, rows [bth RB, bth RB + RB)
   const int bl = tid % kCB, bth = tid / kCB;
-  const int bc = c0 + bl;
-  const int bdrow = bc < C ? a.mpos[bc] : -1;  // monitored row of its own branch (LODF[c, c] = -1)
+  const int bc = s_ci[bl];
+  const int bdrow = bc >= 0 ? a.mpos[bc] : -1;  // monitored row of its own branch (LODF[c, c] = -1)
   // compute role: contingencies c0 + cg + 16 i, timesteps TR tg + j
   constexpr int TP = L::kTP, SP = L::kSP;
   const int cg = tid % R::CG, tg = tid / R::CG;
   for (int i = tid; i < RMAX * kCB; i += R::NT) {
-    const int j = i / kCB, c = c0 + i % kCB;
-    s_vt[i] = c < C ? -VtR[(size_t)j * C + c] : 0.f;
+    const int j = i / kCB, c = s_ci[i % kCB];
+    s_vt[i] = c >= 0 ? -VtR[(size_t)j * C + c] : 0.f;
   }
   for (int i = tid; i < TT * kCB; i += R::NT) {
-    const int t = i / kCB, cl = i % kCB, c = c0 + cl;
-    s_s[t * SP + cl] = (c < C && t0 + t < T) ? sv[(size_t)(t0 + t) * C + c] : 0.f;
+    const int t = i / kCB, cl = i % kCB, c = s_ci[cl];
+    s_s[t * SP + cl] = (c >= 0 && t0 + t < T) ? sv[(size_t)(t0 + t) * C + c] : 0.f;
     s_ov[t * SP + cl] = 0.f;  // overload partial sums, scaled by 2^-20
   }
   if (tid == 0) {
@@ -126,13 +159,35 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
     const uint32_t bar = smem_u32(&bars[st]);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, L::kTx);
-    tma_load_2d(smem_u32(base), &maps.phi, c0, k * kLT, bar);
+    if constexpr (!SEL) tma_load_2d(smem_u32(base), &maps.phi, c0, k * kLT, bar);
     tma_load_3d(smem_u32(base + L::kOffZt), &maps.zt, k * kLT, 0, q, bar);
     tma_load_3d(smem_u32(base + L::kOffPt), &maps.pt, k * kLT, t0, q, bar);
     tma_load_3d(smem_u32(base + L::kOffMeta), &maps.meta, k * kLT, 0, q, bar);
   };
-  if (tid == 0)
-    for (int k = 0; k < kRegStages - 1 && k < ntiles; ++k) issue(k);
+  // SEL: every builder of rows 0.. copies its contingency's 16 rows of tile k
+  // (one cp.async group per thread and tile, possibly empty)
+  auto issue_phi = [&](int k) {
+    if constexpr (SEL) {
+      float* dst = reinterpret_cast<float*>(sm + (k % kRegStages) * L::kStage) + bl * kPP;
+      if (bth == 0) {
+        if (bc >= 0) {
+          const float* src = sel.phicm + (size_t)bc * sel.mp + (size_t)k * kLT;
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + 4 * i)), "l"(src + 4 * i)
+                         : "memory");
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) *reinterpret_cast<float4*>(dst + 4 * i) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+  };
+  for (int k = 0; k < kRegStages - 1 && k < ntiles; ++k) {
+    if (tid == 0) issue(k);
+    issue_phi(k);
+  }
   float mx[CR][TR];
 #pragma unroll
   for (int i = 0; i < CR; ++i)
@@ -141,6 +196,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
   bool failed = false;
   for (int k = 0; k < ntiles; ++k) {
     const int st = k % kRegStages;
+    if constexpr (SEL) asm volatile("cp.async.wait_group 0;" ::: "memory");  // this thread's copies of tile k
     const bool got = mbar_wait(smem_u32(&bars[st]), (uint32_t)((k / kRegStages) & 1));
     // one barrier: the block-uniform failure decision, and proof that every
     // thread is done with tile k-1 (its stage is refilled next, s_ph / s_pt rebuilt)
@@ -150,7 +206,10 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
       for (int k2 = k; k2 <= last; ++k2) mbar_wait(smem_u32(&bars[k2 % kRegStages]), (uint32_t)((k2 / kRegStages) & 1));
       break;
     }
-    if (tid == 0 && k + kRegStages - 1 < ntiles) issue(k + kRegStages - 1);
+    if (k + kRegStages - 1 < ntiles) {
+      if (tid == 0) issue(k + kRegStages - 1);
+      issue_phi(k + kRegStages - 1);
+    }
     const unsigned char* base = sm + st * L::kStage;
     const float* phi_t = reinterpret_cast<const float*>(base);
     const float* zt_t = reinterpret_cast<const float*>(base + L::kOffZt);
@@ -160,8 +219,10 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
       const int r0 = bth * RB;
       float2 p[RB / 2];
 #pragma unroll
-      for (int i2 = 0; i2 < RB / 2; ++i2)
-        p[i2] = make_float2(phi_t[(r0 + 2 * i2) * kCB + bl], phi_t[(r0 + 2 * i2 + 1) * kCB + bl]);
+      for (int i2 = 0; i2 < RB / 2; ++i2) {
+        if constexpr (SEL) p[i2] = *reinterpret_cast<const float2*>(&phi_t[bl * kPP + r0 + 2 * i2]);
+        else p[i2] = make_float2(phi_t[(r0 + 2 * i2) * kCB + bl], phi_t[(r0 + 2 * i2 + 1) * kCB + bl]);
+      }
 #pragma unroll
       for (int j = 0; j < RMAX; ++j) {
         const float v = s_vt[j * kCB + bl];
@@ -267,6 +328,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
     }
   }
   if (failed) {
+    if constexpr (SEL) asm volatile("cp.async.wait_all;" ::: "memory");
     if (tid == 0) atomicExch(a.err, 1);
     return;
   }
@@ -279,12 +341,12 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
   for (int i = 0; i < CR; ++i)
 #pragma unroll
     for (int j = 0; j < TR; ++j) s_s[(tg * TR + j) * SP + cg + R::CG * i] = mx[i][j];
-  if (tid < kCB) okc[tid] = (c0 + tid < C) && a.valid[(size_t)q * C + c0 + tid];
+  if (tid < kCB) okc[tid] = (s_ci[tid] >= 0) && a.valid[(size_t)q * C + s_ci[tid]];
   __syncthreads();
   if (a.out.n1_cont_max) {  // per-contingency maxima (screener labels)
     for (int i = tid; i < TT * kCB; i += R::NT) {
-      const int t = t0 + i / kCB, cl = i % kCB, c = c0 + cl;
-      if (t < T && c < C)
+      const int t = t0 + i / kCB, cl = i % kCB, c = s_ci[cl];
+      if (t < T && c >= 0)
         a.out.n1_cont_max[((size_t)qi.tau * T + t) * C + a.cont_pos[c]] = okc[cl] ? s_s[(i / kCB) * SP + cl] : -1.f;
     }
   }
@@ -298,11 +360,11 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
       const float v = s_s[t * SP + k2];
       if (v > bv) {
         bv = v;
-        ba = c0 + k2;
+        ba = s_ci[k2];
       }
       o += (double)s_ov[t * SP + k2] * 1048576.0;
     }
-    const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + blockIdx.x;
+    const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + cb;
     static_cast<float*>(a.pmax)[o2] = bv;
     a.parg[o2] = ba;
     a.povl[o2] = o;

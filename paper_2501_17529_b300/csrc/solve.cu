@@ -1217,7 +1217,7 @@ int launch_tma_t(const N1Maps& maps, const Args& a, dim3 grid, cudaStream_t st, 
         return DCFLOW_ERR_CUDA;
       attr = true;
     }
-    k_n1_reg<TT, RMAX, OVL><<<grid, RegTile<TT>::NT, L::kBytes, st>>>(maps, a, t0);
+    k_n1_reg<TT, RMAX, OVL><<<grid, RegTile<TT>::NT, L::kBytes, st>>>(maps, a, t0, SelArgs{});
   } else {  // one timestep: one thread per contingency
     using L = TmaLayout<TT, RMAX>;
     if (!attr) {
@@ -1247,6 +1247,38 @@ int launch_tma_r(const N1Maps& maps, const Args& a, int TT, dim3 grid, cudaStrea
     case 24: return launch_tma_t<24, RMAX>(maps, a, grid, st, t0);
     default: return launch_tma_t<32, RMAX>(maps, a, grid, st, t0);
   }
+}
+
+// selected-contingency mode (screened N-1), FP32, TT >= 4
+template <int TT, int RMAX>
+int launch_reg_sel_t(const N1Maps& maps, const Args& a, const SelArgs& sel, int items, cudaStream_t st, int t0) {
+  using L = RegLayout<TT, RMAX, true>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_n1_reg<TT, RMAX, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) !=
+        cudaSuccess)
+      return DCFLOW_ERR_CUDA;
+    attr = true;
+  }
+  k_n1_reg<TT, RMAX, true, true><<<items, RegTile<TT>::NT, L::kBytes, st>>>(maps, a, t0, sel);
+  return 0;
+}
+template <int RMAX>
+int launch_reg_sel_r(const N1Maps& maps, const Args& a, const SelArgs& sel, int TT, int items, cudaStream_t st,
+                     int t0) {
+  switch (TT) {
+    case 4: return launch_reg_sel_t<4, RMAX>(maps, a, sel, items, st, t0);
+    case 8: return launch_reg_sel_t<8, RMAX>(maps, a, sel, items, st, t0);
+    case 16: return launch_reg_sel_t<16, RMAX>(maps, a, sel, items, st, t0);
+    case 24: return launch_reg_sel_t<24, RMAX>(maps, a, sel, items, st, t0);
+    default: return launch_reg_sel_t<32, RMAX>(maps, a, sel, items, st, t0);
+  }
+}
+int launch_reg_sel(const N1Maps& maps, const Args& a, const SelArgs& sel, int RMAX, int TT, int items,
+                   cudaStream_t st, int t0) {
+  if (RMAX == 4) return launch_reg_sel_r<4>(maps, a, sel, TT, items, st, t0);
+  if (RMAX == 8) return launch_reg_sel_r<8>(maps, a, sel, TT, items, st, t0);
+  return launch_reg_sel_r<16>(maps, a, sel, TT, items, st, t0);
 }
 
 int launch_tma(const N1Maps& maps, const Args& a, int RMAX, int TT, dim3 grid, cudaStream_t st, int t0) {
@@ -1573,10 +1605,8 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   const size_t dyn = (size_t)kRMax * Text * rs;
   // N-1 passes over Tn (virtual) timesteps whose operands are a.ptil / a.s;
   // ovl = false screens the maximum only (FP32 form)
-  auto run_n1 = [&](const Args& a, int RMAX, int Tn, bool ovl) -> int {
-    const int TTn = ovl ? pick_tt(Tn, fp64) : (fp64 ? 8 : 32);
-    N1Maps maps;
-    if (!fp64) {
+  auto encode_maps = [&](const Args& a, int RMAX, int Tn, int TTn, N1Maps& maps) -> int {
+    {
       const uint64_t d_phi[2] = {(uint64_t)C, (uint64_t)M}, s_phi[1] = {(uint64_t)ctx->ldc * 4};
       const uint32_t b_phi[2] = {kCB, kLT};
       const uint64_t d_me[3] = {(uint64_t)M, 4, (uint64_t)cap};
@@ -1592,6 +1622,14 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       if (!rc) rc = encode_map(&maps.meta, a.diagv, 3, d_me, s_me, b_me);
       if (!rc) rc = encode_map(&maps.zt, a.Zs, 3, d_zt, s_zt, b_zt);
       if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt);
+      return rc;
+    }
+  };
+  auto run_n1 = [&](const Args& a, int RMAX, int Tn, bool ovl) -> int {
+    const int TTn = ovl ? pick_tt(Tn, fp64) : (fp64 ? 8 : 32);
+    N1Maps maps;
+    if (!fp64) {
+      int rc = encode_maps(a, RMAX, Tn, TTn, maps);
       if (rc) return rc;
     }
     for (int t0 = 0; t0 < Tn; t0 += TTn) {
@@ -1748,6 +1786,15 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       ctx->launches += 6;
       const int TTs = pick_tt(T, fp64);
       const int sgrid = (int)std::min<int64_t>((int64_t)ch.nq * ncb, 148 * 16);
+      const bool reg_sel = !fp64 && TTs >= 4;  // FP32: the register-tiled kernel over the work items
+      int items = 0;
+      N1Maps smaps;
+      if (reg_sel) {
+        DCF_CUDA(cudaMemcpyAsync(&items, SB.nwork.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DCF_CUDA(cudaStreamSynchronize(st));
+        if ((rc = encode_maps(af, RMAX, T, TTs, smaps))) return rc;
+      }
+      const SelArgs sargs{ctx->PhiCM.as<float>(), Mp, SB.csel.as<int>(), SB.nsel.as<int>(), SB.work.as<int>()};
       for (int t0 = 0; t0 < T; t0 += TTs) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (ctx->prof_on) {
@@ -1761,8 +1808,9 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
           ctx->prof_used += 2;
           DCF_CUDA(cudaEventRecord(e0, st));
         }
-        rc = fp64 ? launch_sel<double>(af, ctx->PhiCM.p, SB, RMAX, TTs, sgrid, st, t0)
-                  : launch_sel<float>(af, ctx->PhiCM.p, SB, RMAX, TTs, sgrid, st, t0);
+        if (reg_sel) rc = items ? launch_reg_sel(smaps, af, sargs, RMAX, TTs, items, st, t0) : 0;
+        else rc = fp64 ? launch_sel<double>(af, ctx->PhiCM.p, SB, RMAX, TTs, sgrid, st, t0)
+                       : launch_sel<float>(af, ctx->PhiCM.p, SB, RMAX, TTs, sgrid, st, t0);
         if (rc) return rc;
         ++ctx->launches;
         DCF_CHECK_LAUNCH();
