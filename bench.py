@@ -118,6 +118,28 @@ def _dist():
     return ws, rank, local
 
 
+def rank_topologies(w, shape, n_topo, rank):
+    """Weak scaling: rank 0 keeps the workload's batch, every other rank draws
+    its own batch of the same shape (independent topologies, no exchange)."""
+    from paper_2501_17529_b300 import synth
+    if rank == 0:
+        return w.topo
+    spec = {2: ((1, 4), (0, 3)), 3: (synth.geometric_count(0.5, 1, 8), synth.geometric_count(0.5, 0, 4)),
+            4: ((1, 6), (0, 0))}[shape]
+    return synth.make_topologies(w.grid, w.subs, n_topo, 1000 * rank + 200 + shape, *spec)
+
+
+def reduce_over_ranks(t_dev, lf, device):
+    """Whole-job timing: the slowest rank's device time and the loadflows of all ranks."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_dev], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    lft = torch.tensor([lf], device=device, dtype=torch.float64)
+    dist.all_reduce(lft)
+    return float(tt.item()), float(lft.item())
+
+
 def _loadflows(topo, status, n_island_cont, cont, T):
     """N-1 cases solved: valid contingencies of non-islanded topologies x T."""
     cset = set(int(c) for c in cont)
@@ -141,7 +163,9 @@ def _cpu_worker(args):
     r = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, var=w.var, idx=idx)
     dt = time.perf_counter() - t0
     nv = 0 if w.var is None else w.var.n_var
-    return oracle.loadflow_count(r, w.inj.shape[0], nv), dt
+    keep = {k: r[k] for k in ("n0_max", "n1_max", "ovl", "worst_cont", "status", "n_island_cont")}
+    keep["idx"] = np.asarray(idx, np.int64)
+    return oracle.loadflow_count(r, w.inj.shape[0], nv), dt, keep
 
 
 def cpu_baseline(workload: str, budget_s: float = 20.0):
@@ -155,7 +179,7 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
         probe = pool.map(_cpu_worker, [(shape, [i]) for i in range(cores)])
-        per_topo = max(1e-3, statistics.median(dt for _, dt in probe))
+        per_topo = max(1e-3, statistics.median(dt for _, dt, _ in probe))
         n_each = max(1, int(budget_s / per_topo))
         n_each = min(n_each, max(1, (n_all - cores) // cores))
         chunks = [(shape, list(range(cores + k * n_each, cores + (k + 1) * n_each))) for k in range(cores)]
@@ -164,9 +188,27 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
         wall = time.perf_counter() - t0
     lf = sum(r[0] for r in res)
     ntop = n_each * cores
+    ref = {k: np.concatenate([r[2][k] for r in probe + res]) for k in probe[0][2]}
     return {"value": lf / wall, "unit": "loadflows/s", "cores": cores, "kind": "oracle",
             "sample": f"{ntop} of the {n_all} topologies of {workload} (all timesteps, candidates and contingencies), "
-                      f"{cores} spawn workers, 1 BLAS thread each, {wall:.1f} s wall"}
+                      f"{cores} spawn workers, 1 BLAS thread each, {wall:.1f} s wall"}, ref
+
+
+def _errors(host, ref):
+    """Errors of one form against the oracle on the oracle's topology sample
+    (loadings |x - x_ref| / max(x_ref, 1), overload sums likewise; integer
+    outputs as the fraction that agrees exactly)."""
+    idx = ref["idx"]
+    st = host["status"][idx]
+    ok = ref["status"] == 0
+    out = {"topologies": int(idx.size), "status_agree": float(np.mean(st == ref["status"])),
+           "n_island_cont_agree": float(np.mean(host["n_island_cont"][idx][ok] == ref["n_island_cont"][ok]))
+           if ok.any() else 1.0}
+    for key, name in (("n0_max", "n0_max_loading"), ("n1_max", "n1_max_loading"), ("ovl", "overload_sum")):
+        g, r = host[key][idx][ok], ref[key][ok]
+        out[f"max_err_{name}"] = float((np.abs(g - r) / np.maximum(np.abs(r), 1.0)).max()) if ok.any() else 0.0
+    out["worst_cont_agree"] = float(np.mean(host["worst_cont"][idx][ok] == ref["worst_cont"][ok])) if ok.any() else 1.0
+    return out
 
 
 def run_reference(args):
@@ -223,8 +265,7 @@ def run_ours(args):
     shape, n_default, desc = WORKLOADS[args.workload]
     n_topo = args.topologies or n_default
     w = synth.workload(shape, n_topo=n_topo)
-    if ws > 1 and rank > 0:  # each rank its own batch of the same shape
-        w.topo = synth.make_topologies(w.grid, w.subs, n_topo, 1000 * rank + 200 + shape, (1, 4), (0, 3))
+    w.topo = rank_topologies(w, shape, n_topo, rank)
     # limits from the unsplit grid's N-0 flows on the monitored branches, computed on the device
     base = Solver(w.grid, precision="fp64")
     pt = base.base_ptdf(w.mon).cpu().numpy()
@@ -234,7 +275,7 @@ def run_ours(args):
     n_mon = len(w.mon)
     T_STEPS = w.inj.shape[0]
 
-    results = {}
+    results, hosts = {}, {}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
     peaks, peak_kind = _peaks()
     for form in (args.forms.split(",")):
@@ -252,6 +293,7 @@ def run_ours(args):
             solver.solve(db, results=res)
         torch.cuda.synchronize()
         host = res.to_host()
+        hosts[form] = host
         lf = _loadflows(w.topo, host["status"], host["n_island_cont"], w.cont, T_STEPS) * max(1, db.n_var)
         lib = __import__("paper_2501_17529_b300.dcflow", fromlist=["x"])
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -275,12 +317,7 @@ def run_ours(args):
         kern = lib.dcflow_profile_read(solver.ctx)
         lib.dcflow_profile(solver.ctx, False)
         if ws > 1:
-            tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_dev = float(tt.item())
-            lft = torch.tensor([lf], device="cuda", dtype=torch.float64)
-            dist.all_reduce(lft)
-            lf_all = float(lft.item())
+            t_dev, lf_all = reduce_over_ranks(t_dev, lf, "cuda")
         else:
             lf_all = lf
         results[form] = {"value": lf_all * steps / t_dev, "ms_per_step": 1e3 * t_dev / steps,
@@ -336,7 +373,9 @@ def run_ours(args):
     if roof:
         line["roofline"] = roof
     if ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_budget)
+        line["cpu_baseline"], ref = cpu_baseline(args.workload, args.cpu_budget)
+        if n_topo == WORKLOADS[args.workload][1]:  # the oracle's sample is of this very batch
+            line["error_vs_oracle"] = {f: _errors(h, ref) for f, h in hosts.items()}
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
