@@ -2,13 +2,17 @@
 // in tensor memory: D[M x N] = A[M x K] * B[N x K]^T (+ bias[N], optional ReLU),
 // both operands K-major bf16, D row-major in FP32 or BF16.
 //
-// One CTA per 128 x 128 output tile, 128 threads.  Thread 0 drives a 4-stage
-// ring: TMA loads 128 x 64 bf16 boxes of A and B with 128-byte swizzle into
-// shared memory (completion on a "full" mbarrier), issues four
-// tcgen05.mma.kind::f16 (K = 16 each) per stage into a 128 x 128 FP32
-// accumulator in tensor memory, and tcgen05.commit frees the stage on an
-// "empty" mbarrier.  After the last stage a commit signals the epilogue: each
-// warp reads its 32 accumulator lanes (rows) with tcgen05.ld.32x32b.
+// One CTA per 128 x 128 output tile, 128 threads, a 6-stage shared-memory
+// ring with two single-thread roles: warp 0 lane 0 is the TMA producer (waits
+// for a stage to be free on its "empty" mbarrier, then loads 128 x 64 bf16
+// boxes of A and B with 128-byte swizzle, completion on the stage's "full"
+// mbarrier); warp 1 lane 0 issues the MMAs (waits for "full", four
+// tcgen05.mma.kind::f16 with K = 16 into a 128 x 128 FP32 accumulator in
+// tensor memory, then tcgen05.commit frees the stage on "empty").  Neither
+// role waits for the other's latest step, so loads run STAGES - 1 k-tiles
+// ahead of the tensor pipe.  After the last k-tile a commit signals the
+// epilogue: each warp reads its 32 accumulator lanes (rows) with
+// tcgen05.ld.32x32b.
 // Epilogue options: bias[N], ReLU, a ReLU-derivative mask (D := 0 where a
 // bf16 tensor of D's shape is <= 0), FP32 or BF16 output, an optional second
 // BF16 store of D transposed, and split-K: gridDim.z CTAs share the K range of
@@ -25,7 +29,7 @@
 namespace dcf {
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
 constexpr int kTileBytes = BM * BK * 2;          // 16 KB per operand tile
 constexpr int kStageBytes = 2 * kTileBytes;      // A + B
 constexpr int kSmemBytes = 1024 /*align*/ + STAGES * kStageBytes + 256 /*barriers, tmem slot*/;
@@ -133,50 +137,53 @@ __global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUten
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   uint32_t tmem;
   asm volatile("ld.shared.b32 %0, [%1];" : "=r"(tmem) : "r"(tslot) : "memory");
-  __shared__ int failed;
-  if (tid == 0) failed = 0;
-  __syncthreads();
+  __shared__ int failed;    // a role gave up on a bounded wait
+  __shared__ int consumed;  // k-tiles whose MMAs were issued
+  __shared__ int issued;    // k-tiles whose loads were issued
   if (tid == 0) {
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
-    auto load = [&](int kt) {
+    failed = 0;
+    consumed = 0;
+    issued = 0;
+  }
+  __syncthreads();
+  volatile int* vfailed = &failed;
+  volatile int* vconsumed = &consumed;
+  if (tid == 0) {  // TMA producer
+    int kt = 0;
+    for (; kt < KT; ++kt) {
       const int s = kt % STAGES;
+      if (kt >= STAGES && !bar_wait(empty(s), (uint32_t)((kt / STAGES - 1) & 1))) {
+        *vfailed = 1;
+        break;
+      }
+      if (*vfailed) break;
       const uint32_t a = base + s * kStageBytes, b = a + kTileBytes;
       bar_expect(full(s), kStageBytes);
       tma2d(a, &mA, (kt0 + kt) * BK, m0, full(s));
       tma2d(b, &mB, (kt0 + kt) * BK, n0, full(s));
-    };
-    int issued = 0, landed = 0;  // loads issued / loads whose arrival was observed
-    for (int kt = 0; kt < KT && kt < STAGES; ++kt, ++issued) load(kt);
-    bool ok = true;
-    for (int kt = 0; kt < KT && ok; ++kt) {
+      issued = kt + 1;
+    }
+  } else if (tid == 32) {  // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    for (int kt = 0; kt < KT; ++kt) {
       const int s = kt % STAGES;
-      if (!bar_wait(full(s), (uint32_t)((kt / STAGES) & 1))) {
-        ok = false;
+      if (*vfailed || !bar_wait(full(s), (uint32_t)((kt / STAGES) & 1))) {
+        *vfailed = 1;
         break;
       }
-      ++landed;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a = base + s * kStageBytes, b = a + kTileBytes;
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk)  // 16 bf16 = 32 bytes per K step inside the swizzle atom
         mma_bf16(tmem, sw128_desc(a + 32 * kk), sw128_desc(b + 32 * kk), idesc, (kt | kk) != 0);
       mma_commit(empty(s));
-      if (kt + STAGES < KT) {
-        if (!bar_wait(empty(s), (uint32_t)((kt / STAGES) & 1))) {
-          ok = false;
-          break;
-        }
-        load(kt + STAGES);
-        ++issued;
-      }
+      *vconsumed = kt + 1;
     }
     mma_commit(done);
-    if (!ok) {
-      failed = 1;
-      for (int k = landed; k < issued; ++k) bar_wait(full(k % STAGES), (uint32_t)((k / STAGES) & 1));  // bounded drain
-    }
   }
   __syncthreads();
+  if (failed && tid == 0)  // loads issued but never consumed: bounded waits on phases not yet waited for
+    for (int k = consumed; k < issued; ++k) bar_wait(full(k % STAGES), (uint32_t)((k / STAGES) & 1));
   const bool fin = bar_wait(done, 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (failed || !fin) {
