@@ -25,8 +25,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-// 2-D bf16 K-major operand [rows x K] (row pitch ld elements) as 64 x 128 boxes with 128-byte swizzle.
-static int bf16_operand_map(CUtensorMap* m, const void* base, int rows, int K, int ld) {
+// 2-D bf16 K-major operand [rows x K] (row pitch ld elements) as 64 x box_rows boxes with 128-byte swizzle.
+static int bf16_operand_map(CUtensorMap* m, const void* base, int rows, int K, int ld, int box_rows) {
   auto fn = encoder();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -38,7 +38,7 @@ static int bf16_operand_map(CUtensorMap* m, const void* base, int rows, int K, i
   }
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {tc::BK, tc::BM};
+  cuuint32_t box[2] = {tc::BK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -61,7 +61,7 @@ __global__ void k_splitk_reduce(const float* __restrict__ part, int S, int M, in
 }
 
 int gemm_run(const GemmSpec& s, int* err, cudaStream_t st) {
-  if (s.M <= 0 || s.N <= 0 || s.K <= 0 || s.M % tc::BM || s.N % tc::BN || s.splits < 1 ||
+  if (s.M <= 0 || s.N <= 0 || s.K <= 0 || s.M % tc::BM || s.N % 128 || s.splits < 1 ||
       s.K % (tc::BK * s.splits)) {
     set_error("tensor-core GEMM needs M, N multiples of 128 and K a multiple of 64 x splits");
     return DCFLOW_ERR_INVALID_ARG;
@@ -75,13 +75,19 @@ int gemm_run(const GemmSpec& s, int* err, cudaStream_t st) {
     set_error("tensor-core GEMM: D and mask need 16-byte aligned rows");
     return DCFLOW_ERR_INVALID_ARG;
   }
+  // the wide tile where it still gives at least 120 CTAs
+  const bool wide = s.N % 256 == 0 && (int64_t)(s.M / 128) * (s.N / 256) * s.splits >= 120;
+  const int BN = wide ? 256 : 128;
   CUtensorMap ma, mb;
-  int rc = bf16_operand_map(&ma, s.A, s.M, s.K, s.lda);
-  if (!rc) rc = bf16_operand_map(&mb, s.B, s.N, s.K, s.ldb);
+  int rc = bf16_operand_map(&ma, s.A, s.M, s.K, s.lda, tc::BM);
+  if (!rc) rc = bf16_operand_map(&mb, s.B, s.N, s.K, s.ldb, BN);
   if (rc) return rc;
   static bool attr = false;
   if (!attr) {
-    DCF_CUDA(cudaFuncSetAttribute(tc::k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
+    DCF_CUDA(cudaFuncSetAttribute(tc::k_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::Cfg<128>::kSmemBytes));
+    DCF_CUDA(cudaFuncSetAttribute(tc::k_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::Cfg<256>::kSmemBytes));
     attr = true;
   }
   tc::GemmArgs g{};
@@ -99,7 +105,10 @@ int gemm_run(const GemmSpec& s, int* err, cudaStream_t st) {
   g.lddt = s.lddt;
   g.split_stride = (long long)s.M * s.ldd;
   g.err = err;
-  tc::k_gemm_bf16<<<dim3(s.N / tc::BN, s.M / tc::BM, s.splits), 128, tc::kSmemBytes, st>>>(ma, mb, g);
+  if (wide)
+    tc::k_gemm_bf16<256><<<dim3(s.N / 256, s.M / tc::BM, s.splits), 128, tc::Cfg<256>::kSmemBytes, st>>>(ma, mb, g);
+  else
+    tc::k_gemm_bf16<128><<<dim3(s.N / 128, s.M / tc::BM, s.splits), 128, tc::Cfg<128>::kSmemBytes, st>>>(ma, mb, g);
   DCF_CHECK_LAUNCH();
   if (s.splits > 1) {
     k_splitk_reduce<<<592, 256, 0, st>>>(s.part, s.splits, s.M, s.N, s.ldd, static_cast<float*>(s.D));

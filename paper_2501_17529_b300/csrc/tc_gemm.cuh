@@ -29,10 +29,18 @@
 namespace dcf {
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
-constexpr int kTileBytes = BM * BK * 2;          // 16 KB per operand tile
-constexpr int kStageBytes = 2 * kTileBytes;      // A + B
-constexpr int kSmemBytes = 1024 /*align*/ + STAGES * kStageBytes + 256 /*barriers, tmem slot*/;
+constexpr int BM = 128, BK = 64;
+// Output tile 128 x BN (BN = 128 or 256): an N = 256 MMA reads 12 KB of
+// operands from shared memory per 1 MFLOP, an N = 128 one 8 KB per 0.5 MFLOP,
+// so the wide tile leaves the shared-memory port headroom.
+template <int BN>
+struct Cfg {
+  static constexpr int STAGES = BN == 256 ? 4 : 6;
+  static constexpr int kTileA = BM * BK * 2;                  // 16 KB
+  static constexpr int kTileB = BN * BK * 2;                  // 16 or 32 KB
+  static constexpr int kStageBytes = kTileA + kTileB;
+  static constexpr int kSmemBytes = 1024 /*align*/ + STAGES * kStageBytes + 256 /*barriers, tmem slot*/;
+};
 constexpr long long kWait = 4000000000LL;        // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -106,8 +114,10 @@ struct GemmArgs {
   int* err;
 };
 
+template <int BN>
 __global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUtensorMap mA,
                                                    const __grid_constant__ CUtensorMap mB, GemmArgs g) {
+  constexpr int STAGES = Cfg<BN>::STAGES, kStageBytes = Cfg<BN>::kStageBytes, kTileBytes = Cfg<BN>::kTileA;
   extern __shared__ __align__(1024) unsigned char smem[];
   const uint32_t raw = su32(smem);
   const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned tile area
@@ -117,7 +127,17 @@ __global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUten
   const uint32_t done = bars + 8u * (2 * STAGES);
   const uint32_t tslot = done + 8u;  // tensor-memory address written by tcgen05.alloc
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // tiles in groups of 8 M-rows: a wave of CTAs covers a compact block of the
+  // output, so the A rows and B columns it streams are shared through L2
+  int tm, tn;
+  {
+    const int gx = gridDim.x, gy = gridDim.y, lin = blockIdx.y * gx + blockIdx.x;
+    const int G = 8, grp = lin / (G * gx), first = grp * G, rows = min(G, gy - first);
+    const int r = lin - grp * G * gx;
+    tm = first + r % rows;
+    tn = r / rows;
+  }
+  const int m0 = tm * BM, n0 = tn * BN;
   const int KT = g.K / BK / (int)gridDim.z;  // k-tiles of this CTA's share
   const int kt0 = (int)blockIdx.z * KT;
   if (tid == 0) {
@@ -129,7 +149,7 @@ __global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUten
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(128) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(BN) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -158,7 +178,7 @@ __global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUten
       }
       if (*vfailed) break;
       const uint32_t a = base + s * kStageBytes, b = a + kTileBytes;
-      bar_expect(full(s), kStageBytes);
+      bar_expect(full(s), (uint32_t)kStageBytes);
       tma2d(a, &mA, (kt0 + kt) * BK, m0, full(s));
       tma2d(b, &mB, (kt0 + kt) * BK, n0, full(s));
       issued = kt + 1;
@@ -242,7 +262,7 @@ __global__ __launch_bounds__(128) void k_gemm_bf16(const __grid_constant__ CUten
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
 
 }  // namespace tc

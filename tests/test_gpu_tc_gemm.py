@@ -14,7 +14,9 @@ def _cuda():
     build.build()
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 192), (512, 256, 3200), (128, 1024, 256)])
+# the last two shapes give >= 120 tiles of 128 x 256: the wide-tile kernel
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 192), (512, 256, 3200), (128, 1024, 256),
+                                   (4096, 1024, 192), (7680, 512, 3072)])
 @pytest.mark.parametrize("epi", ["plain", "bias_relu", "bf16_out"])
 def test_gemm_matches_fp32_reference(M, N, K, epi):
     from paper_2501_17529_b300.dcflow import dcflow_gemm_bf16
