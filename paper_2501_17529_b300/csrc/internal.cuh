@@ -102,7 +102,7 @@ struct dcflow_ctx {
   int C_eff = 0;
   std::vector<int> h_cont_pos;  // internal index -> caller's position
   dcf::DevBuf cont_pos, cont_inv;  // int[C]: internal -> caller position, caller position -> internal
-  dcf::DevBuf PhiCM;       // Real[C*Mpad] the same factors transposed (screened N-1; built on first use)
+  dcf::DevBuf PhiCM;       // Real[C*Mpad] the same factors transposed (final pass, screened N-1; first solve builds it)
   bool phicm_ready = false;
   dcf::DevBuf Y;           // solve workspace
   // batch scratch

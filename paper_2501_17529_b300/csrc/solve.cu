@@ -608,7 +608,7 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
 // the same arithmetic as the N-1 kernel, write every output of the topology
 // ---------------------------------------------------------------------------
 template <class Real, int RMAX>
-__global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ nsel) {
+__global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ nsel, const Real* __restrict__ PhiCM) {
   const int q = blockIdx.x;
   const QInfo qi = a.qi[q];
   const int tau = qi.tau, T = a.T, M = a.M, C = a.C, Mp = a.Mpad, tid = threadIdx.x;
@@ -639,7 +639,6 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       const int t = k / (C - a.C_eff), c = a.C_eff + k % (C - a.C_eff);
       o.n1_cont_max[((size_t)tau * T + t) * C + a.cont_pos[c]] = -1.f;
     }
-  const Real* PhiMC = static_cast<const Real*>(a.PhiMC);
   const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
   const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
   const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
@@ -688,7 +687,7 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
           Real zr[RMAX];
 #pragma unroll
           for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
-          const Real ph = phi_entry<Real, RMAX>(PhiMC[(size_t)l * a.ldc + c], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
+          const Real ph = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
           const double x = (double)fabs(fma(ph, st, ptil[(size_t)t * Mp + l]));
           if (x > v) {
             v = x;
@@ -1145,10 +1144,11 @@ int launch_n1(const Args& a, int RMAX, int TT, dim3 grid, cudaStream_t st, int t
 }
 
 template <class Real>
-void launch_final(const Args& a, int RMAX, cudaStream_t st, const int* nsel = nullptr) {
-  if (RMAX == 4) k_final<Real, 4><<<a.nq, 128, 0, st>>>(a, nsel);
-  else if (RMAX == 8) k_final<Real, 8><<<a.nq, 128, 0, st>>>(a, nsel);
-  else k_final<Real, 16><<<a.nq, 128, 0, st>>>(a, nsel);
+void launch_final(const Args& a, int RMAX, cudaStream_t st, const void* phicm, const int* nsel = nullptr) {
+  const Real* pc = static_cast<const Real*>(phicm);
+  if (RMAX == 4) k_final<Real, 4><<<a.nq, 128, 0, st>>>(a, nsel, pc);
+  else if (RMAX == 8) k_final<Real, 8><<<a.nq, 128, 0, st>>>(a, nsel, pc);
+  else k_final<Real, 16><<<a.nq, 128, 0, st>>>(a, nsel, pc);
 }
 
 int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
@@ -1535,17 +1535,17 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
         scr->iX.ensure((size_t)srows * scr->Fp * 2) || scr->iH1.ensure((size_t)srows * scr->H * 2) ||
         scr->iH2.ensure((size_t)srows * scr->H * 2) || scr->iZ.ensure((size_t)srows * scr->Cp * 4))
       return DCFLOW_ERR_OOM;
-    if (!ctx->phicm_ready) {
-      if (ctx->PhiCM.ensure((size_t)std::max(C, 1) * Mp * rs)) return DCFLOW_ERR_OOM;
-      const dim3 blk(32, 8), grd((Mp + 31) / 32, (C + 31) / 32);
-      if (fp64)
-        k_phi_cm<double><<<grd, blk, 0, st>>>(ctx->PhiMC.as<double>(), M, C, ctx->ldc, Mp, ctx->PhiCM.as<double>());
-      else
-        k_phi_cm<float><<<grd, blk, 0, st>>>(ctx->PhiMC.as<float>(), M, C, ctx->ldc, Mp, ctx->PhiCM.as<float>());
-      DCF_CHECK_LAUNCH();
-      ++ctx->launches;
-      ctx->phicm_ready = true;
-    }
+  }
+  if (!ctx->phicm_ready) {  // transposed factors: contiguous contingency columns (final pass, screened N-1)
+    if (ctx->PhiCM.ensure((size_t)std::max(C, 1) * Mp * rs)) return DCFLOW_ERR_OOM;
+    const dim3 blk(32, 8), grd((Mp + 31) / 32, (std::max(C, 1) + 31) / 32);
+    if (fp64)
+      k_phi_cm<double><<<grd, blk, 0, st>>>(ctx->PhiMC.as<double>(), M, C, ctx->ldc, Mp, ctx->PhiCM.as<double>());
+    else
+      k_phi_cm<float><<<grd, blk, 0, st>>>(ctx->PhiMC.as<float>(), M, C, ctx->ldc, Mp, ctx->PhiCM.as<float>());
+    DCF_CHECK_LAUNCH();
+    ++ctx->launches;
+    ctx->phicm_ready = true;
   }
   ctx->chunk_cap = cap;
   if (!ctx->side) {
@@ -1821,8 +1821,8 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       int rc = run_n1(af, RMAX, T, true);
       if (rc) return rc;
     }
-    if (fp64) launch_final<double>(af, RMAX, st, nsel_dev);
-    else launch_final<float>(af, RMAX, st, nsel_dev);
+    if (fp64) launch_final<double>(af, RMAX, st, ctx->PhiCM.p, nsel_dev);
+    else launch_final<float>(af, RMAX, st, ctx->PhiCM.p, nsel_dev);
     ++ctx->launches;
     DCF_CHECK_LAUNCH();
     DCF_CUDA(cudaEventRecord(ctx->ev_free[bi], st));
