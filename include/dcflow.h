@@ -192,6 +192,15 @@ typedef struct {
  *                 limit for every contingency c (-1 where c is skipped or the topology
  *                 islands), or NULL: the per-contingency summary that labels the
  *                 learned screener
+ *  top_k, top_cont, top_mon, top_loading   sparse worst results (agg_i of
+ *                 Sec. III-A): per (topology, timestep) the top_k N-1 cases with the
+ *                 highest maximum loading, each with its most loaded monitored
+ *                 branch (the top 1 inside every case, then the top k over the cases;
+ *                 ties to the lower contingency / monitored position), in
+ *                 descending order: int32 positions in `cont` and `mon` and float
+ *                 loadings [n_topo * n_time * top_k]; -1 / -1 / 0 beyond the valid
+ *                 cases.  top_k = 0 (or NULL arrays) skips them; 1 <= top_k <= 64;
+ *                 not available with the screened solve.
  * Outaged monitored branches load 0; outaged contingencies are skipped.
  */
 typedef struct {
@@ -205,6 +214,10 @@ typedef struct {
   uint8_t* island_flag;
   int32_t* n_island_cont;
   float* n1_cont_max;
+  int32_t top_k;
+  int32_t* top_cont;
+  int32_t* top_mon;
+  float* top_loading;
 } dcflow_results;
 
 /*

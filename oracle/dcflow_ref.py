@@ -351,6 +351,7 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
         res["n0_flow"] = np.zeros((T, M))
     if want_cmax:
         res["cmax"] = -np.ones((T, C))  # per contingency: max_l rho (-1 if skipped)
+        res["cargmax"] = -np.ones((T, C), np.int64)  # its monitored position (lowest on ties)
     st, n, f2, t2, alive, k_eff = build_topology(V, f, t, inc, splits, outages)
     if st != OK:
         res["status"] = st
@@ -424,7 +425,7 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
         k = int(np.argmax(flat))
         jc, im = divmod(k, M)
         ovl = float(np.maximum(rho - 1.0, 0.0).sum())
-        return n0m, float(flat[k]), ovl, int(vj[jc]), int(im), rho.max(axis=0)
+        return n0m, float(flat[k]), ovl, int(vj[jc]), int(im), (rho.max(axis=0), rho.argmax(axis=0))
 
     for ti in range(T):
         if not nvar:
@@ -446,7 +447,8 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
         res["n0_max"][ti], res["n1_max"][ti], res["ovl"][ti] = r[0], r[1], r[2]
         res["worst_cont"][ti], res["worst_mon"][ti] = r[3], r[4]
         if want_cmax and r[5] is not None:
-            res["cmax"][ti, vj] = r[5]
+            res["cmax"][ti, vj] = r[5][0]
+            res["cargmax"][ti, vj] = r[5][1]
     return res
 
 
@@ -476,7 +478,30 @@ def evaluate(grid, topo, P, mon, cont, limit, var=None, mode="lodf", idx=None,
         r["n0_flow"] = np.stack([o["n0_flow"] for o in outs]) if outs else np.zeros((0, P.shape[0], len(mon)))
     if want_cmax:
         r["cmax"] = np.stack([o["cmax"] for o in outs]) if outs else np.zeros((0, P.shape[0], len(cont)))
+        r["cargmax"] = (np.stack([o["cargmax"] for o in outs]) if outs
+                        else np.zeros((0, P.shape[0], len(cont)), np.int64))
     return r
+
+
+def top_cases(cmax, cargmax, k):
+    """Sparse worst results (agg_i of Sec. III-A): per (topology, timestep) the k
+    N-1 cases with the highest maximum loading, each with its most loaded
+    monitored branch -- the top 1 inside every N-1 case, then the top k over
+    the cases.  Ties: lower contingency position first.  Returns (cont, mon,
+    loading), each [..., k]; slots beyond the valid cases hold -1 / -1 / 0."""
+    cm = np.asarray(cmax, np.float64)
+    ca = np.asarray(cargmax, np.int64)
+    shp = cm.shape[:-1]
+    cmf, caf = cm.reshape(-1, cm.shape[-1]), ca.reshape(-1, ca.shape[-1])
+    oc = -np.ones((cmf.shape[0], k), np.int64)
+    om = -np.ones((cmf.shape[0], k), np.int64)
+    ol = np.zeros((cmf.shape[0], k))
+    for r in range(cmf.shape[0]):
+        valid = [c for c in range(cmf.shape[1]) if cmf[r, c] >= 0]
+        order = sorted(valid, key=lambda c: (-cmf[r, c], c))[:k]
+        for j, c in enumerate(order):
+            oc[r, j], om[r, j], ol[r, j] = c, caf[r, c], cmf[r, c]
+    return oc.reshape(shp + (k,)), om.reshape(shp + (k,)), ol.reshape(shp + (k,))
 
 
 def n1_loading_column(grid, splits, outages, P_t, mon, c_branch, limit):

@@ -1089,6 +1089,112 @@ __global__ __launch_bounds__(64) void k_n1_sel(Args a, const Real* __restrict__ 
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// sparse worst results (agg_i, Sec. III-A): per (topology, timestep) the top k
+// N-1 cases by maximum loading, each with its most loaded monitored branch,
+// from the per-contingency maxima of the N-1 kernel (one warp per timestep)
+// ---------------------------------------------------------------------------
+template <class Real, int RMAX, int NPL>
+__global__ __launch_bounds__(128) void k_topcases(Args a, const float* __restrict__ cmax,
+                                                   const int* __restrict__ cont_inv, const Real* __restrict__ PhiCM,
+                                                   int k) {
+  __shared__ float sv_[4][64];
+  __shared__ int sp_[4][64];
+  __shared__ float ov_[4][64];
+  __shared__ int op_[4][64];
+  const int q = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.y * 4 + w;
+  const QInfo qi = a.qi[q];
+  const int T = a.T, M = a.M, C = a.C, Mp = a.Mpad, tau = qi.tau;
+  if (t >= T) return;
+  const dcflow_results& o = a.out;
+  const size_t ob = ((size_t)tau * T + t) * k;
+  if (qi.status != ST_OK) {
+    for (int j = lane; j < k; j += 32) {
+      o.top_cont[ob + j] = -1;
+      o.top_mon[ob + j] = -1;
+      o.top_loading[ob + j] = 0.f;
+    }
+    return;
+  }
+  const float* row = cmax + ((size_t)tau * T + t) * C;
+  uint32_t key[NPL];
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {
+    const int p = lane + 32 * i;
+    key[i] = p < C ? float_key(row[p]) : 0u;
+  }
+  const int kk = k < C ? k : C;
+  bool sel[NPL];
+  uint32_t thr;
+  warp_top_k<NPL>(key, kk, sel, thr);
+  int off = 0;
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {  // the selected cases in ascending position
+    const uint32_t b = __ballot_sync(0xffffffffu, sel[i]);
+    if (sel[i]) {
+      const int j = off + __popc(b & ((1u << lane) - 1u));
+      sp_[w][j] = lane + 32 * i;
+      sv_[w][j] = row[lane + 32 * i];
+    }
+    off += __popc(b);
+  }
+  __syncwarp();
+  for (int j = lane; j < kk; j += 32) {  // descending loading, ties to the lower position
+    const float v = sv_[w][j];
+    const int p = sp_[w][j];
+    int rank = 0;
+    for (int m = 0; m < kk; ++m) rank += sv_[w][m] > v || (sv_[w][m] == v && sp_[w][m] < p);
+    ov_[w][rank] = v;
+    op_[w][rank] = p;
+  }
+  __syncwarp();
+  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
+  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
+  const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
+  const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
+  const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
+  for (int j = 0; j < k; ++j) {
+    const bool valid = j < kk && ov_[w][j] >= 0.f;
+    int l_best = -1;
+    if (valid) {  // its most loaded monitored branch: the column recomputed as in the N-1 kernel
+      const int c = cont_inv[op_[w][j]];
+      Real vt[RMAX];
+#pragma unroll
+      for (int jj = 0; jj < RMAX; ++jj) vt[jj] = VtR[(size_t)jj * C + c];
+      const Real st = sv[(size_t)t * C + c];
+      double v = -1.0;
+      int arg = 0x7fffffff;
+      for (int l = lane; l < M; l += 32) {
+        Real zr[RMAX];
+#pragma unroll
+        for (int jj = 0; jj < RMAX; ++jj) zr[jj] = Zs[(size_t)jj * Mp + l];
+        const Real ph = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
+        const double x = (double)fabs(fma(ph, st, ptil[(size_t)t * Mp + l]));
+        if (x > v) {
+          v = x;
+          arg = l;
+        }
+      }
+      for (int off2 = 16; off2; off2 >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, off2);
+        const int a2 = __shfl_xor_sync(0xffffffffu, arg, off2);
+        if (v2 > v || (v2 == v && a2 < arg)) {
+          v = v2;
+          arg = a2;
+        }
+      }
+      l_best = arg;
+    }
+    if (lane == 0) {
+      o.top_cont[ob + j] = valid ? op_[w][j] : -1;
+      o.top_mon[ob + j] = valid ? l_best : -1;
+      o.top_loading[ob + j] = valid ? ov_[w][j] : 0.f;
+    }
+  }
+}
+
 }  // namespace dcf
 
 #include "n1_reg.cuh"
@@ -1149,6 +1255,23 @@ void launch_final(const Args& a, int RMAX, cudaStream_t st, const void* phicm, c
   if (RMAX == 4) k_final<Real, 4><<<a.nq, 128, 0, st>>>(a, nsel, pc);
   else if (RMAX == 8) k_final<Real, 8><<<a.nq, 128, 0, st>>>(a, nsel, pc);
   else k_final<Real, 16><<<a.nq, 128, 0, st>>>(a, nsel, pc);
+}
+
+template <class Real, int RMAX>
+void launch_topcases_r(const Args& a, const float* cmax, const int* cinv, const void* phicm, int k, cudaStream_t st) {
+  const dim3 grid(a.nq, (a.T + 3) / 4);
+  const Real* pc = static_cast<const Real*>(phicm);
+  if (a.C <= 256) k_topcases<Real, RMAX, 8><<<grid, 128, 0, st>>>(a, cmax, cinv, pc, k);
+  else if (a.C <= 512) k_topcases<Real, RMAX, 16><<<grid, 128, 0, st>>>(a, cmax, cinv, pc, k);
+  else if (a.C <= 1024) k_topcases<Real, RMAX, 32><<<grid, 128, 0, st>>>(a, cmax, cinv, pc, k);
+  else k_topcases<Real, RMAX, 64><<<grid, 128, 0, st>>>(a, cmax, cinv, pc, k);
+}
+template <class Real>
+void launch_topcases(const Args& a, int RMAX, const float* cmax, const int* cinv, const void* phicm, int k,
+                     cudaStream_t st) {
+  if (RMAX == 4) launch_topcases_r<Real, 4>(a, cmax, cinv, phicm, k, st);
+  else if (RMAX == 8) launch_topcases_r<Real, 8>(a, cmax, cinv, phicm, k, st);
+  else launch_topcases_r<Real, 16>(a, cmax, cinv, phicm, k, st);
 }
 
 int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
@@ -1392,6 +1515,13 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   // injection candidates T_i (Eq. (8)): read the small CSR to the host, validate
   // it, and map every entry to a pool bus (a column of the extended base flows)
   const int U = bt->n_var;
+  const int top_k = mode == kModeFeatures ? 0 : res->top_k;
+  if (top_k != 0 && (top_k < 1 || top_k > 64 || !res->top_cont || !res->top_mon || !res->top_loading ||
+                     mode != kModeFull || ctx->C > 2048)) {
+    set_error("dcflow_solve_batch: top_k in [1, 64] with its three arrays, at most 2048 contingencies, "
+              "not with the screened solve");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
   if (mode != kModeFull && U > 0) {
     set_error("dcflow_solve_batch: the screener runs without injection candidates");
     return DCFLOW_ERR_INVALID_ARG;
@@ -1577,6 +1707,10 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   base.err = ctx->err.as<int>();
   base.best_u = nullptr;
   base.out = *res;
+  if (top_k > 0 && !res->n1_cont_max) {  // the top-k pass reads the per-contingency maxima
+    if (ctx->cm_scratch.ensure((size_t)N * T * std::max(C, 1) * sizeof(float))) return DCFLOW_ERR_OOM;
+    base.out.n1_cont_max = ctx->cm_scratch.as<float>();
+  }
   auto chunk_args = [&](int bi) {
     Args a = base;
     ChunkBufs& B = ctx->bufs[bi];
@@ -1825,6 +1959,14 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     else launch_final<float>(af, RMAX, st, ctx->PhiCM.p, nsel_dev);
     ++ctx->launches;
     DCF_CHECK_LAUNCH();
+    if (top_k > 0) {
+      if (fp64)
+        launch_topcases<double>(af, RMAX, af.out.n1_cont_max, ctx->cont_inv.as<int>(), ctx->PhiCM.p, top_k, st);
+      else
+        launch_topcases<float>(af, RMAX, af.out.n1_cont_max, ctx->cont_inv.as<int>(), ctx->PhiCM.p, top_k, st);
+      ++ctx->launches;
+      DCF_CHECK_LAUNCH();
+    }
     DCF_CUDA(cudaEventRecord(ctx->ev_free[bi], st));
   }
   return DCFLOW_OK;

@@ -44,7 +44,8 @@ class Results(ctypes.Structure):
     _fields_ = [("n0_flow", c_void_p), ("n0_max_loading", c_void_p), ("n1_max_loading", c_void_p),
                 ("overload_sum", c_void_p), ("worst_cont", c_void_p), ("worst_mon", c_void_p),
                 ("best_var", c_void_p), ("island_flag", c_void_p), ("n_island_cont", c_void_p),
-                ("n1_cont_max", c_void_p)]
+                ("n1_cont_max", c_void_p), ("top_k", c_int32), ("top_cont", c_void_p), ("top_mon", c_void_p),
+                ("top_loading", c_void_p)]
 
 
 class ScreenOptions(ctypes.Structure):
@@ -379,7 +380,7 @@ class DeviceResults:
     """Caller-owned device outputs of one batch."""
 
     def __init__(self, n_topo, n_time, n_mon, want_flows=False, want_var=False, device="cuda", n_cont=0,
-                 want_cont_max=False):
+                 want_cont_max=False, top_k=0):
         import torch
         nt = max(1, n_topo * n_time)
         self.n0_flow = torch.empty(max(1, n_topo * n_time * n_mon), dtype=torch.float64, device=device) if want_flows else None
@@ -393,6 +394,11 @@ class DeviceResults:
         self.n_island_cont = torch.empty(max(1, n_topo), dtype=torch.int32, device=device)
         self.n1_cont_max = (torch.empty(max(1, n_topo * n_time * n_cont), dtype=torch.float32, device=device)
                             if want_cont_max else None)
+        self.top_k = int(top_k)
+        nk = max(1, n_topo * n_time * self.top_k)
+        self.top_cont = torch.empty(nk, dtype=torch.int32, device=device) if top_k else None
+        self.top_mon = torch.empty(nk, dtype=torch.int32, device=device) if top_k else None
+        self.top_loading = torch.empty(nk, dtype=torch.float32, device=device) if top_k else None
         self.shape = (n_topo, n_time, n_mon)
         self.n_cont = n_cont
 
@@ -400,7 +406,8 @@ class DeviceResults:
         return Results(_ptr(self.n0_flow), _ptr(self.n0_max_loading), _ptr(self.n1_max_loading),
                        _ptr(self.overload_sum), _ptr(self.worst_cont), _ptr(self.worst_mon),
                        _ptr(self.best_var), _ptr(self.island_flag), _ptr(self.n_island_cont),
-                       _ptr(self.n1_cont_max))
+                       _ptr(self.n1_cont_max), self.top_k, _ptr(self.top_cont), _ptr(self.top_mon),
+                       _ptr(self.top_loading))
 
     def to_host(self) -> dict:
         N, T, M = self.shape
@@ -419,6 +426,11 @@ class DeviceResults:
             out["n0_flow"] = self.n0_flow[:N * T * M].cpu().numpy().reshape(N, T, M)
         if self.n1_cont_max is not None:
             out["cont_max"] = self.n1_cont_max[:N * T * self.n_cont].cpu().numpy().reshape(N, T, self.n_cont)
+        if self.top_k:
+            k = self.top_k
+            out["top_cont"] = self.top_cont[:N * T * k].cpu().numpy().reshape(N, T, k).astype(np.int64)
+            out["top_mon"] = self.top_mon[:N * T * k].cpu().numpy().reshape(N, T, k).astype(np.int64)
+            out["top_loading"] = self.top_loading[:N * T * k].cpu().numpy().reshape(N, T, k).astype(np.float64)
         return out
 
 
@@ -445,9 +457,9 @@ class Solver:
         return out
 
     def solve(self, dbatch: DeviceBatch, want_flows=False, results: DeviceResults | None = None, stream=None,
-              want_cont_max=False):
+              want_cont_max=False, top_k=0):
         res = results or DeviceResults(dbatch.n_topo, dbatch.n_time, self.n_mon, want_flows, dbatch.n_var > 0,
-                                       n_cont=self.n_cont, want_cont_max=want_cont_max)
+                                       n_cont=self.n_cont, want_cont_max=want_cont_max, top_k=top_k)
         dcflow_solve_batch(self.ctx, dbatch.cstruct(), res.cstruct(), stream)
         return res
 

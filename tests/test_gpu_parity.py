@@ -283,3 +283,43 @@ def test_grid10000_sample(precision):
     w = synth.workload(4, n_topo=3)
     lim = oracle.thermal_limits(w.grid, w.inj)
     compare(_gpu(w, lim, precision), _ref(w, lim), w, w.topo, lim, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_top_cases_match_oracle(precision):
+    """agg_i: the k worst N-1 cases per (topology, timestep) with their most loaded branch."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch
+    w = synth.workload(2, n_topo=16, T=3)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    k = 5
+    s = _solver(w, lim, precision)
+    res = s.solve(DeviceBatch(w.topo, w.inj), top_k=k)
+    torch.cuda.synchronize()
+    g = res.to_host()
+    s.close()
+    ref = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, want_cmax=True)
+    rc, rm, rl = oracle.top_cases(ref["cmax"], ref["cargmax"], k)
+    tol = max(TOL[precision], 2e-7)  # the loadings are float32 outputs in both forms
+    mon = np.asarray(w.mon)
+    for i in range(w.topo.n_topo):
+        if ref["status"][i] != 0:
+            assert (g["top_cont"][i] == -1).all() and (g["top_mon"][i] == -1).all()
+            continue
+        for t in range(3):
+            np.testing.assert_allclose(g["top_loading"][i, t], rl[i, t], rtol=0, atol=tol * max(1.0, rl[i, t, 0]))
+            for j in range(k):
+                c, l = g["top_cont"][i, t, j], g["top_mon"][i, t, j]
+                if rc[i, t, j] < 0:
+                    assert c == -1 and l == -1
+                    continue
+                # the pick is a case of (near) the same loading, and l its (near) most loaded branch
+                assert abs(ref["cmax"][i, t, c] - rl[i, t, j]) <= 2 * tol * max(1.0, rl[i, t, j])
+                if c == rc[i, t, j]:
+                    if l != rm[i, t, j]:
+                        a, b = w.topo.split_ptr[i], w.topo.split_ptr[i + 1]
+                        splits = list(zip(w.topo.split_sub[a:b], w.topo.split_mask[a:b]))
+                        a, b = w.topo.out_ptr[i], w.topo.out_ptr[i + 1]
+                        col = oracle.n1_loading_column(w.grid, splits, list(w.topo.out_branch[a:b]), w.inj[t],
+                                                       w.mon, w.cont[c], lim).copy()
+                        col[mon == w.cont[c]] = 0.0
+                        assert col[l] >= col.max() - 2 * tol * max(1.0, col.max())

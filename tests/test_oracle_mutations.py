@@ -192,3 +192,25 @@ def test_screener_mutation_is_caught(monkeypatch, golden_dir, name, attr, fake, 
           "labels": spins.test_labels_characterisation,
           "bf16": spins.test_bf16_round_known_values_and_torch}[pin]
     assert _fails(fn), name
+
+
+def _top_cases_ascending(cmax, cargmax, k):
+    cm = np.asarray(cmax, np.float64)
+    ca = np.asarray(cargmax, np.int64)
+    shp = cm.shape[:-1]
+    cmf, caf = cm.reshape(-1, cm.shape[-1]), ca.reshape(-1, ca.shape[-1])
+    oc = -np.ones((cmf.shape[0], k), np.int64)
+    om = -np.ones((cmf.shape[0], k), np.int64)
+    ol = np.zeros((cmf.shape[0], k))
+    for r in range(cmf.shape[0]):
+        valid = [c for c in range(cmf.shape[1]) if cmf[r, c] >= 0]
+        order = sorted(valid, key=lambda c: (cmf[r, c], c))[:k]  # planted: lowest loadings first
+        for j, c in enumerate(order):
+            oc[r, j], om[r, j], ol[r, j] = c, caf[r, c], cmf[r, c]
+    return oc.reshape(shp + (k,)), om.reshape(shp + (k,)), ol.reshape(shp + (k,))
+
+
+def test_top_cases_mutation_is_caught(monkeypatch):
+    monkeypatch.setattr(ref, "top_cases", _top_cases_ascending)
+    monkeypatch.setattr(oracle, "top_cases", _top_cases_ascending)
+    assert _fails(pins.test_top_cases_k1_is_the_worst_case_and_k3_matches_refactorisation)

@@ -472,3 +472,31 @@ def test_variation_argmin_is_bruteforce():
                 assert r["worst_cont"][i, ti] == rb["worst_cont"][i, ti * U + ub]
                 exact += 1
     assert exact > 0
+
+
+def test_top_cases_k1_is_the_worst_case_and_k3_matches_refactorisation():
+    """agg_i (Sec. III-A): top 1 per N-1 case, then top k over the cases."""
+    from paper_2501_17529_b300 import synth
+    w = synth.workload(2, n_topo=6, T=2)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    r = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, want_cmax=True)
+    c1, m1, l1 = oracle.top_cases(r["cmax"], r["cargmax"], 1)
+    ok = r["status"] == 0
+    np.testing.assert_array_equal(c1[ok, :, 0], r["worst_cont"][ok])
+    np.testing.assert_array_equal(m1[ok, :, 0], r["worst_mon"][ok])
+    np.testing.assert_allclose(l1[ok, :, 0], r["n1_max"][ok], rtol=1e-12)
+    c3, m3, l3 = oracle.top_cases(r["cmax"], r["cargmax"], 3)
+    for i in np.nonzero(ok)[0][:3]:
+        a, b = w.topo.split_ptr[i], w.topo.split_ptr[i + 1]
+        splits = list(zip(w.topo.split_sub[a:b], w.topo.split_mask[a:b]))
+        a, b = w.topo.out_ptr[i], w.topo.out_ptr[i + 1]
+        outs = list(w.topo.out_branch[a:b])
+        for t in range(2):
+            assert np.all(np.diff(l3[i, t]) <= 0)
+            for j in range(3):
+                col = oracle.n1_loading_column(w.grid, splits, outs, w.inj[t], w.mon, w.cont[c3[i, t, j]], lim)
+                col = col.copy()
+                mon_pos = np.nonzero(np.asarray(w.mon) == w.cont[c3[i, t, j]])[0]
+                col[mon_pos] = 0.0  # the outaged branch itself carries nothing
+                assert l3[i, t, j] == pytest.approx(col.max(), rel=1e-9)
+                assert col[m3[i, t, j]] == pytest.approx(col.max(), rel=1e-9)
