@@ -163,6 +163,66 @@ def evaluate(solver: Solver, screener: Screener, topo, inj, Y, cont_max, n1_exac
     }
 
 
+def _study():
+    from . import synth
+    return synth.workload(5, n_topo=16)
+
+
+def _limits(w):
+    base = Solver(w.grid, precision="fp64")
+    pt = base.base_ptdf(w.mon).cpu().numpy()
+    base.close()
+    lim = np.ones(w.grid.n_branch)
+    lim[w.mon] = 1.2 * np.abs(w.inj @ pt.T).max(axis=0) + 0.1
+    return lim
+
+
+def profile(a):
+    """Timing of a trained screener (loaded from a checkpoint) on held-out topologies."""
+    import torch
+
+    from . import synth
+    from .csrc import build
+    build.build()
+    torch.cuda.set_device(0)
+    w = _study()
+    ev = synth.make_topologies(w.grid, w.subs, a.eval, 605, (1, 8), (0, 0))
+    solver = Solver(w.grid, precision="fp32")
+    solver.set_study(w.mon, w.cont, _limits(w), split_bus=w.subs)
+    scr = Screener(solver, max_rows=a.batch, seed=1)
+    scr.load(a.profile)
+    db = DeviceBatch(ev, w.inj)
+    r = DeviceResults(ev.n_topo, w.inj.shape[0], solver.n_mon, n_cont=solver.n_cont)
+
+    def tm(fn, n=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    t_full = tm(lambda: solver.solve(db, results=r))
+    t_scr = tm(lambda: solver.solve_screened(db, scr, a.top_k, a.fallback_logit, results=r))
+    rows = 8 * a.batch
+    X = torch.zeros(rows, scr.F_pad, dtype=torch.bfloat16, device="cuda")
+    X[:, :scr.F] = torch.randn(rows, scr.F, device="cuda").to(torch.bfloat16)
+    Y = (torch.rand(rows, scr.C_pad, device="cuda") < 0.06).to(torch.uint8)
+    loss = torch.zeros(1, device="cuda")
+    perm = torch.randperm(rows, device="cuda").to(torch.int32)
+
+    def steps():
+        for i in range(0, rows, a.batch):
+            scr.train_step(X, Y, perm[i:i + a.batch], 1e-4, loss)
+
+    t_step = tm(steps, 2) / 8
+    print(json.dumps({"topologies": a.eval, "top_k": a.top_k, "full_ms": t_full, "screened_ms": t_scr,
+                      "speedup": t_full / t_scr, "train_step_ms": t_step, "train_rows": a.batch}))
+
+
 def main():
     import torch
     from . import synth
@@ -179,16 +239,17 @@ def main():
     ap.add_argument("--cosine", action="store_true", help="cosine-decayed step size")
     ap.add_argument("--fallback-logit", type=float, default=float("inf"))
     ap.add_argument("--save", default=None, help="checkpoint path (.npz)")
+    ap.add_argument("--profile", default=None, metavar="CKPT",
+                    help="no training: load CKPT and time a full and a screened solve of --eval "
+                         "held-out topologies, and 8 training steps of --batch rows")
     a = ap.parse_args()
+    if a.profile:
+        return profile(a)
     build.build()
     torch.cuda.set_device(0)
     w = synth.workload(5, n_topo=a.train)
     ev_topo = synth.make_topologies(w.grid, w.subs, a.eval, 605, (1, 8), (0, 0))
-    base = Solver(w.grid, precision="fp64")
-    pt = base.base_ptdf(w.mon).cpu().numpy()
-    base.close()
-    lim = np.ones(w.grid.n_branch)
-    lim[w.mon] = 1.2 * np.abs(w.inj @ pt.T).max(axis=0) + 0.1
+    lim = _limits(w)
     solver = Solver(w.grid, precision="fp32")
     solver.set_study(w.mon, w.cont, lim, split_bus=w.subs)
     scr = Screener(solver, max_rows=a.batch, seed=1)
