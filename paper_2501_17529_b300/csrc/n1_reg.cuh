@@ -72,8 +72,9 @@ struct RegLayout {
   static constexpr int kSP = kCB + 1;  // row pitch (float) of the per-timestep arrays: spreads the banks
   static constexpr int kOffPh = kRegStages * kStage;              // float2 [kLT/2][kCB]
   static constexpr int kOffPtT = kOffPh + kLT * kCB * 4;          // float2 [kLT/2][kTP]
-  static constexpr int kOffS = kOffPtT + a128(kLT / 2 * kTP * 8); // float [TT][kSP]
-  static constexpr int kOffOv = kOffS + a128(TT * kSP * 4);       // float [TT][kSP]
+  static constexpr int kOffOv = kOffPtT + a128(kLT / 2 * kTP * 8); // float [TT][kSP]
+  // the per-timestep maxima of the final scan reuse the (then idle) stages
+  static_assert(TT * kSP * 4 <= kRegStages * kStage, "final scan fits the stages");
   static constexpr int kOffVt = kOffOv + a128(TT * kSP * 4);      // float [RMAX][kCB]: -Vt
   static constexpr int kOffBar = kOffVt + a128(RMAX * kCB * 4);   // uint64 [kRegStages]
   static constexpr int kOffOk = kOffBar + 64;                     // uint8 [kCB]
@@ -106,7 +107,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
   }
   float2* s_ph = reinterpret_cast<float2*>(sm + L::kOffPh);
   float2* s_pt = reinterpret_cast<float2*>(sm + L::kOffPtT);
-  float* s_s = reinterpret_cast<float*>(sm + L::kOffS);
+  float* s_s = reinterpret_cast<float*>(sm);  // after the tile loop: per-timestep maxima (stage memory)
   float* s_ov = reinterpret_cast<float*>(sm + L::kOffOv);
   float* s_vt = reinterpret_cast<float*>(sm + L::kOffVt);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kOffBar);
@@ -134,11 +135,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
     const int j = i / kCB, c = s_ci[i % kCB];
     s_vt[i] = c >= 0 ? -VtR[(size_t)j * C + c] : 0.f;
   }
-  for (int i = tid; i < TT * kCB; i += R::NT) {
-    const int t = i / kCB, cl = i % kCB, c = s_ci[cl];
-    s_s[t * SP + cl] = (c >= 0 && t0 + t < T) ? sv[(size_t)(t0 + t) * C + c] : 0.f;
-    s_ov[t * SP + cl] = 0.f;  // overload partial sums, scaled by 2^-20
-  }
+  for (int i = tid; i < TT * kCB; i += R::NT) s_ov[(i / kCB) * SP + i % kCB] = 0.f;  // overload sums, x 2^-20
   if (tid == 0) {
     for (int st = 0; st < kRegStages; ++st) mbar_init(smem_u32(&bars[st]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -149,7 +146,8 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
   for (int i = 0; i < CR; ++i)
 #pragma unroll
     for (int j = 0; j < TR; ++j) {
-      const float v = s_s[(tg * TR + j) * SP + cg + R::CG * i];
+      const int c = s_ci[cg + R::CG * i], t = tg * TR + j;
+      const float v = (c >= 0 && t0 + t < T) ? sv[(size_t)(t0 + t) * C + c] : 0.f;
       s2[i][j] = make_float2(v, v);
     }
   const int ntiles = (M + kLT - 1) / kLT;
@@ -312,7 +310,8 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
           const int item = queue[jq];
           const int src = (tid & ~31) | (item >> 8), b = item & 255;
           const int cl = src % R::CG + R::CG * (b / TR), t = (src / R::CG) * TR + b % TR;
-          const float stv = s_s[t * SP + cl];
+          const int cs = s_ci[cl];
+          const float stv = (cs >= 0 && t0 + t < T) ? sv[(size_t)(t0 + t) * C + cs] : 0.f;
           const float2 s22 = make_float2(stv, stv);
           float2 o2 = make_float2(0.f, 0.f);
 #pragma unroll
