@@ -350,6 +350,13 @@ int dcflow_solve_batch_screened(dcflow_ctx* ctx, const dcflow_batch* batch, cons
                                 dcflow_screen* s, const dcflow_screen_options* opt, const dcflow_screen_report* report,
                                 void* stream);
 
+/* Failure-path self-test (no counterpart in the paper): one block waits on an
+ * mbarrier that is never completed, with the same bounded wait (about 2 s at
+ * 2 GHz) as the N-1 kernels; when the budget runs out the kernel records the
+ * expiry in an error word and returns without faulting.  Returns
+ * DCFLOW_ERR_TIMEOUT (the expected outcome); the context stays usable. */
+int dcflow_selftest_bounded_wait(dcflow_ctx* ctx, void* stream);
+
 void dcflow_destroy(dcflow_ctx* ctx);
 const char* dcflow_strerror(int code);
 const char* dcflow_last_error(void);

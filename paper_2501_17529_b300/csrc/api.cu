@@ -67,3 +67,50 @@ extern "C" const char* dcflow_strerror(int code) {
 }
 
 extern "C" const char* dcflow_last_error(void) { return dcf::g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// failure-path self-test: one block waits on an mbarrier that nothing ever
+// completes, with the bounded wait of the N-1 kernels; when the budget runs
+// out it records the expiry in an error word and returns.  The host reads the
+// word: DCFLOW_ERR_TIMEOUT, and the context stays usable.
+// ---------------------------------------------------------------------------
+#include "args.cuh"
+#include "n1_tma.cuh"
+
+namespace dcf {
+__global__ void k_wait_selftest(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);  // one arrival expected; none ever comes
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool got = mbar_wait(smem_u32(&bar), 0);
+  if (__syncthreads_or(!got) && threadIdx.x == 0) atomicExch(err, 1);
+}
+}  // namespace dcf
+
+extern "C" int dcflow_selftest_bounded_wait(dcflow_ctx* ctx, void* stream) {
+  if (!ctx) return DCFLOW_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  dcf::DevBuf e;
+  if (e.ensure(sizeof(int))) return DCFLOW_ERR_OOM;
+  int h = 0;
+  cudaError_t rc = cudaMemsetAsync(e.p, 0, sizeof(int), st);
+  if (rc == cudaSuccess) {
+    dcf::k_wait_selftest<<<1, 32, 0, st>>>(e.as<int>());
+    rc = cudaGetLastError();
+  }
+  if (rc == cudaSuccess) rc = cudaMemcpyAsync(&h, e.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (rc == cudaSuccess) rc = cudaStreamSynchronize(st);
+  e.release();
+  if (rc != cudaSuccess) {
+    dcf::set_error(std::string("dcflow_selftest_bounded_wait: ") + cudaGetErrorString(rc));
+    return DCFLOW_ERR_CUDA;
+  }
+  if (h) {
+    dcf::set_error("dcflow_selftest_bounded_wait: the bounded wait expired as designed");
+    return DCFLOW_ERR_TIMEOUT;
+  }
+  return DCFLOW_OK;
+}

@@ -63,7 +63,7 @@ EXPORTED = ["dcflow_default_options", "dcflow_setup", "dcflow_base_ptdf", "dcflo
             "dcflow_screen_create", "dcflow_screen_destroy", "dcflow_screen_dims", "dcflow_screen_features",
             "dcflow_screen_labels", "dcflow_screen_backward", "dcflow_screen_adam", "dcflow_screen_train_step",
             "dcflow_screen_check", "dcflow_screen_logits", "dcflow_screen_get", "dcflow_screen_set",
-            "dcflow_screen_adam_step", "dcflow_solve_batch_screened",
+            "dcflow_screen_adam_step", "dcflow_solve_batch_screened", "dcflow_selftest_bounded_wait",
             "dcflow_destroy", "dcflow_strerror", "dcflow_last_error"]
 
 SCREEN_TENSORS = ("W1", "b1", "W2", "b2", "W3", "b3")
@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH):
         "dcflow_screen_adam_step": ([c_void_p, POINTER(c_int64), c_int32], c_int32),
         "dcflow_solve_batch_screened": ([c_void_p, POINTER(Batch), POINTER(Results), c_void_p,
                                          POINTER(ScreenOptions), POINTER(ScreenReport), c_void_p], c_int32),
+        "dcflow_selftest_bounded_wait": ([c_void_p, c_void_p], c_int32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -334,6 +335,11 @@ def dcflow_solve_batch_screened(ctx, batch: Batch, results: Results, scr, opt: S
     _check(load_library().dcflow_solve_batch_screened(ctx, byref(batch), byref(results), scr, byref(opt),
                                                       byref(report), _stream_ptr(stream)),
            "dcflow_solve_batch_screened")
+
+
+def dcflow_selftest_bounded_wait(ctx, stream=None) -> int:
+    """Return code of the bounded-wait self-test (DCFLOW_ERR_TIMEOUT = -5 is the designed outcome)."""
+    return int(load_library().dcflow_selftest_bounded_wait(ctx, _stream_ptr(stream)))
 
 
 def dcflow_destroy(ctx):

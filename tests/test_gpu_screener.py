@@ -236,3 +236,25 @@ def test_trained_screener_gains_over_full_n1():
     assert after["worst_cont_hit_rate"] >= 0.95
     scr.close()
     s.close()
+
+
+def test_screened_solve_fp64_matches_oracle():
+    """The FP64 form of the screened N-1 (selected-contingency kernel in FP64)."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch, Screener, Solver
+    w = synth.workload(2, n_topo=8, T=2)
+    lim = ref.thermal_limits(w.grid, w.inj)
+    s = Solver(w.grid, precision="fp64")
+    s.set_study(w.mon, w.cont, lim, split_bus=w.subs)
+    scr = Screener(s, max_rows=128, seed=9)
+    res, rep = s.solve_screened(DeviceBatch(w.topo, w.inj), scr, top_k=16, want_pred=True)
+    out = res.to_host()
+    pred = rep["pred"].cpu().numpy().reshape(8, 2, 16)
+    for i in range(8):
+        if out["status"][i] != 0:
+            continue
+        union = np.unique(pred[i])
+        o = ref.evaluate(w.grid, w.topo.subset([i]), w.inj, w.mon, w.cont[union], lim)
+        np.testing.assert_allclose(out["n1_max"][i], o["n1_max"][0], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(out["ovl"][i], o["ovl"][0], rtol=1e-10, atol=1e-10)
+    scr.close()
+    s.close()
