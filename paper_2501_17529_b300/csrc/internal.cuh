@@ -67,6 +67,19 @@ struct ChunkBufs {
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Raise a kernel's dynamic shared-memory limit once per device (a function
+// attribute lives in each device's context); `done` holds one bit per device.
+template <class K>
+inline cudaError_t smem_attr_once(K kernel, int bytes, uint64_t& done) {
+  int d = 0;
+  cudaError_t e = cudaGetDevice(&d);
+  if (e != cudaSuccess) return e;
+  if (d < 64 && ((done >> d) & 1ull)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && d < 64) done |= 1ull << d;
+  return e;
+}
+
 }  // namespace dcf
 
 struct dcflow_ctx {

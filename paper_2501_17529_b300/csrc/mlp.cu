@@ -82,14 +82,9 @@ int gemm_run(const GemmSpec& s, int* err, cudaStream_t st) {
   int rc = bf16_operand_map(&ma, s.A, s.M, s.K, s.lda, tc::BM);
   if (!rc) rc = bf16_operand_map(&mb, s.B, s.N, s.K, s.ldb, BN);
   if (rc) return rc;
-  static bool attr = false;
-  if (!attr) {
-    DCF_CUDA(cudaFuncSetAttribute(tc::k_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::Cfg<128>::kSmemBytes));
-    DCF_CUDA(cudaFuncSetAttribute(tc::k_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::Cfg<256>::kSmemBytes));
-    attr = true;
-  }
+  static uint64_t attr128 = 0, attr256 = 0;
+  DCF_CUDA(smem_attr_once(tc::k_gemm_bf16<128>, tc::Cfg<128>::kSmemBytes, attr128));
+  DCF_CUDA(smem_attr_once(tc::k_gemm_bf16<256>, tc::Cfg<256>::kSmemBytes, attr256));
   tc::GemmArgs g{};
   g.M = s.M;
   g.N = s.N;
@@ -387,16 +382,25 @@ extern "C" int dcflow_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, 
                                 int32_t ldb, const float* bias, int32_t relu, void* D, int32_t ldd, int32_t out_bf16,
                                 void* stream) {
   static std::mutex mu;
-  static int* d_err = nullptr;
+  static int* d_errs[64] = {};  // one error word per device
+  int dev = 0;
+  DCF_CUDA(cudaGetDevice(&dev));
+  if (dev >= 64) {
+    set_error("dcflow_gemm_bf16: device index above 63");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  int* d_err = nullptr;
   {
     std::lock_guard<std::mutex> lk(mu);
-    if (!d_err) {
-      if (cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) {
+    if (!d_errs[dev]) {
+      if (cudaMalloc(&d_errs[dev], sizeof(int)) != cudaSuccess) {
+        d_errs[dev] = nullptr;
         set_error("dcflow_gemm_bf16: allocation of the error word failed");
         return DCFLOW_ERR_OOM;
       }
-      cudaMemset(d_err, 0, sizeof(int));
+      cudaMemset(d_errs[dev], 0, sizeof(int));
     }
+    d_err = d_errs[dev];
   }
   if (!A || !B || !D) {
     set_error("dcflow_gemm_bf16: null operand");

@@ -1331,24 +1331,14 @@ int encode_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
 
 template <int TT, int RMAX, bool OVL = true>
 int launch_tma_t(const N1Maps& maps, const Args& a, dim3 grid, cudaStream_t st, int t0) {
-  static bool attr = false;
+  static uint64_t attr = 0;
   if constexpr (TT >= 4) {  // register-tiled kernel
     using L = RegLayout<TT, RMAX>;
-    if (!attr) {
-      if (cudaFuncSetAttribute(k_n1_reg<TT, RMAX, OVL>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) !=
-          cudaSuccess)
-        return DCFLOW_ERR_CUDA;
-      attr = true;
-    }
+    if (smem_attr_once(k_n1_reg<TT, RMAX, OVL>, L::kBytes, attr) != cudaSuccess) return DCFLOW_ERR_CUDA;
     k_n1_reg<TT, RMAX, OVL><<<grid, RegTile<TT>::NT, L::kBytes, st>>>(maps, a, t0, SelArgs{});
   } else {  // one timestep: one thread per contingency
     using L = TmaLayout<TT, RMAX>;
-    if (!attr) {
-      if (cudaFuncSetAttribute(k_n1_tma<TT, RMAX, 1, OVL>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) !=
-          cudaSuccess)
-        return DCFLOW_ERR_CUDA;
-      attr = true;
-    }
+    if (smem_attr_once(k_n1_tma<TT, RMAX, 1, OVL>, L::kBytes, attr) != cudaSuccess) return DCFLOW_ERR_CUDA;
     k_n1_tma<TT, RMAX, 1, OVL><<<grid, kCB, L::kBytes, st>>>(maps, a, t0);
   }
   return 0;
@@ -1376,13 +1366,8 @@ int launch_tma_r(const N1Maps& maps, const Args& a, int TT, dim3 grid, cudaStrea
 template <int TT, int RMAX>
 int launch_reg_sel_t(const N1Maps& maps, const Args& a, const SelArgs& sel, int items, cudaStream_t st, int t0) {
   using L = RegLayout<TT, RMAX, true>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_n1_reg<TT, RMAX, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) !=
-        cudaSuccess)
-      return DCFLOW_ERR_CUDA;
-    attr = true;
-  }
+  static uint64_t attr = 0;
+  if (smem_attr_once(k_n1_reg<TT, RMAX, true, true>, L::kBytes, attr) != cudaSuccess) return DCFLOW_ERR_CUDA;
   k_n1_reg<TT, RMAX, true, true><<<items, RegTile<TT>::NT, L::kBytes, st>>>(maps, a, t0, sel);
   return 0;
 }
