@@ -43,7 +43,7 @@ WORKLOADS = {
 # profiles/k_n1_reg_grid500.md, keyed by the sha1 of the kernel's source and of
 # its argument block at the time of the capture
 N1_TRAFFIC = {
-    ("251593e01c0a", "fp32"): {"bytes": 1.097e9, "per": "bench step of the 500-bus study (2 launches)",
+    ("a1a5e5fcabd4", "fp32"): {"bytes": 1.095e9, "per": "bench step of the 500-bus study (2 launches)",
                                "how": "1,000-topology capture (626 + 374 topologies) scaled by topologies "
                                       "per rank class to 6,233 + 3,767"},
 }
