@@ -323,3 +323,32 @@ def test_top_cases_match_oracle(precision):
                                                        w.mon, w.cont[c], lim).copy()
                         col[mon == w.cont[c]] = 0.0
                         assert col[l] >= col.max() - 2 * tol * max(1.0, col.max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("which", ["bridges_only", "empty"])
+def test_degenerate_contingency_sets(precision, which):
+    """Contingencies that are all base-grid bridges (no N-1 launch at all) and
+    an empty contingency set: N-0 outputs as usual, no valid N-1 case."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch
+    w = synth.workload(2, n_topo=12, T=2)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    br = oracle.bridges(w.grid.n_bus, w.grid.f, w.grid.t, np.ones(w.grid.n_branch, bool))
+    cont = np.nonzero(br)[0].astype(np.int32)[:40] if which == "bridges_only" else np.zeros(0, np.int32)
+    w.cont = cont
+    s = _solver(w, lim, precision)
+    res = s.solve(DeviceBatch(w.topo, w.inj), want_flows=True, want_cont_max=cont.size > 0,
+                  top_k=3 if cont.size else 0)
+    torch.cuda.synchronize()
+    g = res.to_host()
+    s.close()
+    ref = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, cont, lim, want_flows=True, want_cmax=cont.size > 0)
+    np.testing.assert_array_equal(g["status"], ref["status"])
+    ok = ref["status"] == 0
+    np.testing.assert_array_equal(g["n_island_cont"][ok], ref["n_island_cont"][ok])
+    assert (g["worst_cont"][ok] == -1).all() and (g["n1_max"][ok] == 0).all() and (g["ovl"][ok] == 0).all()
+    tol = TOL[precision]
+    np.testing.assert_allclose(g["n0_max"][ok], ref["n0_max"][ok], rtol=tol, atol=tol)
+    if cont.size:
+        assert (g["cont_max"] == -1).all()
+        assert (g["top_cont"] == -1).all() and (g["top_mon"] == -1).all()
