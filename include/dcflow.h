@@ -170,6 +170,13 @@ typedef struct {
   const int32_t* var_ptr;
   const int32_t* var_bus;
   const double* var_delta;
+  /* generator-failure N-1 (the "N-1 generator" case of Sec. III-A), optional:
+   * generator g sits at bus gen_bus[g] (int32[n_gen]) with output gen_p[t * n_gen + g]
+   * (double[n_time * n_gen]); its failure removes that injection and the slack
+   * takes it up.  n_gen = 0 skips them; not with candidates or the screener. */
+  int32_t n_gen;
+  const int32_t* gen_bus;
+  const double* gen_p;
 } dcflow_batch;
 
 /*
@@ -218,6 +225,10 @@ typedef struct {
   int32_t* top_cont;
   int32_t* top_mon;
   float* top_loading;
+  double* gen_max_loading;   /* [n_topo * n_time] max over generators g and monitored l of
+                                |p_f[l] - P_g PTDF_f[l, bus_g]| / limit (with n_gen > 0) */
+  int32_t* worst_gen;        /* [n_topo * n_time] the generator reaching it (lowest on ties), -1 if none */
+  double* gen_overload_sum;  /* [n_topo * n_time] sum of max(0, rho - 1) over the same cases */
 } dcflow_results;
 
 /*

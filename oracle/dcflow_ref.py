@@ -545,3 +545,49 @@ def topology_flows(grid, splits, outages, P):
     Pn = np.zeros((n,) + P.shape[1:])
     Pn[:grid.n_bus] = P
     return _flows_from_angles(fac.solve_full(Pn), f2, t2, grid.b, alive), (OK, n, f2, t2, alive)
+
+
+def generator_n1(grid, topo, P, gen_bus, gen_p, mon, limit, idx=None):
+    """Generator-failure N-1 (the "N-1 generator" case of the injection module,
+    Sec. III-A): generator g at bus gen_bus[g] with output gen_p[t, g] fails and
+    the slack takes up its output.  Per topology the split/outaged graph is
+    rebuilt and factored, and the flows of P[t] - gen_p[t, g] e_{gen_bus[g]}
+    are solved for every (t, g).  Returns per topology and timestep the maximum
+    loading over generators and monitored branches, the failing generator that
+    reaches it (lowest index on ties; -1 if none), the overload sum and every
+    generator's own maximum (gen_each [T, G]), plus the topology status."""
+    P = np.atleast_2d(np.asarray(P, np.float64))
+    gp = np.atleast_2d(np.asarray(gen_p, np.float64))
+    gb = np.asarray(gen_bus, np.int64)
+    mon = np.asarray(mon, np.int64)
+    lim = np.asarray(limit, np.float64)[mon]
+    T, G = P.shape[0], gb.size
+    ids = range(topo.n_topo) if idx is None else [int(i) for i in idx]
+    out = {k: [] for k in ("gen_max", "worst_gen", "gen_ovl", "gen_each", "status")}
+    for i in ids:
+        a, c = topo.split_ptr[i], topo.split_ptr[i + 1]
+        splits = list(zip(topo.split_sub[a:c], topo.split_mask[a:c]))
+        a, c = topo.out_ptr[i], topo.out_ptr[i + 1]
+        outages = list(topo.out_branch[a:c])
+        gm, wg, go, ge = np.zeros(T), -np.ones(T, np.int64), np.zeros(T), np.zeros((T, G))
+        fl0, info = topology_flows(grid, splits, outages, P.T)
+        st = info[0]
+        if fl0 is not None and G:
+            # injections minus each generator's output, column (t, g) = P[t] - gp[t, g] e_b
+            rhs = np.repeat(P.T[:, :, None], G, axis=2)  # [V, T, G]
+            for g in range(G):
+                rhs[gb[g], :, g] -= gp[:, g]
+            fl, _ = topology_flows(grid, splits, outages, rhs.reshape(grid.n_bus, T * G))
+            rho = np.abs(fl[mon].reshape(mon.size, T, G)) / lim[:, None, None]  # [M, T, G]
+            for t in range(T):
+                per_g = rho[:, t, :].max(axis=0)
+                ge[t] = per_g
+                g = int(np.argmax(per_g))
+                gm[t], wg[t] = per_g[g], g
+                go[t] = float(np.maximum(rho[:, t, :] - 1.0, 0.0).sum())
+        out["gen_max"].append(gm)
+        out["worst_gen"].append(wg)
+        out["gen_ovl"].append(go)
+        out["gen_each"].append(ge)
+        out["status"].append(st)
+    return {k: np.asarray(v) for k, v in out.items()}

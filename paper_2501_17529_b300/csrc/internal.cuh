@@ -124,6 +124,7 @@ struct dcflow_ctx {
   dcf::DevBuf dp;          // double[NN*U] base flow change of each candidate
   dcf::DevBuf rank, status, perm, hist, hist_host;
   dcf::DevBuf cm_scratch;  // float[N*T*C] per-contingency maxima for the top-k pass when not requested
+  dcf::DevBuf gen_cols;    // Real[G*M] PTDF[mon, gen_bus] / limit of the batch's generators
   dcf::ChunkBufs bufs[2];
   cudaStream_t side = nullptr;           // preparation stream (created on first use)
   cudaEvent_t ev_ready = nullptr, ev_prep[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};

@@ -1195,6 +1195,97 @@ __global__ __launch_bounds__(128) void k_topcases(Args a, const float* __restric
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// generator-failure N-1 (the "N-1 generator" case of Sec. III-A): generator g
+// at bus b with output P_g[t] fails, the slack takes it up, and the flows
+// become p_f - P_g PTDF_f[:, b].  The topology's PTDF column follows from the
+// same rank-r update as p_f from p0 (Eq. (3)):
+//   PTDF_f[l, b] = PTDF[l, b] - Z[l, :] K^{-1} Sigma^T PTDF[:, b]
+// One warp per (topology, timestep): max over generators and monitored
+// branches of |flow| / limit, the generator reaching it (lowest on ties), and
+// the overload sum.
+// ---------------------------------------------------------------------------
+// PTDF[mon, gen_bus] / limit, one row per generator (once per solve)
+template <class Real>
+__global__ void k_gen_cols(int G, int M, int V, const int* __restrict__ gen_bus, const int* __restrict__ monN,
+                           const double* __restrict__ PtdfN, const double* __restrict__ inv_lim, Real* __restrict__ PG) {
+  const int g = blockIdx.y;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x)
+    PG[(size_t)g * M + l] = (Real)(PtdfN[(size_t)monN[l] * V + gen_bus[g]] * inv_lim[l]);
+}
+
+template <class Real, int RMAX>
+__global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __restrict__ gen_bus,
+                                                 const double* __restrict__ gen_p, const double* __restrict__ PtdfN,
+                                                 int V, const Real* __restrict__ PG) {
+  __shared__ EntSmem S;
+  const int q = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const QInfo qi = a.qi[q];
+  const int T = a.T, M = a.M, Mp = a.Mpad, tau = qi.tau;
+  const int t = blockIdx.y * 4 + w;
+  const dcflow_results& o = a.out;
+  if (qi.status != ST_OK) {
+    if (t < T && lane == 0) {
+      o.gen_max_loading[(size_t)tau * T + t] = 0.0;
+      o.worst_gen[(size_t)tau * T + t] = -1;
+      o.gen_overload_sum[(size_t)tau * T + t] = 0.0;
+    }
+    return;
+  }
+  const int r = qi.r;
+  load_entries(S, a, q, r);  // block-wide (contains a barrier)
+  if (t >= T) return;
+  const double* Kinv = a.Kinv + (size_t)q * kRMax * kRMax;
+  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
+  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
+  const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
+  double best = -1.0, ovl = 0.0;
+  int arg = 0x7fffffff;
+  for (int g = 0; g < G; ++g) {
+    const int b = gen_bus[g];
+    // Sigma^T PTDF[:, b] in lane i < r, then beta = K^{-1} (Sigma^T PTDF[:, b]) in every lane
+    double sv = 0.0;
+    if (lane < r)
+      for (int e = S.mp[lane]; e < S.mp[lane + 1]; ++e) sv = fma((double)S.es[e], PtdfN[(size_t)S.en[e] * V + b], sv);
+    Real beta[RMAX];
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) {
+      double x = 0.0;
+#pragma unroll
+      for (int i = 0; i < RMAX; ++i) x = fma(Kinv[j * kRMax + i], __shfl_sync(0xffffffffu, sv, i), x);
+      beta[j] = (Real)x;
+    }
+    const Real pg = (Real)gen_p[(size_t)t * G + g];
+    for (int l = lane; l < M; l += 32) {
+      Real col = PG[(size_t)g * M + l];
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) col = fma(-Zs[(size_t)j * Mp + l], beta[j], col);
+      col *= meta[Mp + l];  // an outaged monitored branch carries nothing
+      const double x = (double)fabs(fma(-pg, col, ptil[(size_t)t * Mp + l]));
+      if (x > best) {
+        best = x;
+        arg = g;
+      }
+      ovl += fmax(x - 1.0, 0.0);
+    }
+  }
+  for (int off = 16; off; off >>= 1) {
+    const double b2 = __shfl_xor_sync(0xffffffffu, best, off);
+    const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
+    ovl += __shfl_xor_sync(0xffffffffu, ovl, off);
+    if (b2 > best || (b2 == best && a2 < arg)) {
+      best = b2;
+      arg = a2;
+    }
+  }
+  if (lane == 0) {
+    o.gen_max_loading[(size_t)tau * T + t] = G ? best : 0.0;
+    o.worst_gen[(size_t)tau * T + t] = G ? arg : -1;
+    o.gen_overload_sum[(size_t)tau * T + t] = ovl;
+  }
+}
+
 }  // namespace dcf
 
 #include "n1_reg.cuh"
@@ -1272,6 +1363,16 @@ void launch_topcases(const Args& a, int RMAX, const float* cmax, const int* cinv
   if (RMAX == 4) launch_topcases_r<Real, 4>(a, cmax, cinv, phicm, k, st);
   else if (RMAX == 8) launch_topcases_r<Real, 8>(a, cmax, cinv, phicm, k, st);
   else launch_topcases_r<Real, 16>(a, cmax, cinv, phicm, k, st);
+}
+
+template <class Real>
+void launch_gen(const Args& a, int RMAX, int G, const int* gen_bus, const double* gen_p, const double* ptdf, int V,
+                const void* pg, cudaStream_t st) {
+  const dim3 grid(a.nq, (a.T + 3) / 4);
+  const Real* P = static_cast<const Real*>(pg);
+  if (RMAX == 4) k_gen_n1<Real, 4><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
+  else if (RMAX == 8) k_gen_n1<Real, 8><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
+  else k_gen_n1<Real, 16><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
 }
 
 int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
@@ -1507,6 +1608,13 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
               "not with the screened solve");
     return DCFLOW_ERR_INVALID_ARG;
   }
+  const int G = mode == kModeFull ? bt->n_gen : 0;
+  if (bt->n_gen < 0 || (bt->n_gen > 0 && (mode != kModeFull || U > 0 || !bt->gen_bus || !bt->gen_p ||
+                                          !res->gen_max_loading || !res->worst_gen || !res->gen_overload_sum))) {
+    set_error("dcflow_solve_batch: generator failures need gen_bus, gen_p and the three generator outputs, "
+              "without injection candidates or the screener");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
   if (mode != kModeFull && U > 0) {
     set_error("dcflow_solve_batch: the screener runs without injection candidates");
     return DCFLOW_ERR_INVALID_ARG;
@@ -1661,6 +1769,26 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     DCF_CHECK_LAUNCH();
     ++ctx->launches;
     ctx->phicm_ready = true;
+  }
+  if (G > 0) {  // generator buses in range; base PTDF columns of the monitored rows, scaled by 1 / limit
+    std::vector<int> gb(G);
+    DCF_CUDA(cudaMemcpyAsync(gb.data(), bt->gen_bus, sizeof(int) * G, cudaMemcpyDeviceToHost, st));
+    DCF_CUDA(cudaStreamSynchronize(st));
+    for (int g = 0; g < G; ++g)
+      if (gb[g] < 0 || gb[g] >= ctx->V) {
+        set_error("dcflow_solve_batch: gen_bus out of range");
+        return DCFLOW_ERR_INVALID_ARG;
+      }
+    if (ctx->gen_cols.ensure((size_t)G * std::max(M, 1) * rs)) return DCFLOW_ERR_OOM;
+    const dim3 grd((M + 255) / 256, G);
+    if (fp64)
+      k_gen_cols<double><<<grd, 256, 0, st>>>(G, M, ctx->V, bt->gen_bus, ctx->monN.as<int>(), ctx->PtdfN.as<double>(),
+                                              ctx->inv_lim.as<double>(), ctx->gen_cols.as<double>());
+    else
+      k_gen_cols<float><<<grd, 256, 0, st>>>(G, M, ctx->V, bt->gen_bus, ctx->monN.as<int>(), ctx->PtdfN.as<double>(),
+                                             ctx->inv_lim.as<double>(), ctx->gen_cols.as<float>());
+    DCF_CHECK_LAUNCH();
+    ++ctx->launches;
   }
   ctx->chunk_cap = cap;
   if (!ctx->side) {
@@ -1944,6 +2072,14 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     else launch_final<float>(af, RMAX, st, ctx->PhiCM.p, nsel_dev);
     ++ctx->launches;
     DCF_CHECK_LAUNCH();
+    if (G > 0) {
+      if (fp64)
+        launch_gen<double>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V, ctx->gen_cols.p, st);
+      else
+        launch_gen<float>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V, ctx->gen_cols.p, st);
+      ++ctx->launches;
+      DCF_CHECK_LAUNCH();
+    }
     if (top_k > 0) {
       if (fp64)
         launch_topcases<double>(af, RMAX, af.out.n1_cont_max, ctx->cont_inv.as<int>(), ctx->PhiCM.p, top_k, st);

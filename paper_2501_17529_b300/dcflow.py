@@ -37,7 +37,8 @@ class Batch(ctypes.Structure):
     _fields_ = [("n_topo", c_int32), ("split_ptr", c_void_p), ("split_sub", c_void_p),
                 ("split_mask", c_void_p), ("out_ptr", c_void_p), ("out_branch", c_void_p),
                 ("n_time", c_int32), ("inj", c_void_p), ("n_var", c_int32),
-                ("var_ptr", c_void_p), ("var_bus", c_void_p), ("var_delta", c_void_p)]
+                ("var_ptr", c_void_p), ("var_bus", c_void_p), ("var_delta", c_void_p),
+                ("n_gen", c_int32), ("gen_bus", c_void_p), ("gen_p", c_void_p)]
 
 
 class Results(ctypes.Structure):
@@ -45,7 +46,8 @@ class Results(ctypes.Structure):
                 ("overload_sum", c_void_p), ("worst_cont", c_void_p), ("worst_mon", c_void_p),
                 ("best_var", c_void_p), ("island_flag", c_void_p), ("n_island_cont", c_void_p),
                 ("n1_cont_max", c_void_p), ("top_k", c_int32), ("top_cont", c_void_p), ("top_mon", c_void_p),
-                ("top_loading", c_void_p)]
+                ("top_loading", c_void_p), ("gen_max_loading", c_void_p), ("worst_gen", c_void_p),
+                ("gen_overload_sum", c_void_p)]
 
 
 class ScreenOptions(ctypes.Structure):
@@ -358,7 +360,7 @@ def dcflow_strerror(code: int) -> str:
 class DeviceBatch:
     """Device copies of the topology CSR, injections and optional candidates."""
 
-    def __init__(self, topo, inj, var=None, device="cuda"):
+    def __init__(self, topo, inj, var=None, device="cuda", gen_bus=None, gen_p=None):
         import torch
         self.n_topo = int(topo.n_topo)
         self.n_time = int(np.atleast_2d(inj).shape[0])
@@ -375,18 +377,25 @@ class DeviceBatch:
             self.var_delta = torch.as_tensor(np.asarray(var.var_delta, np.float64), device=device)
         else:
             self.var_ptr = self.var_bus = self.var_delta = None
+        self.n_gen = 0 if gen_bus is None else int(np.asarray(gen_bus).size)
+        if self.n_gen:
+            self.gen_bus = torch.as_tensor(np.asarray(gen_bus, np.int32), device=device)
+            self.gen_p = torch.as_tensor(np.ascontiguousarray(np.atleast_2d(gen_p), np.float64), device=device)
+        else:
+            self.gen_bus = self.gen_p = None
 
     def cstruct(self) -> Batch:
         return Batch(self.n_topo, _ptr(self.split_ptr), _ptr(self.split_sub), _ptr(self.split_mask),
                      _ptr(self.out_ptr), _ptr(self.out_branch), self.n_time, _ptr(self.inj), self.n_var,
-                     _ptr(self.var_ptr), _ptr(self.var_bus), _ptr(self.var_delta))
+                     _ptr(self.var_ptr), _ptr(self.var_bus), _ptr(self.var_delta), self.n_gen,
+                     _ptr(self.gen_bus), _ptr(self.gen_p))
 
 
 class DeviceResults:
     """Caller-owned device outputs of one batch."""
 
     def __init__(self, n_topo, n_time, n_mon, want_flows=False, want_var=False, device="cuda", n_cont=0,
-                 want_cont_max=False, top_k=0):
+                 want_cont_max=False, top_k=0, want_gen=False):
         import torch
         nt = max(1, n_topo * n_time)
         self.n0_flow = torch.empty(max(1, n_topo * n_time * n_mon), dtype=torch.float64, device=device) if want_flows else None
@@ -405,6 +414,9 @@ class DeviceResults:
         self.top_cont = torch.empty(nk, dtype=torch.int32, device=device) if top_k else None
         self.top_mon = torch.empty(nk, dtype=torch.int32, device=device) if top_k else None
         self.top_loading = torch.empty(nk, dtype=torch.float32, device=device) if top_k else None
+        self.gen_max_loading = torch.empty(nt, dtype=torch.float64, device=device) if want_gen else None
+        self.worst_gen = torch.empty(nt, dtype=torch.int32, device=device) if want_gen else None
+        self.gen_overload_sum = torch.empty(nt, dtype=torch.float64, device=device) if want_gen else None
         self.shape = (n_topo, n_time, n_mon)
         self.n_cont = n_cont
 
@@ -413,7 +425,8 @@ class DeviceResults:
                        _ptr(self.overload_sum), _ptr(self.worst_cont), _ptr(self.worst_mon),
                        _ptr(self.best_var), _ptr(self.island_flag), _ptr(self.n_island_cont),
                        _ptr(self.n1_cont_max), self.top_k, _ptr(self.top_cont), _ptr(self.top_mon),
-                       _ptr(self.top_loading))
+                       _ptr(self.top_loading), _ptr(self.gen_max_loading), _ptr(self.worst_gen),
+                       _ptr(self.gen_overload_sum))
 
     def to_host(self) -> dict:
         N, T, M = self.shape
@@ -432,6 +445,10 @@ class DeviceResults:
             out["n0_flow"] = self.n0_flow[:N * T * M].cpu().numpy().reshape(N, T, M)
         if self.n1_cont_max is not None:
             out["cont_max"] = self.n1_cont_max[:N * T * self.n_cont].cpu().numpy().reshape(N, T, self.n_cont)
+        if self.gen_max_loading is not None:
+            out["gen_max"] = self.gen_max_loading[:N * T].cpu().numpy().reshape(N, T)
+            out["worst_gen"] = self.worst_gen[:N * T].cpu().numpy().reshape(N, T).astype(np.int64)
+            out["gen_ovl"] = self.gen_overload_sum[:N * T].cpu().numpy().reshape(N, T)
         if self.top_k:
             k = self.top_k
             out["top_cont"] = self.top_cont[:N * T * k].cpu().numpy().reshape(N, T, k).astype(np.int64)
@@ -465,7 +482,8 @@ class Solver:
     def solve(self, dbatch: DeviceBatch, want_flows=False, results: DeviceResults | None = None, stream=None,
               want_cont_max=False, top_k=0):
         res = results or DeviceResults(dbatch.n_topo, dbatch.n_time, self.n_mon, want_flows, dbatch.n_var > 0,
-                                       n_cont=self.n_cont, want_cont_max=want_cont_max, top_k=top_k)
+                                       n_cont=self.n_cont, want_cont_max=want_cont_max, top_k=top_k,
+                                       want_gen=dbatch.n_gen > 0)
         dcflow_solve_batch(self.ctx, dbatch.cstruct(), res.cstruct(), stream)
         return res
 

@@ -352,3 +352,30 @@ def test_degenerate_contingency_sets(precision, which):
     if cont.size:
         assert (g["cont_max"] == -1).all()
         assert (g["top_cont"] == -1).all() and (g["top_mon"] == -1).all()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_generator_failures_match_oracle(precision):
+    """Generator-failure N-1 against refactorisation with each generator's output removed."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch
+    w = synth.workload(2, n_topo=14, T=3)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    rng = np.random.default_rng(61)
+    gb = np.sort(rng.choice(np.arange(1, w.grid.n_bus), 9, replace=False)).astype(np.int32)
+    gp = np.abs(rng.normal(1.0, 0.5, (3, 9)))
+    s = _solver(w, lim, precision)
+    g = s.solve(DeviceBatch(w.topo, w.inj, gen_bus=gb, gen_p=gp)).to_host()
+    s.close()
+    ref = oracle.generator_n1(w.grid, w.topo, w.inj, gb, gp, w.mon, lim)
+    tol = TOL[precision]
+    ok = ref["status"] == 0
+    np.testing.assert_array_equal(g["status"], ref["status"])
+    np.testing.assert_allclose(g["gen_max"][ok], ref["gen_max"][ok], rtol=tol, atol=tol)
+    d = np.abs(g["gen_ovl"][ok] - ref["gen_ovl"][ok]) / np.maximum(ref["gen_ovl"][ok], 1.0)
+    assert d.max() <= tol
+    for i in np.nonzero(ok)[0]:
+        for t in range(3):
+            wg = g["worst_gen"][i, t]
+            assert wg == ref["worst_gen"][i, t] or \
+                ref["gen_each"][i, t, wg] >= ref["gen_max"][i, t] - 2 * tol * max(1.0, ref["gen_max"][i, t])
+    assert (g["worst_gen"][~ok] == -1).all()

@@ -500,3 +500,29 @@ def test_top_cases_k1_is_the_worst_case_and_k3_matches_refactorisation():
                 col[mon_pos] = 0.0  # the outaged branch itself carries nothing
                 assert l3[i, t, j] == pytest.approx(col.max(), rel=1e-9)
                 assert col[m3[i, t, j]] == pytest.approx(col.max(), rel=1e-9)
+
+
+def test_generator_n1_closed_forms():
+    """Generator-failure N-1: a generator with zero output changes nothing (the
+    maximum is the N-0 loading), and on the unsplit grid the flows follow
+    p0 - P_g PTDF[:, b] (Eq. (3), the slack column being zero)."""
+    from paper_2501_17529_b300 import synth
+    w = synth.workload(2, n_topo=4, T=2)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    gb = np.array([3, 17, 40])
+    r0 = oracle.generator_n1(w.grid, w.topo, w.inj, gb, np.zeros((2, 3)), w.mon, lim)
+    ev = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim)
+    ok = ev["status"] == 0
+    np.testing.assert_allclose(r0["gen_max"][ok], ev["n0_max"][ok], rtol=1e-12)
+    assert (r0["worst_gen"][ok] == 0).all()  # all equal: the lowest index
+    empty = synth.Topologies(np.zeros(2, np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint64),
+                             np.zeros(2, np.int32), np.zeros(0, np.int32))
+    gp = np.array([[0.7, 1.3, 0.4], [0.9, 1.1, 0.2]])
+    r = oracle.generator_n1(w.grid, empty, w.inj, gb, gp, w.mon, lim)
+    ptdf = oracle.ptdf(w.grid.n_bus, w.grid.f, w.grid.t, w.grid.b, w.grid.slack)
+    p0 = w.inj @ ptdf.T  # [T, E]
+    for t in range(2):
+        rho = np.abs(p0[t][:, None] - gp[t][None, :] * ptdf[:, gb]) / lim[:, None]
+        assert r["gen_max"][0, t] == pytest.approx(rho.max(), rel=1e-10)
+        assert r["worst_gen"][0, t] == int(np.argmax(rho.max(axis=0)))
+        assert r["gen_ovl"][0, t] == pytest.approx(np.maximum(rho - 1, 0).sum(), rel=1e-9, abs=1e-12)
