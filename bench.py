@@ -326,6 +326,54 @@ def run_ours(args):
         # end to end through host buffers: H2D of the batch, solve, D2H of the results
         if form == "fp32" and not args.no_e2e:
             results[form]["e2e"] = _e2e(solver, w, lim, steps, args.warmup, lf)
+        # the same solve with the sparse worst results (agg_i, top k per topology and timestep)
+        if form == "fp32" and args.top_k > 0:
+            rk = DeviceResults(db.n_topo, db.n_time, len(w.mon), want_var=db.n_var > 0, top_k=args.top_k)
+            for _ in range(args.warmup):
+                solver.solve(db, results=rk)
+            torch.cuda.synchronize()
+            evk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k2 in range(steps):
+                flush.fill_(k2 & 0xFF)
+                evk[k2][0].record(stream)
+                solver.solve(db, results=rk)
+                evk[k2][1].record(stream)
+            torch.cuda.synchronize()
+            tk = sum(a.elapsed_time(b) for a, b in evk) / 1e3
+            if ws > 1:
+                tk, _ = reduce_over_ranks(tk, lf, "cuda")
+            results[f"fp32_top{args.top_k}"] = {"value": lf_all * steps / tk, "ms_per_step": 1e3 * tk / steps,
+                                                "loadflows_per_step": lf_all, "steps": steps,
+                                                "note": f"fp32 solve plus the {args.top_k} worst N-1 cases "
+                                                        "(contingency, monitored branch, loading) per topology "
+                                                        "and timestep"}
+        # the same solve with generator-failure N-1 cases (16 generators at seeded buses)
+        if form == "fp32" and args.gens > 0:
+            rng = np.random.default_rng(700)
+            gb = np.sort(rng.choice(np.arange(1, w.grid.n_bus), args.gens, replace=False)).astype(np.int32)
+            gp = np.abs(rng.normal(1.0, 0.5, (T_STEPS, args.gens)))
+            dbg = DeviceBatch(w.topo, w.inj, w.var, gen_bus=gb, gen_p=gp)
+            rg = DeviceResults(db.n_topo, db.n_time, len(w.mon), want_var=db.n_var > 0, want_gen=True)
+            for _ in range(args.warmup):
+                solver.solve(dbg, results=rg)
+            torch.cuda.synchronize()
+            evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k2 in range(steps):
+                flush.fill_(k2 & 0xFF)
+                evg[k2][0].record(stream)
+                solver.solve(dbg, results=rg)
+                evg[k2][1].record(stream)
+            torch.cuda.synchronize()
+            tg = sum(a.elapsed_time(b) for a, b in evg) / 1e3
+            if ws > 1:
+                tg, _ = reduce_over_ranks(tg, lf, "cuda")
+            ngen_cases = int((rg.island_flag[:db.n_topo] == 0).sum().item()) * T_STEPS * args.gens * ws
+            results[f"fp32_gen{args.gens}"] = {"value": lf_all * steps / tg, "ms_per_step": 1e3 * tg / steps,
+                                               "loadflows_per_step": lf_all,
+                                               "generator_cases_per_step": ngen_cases, "steps": steps,
+                                               "note": f"fp32 solve plus {args.gens} generator-failure N-1 cases "
+                                                       "per topology and timestep (value counts the branch "
+                                                       "N-1 cases only)"}
         results[form]["setup_s"] = setup_s
         solver.close()
     if rank != 0:
@@ -428,6 +476,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--topologies", type=int, default=0, help="batch size (0 = the workload's own)")
     ap.add_argument("--workload", default="grid500", choices=sorted(WORKLOADS))
+    ap.add_argument("--gens", type=int, default=16,
+                    help="also time the FP32 solve with this many generator-failure cases; 0 = skip")
+    ap.add_argument("--top-k", type=int, default=8,
+                    help="also time the FP32 solve with the k worst N-1 cases per (topology, timestep); 0 = skip")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

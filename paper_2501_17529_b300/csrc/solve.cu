@@ -679,6 +679,7 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       double v = -1.0;
       int arg = 0x7fffffff;
       if (c >= 0) {
+        Real vr = (Real)-1;
         Real vt[RMAX];
 #pragma unroll
         for (int j = 0; j < RMAX; ++j) vt[j] = VtR[(size_t)j * C + c];
@@ -688,12 +689,13 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
 #pragma unroll
           for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
           const Real ph = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
-          const double x = (double)fabs(fma(ph, st, ptil[(size_t)t * Mp + l]));
-          if (x > v) {
-            v = x;
+          const Real x = fabs(fma(ph, st, ptil[(size_t)t * Mp + l]));
+          if (x > vr) {
+            vr = x;
             arg = l;
           }
         }
+        v = (double)vr;
       }
       for (int off = 16; off; off >>= 1) {
         const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
@@ -1101,6 +1103,7 @@ __global__ __launch_bounds__(128) void k_topcases(Args a, const float* __restric
                                                    int k) {
   __shared__ float sv_[4][64];
   __shared__ int sp_[4][64];
+  __shared__ Real vts[4][8][RMAX];  // Vt columns of the 8 cases of a pass, per warp
   __shared__ float ov_[4][64];
   __shared__ int op_[4][64];
   const int q = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1155,42 +1158,64 @@ __global__ __launch_bounds__(128) void k_topcases(Args a, const float* __restric
   const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
   const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
   const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
-  for (int j = 0; j < k; ++j) {
-    const bool valid = j < kk && ov_[w][j] >= 0.f;
-    int l_best = -1;
-    if (valid) {  // its most loaded monitored branch: the column recomputed as in the N-1 kernel
-      const int c = cont_inv[op_[w][j]];
-      Real vt[RMAX];
+  // the most loaded monitored branch of every case: the columns recomputed as in
+  // the N-1 kernel, 8 cases per pass over the rows (the row operands are shared)
+  constexpr int KG = 8;
+  for (int j0 = 0; j0 < k; j0 += KG) {
+    int cj[KG];
+    Real stj[KG], vr[KG];
+    int arg[KG];
 #pragma unroll
-      for (int jj = 0; jj < RMAX; ++jj) vt[jj] = VtR[(size_t)jj * C + c];
-      const Real st = sv[(size_t)t * C + c];
-      double v = -1.0;
-      int arg = 0x7fffffff;
-      for (int l = lane; l < M; l += 32) {
-        Real zr[RMAX];
+    for (int g = 0; g < KG; ++g) {
+      const int j = j0 + g;
+      const bool valid = j < kk && ov_[w][j] >= 0.f;
+      cj[g] = valid ? cont_inv[op_[w][j]] : -1;
+      stj[g] = cj[g] >= 0 ? sv[(size_t)t * C + cj[g]] : (Real)0;
+      vr[g] = (Real)-1;
+      arg[g] = 0x7fffffff;
+    }
+    __syncwarp();
+    for (int p = lane; p < KG * RMAX; p += 32) {
+      const int g = p / RMAX, jj = p % RMAX;
+      vts[w][g][jj] = cj[g] >= 0 ? VtR[(size_t)jj * C + cj[g]] : (Real)0;
+    }
+    __syncwarp();
+    for (int l = lane; l < M; l += 32) {
+      Real zr[RMAX];
 #pragma unroll
-        for (int jj = 0; jj < RMAX; ++jj) zr[jj] = Zs[(size_t)jj * Mp + l];
-        const Real ph = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
-        const double x = (double)fabs(fma(ph, st, ptil[(size_t)t * Mp + l]));
-        if (x > v) {
-          v = x;
-          arg = l;
+      for (int jj = 0; jj < RMAX; ++jj) zr[jj] = Zs[(size_t)jj * Mp + l];
+      const Real pt = ptil[(size_t)t * Mp + l], rm = meta[Mp + l], dg = meta[l];
+      const int cp = a.cpos[l];
+#pragma unroll
+      for (int g = 0; g < KG; ++g) {
+        if (cj[g] < 0) continue;
+        const Real ph = phi_entry<Real, RMAX>(PhiCM[(size_t)cj[g] * Mp + l], zr, vts[w][g], rm, cp, cj[g], dg);
+        const Real x = fabs(fma(ph, stj[g], pt));
+        if (x > vr[g]) {
+          vr[g] = x;
+          arg[g] = l;
         }
       }
+    }
+#pragma unroll
+    for (int g = 0; g < KG; ++g) {
+      double v = (double)vr[g];
+      int ar = arg[g];
       for (int off2 = 16; off2; off2 >>= 1) {
         const double v2 = __shfl_xor_sync(0xffffffffu, v, off2);
-        const int a2 = __shfl_xor_sync(0xffffffffu, arg, off2);
-        if (v2 > v || (v2 == v && a2 < arg)) {
+        const int a2 = __shfl_xor_sync(0xffffffffu, ar, off2);
+        if (v2 > v || (v2 == v && a2 < ar)) {
           v = v2;
-          arg = a2;
+          ar = a2;
         }
       }
-      l_best = arg;
-    }
-    if (lane == 0) {
-      o.top_cont[ob + j] = valid ? op_[w][j] : -1;
-      o.top_mon[ob + j] = valid ? l_best : -1;
-      o.top_loading[ob + j] = valid ? ov_[w][j] : 0.f;
+      const int j = j0 + g;
+      if (lane == 0 && j < k) {
+        const bool valid = cj[g] >= 0;
+        o.top_cont[ob + j] = valid ? op_[w][j] : -1;
+        o.top_mon[ob + j] = valid ? ar : -1;
+        o.top_loading[ob + j] = valid ? ov_[w][j] : 0.f;
+      }
     }
   }
 }
@@ -1215,18 +1240,26 @@ __global__ void k_gen_cols(int G, int M, int V, const int* __restrict__ gen_bus,
     PG[(size_t)g * M + l] = (Real)(PtdfN[(size_t)monN[l] * V + gen_bus[g]] * inv_lim[l]);
 }
 
-template <class Real, int RMAX>
+// One block per topology; thread i owns monitored rows i, i + 128, ...: per
+// row its p_f over TT timesteps and its Z row are loaded once, and each
+// generator's column entry (independent of t) is formed once and applied to
+// every timestep; per-timestep (max, generator, overload) accumulators live in
+// registers until one block reduction per timestep.
+template <class Real, int RMAX, int TT>
 __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __restrict__ gen_bus,
                                                  const double* __restrict__ gen_p, const double* __restrict__ PtdfN,
-                                                 int V, const Real* __restrict__ PG) {
+                                                 int V, const Real* __restrict__ PG, int t0) {
   __shared__ EntSmem S;
-  const int q = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ Real beta_s[64][RMAX];  // K^{-1} Sigma^T PTDF[:, bus_g], up to 64 generators per round
+  __shared__ Real pg_s[TT][64];      // their outputs over this pass's timesteps
+  __shared__ double rv[4], ro[4];
+  __shared__ int ra[4];
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const QInfo qi = a.qi[q];
   const int T = a.T, M = a.M, Mp = a.Mpad, tau = qi.tau;
-  const int t = blockIdx.y * 4 + w;
   const dcflow_results& o = a.out;
   if (qi.status != ST_OK) {
-    if (t < T && lane == 0) {
+    for (int t = t0 + tid; t < T && t < t0 + TT; t += blockDim.x) {
       o.gen_max_loading[(size_t)tau * T + t] = 0.0;
       o.worst_gen[(size_t)tau * T + t] = -1;
       o.gen_overload_sum[(size_t)tau * T + t] = 0.0;
@@ -1235,54 +1268,98 @@ __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __rest
   }
   const int r = qi.r;
   load_entries(S, a, q, r);  // block-wide (contains a barrier)
-  if (t >= T) return;
   const double* Kinv = a.Kinv + (size_t)q * kRMax * kRMax;
   const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
   const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
   const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
-  double best = -1.0, ovl = 0.0;
-  int arg = 0x7fffffff;
-  for (int g = 0; g < G; ++g) {
-    const int b = gen_bus[g];
-    // Sigma^T PTDF[:, b] in lane i < r, then beta = K^{-1} (Sigma^T PTDF[:, b]) in every lane
-    double sv = 0.0;
-    if (lane < r)
-      for (int e = S.mp[lane]; e < S.mp[lane + 1]; ++e) sv = fma((double)S.es[e], PtdfN[(size_t)S.en[e] * V + b], sv);
-    Real beta[RMAX];
+  Real mx[TT], ov[TT];  // working precision per entry (FP32 form: overload via the saturating FMA, x 2^-20)
+  int ag[TT];
 #pragma unroll
-    for (int j = 0; j < RMAX; ++j) {
+  for (int j = 0; j < TT; ++j) {
+    mx[j] = (Real)-1;
+    ov[j] = (Real)0;
+    ag[j] = 0x7fffffff;
+  }
+  for (int g0 = 0; g0 < G; g0 += 64) {
+    const int gn = min(64, G - g0);
+    __syncthreads();
+    for (int p = tid; p < gn * RMAX; p += blockDim.x) {  // beta of generator g0 + p / RMAX, component p % RMAX
+      const int g = p / RMAX, j = p % RMAX, b = gen_bus[g0 + g];
       double x = 0.0;
-#pragma unroll
-      for (int i = 0; i < RMAX; ++i) x = fma(Kinv[j * kRMax + i], __shfl_sync(0xffffffffu, sv, i), x);
-      beta[j] = (Real)x;
-    }
-    const Real pg = (Real)gen_p[(size_t)t * G + g];
-    for (int l = lane; l < M; l += 32) {
-      Real col = PG[(size_t)g * M + l];
-#pragma unroll
-      for (int j = 0; j < RMAX; ++j) col = fma(-Zs[(size_t)j * Mp + l], beta[j], col);
-      col *= meta[Mp + l];  // an outaged monitored branch carries nothing
-      const double x = (double)fabs(fma(-pg, col, ptil[(size_t)t * Mp + l]));
-      if (x > best) {
-        best = x;
-        arg = g;
+      for (int i = 0; i < r; ++i) {
+        double sv = 0.0;
+        for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) sv = fma((double)S.es[e], PtdfN[(size_t)S.en[e] * V + b], sv);
+        x = fma(Kinv[j * kRMax + i], sv, x);
       }
-      ovl += fmax(x - 1.0, 0.0);
+      beta_s[g][j] = (Real)x;
+    }
+    for (int p = tid; p < TT * 64; p += blockDim.x) {
+      const int j = p / 64, g = p % 64;
+      pg_s[j][g] = (g < gn && t0 + j < T) ? (Real)gen_p[(size_t)(t0 + j) * G + g0 + g] : (Real)0;
+    }
+    __syncthreads();
+    for (int l = tid; l < M; l += blockDim.x) {
+      Real zr[RMAX], pt[TT];
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
+#pragma unroll
+      for (int j = 0; j < TT; ++j) pt[j] = (t0 + j < T) ? ptil[(size_t)(t0 + j) * Mp + l] : (Real)0;
+      const Real rm = meta[Mp + l];  // an outaged monitored branch carries nothing
+      for (int g = 0; g < gn; ++g) {
+        Real col = PG[(size_t)(g0 + g) * M + l];
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) col = fma(-zr[j], beta_s[g][j], col);
+        col *= rm;
+#pragma unroll
+        for (int j = 0; j < TT; ++j) {
+          const Real v = fma(-pg_s[j][g], col, pt[j]);
+          if (fabs(v) > mx[j]) {
+            mx[j] = fabs(v);
+            ag[j] = g0 + g;
+          }
+          Real dummy = (Real)0;
+          Acc<Real>::add(dummy, ov[j], v);
+        }
+      }
     }
   }
-  for (int off = 16; off; off >>= 1) {
-    const double b2 = __shfl_xor_sync(0xffffffffu, best, off);
-    const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
-    ovl += __shfl_xor_sync(0xffffffffu, ovl, off);
-    if (b2 > best || (b2 == best && a2 < arg)) {
-      best = b2;
-      arg = a2;
+  // per timestep: block reduction (max, lowest generator on ties; overload sum)
+#pragma unroll
+  for (int j = 0; j < TT; ++j) {
+    if (t0 + j >= T) break;  // uniform over the block
+    double v = (double)mx[j], s2 = (double)ov[j] * Acc<Real>::ovl_scale();
+    int g = ag[j];
+    for (int off = 16; off; off >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+      const int g2 = __shfl_xor_sync(0xffffffffu, g, off);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+      if (v2 > v || (v2 == v && g2 < g)) {
+        v = v2;
+        g = g2;
+      }
     }
-  }
-  if (lane == 0) {
-    o.gen_max_loading[(size_t)tau * T + t] = G ? best : 0.0;
-    o.worst_gen[(size_t)tau * T + t] = G ? arg : -1;
-    o.gen_overload_sum[(size_t)tau * T + t] = ovl;
+    if (lane == 0) {
+      rv[w] = v;
+      ra[w] = g;
+      ro[w] = s2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = rv[0], bo = ro[0];
+      int bg = ra[0];
+      for (int k = 1; k < 4; ++k) {
+        bo += ro[k];
+        if (rv[k] > bv || (rv[k] == bv && ra[k] < bg)) {
+          bv = rv[k];
+          bg = ra[k];
+        }
+      }
+      const size_t k2 = (size_t)tau * T + t0 + j;
+      o.gen_max_loading[k2] = G ? bv : 0.0;
+      o.worst_gen[k2] = G ? bg : -1;
+      o.gen_overload_sum[k2] = bo;
+    }
+    __syncthreads();
   }
 }
 
@@ -1365,14 +1442,20 @@ void launch_topcases(const Args& a, int RMAX, const float* cmax, const int* cinv
   else launch_topcases_r<Real, 16>(a, cmax, cinv, phicm, k, st);
 }
 
+template <class Real, int RMAX>
+void launch_gen_r(const Args& a, int G, const int* gen_bus, const double* gen_p, const double* ptdf, int V,
+                  const Real* P, cudaStream_t st) {
+  constexpr int TT = 8;  // timesteps per pass (per-thread accumulators)
+  for (int t0 = 0; t0 < a.T; t0 += TT)
+    k_gen_n1<Real, RMAX, TT><<<a.nq, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P, t0);
+}
 template <class Real>
 void launch_gen(const Args& a, int RMAX, int G, const int* gen_bus, const double* gen_p, const double* ptdf, int V,
                 const void* pg, cudaStream_t st) {
-  const dim3 grid(a.nq, (a.T + 3) / 4);
   const Real* P = static_cast<const Real*>(pg);
-  if (RMAX == 4) k_gen_n1<Real, 4><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
-  else if (RMAX == 8) k_gen_n1<Real, 8><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
-  else k_gen_n1<Real, 16><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
+  if (RMAX == 4) launch_gen_r<Real, 4>(a, G, gen_bus, gen_p, ptdf, V, P, st);
+  else if (RMAX == 8) launch_gen_r<Real, 8>(a, G, gen_bus, gen_p, ptdf, V, P, st);
+  else launch_gen_r<Real, 16>(a, G, gen_bus, gen_p, ptdf, V, P, st);
 }
 
 int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
