@@ -446,10 +446,10 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
   if (a.out.n0_max_loading) {
     const int lane = tid & 31, nw = blockDim.x >> 5;
     for (int t = tid >> 5; t < T; t += nw) {
-      double m = 0.0;
-      for (int l = lane; l < M; l += 32) m = fmax(m, fabs((double)ptil[(size_t)t * Mp + l]));
+      Real m = 0;  // the working precision per row (B300's FP64 rate is far below FP32)
+      for (int l = lane; l < M; l += 32) m = fmax(m, fabs(ptil[(size_t)t * Mp + l]));
       for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) a.out.n0_max_loading[(size_t)tau * T + t] = m;
+      if (lane == 0) a.out.n0_max_loading[(size_t)tau * T + t] = (double)m;
     }
   }
 }
@@ -790,23 +790,23 @@ __global__ void k_var_gather(Args af, int U, const Real* __restrict__ ptv, const
   const Real* si = svv + ((size_t)q * TV + (size_t)t * U + u) * C;
   Real* po = static_cast<Real*>(af.ptil) + ((size_t)q * T + t) * Mp;
   Real* so = static_cast<Real*>(af.s) + ((size_t)q * T + t) * C;
-  double m = 0.0;
+  Real m = 0;
   for (int l = threadIdx.x; l < M; l += blockDim.x) {
     const Real v = pi[l];
     po[l] = v;
-    m = fmax(m, fabs((double)v));
+    m = fmax(m, fabs(v));
     if (af.out.n0_flow) af.out.n0_flow[((size_t)qi.tau * T + t) * M + l] = (double)v / af.inv_lim[l];
   }
   for (int c = threadIdx.x; c < C; c += blockDim.x) so[c] = si[c];
   if (af.out.n0_max_loading) {
-    __shared__ double red[32];
+    __shared__ Real red[32];
     for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double x = red[0];
+      Real x = red[0];
       for (int w = 1; w < (int)(blockDim.x >> 5); ++w) x = fmax(x, red[w]);
-      af.out.n0_max_loading[(size_t)qi.tau * T + t] = x;
+      af.out.n0_max_loading[(size_t)qi.tau * T + t] = (double)x;
     }
   }
 }
