@@ -214,3 +214,15 @@ def test_top_cases_mutation_is_caught(monkeypatch):
     monkeypatch.setattr(ref, "top_cases", _top_cases_ascending)
     monkeypatch.setattr(oracle, "top_cases", _top_cases_ascending)
     assert _fails(pins.test_top_cases_k1_is_the_worst_case_and_k3_matches_refactorisation)
+
+
+def test_generator_n1_mutation_is_caught(monkeypatch):
+    """A generator failure that adds its output instead of removing it."""
+    orig = ref.generator_n1
+
+    def wrong_sign(grid, topo, P, gen_bus, gen_p, mon, limit, idx=None):
+        return orig(grid, topo, P, gen_bus, -np.asarray(gen_p, np.float64), mon, limit, idx)  # planted
+
+    monkeypatch.setattr(ref, "generator_n1", wrong_sign)
+    monkeypatch.setattr(oracle, "generator_n1", wrong_sign)
+    assert _fails(pins.test_generator_n1_closed_forms)
