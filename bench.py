@@ -374,6 +374,35 @@ def run_ours(args):
                                                "note": f"fp32 solve plus {args.gens} generator-failure N-1 cases "
                                                        "per topology and timestep (value counts the branch "
                                                        "N-1 cases only)"}
+        # the same solve with multi-outage N-1 cases (sets of 2-4 branches that fail together)
+        if form == "fp32" and args.multi > 0 and db.n_var == 0:
+            rng = np.random.default_rng(800)
+            E = w.grid.n_branch
+            sets = [[int(b) for b in rng.choice(E, 2 + k % 3, replace=False)] for k in range(args.multi)]
+            solver.set_study(w.mon, w.cont, lim, split_bus=w.subs, multi=sets)
+            rm = DeviceResults(db.n_topo, db.n_time, len(w.mon), want_multi=True)
+            for _ in range(args.warmup):
+                solver.solve(db, results=rm)
+            torch.cuda.synchronize()
+            evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k2 in range(steps):
+                flush.fill_(k2 & 0xFF)
+                evm[k2][0].record(stream)
+                solver.solve(db, results=rm)
+                evm[k2][1].record(stream)
+            torch.cuda.synchronize()
+            tm = sum(a.elapsed_time(b) for a, b in evm) / 1e3
+            if ws > 1:
+                tm, _ = reduce_over_ranks(tm, lf, "cuda")
+            okm = rm.island_flag[:db.n_topo] == 0
+            nm_cases = (int(okm.sum().item()) * args.multi - int(rm.n_island_multi[:db.n_topo][okm].sum().item())) \
+                * T_STEPS * ws
+            results[f"fp32_multi{args.multi}"] = {
+                "value": lf_all * steps / tm, "ms_per_step": 1e3 * tm / steps, "loadflows_per_step": lf_all,
+                "multi_cases_per_step": nm_cases, "steps": steps,
+                "note": f"fp32 solve plus {args.multi} multi-outage N-1 sets of 2-4 branches per topology and "
+                        "timestep (value counts the single-branch N-1 cases only; multi_cases_per_step counts "
+                        "the sets evaluated, sets a topology already lost counted too)"}
         results[form]["setup_s"] = setup_s
         solver.close()
     if rank != 0:
@@ -478,6 +507,8 @@ def main():
     ap.add_argument("--workload", default="grid500", choices=sorted(WORKLOADS))
     ap.add_argument("--gens", type=int, default=16,
                     help="also time the FP32 solve with this many generator-failure cases; 0 = skip")
+    ap.add_argument("--multi", type=int, default=32,
+                    help="also time the FP32 solve with this many multi-outage sets; 0 = skip")
     ap.add_argument("--top-k", type=int, default=8,
                     help="also time the FP32 solve with the k worst N-1 cases per (topology, timestep); 0 = skip")
     args = ap.parse_args()

@@ -123,6 +123,10 @@ int dcflow_base_ptdf_noalloc(dcflow_ctx* ctx, const int32_t* rows, int32_t n_row
  * rho = |flow| / limit.  split_bus: host int32[n_split_bus] substations that
  * batches may split (NULL = every bus); outage_cand: host
  * int32[n_outage_cand] branches batches may outage (NULL = every branch).
+ * multi_ptr / multi_branch (optional, host): n_multi N-1 cases that take out
+ * several branches at once (Def. 4, MODF; e.g. the windings of a
+ * three-winding transformer), set m = multi_branch[multi_ptr[m] ..
+ * multi_ptr[m + 1]), 1 to 4 distinct branches each.
  * Synchronous; may be called again to change the study.
  */
 typedef struct {
@@ -131,6 +135,9 @@ typedef struct {
   const double* limit;
   const int32_t* split_bus;   int32_t n_split_bus;
   const int32_t* outage_cand; int32_t n_outage_cand;
+  int32_t n_multi;
+  const int32_t* multi_ptr;
+  const int32_t* multi_branch;
 } dcflow_study;
 
 int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* study);
@@ -229,6 +236,14 @@ typedef struct {
                                 |p_f[l] - P_g PTDF_f[l, bus_g]| / limit (with n_gen > 0) */
   int32_t* worst_gen;        /* [n_topo * n_time] the generator reaching it (lowest on ties), -1 if none */
   double* gen_overload_sum;  /* [n_topo * n_time] sum of max(0, rho - 1) over the same cases */
+  /* multi-outage N-1 cases of the study (Def. 4), optional (all four or none): the maximum
+   * over the sets and monitored branches of |p_n1| / limit, the set reaching it (lowest
+   * on ties, -1 if none), the overload sum, and per topology the sets skipped because
+   * they island it (a set with a branch the topology already lost is skipped, not counted) */
+  double* multi_max_loading;   /* [n_topo * n_time] */
+  int32_t* worst_multi;        /* [n_topo * n_time] */
+  double* multi_overload_sum;  /* [n_topo * n_time] */
+  int32_t* n_island_multi;     /* [n_topo] */
 } dcflow_results;
 
 /*

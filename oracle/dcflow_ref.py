@@ -591,3 +591,54 @@ def generator_n1(grid, topo, P, gen_bus, gen_p, mon, limit, idx=None):
         out["gen_each"].append(ge)
         out["status"].append(st)
     return {k: np.asarray(v) for k, v in out.items()}
+
+
+def multi_outage_n1(grid, topo, P, multi, mon, limit, idx=None):
+    """N-1 cases that take out several branches at once (Def. 4, MODF; e.g. the
+    windings of a three-winding transformer).  multi: list of branch lists.
+    Per topology the graph is rebuilt without each set (on top of the
+    topology's own outages) and refactored.  A set that islands the topology
+    is skipped and counted; a set with a branch the topology already lost is
+    skipped and not counted.  Returns per topology and timestep the maximum
+    loading over sets and monitored branches, the set reaching it (lowest index
+    on ties; -1 if none), the overload sum, every set's own maximum
+    (multi_each [T, S], -1 if skipped), and per topology the islanding count
+    and the status."""
+    P = np.atleast_2d(np.asarray(P, np.float64))
+    mon = np.asarray(mon, np.int64)
+    lim = np.asarray(limit, np.float64)[mon]
+    T, S = P.shape[0], len(multi)
+    ids = range(topo.n_topo) if idx is None else [int(i) for i in idx]
+    out = {k: [] for k in ("multi_max", "worst_multi", "multi_ovl", "multi_each", "n_island_multi", "status")}
+    for i in ids:
+        a, c = topo.split_ptr[i], topo.split_ptr[i + 1]
+        splits = list(zip(topo.split_sub[a:c], topo.split_mask[a:c]))
+        a, c = topo.out_ptr[i], topo.out_ptr[i + 1]
+        outages = [int(x) for x in topo.out_branch[a:c]]
+        mm, wm, mo = np.zeros(T), -np.ones(T, np.int64), np.zeros(T)
+        me = -np.ones((T, S))
+        nisl = 0
+        fl0, info = topology_flows(grid, splits, outages, P.T)
+        st = info[0]
+        if fl0 is not None:
+            for m, br in enumerate(multi):
+                if any(int(b) in outages for b in br):
+                    continue
+                fl, inf2 = topology_flows(grid, splits, outages + [int(b) for b in br], P.T)
+                if fl is None:
+                    nisl += 1
+                    continue
+                rho = np.abs(fl[mon]) / lim[:, None]  # [M, T]; the outaged set carries nothing
+                me[:, m] = rho.max(axis=0)
+                mo += np.maximum(rho - 1.0, 0.0).sum(axis=0)
+            for t in range(T):
+                if (me[t] >= 0).any():
+                    m = int(np.argmax(me[t]))
+                    mm[t], wm[t] = me[t, m], m
+        out["multi_max"].append(mm)
+        out["worst_multi"].append(wm)
+        out["multi_ovl"].append(mo)
+        out["multi_each"].append(me)
+        out["n_island_multi"].append(nisl)
+        out["status"].append(st)
+    return {k: np.asarray(v) for k, v in out.items()}

@@ -115,6 +115,10 @@ struct dcflow_ctx {
   int C_eff = 0;
   std::vector<int> h_cont_pos;  // internal index -> caller's position
   dcf::DevBuf cont_pos, cont_inv;  // int[C]: internal -> caller position, caller position -> internal
+  // multi-outage N-1 sets (Def. 4): CSR over entries, each entry's needed-row
+  // index and monitored position, and Phi[mon, entry] / limit transposed [entries][Mpad]
+  int n_multi = 0, n_multi_ent = 0;
+  dcf::DevBuf multi_ptr, multiN, multi_mpos, PhiMO;
   dcf::DevBuf PhiCM;       // Real[C*Mpad] the same factors transposed (final pass, screened N-1; first solve builds it)
   bool phicm_ready = false;
   dcf::DevBuf Y;           // solve workspace

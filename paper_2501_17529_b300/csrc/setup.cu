@@ -284,6 +284,17 @@ extern "C" int dcflow_base_ptdf(dcflow_ctx* ctx, const int32_t* rows, int32_t n_
   return rc;
 }
 
+// Phi[mon, o] / limit for every multi-outage entry o, transposed [entries][Mpad]
+// (zero padding rows): a set's columns are contiguous over the monitored rows.
+template <class Real>
+__global__ void k_phi_multi(int M, int Mp, int NN, const int* __restrict__ monN, const int* __restrict__ multiN,
+                            const double* __restrict__ inv_lim, const double* __restrict__ PhiN,
+                            Real* __restrict__ PhiMO) {
+  const int e = blockIdx.y, l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= Mp) return;
+  PhiMO[(size_t)e * Mp + l] = l < M ? (Real)(PhiN[(size_t)monN[l] * NN + multiN[e]] * inv_lim[l]) : (Real)0;
+}
+
 // Bridges of the base multigraph (iterative Tarjan low-link over edge ids, so
 // that a parallel branch is never a bridge).
 static std::vector<char> base_bridges(int V, int E, const std::vector<int>& f, const std::vector<int>& t) {
@@ -376,6 +387,36 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
     }
   } else {
     std::fill(need.begin(), need.end(), 1);
+  }
+  const int n_multi = s->n_multi > 0 ? s->n_multi : 0;
+  std::vector<int> mptr(1, 0), mbr;
+  if (n_multi > 0) {  // multi-outage sets: 1 to 4 distinct branches each
+    if (!s->multi_ptr || !s->multi_branch || s->multi_ptr[0] != 0) {
+      set_error("dcflow_set_study: multi-outage sets need multi_ptr (from 0) and multi_branch");
+      return DCFLOW_ERR_INVALID_ARG;
+    }
+    for (int m = 0; m < n_multi; ++m) {
+      const int a0 = s->multi_ptr[m], a1 = s->multi_ptr[m + 1];
+      if (a1 - a0 < 1 || a1 - a0 > 4) {
+        set_error("dcflow_set_study: a multi-outage set has 1 to 4 branches");
+        return DCFLOW_ERR_INVALID_ARG;
+      }
+      for (int k = a0; k < a1; ++k) {
+        const int l = s->multi_branch[k];
+        if (l < 0 || l >= E) {
+          set_error("dcflow_set_study: multi-outage branch out of range");
+          return DCFLOW_ERR_INVALID_ARG;
+        }
+        for (int k2 = a0; k2 < k; ++k2)
+          if (s->multi_branch[k2] == l) {
+            set_error("dcflow_set_study: a multi-outage set repeats a branch");
+            return DCFLOW_ERR_INVALID_ARG;
+          }
+        need[l] = 1;
+        mbr.push_back(l);
+      }
+      mptr.push_back((int)mbr.size());
+    }
   }
   ctx->has_study = false;
   ctx->M = s->n_mon;
@@ -473,6 +514,36 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
     else
       k_phi_mc<float><<<g, 128, 0, st>>>(M, C, ctx->ldc, NN, ctx->monN.as<int>(), ctx->contN.as<int>(),
                                         ctx->inv_lim.as<double>(), ctx->PhiN.as<double>(), ctx->PhiMC.as<float>());
+    ++ctx->launches;
+  }
+  ctx->n_multi = n_multi;
+  ctx->n_multi_ent = (int)mbr.size();
+  if (n_multi > 0) {  // per entry: needed-row index, monitored position, Phi[mon, entry] / limit
+    const int nE = (int)mbr.size(), Mp = (int)round_up(M, 16);
+    std::vector<int> mN(nE), mmp(nE);
+    for (int e = 0; e < nE; ++e) {
+      mN[e] = ctx->h_nidx[mbr[e]];
+      mmp[e] = pos_in_mon[mbr[e]];
+    }
+    if ((rc = upload(ctx->multi_ptr, mptr.data(), sizeof(int) * mptr.size())) ||
+        (rc = upload(ctx->multiN, mN.data(), sizeof(int) * nE)) ||
+        (rc = upload(ctx->multi_mpos, mmp.data(), sizeof(int) * nE))) {
+      d_N.release();
+      return rc;
+    }
+    if (ctx->PhiMO.ensure((size_t)nE * Mp * rs)) {
+      d_N.release();
+      return DCFLOW_ERR_OOM;
+    }
+    const dim3 g((Mp + 127) / 128, nE);
+    if (ctx->opt.precision == DCFLOW_FP64)
+      k_phi_multi<double><<<g, 128, 0, st>>>(M, Mp, NN, ctx->monN.as<int>(), ctx->multiN.as<int>(),
+                                             ctx->inv_lim.as<double>(), ctx->PhiN.as<double>(),
+                                             ctx->PhiMO.as<double>());
+    else
+      k_phi_multi<float><<<g, 128, 0, st>>>(M, Mp, NN, ctx->monN.as<int>(), ctx->multiN.as<int>(),
+                                            ctx->inv_lim.as<double>(), ctx->PhiN.as<double>(),
+                                            ctx->PhiMO.as<float>());
     ++ctx->launches;
   }
   cudaError_t e = cudaStreamSynchronize(st);

@@ -1363,6 +1363,224 @@ __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __rest
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// multi-outage N-1 (Def. 4, MODF): a set O of up to 4 branches fails at once,
+//   p_n1 = p_f + Phi_f[:, O] (I - Phi_f[O, O])^{-1} p_f[O],
+// with Phi_f[:, o] = Phi[:, o] - Z K^{-1} (Sigma^T Phi[:, o] - s_o) as for the
+// single contingencies; the natural-order LU pivots of I - Phi_f[O, O] are the
+// sequential LODF denominators, so a pivot at or below the threshold means the
+// set islands the topology.  One block per topology and pass of TT timesteps:
+// per set a few threads do the FP64 r x |O| and |O| x |O| work, then every
+// thread sweeps its monitored rows with per-timestep accumulators.
+// ---------------------------------------------------------------------------
+template <class Real, int RMAX, int TT>
+__global__ __launch_bounds__(128) void k_multi(Args a, int n_multi, const int* __restrict__ mptr,
+                                               const int* __restrict__ mN, const int* __restrict__ mmpos,
+                                               const Real* __restrict__ PhiMO, int t0) {
+  __shared__ EntSmem S;
+  __shared__ int outN[kRMax];
+  __shared__ int nout, skip_s, nisl_s;
+  __shared__ double bv_s[4][kRMax], vt_s[4][kRMax], z_s[4][kRMax];
+  __shared__ Real vtr_s[4][kRMax];
+  __shared__ Real w_s[TT][4];
+  __shared__ double A_s[4][4];
+  __shared__ double rv_s[TT][4], ro_s[TT][4];
+  __shared__ int ra_s[TT][4];
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const QInfo qi = a.qi[q];
+  const int T = a.T, M = a.M, Mp = a.Mpad, NN = a.NN, tau = qi.tau;
+  const dcflow_results& o = a.out;
+  if (qi.status != ST_OK) {
+    for (int t = t0 + tid; t < T && t < t0 + TT; t += blockDim.x) {
+      o.multi_max_loading[(size_t)tau * T + t] = 0.0;
+      o.worst_multi[(size_t)tau * T + t] = -1;
+      o.multi_overload_sum[(size_t)tau * T + t] = 0.0;
+    }
+    if (t0 == 0 && tid == 0) o.n_island_multi[tau] = 0;
+    return;
+  }
+  const int r = qi.r, ks = qi.ks;
+  load_entries(S, a, q, r);  // block-wide (contains a barrier)
+  if (tid == 0) {
+    nout = r - ks;
+    nisl_s = 0;
+  }
+  for (int i = tid; i < r - ks; i += blockDim.x) outN[i] = S.en[S.mp[ks + i]];
+  __syncthreads();
+  const double* Kinv = a.Kinv + (size_t)q * kRMax * kRMax;
+  const double* alpha = a.alpha + (size_t)q * kRMax * T;
+  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
+  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
+  const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
+  Real mx[TT], ov[TT];
+  int ag[TT];
+#pragma unroll
+  for (int j = 0; j < TT; ++j) {
+    mx[j] = (Real)-1;
+    ov[j] = (Real)0;
+    ag[j] = 0x7fffffff;
+  }
+  for (int m = 0; m < n_multi; ++m) {
+    const int e0 = mptr[m], n = mptr[m + 1] - e0;
+    __syncthreads();  // the previous set's shared values are consumed
+    if (tid == 0) {
+      int sk = 0;  // a member the topology already lost: skipped, not counted
+      for (int a2 = 0; a2 < n; ++a2)
+        for (int k = 0; k < nout; ++k) sk |= outN[k] == mN[e0 + a2];
+      skip_s = sk;
+    }
+    if (tid < n * kRMax) {  // Sigma^T Phi[:, o] - s_o and the Z row of member o
+      const int a2 = tid / kRMax, i = tid % kRMax, oN = mN[e0 + a2];
+      double acc = 0.0, z = 0.0;
+      if (i < r) {
+        for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
+          const int mm = S.en[e];
+          acc = fma((double)S.es[e], a.PhiN[(size_t)mm * NN + oN], acc);
+          if (i < ks && mm == oN) acc -= (double)S.es[e];
+        }
+        z = z_entry_col(S, a.PhiN, NN, a.bN, oN, i);
+      }
+      bv_s[a2][i] = acc;
+      z_s[a2][i] = z;
+    }
+    __syncthreads();
+    if (skip_s) continue;  // uniform
+    if (tid < n * kRMax) {
+      const int a2 = tid / kRMax, j = tid % kRMax;
+      double x = 0.0;
+      for (int i = 0; i < r; ++i) x = fma(Kinv[j * kRMax + i], bv_s[a2][i], x);
+      vt_s[a2][j] = x;
+      vtr_s[a2][j] = (Real)x;
+    }
+    __syncthreads();
+    if (tid < n * n) {  // A = I - Phi_f[O, O]
+      const int a2 = tid / n, b2 = tid % n;
+      double phi = a.PhiN[(size_t)mN[e0 + a2] * NN + mN[e0 + b2]];
+      for (int j = 0; j < r; ++j) phi = fma(-z_s[a2][j], vt_s[b2][j], phi);
+      A_s[a2][b2] = (a2 == b2 ? 1.0 : 0.0) - phi;
+    }
+    __syncthreads();
+    if (tid == 0) {  // natural-order LU; its pivots are the sequential LODF denominators
+      for (int k = 0; k < n; ++k) {
+        if (!(A_s[k][k] > a.tol)) {
+          skip_s = 2;
+          ++nisl_s;
+          break;
+        }
+        for (int i = k + 1; i < n; ++i) {
+          A_s[i][k] /= A_s[k][k];
+          for (int j = k + 1; j < n; ++j) A_s[i][j] = fma(-A_s[i][k], A_s[k][j], A_s[i][j]);
+        }
+      }
+    }
+    __syncthreads();
+    if (skip_s) continue;  // uniform
+    if (tid < TT) {  // weights of timestep t: A^{-1} p_f[O, t]
+      const int t = t0 + tid < T ? t0 + tid : T - 1;
+      double y[4];
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2) {
+        double pf = 0.0;
+        if (a2 < n) {
+          pf = a.p0[(size_t)mN[e0 + a2] * T + t];
+          for (int j = 0; j < r; ++j) pf = fma(-z_s[a2][j], alpha[j * T + t], pf);
+        }
+        y[a2] = pf;
+      }
+#pragma unroll
+      for (int i = 1; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < i; ++k)
+          if (i < n) y[i] = fma(-A_s[i][k], y[k], y[i]);
+#pragma unroll
+      for (int i = 3; i >= 0; --i) {
+        if (i < n) {
+#pragma unroll
+          for (int k = i + 1; k < 4; ++k)
+            if (k < n) y[i] = fma(-A_s[i][k], y[k], y[i]);
+          y[i] /= A_s[i][i];
+        }
+      }
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2) w_s[tid][a2] = a2 < n ? (Real)y[a2] : (Real)0;
+    }
+    __syncthreads();
+    if (skip_s) continue;  // uniform
+    for (int l = tid; l < M; l += blockDim.x) {
+      Real zr[RMAX];
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
+      const Real rm = meta[Mp + l];  // an outaged monitored branch carries nothing
+      Real col[4];
+      bool in_set = false;  // a member itself carries nothing (the MODF rows O := -I)
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2) {
+        col[a2] = (Real)0;
+        if (a2 < n) {
+          Real c = PhiMO[(size_t)(e0 + a2) * Mp + l];
+#pragma unroll
+          for (int j = 0; j < RMAX; ++j) c = fma(-zr[j], vtr_s[a2][j], c);
+          col[a2] = c * rm;
+          in_set |= mmpos[e0 + a2] == l;
+        }
+      }
+#pragma unroll
+      for (int jt = 0; jt < TT; ++jt) {
+        const int t = t0 + jt < T ? t0 + jt : T - 1;  // a tail pass repeats the last timestep, never written
+        Real v = ptil[(size_t)t * Mp + l];
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2) v = fma(col[a2], w_s[jt][a2], v);
+        if (in_set) v = (Real)0;
+        if (fabs(v) > mx[jt]) {
+          mx[jt] = fabs(v);
+          ag[jt] = m;
+        }
+        Real dummy = (Real)0;
+        Acc<Real>::add(dummy, ov[jt], v);
+      }
+    }
+  }
+  if (t0 == 0 && tid == 0) o.n_island_multi[tau] = nisl_s;
+#pragma unroll
+  for (int jt = 0; jt < TT; ++jt) {
+    double v = (double)mx[jt], s2 = (double)ov[jt] * Acc<Real>::ovl_scale();
+    int g = ag[jt];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+      const int g2 = __shfl_xor_sync(0xffffffffu, g, off);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+      if (v2 > v || (v2 == v && g2 < g)) {
+        v = v2;
+        g = g2;
+      }
+    }
+    if (lane == 0) {
+      rv_s[jt][wp] = v;
+      ra_s[jt][wp] = g;
+      ro_s[jt][wp] = s2;
+    }
+  }
+  __syncthreads();
+  if (tid < TT && t0 + tid < T) {
+    double bv = rv_s[tid][0], bo = ro_s[tid][0];
+    int bg = ra_s[tid][0];
+    for (int k = 1; k < 4; ++k) {
+      bo += ro_s[tid][k];
+      if (rv_s[tid][k] > bv || (rv_s[tid][k] == bv && ra_s[tid][k] < bg)) {
+        bv = rv_s[tid][k];
+        bg = ra_s[tid][k];
+      }
+    }
+    const size_t k2 = (size_t)tau * T + t0 + tid;
+    const bool any = bg != 0x7fffffff;
+    o.multi_max_loading[k2] = any ? bv : 0.0;
+    o.worst_multi[k2] = any ? bg : -1;
+    o.multi_overload_sum[k2] = bo;
+  }
+}
+
 }  // namespace dcf
 
 #include "n1_reg.cuh"
@@ -1456,6 +1674,18 @@ void launch_gen(const Args& a, int RMAX, int G, const int* gen_bus, const double
   if (RMAX == 4) launch_gen_r<Real, 4>(a, G, gen_bus, gen_p, ptdf, V, P, st);
   else if (RMAX == 8) launch_gen_r<Real, 8>(a, G, gen_bus, gen_p, ptdf, V, P, st);
   else launch_gen_r<Real, 16>(a, G, gen_bus, gen_p, ptdf, V, P, st);
+}
+
+template <class Real>
+void launch_multi(const Args& a, int RMAX, int n_multi, const int* mptr, const int* mN, const int* mmpos,
+                  const void* phimo, cudaStream_t st) {
+  constexpr int TT = 8;
+  const Real* P = static_cast<const Real*>(phimo);
+  for (int t0 = 0; t0 < a.T; t0 += TT) {
+    if (RMAX == 4) k_multi<Real, 4, TT><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mN, mmpos, P, t0);
+    else if (RMAX == 8) k_multi<Real, 8, TT><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mN, mmpos, P, t0);
+    else k_multi<Real, 16, TT><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mN, mmpos, P, t0);
+  }
 }
 
 int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
@@ -1689,6 +1919,14 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                      mode != kModeFull || ctx->C > 2048)) {
     set_error("dcflow_solve_batch: top_k in [1, 64] with its three arrays, at most 2048 contingencies, "
               "not with the screened solve");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  const bool want_multi = mode == kModeFull && res->multi_max_loading;
+  if ((res->multi_max_loading || res->worst_multi || res->multi_overload_sum || res->n_island_multi) &&
+      (!res->multi_max_loading || !res->worst_multi || !res->multi_overload_sum || !res->n_island_multi ||
+       mode != kModeFull || U > 0 || ctx->n_multi == 0)) {
+    set_error("dcflow_solve_batch: multi-outage outputs need all four arrays and a study with multi-outage sets, "
+              "without injection candidates or the screener");
     return DCFLOW_ERR_INVALID_ARG;
   }
   const int G = mode == kModeFull ? bt->n_gen : 0;
@@ -2155,6 +2393,16 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     else launch_final<float>(af, RMAX, st, ctx->PhiCM.p, nsel_dev);
     ++ctx->launches;
     DCF_CHECK_LAUNCH();
+    if (want_multi) {
+      if (fp64)
+        launch_multi<double>(af, RMAX, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(),
+                             ctx->multi_mpos.as<int>(), ctx->PhiMO.p, st);
+      else
+        launch_multi<float>(af, RMAX, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(),
+                            ctx->multi_mpos.as<int>(), ctx->PhiMO.p, st);
+      ctx->launches += (T + 7) / 8;
+      DCF_CHECK_LAUNCH();
+    }
     if (G > 0) {
       if (fp64)
         launch_gen<double>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V, ctx->gen_cols.p, st);

@@ -30,7 +30,8 @@ class Study(ctypes.Structure):
                 ("cont", POINTER(c_int32)), ("n_cont", c_int32),
                 ("limit", POINTER(c_double)),
                 ("split_bus", POINTER(c_int32)), ("n_split_bus", c_int32),
-                ("outage_cand", POINTER(c_int32)), ("n_outage_cand", c_int32)]
+                ("outage_cand", POINTER(c_int32)), ("n_outage_cand", c_int32),
+                ("n_multi", c_int32), ("multi_ptr", POINTER(c_int32)), ("multi_branch", POINTER(c_int32))]
 
 
 class Batch(ctypes.Structure):
@@ -47,7 +48,8 @@ class Results(ctypes.Structure):
                 ("best_var", c_void_p), ("island_flag", c_void_p), ("n_island_cont", c_void_p),
                 ("n1_cont_max", c_void_p), ("top_k", c_int32), ("top_cont", c_void_p), ("top_mon", c_void_p),
                 ("top_loading", c_void_p), ("gen_max_loading", c_void_p), ("worst_gen", c_void_p),
-                ("gen_overload_sum", c_void_p)]
+                ("gen_overload_sum", c_void_p), ("multi_max_loading", c_void_p), ("worst_multi", c_void_p),
+                ("multi_overload_sum", c_void_p), ("n_island_multi", c_void_p)]
 
 
 class ScreenOptions(ctypes.Structure):
@@ -214,11 +216,12 @@ def dcflow_base_ptdf_noalloc(ctx, rows, out, stream=None):
            "dcflow_base_ptdf_noalloc")
 
 
-def dcflow_set_study(ctx, mon, cont, limit, split_bus=None, outage_cand=None):
+def dcflow_set_study(ctx, mon, cont, limit, split_bus=None, outage_cand=None, multi=None):
+    """multi: optional list of branch sets (1-4 branches each) that fail together."""
     ma, mp = _i32(mon)
     ca, cp = _i32(cont)
     la, lp = _f64(limit)
-    s = Study(mp, int(ma.size), cp, int(ca.size), lp, None, 0, None, 0)
+    s = Study(mp, int(ma.size), cp, int(ca.size), lp, None, 0, None, 0, 0, None, None)
     keep = [ma, ca, la]
     if split_bus is not None:
         sa, spp = _i32(split_bus)
@@ -228,6 +231,13 @@ def dcflow_set_study(ctx, mon, cont, limit, split_bus=None, outage_cand=None):
         oa, op = _i32(outage_cand)
         keep.append(oa)
         s.outage_cand, s.n_outage_cand = op, int(oa.size)
+    if multi is not None and len(multi):
+        ptr = np.zeros(len(multi) + 1, np.int64)
+        ptr[1:] = np.cumsum([len(m) for m in multi])
+        pa, pp = _i32(ptr)
+        ba, bp = _i32(np.concatenate([np.asarray(m, np.int64).ravel() for m in multi]))
+        keep += [pa, ba]
+        s.n_multi, s.multi_ptr, s.multi_branch = len(multi), pp, bp
     _check(load_library().dcflow_set_study(ctx, byref(s)), "dcflow_set_study")
 
 
@@ -395,7 +405,7 @@ class DeviceResults:
     """Caller-owned device outputs of one batch."""
 
     def __init__(self, n_topo, n_time, n_mon, want_flows=False, want_var=False, device="cuda", n_cont=0,
-                 want_cont_max=False, top_k=0, want_gen=False):
+                 want_cont_max=False, top_k=0, want_gen=False, want_multi=False):
         import torch
         nt = max(1, n_topo * n_time)
         self.n0_flow = torch.empty(max(1, n_topo * n_time * n_mon), dtype=torch.float64, device=device) if want_flows else None
@@ -417,6 +427,10 @@ class DeviceResults:
         self.gen_max_loading = torch.empty(nt, dtype=torch.float64, device=device) if want_gen else None
         self.worst_gen = torch.empty(nt, dtype=torch.int32, device=device) if want_gen else None
         self.gen_overload_sum = torch.empty(nt, dtype=torch.float64, device=device) if want_gen else None
+        self.multi_max_loading = torch.empty(nt, dtype=torch.float64, device=device) if want_multi else None
+        self.worst_multi = torch.empty(nt, dtype=torch.int32, device=device) if want_multi else None
+        self.multi_overload_sum = torch.empty(nt, dtype=torch.float64, device=device) if want_multi else None
+        self.n_island_multi = torch.empty(max(1, n_topo), dtype=torch.int32, device=device) if want_multi else None
         self.shape = (n_topo, n_time, n_mon)
         self.n_cont = n_cont
 
@@ -426,7 +440,8 @@ class DeviceResults:
                        _ptr(self.best_var), _ptr(self.island_flag), _ptr(self.n_island_cont),
                        _ptr(self.n1_cont_max), self.top_k, _ptr(self.top_cont), _ptr(self.top_mon),
                        _ptr(self.top_loading), _ptr(self.gen_max_loading), _ptr(self.worst_gen),
-                       _ptr(self.gen_overload_sum))
+                       _ptr(self.gen_overload_sum), _ptr(self.multi_max_loading), _ptr(self.worst_multi),
+                       _ptr(self.multi_overload_sum), _ptr(self.n_island_multi))
 
     def to_host(self) -> dict:
         N, T, M = self.shape
@@ -449,6 +464,11 @@ class DeviceResults:
             out["gen_max"] = self.gen_max_loading[:N * T].cpu().numpy().reshape(N, T)
             out["worst_gen"] = self.worst_gen[:N * T].cpu().numpy().reshape(N, T).astype(np.int64)
             out["gen_ovl"] = self.gen_overload_sum[:N * T].cpu().numpy().reshape(N, T)
+        if self.multi_max_loading is not None:
+            out["multi_max"] = self.multi_max_loading[:N * T].cpu().numpy().reshape(N, T)
+            out["worst_multi"] = self.worst_multi[:N * T].cpu().numpy().reshape(N, T).astype(np.int64)
+            out["multi_ovl"] = self.multi_overload_sum[:N * T].cpu().numpy().reshape(N, T)
+            out["n_island_multi"] = self.n_island_multi[:N].cpu().numpy().astype(np.int64)
         if self.top_k:
             k = self.top_k
             out["top_cont"] = self.top_cont[:N * T * k].cpu().numpy().reshape(N, T, k).astype(np.int64)
@@ -466,11 +486,13 @@ class Solver:
                                 device=device, chunk_topo=chunk_topo, island_tol=island_tol)
         self.n_mon = 0
         self.n_cont = 0
+        self.n_multi = 0
 
-    def set_study(self, mon, cont, limit, split_bus=None, outage_cand=None):
-        dcflow_set_study(self.ctx, mon, cont, limit, split_bus, outage_cand)
+    def set_study(self, mon, cont, limit, split_bus=None, outage_cand=None, multi=None):
+        dcflow_set_study(self.ctx, mon, cont, limit, split_bus, outage_cand, multi)
         self.n_mon = int(np.asarray(mon).size)
         self.n_cont = int(np.asarray(cont).size)
+        self.n_multi = 0 if multi is None else len(multi)
 
     def base_ptdf(self, rows, stream=None):
         import torch
@@ -480,10 +502,14 @@ class Solver:
         return out
 
     def solve(self, dbatch: DeviceBatch, want_flows=False, results: DeviceResults | None = None, stream=None,
-              want_cont_max=False, top_k=0):
+              want_cont_max=False, top_k=0, want_multi=None):
+        """want_multi: evaluate the study's multi-outage sets (default: whenever it has some and the batch
+        has no injection candidates)."""
+        if want_multi is None:
+            want_multi = self.n_multi > 0 and dbatch.n_var == 0
         res = results or DeviceResults(dbatch.n_topo, dbatch.n_time, self.n_mon, want_flows, dbatch.n_var > 0,
                                        n_cont=self.n_cont, want_cont_max=want_cont_max, top_k=top_k,
-                                       want_gen=dbatch.n_gen > 0)
+                                       want_gen=dbatch.n_gen > 0, want_multi=want_multi)
         dcflow_solve_batch(self.ctx, dbatch.cstruct(), res.cstruct(), stream)
         return res
 

@@ -379,3 +379,74 @@ def test_generator_failures_match_oracle(precision):
             assert wg == ref["worst_gen"][i, t] or \
                 ref["gen_each"][i, t, wg] >= ref["gen_max"][i, t] - 2 * tol * max(1.0, ref["gen_max"][i, t])
     assert (g["worst_gen"][~ok] == -1).all()
+
+
+def _multi_sets(w, rng):
+    """Sets of 1-4 branches: random ones, ones holding a branch some topology already lost, the
+    single branch of a degree-1 bus and every branch of a degree-3 bus (both island)."""
+    g = w.grid
+    E = len(g.f)
+    deg = np.bincount(np.concatenate([g.f, g.t]), minlength=g.n_bus)
+    pool = np.nonzero(~oracle.bridges(g.n_bus, g.f, g.t, np.ones(E, bool)))[0]
+    sets = [[int(b) for b in rng.choice(pool, k, replace=False)] for k in (1, 2, 2, 3, 4, 4, 1, 3)]
+    lost = [int(b) for b in w.topo.out_branch[:3]]
+    sets += [[lost[0]], [lost[1], int((lost[1] + 7) % E)], [int((lost[2] + 11) % E), lost[2], 3]]
+    leaf = int(np.nonzero(deg == 1)[0][0])
+    sets.append([int(np.nonzero((g.f == leaf) | (g.t == leaf))[0][0])])
+    v3 = int([v for v in np.nonzero(deg == 3)[0] if v != g.slack][0])
+    sets.append([int(b) for b in np.nonzero((g.f == v3) | (g.t == v3))[0]])
+    return sets
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_multi_outages_match_oracle(precision):
+    """Multi-outage N-1 (MODF) against refactorisation of each topology without each set."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch, Solver
+    w = synth.workload(2, n_topo=14, T=11)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    sets = _multi_sets(w, np.random.default_rng(71))
+    s = Solver(w.grid, precision=precision)
+    s.set_study(w.mon, w.cont, lim, split_bus=w.subs, multi=sets)
+    g = s.solve(DeviceBatch(w.topo, w.inj)).to_host()
+    s.close()
+    ref = oracle.multi_outage_n1(w.grid, w.topo, w.inj, sets, w.mon, lim)
+    tol = TOL[precision]
+    ok = ref["status"] == 0
+    np.testing.assert_array_equal(g["status"], ref["status"])
+    np.testing.assert_array_equal(g["n_island_multi"][ok], ref["n_island_multi"][ok])
+    assert (ref["n_island_multi"][ok] >= 1).all()  # the leaf branch islands every topology
+    np.testing.assert_allclose(g["multi_max"][ok], ref["multi_max"][ok], rtol=tol, atol=tol)
+    d = np.abs(g["multi_ovl"][ok] - ref["multi_ovl"][ok]) / np.maximum(ref["multi_ovl"][ok], 1.0)
+    assert d.max() <= tol
+    for i in np.nonzero(ok)[0]:
+        for t in range(w.inj.shape[0]):
+            wm = g["worst_multi"][i, t]
+            assert wm == ref["worst_multi"][i, t] or \
+                ref["multi_each"][i, t, wm] >= ref["multi_max"][i, t] - 2 * tol * max(1.0, ref["multi_max"][i, t])
+    assert (g["worst_multi"][~ok] == -1).all()
+    assert (g["n_island_multi"][~ok] == 0).all()
+
+
+def test_multi_outages_rejected_forms():
+    """Multi-outage outputs need a study with sets, all four arrays and no injection candidates;
+    a set has 1-4 distinct in-range branches."""
+    from paper_2501_17529_b300.dcflow import DCFlowError, DeviceBatch, DeviceResults, Solver
+    w = synth.workload(1)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    s = Solver(w.grid, precision="fp32")
+    E = len(w.grid.f)
+    for bad in ([[]], [[0, 1, 2, 3, 4]], [[2, 2]], [[E]], [[-1]]):
+        with pytest.raises(DCFlowError):
+            s.set_study(w.mon, w.cont, lim, split_bus=w.subs, multi=bad)
+    s.set_study(w.mon, w.cont, lim, split_bus=w.subs)
+    db = DeviceBatch(w.topo, w.inj)
+    with pytest.raises(DCFlowError):  # no sets in the study
+        s.solve(db, results=DeviceResults(w.topo.n_topo, w.inj.shape[0], len(w.mon), want_multi=True))
+    s.set_study(w.mon, w.cont, lim, split_bus=w.subs, multi=[[0, 1]])
+    r = DeviceResults(w.topo.n_topo, w.inj.shape[0], len(w.mon), want_multi=True)
+    r.n_island_multi = None
+    with pytest.raises(DCFlowError):  # not all four arrays
+        s.solve(db, results=r)
+    out = s.solve(db).to_host()
+    assert out["worst_multi"].shape == (w.topo.n_topo, w.inj.shape[0])
+    s.close()

@@ -226,3 +226,15 @@ def test_generator_n1_mutation_is_caught(monkeypatch):
     monkeypatch.setattr(ref, "generator_n1", wrong_sign)
     monkeypatch.setattr(oracle, "generator_n1", wrong_sign)
     assert _fails(pins.test_generator_n1_closed_forms)
+
+
+def test_multi_outage_mutation_is_caught(monkeypatch):
+    """A multi-outage case that takes out only the first branch of each set."""
+    orig = ref.multi_outage_n1
+
+    def first_only(grid, topo, P, multi, mon, limit, idx=None):
+        return orig(grid, topo, P, [list(m)[:1] for m in multi], mon, limit, idx)  # planted
+
+    monkeypatch.setattr(ref, "multi_outage_n1", first_only)
+    monkeypatch.setattr(oracle, "multi_outage_n1", first_only)
+    assert _fails(pins.test_multi_outage_reduces_to_lodf_and_modf)

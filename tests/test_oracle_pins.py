@@ -526,3 +526,30 @@ def test_generator_n1_closed_forms():
         assert r["gen_max"][0, t] == pytest.approx(rho.max(), rel=1e-10)
         assert r["worst_gen"][0, t] == int(np.argmax(rho.max(axis=0)))
         assert r["gen_ovl"][0, t] == pytest.approx(np.maximum(rho - 1, 0).sum(), rel=1e-9, abs=1e-12)
+
+
+def test_multi_outage_reduces_to_lodf_and_modf():
+    """A one-branch set is the LODF case of Def. 3 (the evaluator's per-contingency
+    maxima); a two-branch set on the unsplit grid follows the MODF of Def. 4."""
+    from paper_2501_17529_b300 import synth
+    w = synth.workload(2, n_topo=5, T=2)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    single = [[int(c)] for c in w.cont[:12]]
+    r = oracle.multi_outage_n1(w.grid, w.topo, w.inj, single, w.mon, lim)
+    ev = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont[:12], lim, want_cmax=True)
+    ok = ev["status"] == 0
+    np.testing.assert_allclose(r["multi_each"][ok], ev["cmax"][ok], rtol=1e-9, atol=1e-12)
+    np.testing.assert_array_equal(r["n_island_multi"][ok], ev["n_island_cont"][ok])
+    empty = synth.Topologies(np.zeros(2, np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint64),
+                             np.zeros(2, np.int32), np.zeros(0, np.int32))
+    br = oracle.bridges(w.grid.n_bus, w.grid.f, w.grid.t, np.ones(w.grid.n_branch, bool))
+    pair = [int(b) for b in np.nonzero(~br)[0][:2]]
+    r2 = oracle.multi_outage_n1(w.grid, empty, w.inj, [pair], w.mon, lim)
+    ptdf = oracle.ptdf(w.grid.n_bus, w.grid.f, w.grid.t, w.grid.b, w.grid.slack)
+    p0 = w.inj @ ptdf.T
+    modf = oracle.modf(ptdf, w.grid.f, w.grid.t, pair)
+    for t in range(2):
+        n1 = oracle.apply_modf(p0[t], modf, pair)
+        rho = np.abs(n1[w.mon]) / lim[w.mon]
+        if r2["n_island_multi"][0] == 0:
+            assert r2["multi_each"][0, t, 0] == pytest.approx(rho.max(), rel=1e-9)
