@@ -57,10 +57,12 @@ struct ChunkBufs {
   // learned screener: selected-contingency bit masks, fallback flags, the
   // selected lists and their counts, the N-1 work list and its length
   DevBuf selmask, sfb, csel, nsel, work, nwork;
+  // multi-outage sets: per (topology, set) K^{-1}-weighted columns, weights, flags
+  DevBuf mvt, mw, mflag;
   void release_all() {
     DevBuf* b[] = {&ent_n, &ent_s, &ent_w, &mod_ptr, &q_info, &Kinv, &alpha, &Vt64, &VtR, &Zs, &ptil, &meta,
                    &s, &valid, &nisl, &pmax, &parg, &povl, &ptv, &svv, &pmaxv, &pargv, &povlv, &bestu, &ptb, &sb,
-                   &selmask, &sfb, &csel, &nsel, &work, &nwork};
+                   &selmask, &sfb, &csel, &nsel, &work, &nwork, &mvt, &mw, &mflag};
     for (auto* x : b) x->release();
   }
 };

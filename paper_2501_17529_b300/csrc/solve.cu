@@ -1370,215 +1370,266 @@ __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __rest
 // with Phi_f[:, o] = Phi[:, o] - Z K^{-1} (Sigma^T Phi[:, o] - s_o) as for the
 // single contingencies; the natural-order LU pivots of I - Phi_f[O, O] are the
 // sequential LODF denominators, so a pivot at or below the threshold means the
-// set islands the topology.  One block per topology and pass of TT timesteps:
-// per set a few threads do the FP64 r x |O| and |O| x |O| work, then every
-// thread sweeps its monitored rows with per-timestep accumulators.
+// set islands the topology.
+// k_multi_prep (one warp per topology and set, FP64 for the small systems):
+//   vt [q][set][4][kRMax]  K^{-1} (Sigma^T Phi[:, o_a] - s_{o_a})  (Real)
+//   w  [q][set][T][4]      (I - Phi_f[O, O])^{-1} p_f[O, t]        (Real)
+//   flag [q][set]          0 evaluated, 1 islands the topology, 2 a member is
+//                          already out in the topology (skipped, not counted)
+// k_multi_rows (one block per topology): every monitored row against every set.
 // ---------------------------------------------------------------------------
-template <class Real, int RMAX, int TT>
-__global__ __launch_bounds__(128) void k_multi(Args a, int n_multi, const int* __restrict__ mptr,
-                                               const int* __restrict__ mN, const int* __restrict__ mmpos,
-                                               const Real* __restrict__ PhiMO, int t0) {
+template <class Real>
+__global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const int* __restrict__ mptr,
+                                                    const int* __restrict__ mN, Real* __restrict__ mvt,
+                                                    Real* __restrict__ mw, int* __restrict__ mflag) {
   __shared__ EntSmem S;
   __shared__ int outN[kRMax];
-  __shared__ int nout, skip_s, nisl_s;
-  __shared__ double bv_s[4][kRMax], vt_s[4][kRMax], z_s[4][kRMax];
-  __shared__ Real vtr_s[4][kRMax];
-  __shared__ Real w_s[TT][4];
-  __shared__ double A_s[4][4];
+  __shared__ double bv_s[4][4][kRMax], z_s[4][4][kRMax], vt_s[4][4][kRMax];
+  __shared__ double A_s[4][4][4];
+  __shared__ int flag_s[4];
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const QInfo qi = a.qi[q];
+  if (qi.status != ST_OK) return;
+  const int r = qi.r, ks = qi.ks, nout = qi.r - qi.ks, T = a.T, NN = a.NN;
+  load_entries(S, a, q, r);  // block-wide (contains a barrier)
+  for (int i = tid; i < nout; i += blockDim.x) outN[i] = S.en[S.mp[ks + i]];
+  __syncthreads();
+  const int m = blockIdx.y * 4 + wp;
+  if (m >= n_multi) return;  // warp-uniform; no block barrier follows
+  const int e0 = mptr[m], n = mptr[m + 1] - e0;
+  const size_t qm = (size_t)q * n_multi + m;
+  bool lost = false;  // a member the topology already lost
+  for (int p = lane; p < n * nout; p += 32) lost |= outN[p % nout] == mN[e0 + p / nout];
+  if (__any_sync(0xffffffffu, lost)) {
+    if (lane == 0) mflag[qm] = 2;
+    return;
+  }
+  const double* Kinv = a.Kinv + (size_t)q * kRMax * kRMax;
+  const double* alpha = a.alpha + (size_t)q * kRMax * T;
+  for (int p = lane; p < 4 * kRMax; p += 32) {  // Sigma^T Phi[:, o] - s_o and the Z row of member o
+    const int a2 = p / kRMax, i = p % kRMax;
+    double acc = 0.0, z = 0.0;
+    if (a2 < n && i < r) {
+      const int oN = mN[e0 + a2];
+      for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
+        const int mm = S.en[e];
+        acc = fma((double)S.es[e], a.PhiN[(size_t)mm * NN + oN], acc);
+        if (i < ks && mm == oN) acc -= (double)S.es[e];
+      }
+      z = z_entry_col(S, a.PhiN, NN, a.bN, oN, i);
+    }
+    bv_s[wp][a2][i] = acc;
+    z_s[wp][a2][i] = z;
+  }
+  __syncwarp();
+  Real* vt = mvt + qm * 4 * kRMax;
+  for (int p = lane; p < 4 * kRMax; p += 32) {  // K^{-1} is zero outside r x r
+    const int a2 = p / kRMax, j = p % kRMax;
+    double x = 0.0;
+    if (a2 < n)
+      for (int i = 0; i < r; ++i) x = fma(Kinv[j * kRMax + i], bv_s[wp][a2][i], x);
+    vt_s[wp][a2][j] = x;
+    vt[p] = (Real)x;
+  }
+  __syncwarp();
+  if (lane < n * n) {  // A = I - Phi_f[O, O]
+    const int a2 = lane / n, b2 = lane % n;
+    double phi = a.PhiN[(size_t)mN[e0 + a2] * NN + mN[e0 + b2]];
+    for (int j = 0; j < r; ++j) phi = fma(-z_s[wp][a2][j], vt_s[wp][b2][j], phi);
+    A_s[wp][a2][b2] = (a2 == b2 ? 1.0 : 0.0) - phi;
+  }
+  __syncwarp();
+  if (lane == 0) {  // natural-order LU
+    int f = 0;
+    for (int k = 0; k < n && !f; ++k) {
+      if (!(A_s[wp][k][k] > a.tol)) {
+        f = 1;
+        break;
+      }
+      for (int i = k + 1; i < n; ++i) {
+        A_s[wp][i][k] /= A_s[wp][k][k];
+        for (int j = k + 1; j < n; ++j) A_s[wp][i][j] = fma(-A_s[wp][i][k], A_s[wp][k][j], A_s[wp][i][j]);
+      }
+    }
+    flag_s[wp] = f;
+    mflag[qm] = f;
+  }
+  __syncwarp();
+  if (flag_s[wp]) return;
+  Real L[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) L[i][k] = (i < n && k < n) ? (Real)A_s[wp][i][k] : (Real)(i == k);
+  Real* w = mw + qm * T * 4;
+  for (int t = lane; t < T; t += 32) {  // p_f[O, t] as the row operands do, then the two triangular solves
+    Real y[4];
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) {
+      Real pf = (Real)0;
+      if (a2 < n) {
+        pf = (Real)a.p0[(size_t)mN[e0 + a2] * T + t];
+        for (int j = 0; j < r; ++j) pf = fma(-(Real)z_s[wp][a2][j], (Real)alpha[j * T + t], pf);
+      }
+      y[a2] = pf;
+    }
+#pragma unroll
+    for (int i = 1; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < i; ++k) y[i] = fma(-L[i][k], y[k], y[i]);
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+#pragma unroll
+      for (int k = i + 1; k < 4; ++k) y[i] = fma(-L[i][k], y[k], y[i]);
+      y[i] /= L[i][i];
+    }
+#pragma unroll
+    for (int a2 = 0; a2 < 4; ++a2) w[t * 4 + a2] = y[a2];
+  }
+}
+
+template <class Real, int RMAX, int TT, int SG>
+__global__ __launch_bounds__(128) void k_multi_rows(Args a, int n_multi, const int* __restrict__ mptr,
+                                                    const int* __restrict__ mmpos, const Real* __restrict__ PhiMO,
+                                                    const Real* __restrict__ mvt, const Real* __restrict__ mw,
+                                                    const int* __restrict__ mflag) {
+  __shared__ __align__(16) Real vt_s[SG][4][RMAX];
+  __shared__ __align__(16) Real w_s[SG][TT][4];
+  __shared__ int fl_s[SG], e0_s[SG], mp_s[SG][4];
+  __shared__ int nisl_s;
   __shared__ double rv_s[TT][4], ro_s[TT][4];
   __shared__ int ra_s[TT][4];
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const QInfo qi = a.qi[q];
-  const int T = a.T, M = a.M, Mp = a.Mpad, NN = a.NN, tau = qi.tau;
+  const int T = a.T, M = a.M, Mp = a.Mpad, tau = qi.tau;
   const dcflow_results& o = a.out;
   if (qi.status != ST_OK) {
-    for (int t = t0 + tid; t < T && t < t0 + TT; t += blockDim.x) {
+    for (int t = tid; t < T; t += blockDim.x) {
       o.multi_max_loading[(size_t)tau * T + t] = 0.0;
       o.worst_multi[(size_t)tau * T + t] = -1;
       o.multi_overload_sum[(size_t)tau * T + t] = 0.0;
     }
-    if (t0 == 0 && tid == 0) o.n_island_multi[tau] = 0;
+    if (tid == 0) o.n_island_multi[tau] = 0;
     return;
   }
-  const int r = qi.r, ks = qi.ks;
-  load_entries(S, a, q, r);  // block-wide (contains a barrier)
-  if (tid == 0) {
-    nout = r - ks;
-    nisl_s = 0;
-  }
-  for (int i = tid; i < r - ks; i += blockDim.x) outN[i] = S.en[S.mp[ks + i]];
-  __syncthreads();
-  const double* Kinv = a.Kinv + (size_t)q * kRMax * kRMax;
-  const double* alpha = a.alpha + (size_t)q * kRMax * T;
   const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
   const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
   const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
-  Real mx[TT], ov[TT];
-  int ag[TT];
+  const size_t qS = (size_t)q * n_multi;
+  if (tid == 0) nisl_s = 0;
+  for (int t0 = 0; t0 < T; t0 += TT) {
+    Real mx[TT], ov[TT];
+    int ag[TT];
 #pragma unroll
-  for (int j = 0; j < TT; ++j) {
-    mx[j] = (Real)-1;
-    ov[j] = (Real)0;
-    ag[j] = 0x7fffffff;
-  }
-  for (int m = 0; m < n_multi; ++m) {
-    const int e0 = mptr[m], n = mptr[m + 1] - e0;
-    __syncthreads();  // the previous set's shared values are consumed
-    if (tid == 0) {
-      int sk = 0;  // a member the topology already lost: skipped, not counted
-      for (int a2 = 0; a2 < n; ++a2)
-        for (int k = 0; k < nout; ++k) sk |= outN[k] == mN[e0 + a2];
-      skip_s = sk;
+    for (int j = 0; j < TT; ++j) {
+      mx[j] = (Real)-1;
+      ov[j] = (Real)0;
+      ag[j] = 0x7fffffff;
     }
-    if (tid < n * kRMax) {  // Sigma^T Phi[:, o] - s_o and the Z row of member o
-      const int a2 = tid / kRMax, i = tid % kRMax, oN = mN[e0 + a2];
-      double acc = 0.0, z = 0.0;
-      if (i < r) {
-        for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
-          const int mm = S.en[e];
-          acc = fma((double)S.es[e], a.PhiN[(size_t)mm * NN + oN], acc);
-          if (i < ks && mm == oN) acc -= (double)S.es[e];
-        }
-        z = z_entry_col(S, a.PhiN, NN, a.bN, oN, i);
-      }
-      bv_s[a2][i] = acc;
-      z_s[a2][i] = z;
-    }
-    __syncthreads();
-    if (skip_s) continue;  // uniform
-    if (tid < n * kRMax) {
-      const int a2 = tid / kRMax, j = tid % kRMax;
-      double x = 0.0;
-      for (int i = 0; i < r; ++i) x = fma(Kinv[j * kRMax + i], bv_s[a2][i], x);
-      vt_s[a2][j] = x;
-      vtr_s[a2][j] = (Real)x;
-    }
-    __syncthreads();
-    if (tid < n * n) {  // A = I - Phi_f[O, O]
-      const int a2 = tid / n, b2 = tid % n;
-      double phi = a.PhiN[(size_t)mN[e0 + a2] * NN + mN[e0 + b2]];
-      for (int j = 0; j < r; ++j) phi = fma(-z_s[a2][j], vt_s[b2][j], phi);
-      A_s[a2][b2] = (a2 == b2 ? 1.0 : 0.0) - phi;
-    }
-    __syncthreads();
-    if (tid == 0) {  // natural-order LU; its pivots are the sequential LODF denominators
-      for (int k = 0; k < n; ++k) {
-        if (!(A_s[k][k] > a.tol)) {
-          skip_s = 2;
-          ++nisl_s;
-          break;
-        }
-        for (int i = k + 1; i < n; ++i) {
-          A_s[i][k] /= A_s[k][k];
-          for (int j = k + 1; j < n; ++j) A_s[i][j] = fma(-A_s[i][k], A_s[k][j], A_s[i][j]);
+    for (int g0 = 0; g0 < n_multi; g0 += SG) {
+      const int ng = min(SG, n_multi - g0);
+      __syncthreads();  // the previous group's shared values are consumed
+      for (int s = tid; s < SG; s += blockDim.x) {
+        const int m = g0 + s;
+        const int f = s < ng ? mflag[qS + m] : 3;
+        fl_s[s] = f;
+        if (s < ng) {
+          const int e0 = mptr[m], n = mptr[m + 1] - e0;
+          e0_s[s] = e0;
+          for (int k = 0; k < 4; ++k) mp_s[s][k] = k < n ? mmpos[e0 + k] : -2;
+          if (t0 == 0 && f == 1) atomicAdd(&nisl_s, 1);
         }
       }
-    }
-    __syncthreads();
-    if (skip_s) continue;  // uniform
-    if (tid < TT) {  // weights of timestep t: A^{-1} p_f[O, t]
-      const int t = t0 + tid < T ? t0 + tid : T - 1;
-      double y[4];
-#pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) {
-        double pf = 0.0;
-        if (a2 < n) {
-          pf = a.p0[(size_t)mN[e0 + a2] * T + t];
-          for (int j = 0; j < r; ++j) pf = fma(-z_s[a2][j], alpha[j * T + t], pf);
-        }
-        y[a2] = pf;
+      for (int p = tid; p < ng * 4 * RMAX; p += blockDim.x) {
+        const int s = p / (4 * RMAX), a2 = (p / RMAX) % 4, j = p % RMAX;
+        vt_s[s][a2][j] = mvt[(qS + g0 + s) * 4 * kRMax + a2 * kRMax + j];
       }
-#pragma unroll
-      for (int i = 1; i < 4; ++i)
-#pragma unroll
-        for (int k = 0; k < i; ++k)
-          if (i < n) y[i] = fma(-A_s[i][k], y[k], y[i]);
-#pragma unroll
-      for (int i = 3; i >= 0; --i) {
-        if (i < n) {
-#pragma unroll
-          for (int k = i + 1; k < 4; ++k)
-            if (k < n) y[i] = fma(-A_s[i][k], y[k], y[i]);
-          y[i] /= A_s[i][i];
-        }
-      }
-#pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) w_s[tid][a2] = a2 < n ? (Real)y[a2] : (Real)0;
-    }
-    __syncthreads();
-    if (skip_s) continue;  // uniform
-    for (int l = tid; l < M; l += blockDim.x) {
-      Real zr[RMAX];
-#pragma unroll
-      for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
-      const Real rm = meta[Mp + l];  // an outaged monitored branch carries nothing
-      Real col[4];
-      bool in_set = false;  // a member itself carries nothing (the MODF rows O := -I)
-#pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2) {
-        col[a2] = (Real)0;
-        if (a2 < n) {
-          Real c = PhiMO[(size_t)(e0 + a2) * Mp + l];
-#pragma unroll
-          for (int j = 0; j < RMAX; ++j) c = fma(-zr[j], vtr_s[a2][j], c);
-          col[a2] = c * rm;
-          in_set |= mmpos[e0 + a2] == l;
-        }
-      }
-#pragma unroll
-      for (int jt = 0; jt < TT; ++jt) {
+      for (int p = tid; p < ng * TT * 4; p += blockDim.x) {
+        const int s = p / (TT * 4), jt = (p / 4) % TT, a2 = p % 4;
         const int t = t0 + jt < T ? t0 + jt : T - 1;  // a tail pass repeats the last timestep, never written
-        Real v = ptil[(size_t)t * Mp + l];
+        w_s[s][jt][a2] = mflag[qS + g0 + s] == 0 ? mw[((qS + g0 + s) * T + t) * 4 + a2] : (Real)0;
+      }
+      __syncthreads();
+      for (int l = tid; l < M; l += blockDim.x) {
+        Real zr[RMAX], pt[TT];
 #pragma unroll
-        for (int a2 = 0; a2 < 4; ++a2) v = fma(col[a2], w_s[jt][a2], v);
-        if (in_set) v = (Real)0;
-        if (fabs(v) > mx[jt]) {
-          mx[jt] = fabs(v);
-          ag[jt] = m;
+        for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
+#pragma unroll
+        for (int jt = 0; jt < TT; ++jt) pt[jt] = ptil[(size_t)(t0 + jt < T ? t0 + jt : T - 1) * Mp + l];
+        const Real rm = meta[Mp + l];  // an outaged monitored branch carries nothing
+        for (int s = 0; s < ng; ++s) {
+          if (fl_s[s]) continue;  // uniform
+          const int e0 = e0_s[s];
+          Real col[4];
+          bool in_set = false;  // a member itself carries nothing (the MODF rows of O are -I)
+#pragma unroll
+          for (int a2 = 0; a2 < 4; ++a2) {
+            const int mp = mp_s[s][a2];
+            Real c = (Real)0;
+            if (mp != -2) {
+              c = PhiMO[(size_t)(e0 + a2) * Mp + l];
+#pragma unroll
+              for (int j = 0; j < RMAX; ++j) c = fma(-zr[j], vt_s[s][a2][j], c);
+            }
+            col[a2] = c * rm;
+            in_set |= mp == l;
+          }
+#pragma unroll
+          for (int jt = 0; jt < TT; ++jt) {
+            Real v = pt[jt];
+#pragma unroll
+            for (int a2 = 0; a2 < 4; ++a2) v = fma(col[a2], w_s[s][jt][a2], v);
+            v = in_set ? (Real)0 : v;
+            if (fabs(v) > mx[jt]) {
+              mx[jt] = fabs(v);
+              ag[jt] = g0 + s;
+            }
+            Real dummy = (Real)0;
+            Acc<Real>::add(dummy, ov[jt], v);
+          }
         }
-        Real dummy = (Real)0;
-        Acc<Real>::add(dummy, ov[jt], v);
       }
     }
-  }
-  if (t0 == 0 && tid == 0) o.n_island_multi[tau] = nisl_s;
 #pragma unroll
-  for (int jt = 0; jt < TT; ++jt) {
-    double v = (double)mx[jt], s2 = (double)ov[jt] * Acc<Real>::ovl_scale();
-    int g = ag[jt];
+    for (int jt = 0; jt < TT; ++jt) {
+      double v = (double)mx[jt], s2 = (double)ov[jt] * Acc<Real>::ovl_scale();
+      int g = ag[jt];
 #pragma unroll
-    for (int off = 16; off; off >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
-      const int g2 = __shfl_xor_sync(0xffffffffu, g, off);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-      if (v2 > v || (v2 == v && g2 < g)) {
-        v = v2;
-        g = g2;
+      for (int off = 16; off; off >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+        const int g2 = __shfl_xor_sync(0xffffffffu, g, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+        if (v2 > v || (v2 == v && g2 < g)) {
+          v = v2;
+          g = g2;
+        }
+      }
+      if (lane == 0) {
+        rv_s[jt][wp] = v;
+        ra_s[jt][wp] = g;
+        ro_s[jt][wp] = s2;
       }
     }
-    if (lane == 0) {
-      rv_s[jt][wp] = v;
-      ra_s[jt][wp] = g;
-      ro_s[jt][wp] = s2;
+    __syncthreads();
+    if (tid < TT && t0 + tid < T) {
+      double bv = rv_s[tid][0], bo = ro_s[tid][0];
+      int bg = ra_s[tid][0];
+      for (int k = 1; k < 4; ++k) {
+        bo += ro_s[tid][k];
+        if (rv_s[tid][k] > bv || (rv_s[tid][k] == bv && ra_s[tid][k] < bg)) {
+          bv = rv_s[tid][k];
+          bg = ra_s[tid][k];
+        }
+      }
+      const size_t k2 = (size_t)tau * T + t0 + tid;
+      const bool any = bg != 0x7fffffff;
+      o.multi_max_loading[k2] = any ? bv : 0.0;
+      o.worst_multi[k2] = any ? bg : -1;
+      o.multi_overload_sum[k2] = bo;
     }
   }
   __syncthreads();
-  if (tid < TT && t0 + tid < T) {
-    double bv = rv_s[tid][0], bo = ro_s[tid][0];
-    int bg = ra_s[tid][0];
-    for (int k = 1; k < 4; ++k) {
-      bo += ro_s[tid][k];
-      if (rv_s[tid][k] > bv || (rv_s[tid][k] == bv && ra_s[tid][k] < bg)) {
-        bv = rv_s[tid][k];
-        bg = ra_s[tid][k];
-      }
-    }
-    const size_t k2 = (size_t)tau * T + t0 + tid;
-    const bool any = bg != 0x7fffffff;
-    o.multi_max_loading[k2] = any ? bv : 0.0;
-    o.worst_multi[k2] = any ? bg : -1;
-    o.multi_overload_sum[k2] = bo;
-  }
+  if (tid == 0) o.n_island_multi[tau] = nisl_s;
 }
 
 }  // namespace dcf
@@ -1677,15 +1728,21 @@ void launch_gen(const Args& a, int RMAX, int G, const int* gen_bus, const double
 }
 
 template <class Real>
-void launch_multi(const Args& a, int RMAX, int n_multi, const int* mptr, const int* mN, const int* mmpos,
-                  const void* phimo, cudaStream_t st) {
-  constexpr int TT = 8;
+void launch_multi_prep(const Args& a, int n_multi, const int* mptr, const int* mN, ChunkBufs& B, cudaStream_t st) {
+  k_multi_prep<Real><<<dim3(a.nq, (n_multi + 3) / 4), 128, 0, st>>>(a, n_multi, mptr, mN, B.mvt.as<Real>(),
+                                                                    B.mw.as<Real>(), B.mflag.as<int>());
+}
+
+template <class Real>
+void launch_multi_rows(const Args& a, int RMAX, int n_multi, const int* mptr, const int* mmpos, const void* phimo,
+                       ChunkBufs& B, cudaStream_t st) {
+  constexpr int TT = 12, SG = 32;
   const Real* P = static_cast<const Real*>(phimo);
-  for (int t0 = 0; t0 < a.T; t0 += TT) {
-    if (RMAX == 4) k_multi<Real, 4, TT><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mN, mmpos, P, t0);
-    else if (RMAX == 8) k_multi<Real, 8, TT><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mN, mmpos, P, t0);
-    else k_multi<Real, 16, TT><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mN, mmpos, P, t0);
-  }
+  const Real *vt = B.mvt.as<Real>(), *w = B.mw.as<Real>();
+  const int* f = B.mflag.as<int>();
+  if (RMAX == 4) k_multi_rows<Real, 4, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
+  else if (RMAX == 8) k_multi_rows<Real, 8, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
+  else k_multi_rows<Real, 16, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
 }
 
 int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
@@ -2046,6 +2103,8 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                     (size_t)T * ncb * (rs + 4 + 8) + 64;
   if (U > 0)
     per_slot += (size_t)TV * (Mp + C) * rs + (size_t)TV * ncb * (rs + 4 + 8) + (size_t)T * 4 + (size_t)T * (Mp + C) * rs;
+  const size_t SM_ = want_multi ? (size_t)ctx->n_multi : 0;
+  per_slot += SM_ * ((4 * kRMax + 4 * (size_t)T) * rs + 4);
   int64_t cap = ctx->opt.chunk_topo > 0 ? ctx->opt.chunk_topo : (int64_t)((size_t)2 << 30) / (int64_t)per_slot;
   cap = std::max<int64_t>(1, std::min<int64_t>({cap, 8192, (int64_t)N}));
   for (int bi = 0; bi < 2; ++bi) {
@@ -2067,6 +2126,9 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                   B.pargv.ensure(c * TV * std::max(ncb, 1) * sizeof(int)) ||
                   B.povlv.ensure(c * TV * std::max(ncb, 1) * sizeof(double)) || B.bestu.ensure(c * T * sizeof(int)) ||
                   B.ptb.ensure(c * T * Mp * rs) || B.sb.ensure(c * T * std::max(C, 1) * rs)))
+      return DCFLOW_ERR_OOM;
+    if (SM_ > 0 && (B.mvt.ensure(c * SM_ * 4 * kRMax * rs) || B.mw.ensure(c * SM_ * T * 4 * rs) ||
+                    B.mflag.ensure(c * SM_ * sizeof(int))))
       return DCFLOW_ERR_OOM;
   }
   dcflow_screen* scr = sc ? sc->scr : nullptr;
@@ -2262,6 +2324,12 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     else launch_prep<float>(ap, RMAX, ch.nq, dyn, side);
     ctx->launches += 3;
     DCF_CHECK_LAUNCH();
+    if (want_multi) {  // the multi-outage small systems ride with the FP64 preparation
+      if (fp64) launch_multi_prep<double>(ap, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(), B, side);
+      else launch_multi_prep<float>(ap, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(), B, side);
+      ++ctx->launches;
+      DCF_CHECK_LAUNCH();
+    }
     DCF_CUDA(cudaEventRecord(ctx->ev_prep[bi], side));
     DCF_CUDA(cudaStreamWaitEvent(st, ctx->ev_prep[bi], 0));
     Args af = a;  // final stage: T real timesteps
@@ -2395,12 +2463,12 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     DCF_CHECK_LAUNCH();
     if (want_multi) {
       if (fp64)
-        launch_multi<double>(af, RMAX, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(),
-                             ctx->multi_mpos.as<int>(), ctx->PhiMO.p, st);
+        launch_multi_rows<double>(af, RMAX, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multi_mpos.as<int>(),
+                                  ctx->PhiMO.p, B, st);
       else
-        launch_multi<float>(af, RMAX, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(),
-                            ctx->multi_mpos.as<int>(), ctx->PhiMO.p, st);
-      ctx->launches += (T + 7) / 8;
+        launch_multi_rows<float>(af, RMAX, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multi_mpos.as<int>(),
+                                 ctx->PhiMO.p, B, st);
+      ++ctx->launches;
       DCF_CHECK_LAUNCH();
     }
     if (G > 0) {
