@@ -332,11 +332,33 @@ def _flows_from_angles(th, f2, t2, b, alive):
 # one topology, plain definition
 # ---------------------------------------------------------------------------
 
+def eligible_injections(inc, splits, inj_bus, cap=64):
+    """Injections whose busbar an injection topology t_i chooses (Sec. III-A):
+    those at the bus of one of the topology's effective splits, in ascending
+    injection index, at most `cap` (one bit each of a candidate mask).
+    Returns [(injection, position of its split among the effective splits)]
+    and the effective split buses in that order."""
+    buses = []
+    for (A, mask) in splits:
+        nb = bin(int(mask)).count("1")
+        if nb == 0 or nb == len(inc[int(A)]):
+            continue  # one busbar empty: no split, no busbar B
+        buses.append(int(A))
+    pos = {A: i for i, A in enumerate(buses)}
+    el = [(e, pos[int(b)]) for e, b in enumerate(inj_bus) if int(b) in pos]
+    return el[:cap], buses
+
+
 def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
-                      var=None, mode="lodf", want_flows=False, want_cmax=False):
+                      var=None, mode="lodf", want_flows=False, want_cmax=False, ti=None):
     """Outputs of one topology for every timestep (and variation).
 
     P: [T, V] injections.  var: (var_ptr, var_bus, var_delta) or None.
+    ti: injection topologies T_i of this topology (Sec. III-A) as
+    (masks, inj_bus, inj_p [T, n_inj]) or None: candidate u moves the j-th
+    eligible injection (eligible_injections) from bus A onto busbar B of its
+    split when bit j of masks[u] is set; an empty candidate list or a bit
+    beyond the eligible injections makes the topology invalid.
     Returns a dict with per-timestep arrays: n0_max, n1_max, ovl, worst_cont,
     worst_mon, best_var, plus island status and n_island_cont (and n0 flows
     of the monitored branches if want_flows)."""
@@ -356,6 +378,12 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
     if st != OK:
         res["status"] = st
         return res
+    if ti is not None:
+        masks, inj_bus, inj_p = ti
+        el, sbus = eligible_injections(inc, splits, inj_bus)
+        if len(masks) == 0 or any(int(m) >> len(el) for m in masks):
+            res["status"] = INVALID
+            return res
     if components(n, f2, t2, alive) > 1:
         res["status"] = ISLANDED
         return res
@@ -375,14 +403,27 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
     Pn[:V, :] = P.T
     base_flows = _flows_from_angles(fac.solve_full(Pn), f2, t2, b, alive)  # [E, T]
 
-    nvar = 0 if var is None else len(var[0]) - 1
-    if nvar:
-        dP = np.zeros((n, nvar))
+    # candidate injection changes dP [n, T, U]: the same for every timestep for
+    # the nodal candidates of Eq. (8); per timestep for the injection topologies
+    nvar = 0
+    if var is not None and len(var[0]) > 1:
         vp, vb, vd = var
+        nvar = len(vp) - 1
+        dP = np.zeros((n, T, nvar))
         for u in range(nvar):
             for k in range(vp[u], vp[u + 1]):
-                dP[vb[k], u] += vd[k]
-        dflow = _flows_from_angles(fac.solve_full(dP), f2, t2, b, alive)  # [E, U]
+                dP[vb[k], :, u] += vd[k]
+    elif ti is not None:
+        nvar = len(masks)
+        dP = np.zeros((n, T, nvar))
+        inj_p = np.atleast_2d(np.asarray(inj_p, np.float64))
+        for u, m in enumerate(masks):
+            for j, (e, i) in enumerate(el):
+                if (int(m) >> j) & 1:
+                    dP[V + i, :, u] += inj_p[:, e]  # onto busbar B (new bus V + i)
+                    dP[sbus[i], :, u] -= inj_p[:, e]  # off busbar A
+    if nvar:
+        dflow = _flows_from_angles(fac.solve_full(dP.reshape(n, T * nvar)), f2, t2, b, alive).reshape(-1, T, nvar)
 
     if mode == "lodf":
         # Phi_tau[l, c] = PTDF_tau[l, f'_c] - PTDF_tau[l, t'_c]: flows of a unit
@@ -436,8 +477,8 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
         else:
             best = None
             for u in range(nvar):
-                p = base_flows[:, ti] + dflow[:, u]
-                r_u = metrics(p, Pn[:, ti] + dP[:, u])
+                p = base_flows[:, ti] + dflow[:, ti, u]
+                r_u = metrics(p, Pn[:, ti] + dP[:, ti, u])
                 if best is None or r_u[1] < best[0][1]:
                     best = (r_u, u, p)
             r, u_best, p = best
@@ -453,8 +494,9 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
 
 
 def evaluate(grid, topo, P, mon, cont, limit, var=None, mode="lodf", idx=None,
-             want_flows=False, want_cmax=False):
-    """Evaluate a batch of topologies (or the subset ``idx``); arrays per topology."""
+             want_flows=False, want_cmax=False, ti=None):
+    """Evaluate a batch of topologies (or the subset ``idx``); arrays per topology.
+    ti: injection topologies as (ti_ptr [n_topo + 1], ti_mask, inj_bus, inj_p [T, n_inj])."""
     inc = incident_lists(grid.n_bus, grid.f, grid.t)
     P = np.atleast_2d(np.asarray(P, np.float64))
     ids = range(topo.n_topo) if idx is None else [int(i) for i in idx]
@@ -467,8 +509,12 @@ def evaluate(grid, topo, P, mon, cont, limit, var=None, mode="lodf", idx=None,
         splits = list(zip(topo.split_sub[a:c], topo.split_mask[a:c]))
         a, c = topo.out_ptr[i], topo.out_ptr[i + 1]
         outages = list(topo.out_branch[a:c])
+        tti = None
+        if ti is not None:
+            tp, tm, ib, ip = ti
+            tti = ([int(x) for x in tm[tp[i]:tp[i + 1]]], ib, ip)
         outs.append(evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
-                                      vtuple, mode, want_flows, want_cmax))
+                                      vtuple, mode, want_flows, want_cmax, tti))
     keys = ["n0_max", "n1_max", "ovl", "worst_cont", "worst_mon", "best_var"]
     r = {k: np.stack([o[k] for o in outs]) if outs else np.zeros((0, P.shape[0])) for k in keys}
     r["status"] = np.array([o["status"] for o in outs], np.int64)

@@ -222,6 +222,59 @@ def make_variations(grid: Grid, n_var: int, n_pool: int, seed: int,
 
 
 @dataclass
+class InjectionTopologies:
+    """Injections whose busbar can be chosen and, per topology, its candidate
+    injection topologies T_i.  inj_bus [n_inj] ascending; inj_p [T, n_inj];
+    ti_ptr [n_topo + 1]; ti_mask: bit j puts the topology's j-th eligible
+    injection (at one of its split buses, ascending index) on busbar B."""
+    inj_bus: np.ndarray
+    inj_p: np.ndarray
+    ti_ptr: np.ndarray
+    ti_mask: np.ndarray
+
+    @property
+    def n_inj(self) -> int:
+        return int(self.inj_bus.size)
+
+
+def make_injection_topologies(grid: Grid, subs: np.ndarray, topo: Topologies, P: np.ndarray, n_cand: int,
+                              seed: int, per_bus: int = 3) -> InjectionTopologies:
+    """per_bus injections at every split-capable bus: a generator / load pair
+    and a remainder, summing to the bus injection P[t, bus] of every timestep;
+    n_cand random busbar assignments per topology (the first keeps every
+    injection on busbar A) over the injections at its split buses, counted per
+    split entry (a split with an empty busbar has no busbar B, so a topology
+    with one draws over fewer bits)."""
+    rng = np.random.default_rng(seed)
+    P = np.atleast_2d(P)
+    subs = np.sort(np.asarray(subs, np.int32))
+    inj_bus = np.repeat(subs, per_bus).astype(np.int32)
+    T = P.shape[0]
+    inj_p = np.zeros((T, inj_bus.size))
+    for k, a in enumerate(subs):
+        x = np.abs(rng.normal(0.5, 0.25, (T, per_bus - 1)))
+        sgn = np.where(np.arange(per_bus - 1) % 2 == 0, 1.0, -1.0)
+        inj_p[:, k * per_bus:k * per_bus + per_bus - 1] = x * sgn
+        inj_p[:, k * per_bus + per_bus - 1] = P[:, a] - (x * sgn).sum(axis=1)
+    per_sub = {int(a): per_bus for a in subs}
+    tp, tm = [0], []
+    inc = grid.incident()
+    for i in range(topo.n_topo):
+        a, c = topo.split_ptr[i], topo.split_ptr[i + 1]
+        k = 0
+        for A, m in zip(topo.split_sub[a:c], topo.split_mask[a:c]):
+            nb = bin(int(m)).count("1")
+            if 0 < nb < int(inc[int(A)].size):
+                k += per_sub.get(int(A), 0)
+        k = min(k, 64)
+        tm.append(0)
+        for _ in range(n_cand - 1):
+            tm.append(int(rng.integers(0, 1 << k, dtype=np.uint64)) if k else 0)
+        tp.append(len(tm))
+    return InjectionTopologies(inj_bus, inj_p, np.array(tp, np.int32), np.array(tm, dtype=np.uint64))
+
+
+@dataclass
 class Workload:
     name: str
     grid: Grid

@@ -238,3 +238,27 @@ def test_multi_outage_mutation_is_caught(monkeypatch):
     monkeypatch.setattr(ref, "multi_outage_n1", first_only)
     monkeypatch.setattr(oracle, "multi_outage_n1", first_only)
     assert _fails(pins.test_multi_outage_reduces_to_lodf_and_modf)
+
+
+_orig_eligible = ref.eligible_injections
+
+
+def _eligible_descending(inc, splits, inj_bus, cap=64):
+    el, buses = _orig_eligible(inc, splits, inj_bus, cap)
+    return el[::-1], buses  # planted: mask bits counted from the highest injection index
+
+
+def _eligible_first_split(inc, splits, inj_bus, cap=64):
+    el, buses = _orig_eligible(inc, splits, inj_bus, cap)
+    return [(e, 0) for e, _ in el], buses  # planted: every injection onto the first split's busbar B
+
+
+def _eligible_off_slack(inc, splits, inj_bus, cap=64):
+    el, buses = _orig_eligible(inc, splits, inj_bus, cap)
+    return el, [0 for _ in buses]  # planted: the moved power is taken off bus 0 (the slack), not bus A
+
+
+@pytest.mark.parametrize("mut", [_eligible_descending, _eligible_first_split, _eligible_off_slack])
+def test_injection_topology_mutation_is_caught(monkeypatch, mut):
+    monkeypatch.setattr(ref, "eligible_injections", mut)
+    assert _fails(pins.test_injection_topology_flows_match_the_split_grid_by_hand)

@@ -553,3 +553,148 @@ def test_multi_outage_reduces_to_lodf_and_modf():
         rho = np.abs(n1[w.mon]) / lim[w.mon]
         if r2["n_island_multi"][0] == 0:
             assert r2["multi_each"][0, t, 0] == pytest.approx(rho.max(), rel=1e-9)
+
+
+# --------------------------------------------------------------------------
+# injection topologies t_i (Sec. III-A): busbar choice of the injections at
+# split substations
+# --------------------------------------------------------------------------
+
+def _split_graph_by_hand(g, splits, outages):
+    """The split topology written out directly: busbar B of the i-th split with both busbars
+    non-empty is bus V + i and takes the masked incident branches (ascending branch id)."""
+    f2, t2 = g.f.astype(np.int64).copy(), g.t.astype(np.int64).copy()
+    inc = [sorted(np.nonzero((g.f == v) | (g.t == v))[0]) for v in range(g.n_bus)]
+    buses = []
+    for A, m in splits:
+        A, m = int(A), int(m)
+        moved = [l for j, l in enumerate(inc[A]) if (m >> j) & 1]
+        if not moved or len(moved) == len(inc[A]):
+            continue
+        nb = g.n_bus + len(buses)
+        buses.append(A)
+        for l in moved:
+            if g.f[l] == A:
+                f2[l] = nb
+            if g.t[l] == A:
+                t2[l] = nb
+    alive = np.ones(g.n_branch, bool)
+    alive[list(outages)] = False
+    return g.n_bus + len(buses), f2, t2, alive, buses
+
+
+def _ti_case(n_cand=5, T=3, seed=81):
+    g = _grid(80, 120, seed)
+    subs = synth.split_capable(g, 24, seed)
+    topo = synth.make_topologies(g, subs, 12, seed + 1, (1, 3), (0, 2))
+    P = synth.make_injections(g, T, seed + 2, daily=False)
+    mon = np.arange(g.n_branch)
+    w = synth.Workload("ti", g, topo, P, mon, mon.copy(), subs)
+    ti = synth.make_injection_topologies(g, subs, topo, P, n_cand, seed + 3)
+    lim = oracle.thermal_limits(g, P)
+    return w, ti, lim, mon
+
+
+def _one_candidate(ti, topo, u):
+    """The same injection topologies with only candidate u of every topology."""
+    tp = np.arange(topo.n_topo + 1, dtype=np.int32)
+    tm = np.array([ti.ti_mask[ti.ti_ptr[i] + u] for i in range(topo.n_topo)], dtype=np.uint64)
+    return (tp, tm, ti.inj_bus, ti.inj_p)
+
+
+def test_injection_topology_flows_match_the_split_grid_by_hand():
+    """A candidate's N-0 flows equal the PTDF of the hand-built split graph (Def. 2) applied to the
+    nodal injections with the chosen injections moved from bus A to busbar B; Kirchhoff holds at
+    busbar B with exactly the moved injections; candidate 0 (all on A) equals the plain evaluation."""
+    w, ti, lim, mon = _ti_case()
+    g = w.grid
+    plain = oracle.evaluate(g, w.topo, w.inj, mon, w.cont, lim, want_flows=True)
+    checked = 0
+    for u in range(4):
+        r = oracle.evaluate(g, w.topo, w.inj, mon, w.cont, lim, want_flows=True, ti=_one_candidate(ti, w.topo, u))
+        for i in range(w.topo.n_topo):
+            if r["status"][i] != 0:
+                continue
+            a, c = w.topo.split_ptr[i], w.topo.split_ptr[i + 1]
+            splits = list(zip(w.topo.split_sub[a:c], w.topo.split_mask[a:c]))
+            a, c = w.topo.out_ptr[i], w.topo.out_ptr[i + 1]
+            n, f2, t2, alive, buses = _split_graph_by_hand(g, splits, list(w.topo.out_branch[a:c]))
+            elig = [e for e in range(ti.n_inj) if int(ti.inj_bus[e]) in buses][:64]
+            m = int(ti.ti_mask[ti.ti_ptr[i] + u])
+            Pn = np.zeros((w.inj.shape[0], n))
+            Pn[:, :g.n_bus] = w.inj
+            moved = np.zeros((w.inj.shape[0], len(buses)))
+            for j, e in enumerate(elig):
+                if (m >> j) & 1:
+                    k = buses.index(int(ti.inj_bus[e]))
+                    Pn[:, g.n_bus + k] += ti.inj_p[:, e]
+                    Pn[:, buses[k]] -= ti.inj_p[:, e]
+                    moved[:, k] += ti.inj_p[:, e]
+            H = oracle.ptdf(n, f2[alive], t2[alive], g.b[alive], g.slack)
+            fl = np.zeros((w.inj.shape[0], g.n_branch))
+            fl[:, alive] = Pn @ H.T
+            np.testing.assert_allclose(r["n0_flow"][i], fl[:, mon], atol=1e-9)
+            for k in range(len(buses)):  # Kirchhoff at busbar B
+                out = fl[:, f2 == g.n_bus + k].sum(axis=1) - fl[:, t2 == g.n_bus + k].sum(axis=1)
+                np.testing.assert_allclose(out, moved[:, k], atol=1e-9)
+            if u == 0:
+                np.testing.assert_allclose(r["n0_flow"][i], plain["n0_flow"][i], atol=1e-12)
+                np.testing.assert_allclose(r["n1_max"][i], plain["n1_max"][i], atol=1e-12)
+            checked += int(m != 0)
+    assert checked >= 10
+
+
+def test_injection_topology_n1_equals_refactorisation():
+    """The N-1 of every injection topology by Def. 3 (LODF of the topology's own PTDF) equals a
+    fresh factorisation without each contingency under the moved injections."""
+    w, ti, lim, mon = _ti_case(n_cand=3, T=2, seed=82)
+    differs = 0
+    for u in range(3):  # one candidate at a time: no argmin between near-equal candidates
+        t = _one_candidate(ti, w.topo, u)
+        a = oracle.evaluate(w.grid, w.topo, w.inj, mon, w.cont, lim, ti=t, idx=range(6))
+        b = oracle.evaluate(w.grid, w.topo, w.inj, mon, w.cont, lim, ti=t, idx=range(6), mode="refactor")
+        np.testing.assert_array_equal(a["status"], b["status"])
+        np.testing.assert_allclose(a["n1_max"], b["n1_max"], atol=1e-9)
+        np.testing.assert_allclose(a["ovl"], b["ovl"], rtol=1e-10, atol=1e-8)
+        np.testing.assert_array_equal(a["worst_cont"], b["worst_cont"])
+        if u == 0:
+            ovl0 = a["ovl"]
+        else:
+            differs += int((np.abs(a["ovl"] - ovl0) > 1e-6).sum())
+    assert differs > 0  # the candidates do change the N-1 flows
+
+
+def test_injection_topology_argmin_and_invalid_lists():
+    """t_i* is the argmin of agg_m over T_i, ties to the lowest index (a duplicated candidate never
+    wins); an empty list or a mask bit beyond the eligible injections makes the topology invalid."""
+    w, ti, lim, mon = _ti_case(n_cand=4, T=2, seed=83)
+    N = w.topo.n_topo
+    # append a copy of candidate 2 to every list
+    tp, tm = [0], []
+    for i in range(N):
+        lst = list(ti.ti_mask[ti.ti_ptr[i]:ti.ti_ptr[i + 1]])
+        tm.extend(lst + [lst[2]])
+        tp.append(len(tm))
+    t = (np.array(tp, np.int32), np.array(tm, dtype=np.uint64), ti.inj_bus, ti.inj_p)
+    r = oracle.evaluate(w.grid, w.topo, w.inj, mon, w.cont, lim, ti=t)
+    each = [oracle.evaluate(w.grid, w.topo, w.inj, mon, w.cont, lim, ti=_one_candidate(ti, w.topo, u))
+            for u in range(4)]
+    ok = r["status"] == 0
+    assert ok.sum() >= 6
+    vals = np.stack([e["n1_max"] for e in each], axis=2)  # [N, T, U]
+    np.testing.assert_allclose(r["n1_max"][ok], vals[ok].min(axis=2), atol=1e-12)
+    assert (r["best_var"][ok] != 4).all()
+    for i in np.nonzero(ok)[0]:
+        for tt in range(2):
+            u = r["best_var"][i, tt]
+            assert vals[i, tt, u] == pytest.approx(vals[i, tt].min(), abs=1e-12)
+            assert r["ovl"][i, tt] == pytest.approx(each[u]["ovl"][i, tt], abs=1e-10)
+    # invalid: topology 0 without candidates, topology 1 with a bit beyond its eligible injections
+    inc = oracle.incident_lists(w.grid.n_bus, w.grid.f, w.grid.t)
+    a, c = w.topo.split_ptr[1], w.topo.split_ptr[2]
+    el, _ = oracle.eligible_injections(inc, list(zip(w.topo.split_sub[a:c], w.topo.split_mask[a:c])), ti.inj_bus)
+    tp = np.array([0, 0] + [1 + k for k in range(N - 1)], np.int32)
+    tm = np.array([1 << len(el)] + [0] * (N - 2), dtype=np.uint64)
+    r2 = oracle.evaluate(w.grid, w.topo, w.inj, mon, w.cont, lim, ti=(tp, tm, ti.inj_bus, ti.inj_p))
+    assert r2["status"][0] == 2 and r2["status"][1] == 2
+    assert (r2["status"][2:] == r["status"][2:]).all()
