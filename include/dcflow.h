@@ -184,6 +184,28 @@ typedef struct {
   int32_t n_gen;
   const int32_t* gen_bus;
   const double* gen_p;
+  /* injection topologies t_i (Sec. III-A: the busbar of every injection of a
+   * split substation), optional (ti_ptr = NULL disables; not with var_*,
+   * generator failures, multi-outage outputs or the screener).
+   *  n_inj    injections whose busbar can be chosen
+   *  inj_bus  int32[n_inj]  bus of each (its power is already part of inj)
+   *  inj_p    double[n_time * n_inj]  their power per timestep
+   *  ti_ptr   int32[n_topo + 1]  topology tau evaluates the candidates
+   *           ti_mask[ti_ptr[tau] .. ti_ptr[tau + 1]) (its set T_i)
+   *  ti_mask  uint64[]  bit j moves the topology's j-th eligible injection
+   *           from busbar A onto busbar B
+   * A topology's eligible injections are those at the bus of one of its splits
+   * with both busbars non-empty, in ascending injection index, at most 64.
+   * Per (topology, timestep) the candidate with the lowest n1_max_loading wins
+   * (ties: lowest index; Eq. (8) over T_i) and best_var reports its index in
+   * the topology's list; every other output is that candidate's.  A topology
+   * without candidates, or with a mask bit at or beyond its number of eligible
+   * injections, is invalid (island_flag 2).  n_time * max_tau |T_i| <= 2^20. */
+  int32_t n_inj;
+  const int32_t* inj_bus;
+  const double* inj_p;
+  const int32_t* ti_ptr;
+  const uint64_t* ti_mask;
 } dcflow_batch;
 
 /*
@@ -198,7 +220,8 @@ typedef struct {
  *  worst_mon      int32[n_topo * n_time]  position in `mon` of the arg-max (ties:
  *                 lowest), -1 if none, or NULL
  *  best_var       int32[n_topo * n_time]  chosen candidate (argmin of n1_max_loading,
- *                 ties to the lowest index), or NULL; -1 without candidates
+ *                 ties to the lowest index; for injection topologies the index in
+ *                 the topology's own list), or NULL; -1 without candidates
  *  island_flag    uint8[n_topo]  0 ok, 1 the topology islands (outputs zero / -1),
  *                 2 invalid topology input
  *  n_island_cont  int32[n_topo]  contingencies skipped because they island

@@ -550,10 +550,12 @@ def top_cases(cmax, cargmax, k):
     return oc.reshape(shp + (k,)), om.reshape(shp + (k,)), ol.reshape(shp + (k,))
 
 
-def n1_loading_column(grid, splits, outages, P_t, mon, c_branch, limit):
+def n1_loading_column(grid, splits, outages, P_t, mon, c_branch, limit, moved=None):
     """|p_n1| / limit over the monitored branches for one contingency branch, by
-    refactorisation of the topology without it (None if it islands)."""
-    fl, info = topology_flows(grid, splits, list(outages) + [int(c_branch)], P_t)
+    refactorisation of the topology without it (None if it islands).  moved:
+    optional [(position of an effective split, power)] put on that split's
+    busbar B and taken off its bus A (an injection topology, Sec. III-A)."""
+    fl, info = topology_flows(grid, splits, list(outages) + [int(c_branch)], P_t, moved)
     if fl is None:
         return None
     return np.abs(fl[np.asarray(mon)]) / np.asarray(limit)[np.asarray(mon)]
@@ -580,8 +582,9 @@ def loadflow_count(res, n_timesteps, n_var=0):
     return int(res["n_valid_cont"][ok].sum()) * n_timesteps * max(1, n_var)
 
 
-def topology_flows(grid, splits, outages, P):
-    """N-0 flows [E] (or [E, T]) of one rebuilt topology; also returns (status, n, f2, t2, alive)."""
+def topology_flows(grid, splits, outages, P, moved=None):
+    """N-0 flows [E] (or [E, T]) of one rebuilt topology; also returns (status, n, f2, t2, alive).
+    moved: optional [(position of an effective split, power)] moved from its bus A onto its busbar B."""
     inc = incident_lists(grid.n_bus, grid.f, grid.t)
     st, n, f2, t2, alive, _ = build_topology(grid.n_bus, grid.f, grid.t, inc, splits, outages)
     if st != OK or components(n, f2, t2, alive) > 1:
@@ -590,6 +593,11 @@ def topology_flows(grid, splits, outages, P):
     P = np.asarray(P, np.float64)
     Pn = np.zeros((n,) + P.shape[1:])
     Pn[:grid.n_bus] = P
+    if moved:
+        _, sbus = eligible_injections(inc, splits, [])
+        for i, pw in moved:
+            Pn[grid.n_bus + i] += pw
+            Pn[sbus[i]] -= pw
     return _flows_from_angles(fac.solve_full(Pn), f2, t2, grid.b, alive), (OK, n, f2, t2, alive)
 
 

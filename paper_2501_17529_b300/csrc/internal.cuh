@@ -59,10 +59,12 @@ struct ChunkBufs {
   DevBuf selmask, sfb, csel, nsel, work, nwork;
   // multi-outage sets: per (topology, set) K^{-1}-weighted columns, weights, flags
   DevBuf mvt, mw, mflag;
+  // injection topologies: Z[c, :] / den_c, eligible injections and their split rows, their count
+  DevBuf zcd, tiel, tirow, nel;
   void release_all() {
     DevBuf* b[] = {&ent_n, &ent_s, &ent_w, &mod_ptr, &q_info, &Kinv, &alpha, &Vt64, &VtR, &Zs, &ptil, &meta,
                    &s, &valid, &nisl, &pmax, &parg, &povl, &ptv, &svv, &pmaxv, &pargv, &povlv, &bestu, &ptb, &sb,
-                   &selmask, &sfb, &csel, &nsel, &work, &nwork, &mvt, &mw, &mflag};
+                   &selmask, &sfb, &csel, &nsel, &work, &nwork, &mvt, &mw, &mflag, &zcd, &tiel, &tirow, &nel};
     for (auto* x : b) x->release();
   }
 };

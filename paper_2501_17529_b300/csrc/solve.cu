@@ -360,7 +360,7 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
 //                       row 1: 1 (0 for an outaged l), row 2: position of l in
 //                       the contingency list as int bits (-1 if none), row 3: 0
 template <class Real, int RMAX>
-__global__ __launch_bounds__(128) void k_rows(Args a) {
+__global__ __launch_bounds__(128) void k_rows(Args a, Real* __restrict__ zcd) {
   const int q = blockIdx.x;
   __shared__ EntSmem S;
   __shared__ int outN[kRMax];
@@ -432,6 +432,9 @@ __global__ __launch_bounds__(128) void k_rows(Args a) {
     if (mp >= 0) meta[mp] = (Real)(-den * a.inv_lim[mp]);
     // the denominator is FP64; its reciprocal only needs the working precision
     const Real invd = ok ? (Real)1 / (Real)den : (Real)0;
+    if (zcd)  // Z[c, :] / den_c for the injection-topology candidates
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) zcd[((size_t)q * kRMax + j) * C + c] = (Real)z[j] * invd;
     for (int t = 0; t < T; ++t) {
       Real pf = (Real)a.p0[(size_t)nc * T + t];
 #pragma unroll
@@ -738,6 +741,134 @@ __global__ void k_var_expand(Args ap, int T, int U, const int* __restrict__ var_
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
     Real v = sv[(size_t)t * C + c];
     for (int k = k0; k < k1; ++k) v = fma((Real)var_delta[k], sv[(size_t)(T + var_k[k]) * C + c], v);
+    so[c] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// injection topologies t_i (Sec. III-A): the busbar of every injection at a
+// split substation.  Moving injections of power q_i onto busbar B of split i
+// changes only the right-hand side of that split's row of the r x r system:
+// Sigma^T p_f = q instead of 0, so alpha' = alpha - K^{-1} q and
+//   p_f' = p_f + Z K^{-1} q,   s' = s + (Z[c, :] / den_c) K^{-1} q.
+// Z, K and Phi_f stay those of the branch topology: a candidate is a rank-r
+// correction of the N-0 operands, then the candidate machinery of Eq. (8)
+// (screen on the maximum, argmin, full N-1 of the winner) runs unchanged.
+// ---------------------------------------------------------------------------
+// Per slot: the eligible injections (at an effective split's bus, ascending
+// index, at most 64) and their split rows; a topology with no candidate or a
+// mask bit beyond its eligible injections becomes invalid.
+__global__ __launch_bounds__(128) void k_ti_decode(GridDev g, BatchDev in, Args a, int n_inj,
+                                                   const int* __restrict__ inj_bus, const int* __restrict__ ti_ptr,
+                                                   const uint64_t* __restrict__ ti_mask, int* __restrict__ tiel,
+                                                   int* __restrict__ tirow, int* __restrict__ nel) {
+  __shared__ int sbus[kRMax];
+  __shared__ int nsb, cnt;
+  __shared__ int wcnt[4];
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  QInfo qi = a.qi[q];
+  if (qi.status != ST_OK) {
+    if (tid == 0) nel[q] = 0;
+    return;
+  }
+  const int tau = qi.tau;
+  if (tid == 0) {  // effective splits in decode order (the rows i < ks)
+    int k = 0;
+    for (int e = in.split_ptr[tau]; e < in.split_ptr[tau + 1]; ++e) {
+      const int A = in.split_sub[e];
+      const int deg = g.inc_ptr[A + 1] - g.inc_ptr[A], nb = __popcll(in.split_mask[e]);
+      if (nb == 0 || nb == deg) continue;
+      if (k < kRMax) sbus[k] = A;
+      ++k;
+    }
+    nsb = k < kRMax ? k : kRMax;
+    cnt = 0;
+  }
+  __syncthreads();
+  for (int e0 = 0; e0 < n_inj; e0 += blockDim.x) {  // stable compaction, ascending injection index
+    if (cnt >= 64) break;  // uniform: read after a barrier
+    const int e = e0 + tid;
+    int row = -1;
+    if (e < n_inj) {
+      const int b = inj_bus[e];
+      for (int i = 0; i < nsb; ++i)
+        if (sbus[i] == b) row = i;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, row >= 0);
+    if (lane == 0) wcnt[wp] = __popc(bal);
+    __syncthreads();
+    int off = cnt + __popc(bal & ((1u << lane) - 1u));
+    for (int w = 0; w < wp; ++w) off += wcnt[w];
+    if (row >= 0 && off < 64) {
+      tiel[(size_t)q * 64 + off] = e;
+      tirow[(size_t)q * 64 + off] = row;
+    }
+    __syncthreads();
+    if (tid == 0) cnt += wcnt[0] + wcnt[1] + wcnt[2] + wcnt[3];
+    __syncthreads();
+  }
+  const int ne = cnt < 64 ? cnt : 64;
+  const int u0 = ti_ptr[tau], u1 = ti_ptr[tau + 1];
+  int bad = u1 <= u0;
+  for (int u = u0 + tid; u < u1; u += blockDim.x) bad |= ne < 64 && (ti_mask[u] >> ne) != 0ull;
+  bad = __syncthreads_or(bad);
+  if (tid == 0) {
+    nel[q] = ne;
+    if (bad) {
+      qi.status = ST_INVALID;
+      a.qi[q] = qi;
+    }
+  }
+}
+
+// Operands of every (timestep, candidate): the rank-r correction above; a
+// topology with fewer candidates than U repeats its first one (an exact tie
+// that the argmin resolves to the original)
+template <class Real>
+__global__ __launch_bounds__(128) void k_ti_expand(Args ap, int T, int U, const int* __restrict__ ti_ptr,
+                                                   const uint64_t* __restrict__ ti_mask,
+                                                   const double* __restrict__ inj_p, int n_inj,
+                                                   const int* __restrict__ tiel, const int* __restrict__ tirow,
+                                                   const int* __restrict__ nel, const Real* __restrict__ zcd,
+                                                   Real* __restrict__ ptv, Real* __restrict__ svv) {
+  const int q = blockIdx.y;
+  const QInfo qi = ap.qi[q];
+  if (qi.status != ST_OK) return;
+  __shared__ double qv[kRMax];
+  __shared__ Real w_s[kRMax];
+  const int vt = blockIdx.x, t = vt / U, u = vt % U;
+  const int Mp = ap.Mpad, M = ap.M, C = ap.C, TV = T * U, r = qi.r, ks = qi.ks, tid = threadIdx.x;
+  const int u0 = ti_ptr[qi.tau], nu = ti_ptr[qi.tau + 1] - u0;
+  const uint64_t m = ti_mask[u0 + (u < nu ? u : 0)];
+  if (tid < kRMax) {  // q_i: power moved onto busbar B of split i at timestep t
+    double acc = 0.0;
+    if (tid < ks)
+      for (int j = 0; j < nel[q]; ++j)
+        if (((m >> j) & 1ull) && tirow[(size_t)q * 64 + j] == tid) acc += inj_p[(size_t)t * n_inj + tiel[(size_t)q * 64 + j]];
+    qv[tid] = acc;
+  }
+  __syncthreads();
+  if (tid < kRMax) {  // w = K^{-1} q (only the split rows of q are nonzero)
+    const double* Kinv = ap.Kinv + (size_t)q * kRMax * kRMax;
+    double x = 0.0;
+    for (int i = 0; i < ks; ++i) x = fma(Kinv[tid * kRMax + i], qv[i], x);
+    w_s[tid] = tid < r ? (Real)x : (Real)0;
+  }
+  __syncthreads();
+  const Real* pt = static_cast<const Real*>(ap.ptil) + (size_t)q * T * Mp;
+  const Real* sv = static_cast<const Real*>(ap.s) + (size_t)q * T * C;
+  const Real* Zs = static_cast<const Real*>(ap.Zs) + (size_t)q * kRMax * Mp;
+  const Real* zc = zcd + (size_t)q * kRMax * C;
+  Real* po = ptv + ((size_t)q * TV + vt) * Mp;
+  Real* so = svv + ((size_t)q * TV + vt) * C;
+  for (int l = tid; l < M; l += blockDim.x) {
+    Real v = pt[(size_t)t * Mp + l];
+    for (int j = 0; j < r; ++j) v = fma(Zs[(size_t)j * Mp + l], w_s[j], v);
+    po[l] = v;
+  }
+  for (int c = tid; c < C; c += blockDim.x) {
+    Real v = sv[(size_t)t * C + c];
+    for (int j = 0; j < r; ++j) v = fma(zc[(size_t)j * C + c], w_s[j], v);
     so[c] = v;
   }
 }
@@ -1749,16 +1880,17 @@ int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
 
 // per-topology r x r systems and row operands of one chunk
 template <class Real>
-void launch_prep(const Args& a, int RMAX, int nq, size_t dyn, cudaStream_t st) {
+void launch_prep(const Args& a, int RMAX, int nq, size_t dyn, cudaStream_t st, void* zcd) {
+  Real* zc = static_cast<Real*>(zcd);
   if (RMAX == 4) {
     k_small<Real, 4><<<nq, 128, 0, st>>>(a);
-    k_rows<Real, 4><<<nq, 128, dyn, st>>>(a);
+    k_rows<Real, 4><<<nq, 128, dyn, st>>>(a, zc);
   } else if (RMAX == 8) {
     k_small<Real, 8><<<nq, 128, 0, st>>>(a);
-    k_rows<Real, 8><<<nq, 128, dyn, st>>>(a);
+    k_rows<Real, 8><<<nq, 128, dyn, st>>>(a, zc);
   } else {
     k_small<Real, 16><<<nq, 128, 0, st>>>(a);
-    k_rows<Real, 16><<<nq, 128, dyn, st>>>(a);
+    k_rows<Real, 16><<<nq, 128, dyn, st>>>(a, zc);
   }
 }
 
@@ -1971,6 +2103,39 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   // injection candidates T_i (Eq. (8)): read the small CSR to the host, validate
   // it, and map every entry to a pool bus (a column of the extended base flows)
   const int U = bt->n_var;
+  // injection topologies t_i: the per-topology candidate counts come to the
+  // host (one int per topology) to size the candidate pipeline
+  const bool TI = bt->ti_ptr != nullptr;
+  int UI = 0;
+  if (TI) {
+    if (mode != kModeFull || U > 0 || bt->n_inj < 0 || (bt->n_inj > 0 && (!bt->inj_bus || !bt->inj_p))) {
+      set_error("dcflow_solve_batch: injection topologies need inj_bus and inj_p (n_inj >= 0), without "
+                "injection candidates or the screener");
+      return DCFLOW_ERR_INVALID_ARG;
+    }
+    std::vector<int> tp(N + 1), ib(std::max(bt->n_inj, 1));
+    DCF_CUDA(cudaMemcpyAsync(tp.data(), bt->ti_ptr, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, st));
+    if (bt->n_inj)
+      DCF_CUDA(cudaMemcpyAsync(ib.data(), bt->inj_bus, sizeof(int) * bt->n_inj, cudaMemcpyDeviceToHost, st));
+    DCF_CUDA(cudaStreamSynchronize(st));
+    bool ok = tp[0] == 0;
+    for (int i = 0; i < N && ok; ++i) {
+      ok = tp[i + 1] >= tp[i];
+      UI = std::max(UI, tp[i + 1] - tp[i]);
+    }
+    for (int e = 0; e < bt->n_inj && ok; ++e) ok = ib[e] >= 0 && ib[e] < ctx->V;
+    if (!ok || (tp[N] > 0 && !bt->ti_mask)) {
+      set_error("dcflow_solve_batch: ti_ptr must start at 0 and not decrease, ti_mask must be given, "
+                "inj_bus in range");
+      return DCFLOW_ERR_INVALID_ARG;
+    }
+    UI = std::max(UI, 1);  // every topology without candidates is invalid; keep the pipeline shape
+    if ((int64_t)T * UI > (1 << 20)) {
+      set_error("dcflow_solve_batch: n_time * max |T_i| > 2^20");
+      return DCFLOW_ERR_INVALID_ARG;
+    }
+  }
+  const int Uc = U > 0 ? U : UI;  // candidates per (topology, timestep) of either form
   const int top_k = mode == kModeFeatures ? 0 : res->top_k;
   if (top_k != 0 && (top_k < 1 || top_k > 64 || !res->top_cont || !res->top_mon || !res->top_loading ||
                      mode != kModeFull || ctx->C > 2048)) {
@@ -1981,19 +2146,19 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   const bool want_multi = mode == kModeFull && res->multi_max_loading;
   if ((res->multi_max_loading || res->worst_multi || res->multi_overload_sum || res->n_island_multi) &&
       (!res->multi_max_loading || !res->worst_multi || !res->multi_overload_sum || !res->n_island_multi ||
-       mode != kModeFull || U > 0 || ctx->n_multi == 0)) {
+       mode != kModeFull || Uc > 0 || ctx->n_multi == 0)) {
     set_error("dcflow_solve_batch: multi-outage outputs need all four arrays and a study with multi-outage sets, "
               "without injection candidates or the screener");
     return DCFLOW_ERR_INVALID_ARG;
   }
   const int G = mode == kModeFull ? bt->n_gen : 0;
-  if (bt->n_gen < 0 || (bt->n_gen > 0 && (mode != kModeFull || U > 0 || !bt->gen_bus || !bt->gen_p ||
+  if (bt->n_gen < 0 || (bt->n_gen > 0 && (mode != kModeFull || Uc > 0 || !bt->gen_bus || !bt->gen_p ||
                                           !res->gen_max_loading || !res->worst_gen || !res->gen_overload_sum))) {
     set_error("dcflow_solve_batch: generator failures need gen_bus, gen_p and the three generator outputs, "
               "without injection candidates or the screener");
     return DCFLOW_ERR_INVALID_ARG;
   }
-  if (mode != kModeFull && U > 0) {
+  if (mode != kModeFull && Uc > 0) {
     set_error("dcflow_solve_batch: the screener runs without injection candidates");
     return DCFLOW_ERR_INVALID_ARG;
   }
@@ -2092,7 +2257,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   const int C_eff = ctx->C_eff;       // contingencies that can be valid (base-grid bridges excluded)
   const int ncb = (C_eff + 63) / 64;  // 64-contingency blocks of the N-1 kernels
   const int Mp = (int)round_up(M, 16);
-  const int TV = T * U;  // virtual timesteps: (timestep, candidate) pairs
+  const int TV = T * Uc;  // virtual timesteps: (timestep, candidate) pairs
   if (R > 64) {
     set_error("dcflow_solve_batch: at most 64 distinct candidate buses");
     return DCFLOW_ERR_INVALID_ARG;
@@ -2101,7 +2266,8 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                     (size_t)kRMax * kRMax * 8 + (size_t)kRMax * Text * 8 + (size_t)kRMax * C * (8 + rs) +
                     (size_t)Mp * (kRMax + Text + 4) * rs + (size_t)Text * C * rs + C + 4 +
                     (size_t)T * ncb * (rs + 4 + 8) + 64;
-  if (U > 0)
+  if (TI) per_slot += (size_t)kRMax * C * rs + 64 * 8 + 4;
+  if (Uc > 0)
     per_slot += (size_t)TV * (Mp + C) * rs + (size_t)TV * ncb * (rs + 4 + 8) + (size_t)T * 4 + (size_t)T * (Mp + C) * rs;
   const size_t SM_ = want_multi ? (size_t)ctx->n_multi : 0;
   per_slot += SM_ * ((4 * kRMax + 4 * (size_t)T) * rs + 4);
@@ -2121,7 +2287,10 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
         B.parg.ensure(c * T * std::max(ncb, 1) * sizeof(int)) ||
         B.povl.ensure(c * T * std::max(ncb, 1) * sizeof(double)))
       return DCFLOW_ERR_OOM;
-    if (U > 0 && (B.ptv.ensure(c * TV * Mp * rs) || B.svv.ensure(c * TV * std::max(C, 1) * rs) ||
+    if (TI && (B.zcd.ensure(c * kRMax * std::max(C, 1) * rs) || B.tiel.ensure(c * 64 * sizeof(int)) ||
+               B.tirow.ensure(c * 64 * sizeof(int)) || B.nel.ensure(c * sizeof(int))))
+      return DCFLOW_ERR_OOM;
+    if (Uc > 0 && (B.ptv.ensure(c * TV * Mp * rs) || B.svv.ensure(c * TV * std::max(C, 1) * rs) ||
                   B.pmaxv.ensure(c * TV * std::max(ncb, 1) * rs) ||
                   B.pargv.ensure(c * TV * std::max(ncb, 1) * sizeof(int)) ||
                   B.povlv.ensure(c * TV * std::max(ncb, 1) * sizeof(double)) || B.bestu.ensure(c * T * sizeof(int)) ||
@@ -2184,7 +2353,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   base.C = C;
   base.NN = NN;
   base.T = T;
-  base.U = U;
+  base.U = Uc;
   base.monN = ctx->monN.as<int>();
   base.contN = ctx->contN.as<int>();
   base.cpos = ctx->cpos_of_mon.as<int>();
@@ -2313,15 +2482,20 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     // the N-0 outputs to the gather of the chosen candidate
     Args ap = a;
     ap.T = Text;
-    if (U > 0) {
+    if (Uc > 0) {
       ap.out.n0_flow = nullptr;
       ap.out.n0_max_loading = nullptr;
     }
     if (i >= 2) DCF_CUDA(cudaStreamWaitEvent(side, ctx->ev_free[bi], 0));
     const int* dperm = ctx->perm.as<int>() + ch.c0;
     k_decode<<<(ch.nq + 127) / 128, 128, 0, side>>>(g, in, dperm, ap);
-    if (fp64) launch_prep<double>(ap, RMAX, ch.nq, dyn, side);
-    else launch_prep<float>(ap, RMAX, ch.nq, dyn, side);
+    if (TI) {
+      k_ti_decode<<<ch.nq, 128, 0, side>>>(g, in, ap, bt->n_inj, bt->inj_bus, bt->ti_ptr, bt->ti_mask,
+                                            B.tiel.as<int>(), B.tirow.as<int>(), B.nel.as<int>());
+      ++ctx->launches;
+    }
+    if (fp64) launch_prep<double>(ap, RMAX, ch.nq, dyn, side, TI ? B.zcd.p : nullptr);
+    else launch_prep<float>(ap, RMAX, ch.nq, dyn, side, TI ? B.zcd.p : nullptr);
     ctx->launches += 3;
     DCF_CHECK_LAUNCH();
     if (want_multi) {  // the multi-outage small systems ride with the FP64 preparation
@@ -2333,14 +2507,24 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     DCF_CUDA(cudaEventRecord(ctx->ev_prep[bi], side));
     DCF_CUDA(cudaStreamWaitEvent(st, ctx->ev_prep[bi], 0));
     Args af = a;  // final stage: T real timesteps
-    if (U > 0) {
+    if (Uc > 0) {
       // expand, screen (metric-first: maximum only), select, gather
-      if (fp64)
+      if (TI) {
+        if (fp64)
+          k_ti_expand<double><<<dim3(TV, ch.nq), 128, 0, st>>>(
+              ap, T, Uc, bt->ti_ptr, bt->ti_mask, bt->inj_p, bt->n_inj, B.tiel.as<int>(), B.tirow.as<int>(),
+              B.nel.as<int>(), B.zcd.as<double>(), B.ptv.as<double>(), B.svv.as<double>());
+        else
+          k_ti_expand<float><<<dim3(TV, ch.nq), 128, 0, st>>>(
+              ap, T, Uc, bt->ti_ptr, bt->ti_mask, bt->inj_p, bt->n_inj, B.tiel.as<int>(), B.tirow.as<int>(),
+              B.nel.as<int>(), B.zcd.as<float>(), B.ptv.as<float>(), B.svv.as<float>());
+      } else if (fp64) {
         k_var_expand<double><<<dim3(TV, ch.nq), 128, 0, st>>>(ap, T, U, bt->var_ptr, ctx->var_k.as<int>(),
                                                                bt->var_delta, B.ptv.as<double>(), B.svv.as<double>());
-      else
+      } else {
         k_var_expand<float><<<dim3(TV, ch.nq), 128, 0, st>>>(ap, T, U, bt->var_ptr, ctx->var_k.as<int>(),
                                                               bt->var_delta, B.ptv.as<float>(), B.svv.as<float>());
+      }
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
       Args av = a;
@@ -2358,13 +2542,13 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
         DCF_CUDA(cudaMemsetAsync(B.pargv.p, 0xff, (size_t)ch.nq * TV * sizeof(int), st));
       }
       const dim3 gs(ch.nq, (T + 7) / 8);
-      if (fp64) k_var_select<double><<<gs, 256, 0, st>>>(av, T, U, B.bestu.as<int>());
-      else k_var_select<float><<<gs, 256, 0, st>>>(av, T, U, B.bestu.as<int>());
+      if (fp64) k_var_select<double><<<gs, 256, 0, st>>>(av, T, Uc, B.bestu.as<int>());
+      else k_var_select<float><<<gs, 256, 0, st>>>(av, T, Uc, B.bestu.as<int>());
       af.ptil = B.ptb.p;
       af.s = B.sb.p;
       af.best_u = B.bestu.as<int>();
-      if (fp64) k_var_gather<double><<<dim3(T, ch.nq), 128, 0, st>>>(af, U, B.ptv.as<double>(), B.svv.as<double>());
-      else k_var_gather<float><<<dim3(T, ch.nq), 128, 0, st>>>(af, U, B.ptv.as<float>(), B.svv.as<float>());
+      if (fp64) k_var_gather<double><<<dim3(T, ch.nq), 128, 0, st>>>(af, Uc, B.ptv.as<double>(), B.svv.as<double>());
+      else k_var_gather<float><<<dim3(T, ch.nq), 128, 0, st>>>(af, Uc, B.ptv.as<float>(), B.svv.as<float>());
       ctx->launches += 2;
       DCF_CHECK_LAUNCH();
     }

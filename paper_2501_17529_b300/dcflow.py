@@ -39,7 +39,9 @@ class Batch(ctypes.Structure):
                 ("split_mask", c_void_p), ("out_ptr", c_void_p), ("out_branch", c_void_p),
                 ("n_time", c_int32), ("inj", c_void_p), ("n_var", c_int32),
                 ("var_ptr", c_void_p), ("var_bus", c_void_p), ("var_delta", c_void_p),
-                ("n_gen", c_int32), ("gen_bus", c_void_p), ("gen_p", c_void_p)]
+                ("n_gen", c_int32), ("gen_bus", c_void_p), ("gen_p", c_void_p),
+                ("n_inj", c_int32), ("inj_bus", c_void_p), ("inj_p", c_void_p), ("ti_ptr", c_void_p),
+                ("ti_mask", c_void_p)]
 
 
 class Results(ctypes.Structure):
@@ -370,7 +372,9 @@ def dcflow_strerror(code: int) -> str:
 class DeviceBatch:
     """Device copies of the topology CSR, injections and optional candidates."""
 
-    def __init__(self, topo, inj, var=None, device="cuda", gen_bus=None, gen_p=None):
+    def __init__(self, topo, inj, var=None, device="cuda", gen_bus=None, gen_p=None, ti=None):
+        """ti: injection topologies (inj_bus, inj_p [T, n_inj], ti_ptr, ti_mask), e.g.
+        synth.InjectionTopologies."""
         import torch
         self.n_topo = int(topo.n_topo)
         self.n_time = int(np.atleast_2d(inj).shape[0])
@@ -393,12 +397,22 @@ class DeviceBatch:
             self.gen_p = torch.as_tensor(np.ascontiguousarray(np.atleast_2d(gen_p), np.float64), device=device)
         else:
             self.gen_bus = self.gen_p = None
+        self.has_ti = ti is not None
+        self.n_inj = 0
+        self.inj_bus = self.inj_p = self.ti_ptr = self.ti_mask = None
+        if self.has_ti:
+            self.n_inj = int(np.asarray(ti.inj_bus).size)
+            self.inj_bus = torch.as_tensor(np.asarray(ti.inj_bus, np.int32), device=device)
+            self.inj_p = torch.as_tensor(np.ascontiguousarray(np.atleast_2d(ti.inj_p), np.float64), device=device)
+            self.ti_ptr = torch.as_tensor(np.asarray(ti.ti_ptr, np.int32), device=device)
+            self.ti_mask = torch.as_tensor(np.asarray(ti.ti_mask, np.uint64).view(np.int64), device=device)
 
     def cstruct(self) -> Batch:
         return Batch(self.n_topo, _ptr(self.split_ptr), _ptr(self.split_sub), _ptr(self.split_mask),
                      _ptr(self.out_ptr), _ptr(self.out_branch), self.n_time, _ptr(self.inj), self.n_var,
                      _ptr(self.var_ptr), _ptr(self.var_bus), _ptr(self.var_delta), self.n_gen,
-                     _ptr(self.gen_bus), _ptr(self.gen_p))
+                     _ptr(self.gen_bus), _ptr(self.gen_p), self.n_inj, _ptr(self.inj_bus), _ptr(self.inj_p),
+                     _ptr(self.ti_ptr), _ptr(self.ti_mask))
 
 
 class DeviceResults:
@@ -506,8 +520,9 @@ class Solver:
         """want_multi: evaluate the study's multi-outage sets (default: whenever it has some and the batch
         has no injection candidates)."""
         if want_multi is None:
-            want_multi = self.n_multi > 0 and dbatch.n_var == 0
-        res = results or DeviceResults(dbatch.n_topo, dbatch.n_time, self.n_mon, want_flows, dbatch.n_var > 0,
+            want_multi = self.n_multi > 0 and dbatch.n_var == 0 and not dbatch.has_ti
+        res = results or DeviceResults(dbatch.n_topo, dbatch.n_time, self.n_mon, want_flows,
+                                       dbatch.n_var > 0 or dbatch.has_ti,
                                        n_cont=self.n_cont, want_cont_max=want_cont_max, top_k=top_k,
                                        want_gen=dbatch.n_gen > 0, want_multi=want_multi)
         dcflow_solve_batch(self.ctx, dbatch.cstruct(), res.cstruct(), stream)

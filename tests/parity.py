@@ -21,9 +21,12 @@ def _topo_lists(topo, i):
     return splits, list(topo.out_branch[a:c])
 
 
-def compare(gpu, ref, w, topo, lim, tol, report=None):
+def compare(gpu, ref, w, topo, lim, tol, report=None, column=None):
     """gpu/ref: dicts of per-topology arrays for the same topologies (ref from
-    oracle.evaluate(..., want_flows=True, want_cmax=True)).  Raises AssertionError."""
+    oracle.evaluate(..., want_flows=True, want_cmax=True)).  Raises AssertionError.
+    column(i, t, c): the oracle's loading column of contingency position c for
+    the near-tie check of the worst monitored branch (default: refactorisation
+    with the batch injections w.inj)."""
     rep = {"max_err_flow": 0.0, "max_err_n1": 0.0, "max_err_n0": 0.0, "max_err_ovl": 0.0,
            "near_ties": 0, "exact_argmax": 0}
     np.testing.assert_array_equal(gpu["status"], ref["status"], err_msg="island flags")
@@ -71,8 +74,11 @@ def compare(gpu, ref, w, topo, lim, tol, report=None):
                 rep["near_ties"] += 1
             gm, rm = int(gpu["worst_mon"][i, t]), int(ref["worst_mon"][i, t])
             if go == ro and gm != rm:
-                splits, outs = _topo_lists(topo, i)
-                col = oracle.n1_loading_column(w.grid, splits, outs, w.inj[t], mon, w.cont[go], lim)
+                if column is not None:
+                    col = column(i, t, go)
+                else:
+                    splits, outs = _topo_lists(topo, i)
+                    col = oracle.n1_loading_column(w.grid, splits, outs, w.inj[t], mon, w.cont[go], lim)
                 best = col.max()
                 assert col[gm] >= best - 2 * tol * max(1.0, best), \
                     f"topology {i} t {t}: worst monitored {gm} != {rm} beyond tolerance"

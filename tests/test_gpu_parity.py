@@ -450,3 +450,112 @@ def test_multi_outages_rejected_forms():
     out = s.solve(db).to_host()
     assert out["worst_multi"].shape == (w.topo.n_topo, w.inj.shape[0])
     s.close()
+
+
+def _ti_lists(ti, topo, u):
+    """Candidate u of every topology as one-candidate lists (oracle input)."""
+    tp = np.arange(topo.n_topo + 1, dtype=np.int32)
+    tm = np.array([ti.ti_mask[ti.ti_ptr[i] + u] for i in range(topo.n_topo)], dtype=np.uint64)
+    return (tp, tm, ti.inj_bus, ti.inj_p)
+
+
+def _ti_moved(w, ti, i, u):
+    """[(effective split position, power [T])] that candidate u of topology i puts on busbar B."""
+    inc = oracle.incident_lists(w.grid.n_bus, w.grid.f, w.grid.t)
+    a, c = w.topo.split_ptr[i], w.topo.split_ptr[i + 1]
+    el, _ = oracle.eligible_injections(inc, list(zip(w.topo.split_sub[a:c], w.topo.split_mask[a:c])), ti.inj_bus)
+    m = int(ti.ti_mask[ti.ti_ptr[i] + u])
+    return [(pos, ti.inj_p[:, e]) for j, (e, pos) in enumerate(el) if (m >> j) & 1]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_injection_topologies_match_oracle(precision):
+    """Injection topologies t_i (Sec. III-A): per (topology, timestep) the argmin over the topology's
+    busbar assignments of agg_m (exact where the runner-up is clear, within tolerance on near-ties),
+    and every output equal to the oracle's for the GPU's pick."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch
+    w = synth.workload(2, n_topo=12, T=3)
+    U = 5
+    ti = synth.make_injection_topologies(w.grid, w.subs, w.topo, w.inj, U, 91)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    s = _solver(w, lim, precision)
+    out = s.solve(DeviceBatch(w.topo, w.inj, ti=ti), want_flows=True, want_cont_max=True).to_host()
+    torch.cuda.synchronize()
+    s.close()
+    per_u = [oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, want_flows=True, want_cmax=True,
+                             ti=_ti_lists(ti, w.topo, u)) for u in range(U)]
+    tol = TOL[precision]
+    np.testing.assert_array_equal(out["status"], per_u[0]["status"])
+    ok = per_u[0]["status"] == 0
+    assert ok.sum() >= 8
+    assert np.all(out["best_var"][~ok] == -1)
+    N, T = w.topo.n_topo, w.inj.shape[0]
+    vals = np.stack([p["n1_max"] for p in per_u], axis=2)  # [N, T, U]
+    pick = out["best_var"]
+    moved_any = 0
+    for i in np.nonzero(ok)[0]:
+        for t in range(T):
+            srt = np.sort(vals[i, t])
+            gu = int(pick[i, t])
+            assert 0 <= gu < U
+            if srt[1] - srt[0] > 2 * tol * max(1.0, srt[0]):
+                assert gu == int(np.argmin(vals[i, t])), (i, t, gu)
+            else:
+                assert vals[i, t, gu] <= srt[0] + 2 * tol * max(1.0, srt[0]), (i, t, gu)
+            moved_any += int(gu != 0)
+    ref = {k: per_u[0][k] for k in ("status", "n_island_cont", "n_valid_cont")}
+    for k in ("n0_max", "n1_max", "ovl", "worst_cont", "worst_mon", "cmax", "n0_flow"):
+        ref[k] = np.stack([np.stack([per_u[max(int(pick[i, t]), 0)][k][i, t] for t in range(T)])
+                           for i in range(N)])
+
+    def column(i, t, c):
+        a, b = w.topo.split_ptr[i], w.topo.split_ptr[i + 1]
+        splits = list(zip(w.topo.split_sub[a:b], w.topo.split_mask[a:b]))
+        a, b = w.topo.out_ptr[i], w.topo.out_ptr[i + 1]
+        mv = [(p, pw[t]) for p, pw in _ti_moved(w, ti, i, int(pick[i, t]))]
+        return oracle.n1_loading_column(w.grid, splits, list(w.topo.out_branch[a:b]), w.inj[t], w.mon,
+                                        w.cont[c], lim, moved=mv)
+
+    compare(out, ref, w, w.topo, lim, tol, column=column)
+    assert moved_any > 0  # some picks move injections to busbar B
+
+
+def test_injection_topologies_uneven_and_invalid_lists():
+    """Lists of different lengths (shorter ones are padded on the device and never pick the pad),
+    an empty list and a mask bit beyond the eligible injections (both invalid, flag 2)."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch
+    g = synth.make_grid(120, 170, 95)
+    subs = synth.split_capable(g, 30, 95)
+    topo = synth.make_topologies(g, subs, 14, 96, (1, 3), (0, 2))
+    inj = synth.make_injections(g, 2, 97, daily=False)
+    mon = np.arange(g.n_branch, dtype=np.int32)
+    w = synth.Workload("ti", g, topo, inj, mon, mon.copy(), subs)
+    full = synth.make_injection_topologies(g, subs, topo, inj, 6, 98)
+    inc = oracle.incident_lists(g.n_bus, g.f, g.t)
+    tp, tm = [0], []
+    for i in range(topo.n_topo):
+        lst = [int(x) for x in full.ti_mask[full.ti_ptr[i]:full.ti_ptr[i + 1]]][:1 + i % 6]
+        if i == 0:
+            lst = []
+        if i == 1:
+            a, c = topo.split_ptr[1], topo.split_ptr[2]
+            el, _ = oracle.eligible_injections(inc, list(zip(topo.split_sub[a:c], topo.split_mask[a:c])), full.inj_bus)
+            lst = [0, 1 << len(el)]
+        tm.extend(lst)
+        tp.append(len(tm))
+    ti = synth.InjectionTopologies(full.inj_bus, full.inj_p, np.array(tp, np.int32), np.array(tm, dtype=np.uint64))
+    lim = oracle.thermal_limits(g, inj)
+    ref = oracle.evaluate(g, topo, inj, mon, mon, lim, ti=(ti.ti_ptr, ti.ti_mask, ti.inj_bus, ti.inj_p))
+    assert ref["status"][0] == 2 and ref["status"][1] == 2
+    for precision in ("fp64", "fp32"):
+        s = _solver(w, lim, precision)
+        out = s.solve(DeviceBatch(topo, inj, ti=ti)).to_host()
+        torch.cuda.synchronize()
+        s.close()
+        np.testing.assert_array_equal(out["status"], ref["status"])
+        ok = ref["status"] == 0
+        tol = TOL[precision]
+        np.testing.assert_allclose(out["n1_max"][ok], ref["n1_max"][ok], rtol=tol, atol=tol)
+        cnt = np.diff(ti.ti_ptr)
+        assert np.all(out["best_var"][ok] < cnt[ok][:, None])
+        assert np.all(out["best_var"][~ok] == -1)

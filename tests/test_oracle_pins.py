@@ -634,6 +634,9 @@ def test_injection_topology_flows_match_the_split_grid_by_hand():
             fl = np.zeros((w.inj.shape[0], g.n_branch))
             fl[:, alive] = Pn @ H.T
             np.testing.assert_allclose(r["n0_flow"][i], fl[:, mon], atol=1e-9)
+            mv = [(buses.index(int(ti.inj_bus[e])), ti.inj_p[:, e]) for j, e in enumerate(elig) if (m >> j) & 1]
+            fl2, _ = oracle.topology_flows(g, splits, list(w.topo.out_branch[a:c]), w.inj.T, moved=mv)
+            np.testing.assert_allclose(fl2.T, fl, atol=1e-9)
             for k in range(len(buses)):  # Kirchhoff at busbar B
                 out = fl[:, f2 == g.n_bus + k].sum(axis=1) - fl[:, t2 == g.n_bus + k].sum(axis=1)
                 np.testing.assert_allclose(out, moved[:, k], atol=1e-9)
