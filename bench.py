@@ -374,6 +374,36 @@ def run_ours(args):
                                                "note": f"fp32 solve plus {args.gens} generator-failure N-1 cases "
                                                        "per topology and timestep (value counts the branch "
                                                        "N-1 cases only)"}
+        # injection topologies t_i (Sec. III-A): |T_i| busbar assignments of the injections at the split
+        # substations per topology, brute-forced for the lowest agg_m (on a subset of the topologies)
+        if form == "fp32" and args.ti > 0 and db.n_var == 0:
+            nsub = min(args.ti_topologies, w.topo.n_topo)
+            tsub = w.topo.subset(np.arange(nsub))
+            tis = synth.make_injection_topologies(w.grid, w.subs, tsub, w.inj, args.ti, 900)
+            dbt = DeviceBatch(tsub, w.inj, ti=tis)
+            rt = DeviceResults(nsub, db.n_time, len(w.mon), want_var=True)
+            for _ in range(args.warmup):
+                solver.solve(dbt, results=rt)
+            torch.cuda.synchronize()
+            evt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k2 in range(steps):
+                flush.fill_(k2 & 0xFF)
+                evt[k2][0].record(stream)
+                solver.solve(dbt, results=rt)
+                evt[k2][1].record(stream)
+            torch.cuda.synchronize()
+            tt = sum(a.elapsed_time(b) for a, b in evt) / 1e3
+            st_h = rt.island_flag[:nsub].cpu().numpy()
+            ni_h = rt.n_island_cont[:nsub].cpu().numpy()
+            lft = _loadflows(tsub, st_h, ni_h, w.cont, T_STEPS) * args.ti
+            if ws > 1:
+                tt, lft = reduce_over_ranks(tt, lft, "cuda")
+            results[f"fp32_ti{args.ti}"] = {
+                "value": lft * steps / tt, "ms_per_step": 1e3 * tt / steps, "loadflows_per_step": lft,
+                "topologies": nsub, "steps": steps,
+                "note": f"injection topologies: {args.ti} busbar assignments of the injections at the split "
+                        f"substations per topology ({nsub} topologies x {T_STEPS} timesteps), metric-first "
+                        "brute force; loadflows count every (topology, timestep, assignment, contingency)"}
         # the same solve with multi-outage N-1 cases (sets of 2-4 branches that fail together)
         if form == "fp32" and args.multi > 0 and db.n_var == 0:
             rng = np.random.default_rng(800)
@@ -507,6 +537,10 @@ def main():
     ap.add_argument("--workload", default="grid500", choices=sorted(WORKLOADS))
     ap.add_argument("--gens", type=int, default=16,
                     help="also time the FP32 solve with this many generator-failure cases; 0 = skip")
+    ap.add_argument("--ti", type=int, default=16,
+                    help="also time the FP32 solve with this many injection topologies per topology; 0 = skip")
+    ap.add_argument("--ti-topologies", type=int, default=1000,
+                    help="topologies of the injection-topology form")
     ap.add_argument("--multi", type=int, default=32,
                     help="also time the FP32 solve with this many multi-outage sets; 0 = skip")
     ap.add_argument("--top-k", type=int, default=8,
