@@ -274,6 +274,17 @@ def run_ours(args):
     lim[w.mon] = 1.2 * np.abs(w.inj @ pt.T).max(axis=0) + 0.1
     n_mon = len(w.mon)
     T_STEPS = w.inj.shape[0]
+    # PTDF row restriction (Sec. II): the study needs the rows of the monitored, contingency, split-bus
+    # and outaged branches only; "full" keeps every branch row
+    ocand = np.unique(np.asarray(w.topo.out_branch, np.int32)) if args.rows == "restricted" else None
+    need = np.zeros(w.grid.n_branch, bool)
+    need[w.mon] = need[w.cont] = True
+    for v in w.subs:
+        need[(w.grid.f == v) | (w.grid.t == v)] = True
+    if ocand is None:
+        need[:] = True
+    else:
+        need[ocand] = True
 
     results, hosts = {}, {}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
@@ -282,7 +293,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         ts = time.perf_counter()
         solver = Solver(w.grid, precision=form)
-        solver.set_study(w.mon, w.cont, lim, split_bus=w.subs)
+        solver.set_study(w.mon, w.cont, lim, split_bus=w.subs, outage_cand=ocand)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - ts
         db = DeviceBatch(w.topo, w.inj, w.var)
@@ -409,7 +420,7 @@ def run_ours(args):
             rng = np.random.default_rng(800)
             E = w.grid.n_branch
             sets = [[int(b) for b in rng.choice(E, 2 + k % 3, replace=False)] for k in range(args.multi)]
-            solver.set_study(w.mon, w.cont, lim, split_bus=w.subs, multi=sets)
+            solver.set_study(w.mon, w.cont, lim, split_bus=w.subs, outage_cand=ocand, multi=sets)
             rm = DeviceResults(db.n_topo, db.n_time, len(w.mon), want_multi=True)
             for _ in range(args.warmup):
                 solver.solve(db, results=rm)
@@ -469,6 +480,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "topologies": n_topo, "timesteps": T_STEPS, "monitored": n_mon,
                        "contingencies": len(w.cont), "candidates": 0 if w.var is None else w.var.n_var,
+                       "ptdf_rows": int(need.sum()), "branches": int(w.grid.n_branch),
                        "l2": "flushed between steps (256 MB write)",
                        "max_err_stated": {"fp32": 1e-4, "fp64": 1e-10}},
             "gpu_launches": head["launches"], "clocks": head["clocks"],
@@ -541,6 +553,8 @@ def main():
                     help="also time the FP32 solve with this many injection topologies per topology; 0 = skip")
     ap.add_argument("--ti-topologies", type=int, default=1000,
                     help="topologies of the injection-topology form")
+    ap.add_argument("--rows", default="restricted", choices=["restricted", "full"],
+                    help="PTDF rows of the study: the needed branches only, or every branch")
     ap.add_argument("--multi", type=int, default=32,
                     help="also time the FP32 solve with this many multi-outage sets; 0 = skip")
     ap.add_argument("--top-k", type=int, default=8,
