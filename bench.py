@@ -292,7 +292,7 @@ def run_ours(args):
     for form in (args.forms.split(",")):
         torch.cuda.synchronize()
         ts = time.perf_counter()
-        solver = Solver(w.grid, precision=form)
+        solver = Solver(w.grid, precision=form, dense_n1=args.dense)
         solver.set_study(w.mon, w.cont, lim, split_bus=w.subs, outage_cand=ocand)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - ts
@@ -555,6 +555,8 @@ def main():
                     help="topologies of the injection-topology form")
     ap.add_argument("--rows", default="restricted", choices=["restricted", "full"],
                     help="PTDF rows of the study: the needed branches only, or every branch")
+    ap.add_argument("--dense", action="store_true",
+                    help="FP32 N-1 over every contingency column instead of each topology's valid ones")
     ap.add_argument("--multi", type=int, default=32,
                     help="also time the FP32 solve with this many multi-outage sets; 0 = skip")
     ap.add_argument("--top-k", type=int, default=8,

@@ -60,9 +60,13 @@ typedef struct {
   int32_t device;        /* CUDA device ordinal; -1 = the current device */
   int32_t chunk_topo;    /* topologies per internal chunk; 0 = automatic */
   double island_tol;     /* pivot / denominator threshold for islanding; 0 = 1e-9 */
+  int32_t dense_n1;      /* FP32 form: 0 = the N-1 kernel runs over each topology's valid
+                            contingencies only (compacted per topology), 1 = over every
+                            contingency column, discarding the invalid ones afterwards */
 } dcflow_options;
 
-/* Fill `opt` with the defaults (FP32 form, current device, automatic chunk, 1e-9). */
+/* Fill `opt` with the defaults (FP32 form, current device, automatic chunk, 1e-9,
+ * compacted N-1). */
 void dcflow_default_options(dcflow_options* opt);
 
 /*

@@ -17,11 +17,15 @@
 //           a serving round read consecutive contingencies: no bank
 //           conflicts), and their 16 entries recomputed with the
 //           saturating-FMA overload term.
-// SEL (learned screener): a block is one work item (topology, 64 of its
-// selected contingencies) and its Phi tile is gathered from the transposed
-// factors [cont][Mpad]: each contingency's 16 rows are one 64-byte run,
-// copied with cp.async into a contingency-major tile (pitch 20 floats: the
-// builders' reads spread over all banks); the other operands arrive by TMA.
+// SEL (a per-topology contingency list): block (cb, q) takes the cb-th 64
+// contingencies of topology q's list, either from a work list (the learned
+// screener's selection: one work item per block) or from the grid itself
+// (every valid contingency of the topology, compacted: the contingencies that
+// island the topology are never computed; a block past the end of its list
+// writes an empty partial result).  The Phi tile is gathered from the
+// transposed factors [cont][Mpad]: each contingency's 16 rows are one 64-byte
+// run, copied with cp.async into a contingency-major tile (pitch 20 floats:
+// the builders' reads spread over all banks); the other operands arrive by TMA.
 #pragma once
 
 #include <cuda.h>
@@ -51,7 +55,7 @@ struct SelArgs {
   int mp;
   const int* csel;     // [nq][C] selected internal contingencies, ascending
   const int* nsel;     // [nq]
-  const int* work;     // [items] (topology << 6) | 64-contingency block
+  const int* work;     // [items] (topology << 6) | 64-contingency block, or null: block (cb, q) of the grid
 };
 constexpr int kPP = 20;  // pitch (floats) of a gathered Phi column: 16 rows + bank spread
 
@@ -89,17 +93,28 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
   using L = RegLayout<TT, RMAX, SEL>;
   using R = RegTile<TT>;
   constexpr int CR = R::CR, TR = R::TR, RB = R::RB;
-  int q, cb;  // topology slot and 64-contingency block
+  int q = blockIdx.y, cb = blockIdx.x;  // topology slot and 64-contingency block
   if constexpr (SEL) {
-    const int item = sel.work[blockIdx.x];
-    q = item >> 6;
-    cb = item & 63;
-  } else {
-    q = blockIdx.y;
-    cb = blockIdx.x;
+    if (sel.work) {
+      const int item = sel.work[blockIdx.x];
+      q = item >> 6;
+      cb = item & 63;
+    }
   }
   const QInfo qi = a.qi[q];
   if (qi.status != ST_OK) return;  // whole block: before any barrier
+  if constexpr (SEL) {
+    if (!sel.work && cb * kCB >= sel.nsel[q]) {  // past the end of the list: an empty partial result
+      for (int t = threadIdx.x; t < TT; t += blockDim.x)
+        if (t0 + t < a.T) {
+          const size_t o2 = ((size_t)q * a.T + t0 + t) * a.ncb + cb;
+          static_cast<float*>(a.pmax)[o2] = 0.f;
+          a.parg[o2] = -1;
+          a.povl[o2] = 0.0;
+        }
+      return;
+    }
+  }
   extern __shared__ __align__(128) unsigned char sm[];
   if (smem_u32(sm) & 127u) {  // the TMA destinations need the alignment: refuse, never fault
     if (threadIdx.x == 0) atomicExch(a.err, 2);
@@ -191,6 +206,13 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
   for (int i = 0; i < CR; ++i)
 #pragma unroll
     for (int j = 0; j < TR; ++j) mx[i][j] = 0.f;
+  // the builder's K^{-1}-weighted factors of its contingency, fixed for the block
+  constexpr bool kVtReg = RMAX <= 8;
+  float vb[kVtReg ? RMAX : 1];
+  if constexpr (kVtReg) {
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) vb[j] = s_vt[j * kCB + bl];
+  }
   bool failed = false;
   for (int k = 0; k < ntiles; ++k) {
     const int st = k % kRegStages;
@@ -223,7 +245,9 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
       }
 #pragma unroll
       for (int j = 0; j < RMAX; ++j) {
-        const float v = s_vt[j * kCB + bl];
+        float v;
+        if constexpr (kVtReg) v = vb[j];
+        else v = s_vt[j * kCB + bl];
         const float2 v2 = make_float2(v, v);
 #pragma unroll
         for (int i4 = 0; i4 < RB / 4; ++i4) {

@@ -1026,6 +1026,35 @@ __global__ void k_select(const QInfo* __restrict__ qinfo, int nq, int T, int C, 
 // Per topology (one warp): the selected contingencies in ascending order
 // (all of them after a fallback), their count, and one work item per
 // 64 of them for the N-1 kernel.
+// Every valid contingency of a topology (not outaged, not islanding it; the
+// base-grid bridges are already outside [0, C_eff)), compacted in internal
+// order for the grid mode of the register-tiled N-1 kernel, so that the
+// contingencies a topology's splits turn into bridges are never computed.
+// Their per-contingency maxima (when requested) are -1 here.  One warp per slot.
+__global__ void k_valid_compact(Args a, int* __restrict__ csel, int* __restrict__ nsel) {
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (q >= a.nq) return;
+  const QInfo qi = a.qi[q];
+  if (qi.status != ST_OK) {
+    if (lane == 0) nsel[q] = 0;
+    return;
+  }
+  const int C = a.C, T = a.T;
+  const uint8_t* valid = a.valid + (size_t)q * C;
+  float* cm = a.out.n1_cont_max;
+  int base = 0;
+  for (int c0 = 0; c0 < a.C_eff; c0 += 32) {
+    const int c = c0 + lane;
+    const bool v = c < a.C_eff && valid[c];
+    const uint32_t m = __ballot_sync(0xffffffffu, v);
+    if (v) csel[(size_t)q * C + base + __popc(m & ((1u << lane) - 1u))] = c;
+    base += __popc(m);
+    if (cm && c < a.C_eff && !v)
+      for (int t = 0; t < T; ++t) cm[((size_t)qi.tau * T + t) * C + a.cont_pos[c]] = -1.f;
+  }
+  if (lane == 0) nsel[q] = base;
+}
+
 __global__ void k_compact(const QInfo* __restrict__ qinfo, int nq, int C, int C_eff, const int* __restrict__ cont_inv,
                           int W, const uint32_t* __restrict__ selmask, const uint8_t* __restrict__ fb,
                           int* __restrict__ csel, int* __restrict__ nsel, int* __restrict__ work,
@@ -1992,6 +2021,34 @@ int launch_reg_sel(const N1Maps& maps, const Args& a, const SelArgs& sel, int RM
   return launch_reg_sel_r<16>(maps, a, sel, TT, items, st, t0);
 }
 
+// every topology's valid contingencies, compacted: grid (blocks per topology, slots)
+template <int TT, int RMAX, bool OVL>
+int launch_reg_cmp_t(const N1Maps& maps, const Args& a, const SelArgs& sel, dim3 grid, cudaStream_t st, int t0) {
+  using L = RegLayout<TT, RMAX, true>;
+  static uint64_t attr = 0;
+  if (smem_attr_once(k_n1_reg<TT, RMAX, OVL, true>, L::kBytes, attr) != cudaSuccess) return DCFLOW_ERR_CUDA;
+  k_n1_reg<TT, RMAX, OVL, true><<<grid, RegTile<TT>::NT, L::kBytes, st>>>(maps, a, t0, sel);
+  return 0;
+}
+template <int RMAX>
+int launch_reg_cmp_r(const N1Maps& maps, const Args& a, const SelArgs& sel, int TT, bool ovl, dim3 grid,
+                     cudaStream_t st, int t0) {
+  if (!ovl) return launch_reg_cmp_t<32, RMAX, false>(maps, a, sel, grid, st, t0);
+  switch (TT) {
+    case 4: return launch_reg_cmp_t<4, RMAX, true>(maps, a, sel, grid, st, t0);
+    case 8: return launch_reg_cmp_t<8, RMAX, true>(maps, a, sel, grid, st, t0);
+    case 16: return launch_reg_cmp_t<16, RMAX, true>(maps, a, sel, grid, st, t0);
+    case 24: return launch_reg_cmp_t<24, RMAX, true>(maps, a, sel, grid, st, t0);
+    default: return launch_reg_cmp_t<32, RMAX, true>(maps, a, sel, grid, st, t0);
+  }
+}
+int launch_reg_cmp(const N1Maps& maps, const Args& a, const SelArgs& sel, int RMAX, int TT, bool ovl, dim3 grid,
+                   cudaStream_t st, int t0) {
+  if (RMAX == 4) return launch_reg_cmp_r<4>(maps, a, sel, TT, ovl, grid, st, t0);
+  if (RMAX == 8) return launch_reg_cmp_r<8>(maps, a, sel, TT, ovl, grid, st, t0);
+  return launch_reg_cmp_r<16>(maps, a, sel, TT, ovl, grid, st, t0);
+}
+
 int launch_tma(const N1Maps& maps, const Args& a, int RMAX, int TT, dim3 grid, cudaStream_t st, int t0) {
   if (RMAX == 4) return launch_tma_r<4>(maps, a, TT, grid, st, t0);
   if (RMAX == 8) return launch_tma_r<8>(maps, a, TT, grid, st, t0);
@@ -2256,6 +2313,8 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   // memory, so preparation kernels of the next chunk only run in its tail)
   const int C_eff = ctx->C_eff;       // contingencies that can be valid (base-grid bridges excluded)
   const int ncb = (C_eff + 63) / 64;  // 64-contingency blocks of the N-1 kernels
+  // FP32 full solve: the N-1 kernel runs over each topology's compacted valid contingencies
+  const bool cmp = !fp64 && mode == kModeFull && C_eff > 0 && !ctx->opt.dense_n1;
   const int Mp = (int)round_up(M, 16);
   const int TV = T * Uc;  // virtual timesteps: (timestep, candidate) pairs
   if (R > 64) {
@@ -2267,6 +2326,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                     (size_t)Mp * (kRMax + Text + 4) * rs + (size_t)Text * C * rs + C + 4 +
                     (size_t)T * ncb * (rs + 4 + 8) + 64;
   if (TI) per_slot += (size_t)kRMax * C * rs + 64 * 8 + 4;
+  if (cmp) per_slot += (size_t)C * 4 + 4;
   if (Uc > 0)
     per_slot += (size_t)TV * (Mp + C) * rs + (size_t)TV * ncb * (rs + 4 + 8) + (size_t)T * 4 + (size_t)T * (Mp + C) * rs;
   const size_t SM_ = want_multi ? (size_t)ctx->n_multi : 0;
@@ -2286,6 +2346,8 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
         B.nisl.ensure(c * sizeof(int)) || B.pmax.ensure(c * T * std::max(ncb, 1) * rs) ||
         B.parg.ensure(c * T * std::max(ncb, 1) * sizeof(int)) ||
         B.povl.ensure(c * T * std::max(ncb, 1) * sizeof(double)))
+      return DCFLOW_ERR_OOM;
+    if (cmp && (B.csel.ensure(c * std::max(C, 1) * sizeof(int)) || B.nsel.ensure(c * sizeof(int))))
       return DCFLOW_ERR_OOM;
     if (TI && (B.zcd.ensure(c * kRMax * std::max(C, 1) * rs) || B.tiel.ensure(c * 64 * sizeof(int)) ||
                B.tirow.ensure(c * 64 * sizeof(int)) || B.nel.ensure(c * sizeof(int))))
@@ -2424,8 +2486,10 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       return rc;
     }
   };
-  auto run_n1 = [&](const Args& a, int RMAX, int Tn, bool ovl) -> int {
+  // cmp: the chunk's compacted valid-contingency lists (FP32, TT >= 4), or null
+  auto run_n1 = [&](const Args& a, int RMAX, int Tn, bool ovl, const ChunkBufs* cmp) -> int {
     const int TTn = ovl ? pick_tt(Tn, fp64) : (fp64 ? 8 : 32);
+    if (TTn < 4) cmp = nullptr;
     N1Maps maps;
     if (!fp64) {
       int rc = encode_maps(a, RMAX, Tn, TTn, maps);
@@ -2448,6 +2512,9 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       }
       int rc;
       if (fp64) rc = launch_n1<double>(a, RMAX, TTn, grid, st, t0);
+      else if (cmp)
+        rc = launch_reg_cmp(maps, a, SelArgs{ctx->PhiCM.as<float>(), Mp, cmp->csel.as<int>(), cmp->nsel.as<int>(), nullptr},
+                            RMAX, TTn, ovl, grid, st, t0);
       else rc = ovl ? launch_tma(maps, a, RMAX, TTn, grid, st, t0) : launch_tma_screen(maps, a, RMAX, grid, st, t0);
       if (rc) return rc;
       ++ctx->launches;
@@ -2498,6 +2565,11 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     else launch_prep<float>(ap, RMAX, ch.nq, dyn, side, TI ? B.zcd.p : nullptr);
     ctx->launches += 3;
     DCF_CHECK_LAUNCH();
+    if (cmp) {  // the valid contingencies of every topology (after the denominators)
+      k_valid_compact<<<(ch.nq * 32 + 127) / 128, 128, 0, side>>>(a, B.csel.as<int>(), B.nsel.as<int>());
+      ++ctx->launches;
+      DCF_CHECK_LAUNCH();
+    }
     if (want_multi) {  // the multi-outage small systems ride with the FP64 preparation
       if (fp64) launch_multi_prep<double>(ap, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(), B, side);
       else launch_multi_prep<float>(ap, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(), B, side);
@@ -2536,7 +2608,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       av.parg = B.pargv.as<int>();
       av.povl = B.povlv.as<double>();
       if (C_eff > 0) {
-        int rc = run_n1(av, RMAX, TV, false);
+        int rc = run_n1(av, RMAX, TV, false, cmp ? &B : nullptr);
         if (rc) return rc;
       } else {
         DCF_CUDA(cudaMemsetAsync(B.pargv.p, 0xff, (size_t)ch.nq * TV * sizeof(int), st));
@@ -2638,7 +2710,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       }
       nsel_dev = SB.nsel.as<int>();
     } else if (C_eff > 0) {
-      int rc = run_n1(af, RMAX, T, true);
+      int rc = run_n1(af, RMAX, T, true, cmp ? &B : nullptr);
       if (rc) return rc;
     }
     if (fp64) launch_final<double>(af, RMAX, st, ctx->PhiCM.p, nsel_dev);
