@@ -43,7 +43,7 @@ WORKLOADS = {
 # profiles/k_n1_reg_grid500.md, keyed by the sha1 of the kernel's source and of
 # its argument block at the time of the capture
 N1_TRAFFIC = {
-    ("a1a5e5fcabd4", "fp32"): {"bytes": 1.095e9, "per": "bench step of the 500-bus study (2 launches)",
+    ("bc173a8d1288", "fp32"): {"bytes": 1.061e9, "per": "bench step of the 500-bus study (2 launches)",
                                "how": "1,000-topology capture (626 + 374 topologies) scaled by topologies "
                                       "per rank class to 6,233 + 3,767"},
 }
@@ -463,13 +463,14 @@ def run_ours(args):
         entries = head["loadflows_per_step"] * n_mon * head["steps"]
         peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
         ach = entries / (k["n1_ms"] / 1e3) / 1e12
-        key = (_src_hash(), "fp32")
+        key = (_src_hash(), "fp32" if not args.dense else "fp32_dense")
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T N-1 entries/s", "frac": ach / peak,
                 "traffic": (N1_TRAFFIC[key]["bytes"] if key in N1_TRAFFIC and args.workload == "grid500"
                             and n_topo == 10000 else None),
                 "traffic_note": (N1_TRAFFIC[key] if key in N1_TRAFFIC and args.workload == "grid500"
                                  and n_topo == 10000 else "no capture for this kernel source and workload"),
-                "kernel": "k_n1_reg (FP32 fused N-1)",
+                "kernel": "k_n1_reg (FP32 fused N-1, " + ("every contingency column)" if args.dense
+                                                           else "each topology's valid contingencies)"),
                 "peak_note": f"1 FP32 issue slot per entry at the {peak_kind} max SM clock "
                              f"({peaks.get('sm_max_mhz', 2032.0):.0f} MHz), 148 SMs x 128 lanes",
                 "n1_ms_per_step": k["n1_ms"] / head["steps"],
