@@ -476,10 +476,15 @@ struct Acc<float> {
 
 template <>
 struct Acc<double> {
+  // |v|, the running maximum and max(|v| - 1, 0) through the bit patterns on the
+  // integer pipe (sign bit; non-negative doubles order like their bits): of the
+  // FP64 pipe only the two additions remain (B300's FP64 rate is low)
   static __device__ __forceinline__ void add(double& mx, double& ov, double v) {
-    const double av = fabs(v);
-    mx = fmax(mx, av);
-    ov += fmax(av - 1.0, 0.0);
+    const long long b = __double_as_longlong(v) & 0x7fffffffffffffffll;
+    const double av = __longlong_as_double(b);
+    mx = b > __double_as_longlong(mx) ? av : mx;  // mx >= 0
+    const double d = av - 1.0;
+    ov += __double_as_longlong(d) < 0 ? 0.0 : d;
   }
   static __device__ __forceinline__ double ovl_scale() { return 1.0; }
 };
@@ -1807,9 +1812,9 @@ struct Plan {
 
 int pick_tt(int T, bool fp64) {
   const int opts32[] = {1, 4, 8, 16, 24, 32};
-  const int opts64[] = {1, 4, 8};
+  const int opts64[] = {1, 4, 8, 12};
   const int* o = fp64 ? opts64 : opts32;
-  const int n = fp64 ? 3 : 6;
+  const int n = fp64 ? 4 : 6;
   for (int i = 0; i < n; ++i)
     if (T <= o[i]) return o[i];
   return o[n - 1];
@@ -1833,7 +1838,8 @@ int launch_n1_r(const Args& a, int TT, dim3 grid, cudaStream_t st, int t0) {
         else if (TT == 24) launch_n1_t<Real, 24, RMAX>(a, grid, st, t0);
         else launch_n1_t<Real, 32, RMAX>(a, grid, st, t0);
       } else {
-        return DCFLOW_ERR_INVALID_ARG;
+        if (TT != 12) return DCFLOW_ERR_INVALID_ARG;
+        launch_n1_t<Real, 12, RMAX>(a, grid, st, t0);
       }
   }
   return 0;
@@ -2092,7 +2098,8 @@ int launch_sel_r(const Args& a, const void* phicm, const ChunkBufs& B, int TT, i
         else if (TT == 24) launch_sel_t<Real, 24, RMAX>(a, phicm, B, grid, st, t0);
         else launch_sel_t<Real, 32, RMAX>(a, phicm, B, grid, st, t0);
       } else {
-        return DCFLOW_ERR_INVALID_ARG;
+        if (TT != 12) return DCFLOW_ERR_INVALID_ARG;
+        launch_sel_t<Real, 12, RMAX>(a, phicm, B, grid, st, t0);
       }
   }
   return 0;
