@@ -43,9 +43,12 @@ WORKLOADS = {
 # profiles/k_n1_reg_grid500.md, keyed by the sha1 of the kernel's source and of
 # its argument block at the time of the capture
 N1_TRAFFIC = {
-    ("bc173a8d1288", "fp32"): {"bytes": 1.061e9, "per": "bench step of the 500-bus study (2 launches)",
+    ("bc173a8d1288", "fp32"): {"bytes": 1.096e9, "per": "bench step of the 500-bus study (2 launches)",
                                "how": "1,000-topology capture (626 + 374 topologies) scaled by topologies "
                                       "per rank class to 6,233 + 3,767"},
+    ("bc173a8d1288", "fp32_compact"): {"bytes": 1.061e9, "per": "bench step of the 500-bus study (2 launches)",
+                                       "how": "1,000-topology capture (626 + 374 topologies) scaled by "
+                                              "topologies per rank class to 6,233 + 3,767"},
 }
 
 
@@ -292,7 +295,7 @@ def run_ours(args):
     for form in (args.forms.split(",")):
         torch.cuda.synchronize()
         ts = time.perf_counter()
-        solver = Solver(w.grid, precision=form, dense_n1=args.dense)
+        solver = Solver(w.grid, precision=form, compact_n1=args.compact)
         solver.set_study(w.mon, w.cont, lim, split_bus=w.subs, outage_cand=ocand)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - ts
@@ -463,14 +466,14 @@ def run_ours(args):
         entries = head["loadflows_per_step"] * n_mon * head["steps"]
         peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
         ach = entries / (k["n1_ms"] / 1e3) / 1e12
-        key = (_src_hash(), "fp32" if not args.dense else "fp32_dense")
+        key = (_src_hash(), "fp32" if not args.compact else "fp32_compact")
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T N-1 entries/s", "frac": ach / peak,
                 "traffic": (N1_TRAFFIC[key]["bytes"] if key in N1_TRAFFIC and args.workload == "grid500"
                             and n_topo == 10000 else None),
                 "traffic_note": (N1_TRAFFIC[key] if key in N1_TRAFFIC and args.workload == "grid500"
                                  and n_topo == 10000 else "no capture for this kernel source and workload"),
-                "kernel": "k_n1_reg (FP32 fused N-1, " + ("every contingency column)" if args.dense
-                                                           else "each topology's valid contingencies)"),
+                "kernel": "k_n1_reg (FP32 fused N-1, " + ("each topology's valid contingencies)" if args.compact
+                                                           else "every contingency column)"),
                 "peak_note": f"1 FP32 issue slot per entry at the {peak_kind} max SM clock "
                              f"({peaks.get('sm_max_mhz', 2032.0):.0f} MHz), 148 SMs x 128 lanes",
                 "n1_ms_per_step": k["n1_ms"] / head["steps"],
@@ -556,8 +559,8 @@ def main():
                     help="topologies of the injection-topology form")
     ap.add_argument("--rows", default="restricted", choices=["restricted", "full"],
                     help="PTDF rows of the study: the needed branches only, or every branch")
-    ap.add_argument("--dense", action="store_true",
-                    help="FP32 N-1 over every contingency column instead of each topology's valid ones")
+    ap.add_argument("--compact", action="store_true",
+                    help="FP32 N-1 over each topology's valid contingencies instead of every contingency column")
     ap.add_argument("--multi", type=int, default=32,
                     help="also time the FP32 solve with this many multi-outage sets; 0 = skip")
     ap.add_argument("--top-k", type=int, default=8,

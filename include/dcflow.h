@@ -60,13 +60,15 @@ typedef struct {
   int32_t device;        /* CUDA device ordinal; -1 = the current device */
   int32_t chunk_topo;    /* topologies per internal chunk; 0 = automatic */
   double island_tol;     /* pivot / denominator threshold for islanding; 0 = 1e-9 */
-  int32_t dense_n1;      /* FP32 form: 0 = the N-1 kernel runs over each topology's valid
-                            contingencies only (compacted per topology), 1 = over every
-                            contingency column, discarding the invalid ones afterwards */
+  int32_t compact_n1;    /* FP32 form: 0 = the N-1 kernel runs over every contingency column
+                            and discards the invalid ones; 1 = over each topology's valid
+                            contingencies only (compacted per topology, columns gathered from
+                            the transposed factors): pays when a topology's splits island many
+                            contingencies, costs about a tenth per block otherwise */
 } dcflow_options;
 
 /* Fill `opt` with the defaults (FP32 form, current device, automatic chunk, 1e-9,
- * compacted N-1). */
+ * every contingency column). */
 void dcflow_default_options(dcflow_options* opt);
 
 /*

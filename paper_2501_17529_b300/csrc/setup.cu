@@ -130,7 +130,7 @@ extern "C" void dcflow_default_options(dcflow_options* opt) {
   opt->device = -1;
   opt->chunk_topo = 0;
   opt->island_tol = 1e-9;
-  opt->dense_n1 = 0;
+  opt->compact_n1 = 0;
 }
 
 extern "C" int dcflow_setup(dcflow_ctx** out, int32_t n_bus, int32_t n_branch, const int32_t* from,

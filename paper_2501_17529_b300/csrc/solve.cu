@@ -2320,8 +2320,8 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   // memory, so preparation kernels of the next chunk only run in its tail)
   const int C_eff = ctx->C_eff;       // contingencies that can be valid (base-grid bridges excluded)
   const int ncb = (C_eff + 63) / 64;  // 64-contingency blocks of the N-1 kernels
-  // FP32 full solve: the N-1 kernel runs over each topology's compacted valid contingencies
-  const bool cmp = !fp64 && mode == kModeFull && C_eff > 0 && !ctx->opt.dense_n1;
+  // FP32 full solve on request: the N-1 kernel runs over each topology's compacted valid contingencies
+  const bool cmp = !fp64 && mode == kModeFull && C_eff > 0 && ctx->opt.compact_n1;
   const int Mp = (int)round_up(M, 16);
   const int TV = T * Uc;  // virtual timesteps: (timestep, candidate) pairs
   if (R > 64) {

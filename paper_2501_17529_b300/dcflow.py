@@ -22,7 +22,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32}
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("device", c_int32), ("chunk_topo", c_int32),
-                ("island_tol", c_double), ("dense_n1", c_int32)]
+                ("island_tol", c_double), ("compact_n1", c_int32)]
 
 
 class Study(ctypes.Structure):
@@ -187,13 +187,13 @@ def dcflow_default_options() -> Options:
     return o
 
 
-def dcflow_setup(n_bus, f, t, b, slack, precision="fp32", device=-1, chunk_topo=0, island_tol=0.0, dense_n1=False):
+def dcflow_setup(n_bus, f, t, b, slack, precision="fp32", device=-1, chunk_topo=0, island_tol=0.0, compact_n1=False):
     lib = load_library()
     o = dcflow_default_options()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.device = int(device)
     o.chunk_topo = int(chunk_topo)
-    o.dense_n1 = int(bool(dense_n1))
+    o.compact_n1 = int(bool(compact_n1))
     if island_tol:
         o.island_tol = float(island_tol)
     fa, fp = _i32(f)
@@ -495,10 +495,10 @@ class DeviceResults:
 class Solver:
     """One grid + study on the current CUDA device."""
 
-    def __init__(self, grid, precision="fp32", chunk_topo=0, island_tol=0.0, device=-1, dense_n1=False):
+    def __init__(self, grid, precision="fp32", chunk_topo=0, island_tol=0.0, device=-1, compact_n1=False):
         self.grid = grid
         self.ctx = dcflow_setup(grid.n_bus, grid.f, grid.t, grid.b, grid.slack, precision=precision,
-                                device=device, chunk_topo=chunk_topo, island_tol=island_tol, dense_n1=dense_n1)
+                                device=device, chunk_topo=chunk_topo, island_tol=island_tol, compact_n1=compact_n1)
         self.n_mon = 0
         self.n_cont = 0
         self.n_multi = 0

@@ -561,14 +561,14 @@ def test_injection_topologies_uneven_and_invalid_lists():
         assert np.all(out["best_var"][~ok] == -1)
 
 
-@pytest.mark.parametrize("dense", [True, False])
-def test_grid500_dense_and_compacted_n1(dense):
-    """FP32 N-1 over every contingency column (dense_n1) and over each topology's compacted valid
-    contingencies: the same outputs as the oracle, per-contingency maxima (-1 where skipped) included."""
+@pytest.mark.parametrize("compact", [False, True])
+def test_grid500_dense_and_compacted_n1(compact):
+    """FP32 N-1 over every contingency column and over each topology's compacted valid contingencies
+    (compact_n1): the same outputs as the oracle, per-contingency maxima (-1 where skipped) included."""
     from paper_2501_17529_b300.dcflow import DeviceBatch, Solver
     w = synth.workload(2, n_topo=40)
     lim = oracle.thermal_limits(w.grid, w.inj)
-    s = Solver(w.grid, precision="fp32", dense_n1=dense)
+    s = Solver(w.grid, precision="fp32", compact_n1=compact)
     s.set_study(w.mon, w.cont, lim, split_bus=w.subs)
     out = s.solve(DeviceBatch(w.topo, w.inj), want_flows=True, want_cont_max=True).to_host()
     torch.cuda.synchronize()
