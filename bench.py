@@ -295,7 +295,7 @@ def run_ours(args):
     for form in (args.forms.split(",")):
         torch.cuda.synchronize()
         ts = time.perf_counter()
-        solver = Solver(w.grid, precision=form, compact_n1=args.compact)
+        solver = Solver(w.grid, precision=form, compact_n1=args.compact, chunk_topo=args.chunk)
         solver.set_study(w.mon, w.cont, lim, split_bus=w.subs, outage_cand=ocand)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - ts
@@ -559,6 +559,8 @@ def main():
                     help="topologies of the injection-topology form")
     ap.add_argument("--rows", default="restricted", choices=["restricted", "full"],
                     help="PTDF rows of the study: the needed branches only, or every branch")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="topologies per internal chunk of the solver (0 = automatic)")
     ap.add_argument("--compact", action="store_true",
                     help="FP32 N-1 over each topology's valid contingencies instead of every contingency column")
     ap.add_argument("--multi", type=int, default=32,

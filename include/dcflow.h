@@ -132,7 +132,7 @@ int dcflow_base_ptdf_noalloc(dcflow_ctx* ctx, const int32_t* rows, int32_t n_row
  * multi_ptr / multi_branch (optional, host): n_multi N-1 cases that take out
  * several branches at once (Def. 4, MODF; e.g. the windings of a
  * three-winding transformer), set m = multi_branch[multi_ptr[m] ..
- * multi_ptr[m + 1]), 1 to 4 distinct branches each.
+ * multi_ptr[m + 1]), 1 to 4 distinct branches each, at most 262,140 sets.
  * Synchronous; may be called again to change the study.
  */
 typedef struct {

@@ -71,6 +71,10 @@ struct ChunkBufs {
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// multi-outage sets of a study: four per block of the per-set preparation, whose
+// grid y extent is at most 65,535
+constexpr int kMaxMultiSets = 4 * 65535;
+
 // Raise a kernel's dynamic shared-memory limit once per device (a function
 // attribute lives in each device's context); `done` holds one bit per device.
 template <class K>

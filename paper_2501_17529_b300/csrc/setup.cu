@@ -392,8 +392,8 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
   const int n_multi = s->n_multi > 0 ? s->n_multi : 0;
   std::vector<int> mptr(1, 0), mbr;
   if (n_multi > 0) {  // multi-outage sets: 1 to 4 distinct branches each
-    if (!s->multi_ptr || !s->multi_branch || s->multi_ptr[0] != 0) {
-      set_error("dcflow_set_study: multi-outage sets need multi_ptr (from 0) and multi_branch");
+    if (!s->multi_ptr || !s->multi_branch || s->multi_ptr[0] != 0 || n_multi > kMaxMultiSets) {
+      set_error("dcflow_set_study: multi-outage sets need multi_ptr (from 0) and multi_branch, at most 262,140 sets");
       return DCFLOW_ERR_INVALID_ARG;
     }
     for (int m = 0; m < n_multi; ++m) {

@@ -435,7 +435,7 @@ def test_multi_outages_rejected_forms():
     lim = oracle.thermal_limits(w.grid, w.inj)
     s = Solver(w.grid, precision="fp32")
     E = len(w.grid.f)
-    for bad in ([[]], [[0, 1, 2, 3, 4]], [[2, 2]], [[E]], [[-1]]):
+    for bad in ([[]], [[0, 1, 2, 3, 4]], [[2, 2]], [[E]], [[-1]], [[0]] * (4 * 65535 + 1)):
         with pytest.raises(DCFlowError):
             s.set_study(w.mon, w.cont, lim, split_bus=w.subs, multi=bad)
     s.set_study(w.mon, w.cont, lim, split_bus=w.subs)
