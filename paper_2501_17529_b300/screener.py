@@ -5,8 +5,9 @@ the screened N-1 all run in libdcflow's kernels; PyTorch supplies device
 memory, index permutations and reductions of reported statistics.
 
 The exact full N-1 (``Solver.solve(want_cont_max=True)``) is both the source
-of the training labels and the judge of the screener: recall is measured
-against it, and the screened solve falls back to it per topology.
+of the training labels and the reference the screener is scored against:
+recall is measured against it, and the screened solve falls back to it per
+topology.
 
     python -m paper_2501_17529_b300.screener --train 200000 --eval 100000
 """
