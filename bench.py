@@ -292,6 +292,30 @@ def run_ours(args):
     results, hosts = {}, {}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
     peaks, peak_kind = _peaks()
+    alu_peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # T issue slots/s, as the N-1 roofline
+    lib = __import__("paper_2501_17529_b300.dcflow", fromlist=["x"])
+
+    def timed(solver, dbx, resx, steps, stream):
+        """Warm-up, then `steps` timed solves (L2 flushed before each) with the kernel profile on:
+        (seconds over the steps, max over ranks; per-kind kernel milliseconds per step)."""
+        for _ in range(args.warmup):
+            solver.solve(dbx, results=resx)
+        torch.cuda.synchronize()
+        evx = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        lib.dcflow_profile(solver.ctx, True)
+        for k2 in range(steps):
+            flush.fill_(k2 & 0xFF)
+            evx[k2][0].record(stream)
+            solver.solve(dbx, results=resx)
+            evx[k2][1].record(stream)
+        torch.cuda.synchronize()
+        kp = lib.dcflow_profile_read(solver.ctx)
+        lib.dcflow_profile(solver.ctx, False)
+        tx = sum(a.elapsed_time(b) for a, b in evx) / 1e3
+        if ws > 1:
+            tx, _ = reduce_over_ranks(tx, 0, "cuda")
+        return tx, {k: v / steps for k, v in kp.items() if k.endswith("_ms")}
+
     for form in (args.forms.split(",")):
         torch.cuda.synchronize()
         ts = time.perf_counter()
@@ -309,7 +333,6 @@ def run_ours(args):
         host = res.to_host()
         hosts[form] = host
         lf = _loadflows(w.topo, host["status"], host["n_island_cont"], w.cont, T_STEPS) * max(1, db.n_var)
-        lib = __import__("paper_2501_17529_b300.dcflow", fromlist=["x"])
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         launches = 0
         lib.dcflow_profile(solver.ctx, True)
@@ -329,6 +352,7 @@ def run_ours(args):
         ms = [a.elapsed_time(b) for a, b in ev]
         t_dev = sum(ms) / 1e3
         kern = lib.dcflow_profile_read(solver.ctx)
+        kern = {"n1_ms": kern["n1_ms"], "n1_launches": kern["n1_launches"]}
         lib.dcflow_profile(solver.ctx, False)
         if ws > 1:
             t_dev, lf_all = reduce_over_ranks(t_dev, lf, "cuda")
@@ -343,21 +367,14 @@ def run_ours(args):
         # the same solve with the sparse worst results (agg_i, top k per topology and timestep)
         if form == "fp32" and args.top_k > 0:
             rk = DeviceResults(db.n_topo, db.n_time, len(w.mon), want_var=db.n_var > 0, top_k=args.top_k)
-            for _ in range(args.warmup):
-                solver.solve(db, results=rk)
-            torch.cuda.synchronize()
-            evk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-            for k2 in range(steps):
-                flush.fill_(k2 & 0xFF)
-                evk[k2][0].record(stream)
-                solver.solve(db, results=rk)
-                evk[k2][1].record(stream)
-            torch.cuda.synchronize()
-            tk = sum(a.elapsed_time(b) for a, b in evk) / 1e3
-            if ws > 1:
-                tk, _ = reduce_over_ranks(tk, lf, "cuda")
+            tk, kk = timed(solver, db, rk, steps, stream)
+            nok = int((rk.island_flag[:db.n_topo] == 0).sum().item())
+            rec = nok * T_STEPS * args.top_k * n_mon  # entries of the cases' recomputed columns
             results[f"fp32_top{args.top_k}"] = {"value": lf_all * steps / tk, "ms_per_step": 1e3 * tk / steps,
                                                 "loadflows_per_step": lf_all, "steps": steps,
+                                                "kernels": {"name": "k_topcases", "ms_per_step": kk["topcases_ms"],
+                                                           "column_entries_per_s_T": rec / (kk["topcases_ms"] / 1e3) / 1e12
+                                                           if kk["topcases_ms"] else None},
                                                 "note": f"fp32 solve plus the {args.top_k} worst N-1 cases "
                                                         "(contingency, monitored branch, loading) per topology "
                                                         "and timestep"}
@@ -368,23 +385,15 @@ def run_ours(args):
             gp = np.abs(rng.normal(1.0, 0.5, (T_STEPS, args.gens)))
             dbg = DeviceBatch(w.topo, w.inj, w.var, gen_bus=gb, gen_p=gp)
             rg = DeviceResults(db.n_topo, db.n_time, len(w.mon), want_var=db.n_var > 0, want_gen=True)
-            for _ in range(args.warmup):
-                solver.solve(dbg, results=rg)
-            torch.cuda.synchronize()
-            evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-            for k2 in range(steps):
-                flush.fill_(k2 & 0xFF)
-                evg[k2][0].record(stream)
-                solver.solve(dbg, results=rg)
-                evg[k2][1].record(stream)
-            torch.cuda.synchronize()
-            tg = sum(a.elapsed_time(b) for a, b in evg) / 1e3
-            if ws > 1:
-                tg, _ = reduce_over_ranks(tg, lf, "cuda")
+            tg, kg = timed(solver, dbg, rg, steps, stream)
             ngen_cases = int((rg.island_flag[:db.n_topo] == 0).sum().item()) * T_STEPS * args.gens * ws
+            gen_rate = ngen_cases / ws * n_mon / (kg["gen_ms"] / 1e3) / 1e12 if kg["gen_ms"] else None
             results[f"fp32_gen{args.gens}"] = {"value": lf_all * steps / tg, "ms_per_step": 1e3 * tg / steps,
                                                "loadflows_per_step": lf_all,
                                                "generator_cases_per_step": ngen_cases, "steps": steps,
+                                               "kernels": {"name": "k_gen_n1", "ms_per_step": kg["gen_ms"],
+                                                          "entries_per_s_T": gen_rate, "alu_peak_T": alu_peak,
+                                                          "frac": gen_rate / alu_peak if gen_rate else None},
                                                "note": f"fp32 solve plus {args.gens} generator-failure N-1 cases "
                                                        "per topology and timestep (value counts the branch "
                                                        "N-1 cases only)"}
@@ -396,25 +405,21 @@ def run_ours(args):
             tis = synth.make_injection_topologies(w.grid, w.subs, tsub, w.inj, args.ti, 900)
             dbt = DeviceBatch(tsub, w.inj, ti=tis)
             rt = DeviceResults(nsub, db.n_time, len(w.mon), want_var=True)
-            for _ in range(args.warmup):
-                solver.solve(dbt, results=rt)
-            torch.cuda.synchronize()
-            evt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-            for k2 in range(steps):
-                flush.fill_(k2 & 0xFF)
-                evt[k2][0].record(stream)
-                solver.solve(dbt, results=rt)
-                evt[k2][1].record(stream)
-            torch.cuda.synchronize()
-            tt = sum(a.elapsed_time(b) for a, b in evt) / 1e3
+            tt, kt = timed(solver, dbt, rt, steps, stream)
             st_h = rt.island_flag[:nsub].cpu().numpy()
             ni_h = rt.n_island_cont[:nsub].cpu().numpy()
             lft = _loadflows(tsub, st_h, ni_h, w.cont, T_STEPS) * args.ti
+            # the expansion writes every (timestep, assignment)'s N-0 row and N-1 weights
+            exp_bytes = int((st_h == 0).sum()) * T_STEPS * args.ti * (((n_mon + 15) // 16 * 16) + len(w.cont)) * 4
+            exp_gbs = exp_bytes / (kt["expand_ms"] / 1e3) / 1e9 if kt["expand_ms"] else None
             if ws > 1:
-                tt, lft = reduce_over_ranks(tt, lft, "cuda")
+                _, lft = reduce_over_ranks(0.0, lft, "cuda")
             results[f"fp32_ti{args.ti}"] = {
                 "value": lft * steps / tt, "ms_per_step": 1e3 * tt / steps, "loadflows_per_step": lft,
                 "topologies": nsub, "steps": steps,
+                "kernels": {"name": "k_ti_expand", "ms_per_step": kt["expand_ms"], "written_gbs": exp_gbs,
+                           "hbm_peak_gbs": peaks.get("hbm_gbs"), "frac": exp_gbs / peaks["hbm_gbs"] if exp_gbs else None,
+                           "screening_n1_ms_per_step": kt["n1_ms"]},
                 "note": f"injection topologies: {args.ti} busbar assignments of the injections at the split "
                         f"substations per topology ({nsub} topologies x {T_STEPS} timesteps), metric-first "
                         "brute force; loadflows count every (topology, timestep, assignment, contingency)"}
@@ -425,25 +430,18 @@ def run_ours(args):
             sets = [[int(b) for b in rng.choice(E, 2 + k % 3, replace=False)] for k in range(args.multi)]
             solver.set_study(w.mon, w.cont, lim, split_bus=w.subs, outage_cand=ocand, multi=sets)
             rm = DeviceResults(db.n_topo, db.n_time, len(w.mon), want_multi=True)
-            for _ in range(args.warmup):
-                solver.solve(db, results=rm)
-            torch.cuda.synchronize()
-            evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-            for k2 in range(steps):
-                flush.fill_(k2 & 0xFF)
-                evm[k2][0].record(stream)
-                solver.solve(db, results=rm)
-                evm[k2][1].record(stream)
-            torch.cuda.synchronize()
-            tm = sum(a.elapsed_time(b) for a, b in evm) / 1e3
-            if ws > 1:
-                tm, _ = reduce_over_ranks(tm, lf, "cuda")
+            tm, km = timed(solver, db, rm, steps, stream)
             okm = rm.island_flag[:db.n_topo] == 0
             nm_cases = (int(okm.sum().item()) * args.multi - int(rm.n_island_multi[:db.n_topo][okm].sum().item())) \
                 * T_STEPS * ws
             results[f"fp32_multi{args.multi}"] = {
                 "value": lf_all * steps / tm, "ms_per_step": 1e3 * tm / steps, "loadflows_per_step": lf_all,
                 "multi_cases_per_step": nm_cases, "steps": steps,
+                "kernels": {"name": "k_multi_rows", "ms_per_step": km["multi_ms"],
+                           "entries_per_s_T": nm_cases / ws * n_mon / (km["multi_ms"] / 1e3) / 1e12 if km["multi_ms"] else None,
+                           "alu_peak_T": alu_peak,
+                           "frac": (nm_cases / ws * n_mon / (km["multi_ms"] / 1e3) / 1e12 / alu_peak) if km["multi_ms"] else None,
+                           "prep_ms_per_step": km["multi_prep_ms"]},
                 "note": f"fp32 solve plus {args.multi} multi-outage N-1 sets of 2-4 branches per topology and "
                         "timestep (value counts the single-branch N-1 cases only; multi_cases_per_step counts "
                         "the sets evaluated, sets a topology already lost counted too)"}

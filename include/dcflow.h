@@ -289,14 +289,24 @@ int64_t dcflow_last_launch_count(const dcflow_ctx* ctx);
 
 /*
  * Kernel timing.  dcflow_profile(ctx, 1) resets the counters and makes every
- * later dcflow_solve_batch bracket each launch of the fused N-1 kernel (the
- * candidate screening passes included) with CUDA events recorded on the call's
- * stream; dcflow_profile(ctx, 0) stops.
- * dcflow_profile_read synchronises on the recorded events and returns the
- * summed N-1 kernel time in milliseconds and the number of such launches.
+ * later dcflow_solve_batch bracket each launch of the timed kernels with CUDA
+ * events recorded on the stream the kernel runs on; dcflow_profile(ctx, 0)
+ * stops.  dcflow_profile_read_kind synchronises on the recorded events and
+ * returns the summed time in milliseconds and the number of launches of one
+ * kind; dcflow_profile_read is the fused N-1 kernel's (kind DCFLOW_PROF_N1:
+ * the candidate screening passes included).
  */
+enum {
+  DCFLOW_PROF_N1 = 0,          /* fused N-1 (full, screening and screened passes) */
+  DCFLOW_PROF_MULTI = 1,       /* multi-outage rows */
+  DCFLOW_PROF_MULTI_PREP = 2,  /* multi-outage per-set systems (preparation stream) */
+  DCFLOW_PROF_GEN = 3,         /* generator-failure N-1 */
+  DCFLOW_PROF_TOPCASES = 4,    /* the k worst N-1 cases */
+  DCFLOW_PROF_EXPAND = 5       /* operands of every (timestep, candidate) */
+};
 int dcflow_profile(dcflow_ctx* ctx, int32_t enable);
 int dcflow_profile_read(dcflow_ctx* ctx, double* n1_ms, int64_t* n1_launches);
+int dcflow_profile_read_kind(dcflow_ctx* ctx, int32_t kind, double* ms, int64_t* launches);
 
 /*
  * Tensor-core BF16 GEMM used by the learned contingency screener (the paper

@@ -145,6 +145,26 @@ struct dcflow_ctx {
   int64_t chunk_cap = 0;
   // kernel timing (dcflow_profile)
   bool prof_on = false;
-  std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop) per N-1 launch
+  std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop) per timed launch
+  std::vector<int> prof_kind;        // DCFLOW_PROF_* of each pair
   size_t prof_used = 0;
+  // start a timed launch of `kind` on `st` (returns the pair, or -1 when not profiling)
+  int prof_begin(cudaStream_t st) {
+    if (!prof_on) return -1;
+    while (prof_ev.size() < prof_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      prof_ev.push_back(e);
+    }
+    const int p = (int)prof_used;
+    prof_used += 2;
+    prof_kind.resize(prof_used / 2);
+    prof_kind[p / 2] = -1;  // completed by prof_end
+    return cudaEventRecord(prof_ev[p], st) == cudaSuccess ? p : -1;
+  }
+  void prof_end(int p, int kind, cudaStream_t st) {
+    if (p < 0) return;
+    prof_kind[p / 2] = kind;
+    cudaEventRecord(prof_ev[p + 1], st);
+  }
 };

@@ -1653,6 +1653,25 @@ __global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const i
   }
 }
 
+// one set's N members at one monitored row, TT timesteps: the N-1 loading and
+// its running maximum (lowest set on ties) and overload sum
+template <class Real, int N, int TT>
+__device__ __forceinline__ void multi_apply(const Real (&col)[4], const Real* __restrict__ w, const Real (&pt)[TT],
+                                            Real (&mx)[TT], int (&ag)[TT], Real (&ov)[TT], int m) {
+#pragma unroll
+  for (int jt = 0; jt < TT; ++jt) {
+    Real v = pt[jt];
+#pragma unroll
+    for (int a2 = 0; a2 < N; ++a2) v = fma(col[a2], w[jt * 4 + a2], v);
+    if (fabs(v) > mx[jt]) {
+      mx[jt] = fabs(v);
+      ag[jt] = m;
+    }
+    Real dummy = (Real)0;
+    Acc<Real>::add(dummy, ov[jt], v);
+  }
+}
+
 template <class Real, int RMAX, int TT, int SG>
 __global__ __launch_bounds__(128) void k_multi_rows(Args a, int n_multi, const int* __restrict__ mptr,
                                                     const int* __restrict__ mmpos, const Real* __restrict__ PhiMO,
@@ -1727,6 +1746,7 @@ __global__ __launch_bounds__(128) void k_multi_rows(Args a, int n_multi, const i
           const int e0 = e0_s[s];
           Real col[4];
           bool in_set = false;  // a member itself carries nothing (the MODF rows of O are -I)
+          int n = 0;
 #pragma unroll
           for (int a2 = 0; a2 < 4; ++a2) {
             const int mp = mp_s[s][a2];
@@ -1735,22 +1755,25 @@ __global__ __launch_bounds__(128) void k_multi_rows(Args a, int n_multi, const i
               c = PhiMO[(size_t)(e0 + a2) * Mp + l];
 #pragma unroll
               for (int j = 0; j < RMAX; ++j) c = fma(-zr[j], vt_s[s][a2][j], c);
+              ++n;
             }
             col[a2] = c * rm;
             in_set |= mp == l;
           }
+          const int m = g0 + s;
+          if (in_set) {  // rare: loading 0 at every timestep
 #pragma unroll
-          for (int jt = 0; jt < TT; ++jt) {
-            Real v = pt[jt];
-#pragma unroll
-            for (int a2 = 0; a2 < 4; ++a2) v = fma(col[a2], w_s[s][jt][a2], v);
-            v = in_set ? (Real)0 : v;
-            if (fabs(v) > mx[jt]) {
-              mx[jt] = fabs(v);
-              ag[jt] = g0 + s;
-            }
-            Real dummy = (Real)0;
-            Acc<Real>::add(dummy, ov[jt], v);
+            for (int jt = 0; jt < TT; ++jt)
+              if ((Real)0 > mx[jt]) {
+                mx[jt] = (Real)0;
+                ag[jt] = m;
+              }
+          } else {  // n is the same for the whole block
+            const Real* w = &w_s[s][0][0];
+            if (n == 1) multi_apply<Real, 1, TT>(col, w, pt, mx, ag, ov, m);
+            else if (n == 2) multi_apply<Real, 2, TT>(col, w, pt, mx, ag, ov, m);
+            else if (n == 3) multi_apply<Real, 3, TT>(col, w, pt, mx, ag, ov, m);
+            else multi_apply<Real, 4, TT>(col, w, pt, mx, ag, ov, m);
           }
         }
       }
@@ -2504,19 +2527,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     }
     for (int t0 = 0; t0 < Tn; t0 += TTn) {
       const dim3 grid(ncb, a.nq);
-      const bool prof = ctx->prof_on;  // screening and full passes alike
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (prof) {
-        while (ctx->prof_ev.size() < ctx->prof_used + 2) {
-          cudaEvent_t e;
-          DCF_CUDA(cudaEventCreate(&e));
-          ctx->prof_ev.push_back(e);
-        }
-        e0 = ctx->prof_ev[ctx->prof_used];
-        e1 = ctx->prof_ev[ctx->prof_used + 1];
-        ctx->prof_used += 2;
-        DCF_CUDA(cudaEventRecord(e0, st));
-      }
+      const int pe = ctx->prof_begin(st);  // screening and full passes alike
       int rc;
       if (fp64) rc = launch_n1<double>(a, RMAX, TTn, grid, st, t0);
       else if (cmp)
@@ -2526,7 +2537,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       if (rc) return rc;
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
-      if (prof) DCF_CUDA(cudaEventRecord(e1, st));
+      ctx->prof_end(pe, DCFLOW_PROF_N1, st);
     }
     return 0;
   };
@@ -2578,16 +2589,19 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       DCF_CHECK_LAUNCH();
     }
     if (want_multi) {  // the multi-outage small systems ride with the FP64 preparation
+      const int pe = ctx->prof_begin(side);
       if (fp64) launch_multi_prep<double>(ap, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(), B, side);
       else launch_multi_prep<float>(ap, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(), B, side);
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
+      ctx->prof_end(pe, DCFLOW_PROF_MULTI_PREP, side);
     }
     DCF_CUDA(cudaEventRecord(ctx->ev_prep[bi], side));
     DCF_CUDA(cudaStreamWaitEvent(st, ctx->ev_prep[bi], 0));
     Args af = a;  // final stage: T real timesteps
     if (Uc > 0) {
       // expand, screen (metric-first: maximum only), select, gather
+      const int pex = ctx->prof_begin(st);
       if (TI) {
         if (fp64)
           k_ti_expand<double><<<dim3(TV, ch.nq), 128, 0, st>>>(
@@ -2606,6 +2620,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       }
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
+      ctx->prof_end(pex, DCFLOW_PROF_EXPAND, st);
       Args av = a;
       av.T = TV;
       av.out.n1_cont_max = nullptr;
@@ -2695,25 +2710,14 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       }
       const SelArgs sargs{ctx->PhiCM.as<float>(), Mp, SB.csel.as<int>(), SB.nsel.as<int>(), SB.work.as<int>()};
       for (int t0 = 0; t0 < T; t0 += TTs) {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (ctx->prof_on) {
-          while (ctx->prof_ev.size() < ctx->prof_used + 2) {
-            cudaEvent_t e;
-            DCF_CUDA(cudaEventCreate(&e));
-            ctx->prof_ev.push_back(e);
-          }
-          e0 = ctx->prof_ev[ctx->prof_used];
-          e1 = ctx->prof_ev[ctx->prof_used + 1];
-          ctx->prof_used += 2;
-          DCF_CUDA(cudaEventRecord(e0, st));
-        }
+        const int pe = ctx->prof_begin(st);
         if (reg_sel) rc = items ? launch_reg_sel(smaps, af, sargs, RMAX, TTs, items, st, t0) : 0;
         else rc = fp64 ? launch_sel<double>(af, ctx->PhiCM.p, SB, RMAX, TTs, sgrid, st, t0)
                        : launch_sel<float>(af, ctx->PhiCM.p, SB, RMAX, TTs, sgrid, st, t0);
         if (rc) return rc;
         ++ctx->launches;
         DCF_CHECK_LAUNCH();
-        if (e1) DCF_CUDA(cudaEventRecord(e1, st));
+        ctx->prof_end(pe, DCFLOW_PROF_N1, st);
       }
       nsel_dev = SB.nsel.as<int>();
     } else if (C_eff > 0) {
@@ -2725,6 +2729,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     ++ctx->launches;
     DCF_CHECK_LAUNCH();
     if (want_multi) {
+      const int pe = ctx->prof_begin(st);
       if (fp64)
         launch_multi_rows<double>(af, RMAX, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multi_mpos.as<int>(),
                                   ctx->PhiMO.p, B, st);
@@ -2733,22 +2738,27 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                                  ctx->PhiMO.p, B, st);
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
+      ctx->prof_end(pe, DCFLOW_PROF_MULTI, st);
     }
     if (G > 0) {
+      const int pe = ctx->prof_begin(st);
       if (fp64)
         launch_gen<double>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V, ctx->gen_cols.p, st);
       else
         launch_gen<float>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V, ctx->gen_cols.p, st);
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
+      ctx->prof_end(pe, DCFLOW_PROF_GEN, st);
     }
     if (top_k > 0) {
+      const int pe = ctx->prof_begin(st);
       if (fp64)
         launch_topcases<double>(af, RMAX, af.out.n1_cont_max, ctx->cont_inv.as<int>(), ctx->PhiCM.p, top_k, st);
       else
         launch_topcases<float>(af, RMAX, af.out.n1_cont_max, ctx->cont_inv.as<int>(), ctx->PhiCM.p, top_k, st);
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
+      ctx->prof_end(pe, DCFLOW_PROF_TOPCASES, st);
     }
     DCF_CUDA(cudaEventRecord(ctx->ev_free[bi], st));
   }
@@ -2813,16 +2823,23 @@ extern "C" int dcflow_profile(dcflow_ctx* ctx, int32_t enable) {
   return DCFLOW_OK;
 }
 
-extern "C" int dcflow_profile_read(dcflow_ctx* ctx, double* n1_ms, int64_t* n1_launches) {
-  if (!ctx || !n1_ms || !n1_launches) return DCFLOW_ERR_INVALID_ARG;
+extern "C" int dcflow_profile_read_kind(dcflow_ctx* ctx, int32_t kind, double* ms_out, int64_t* launches) {
+  if (!ctx || !ms_out || !launches) return DCFLOW_ERR_INVALID_ARG;
   double ms = 0.0;
+  int64_t n = 0;
   for (size_t i = 0; i + 1 < ctx->prof_used; i += 2) {
+    if (ctx->prof_kind[i / 2] != kind) continue;
     DCF_CUDA(cudaEventSynchronize(ctx->prof_ev[i + 1]));
     float x = 0.f;
     DCF_CUDA(cudaEventElapsedTime(&x, ctx->prof_ev[i], ctx->prof_ev[i + 1]));
     ms += x;
+    ++n;
   }
-  *n1_ms = ms;
-  *n1_launches = (int64_t)(ctx->prof_used / 2);
+  *ms_out = ms;
+  *launches = n;
   return DCFLOW_OK;
+}
+
+extern "C" int dcflow_profile_read(dcflow_ctx* ctx, double* n1_ms, int64_t* n1_launches) {
+  return dcflow_profile_read_kind(ctx, DCFLOW_PROF_N1, n1_ms, n1_launches);
 }

@@ -65,6 +65,7 @@ class ScreenReport(ctypes.Structure):
 EXPORTED = ["dcflow_default_options", "dcflow_setup", "dcflow_base_ptdf", "dcflow_base_ptdf_noalloc",
             "dcflow_set_study",
             "dcflow_solve_batch", "dcflow_last_launch_count", "dcflow_profile", "dcflow_profile_read",
+            "dcflow_profile_read_kind",
             "dcflow_gemm_bf16",
             "dcflow_screen_create", "dcflow_screen_destroy", "dcflow_screen_dims", "dcflow_screen_features",
             "dcflow_screen_labels", "dcflow_screen_backward", "dcflow_screen_adam", "dcflow_screen_train_step",
@@ -105,6 +106,8 @@ def load_library(path: str = LIB_PATH):
     lib.dcflow_profile.restype = c_int32
     lib.dcflow_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int64)]
     lib.dcflow_profile_read.restype = c_int32
+    lib.dcflow_profile_read_kind.argtypes = [c_void_p, c_int32, POINTER(c_double), POINTER(c_int64)]
+    lib.dcflow_profile_read_kind.restype = c_int32
     lib.dcflow_gemm_bf16.argtypes = [c_int32, c_int32, c_int32, c_void_p, c_int32, c_void_p, c_int32, c_void_p,
                                      c_int32, c_void_p, c_int32, c_int32, c_void_p]
     lib.dcflow_gemm_bf16.restype = c_int32
@@ -257,10 +260,23 @@ def dcflow_profile(ctx, enable: bool):
     _check(load_library().dcflow_profile(ctx, 1 if enable else 0), "dcflow_profile")
 
 
-def dcflow_profile_read(ctx):
+PROFILE_KINDS = {"n1": 0, "multi": 1, "multi_prep": 2, "gen": 3, "topcases": 4, "expand": 5}
+
+
+def dcflow_profile_read_kind(ctx, kind):
     ms, n = c_double(), c_int64()
-    _check(load_library().dcflow_profile_read(ctx, byref(ms), byref(n)), "dcflow_profile_read")
-    return {"n1_ms": ms.value, "n1_launches": n.value}
+    k = PROFILE_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(load_library().dcflow_profile_read_kind(ctx, k, byref(ms), byref(n)), "dcflow_profile_read_kind")
+    return ms.value, n.value
+
+
+def dcflow_profile_read(ctx):
+    """Timed kernel milliseconds and launches since dcflow_profile(ctx, True), per kind."""
+    out = {}
+    for name in PROFILE_KINDS:
+        ms, n = dcflow_profile_read_kind(ctx, name)
+        out[f"{name}_ms"], out[f"{name}_launches"] = ms, n
+    return out
 
 
 def dcflow_gemm_bf16(A, B, bias=None, relu=False, out=None, out_bf16=False, stream=None):
