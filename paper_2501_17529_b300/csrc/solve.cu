@@ -1903,15 +1903,8 @@ void launch_topcases(const Args& a, int RMAX, const float* cmax, const int* cinv
 template <class Real, int RMAX>
 void launch_gen_r(const Args& a, int G, const int* gen_bus, const double* gen_p, const double* ptdf, int V,
                   const Real* P, cudaStream_t st) {
-  // timesteps per pass (per-thread accumulators): one pass of 24 in the FP32 form, so that the
-  // generators' columns are built once per topology
-  if constexpr (sizeof(Real) == 4) {
-    if (a.T > 8) {
-      for (int t0 = 0; t0 < a.T; t0 += 24)
-        k_gen_n1<Real, RMAX, 24><<<a.nq, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P, t0);
-      return;
-    }
-  }
+  // timesteps per pass (per-thread accumulators); one pass of 24 (the columns built once per
+  // topology) measured slower: the registers it needs halve the resident blocks
   constexpr int TT = 8;
   for (int t0 = 0; t0 < a.T; t0 += TT)
     k_gen_n1<Real, RMAX, TT><<<a.nq, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P, t0);
