@@ -75,6 +75,12 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // grid y extent is at most 65,535
 constexpr int kMaxMultiSets = 4 * 65535;
 
+// float copy of a double array (grid-stride)
+static __global__ void k_to_float(const double* __restrict__ x, float* __restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
 // Raise a kernel's dynamic shared-memory limit once per device (a function
 // attribute lives in each device's context); `done` holds one bit per device.
 template <class K>
@@ -112,6 +118,7 @@ struct dcflow_ctx {
   dcf::DevBuf inv_lim;     // double[M]
   dcf::DevBuf bN;          // double[NN]: susceptance of the needed branches
   dcf::DevBuf PhiN;        // double[NN*NN] base branch-to-branch factors
+  dcf::DevBuf PhiNf, bNf;  // FP32 form: float copies of PhiN and bN (the monitored rows' Z, no conversions)
   dcf::DevBuf PtdfN;       // double[NN*V] base PTDF rows of the needed branches
   dcf::DevBuf PhiMC;       // Real[M*ldc] Phi[mon, cont] / limit[mon], row stride ldc
   int ldc = 0;             // round_up(C, 4): 16-byte row pitch for the tensor-memory accelerator
@@ -132,6 +139,7 @@ struct dcflow_ctx {
   dcf::DevBuf Y;           // solve workspace
   // batch scratch
   dcf::DevBuf p0;          // double[NN*(T+R)]: base flows, then R pool columns
+  dcf::DevBuf p0f;         // FP32 form: float copy of p0
   dcf::DevBuf pool, var_k;  // candidate pool buses; pool index of every candidate entry
   dcf::DevBuf dp;          // double[NN*U] base flow change of each candidate
   dcf::DevBuf rank, status, perm, hist, hist_host;

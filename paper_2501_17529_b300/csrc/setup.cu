@@ -502,6 +502,16 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
       NN, V, d_N.as<int>(), ctx->b.as<double>(), ctx->rid.as<int>(), ctx->Y.as<double>(), ldy, ctx->PtdfN.as<double>());
   ctx->launches += 2;
   const size_t rs = ctx->opt.precision == DCFLOW_FP64 ? sizeof(double) : sizeof(float);
+  if (ctx->opt.precision != DCFLOW_FP64) {  // float copies for the FP32 form's row operands
+    if (ctx->PhiNf.ensure((size_t)NN * NN * sizeof(float)) || ctx->bNf.ensure((size_t)NN * sizeof(float))) {
+      d_N.release();
+      return DCFLOW_ERR_OOM;
+    }
+    k_to_float<<<(unsigned)std::min<size_t>(((size_t)NN * NN + 255) / 256, 148 * 64), 256, 0, st>>>(
+        ctx->PhiN.as<double>(), ctx->PhiNf.as<float>(), (size_t)NN * NN);
+    k_to_float<<<(NN + 255) / 256, 256, 0, st>>>(ctx->bN.as<double>(), ctx->bNf.as<float>(), (size_t)NN);
+    ctx->launches += 2;
+  }
   ctx->ldc = (int)round_up(std::max(C, 1), 4);
   if (ctx->PhiMC.ensure((size_t)M * ctx->ldc * rs)) {
     d_N.release();

@@ -166,6 +166,7 @@ struct EntSmem {
   int en[kEntMax];
   double ew[kEntMax];
   double ewb[kEntMax];  // ew / b of the entry's branch
+  float ewf[kEntMax], ewbf[kEntMax];  // the same in FP32 (no per-use conversion on the FP64 pipe)
   int8_t es[kEntMax];
   int mp[kRMax + 1];
 };
@@ -178,6 +179,8 @@ __device__ void load_entries(EntSmem& S, const Args& a, int q, int r) {
     S.en[e] = a.ent_n[(size_t)q * kEntMax + e];
     S.ew[e] = a.ent_w[(size_t)q * kEntMax + e];
     S.ewb[e] = S.ew[e] / a.bN[S.en[e]];
+    S.ewf[e] = (float)S.ew[e];
+    S.ewbf[e] = (float)S.ewb[e];
     S.es[e] = a.ent_s[(size_t)q * kEntMax + e];
   }
   __syncthreads();
@@ -210,6 +213,18 @@ __device__ __forceinline__ Real z_entry_col_r(const EntSmem& S, const double* Ph
     if (m == row) wdiag += (Real)S.ew[e];
   }
   return fma(-(Real)bN[row], z, wdiag);
+}
+
+// The same from float copies of Phi and b (FP32 form, monitored rows)
+__device__ __forceinline__ float z_entry_col_f(const EntSmem& S, const float* PhiNf, int NN, const float* bNf, int row,
+                                               int j) {
+  float z = 0.f, wdiag = 0.f;
+  for (int e = S.mp[j]; e < S.mp[j + 1]; ++e) {
+    const int m = S.en[e];
+    z = fmaf(S.ewbf[e], PhiNf[(size_t)m * NN + row], z);
+    if (m == row) wdiag += S.ewf[e];
+  }
+  return fmaf(-bNf[row], z, wdiag);
 }
 
 // Z[row, j] = W[row, j] - sum_{q in mod j} w_q Phi[row, m_q]  (FP64)
@@ -360,7 +375,8 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
 //                       row 1: 1 (0 for an outaged l), row 2: position of l in
 //                       the contingency list as int bits (-1 if none), row 3: 0
 template <class Real, int RMAX>
-__global__ __launch_bounds__(128) void k_rows(Args a, Real* __restrict__ zcd) {
+__global__ __launch_bounds__(128) void k_rows(Args a, Real* __restrict__ zcd, const float* __restrict__ p0f,
+                                              const float* __restrict__ PhiNf, const float* __restrict__ bNf) {
   const int q = blockIdx.x;
   __shared__ EntSmem S;
   __shared__ int outN[kRMax];
@@ -390,7 +406,10 @@ __global__ __launch_bounds__(128) void k_rows(Args a, Real* __restrict__ zcd) {
     for (int k = 0; k < nout; ++k) outd |= (outN[k] == nl);
     Real z[RMAX];
 #pragma unroll
-    for (int j = 0; j < RMAX; ++j) z[j] = (j < r) ? z_entry_col_r<Real>(S, a.PhiN, NN, a.bN, nl, j) : (Real)0;
+    for (int j = 0; j < RMAX; ++j) {
+      if constexpr (sizeof(Real) == 4) z[j] = (j < r) ? z_entry_col_f(S, PhiNf, NN, bNf, nl, j) : 0.f;
+      else z[j] = (j < r) ? z_entry_col_r<Real>(S, a.PhiN, NN, a.bN, nl, j) : (Real)0;
+    }
     const Real il = (Real)a.inv_lim[l];
 #pragma unroll
     for (int j = 0; j < RMAX; ++j) Zs[(size_t)j * Mp + l] = outd ? (Real)0 : z[j] * il;
@@ -403,7 +422,9 @@ __global__ __launch_bounds__(128) void k_rows(Args a, Real* __restrict__ zcd) {
     }
     meta[3 * Mp + l] = (Real)0;
     for (int t = 0; t < T; ++t) {
-      Real pf = (Real)a.p0[(size_t)nl * T + t];
+      Real pf;
+      if constexpr (sizeof(Real) == 4) pf = p0f[(size_t)nl * T + t];
+      else pf = a.p0[(size_t)nl * T + t];
 #pragma unroll
       for (int j = 0; j < RMAX; ++j) pf = fma(-z[j], alph[j * T + t], pf);
       ptil[(size_t)t * Mp + l] = outd ? (Real)0 : pf * il;
@@ -435,10 +456,15 @@ __global__ __launch_bounds__(128) void k_rows(Args a, Real* __restrict__ zcd) {
     if (zcd)  // Z[c, :] / den_c for the injection-topology candidates
 #pragma unroll
       for (int j = 0; j < RMAX; ++j) zcd[((size_t)q * kRMax + j) * C + c] = (Real)z[j] * invd;
-    for (int t = 0; t < T; ++t) {
-      Real pf = (Real)a.p0[(size_t)nc * T + t];
+    Real zr[RMAX];
 #pragma unroll
-      for (int j = 0; j < RMAX; ++j) pf = fma(-(Real)z[j], alph[j * T + t], pf);
+    for (int j = 0; j < RMAX; ++j) zr[j] = (Real)z[j];
+    for (int t = 0; t < T; ++t) {
+      Real pf;
+      if constexpr (sizeof(Real) == 4) pf = p0f[(size_t)nc * T + t];
+      else pf = a.p0[(size_t)nc * T + t];
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) pf = fma(-zr[j], alph[j * T + t], pf);
       sv[(size_t)t * C + c] = pf * invd;
     }
   }
@@ -1940,17 +1966,18 @@ int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
 
 // per-topology r x r systems and row operands of one chunk
 template <class Real>
-void launch_prep(const Args& a, int RMAX, int nq, size_t dyn, cudaStream_t st, void* zcd) {
+void launch_prep(const Args& a, int RMAX, int nq, size_t dyn, cudaStream_t st, void* zcd, const float* p0f,
+                 const float* PhiNf, const float* bNf) {
   Real* zc = static_cast<Real*>(zcd);
   if (RMAX == 4) {
     k_small<Real, 4><<<nq, 128, 0, st>>>(a);
-    k_rows<Real, 4><<<nq, 128, dyn, st>>>(a, zc);
+    k_rows<Real, 4><<<nq, 128, dyn, st>>>(a, zc, p0f, PhiNf, bNf);
   } else if (RMAX == 8) {
     k_small<Real, 8><<<nq, 128, 0, st>>>(a);
-    k_rows<Real, 8><<<nq, 128, dyn, st>>>(a, zc);
+    k_rows<Real, 8><<<nq, 128, dyn, st>>>(a, zc, p0f, PhiNf, bNf);
   } else {
     k_small<Real, 16><<<nq, 128, 0, st>>>(a);
-    k_rows<Real, 16><<<nq, 128, dyn, st>>>(a, zc);
+    k_rows<Real, 16><<<nq, 128, dyn, st>>>(a, zc, p0f, PhiNf, bNf);
   }
 }
 
@@ -2303,6 +2330,12 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                                                 ctx->p0.as<double>());
     ++ctx->launches;
   }
+  if (!fp64) {  // the FP32 form's row operands read a float copy
+    if (ctx->p0f.ensure((size_t)NN * Text * sizeof(float))) return DCFLOW_ERR_OOM;
+    k_to_float<<<(unsigned)std::min<size_t>(((size_t)NN * Text + 255) / 256, 148 * 64), 256, 0, st>>>(
+        ctx->p0.as<double>(), ctx->p0f.as<float>(), (size_t)NN * Text);
+    ++ctx->launches;
+  }
   ++ctx->launches;
   DCF_CHECK_LAUNCH();
   GridDev g{ctx->f.as<int>(), ctx->t.as<int>(), ctx->b.as<double>(), ctx->inc_ptr.as<int>(), ctx->inc_list.as<int>(),
@@ -2581,8 +2614,10 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                                             B.tiel.as<int>(), B.tirow.as<int>(), B.nel.as<int>());
       ++ctx->launches;
     }
-    if (fp64) launch_prep<double>(ap, RMAX, ch.nq, dyn, side, TI ? B.zcd.p : nullptr);
-    else launch_prep<float>(ap, RMAX, ch.nq, dyn, side, TI ? B.zcd.p : nullptr);
+    if (fp64) launch_prep<double>(ap, RMAX, ch.nq, dyn, side, TI ? B.zcd.p : nullptr, nullptr, nullptr, nullptr);
+    else
+      launch_prep<float>(ap, RMAX, ch.nq, dyn, side, TI ? B.zcd.p : nullptr, ctx->p0f.as<float>(),
+                         ctx->PhiNf.as<float>(), ctx->bNf.as<float>());
     ctx->launches += 3;
     DCF_CHECK_LAUNCH();
     if (cmp) {  // the valid contingencies of every topology (after the denominators)
