@@ -764,14 +764,27 @@ __global__ void k_var_expand(Args ap, int T, int U, const int* __restrict__ var_
   Real* po = ptv + ((size_t)q * TV + vt) * Mp;
   Real* so = svv + ((size_t)q * TV + vt) * C;
   const int k0 = var_ptr[u], k1 = var_ptr[u + 1];
+  // the candidate's entries, staged once per block in the working precision (the per-row
+  // conversions would otherwise occupy the FP64 pipe)
+  constexpr int kStage = 64;
+  __shared__ Real d_s[kStage];
+  __shared__ int k_s[kStage];
+  for (int k = k0 + threadIdx.x; k < k1 && k < k0 + kStage; k += blockDim.x) {
+    d_s[k - k0] = (Real)var_delta[k];
+    k_s[k - k0] = var_k[k];
+  }
+  __syncthreads();
+  const int ns = min(k1 - k0, kStage);
   for (int l = threadIdx.x; l < M; l += blockDim.x) {
     Real v = pt[(size_t)t * Mp + l];
-    for (int k = k0; k < k1; ++k) v = fma((Real)var_delta[k], pt[(size_t)(T + var_k[k]) * Mp + l], v);
+    for (int k = 0; k < ns; ++k) v = fma(d_s[k], pt[(size_t)(T + k_s[k]) * Mp + l], v);
+    for (int k = k0 + ns; k < k1; ++k) v = fma((Real)var_delta[k], pt[(size_t)(T + var_k[k]) * Mp + l], v);
     po[l] = v;
   }
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
     Real v = sv[(size_t)t * C + c];
-    for (int k = k0; k < k1; ++k) v = fma((Real)var_delta[k], sv[(size_t)(T + var_k[k]) * C + c], v);
+    for (int k = 0; k < ns; ++k) v = fma(d_s[k], sv[(size_t)(T + k_s[k]) * C + c], v);
+    for (int k = k0 + ns; k < k1; ++k) v = fma((Real)var_delta[k], sv[(size_t)(T + var_k[k]) * C + c], v);
     so[c] = v;
   }
 }
@@ -1572,10 +1585,14 @@ __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __rest
 template <class Real>
 __global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const int* __restrict__ mptr,
                                                     const int* __restrict__ mN, Real* __restrict__ mvt,
-                                                    Real* __restrict__ mw, int* __restrict__ mflag) {
+                                                    Real* __restrict__ mw, int* __restrict__ mflag,
+                                                    const float* __restrict__ p0f) {
+  extern __shared__ unsigned char dyn_mp[];
+  Real* alph_s = reinterpret_cast<Real*>(dyn_mp);  // [r][T] alpha in the working precision
   __shared__ EntSmem S;
   __shared__ int outN[kRMax];
   __shared__ double bv_s[4][4][kRMax], z_s[4][4][kRMax], vt_s[4][4][kRMax];
+  __shared__ Real zr_s[4][4][kRMax];
   __shared__ double A_s[4][4][4];
   __shared__ int flag_s[4];
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
@@ -1584,6 +1601,7 @@ __global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const i
   const int r = qi.r, ks = qi.ks, nout = qi.r - qi.ks, T = a.T, NN = a.NN;
   load_entries(S, a, q, r);  // block-wide (contains a barrier)
   for (int i = tid; i < nout; i += blockDim.x) outN[i] = S.en[S.mp[ks + i]];
+  for (int p = tid; p < r * T; p += blockDim.x) alph_s[p] = (Real)a.alpha[(size_t)q * kRMax * T + p];
   __syncthreads();
   const int m = blockIdx.y * 4 + wp;
   if (m >= n_multi) return;  // warp-uniform; no block barrier follows
@@ -1596,7 +1614,6 @@ __global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const i
     return;
   }
   const double* Kinv = a.Kinv + (size_t)q * kRMax * kRMax;
-  const double* alpha = a.alpha + (size_t)q * kRMax * T;
   for (int p = lane; p < 4 * kRMax; p += 32) {  // Sigma^T Phi[:, o] - s_o and the Z row of member o
     const int a2 = p / kRMax, i = p % kRMax;
     double acc = 0.0, z = 0.0;
@@ -1611,6 +1628,7 @@ __global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const i
     }
     bv_s[wp][a2][i] = acc;
     z_s[wp][a2][i] = z;
+    zr_s[wp][a2][i] = (Real)z;  // the working-precision copy for the weights below
   }
   __syncwarp();
   Real* vt = mvt + qm * 4 * kRMax;
@@ -1659,8 +1677,9 @@ __global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const i
     for (int a2 = 0; a2 < 4; ++a2) {
       Real pf = (Real)0;
       if (a2 < n) {
-        pf = (Real)a.p0[(size_t)mN[e0 + a2] * T + t];
-        for (int j = 0; j < r; ++j) pf = fma(-(Real)z_s[wp][a2][j], (Real)alpha[j * T + t], pf);
+        if constexpr (sizeof(Real) == 4) pf = p0f[(size_t)mN[e0 + a2] * T + t];
+        else pf = a.p0[(size_t)mN[e0 + a2] * T + t];
+        for (int j = 0; j < r; ++j) pf = fma(-zr_s[wp][a2][j], alph_s[j * T + t], pf);
       }
       y[a2] = pf;
     }
@@ -1945,9 +1964,11 @@ void launch_gen(const Args& a, int RMAX, int G, const int* gen_bus, const double
 }
 
 template <class Real>
-void launch_multi_prep(const Args& a, int n_multi, const int* mptr, const int* mN, ChunkBufs& B, cudaStream_t st) {
-  k_multi_prep<Real><<<dim3(a.nq, (n_multi + 3) / 4), 128, 0, st>>>(a, n_multi, mptr, mN, B.mvt.as<Real>(),
-                                                                    B.mw.as<Real>(), B.mflag.as<int>());
+void launch_multi_prep(const Args& a, int n_multi, const int* mptr, const int* mN, ChunkBufs& B, const float* p0f,
+                       cudaStream_t st) {
+  const size_t dyn = (size_t)kRMax * a.T * sizeof(Real);
+  k_multi_prep<Real><<<dim3(a.nq, (n_multi + 3) / 4), 128, dyn, st>>>(a, n_multi, mptr, mN, B.mvt.as<Real>(),
+                                                                      B.mw.as<Real>(), B.mflag.as<int>(), p0f);
 }
 
 template <class Real>
@@ -2627,8 +2648,11 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     }
     if (want_multi) {  // the multi-outage small systems ride with the FP64 preparation
       const int pe = ctx->prof_begin(side);
-      if (fp64) launch_multi_prep<double>(ap, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(), B, side);
-      else launch_multi_prep<float>(ap, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(), B, side);
+      if (fp64)
+        launch_multi_prep<double>(ap, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(), B, nullptr, side);
+      else
+        launch_multi_prep<float>(ap, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multiN.as<int>(), B,
+                                 ctx->p0f.as<float>(), side);
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
       ctx->prof_end(pe, DCFLOW_PROF_MULTI_PREP, side);
