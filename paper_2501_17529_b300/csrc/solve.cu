@@ -594,18 +594,19 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
     for (int t = 0; t < TT; ++t)
       if (t0 + t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t0 + t) * C + a.cont_pos[c]] = ok ? (float)mx[t] : -1.f;
   }
-  __shared__ double rv[2], ro[2];
+  __shared__ Real rv[2];  // maxima compared in the working precision (no FP64-pipe work in the FP32 form)
+  __shared__ double ro[2];
   __shared__ int ra[2];
   const int lane = tid & 31, w = tid >> 5;
 #pragma unroll
   for (int t = 0; t < TT; ++t) {
     if (t0 + t < T) {  // uniform over the block
-      double v = ok ? (double)mx[t] : -1.0;
+      Real v = ok ? mx[t] : (Real)-1;
       int arg = ok ? c : 0x7fffffff;
       double o = ok ? (double)ov[t] * Acc<Real>::ovl_scale() : 0.0;
 #pragma unroll
       for (int off = 16; off; off >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+        const Real v2 = __shfl_xor_sync(0xffffffffu, v, off);
         const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
         o += __shfl_xor_sync(0xffffffffu, o, off);
         if (v2 > v || (v2 == v && a2 < arg)) {
@@ -620,15 +621,15 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
       }
       __syncthreads();
       if (tid == 0) {
-        double bv = rv[0];
+        Real bv = rv[0];
         int ba = ra[0];
         if (rv[1] > bv || (rv[1] == bv && ra[1] < ba)) {
           bv = rv[1];
           ba = ra[1];
         }
         const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + blockIdx.x;
-        static_cast<Real*>(a.pmax)[o2] = (Real)bv;
-        a.parg[o2] = (bv < 0.0) ? -1 : ba;
+        static_cast<Real*>(a.pmax)[o2] = bv;
+        a.parg[o2] = (bv < (Real)0) ? -1 : ba;
         a.povl[o2] = ro[0] + ro[1];
       }
       __syncthreads();
@@ -679,12 +680,13 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
   const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
   const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
   for (int t = tid >> 5; t < T; t += nw) {
-    double bv = -1.0, ovl = 0.0;
+    Real bv = (Real)-1;  // maxima compared in the working precision
+    double ovl = 0.0;
     int ba = 0x7fffffff;
     const int nb = nsel ? (nsel[q] + 63) / 64 : a.ncb;  // blocks of selected contingencies, or all
     for (int b = lane; b < nb; b += 32) {
       const size_t k = ((size_t)q * T + t) * a.ncb + b;
-      const double v = (double)static_cast<const Real*>(a.pmax)[k];
+      const Real v = static_cast<const Real*>(a.pmax)[k];
       const int ar = a.parg[k];
       if (ar >= 0 && (v > bv || (v == bv && ar < ba))) {
         bv = v;
@@ -693,7 +695,7 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       ovl += a.povl[k];
     }
     for (int off = 16; off; off >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, bv, off);
+      const Real v2 = __shfl_xor_sync(0xffffffffu, bv, off);
       const int a2 = __shfl_xor_sync(0xffffffffu, ba, off);
       ovl += __shfl_xor_sync(0xffffffffu, ovl, off);
       if (v2 > bv || (v2 == bv && a2 < ba)) {
@@ -704,13 +706,13 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
     const int c = (ba == 0x7fffffff) ? -1 : ba;
     if (lane == 0) {
       const size_t k = (size_t)tau * T + t;
-      o.n1_max_loading[k] = c >= 0 ? bv : 0.0;
+      o.n1_max_loading[k] = c >= 0 ? (double)bv : 0.0;
       o.overload_sum[k] = ovl;
       o.worst_cont[k] = c >= 0 ? a.cont_pos[c] : -1;  // the caller's position
       if (o.best_var) o.best_var[k] = a.best_u ? a.best_u[(size_t)q * T + t] : -1;
     }
     if (o.worst_mon) {
-      double v = -1.0;
+      Real v = (Real)-1;
       int arg = 0x7fffffff;
       if (c >= 0) {
         Real vr = (Real)-1;
@@ -729,10 +731,10 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
             arg = l;
           }
         }
-        v = (double)vr;
+        v = vr;
       }
       for (int off = 16; off; off >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+        const Real v2 = __shfl_xor_sync(0xffffffffu, v, off);
         const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
         if (v2 > v || (v2 == v && a2 < arg)) {
           v = v2;
@@ -928,22 +930,22 @@ __global__ void k_var_select(Args av, int T, int U, int* __restrict__ best_u) {
     return;
   }
   const int TV = T * U;
-  double bv = 1e300;
+  Real bv = (Real)1e30;  // compared in the working precision
   int bu = 0x7fffffff;
   for (int u = lane; u < U; u += 32) {
-    double v = -1.0;
+    Real v = (Real)-1;
     for (int b = 0; b < av.ncb; ++b) {
       const size_t k = ((size_t)q * TV + (size_t)t * U + u) * av.ncb + b;
-      if (av.parg[k] >= 0) v = fmax(v, (double)static_cast<const Real*>(av.pmax)[k]);
+      if (av.parg[k] >= 0) v = fmax(v, static_cast<const Real*>(av.pmax)[k]);
     }
-    if (v < 0.0) v = 0.0;  // no valid contingency: loading 0
+    if (v < (Real)0) v = (Real)0;  // no valid contingency: loading 0
     if (v < bv || (v == bv && u < bu)) {
       bv = v;
       bu = u;
     }
   }
   for (int off = 16; off; off >>= 1) {
-    const double v2 = __shfl_xor_sync(0xffffffffu, bv, off);
+    const Real v2 = __shfl_xor_sync(0xffffffffu, bv, off);
     const int u2 = __shfl_xor_sync(0xffffffffu, bu, off);
     if (v2 < bv || (v2 == bv && u2 < bu)) {
       bv = v2;
@@ -1178,7 +1180,8 @@ __global__ __launch_bounds__(64) void k_n1_sel(Args a, const Real* __restrict__ 
   __shared__ __align__(16) Real pt[LT][TT];
   __shared__ Real dg[LT], rm[LT];
   __shared__ int cp[LT];
-  __shared__ double rv[2], ro[2];
+  __shared__ Real rv[2];  // maxima compared in the working precision (no FP64-pipe work in the FP32 form)
+  __shared__ double ro[2];
   __shared__ int ra[2];
   const int total = *nwork;
   for (int wi = blockIdx.x; wi < total; wi += gridDim.x) {
@@ -1258,12 +1261,12 @@ __global__ __launch_bounds__(64) void k_n1_sel(Args a, const Real* __restrict__ 
 #pragma unroll
     for (int t = 0; t < TT; ++t) {
       if (t0 + t < T) {  // uniform over the block
-        double v = ok ? (double)mx[t] : -1.0;
+        Real v = ok ? mx[t] : (Real)-1;
         int arg = ok ? c : 0x7fffffff;
         double o = ok ? (double)ov[t] * Acc<Real>::ovl_scale() : 0.0;
 #pragma unroll
         for (int off = 16; off; off >>= 1) {
-          const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+          const Real v2 = __shfl_xor_sync(0xffffffffu, v, off);
           const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
           o += __shfl_xor_sync(0xffffffffu, o, off);
           if (v2 > v || (v2 == v && a2 < arg)) {
@@ -1278,15 +1281,15 @@ __global__ __launch_bounds__(64) void k_n1_sel(Args a, const Real* __restrict__ 
         }
         __syncthreads();
         if (tid == 0) {
-          double bv = rv[0];
+          Real bv = rv[0];
           int ba = ra[0];
           if (rv[1] > bv || (rv[1] == bv && ra[1] < ba)) {
             bv = rv[1];
             ba = ra[1];
           }
           const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + cb;
-          static_cast<Real*>(a.pmax)[o2] = (Real)bv;
-          a.parg[o2] = (bv < 0.0) ? -1 : ba;
+          static_cast<Real*>(a.pmax)[o2] = bv;
+          a.parg[o2] = (bv < (Real)0) ? -1 : ba;
           a.povl[o2] = ro[0] + ro[1];
         }
         __syncthreads();
@@ -1403,10 +1406,10 @@ __global__ __launch_bounds__(128) void k_topcases(Args a, const float* __restric
     }
 #pragma unroll
     for (int g = 0; g < KG; ++g) {
-      double v = (double)vr[g];
+      Real v = vr[g];  // compared in the working precision
       int ar = arg[g];
       for (int off2 = 16; off2; off2 >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, off2);
+        const Real v2 = __shfl_xor_sync(0xffffffffu, v, off2);
         const int a2 = __shfl_xor_sync(0xffffffffu, ar, off2);
         if (v2 > v || (v2 == v && a2 < ar)) {
           v = v2;
@@ -1456,7 +1459,8 @@ __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __rest
   __shared__ EntSmem S;
   __shared__ Real beta_s[64][RMAX];  // K^{-1} Sigma^T PTDF[:, bus_g], up to 64 generators per round
   __shared__ Real pg_s[TT][64];      // their outputs over this pass's timesteps
-  __shared__ double rv[4], ro[4];
+  __shared__ Real rv[4];  // maxima compared in the working precision
+  __shared__ double ro[4];
   __shared__ int ra[4];
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const QInfo qi = a.qi[q];
@@ -1531,10 +1535,11 @@ __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __rest
 #pragma unroll
   for (int j = 0; j < TT; ++j) {
     if (t0 + j >= T) break;  // uniform over the block
-    double v = (double)mx[j], s2 = (double)ov[j] * Acc<Real>::ovl_scale();
+    Real v = mx[j];
+    double s2 = (double)ov[j] * Acc<Real>::ovl_scale();
     int g = ag[j];
     for (int off = 16; off; off >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+      const Real v2 = __shfl_xor_sync(0xffffffffu, v, off);
       const int g2 = __shfl_xor_sync(0xffffffffu, g, off);
       s2 += __shfl_xor_sync(0xffffffffu, s2, off);
       if (v2 > v || (v2 == v && g2 < g)) {
@@ -1549,7 +1554,8 @@ __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __rest
     }
     __syncthreads();
     if (tid == 0) {
-      double bv = rv[0], bo = ro[0];
+      Real bv = rv[0];
+      double bo = ro[0];
       int bg = ra[0];
       for (int k = 1; k < 4; ++k) {
         bo += ro[k];
@@ -1559,7 +1565,7 @@ __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __rest
         }
       }
       const size_t k2 = (size_t)tau * T + t0 + j;
-      o.gen_max_loading[k2] = G ? bv : 0.0;
+      o.gen_max_loading[k2] = G ? (double)bv : 0.0;
       o.worst_gen[k2] = G ? bg : -1;
       o.gen_overload_sum[k2] = bo;
     }
@@ -1726,7 +1732,8 @@ __global__ __launch_bounds__(128) void k_multi_rows(Args a, int n_multi, const i
   __shared__ __align__(16) Real w_s[SG][TT][4];
   __shared__ int fl_s[SG], e0_s[SG], mp_s[SG][4];
   __shared__ int nisl_s;
-  __shared__ double rv_s[TT][4], ro_s[TT][4];
+  __shared__ Real rv_s[TT][4];  // maxima compared in the working precision
+  __shared__ double ro_s[TT][4];
   __shared__ int ra_s[TT][4];
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   const QInfo qi = a.qi[q];
@@ -1825,11 +1832,12 @@ __global__ __launch_bounds__(128) void k_multi_rows(Args a, int n_multi, const i
     }
 #pragma unroll
     for (int jt = 0; jt < TT; ++jt) {
-      double v = (double)mx[jt], s2 = (double)ov[jt] * Acc<Real>::ovl_scale();
+      Real v = mx[jt];
+      double s2 = (double)ov[jt] * Acc<Real>::ovl_scale();
       int g = ag[jt];
 #pragma unroll
       for (int off = 16; off; off >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, off);
+        const Real v2 = __shfl_xor_sync(0xffffffffu, v, off);
         const int g2 = __shfl_xor_sync(0xffffffffu, g, off);
         s2 += __shfl_xor_sync(0xffffffffu, s2, off);
         if (v2 > v || (v2 == v && g2 < g)) {
@@ -1845,7 +1853,8 @@ __global__ __launch_bounds__(128) void k_multi_rows(Args a, int n_multi, const i
     }
     __syncthreads();
     if (tid < TT && t0 + tid < T) {
-      double bv = rv_s[tid][0], bo = ro_s[tid][0];
+      Real bv = rv_s[tid][0];
+      double bo = ro_s[tid][0];
       int bg = ra_s[tid][0];
       for (int k = 1; k < 4; ++k) {
         bo += ro_s[tid][k];
@@ -1856,7 +1865,7 @@ __global__ __launch_bounds__(128) void k_multi_rows(Args a, int n_multi, const i
       }
       const size_t k2 = (size_t)tau * T + t0 + tid;
       const bool any = bg != 0x7fffffff;
-      o.multi_max_loading[k2] = any ? bv : 0.0;
+      o.multi_max_loading[k2] = any ? (double)bv : 0.0;
       o.worst_multi[k2] = any ? bg : -1;
       o.multi_overload_sum[k2] = bo;
     }
