@@ -1889,9 +1889,9 @@ struct Plan {
 
 int pick_tt(int T, bool fp64) {
   const int opts32[] = {1, 4, 8, 16, 24, 32};
-  const int opts64[] = {1, 4, 8, 12};
+  const int opts64[] = {1, 4, 8, 12, 24};
   const int* o = fp64 ? opts64 : opts32;
-  const int n = fp64 ? 4 : 6;
+  const int n = fp64 ? 5 : 6;
   for (int i = 0; i < n; ++i)
     if (T <= o[i]) return o[i];
   return o[n - 1];
@@ -1915,8 +1915,9 @@ int launch_n1_r(const Args& a, int TT, dim3 grid, cudaStream_t st, int t0) {
         else if (TT == 24) launch_n1_t<Real, 24, RMAX>(a, grid, st, t0);
         else launch_n1_t<Real, 32, RMAX>(a, grid, st, t0);
       } else {
-        if (TT != 12) return DCFLOW_ERR_INVALID_ARG;
-        launch_n1_t<Real, 12, RMAX>(a, grid, st, t0);
+        if (TT == 12) launch_n1_t<Real, 12, RMAX>(a, grid, st, t0);
+        else if (TT == 24) launch_n1_t<Real, 24, RMAX>(a, grid, st, t0);
+        else return DCFLOW_ERR_INVALID_ARG;
       }
   }
   return 0;
@@ -2180,8 +2181,9 @@ int launch_sel_r(const Args& a, const void* phicm, const ChunkBufs& B, int TT, i
         else if (TT == 24) launch_sel_t<Real, 24, RMAX>(a, phicm, B, grid, st, t0);
         else launch_sel_t<Real, 32, RMAX>(a, phicm, B, grid, st, t0);
       } else {
-        if (TT != 12) return DCFLOW_ERR_INVALID_ARG;
-        launch_sel_t<Real, 12, RMAX>(a, phicm, B, grid, st, t0);
+        if (TT == 12) launch_sel_t<Real, 12, RMAX>(a, phicm, B, grid, st, t0);
+        else if (TT == 24) launch_sel_t<Real, 24, RMAX>(a, phicm, B, grid, st, t0);
+        else return DCFLOW_ERR_INVALID_ARG;
       }
   }
   return 0;
