@@ -239,6 +239,49 @@ __device__ __forceinline__ double z_entry(const EntSmem& S, const double* PhiRow
   return z;
 }
 
+// Vt[j][c] = K^{-1} (Sigma^T Phi[:, c] - s_c) for the topology's R modifications (FP64), and
+// its working-precision copy; rows R .. RMAX - 1 are written as zeros
+template <class Real, int R, int RMAX>
+__device__ __forceinline__ void vt_cols(const EntSmem& S, const Args& a, int q, int ks,
+                                        const double (*Ki)[kRMax + 1]) {
+  const int C = a.C;
+  Real* VtR = static_cast<Real*>(a.VtR);
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    const int nc = a.contN[c];
+    double v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      double acc = 0.0;
+      for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
+        const int m = S.en[e];
+        acc = fma((double)S.es[e], a.PhiN[(size_t)m * a.NN + nc], acc);
+        if (i < ks && m == nc) acc -= (double)S.es[e];
+      }
+      v[i] = acc;
+    }
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) {
+      double x = 0.0;
+      if (j < R) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) x = fma(Ki[j][i], v[i], x);
+      }
+      const size_t o = ((size_t)q * kRMax + j) * C + c;
+      a.Vt64[o] = x;
+      VtR[o] = (Real)x;
+    }
+  }
+}
+
+template <class Real, int R, int RMAX>
+__device__ __forceinline__ void vt_rank(int r, const EntSmem& S, const Args& a, int q, int ks,
+                                        const double (*Ki)[kRMax + 1]) {
+  if constexpr (R <= RMAX) {
+    if (r == R) vt_cols<Real, R, RMAX>(S, a, q, ks, Ki);
+    else vt_rank<Real, R + 1, RMAX>(r, S, a, q, ks, Ki);
+  }
+}
+
 template <class Real, int RMAX>
 __global__ __launch_bounds__(128) void k_small(Args a) {
   const int q = blockIdx.x;
@@ -336,33 +379,9 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
       a.alpha[((size_t)q * kRMax + j) * T + t] = x;
     }
   }
-  // Vt[j][c]
-  const int C = a.C;
-  Real* VtR = static_cast<Real*>(a.VtR);
-  for (int c = tid; c < C; c += blockDim.x) {
-    const int nc = a.contN[c];
-    double v[RMAX];
-#pragma unroll
-    for (int i = 0; i < RMAX; ++i) {
-      double acc = 0.0;
-      if (i < r)
-        for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
-          const int m = S.en[e];
-          acc = fma((double)S.es[e], a.PhiN[(size_t)m * a.NN + nc], acc);
-          if (i < ks && m == nc) acc -= (double)S.es[e];
-        }
-      v[i] = acc;
-    }
-#pragma unroll
-    for (int j = 0; j < RMAX; ++j) {
-      double x = 0.0;
-#pragma unroll
-      for (int i = 0; i < RMAX; ++i) x = fma(Ki[j][i], v[i], x);  // Ki is zero outside r x r
-      const size_t o = ((size_t)q * kRMax + j) * C + c;
-      a.Vt64[o] = x;
-      VtR[o] = (Real)x;
-    }
-  }
+  // Vt[j][c] at the topology's exact rank (uniform over the block; the rank classes pad r
+  // up to RMAX, and the padded multiply-adds would be FP64 work), zero rows r .. RMAX - 1
+  vt_rank<Real, 1, RMAX>(r, S, a, q, ks, Ki);
 }
 
 // ---------------------------------------------------------------------------
