@@ -558,6 +558,12 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
   __shared__ Real pt[LT][TT];
   __shared__ Real dg[LT], rm[LT];
   __shared__ int cp[LT];
+  // FP64 form: the overload term only for the (contingency, timestep) items whose tile maximum
+  // exceeds 1, queued per warp and served by all its lanes (B300's FP64 pipe is the scarce unit)
+  constexpr bool kQ = sizeof(Real) == 8;
+  __shared__ Real ph_s[kQ ? LT : 1][64];
+  __shared__ Real ov_s[kQ ? TT : 1][64];
+  __shared__ uint16_t qu_s[kQ ? 2 : 1][kQ ? 32 * TT : 1];
   const int Mp = a.Mpad;
   const Real* PhiMC = static_cast<const Real*>(a.PhiMC);
   const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
@@ -574,6 +580,7 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
     s[t] = (cin && t0 + t < T) ? sv[(size_t)(t0 + t) * C + cc] : (Real)0;
     mx[t] = 0;
     ov[t] = 0;
+    if constexpr (kQ) ov_s[t][tid] = (Real)0;
   }
   for (int l0 = 0; l0 < M; l0 += LT) {
     __syncthreads();
@@ -599,12 +606,56 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
       const Real base = (l < M) ? PhiMC[(size_t)l * a.ldc + cc] : (Real)0;
       phi[i] = phi_entry<Real, RMAX>(base, zs[i], vt, rm[i], cp[i], c, dg[i]);
     }
+    if constexpr (kQ) {
 #pragma unroll
-    for (int t = 0; t < TT; ++t) {
-      const Real st = s[t];
+      for (int i = 0; i < LT; ++i) ph_s[i][tid] = phi[i];
+      const int lane = tid & 31, wq = tid >> 5;
+      const uint32_t lt = (1u << lane) - 1u;
+      int n = 0;
 #pragma unroll
-      for (int i = 0; i < LT; ++i) Acc<Real>::add(mx[t], ov[t], fma(phi[i], st, pt[i][t]));
+      for (int t = 0; t < TT; ++t) {
+        const Real st = s[t];
+        long long tb = 0;  // the tile's maximum |v| as bits (non-negative doubles order like their bits)
+#pragma unroll
+        for (int i = 0; i < LT; ++i) {
+          const long long b = __double_as_longlong(fma(phi[i], st, pt[i][t])) & 0x7fffffffffffffffll;
+          tb = b > tb ? b : tb;
+        }
+        mx[t] = tb > __double_as_longlong(mx[t]) ? __longlong_as_double(tb) : mx[t];
+        const bool hit = tb > 0x3ff0000000000000ll;  // some |v| > 1 in the tile
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        if (hit) qu_s[wq][n + __popc(m & lt)] = (uint16_t)((lane << 8) | t);
+        n += __popc(m);
+      }
+      if (n) {
+        __syncwarp();
+        for (int jq = lane; jq < n; jq += 32) {  // the 8 rows of one queued item, in row order
+          const int item = qu_s[wq][jq], src = (wq << 5) | (item >> 8), t = item & 255;
+          const int cs = blockIdx.x * 64 + src;
+          const Real st = (cs < C && t0 + t < T) ? sv[(size_t)(t0 + t) * C + cs] : (Real)0;
+          Real o = ov_s[t][src];
+#pragma unroll
+          for (int i = 0; i < LT; ++i) {
+            const double d = fabs(fma(ph_s[i][src], st, pt[i][t])) - 1.0;
+            o += __double_as_longlong(d) < 0 ? 0.0 : d;
+          }
+          ov_s[t][src] = o;
+        }
+        __syncwarp();
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < TT; ++t) {
+        const Real st = s[t];
+#pragma unroll
+        for (int i = 0; i < LT; ++i) Acc<Real>::add(mx[t], ov[t], fma(phi[i], st, pt[i][t]));
+      }
     }
+  }
+  if constexpr (kQ) {
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < TT; ++t) ov[t] = ov_s[t][tid];
   }
   // reduce the 64 contingencies of this block: max (ties: lowest c) and overload sum
   const bool ok = cin && a.valid[(size_t)q * C + c];
