@@ -545,6 +545,12 @@ __device__ __forceinline__ Real phi_entry(Real base, const Real* zrow, const Rea
   return (cp == c) ? dg : p;
 }
 
+// Fused N-1 (Def. 3, Eq. (5)) of one topology x 64 contingencies (one per
+// thread) x TT timesteps, LT monitored rows at a time staged in shared memory:
+// the FP64 form, and the FP32 form where the register-tiled kernel does not
+// apply.  Per (contingency, timestep) the maximum loading and the overload sum;
+// in FP64 the overload terms are computed only for the tiles whose maximum
+// exceeds 1 (queued per warp), in the same order as a per-entry sum.
 template <class Real, int TT, int RMAX, int LT>
 __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
   const int q = blockIdx.y;
