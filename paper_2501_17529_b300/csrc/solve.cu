@@ -545,12 +545,29 @@ __device__ __forceinline__ Real phi_entry(Real base, const Real* zrow, const Rea
   return (cp == c) ? dg : p;
 }
 
+// The same at the topology's exact rank r <= RMAX: the rank class pads Z and Vt
+// with zero rows, whose terms are exact zeros (at most the sign of a zero Phi_f
+// entry differs, which no |v| sees)
+template <class Real, int RMAX>
+__device__ __forceinline__ Real phi_entry_r(Real base, const Real* zrow, const Real* vt, Real rm, int cp, int c, Real dg,
+                                            int r) {
+  Real p = base;
+#pragma unroll
+  for (int j = 0; j < RMAX; ++j) {
+    if (j >= r) break;
+    p = fma(-zrow[j], vt[j], p);
+  }
+  p = p * rm;
+  return (cp == c) ? dg : p;
+}
+
 // Fused N-1 (Def. 3, Eq. (5)) of one topology x 64 contingencies (one per
 // thread) x TT timesteps, LT monitored rows at a time staged in shared memory:
 // the FP64 form, and the FP32 form where the register-tiled kernel does not
 // apply.  Per (contingency, timestep) the maximum loading and the overload sum;
 // in FP64 the overload terms are computed only for the tiles whose maximum
-// exceeds 1 (queued per warp), in the same order as a per-entry sum.
+// exceeds 1 (queued per warp), in the same order as a per-entry sum, and Phi_f
+// is built at the exact rank.
 template <class Real, int TT, int RMAX, int LT>
 __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
   const int q = blockIdx.y;
@@ -610,7 +627,8 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
     for (int i = 0; i < LT; ++i) {
       const int l = l0 + i;
       const Real base = (l < M) ? PhiMC[(size_t)l * a.ldc + cc] : (Real)0;
-      phi[i] = phi_entry<Real, RMAX>(base, zs[i], vt, rm[i], cp[i], c, dg[i]);
+      if constexpr (kQ) phi[i] = phi_entry_r<Real, RMAX>(base, zs[i], vt, rm[i], cp[i], c, dg[i], qi.r);
+      else phi[i] = phi_entry<Real, RMAX>(base, zs[i], vt, rm[i], cp[i], c, dg[i]);
     }
     if constexpr (kQ) {
 #pragma unroll
