@@ -330,6 +330,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
     peaks, peak_kind = _peaks()
     alu_peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # T issue slots/s, as the N-1 roofline
+    fp64_peak = 148 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # T DFMA lanes/s
     lib = __import__("paper_2501_17529_b300.dcflow", fromlist=["x"])
 
     def timed(solver, dbx, resx, steps, stream):
@@ -397,7 +398,7 @@ def run_ours(args):
             lf_all = lf
         results[form] = {"value": lf_all * steps / t_dev, "ms_per_step": 1e3 * t_dev / steps,
                          "loadflows_per_step": lf_all, "steps": steps, "launches": launches,
-                         "clocks": clk.summary(), "wall_s": wall, "kernel": kern}
+                         "clocks": clk.summary(), "wall_s": wall, "kernel": kern, "lf_rank": lf}
         # end to end through host buffers: H2D of the batch, solve, D2H of the results
         if form == "fp32" and not args.no_e2e:
             results[form]["e2e"] = _e2e(solver, w, lim, steps, args.warmup, lf)
@@ -483,6 +484,12 @@ def run_ours(args):
                         "timestep (value counts the single-branch N-1 cases only; multi_cases_per_step counts "
                         "the sets evaluated, sets a topology already lost counted too)"}
         results[form]["setup_s"] = setup_s
+        if form == "fp64" and kern["n1_ms"]:
+            # the FP64 N-1's floor: one DFMA per entry on the FP64 pipe, 2 lanes per clock per SM
+            # (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained = 2 per SM)
+            e64 = lf * n_mon * steps / (kern["n1_ms"] / 1e3) / 1e12  # this rank's entries over its kernel time
+            results[form]["kernels"] = {"name": "k_n1<double>", "ms_per_step": kern["n1_ms"] / steps,
+                                        "entries_per_s_T": e64, "fp64_peak_T": fp64_peak, "frac": e64 / fp64_peak}
         solver.close()
     if rank != 0:
         if ws > 1:
@@ -491,14 +498,23 @@ def run_ours(args):
         return
     head = results.get("fp32") or next(iter(results.values()))
     roof = None
-    if head.get("kernel"):
+    if "fp32" not in results and "fp64" in results and results["fp64"].get("kernels"):
+        k = results["fp64"]["kernels"]
+        roof = {"bound": "alu", "achieved": k["entries_per_s_T"], "peak": fp64_peak, "unit": "T N-1 entries/s",
+                "frac": k["frac"], "traffic": None, "traffic_note": "no capture for this kernel source and workload",
+                "kernel": "k_n1<double> (FP64 fused N-1)",
+                "peak_note": f"1 DFMA per entry at the {peak_kind} max SM clock "
+                             f"({peaks.get('sm_max_mhz', 2032.0):.0f} MHz), 148 SMs x 2 FP64 lanes",
+                "n1_ms_per_step": k["ms_per_step"],
+                "n1_share_of_step": k["ms_per_step"] / head["ms_per_step"]}
+    elif head.get("kernel"):
         k = head["kernel"]
         # Algorithmic work of the dominant kernel: one N-1 entry per solved
         # (topology, timestep, contingency) case and monitored branch.  Its
         # floor on the CUDA cores is one FP32 issue slot per entry (half a
         # packed FFMA2 for the flow, half a 3-input |max| for the reduction), so
         # the peak is 148 SMs x 128 lanes x the maximum SM clock.
-        entries = head["loadflows_per_step"] * n_mon * head["steps"]
+        entries = head["lf_rank"] * n_mon * head["steps"]  # rank 0's entries over rank 0's kernel time
         peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
         ach = entries / (k["n1_ms"] / 1e3) / 1e12
         key = (_src_hash(), "fp32" if not args.compact else "fp32_compact")
@@ -520,7 +536,7 @@ def run_ours(args):
             "config": dict(_config(w, desc, n_topo, T_STEPS, "flushed between steps (256 MB write)"),
                            ptdf_rows=int(need.sum())),
             "gpu_launches": head["launches"], "clocks": head["clocks"],
-            "forms": {f: {k: v for k, v in r.items() if k not in ("clocks", "kernel")} for f, r in results.items()}}
+            "forms": {f: {k: v for k, v in r.items() if k not in ("clocks", "kernel", "lf_rank")} for f, r in results.items()}}
     if "fp64" in results and "fp32" in results:
         line["forms"]["fp32_over_fp64_speedup"] = results["fp32"]["value"] / results["fp64"]["value"]
     if "e2e" in head:

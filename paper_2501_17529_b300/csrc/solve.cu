@@ -521,14 +521,14 @@ struct Acc<float> {
 
 template <>
 struct Acc<double> {
-  // |v|, the running maximum and max(|v| - 1, 0) through the bit patterns on the
-  // integer pipe (sign bit; non-negative doubles order like their bits): of the
+  // the running maximum through the bit patterns shifted past the sign on the
+  // integer pipe (magnitudes order like these unsigned integers; a masked sign
+  // bit would become a double fabs), max(|v| - 1, 0) by its sign bit: of the
   // FP64 pipe only the two additions remain (B300's FP64 rate is low)
   static __device__ __forceinline__ void add(double& mx, double& ov, double v) {
-    const long long b = __double_as_longlong(v) & 0x7fffffffffffffffll;
-    const double av = __longlong_as_double(b);
-    mx = b > __double_as_longlong(mx) ? av : mx;  // mx >= 0
-    const double d = av - 1.0;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) << 1;
+    if (b > ((unsigned long long)__double_as_longlong(mx) << 1)) mx = __longlong_as_double((long long)(b >> 1));
+    const double d = fabs(v) - 1.0;
     ov += __double_as_longlong(d) < 0 ? 0.0 : d;
   }
   static __device__ __forceinline__ double ovl_scale() { return 1.0; }
@@ -639,14 +639,16 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
 #pragma unroll
       for (int t = 0; t < TT; ++t) {
         const Real st = s[t];
-        long long tb = 0;  // the tile's maximum |v| as bits (non-negative doubles order like their bits)
+        // the tile's maximum |v| as bits shifted past the sign (magnitudes order like these
+        // unsigned integers); a masked sign bit would become a double fabs on the FP64 pipe
+        unsigned long long tb = 0;
 #pragma unroll
         for (int i = 0; i < LT; ++i) {
-          const long long b = __double_as_longlong(fma(phi[i], st, pt[i][t])) & 0x7fffffffffffffffll;
+          const unsigned long long b = (unsigned long long)__double_as_longlong(fma(phi[i], st, pt[i][t])) << 1;
           tb = b > tb ? b : tb;
         }
-        mx[t] = tb > __double_as_longlong(mx[t]) ? __longlong_as_double(tb) : mx[t];
-        const bool hit = tb > 0x3ff0000000000000ll;  // some |v| > 1 in the tile
+        if (tb > ((unsigned long long)__double_as_longlong(mx[t]) << 1)) mx[t] = __longlong_as_double((long long)(tb >> 1));
+        const bool hit = tb > (0x3ff0000000000000ull << 1);  // some |v| > 1 in the tile
         const uint32_t m = __ballot_sync(0xffffffffu, hit);
         if (hit) qu_s[wq][n + __popc(m & lt)] = (uint16_t)((lane << 8) | t);
         n += __popc(m);
