@@ -577,7 +577,9 @@ def _e2e(solver, w, lim, steps, warmup, lf):
             host_out[n].copy_(getattr(res, n), non_blocking=True)
         stream.synchronize()
 
-    for _ in range(warmup):
+    # untimed warm-up: the per-step time of this loop settles over about ten steps
+    # after the device-timed loop (11.6 -> 11.2 ms on the 500-bus study)
+    for _ in range(max(warmup, 10)):
         step()
     t0 = time.perf_counter()
     for _ in range(steps):

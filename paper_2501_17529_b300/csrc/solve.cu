@@ -1400,6 +1400,71 @@ __global__ __launch_bounds__(64) void k_n1_sel(Args a, const Real* __restrict__ 
 // N-1 cases by maximum loading, each with its most loaded monitored branch,
 // from the per-contingency maxima of the N-1 kernel (one warp per timestep)
 // ---------------------------------------------------------------------------
+// The top kk <= 32 of a warp's keys by (key descending, position ascending), as
+// warp_top_k selects them, when few keys reach the kk-th largest lane maximum:
+// the kk lanes with the largest maxima hold kk keys at least that large, so
+// every selected key is among those candidates, which are then ranked exactly.
+// Writes the selected positions (ascending) and their values to sp / sv and
+// returns false, having written nothing, when more than 64 candidates qualify.
+template <int NPL>
+__device__ __forceinline__ bool warp_top_few(const uint32_t (&key)[NPL], int kk, const float* row, uint32_t* ck,
+                                             int* cpos, int* sp, float* sv) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t lm = 0;
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) lm = key[i] > lm ? key[i] : lm;
+  int rk = 0;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t o = __shfl_sync(0xffffffffu, lm, j);
+    rk += (o > lm) || (o == lm && j < lane);
+  }
+  const uint32_t bk = __ballot_sync(0xffffffffu, rk == kk - 1);  // one lane: ranks are distinct
+  const uint32_t thr = __shfl_sync(0xffffffffu, lm, __ffs(bk) - 1);
+  int n = 0;
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {  // candidates in ascending position
+    const bool c = key[i] >= thr;
+    const uint32_t b = __ballot_sync(0xffffffffu, c);
+    const int j = n + __popc(b & lt);
+    if (c && j < 64) {
+      ck[j] = key[i];
+      cpos[j] = lane + 32 * i;
+    }
+    n += __popc(b);
+  }
+  if (n > 64) return false;
+  __syncwarp();
+  bool sel[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int j = lane + 32 * h;
+    int r = 0;
+    if (j < n) {
+      const uint32_t kj = ck[j];
+      for (int m = 0; m < n; ++m) r += ck[m] > kj || (ck[m] == kj && m < j);  // m < j: lower position
+    }
+    sel[h] = j < n && r < kk;
+  }
+  const uint32_t b0 = __ballot_sync(0xffffffffu, sel[0]), b1 = __ballot_sync(0xffffffffu, sel[1]);
+  int pos0 = 0, pos1 = 0;
+  if (sel[0]) pos0 = cpos[lane];
+  if (sel[1]) pos1 = cpos[lane + 32];
+  __syncwarp();
+  if (sel[0]) {
+    const int o = __popc(b0 & lt);
+    sp[o] = pos0;
+    sv[o] = row[pos0];
+  }
+  if (sel[1]) {
+    const int o = __popc(b0) + __popc(b1 & lt);
+    sp[o] = pos1;
+    sv[o] = row[pos1];
+  }
+  return true;
+}
+
 template <class Real, int RMAX, int NPL>
 __global__ __launch_bounds__(128) void k_topcases(Args a, const float* __restrict__ cmax,
                                                    const int* __restrict__ cont_inv, const Real* __restrict__ PhiCM,
@@ -1432,19 +1497,23 @@ __global__ __launch_bounds__(128) void k_topcases(Args a, const float* __restric
     key[i] = p < C ? float_key(row[p]) : 0u;
   }
   const int kk = k < C ? k : C;
-  bool sel[NPL];
-  uint32_t thr;
-  warp_top_k<NPL>(key, kk, sel, thr);
-  int off = 0;
+  __shared__ uint32_t ck_[4][64];
+  __shared__ int cq_[4][64];
+  if (kk < 1 || kk > 32 || !warp_top_few<NPL>(key, kk, row, ck_[w], cq_[w], sp_[w], sv_[w])) {  // warp-uniform
+    bool sel[NPL];
+    uint32_t thr;
+    warp_top_k<NPL>(key, kk, sel, thr);
+    int off = 0;
 #pragma unroll
-  for (int i = 0; i < NPL; ++i) {  // the selected cases in ascending position
-    const uint32_t b = __ballot_sync(0xffffffffu, sel[i]);
-    if (sel[i]) {
-      const int j = off + __popc(b & ((1u << lane) - 1u));
-      sp_[w][j] = lane + 32 * i;
-      sv_[w][j] = row[lane + 32 * i];
+    for (int i = 0; i < NPL; ++i) {  // the selected cases in ascending position
+      const uint32_t b = __ballot_sync(0xffffffffu, sel[i]);
+      if (sel[i]) {
+        const int j = off + __popc(b & ((1u << lane) - 1u));
+        sp_[w][j] = lane + 32 * i;
+        sv_[w][j] = row[lane + 32 * i];
+      }
+      off += __popc(b);
     }
-    off += __popc(b);
   }
   __syncwarp();
   for (int j = lane; j < kk; j += 32) {  // descending loading, ties to the lower position

@@ -325,6 +325,49 @@ def test_top_cases_match_oracle(precision):
                         assert col[l] >= col.max() - 2 * tol * max(1.0, col.max())
 
 
+def _top_k_of(cmax, k):
+    """Per (topology, timestep) the top k of the per-contingency maxima by
+    (value descending, position ascending); -1 / 0 where the value is below 0."""
+    n, T, C = cmax.shape
+    kk = min(k, C)
+    cont = np.full((n, T, k), -1, np.int64)
+    load = np.zeros((n, T, k), np.float32)
+    for i in range(n):
+        for t in range(T):
+            v = cmax[i, t]
+            order = np.lexsort((np.arange(C), -v.astype(np.float64)))[:kk]
+            ok = v[order] >= 0
+            cont[i, t, :kk] = np.where(ok, order, -1)
+            load[i, t, :kk] = np.where(ok, v[order], 0.0)
+    return cont, load
+
+
+@pytest.mark.parametrize("k,cset", [(1, "all"), (5, "all"), (32, "all"), (33, "all"), (64, "all"),
+                                    (8, "bridges+20"), (32, "bridges+20")])
+def test_top_cases_exact_selection(k, cset):
+    """The k worst cases are exactly the top k of the kernel's own per-contingency
+    maxima (ties to the lower position), for the small-k candidate select and the
+    radix select (k > 32, or more than 64 keys tied at the threshold)."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch
+    w = synth.workload(2, n_topo=24, T=3)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    if cset == "bridges+20":  # 100 bridges (maxima -1) first, then 20 ordinary branches
+        br = np.nonzero(oracle.bridges(w.grid.n_bus, w.grid.f, w.grid.t, np.ones(w.grid.n_branch, bool)))[0]
+        rest = np.setdiff1d(np.asarray(w.cont), br)[:20]
+        w.cont = np.concatenate([br[:100], rest]).astype(np.int32)
+    s = _solver(w, lim, "fp32")
+    res = s.solve(DeviceBatch(w.topo, w.inj), want_cont_max=True, top_k=k)
+    torch.cuda.synchronize()
+    g = res.to_host()
+    s.close()
+    cont, load = _top_k_of(g["cont_max"], k)
+    okq = g["status"] == 0
+    assert okq.any()
+    np.testing.assert_array_equal(g["top_cont"][okq], cont[okq])
+    np.testing.assert_array_equal(g["top_loading"][okq], load[okq])
+    assert (g["top_cont"][~okq] == -1).all()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("which", ["bridges_only", "empty"])
 def test_degenerate_contingency_sets(precision, which):
