@@ -168,6 +168,7 @@ struct EntSmem {
   double ewb[kEntMax];  // ew / b of the entry's branch
   float ewf[kEntMax], ewbf[kEntMax];  // the same in FP32 (no per-use conversion on the FP64 pipe)
   int8_t es[kEntMax];
+  double esd[kEntMax];  // es as double (int-to-double conversions run on the FP64 pipe: once per entry)
   int mp[kRMax + 1];
 };
 
@@ -182,6 +183,7 @@ __device__ void load_entries(EntSmem& S, const Args& a, int q, int r) {
     S.ewf[e] = (float)S.ew[e];
     S.ewbf[e] = (float)S.ewb[e];
     S.es[e] = a.ent_s[(size_t)q * kEntMax + e];
+    S.esd[e] = (double)S.es[e];
   }
   __syncthreads();
 }
@@ -254,8 +256,8 @@ __device__ __forceinline__ void vt_cols(const EntSmem& S, const Args& a, int q, 
       double acc = 0.0;
       for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
         const int m = S.en[e];
-        acc = fma((double)S.es[e], a.PhiN[(size_t)m * a.NN + nc], acc);
-        if (i < ks && m == nc) acc -= (double)S.es[e];
+        acc = fma(S.esd[e], a.PhiN[(size_t)m * a.NN + nc], acc);
+        if (i < ks && m == nc) acc -= S.esd[e];
       }
       v[i] = acc;
     }
@@ -268,7 +270,7 @@ __device__ __forceinline__ void vt_cols(const EntSmem& S, const Args& a, int q, 
       }
       const size_t o = ((size_t)q * kRMax + j) * C + c;
       a.Vt64[o] = x;
-      VtR[o] = (Real)x;
+      VtR[o] = (j < R) ? (Real)x : (Real)0;  // no conversion for the zero rows
     }
   }
 }
@@ -298,7 +300,7 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
     double acc = 0.0;
     for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
       const int m = S.en[e];
-      acc = fma((double)S.es[e], z_entry(S, a.PhiN + (size_t)m * a.NN, m, j), acc);
+      acc = fma(S.esd[e], z_entry(S, a.PhiN + (size_t)m * a.NN, m, j), acc);
     }
     K[i][j] = acc;
   }
@@ -368,7 +370,7 @@ __global__ __launch_bounds__(128) void k_small(Args a) {
     for (int i = 0; i < RMAX; ++i) {
       double acc = 0.0;
       if (i < r)
-        for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) acc = fma((double)S.es[e], a.p0[(size_t)S.en[e] * T + t], acc);
+        for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) acc = fma(S.esd[e], a.p0[(size_t)S.en[e] * T + t], acc);
       bv[i] = acc;
     }
 #pragma unroll
@@ -1661,7 +1663,7 @@ __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __rest
       double x = 0.0;
       for (int i = 0; i < r; ++i) {
         double sv = 0.0;
-        for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) sv = fma((double)S.es[e], PtdfN[(size_t)S.en[e] * V + b], sv);
+        for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) sv = fma(S.esd[e], PtdfN[(size_t)S.en[e] * V + b], sv);
         x = fma(Kinv[j * kRMax + i], sv, x);
       }
       beta_s[g][j] = (Real)x;
@@ -1792,8 +1794,8 @@ __global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const i
       const int oN = mN[e0 + a2];
       for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
         const int mm = S.en[e];
-        acc = fma((double)S.es[e], a.PhiN[(size_t)mm * NN + oN], acc);
-        if (i < ks && mm == oN) acc -= (double)S.es[e];
+        acc = fma(S.esd[e], a.PhiN[(size_t)mm * NN + oN], acc);
+        if (i < ks && mm == oN) acc -= S.esd[e];
       }
       z = z_entry_col(S, a.PhiN, NN, a.bN, oN, i);
     }
@@ -1836,11 +1838,17 @@ __global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const i
   }
   __syncwarp();
   if (flag_s[wp]) return;
+  __shared__ Real Lr_s[4][4][4];  // the LU factors in the working precision, converted once per warp
+  if (lane < 16) {
+    const int i = lane >> 2, k = lane & 3;
+    Lr_s[wp][i][k] = (i < n && k < n) ? (Real)A_s[wp][i][k] : (Real)(i == k);
+  }
+  __syncwarp();
   Real L[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) L[i][k] = (i < n && k < n) ? (Real)A_s[wp][i][k] : (Real)(i == k);
+    for (int k = 0; k < 4; ++k) L[i][k] = Lr_s[wp][i][k];
   Real* w = mw + qm * T * 4;
   for (int t = lane; t < T; t += 32) {  // p_f[O, t] as the row operands do, then the two triangular solves
     Real y[4];
