@@ -49,16 +49,6 @@ struct RegTile {
   static_assert(RB % 4 == 0, "build split");
 };
 
-// Selected-contingency mode: where the gathered Phi tile comes from.
-struct SelArgs {
-  const float* phicm;  // [C][mp] Phi[mon, cont] / limit transposed, zero rows mp > M
-  int mp;
-  const int* csel;     // [nq][C] selected internal contingencies, ascending
-  const int* nsel;     // [nq]
-  const int* work;     // [items] (topology << 6) | 64-contingency block, or null: block (cb, q) of the grid
-};
-constexpr int kPP = 20;  // pitch (floats) of a gathered Phi column: 16 rows + bank spread
-
 template <int TT, int RMAX, bool SEL = false>
 struct RegLayout {
   using R = RegTile<TT>;

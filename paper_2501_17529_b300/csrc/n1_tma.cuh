@@ -17,12 +17,11 @@
 
 #include <cuda.h>
 
+#include "n1_types.cuh"
+
 namespace dcf {
 
-constexpr int kLT = 16;     // monitored rows per tile
-constexpr int kCB = 64;     // contingencies per block
 constexpr int kStages = 3;  // TMA ring depth
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier wait
 
 template <int TT, int RMAX>
 struct TmaLayout {
@@ -92,9 +91,6 @@ __device__ __forceinline__ float max3abs(float a, float b, float c) {
   return r;
 }
 
-struct N1Maps {
-  CUtensorMap phi, zt, pt, meta;
-};
 
 // NTH threads per contingency, each owning TT / NTH timesteps; the block
 // builds each tile's Phi_f [16 rows x 64 contingencies] once into shared memory
