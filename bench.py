@@ -40,9 +40,9 @@ WORKLOADS = {
     "grid2000": (3, 1000, "grid2000_splits1-8_outages0-4_T8_cand256_mon3000_cont1000"),
     "grid10000": (4, 50000, "grid10000_splits1-6_T16_mon5000_cont2000"),
 }
-# dram bytes per launch of the dominant kernel from the ncu capture summarised in
-# profiles/k_n1_reg_grid500.md, keyed by the sha1 of the kernel's source and of
-# its argument block at the time of the capture
+# dram bytes per launch of the dominant kernel from an ncu capture of the
+# 500-bus study (its summary sits under profiles/), keyed by the sha1 of the
+# kernel's source and of its argument block at the time of the capture
 N1_TRAFFIC = {
     ("bc173a8d1288", "fp32"): {"bytes": 1.096e9, "per": "bench step of the 500-bus study (2 launches)",
                                "how": "1,000-topology capture (626 + 374 topologies) scaled by topologies "
@@ -588,6 +588,34 @@ def _e2e(solver, w, lim, steps, warmup, lf):
     return {"value": lf * steps / dt, "unit": "loadflows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
+def run_gemm(shapes):
+    """Time the screener's tensor-core GEMM (dcflow_gemm_bf16) on M x N x K shapes:
+    bf16 A [M, K] and B [N, K], D = A B^T in FP32, 3 warm-up calls, then 10
+    timed with CUDA events; one JSON line with ms and TF/s per shape."""
+    import torch
+    from paper_2501_17529_b300.csrc import build as cbuild
+    from paper_2501_17529_b300.dcflow import dcflow_gemm_bf16
+    cbuild.build()
+    out = {}
+    for sh in shapes:
+        M, N, K = (int(x) for x in sh.lower().split("x"))
+        A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda").to(torch.bfloat16)
+        D = torch.empty(M, N, device="cuda")
+        for _ in range(3):
+            dcflow_gemm_bf16(A, B, out=D)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            dcflow_gemm_bf16(A, B, out=D)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        out[sh] = {"ms": ms, "tflops": 2.0 * M * N * K / ms / 1e9}
+    print(json.dumps({"gemm_bf16": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -617,7 +645,12 @@ def main():
                     help="also time the FP32 solve with this many multi-outage sets; 0 = skip")
     ap.add_argument("--top-k", type=int, default=8,
                     help="also time the FP32 solve with the k worst N-1 cases per (topology, timestep); 0 = skip")
+    ap.add_argument("--gemm", default="",
+                    help="only time the screener's tensor-core GEMM on comma-separated MxNxK shapes")
     args = ap.parse_args()
+    if args.gemm:
+        run_gemm(args.gemm.split(","))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

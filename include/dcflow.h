@@ -129,6 +129,10 @@ int dcflow_base_ptdf_noalloc(dcflow_ctx* ctx, const int32_t* rows, int32_t n_row
  * rho = |flow| / limit.  split_bus: host int32[n_split_bus] substations that
  * batches may split (NULL = every bus); outage_cand: host
  * int32[n_outage_cand] branches batches may outage (NULL = every branch).
+ * Only the PTDF rows of monitored, contingency, split-bus and outage-candidate
+ * branches are built; a topology of a later batch that splits a bus outside
+ * split_bus or takes out a branch outside outage_cand is invalid
+ * (island_flag 2).
  * multi_ptr / multi_branch (optional, host): n_multi N-1 cases that take out
  * several branches at once (Def. 4, MODF; e.g. the windings of a
  * three-winding transformer), set m = multi_branch[multi_ptr[m] ..
@@ -160,7 +164,8 @@ int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* study);
  *                               substation (ascending branch id) to the new
  *                               busbar B; a mask with an empty side is a no-op
  *  out_ptr    int32[n_topo+1]   CSR offsets into out_branch
- *  out_branch int32[]           outaged branches (t_d), distinct per topology
+ *  out_branch int32[]           outaged branches (t_d), distinct per topology;
+ *                               each must be an outage candidate of the study
  *  inj        double[n_time * n_bus]  nodal injections per timestep; the slack
  *                               balances them (its PTDF column is zero)
  *  var_*      optional (n_var = 0 disables): candidate u adds

@@ -238,10 +238,16 @@ def incident_lists(n_bus, f, t):
 # topology construction (Sec. III-A: t_b, t_d)
 # ---------------------------------------------------------------------------
 
-def build_topology(n_bus, f, t, inc, splits, outages, max_mod=MAX_MODIFICATIONS):
+def build_topology(n_bus, f, t, inc, splits, outages, max_mod=MAX_MODIFICATIONS, split_bus=None,
+                   outage_cand=None):
     """Rebuild the branch endpoints of one topology.
 
     splits: list of (substation, mask); outages: list of branch ids.
+    split_bus / outage_cand: the study's switchable substations and the
+    branches it may take out (None: every bus / branch).  A topology that
+    splits another substation or outages another branch is not a topology of
+    the study: INVALID (the PTDF row restriction of Sec. II keeps only the
+    rows such a study needs).
     Returns (status, n_bus_new, f2, t2, alive, n_eff_splits)."""
     E = len(f)
     f2 = np.array(f, dtype=np.int64)
@@ -252,7 +258,7 @@ def build_topology(n_bus, f, t, inc, splits, outages, max_mod=MAX_MODIFICATIONS)
     for (A, mask) in splits:
         A = int(A)
         mask = int(mask)
-        if A < 0 or A >= n_bus or A in seen:
+        if A < 0 or A >= n_bus or A in seen or (split_bus is not None and A not in split_bus):
             return INVALID, n_bus, f2, t2, alive, 0
         seen.add(A)
         deg = len(inc[A])
@@ -272,7 +278,7 @@ def build_topology(n_bus, f, t, inc, splits, outages, max_mod=MAX_MODIFICATIONS)
     outs = set()
     for c in outages:
         c = int(c)
-        if c < 0 or c >= E or c in outs:
+        if c < 0 or c >= E or c in outs or (outage_cand is not None and c not in outage_cand):
             return INVALID, n_bus, f2, t2, alive, 0
         outs.add(c)
         alive[c] = False
@@ -349,8 +355,21 @@ def eligible_injections(inc, splits, inj_bus, cap=64):
     return el[:cap], buses
 
 
+def classify_contingencies(cont, alive, br):
+    """Which N-1 cases of one topology are solved (Def. 3 / Eq. (5) need
+    1 - Phi[c, c] != 0): a contingency branch in service that is not a bridge
+    of the topology is solved; one that is a bridge would island the grid and
+    is skipped and counted; an outaged branch is not a contingency of the
+    topology (skipped, not counted).  Returns (solved mask over cont, number
+    of islanding contingencies)."""
+    valid = np.array([bool(alive[c]) and not bool(br[c]) for c in cont], dtype=bool)
+    n_island = int(sum(1 for c in cont if alive[c] and br[c]))
+    return valid, n_island
+
+
 def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
-                      var=None, mode="lodf", want_flows=False, want_cmax=False, ti=None):
+                      var=None, mode="lodf", want_flows=False, want_cmax=False, ti=None,
+                      split_bus=None, outage_cand=None):
     """Outputs of one topology for every timestep (and variation).
 
     P: [T, V] injections.  var: (var_ptr, var_bus, var_delta) or None.
@@ -361,7 +380,8 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
     beyond the eligible injections makes the topology invalid.
     Returns a dict with per-timestep arrays: n0_max, n1_max, ovl, worst_cont,
     worst_mon, best_var, plus island status and n_island_cont (and n0 flows
-    of the monitored branches if want_flows)."""
+    of the monitored branches if want_flows).  split_bus / outage_cand: the
+    study's switchable substations and outage candidates (build_topology)."""
     V, f, t, b, slack = grid.n_bus, grid.f, grid.t, grid.b, grid.slack
     T = P.shape[0]
     M, C = len(mon), len(cont)
@@ -374,7 +394,8 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
     if want_cmax:
         res["cmax"] = -np.ones((T, C))  # per contingency: max_l rho (-1 if skipped)
         res["cargmax"] = -np.ones((T, C), np.int64)  # its monitored position (lowest on ties)
-    st, n, f2, t2, alive, k_eff = build_topology(V, f, t, inc, splits, outages)
+    st, n, f2, t2, alive, k_eff = build_topology(V, f, t, inc, splits, outages, split_bus=split_bus,
+                                                 outage_cand=outage_cand)
     if st != OK:
         res["status"] = st
         return res
@@ -391,8 +412,7 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
     mon = np.asarray(mon, np.int64)
     cont = np.asarray(cont, np.int64)
     lim_mon = np.asarray(limit, np.float64)[mon]
-    valid = np.array([alive[c] and not br[c] for c in cont], dtype=bool)
-    res["n_island_cont"] = int(sum(1 for c in cont if alive[c] and br[c]))
+    valid, res["n_island_cont"] = classify_contingencies(cont, alive, br)
     res["n_valid_cont"] = int(valid.sum())
     vj = np.nonzero(valid)[0]
     vc = cont[vj]
@@ -494,10 +514,14 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
 
 
 def evaluate(grid, topo, P, mon, cont, limit, var=None, mode="lodf", idx=None,
-             want_flows=False, want_cmax=False, ti=None):
+             want_flows=False, want_cmax=False, ti=None, split_bus=None, outage_cand=None):
     """Evaluate a batch of topologies (or the subset ``idx``); arrays per topology.
-    ti: injection topologies as (ti_ptr [n_topo + 1], ti_mask, inj_bus, inj_p [T, n_inj])."""
+    ti: injection topologies as (ti_ptr [n_topo + 1], ti_mask, inj_bus, inj_p [T, n_inj]).
+    split_bus / outage_cand: the study's switchable substations and outage
+    candidates (None: every bus / branch); a topology outside them is INVALID."""
     inc = incident_lists(grid.n_bus, grid.f, grid.t)
+    sb = None if split_bus is None else {int(x) for x in split_bus}
+    oc = None if outage_cand is None else {int(x) for x in outage_cand}
     P = np.atleast_2d(np.asarray(P, np.float64))
     ids = range(topo.n_topo) if idx is None else [int(i) for i in idx]
     vtuple = None
@@ -514,7 +538,7 @@ def evaluate(grid, topo, P, mon, cont, limit, var=None, mode="lodf", idx=None,
             tp, tm, ib, ip = ti
             tti = ([int(x) for x in tm[tp[i]:tp[i + 1]]], ib, ip)
         outs.append(evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
-                                      vtuple, mode, want_flows, want_cmax, tti))
+                                      vtuple, mode, want_flows, want_cmax, tti, sb, oc))
     keys = ["n0_max", "n1_max", "ovl", "worst_cont", "worst_mon", "best_var"]
     r = {k: np.stack([o[k] for o in outs]) if outs else np.zeros((0, P.shape[0])) for k in keys}
     r["status"] = np.array([o["status"] for o in outs], np.int64)
@@ -577,7 +601,11 @@ def thermal_limits(grid, P, factor=1.2, offset=0.1):
 
 
 def loadflow_count(res, n_timesteps, n_var=0):
-    """N-1 cases actually solved: valid contingencies of non-islanded topologies x T x U."""
+    """The throughput metric's numerator (the loadflow arithmetic under the
+    benchmark table of Sec. IV: topologies x |T_i| x N-1 cases): the N-1 cases
+    actually solved, i.e. the solved contingencies (classify_contingencies) of
+    the topologies that neither island nor are invalid, times the timesteps,
+    times the injection candidates when there are any."""
     ok = res["status"] == OK
     return int(res["n_valid_cont"][ok].sum()) * n_timesteps * max(1, n_var)
 

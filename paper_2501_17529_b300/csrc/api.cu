@@ -35,7 +35,7 @@ void DevBuf::release() {
 extern "C" void dcflow_destroy(dcflow_ctx* ctx) {
   if (!ctx) return;
   dcf::DevBuf* bufs[] = {&ctx->f, &ctx->t, &ctx->b, &ctx->inc_ptr, &ctx->inc_list, &ctx->rid, &ctx->L, &ctx->info,
-                         &ctx->nidx, &ctx->split_ok, &ctx->monN, &ctx->contN, &ctx->cpos_of_mon, &ctx->mpos_of_cont,
+                         &ctx->nidx, &ctx->split_ok, &ctx->out_ok, &ctx->monN, &ctx->contN, &ctx->cpos_of_mon, &ctx->mpos_of_cont,
                          &ctx->inv_lim, &ctx->bN, &ctx->PhiN, &ctx->PhiNf, &ctx->bNf, &ctx->p0f, &ctx->PtdfN, &ctx->PhiMC, &ctx->Y, &ctx->p0, &ctx->dp,
                          &ctx->rank, &ctx->status, &ctx->perm, &ctx->hist, &ctx->hist_host, &ctx->err, &ctx->pool, &ctx->var_k, &ctx->PhiCM, &ctx->cont_pos, &ctx->cont_inv,
                          &ctx->cm_scratch, &ctx->gen_cols,

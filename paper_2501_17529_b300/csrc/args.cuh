@@ -17,7 +17,8 @@ struct GridDev {
   const int *f, *t;
   const double* b;
   const int *inc_ptr, *inc_list, *nidx;
-  const uint8_t* split_ok;
+  const uint8_t* split_ok;  // [V] substations the study may split
+  const uint8_t* out_ok;    // [E] branches the study may take out (outage candidates)
   int V, E;
 };
 

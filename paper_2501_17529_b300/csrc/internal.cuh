@@ -94,6 +94,22 @@ inline cudaError_t smem_attr_once(K kernel, int bytes, uint64_t& done) {
   return e;
 }
 
+// Makes `dev` the current device for the lifetime of the guard and puts the
+// caller's device back afterwards: an entry point runs on its context's
+// device whichever device the calling thread has current.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    else prev = -1;  // nothing to restore
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 }  // namespace dcf
 
 struct dcflow_ctx {
@@ -112,6 +128,7 @@ struct dcflow_ctx {
   std::vector<int> h_mon, h_cont, h_N, h_nidx;
   dcf::DevBuf nidx;        // int[E]: branch -> needed-row index or -1
   dcf::DevBuf split_ok;    // uint8[V]
+  dcf::DevBuf out_ok;      // uint8[E]: outage candidates of the study
   dcf::DevBuf monN, contN; // int[M], int[C]: needed-row index of mon / cont
   dcf::DevBuf cpos_of_mon; // int[M]: position in cont of the same branch or -1
   dcf::DevBuf mpos_of_cont;// int[C]: position in mon of the same branch or -1

@@ -57,7 +57,9 @@ __global__ void k_noalloc_rows(int nr, int V, const int* rows, const double* b, 
   }
 }
 
-// Device address of g_noalloc_scratch per device, looked up once per device.
+// Device address of g_noalloc_scratch per device, looked up once per device
+// with that device current (the entry point switches to its context's device
+// before asking).
 static std::mutex g_mu;
 static void* g_addr[128];
 static bool g_have[128];
@@ -113,6 +115,12 @@ extern "C" int dcflow_base_ptdf_noalloc(dcflow_ctx* ctx, const int32_t* rows, in
     set_error("dcflow_base_ptdf_noalloc: needs " + std::to_string(need) + " bytes of scratch, the fixed array holds " +
               std::to_string(kScratchBytes) + " (fewer rows per call, or dcflow_base_ptdf)");
     return DCFLOW_ERR_INVALID_ARG;
+  }
+  // the context's device, whichever device the caller has current (restored on return)
+  DeviceGuard dg(ctx->dev);
+  if (dg.err != cudaSuccess) {
+    set_error(std::string("dcflow_base_ptdf_noalloc: cudaSetDevice: ") + cudaGetErrorString(dg.err));
+    return DCFLOW_ERR_CUDA;
   }
   void* base = nullptr;
   int rc = scratch_address(&base);

@@ -262,6 +262,11 @@ extern "C" int dcflow_base_ptdf(dcflow_ctx* ctx, const int32_t* rows, int32_t n_
       set_error("dcflow_base_ptdf: row out of range");
       return DCFLOW_ERR_INVALID_ARG;
     }
+  DeviceGuard dg(ctx->dev);  // the context's device for this call
+  if (dg.err != cudaSuccess) {
+    set_error(std::string("dcflow_base_ptdf: cudaSetDevice: ") + cudaGetErrorString(dg.err));
+    return DCFLOW_ERR_CUDA;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf d_rows;
   int rc = 0;
@@ -341,6 +346,11 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
     set_error("dcflow_set_study: invalid arguments");
     return DCFLOW_ERR_INVALID_ARG;
   }
+  DeviceGuard dg(ctx->dev);  // the context's device for this call
+  if (dg.err != cudaSuccess) {
+    set_error(std::string("dcflow_set_study: cudaSetDevice: ") + cudaGetErrorString(dg.err));
+    return DCFLOW_ERR_CUDA;
+  }
   const int E = ctx->E, V = ctx->V;
   std::vector<char> is_mon(E, 0), is_cont(E, 0), need(E, 0);
   for (int i = 0; i < s->n_mon; ++i) {
@@ -377,6 +387,7 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
   for (int v = 0; v < V; ++v)
     if (split_ok[v])
       for (int k = ctx->h_inc_ptr[v]; k < ctx->h_inc_ptr[v + 1]; ++k) need[ctx->h_inc_list[k]] = 1;
+  std::vector<uint8_t> out_ok(E, 0);  // branches a batch may take out
   if (s->outage_cand) {
     for (int i = 0; i < s->n_outage_cand; ++i) {
       int l = s->outage_cand[i];
@@ -385,9 +396,11 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
         return DCFLOW_ERR_INVALID_ARG;
       }
       need[l] = 1;
+      out_ok[l] = 1;
     }
   } else {
     std::fill(need.begin(), need.end(), 1);
+    std::fill(out_ok.begin(), out_ok.end(), 1);
   }
   const int n_multi = s->n_multi > 0 ? s->n_multi : 0;
   std::vector<int> mptr(1, 0), mbr;
@@ -463,6 +476,7 @@ extern "C" int dcflow_set_study(dcflow_ctx* ctx, const dcflow_study* s) {
   int rc;
   if ((rc = upload(ctx->nidx, ctx->h_nidx.data(), sizeof(int) * E))) return rc;
   if ((rc = upload(ctx->split_ok, split_ok.data(), V))) return rc;
+  if ((rc = upload(ctx->out_ok, out_ok.data(), E))) return rc;
   if ((rc = upload(ctx->monN, monN.data(), sizeof(int) * M))) return rc;
   if ((rc = upload(ctx->contN, contN.data(), sizeof(int) * contN.size()))) return rc;
   if ((rc = upload(ctx->cpos_of_mon, cpos.data(), sizeof(int) * M))) return rc;

@@ -81,7 +81,7 @@ __device__ int decode_topology(const GridDev& g, const BatchDev& in, int tau, in
   const int ks = r;
   for (int k = o0; k < o1; ++k) {
     const int c = in.out_branch[k];
-    if (c < 0 || c >= g.E || g.nidx[c] < 0) return ST_INVALID;
+    if (c < 0 || c >= g.E || !g.out_ok[c] || g.nidx[c] < 0) return ST_INVALID;
     for (int k2 = o0; k2 < k; ++k2)
       if (in.out_branch[k2] == c) return ST_INVALID;
     if (r >= kRMax || ne >= kEntMax) return ST_INVALID;
@@ -2274,6 +2274,11 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     set_error("dcflow_solve_batch: no study bound (dcflow_set_study)");
     return DCFLOW_ERR_NO_STUDY;
   }
+  DeviceGuard dg(ctx->dev);  // the context's device for this call
+  if (dg.err != cudaSuccess) {
+    set_error(std::string("dcflow_solve_batch: cudaSetDevice: ") + cudaGetErrorString(dg.err));
+    return DCFLOW_ERR_CUDA;
+  }
   const int N = bt->n_topo, T = bt->n_time;
   if (N < 0 || T < 1 || T > 256 || bt->n_var < 0) {
     set_error("dcflow_solve_batch: need n_topo >= 0, 1 <= n_time <= 256, n_var >= 0");
@@ -2414,7 +2419,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   ++ctx->launches;
   DCF_CHECK_LAUNCH();
   GridDev g{ctx->f.as<int>(), ctx->t.as<int>(), ctx->b.as<double>(), ctx->inc_ptr.as<int>(), ctx->inc_list.as<int>(),
-            ctx->nidx.as<int>(), ctx->split_ok.as<uint8_t>(), ctx->V, ctx->E};
+            ctx->nidx.as<int>(), ctx->split_ok.as<uint8_t>(), ctx->out_ok.as<uint8_t>(), ctx->V, ctx->E};
   BatchDev in{bt->split_ptr, bt->split_sub, bt->split_mask, bt->out_ptr, bt->out_branch};
   // rank of every topology -> group by rank class (no dummy padding of uneven k)
   if (ctx->rank.ensure(N)) return DCFLOW_ERR_OOM;

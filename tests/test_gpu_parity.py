@@ -20,16 +20,17 @@ def _cuda():
     build.build()
 
 
-def _solver(w, lim, precision, chunk=0, split_bus="subs"):
+def _solver(w, lim, precision, chunk=0, split_bus="subs", outage_cand=None):
     from paper_2501_17529_b300.dcflow import Solver
     s = Solver(w.grid, precision=precision, chunk_topo=chunk)
-    s.set_study(w.mon, w.cont, lim, split_bus=(w.subs if split_bus == "subs" else split_bus))
+    s.set_study(w.mon, w.cont, lim, split_bus=(w.subs if split_bus == "subs" else split_bus),
+                outage_cand=outage_cand)
     return s
 
 
-def _gpu(w, lim, precision, topo=None, chunk=0, want_flows=True):
+def _gpu(w, lim, precision, topo=None, chunk=0, want_flows=True, outage_cand=None):
     from paper_2501_17529_b300.dcflow import DeviceBatch
-    s = _solver(w, lim, precision, chunk)
+    s = _solver(w, lim, precision, chunk, outage_cand=outage_cand)
     topo = w.topo if topo is None else topo
     res = s.solve(DeviceBatch(topo, w.inj), want_flows=want_flows, want_cont_max=want_flows)
     torch.cuda.synchronize()
@@ -78,6 +79,57 @@ def test_grid500_sample(precision):
     w = synth.workload(2, n_topo=48)
     lim = oracle.thermal_limits(w.grid, w.inj)
     compare(_gpu(w, lim, precision), _ref(w, lim), w, w.topo, lim, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_grid500_row_restricted_study(precision):
+    """The benchmark's study: only the rows of the monitored, contingency,
+    split-bus and outage-candidate branches, the candidates being exactly the
+    batch's outaged branches (PTDF row restriction of Sec. II).  48 topologies
+    of the 500-bus study against the oracle, plus the loadflow count the
+    benchmark reports from these outputs against the oracle's count."""
+    import bench
+    w = synth.workload(2, n_topo=48)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    ocand = np.unique(np.asarray(w.topo.out_branch, np.int32))
+    ref = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, want_flows=True, want_cmax=True,
+                          split_bus=w.subs, outage_cand=ocand)
+    gpu = _gpu(w, lim, precision, outage_cand=ocand)
+    compare(gpu, ref, w, w.topo, lim, TOL[precision])
+    T = w.inj.shape[0]
+    assert bench._loadflows(w.topo, gpu["status"], gpu["n_island_cont"], w.cont, T) == oracle.loadflow_count(ref, T)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_switching_outside_the_study_is_invalid(precision):
+    """A topology that takes out a branch outside the study's outage candidates,
+    or splits a substation outside its split buses, is invalid (flag 2) on both
+    sides; the rest of the batch is unaffected."""
+    w = synth.workload(2, n_topo=12)
+    g = w.grid
+    lim = oracle.thermal_limits(g, w.inj[:4])
+    w.inj = w.inj[:4]
+    ocand = np.unique(np.asarray(w.topo.out_branch, np.int32))
+    other = int(np.setdiff1d(np.arange(g.n_branch), ocand)[0])
+    not_split = int(np.setdiff1d(np.arange(g.n_bus), w.subs)[0])
+    sp = list(w.topo.split_ptr)
+    ss, sm = list(w.topo.split_sub), list(w.topo.split_mask)
+    op, ob = list(w.topo.out_ptr), list(w.topo.out_branch)
+    # topology 12: one outage outside the candidates; topology 13: a split outside the split buses
+    ob.append(other)
+    op.append(len(ob))
+    sp.append(len(ss))
+    ss.append(not_split)
+    sm.append(1)
+    sp.append(len(ss))
+    op.append(len(ob))
+    topo = synth.Topologies(np.array(sp, np.int32), np.array(ss, np.int32), np.array(sm, np.uint64),
+                            np.array(op, np.int32), np.array(ob, np.int32))
+    ref = oracle.evaluate(g, topo, w.inj, w.mon, w.cont, lim, want_flows=True, want_cmax=True,
+                          split_bus=w.subs, outage_cand=ocand)
+    assert ref["status"][12] == oracle.INVALID and ref["status"][13] == oracle.INVALID
+    gpu = _gpu(w, lim, precision, topo=topo, outage_cand=ocand)
+    compare(gpu, ref, w, topo, lim, TOL[precision])
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

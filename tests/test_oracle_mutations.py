@@ -262,3 +262,39 @@ def _eligible_off_slack(inc, splits, inj_bus, cap=64):
 def test_injection_topology_mutation_is_caught(monkeypatch, mut):
     monkeypatch.setattr(ref, "eligible_injections", mut)
     assert _fails(pins.test_injection_topology_flows_match_the_split_grid_by_hand)
+
+
+_orig_classify = ref.classify_contingencies
+_orig_count = ref.loadflow_count
+
+
+def _classify_bridges_solved(cont, alive, br):
+    valid = np.array([bool(alive[c]) for c in cont], dtype=bool)  # planted: bridges counted as solved
+    return valid, 0
+
+
+def _classify_outaged_as_island(cont, alive, br):
+    valid, _ = _orig_classify(cont, alive, br)
+    return valid, int(sum(1 for c in cont if (not alive[c]) or br[c]))  # planted: outaged counted as islanding
+
+
+def _count_without_candidate_guard(res, n_timesteps, n_var=0):
+    ok = res["status"] == ref.OK
+    return int(res["n_valid_cont"][ok].sum()) * n_timesteps * n_var  # planted: max(1, U) dropped
+
+
+def _count_nominal(res, n_timesteps, n_var=0):
+    n = len(res["status"]) * int((res["n_valid_cont"] + res["n_island_cont"]).max())
+    return n * n_timesteps * max(1, n_var)  # planted: nominal cases, skipped ones included
+
+
+@pytest.mark.parametrize("attr,fake", [
+    ("classify_contingencies", _classify_bridges_solved),
+    ("classify_contingencies", _classify_outaged_as_island),
+    ("loadflow_count", _count_without_candidate_guard),
+    ("loadflow_count", _count_nominal),
+], ids=["bridges_solved", "outaged_as_island", "no_candidate_guard", "nominal_count"])
+def test_loadflow_count_mutation_is_caught(monkeypatch, golden_dir, attr, fake):
+    monkeypatch.setattr(ref, attr, fake)
+    monkeypatch.setattr(oracle, attr, fake, raising=False)
+    assert _fails(pins.test_loadflow_count_hand_counted, golden_dir)

@@ -701,3 +701,68 @@ def test_injection_topology_argmin_and_invalid_lists():
     r2 = oracle.evaluate(w.grid, w.topo, w.inj, mon, w.cont, lim, ti=(tp, tm, ti.inj_bus, ti.inj_p))
     assert r2["status"][0] == 2 and r2["status"][1] == 2
     assert (r2["status"][2:] == r["status"][2:]).all()
+
+
+# --------------------------------------------------------------------------
+# the metric's numerator: N-1 cases actually solved (hand count)
+# --------------------------------------------------------------------------
+
+def _count_case(golden_dir):
+    d = json.load(open(os.path.join(golden_dir, "loadflow_count.json")))
+    g = synth.Grid(d["n_bus"], np.array(d["from"], np.int32), np.array(d["to"], np.int32),
+                   np.full(len(d["from"]), 10.0), d["slack"])
+    sp, ss, sm, op, ob = [0], [], [], [0], []
+    for tp in d["topologies"]:
+        for A, m in tp["splits"]:
+            ss.append(A)
+            sm.append(m)
+        sp.append(len(ss))
+        ob.extend(tp["outages"])
+        op.append(len(ob))
+    topo = synth.Topologies(np.array(sp, np.int32), np.array(ss, np.int32), np.array(sm, np.uint64),
+                            np.array(op, np.int32), np.array(ob, np.int32))
+    rng = np.random.default_rng(5)
+    P = rng.normal(size=(d["timesteps"], d["n_bus"]))
+    P -= P.mean(axis=1, keepdims=True)
+    return d, g, topo, P
+
+
+def test_loadflow_count_hand_counted(golden_dir):
+    """Solved N-1 cases per topology and the metric's numerator against a hand
+    count: outaged contingencies are not counted, bridges are counted as
+    islanding only, islanded topologies contribute nothing, and the count
+    multiplies by the timesteps and by the candidates when there are any."""
+    d, g, topo, P = _count_case(golden_dir)
+    assert oracle.incident_lists(g.n_bus, g.f, g.t) == d["incident_lists"]
+    E = g.n_branch
+    cont = np.arange(E, dtype=np.int32)
+    r = oracle.evaluate(g, topo, P, cont, cont, np.ones(E))
+    np.testing.assert_array_equal(r["status"], [x["status"] for x in d["topologies"]])
+    np.testing.assert_array_equal(r["n_island_cont"], [x["n_island_cont"] for x in d["topologies"]])
+    np.testing.assert_array_equal(r["n_valid_cont"], [x["n_valid_cont"] for x in d["topologies"]])
+    assert oracle.loadflow_count(r, d["timesteps"]) == d["loadflows_all_contingencies"]
+    assert oracle.loadflow_count(r, d["timesteps"], d["candidates"]) == \
+        d["loadflows_all_contingencies_with_candidates"]
+    rc = np.array(d["restricted_cont"], np.int32)
+    r2 = oracle.evaluate(g, topo, P, cont, rc, np.ones(E))
+    np.testing.assert_array_equal(r2["n_island_cont"], d["restricted_n_island_cont"])
+    np.testing.assert_array_equal(r2["n_valid_cont"], d["restricted_n_valid_cont"])
+    assert oracle.loadflow_count(r2, d["timesteps"]) == d["loadflows_restricted"]
+
+
+def test_study_switching_sets_make_other_topologies_invalid(golden_dir):
+    """A study names the substations its batches may split and the branches
+    they may take out (PTDF row restriction of Sec. II); a topology that
+    switches anything else is invalid (status 2), the others are unchanged."""
+    d, g, topo, P = _count_case(golden_dir)
+    E = g.n_branch
+    cont = np.arange(E, dtype=np.int32)
+    full = oracle.evaluate(g, topo, P, cont, cont, np.ones(E))
+    r = oracle.evaluate(g, topo, P, cont, cont, np.ones(E), split_bus=[0, 3], outage_cand=[1, 4, 5])
+    # topology 3 splits bus 2, topology 5 outages branch 3: not switchable in this study
+    want = np.array(full["status"])
+    want[[3, 5]] = oracle.INVALID
+    np.testing.assert_array_equal(r["status"], want)
+    same = want != oracle.INVALID
+    np.testing.assert_array_equal(r["n_valid_cont"][same], full["n_valid_cont"][same])
+    np.testing.assert_array_equal(r["n1_max"][same], full["n1_max"][same])

@@ -1,4 +1,4 @@
-"""The allocation-free base-PTDF entry point matches dcflow_base_ptdf.
+"""The allocation-free base-PTDF entry point matches dcflow_base_ptdf and the oracle.
 
 dcflow_base_ptdf_noalloc serves callers that cannot allocate device memory
 (an arena they do not own, allocator-free real-time loops): its workspace is a
@@ -8,6 +8,7 @@ stopping at the first failure has run every other test before it.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2501_17529_b300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -23,6 +24,8 @@ def test_noalloc_matches_base_ptdf_twice():
     from paper_2501_17529_b300 import dcflow
 
     g = synth.make_grid(300, 420, 61)
+    # the base PTDF by its definition (Def. 2 / Eq. (1)), FP64 on the CPU
+    pt_ref = oracle.ptdf(g.n_bus, g.f, g.t, g.b, g.slack)
     ctx = dcflow.dcflow_setup(g.n_bus, g.f, g.t, g.b, g.slack, precision="fp64")
     try:
         # two calls in a row with different row sets: the second must not see the first's contents
@@ -35,6 +38,8 @@ def test_noalloc_matches_base_ptdf_twice():
             err = (got - ref).abs().max().item()
             assert err <= 1e-12, err
             assert torch.all(got[:, g.slack] == 0)
+            err_o = np.abs(got.cpu().numpy() - pt_ref[rows]).max()
+            assert err_o <= 1e-11 * max(1.0, np.abs(pt_ref).max()), err_o
         # a request larger than the fixed workspace is refused, not attempted
         big = np.arange(420, dtype=np.int32).repeat(40)
         out = torch.empty((big.size, g.n_bus), dtype=torch.float64, device="cuda")
