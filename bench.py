@@ -364,7 +364,7 @@ def run_ours(args):
         db = DeviceBatch(w.topo, w.inj, w.var)
         res = DeviceResults(db.n_topo, db.n_time, len(w.mon), want_var=db.n_var > 0)
         stream = torch.cuda.current_stream()
-        steps = args.steps if form == "fp32" else max(1, min(args.steps, args.fp64_steps))
+        steps = args.steps if form != "fp64" or args.fp64_steps <= 0 else max(1, min(args.steps, args.fp64_steps))
         for _ in range(args.warmup):
             solver.solve(db, results=res)
         torch.cuda.synchronize()
@@ -398,7 +398,8 @@ def run_ours(args):
             lf_all = lf
         results[form] = {"value": lf_all * steps / t_dev, "ms_per_step": 1e3 * t_dev / steps,
                          "loadflows_per_step": lf_all, "steps": steps, "launches": launches,
-                         "clocks": clk.summary(), "wall_s": wall, "kernel": kern, "lf_rank": lf}
+                         "clocks": clk.summary(), "wall_s": wall, "kernel": kern, "lf_rank": lf,
+                         "n1_ms_per_step": kern["n1_ms"] / steps if kern["n1_ms"] else None}
         # end to end through host buffers: H2D of the batch, solve, D2H of the results
         if form == "fp32" and not args.no_e2e:
             results[form]["e2e"] = _e2e(solver, w, lim, steps, args.warmup, lf)
@@ -623,7 +624,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="fp32,fp64")
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 form (0 = --steps)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

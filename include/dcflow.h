@@ -51,12 +51,18 @@ enum {
  * The base factorisation, the r x r update systems and the N-1 denominators
  * 1 - Phi_f[c,c] are FP64 in every form. */
 enum {
-  DCFLOW_FP64 = 0, /* everything FP64 */
-  DCFLOW_FP32 = 1  /* N-0 / N-1 contractions and reductions in FP32 */
+  DCFLOW_FP64 = 0,  /* everything FP64 */
+  DCFLOW_FP32 = 1,  /* N-0 / N-1 contractions and reductions in FP32 */
+  DCFLOW_BF16X3 = 2 /* as FP32, with the rank-r LODF update of every N-1 tile,
+                       Phi_f = Phi - Z Vt (Def. 3 / Eq. (5) on the topology of
+                       Eq. (7)), on the tensor cores: each operand split into
+                       BF16 hi + lo, three products hi.hi + hi.lo + lo.hi
+                       accumulated in FP32 (about 2^-16 relative per product).
+                       Passes with one timestep keep the FP32 build. */
 };
 
 typedef struct {
-  int32_t precision;     /* DCFLOW_FP64 or DCFLOW_FP32 */
+  int32_t precision;     /* DCFLOW_FP64, DCFLOW_FP32 or DCFLOW_BF16X3 */
   int32_t device;        /* CUDA device ordinal; -1 = the current device */
   int32_t chunk_topo;    /* topologies per internal chunk; 0 = automatic */
   double island_tol;     /* pivot / denominator threshold for islanding; 0 = 1e-9 */

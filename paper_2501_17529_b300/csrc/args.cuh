@@ -47,13 +47,16 @@ struct Args {
   int16_t* mod_ptr;
   double *Kinv, *alpha, *Vt64;
   void *VtR, *Zs, *ptil, *rowmul, *diagv, *s;
+  uint32_t* Zbf;  // BF16x3 form: Z / limit per monitored row as BF16 [hi KB | lo KB] (KB = 8 or 16), or null
   uint8_t* valid;
   int* nisl;
   void* pmax;
   int* parg;
   double* povl;
-  int ncb;    // 64-contingency blocks of the N-1 kernels: ceil(C_eff / 64)
+  int ncb;    // 64-contingency blocks of the N-1 kernels (the stride of their partial results)
   int C_eff;  // contingencies before the base-grid bridges (internal order)
+  int c_rem;  // first contingency of a short remainder [c_rem, C_eff) left to the final pass
+              // instead of an almost empty N-1 block (C_eff when there is none)
   const int* best_u;  // chosen injection candidate per (slot, timestep), or null
   int* err;  // set to 1 by a kernel whose bounded wait expired
   // outputs

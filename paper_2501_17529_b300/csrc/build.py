@@ -16,7 +16,7 @@ PKG = os.path.dirname(HERE)
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libdcflow.so")
 OBJ = os.path.join(ROOT, "_build", "obj")
-SOURCES = ["api.cu", "dense64.cu", "setup.cu", "solve.cu", "n1_launch.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["api.cu", "dense64.cu", "setup.cu", "solve.cu", "n1_launch.cu", "n1_launch_tc.cu", "noalloc.cu", "mlp.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

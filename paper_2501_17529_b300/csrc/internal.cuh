@@ -49,7 +49,7 @@ struct DevBuf {
 // chunk's preparation overlaps the previous chunk's N-1 kernel.
 struct ChunkBufs {
   DevBuf ent_n, ent_s, ent_w, mod_ptr, q_info;
-  DevBuf Kinv, alpha, Vt64, VtR, Zs, ptil, meta, s, valid, nisl;
+  DevBuf Kinv, alpha, Vt64, VtR, Zs, Zbf, ptil, meta, s, valid, nisl;
   DevBuf pmax, parg, povl;
   // injection candidates: per (timestep, candidate) operands and screening maxima,
   // the chosen candidate per timestep and its operands
@@ -62,7 +62,7 @@ struct ChunkBufs {
   // injection topologies: Z[c, :] / den_c, eligible injections and their split rows, their count
   DevBuf zcd, tiel, tirow, nel;
   void release_all() {
-    DevBuf* b[] = {&ent_n, &ent_s, &ent_w, &mod_ptr, &q_info, &Kinv, &alpha, &Vt64, &VtR, &Zs, &ptil, &meta,
+    DevBuf* b[] = {&ent_n, &ent_s, &ent_w, &mod_ptr, &q_info, &Kinv, &alpha, &Vt64, &VtR, &Zs, &Zbf, &ptil, &meta,
                    &s, &valid, &nisl, &pmax, &parg, &povl, &ptv, &svv, &pmaxv, &pargv, &povlv, &bestu, &ptb, &sb,
                    &selmask, &sfb, &csel, &nsel, &work, &nwork, &mvt, &mw, &mflag, &zcd, &tiel, &tirow, &nel};
     for (auto* x : b) x->release();

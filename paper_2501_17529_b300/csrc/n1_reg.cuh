@@ -26,15 +26,47 @@
 // transposed factors [cont][Mpad]: each contingency's 16 rows are one 64-byte
 // run, copied with cp.async into a contingency-major tile (pitch 20 floats:
 // the builders' reads spread over all banks); the other operands arrive by TMA.
+//
+// TC (the split-BF16x3 form): the Phi_f tile is built on the tensor cores
+// instead of the FFMA2 builders.  Per tile and warp, mma.sync m16n8k16 (k8 for
+// rank classes 4 and 8) computes D[c, l] = Phi[l, c] / limit + sum_j
+// (-Vt[j, c]) Z[l, j] / limit for 16 contingencies x 8 rows, with each operand
+// split as x = hi + lo in BF16 and three products hi.hi + hi.lo + lo.hi
+// accumulated in FP32 (the lo.lo term, below 2^-16 of the product, is
+// dropped).  -Vt^T is the A operand, held in registers for the block; Z rows
+// arrive by TMA already split (BF16 hi and lo per row, written by the row
+// preparation); Phi initialises the accumulator.  The D fragment of a thread
+// holds the row pair (2 q, 2 q + 1) of contingencies g and g + 8: exactly the
+// row-pair layout of s_ph, written with one 8-byte store each.  The tile of Phi
+// is TMA'd 68 columns wide and s_ph has a pitch of 68 pairs, which spreads
+// both the accumulator loads and the stores over all banks.  The shape
+// (16 rows x 64 contingencies, K = the rank class) is below the smallest
+// tcgen05 tile, so the warp-level MMA is the tensor-core instruction here.
 #pragma once
 
 #include <cuda.h>
 
+#include "bf16x3.cuh"
 #include "n1_tma.cuh"
 
 namespace dcf {
 
 constexpr int kRegStages = 2;  // TMA ring depth of this kernel (shared memory sets its occupancy)
+
+// D += A B, m16n8k16 / m16n8k8, BF16 operands, FP32 accumulators
+__device__ __forceinline__ void mma_bf16_k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_bf16_k8(float (&d)[4], const uint32_t (&a)[4], uint32_t b0) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5}, {%6}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(b0));
+}
 
 template <int TT>
 struct RegTile {
@@ -49,12 +81,13 @@ struct RegTile {
   static_assert(RB % 4 == 0, "build split");
 };
 
-template <int TT, int RMAX, bool SEL = false>
+template <int TT, int RMAX, bool SEL = false, bool TC = false>
 struct RegLayout {
   using R = RegTile<TT>;
   static constexpr int a128(int x) { return (x + 127) / 128 * 128; }
-  static constexpr int kPhi = SEL ? kCB * kPP * 4 : kLT * kCB * 4;
-  static constexpr int kZt = RMAX * kLT * 4;
+  static constexpr int kPW = TC ? kPhW : kCB;  // columns of a TMA'd Phi tile row; pairs per s_ph row
+  static constexpr int kPhi = SEL ? kCB * kPP * 4 : kLT * kPW * 4;
+  static constexpr int kZt = TC ? kLT * TcK<RMAX>::KB * 4 : RMAX * kLT * 4;  // TC: [16 rows][hi KB | lo KB] bf16
   static constexpr int kPt = TT * kLT * 4;
   static constexpr int kMeta = 4 * kLT * 4;
   static constexpr int kTx = (SEL ? 0 : kPhi) + kZt + kPt + kMeta;  // bytes landing by TMA
@@ -64,23 +97,24 @@ struct RegLayout {
   static constexpr int kStage = kOffMeta + a128(kMeta);
   static constexpr int kTP = TT + 2;   // row pitch (float2) of the transposed p_f: spreads the banks
   static constexpr int kSP = kCB + 1;  // row pitch (float) of the per-timestep arrays: spreads the banks
-  static constexpr int kOffPh = kRegStages * kStage;              // float2 [kLT/2][kCB]
-  static constexpr int kOffPtT = kOffPh + kLT * kCB * 4;          // float2 [kLT/2][kTP]
+  static constexpr int kOffPh = kRegStages * kStage;              // float2 [kLT/2][kPW]
+  static constexpr int kOffPtT = kOffPh + a128(kLT / 2 * kPW * 8); // float2 [kLT/2][kTP]
   static constexpr int kOffOv = kOffPtT + a128(kLT / 2 * kTP * 8); // float [TT][kSP]
   // the per-timestep maxima of the final scan reuse the (then idle) stages
   static_assert(TT * kSP * 4 <= kRegStages * kStage, "final scan fits the stages");
-  static constexpr int kOffVt = kOffOv + a128(TT * kSP * 4);      // float [RMAX][kCB]: -Vt
-  static constexpr int kOffBar = kOffVt + a128(RMAX * kCB * 4);   // uint64 [kRegStages]
+  static constexpr int kOffVt = kOffOv + a128(TT * kSP * 4);      // float [RMAX][kCB]: -Vt (not with TC)
+  static constexpr int kOffBar = kOffVt + (TC ? 0 : a128(RMAX * kCB * 4));  // uint64 [kRegStages]
   static constexpr int kOffOk = kOffBar + 64;                     // uint8 [kCB]
   static constexpr int kOffCi = kOffOk + 128;                     // int [kCB]: contingency of each column
   static constexpr int kOffQ = kOffCi + kCB * 4;                  // uint16 [warps][32 CR TR]
   static constexpr int kBytes = kOffQ + (R::NT / 32) * 32 * R::CR * R::TR * 2;
 };
 
-template <int TT, int RMAX, bool OVL, bool SEL = false>
-__global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constant__ N1Maps maps, Args a, int t0,
+template <int TT, int RMAX, bool OVL, bool SEL = false, bool TC = false>
+__global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n1_reg(const __grid_constant__ N1Maps maps, Args a, int t0,
                                                             const SelArgs sel) {
-  using L = RegLayout<TT, RMAX, SEL>;
+  using L = RegLayout<TT, RMAX, SEL, TC>;
+  constexpr int PH = L::kPW;  // pitch (pairs) of s_ph
   using R = RegTile<TT>;
   constexpr int CR = R::CR, TR = R::TR, RB = R::RB;
   int q = blockIdx.y, cb = blockIdx.x;  // topology slot and 64-contingency block
@@ -136,9 +170,11 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
   // compute role: contingencies c0 + cg + 16 i, timesteps TR tg + j
   constexpr int TP = L::kTP, SP = L::kSP;
   const int cg = tid % R::CG, tg = tid / R::CG;
-  for (int i = tid; i < RMAX * kCB; i += R::NT) {
-    const int j = i / kCB, c = s_ci[i % kCB];
-    s_vt[i] = c >= 0 ? -VtR[(size_t)j * C + c] : 0.f;
+  if constexpr (!TC) {
+    for (int i = tid; i < RMAX * kCB; i += R::NT) {
+      const int j = i / kCB, c = s_ci[i % kCB];
+      s_vt[i] = c >= 0 ? -VtR[(size_t)j * C + c] : 0.f;
+    }
   }
   for (int i = tid; i < TT * kCB; i += R::NT) s_ov[(i / kCB) * SP + i % kCB] = 0.f;  // overload sums, x 2^-20
   if (tid == 0) {
@@ -163,7 +199,8 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, L::kTx);
     if constexpr (!SEL) tma_load_2d(smem_u32(base), &maps.phi, c0, k * kLT, bar);
-    tma_load_3d(smem_u32(base + L::kOffZt), &maps.zt, k * kLT, 0, q, bar);
+    if constexpr (TC) tma_load_3d(smem_u32(base + L::kOffZt), &maps.zt, 0, k * kLT, q, bar);
+    else tma_load_3d(smem_u32(base + L::kOffZt), &maps.zt, k * kLT, 0, q, bar);
     tma_load_3d(smem_u32(base + L::kOffPt), &maps.pt, k * kLT, t0, q, bar);
     tma_load_3d(smem_u32(base + L::kOffMeta), &maps.meta, k * kLT, 0, q, bar);
   };
@@ -197,11 +234,39 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
 #pragma unroll
     for (int j = 0; j < TR; ++j) mx[i][j] = 0.f;
   // the builder's K^{-1}-weighted factors of its contingency, fixed for the block
-  constexpr bool kVtReg = RMAX <= 8;
+  constexpr bool kVtReg = RMAX <= 8 && !TC;
   float vb[kVtReg ? RMAX : 1];
   if constexpr (kVtReg) {
 #pragma unroll
     for (int j = 0; j < RMAX; ++j) vb[j] = s_vt[j * kCB + bl];
+  }
+  // TC: the MMA A operand -Vt^T, split into BF16 hi / lo, for the warp's m-blocks
+  // (16 contingencies each): lane (g, qd) holds contingencies 16 mb + g and
+  // 16 mb + g + 8 at depths 2 qd, 2 qd + 1 (and 2 qd + 8, 2 qd + 9 for K = 16)
+  constexpr int KB = TcK<RMAX>::KB;
+  constexpr int NW = R::NT / 32, MB = TC ? (kCB / 16) / NW : 1;
+  const int lane_g = (tid & 31) >> 2, lane_q = tid & 3, warp = tid >> 5;
+  uint32_t ah[MB][4], al[MB][4];
+  int drow[MB][2];  // monitored row of each held contingency's own branch, or -1
+  if constexpr (TC) {
+#pragma unroll
+    for (int m = 0; m < MB; ++m) {
+      const int mb = warp + NW * m;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = s_ci[16 * mb + lane_g + 8 * h];
+        drow[m][h] = c >= 0 ? a.mpos[c] : -1;
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = 2 * lane_q + (e & 1) + 8 * (e >> 1);
+          v[e] = (c >= 0 && j < RMAX && (e < 2 || KB == 16)) ? -VtR[(size_t)j * C + c] : 0.f;
+        }
+        // fragment registers: a0 (row g, k 2qd..), a1 (row g + 8, k 2qd..), a2 / a3 the same at k + 8
+        bf16_split2(v[0], v[1], ah[m][h], al[m][h]);
+        bf16_split2(v[2], v[3], ah[m][2 + h], al[m][2 + h]);
+      }
+    }
   }
   bool failed = false;
   for (int k = 0; k < ntiles; ++k) {
@@ -225,7 +290,54 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
     const float* zt_t = reinterpret_cast<const float*>(base + L::kOffZt);
     const float* pt_t = reinterpret_cast<const float*>(base + L::kOffPt);
     const float* meta_t = reinterpret_cast<const float*>(base + L::kOffMeta);
-    {  // build rows [bth RB, bth RB + RB) of Phi_f / limit for contingency bl
+    if constexpr (TC) {  // Phi_f tile on the tensor cores: warp x (m-blocks of 16 contingencies) x 2 row blocks
+      const uint32_t* zb = reinterpret_cast<const uint32_t*>(zt_t);  // row l: KB / 2 words hi, then KB / 2 lo
+#pragma unroll
+      for (int nb = 0; nb < 2; ++nb) {
+        const uint32_t* zr = zb + (8 * nb + lane_g) * KB;
+        const uint32_t bh0 = zr[lane_q], bl0 = zr[KB / 2 + lane_q];
+        uint32_t bh1 = 0, bl1 = 0;
+        if constexpr (KB == 16) {
+          bh1 = zr[4 + lane_q];
+          bl1 = zr[8 + 4 + lane_q];
+        }
+        const int l0 = 8 * nb + 2 * lane_q;  // rows l0, l0 + 1 of the tile
+        const float2 rm = *reinterpret_cast<const float2*>(&meta_t[1 * kLT + l0]);
+        const float2 dg = *reinterpret_cast<const float2*>(&meta_t[l0]);
+#pragma unroll
+        for (int m = 0; m < MB; ++m) {
+          const int cl = 16 * (warp + NW * m) + lane_g;  // contingencies cl and cl + 8 of the block
+          float d[4];
+          if constexpr (SEL) {
+            const float2 u = *reinterpret_cast<const float2*>(&phi_t[cl * kPP + l0]);
+            const float2 w = *reinterpret_cast<const float2*>(&phi_t[(cl + 8) * kPP + l0]);
+            d[0] = u.x; d[1] = u.y; d[2] = w.x; d[3] = w.y;
+          } else {
+            d[0] = phi_t[l0 * kPhW + cl];
+            d[1] = phi_t[(l0 + 1) * kPhW + cl];
+            d[2] = phi_t[l0 * kPhW + cl + 8];
+            d[3] = phi_t[(l0 + 1) * kPhW + cl + 8];
+          }
+          if constexpr (KB == 16) {
+            mma_bf16_k16(d, ah[m], bh0, bh1);
+            mma_bf16_k16(d, ah[m], bl0, bl1);
+            mma_bf16_k16(d, al[m], bh0, bh1);
+          } else {
+            mma_bf16_k8(d, ah[m], bh0);
+            mma_bf16_k8(d, ah[m], bl0);
+            mma_bf16_k8(d, al[m], bh0);
+          }
+          float2 lo = make_float2(d[0] * rm.x, d[1] * rm.y), hi = make_float2(d[2] * rm.x, d[3] * rm.y);
+          const int r0 = k * kLT + l0;  // LODF[c, c] = -1: Phi_f entry := -den_c / limit
+          if (drow[m][0] == r0) lo.x = dg.x;
+          if (drow[m][0] == r0 + 1) lo.y = dg.y;
+          if (drow[m][1] == r0) hi.x = dg.x;
+          if (drow[m][1] == r0 + 1) hi.y = dg.y;
+          s_ph[(l0 / 2) * PH + cl] = lo;
+          s_ph[(l0 / 2) * PH + cl + 8] = hi;
+        }
+      }
+    } else {  // build rows [bth RB, bth RB + RB) of Phi_f / limit for contingency bl
       const int r0 = bth * RB;
       float2 p[RB / 2];
 #pragma unroll
@@ -262,7 +374,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
         }
       }
 #pragma unroll
-      for (int i2 = 0; i2 < RB / 2; ++i2) s_ph[(r0 / 2 + i2) * kCB + bl] = p[i2];
+      for (int i2 = 0; i2 < RB / 2; ++i2) s_ph[(r0 / 2 + i2) * PH + bl] = p[i2];
     }
     // p_f / limit as row pairs per timestep: s_pt[rp][t] = (pt[t][2 rp], pt[t][2 rp + 1])
     for (int i = tid; i < (kLT / 2) * TT; i += R::NT) {
@@ -275,7 +387,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
     for (int rp = 0; rp < kLT / 2; ++rp) {
       float2 ph[CR];
 #pragma unroll
-      for (int i = 0; i < CR; ++i) ph[i] = s_ph[rp * kCB + cg + R::CG * i];
+      for (int i = 0; i < CR; ++i) ph[i] = s_ph[rp * PH + cg + R::CG * i];
       float2 pt[TR];
       if constexpr (TR % 2 == 0) {
 #pragma unroll
@@ -330,7 +442,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT) void k_n1_reg(const __grid_constan
           float2 o2 = make_float2(0.f, 0.f);
 #pragma unroll
           for (int rp = 0; rp < kLT / 2; ++rp) {
-            const float2 v = __ffma2_rn(s_ph[rp * kCB + cl], s22, s_pt[rp * TP + t]);
+            const float2 v = __ffma2_rn(s_ph[rp * PH + cl], s22, s_pt[rp * TP + t]);
             o2 = __fadd2_rn(o2, make_float2(__saturatef(fmaf(fabsf(v.x), 0x1p-20f, -0x1p-20f)),
                                             __saturatef(fmaf(fabsf(v.y), 0x1p-20f, -0x1p-20f))));
           }

@@ -8,6 +8,7 @@ namespace dcf {
 
 constexpr int kLT = 16;     // monitored rows per tile
 constexpr int kCB = 64;     // contingencies per block
+constexpr int kPhW = kCB + 4;  // tensor-core build: width of the TMA'd Phi tile and pitch (pairs) of the built tile
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier wait
 
 // Tensor maps of one N-1 pass: Phi[mon, cont] / limit (per study), Z^T / limit,

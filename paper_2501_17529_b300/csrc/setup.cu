@@ -144,7 +144,7 @@ extern "C" int dcflow_setup(dcflow_ctx** out, int32_t n_bus, int32_t n_branch, c
   dcflow_default_options(&o);
   if (opt) o = *opt;
   if (o.island_tol <= 0) o.island_tol = 1e-9;
-  if (o.precision != DCFLOW_FP64 && o.precision != DCFLOW_FP32) {
+  if (o.precision != DCFLOW_FP64 && o.precision != DCFLOW_FP32 && o.precision != DCFLOW_BF16X3) {
     set_error("dcflow_setup: unknown precision");
     return DCFLOW_ERR_INVALID_ARG;
   }

@@ -29,6 +29,7 @@
 #include <cudaTypedefs.h>
 
 #include "args.cuh"
+#include "bf16x3.cuh"
 #include "internal.cuh"
 #include "screen.cuh"
 
@@ -434,6 +435,21 @@ __global__ __launch_bounds__(128) void k_rows(Args a, Real* __restrict__ zcd, co
     const Real il = (Real)a.inv_lim[l];
 #pragma unroll
     for (int j = 0; j < RMAX; ++j) Zs[(size_t)j * Mp + l] = outd ? (Real)0 : z[j] * il;
+    if constexpr (sizeof(Real) == 4) {
+      if (a.Zbf) {  // BF16x3 form: the same row split into BF16 hi / lo pairs for the tensor-core build
+        constexpr int KB = TcK<RMAX>::KB;
+        uint32_t* zr = a.Zbf + ((size_t)q * Mp + l) * KB;
+#pragma unroll
+        for (int j2 = 0; j2 < KB / 2; ++j2) {
+          const float x0 = (2 * j2 < RMAX && !outd) ? (float)(z[min(2 * j2, RMAX - 1)] * il) : 0.f;
+          const float x1 = (2 * j2 + 1 < RMAX && !outd) ? (float)(z[min(2 * j2 + 1, RMAX - 1)] * il) : 0.f;
+          uint32_t hi, lo;
+          bf16_split2(x0, x1, hi, lo);
+          zr[j2] = hi;
+          zr[KB / 2 + j2] = lo;
+        }
+      }
+    }
     meta[l] = (Real)0;
     meta[Mp + l] = outd ? (Real)0 : (Real)1;
     if (sizeof(Real) == 4) {
@@ -800,6 +816,39 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
         bv = v2;
         ba = a2;
       }
+    }
+    // the short remainder of the contingency range (no N-1 block of its own):
+    // each column over the monitored rows with the N-1 kernels' arithmetic
+    for (int c = nsel ? a.C_eff : a.c_rem; c < a.C_eff; ++c) {
+      const bool okc = a.valid[(size_t)q * C + c];
+      Real vr = (Real)0;
+      double ov = 0.0;
+      if (okc) {
+        Real vt[RMAX];
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) vt[j] = VtR[(size_t)j * C + c];
+        const Real st = sv[(size_t)t * C + c];
+        for (int l = lane; l < M; l += 32) {
+          Real zr[RMAX];
+#pragma unroll
+          for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
+          const Real ph = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
+          const Real x = fabs(fma(ph, st, ptil[(size_t)t * Mp + l]));
+          vr = fmax(vr, x);
+          if (x > (Real)1) ov += (double)x - 1.0;
+        }
+        for (int off = 16; off; off >>= 1) {
+          vr = fmax(vr, __shfl_xor_sync(0xffffffffu, vr, off));
+          ov += __shfl_xor_sync(0xffffffffu, ov, off);
+        }
+        if (vr > bv || (vr == bv && c < ba)) {
+          bv = vr;
+          ba = c;
+        }
+        ovl += ov;
+      }
+      if (lane == 0 && o.n1_cont_max)
+        o.n1_cont_max[((size_t)tau * T + t) * C + a.cont_pos[c]] = okc ? (float)vr : -1.f;
     }
     const int c = (ba == 0x7fffffff) ? -1 : ba;
     if (lane == 0) {
@@ -2294,6 +2343,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   }
   cudaStream_t st = (cudaStream_t)stream;
   const bool fp64 = ctx->opt.precision == DCFLOW_FP64;
+  const bool tc = ctx->opt.precision == DCFLOW_BF16X3;  // the N-1 tiles' Phi_f on the tensor cores
   const size_t rs = fp64 ? sizeof(double) : sizeof(float);
   const int M = ctx->M, C = ctx->C, NN = ctx->NN;
   // injection candidates T_i (Eq. (8)): read the small CSR to the host, validate
@@ -2457,9 +2507,14 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   // overlapping chunks: the N-1 kernel fills the SMs' registers and shared
   // memory, so preparation kernels of the next chunk only run in its tail)
   const int C_eff = ctx->C_eff;       // contingencies that can be valid (base-grid bridges excluded)
-  const int ncb = (C_eff + 63) / 64;  // 64-contingency blocks of the N-1 kernels
   // FP32 full solve on request: the N-1 kernel runs over each topology's compacted valid contingencies
   const bool cmp = !fp64 && mode == kModeFull && C_eff > 0 && ctx->opt.compact_n1;
+  // a remainder of at most kRemCols contingencies beyond the last full block of 64
+  // goes to the final pass (a column each over the monitored rows) instead of an
+  // N-1 block that would compute 64 columns for it (plain full solves only)
+  constexpr int kRemCols = 4;
+  const bool use_rem = mode == kModeFull && Uc == 0 && !cmp && C_eff > 64 && C_eff % 64 > 0 && C_eff % 64 <= kRemCols;
+  const int ncb = use_rem ? C_eff / 64 : (C_eff + 63) / 64;  // 64-contingency blocks of the N-1 kernels
   const int Mp = (int)round_up(M, 16);
   const int TV = T * Uc;  // virtual timesteps: (timestep, candidate) pairs
   if (R > 64) {
@@ -2471,6 +2526,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                     (size_t)Mp * (kRMax + Text + 4) * rs + (size_t)Text * C * rs + C + 4 +
                     (size_t)T * ncb * (rs + 4 + 8) + 64;
   if (TI) per_slot += (size_t)kRMax * C * rs + 64 * 8 + 4;
+  if (tc) per_slot += (size_t)Mp * 16 * 4;  // BF16 hi / lo Z rows
   if (cmp) per_slot += (size_t)C * 4 + 4;
   if (Uc > 0)
     per_slot += (size_t)TV * (Mp + C) * rs + (size_t)TV * ncb * (rs + 4 + 8) + (size_t)T * 4 + (size_t)T * (Mp + C) * rs;
@@ -2494,6 +2550,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       return DCFLOW_ERR_OOM;
     if (cmp && (B.csel.ensure(c * std::max(C, 1) * sizeof(int)) || B.nsel.ensure(c * sizeof(int))))
       return DCFLOW_ERR_OOM;
+    if (tc && B.Zbf.ensure(c * Mp * 16 * 4)) return DCFLOW_ERR_OOM;
     if (TI && (B.zcd.ensure(c * kRMax * std::max(C, 1) * rs) || B.tiel.ensure(c * 64 * sizeof(int)) ||
                B.tirow.ensure(c * 64 * sizeof(int)) || B.nel.ensure(c * sizeof(int))))
       return DCFLOW_ERR_OOM;
@@ -2573,6 +2630,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   base.tol = ctx->opt.island_tol;
   base.ncb = ncb;
   base.C_eff = C_eff;
+  base.c_rem = use_rem ? ncb * 64 : C_eff;
   base.cont_pos = ctx->cont_pos.as<int>();
   base.Mpad = Mp;
   base.ldc = ctx->ldc;
@@ -2596,6 +2654,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     a.Vt64 = B.Vt64.as<double>();
     a.VtR = fp64 ? B.Vt64.p : B.VtR.p;
     a.Zs = B.Zs.p;
+    a.Zbf = tc ? B.Zbf.as<uint32_t>() : nullptr;
     a.ptil = B.ptil.p;
     a.rowmul = nullptr;
     a.diagv = B.meta.p;
@@ -2612,9 +2671,11 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   // N-1 passes over Tn (virtual) timesteps whose operands are a.ptil / a.s;
   // ovl = false screens the maximum only (FP32 form)
   auto encode_maps = [&](const Args& a, int RMAX, int Tn, int TTn, N1Maps& maps) -> int {
+    const bool tc = ctx->opt.precision == DCFLOW_BF16X3 && TTn >= 4;  // one-timestep passes: FFMA build
     {
       const uint64_t d_phi[2] = {(uint64_t)C, (uint64_t)M}, s_phi[1] = {(uint64_t)ctx->ldc * 4};
-      const uint32_t b_phi[2] = {kCB, kLT};
+      // the tensor-core build reads a 68-column tile (its pitch spreads the fragment loads over the banks)
+      const uint32_t b_phi[2] = {tc ? (uint32_t)kPhW : (uint32_t)kCB, kLT};
       const uint64_t d_me[3] = {(uint64_t)M, 4, (uint64_t)cap};
       const uint64_t s_me[2] = {(uint64_t)Mp * 4, (uint64_t)Mp * 16};
       const uint32_t b_me[3] = {kLT, 4, 1};
@@ -2626,7 +2687,14 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       const uint32_t b_pt[3] = {kLT, (uint32_t)TTn, 1};
       int rc = encode_map(&maps.phi, ctx->PhiMC.p, 2, d_phi, s_phi, b_phi);
       if (!rc) rc = encode_map(&maps.meta, a.diagv, 3, d_me, s_me, b_me);
-      if (!rc) rc = encode_map(&maps.zt, a.Zs, 3, d_zt, s_zt, b_zt);
+      if (!rc && !tc) rc = encode_map(&maps.zt, a.Zs, 3, d_zt, s_zt, b_zt);
+      if (!rc && tc) {  // BF16 hi / lo Z rows [slot][Mpad][KB words]
+        const uint64_t KB = RMAX <= 8 ? 8 : 16;
+        const uint64_t d_zb[3] = {KB, (uint64_t)M, (uint64_t)cap};
+        const uint64_t s_zb[2] = {KB * 4, (uint64_t)Mp * KB * 4};
+        const uint32_t b_zb[3] = {(uint32_t)KB, kLT, 1};
+        rc = encode_map(&maps.zt, a.Zbf, 3, d_zb, s_zb, b_zb);
+      }
       if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt);
       return rc;
     }
@@ -2647,8 +2715,9 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       if (fp64) rc = launch_n1<double>(a, RMAX, TTn, grid, st, t0);
       else if (cmp)
         rc = launch_reg_cmp(maps, a, SelArgs{ctx->PhiCM.as<float>(), Mp, cmp->csel.as<int>(), cmp->nsel.as<int>(), nullptr},
-                            RMAX, TTn, ovl, grid, st, t0);
-      else rc = ovl ? launch_tma(maps, a, RMAX, TTn, grid, st, t0) : launch_tma_screen(maps, a, RMAX, grid, st, t0);
+                            RMAX, TTn, ovl, grid, st, t0, tc);
+      else rc = ovl ? launch_tma(maps, a, RMAX, TTn, grid, st, t0, tc)
+                    : launch_tma_screen(maps, a, RMAX, grid, st, t0, tc);
       if (rc) return rc;
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
@@ -2831,7 +2900,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       const SelArgs sargs{ctx->PhiCM.as<float>(), Mp, SB.csel.as<int>(), SB.nsel.as<int>(), SB.work.as<int>()};
       for (int t0 = 0; t0 < T; t0 += TTs) {
         const int pe = ctx->prof_begin(st);
-        if (reg_sel) rc = items ? launch_reg_sel(smaps, af, sargs, RMAX, TTs, items, st, t0) : 0;
+        if (reg_sel) rc = items ? launch_reg_sel(smaps, af, sargs, RMAX, TTs, items, st, t0, tc) : 0;
         else rc = fp64 ? launch_sel<double>(af, ctx->PhiCM.p, SB, RMAX, TTs, sgrid, st, t0)
                        : launch_sel<float>(af, ctx->PhiCM.p, SB, RMAX, TTs, sgrid, st, t0);
         if (rc) return rc;

@@ -16,8 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdcflow.so")
 
 DCFLOW_OK = 0
-FP64, FP32 = 0, 1
-PRECISIONS = {"fp64": FP64, "fp32": FP32}
+FP64, FP32, BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
 
 
 class Options(ctypes.Structure):

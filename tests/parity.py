@@ -11,7 +11,7 @@ import numpy as np
 
 import oracle
 
-TOL = {"fp64": 1e-10, "fp32": 1e-4}
+TOL = {"fp64": 1e-10, "fp32": 1e-4, "bf16x3": 1e-4}
 
 
 def _topo_lists(topo, i):

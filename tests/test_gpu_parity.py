@@ -44,7 +44,7 @@ def _ref(w, lim, topo=None):
     return oracle.evaluate(w.grid, topo, w.inj, w.mon, w.cont, lim, want_flows=True, want_cmax=True)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x3"])
 def test_tiny_grid_all_topologies(precision):
     """14-bus grid, 64 single splits (slack included), full N-1: every output."""
     w = synth.workload(1)
@@ -73,7 +73,7 @@ def test_tiny_grid_every_mask(precision):
     compare(_gpu(w, lim, precision, topo), ref, w, topo, lim, TOL[precision])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x3"])
 def test_grid500_sample(precision):
     """500-bus grid, 1-4 splits + 0-3 outages, 24 timesteps: 48 topologies."""
     w = synth.workload(2, n_topo=48)
@@ -81,7 +81,7 @@ def test_grid500_sample(precision):
     compare(_gpu(w, lim, precision), _ref(w, lim), w, w.topo, lim, TOL[precision])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x3"])
 def test_grid500_row_restricted_study(precision):
     """The benchmark's study: only the rows of the monitored, contingency,
     split-bus and outage-candidate branches, the candidates being exactly the
@@ -132,14 +132,34 @@ def test_switching_outside_the_study_is_invalid(precision):
     compare(gpu, ref, w, topo, lim, TOL[precision])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x3"])
+@pytest.mark.parametrize("rem", [1, 3, 4, 5])
+def test_contingency_remainder_columns(precision, rem):
+    """A contingency range of 64 + rem columns: a remainder of at most 4 is
+    evaluated by the final pass instead of an N-1 block of its own (5 takes
+    the block); every output, per-contingency maxima included, against the oracle."""
+    g = synth.make_grid(200, 300, 81)
+    subs = synth.split_capable(g, 30, 81)
+    br = oracle.bridges(g.n_bus, g.f, g.t, np.ones(g.n_branch, bool))
+    nonbridge = np.nonzero(~br)[0]
+    rng = np.random.default_rng(82 + rem)
+    cont = np.sort(rng.choice(nonbridge, 64 + rem, replace=False)).astype(np.int32)
+    mon = np.sort(rng.choice(g.n_branch, 150, replace=False)).astype(np.int32)
+    topo = synth.make_topologies(g, subs, 24, 83, (1, 3), (0, 2))
+    inj = synth.make_injections(g, 5, 84, daily=True)
+    w = synth.Workload("rem", g, topo, inj, mon, cont, subs)
+    lim = oracle.thermal_limits(g, inj)
+    compare(_gpu(w, lim, precision), _ref(w, lim), w, topo, lim, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x3"])
 def test_ragged_chunks_times_and_sets(precision):
     """Small chunks across rank classes, T beyond one pass, ragged mon / cont subsets."""
     g = synth.make_grid(120, 170, 31)
     subs = synth.split_capable(g, 30, 31)
     rng = np.random.default_rng(32)
     topo = synth.make_topologies(g, subs, 40, 33, (0, 9), (0, 7))
-    T = 37 if precision == "fp32" else 19
+    T = 37 if precision != "fp64" else 19
     inj = synth.make_injections(g, T, 34, daily=True)
     mon = np.sort(rng.choice(g.n_branch, 101, replace=False)).astype(np.int32)
     cont = np.sort(rng.choice(g.n_branch, 77, replace=False)).astype(np.int32)
@@ -275,7 +295,7 @@ def _check_candidates(w, lim, precision):
     return out, ref, inj_pick, cols
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x3"])
 def test_injection_candidates_bruteforce(precision):
     """Injection candidates (Eq. (8), metric-first): argmin over candidates of the
     maximum loading, ties to the lowest index, and that candidate's outputs."""
@@ -318,7 +338,7 @@ def _cand_matrix(g, var, T):
     return np.tile(D, (T, 1))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x3"])
 def test_grid2000_candidates_sample(precision):
     """Full 2000-bus / 3000-branch grid, 1000 random contingencies, uneven k
     (geometric splits and outages), 8 injection candidates, 2 timesteps."""
@@ -328,7 +348,7 @@ def test_grid2000_candidates_sample(precision):
     _compare_picked(out, ref, w, lim, precision, inj_pick, cols)
 
 
-@pytest.mark.parametrize("precision", ["fp32"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 def test_grid10000_sample(precision):
     """Full 10,000-bus / 15,000-branch grid, 5000 monitored x 2000 contingencies,
     1-6 splits, 16 timesteps: three topologies."""
@@ -656,14 +676,16 @@ def test_injection_topologies_uneven_and_invalid_lists():
         assert np.all(out["best_var"][~ok] == -1)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("compact", [False, True])
-def test_grid500_dense_and_compacted_n1(compact):
+def test_grid500_dense_and_compacted_n1(compact, precision):
     """FP32 N-1 over every contingency column and over each topology's compacted valid contingencies
-    (compact_n1): the same outputs as the oracle, per-contingency maxima (-1 where skipped) included."""
+    (compact_n1): the same outputs as the oracle, per-contingency maxima (-1 where skipped) included;
+    with the FFMA2 and the tensor-core (split BF16x3) Phi_f build."""
     from paper_2501_17529_b300.dcflow import DeviceBatch, Solver
     w = synth.workload(2, n_topo=40)
     lim = oracle.thermal_limits(w.grid, w.inj)
-    s = Solver(w.grid, precision="fp32", compact_n1=compact)
+    s = Solver(w.grid, precision=precision, compact_n1=compact)
     s.set_study(w.mon, w.cont, lim, split_bus=w.subs)
     out = s.solve(DeviceBatch(w.topo, w.inj), want_flows=True, want_cont_max=True).to_host()
     torch.cuda.synchronize()
