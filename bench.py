@@ -164,11 +164,21 @@ def _cpu_worker(args):
     w = synth.workload(shape, n_topo=max(idx) + 1)
     lim = oracle.thermal_limits(w.grid, w.inj)
     t0 = time.perf_counter()
-    r = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, var=w.var, idx=idx)
+    r = oracle.evaluate(w.grid, w.topo, w.inj, w.mon, w.cont, lim, var=w.var, idx=idx, want_cmax=w.var is None)
     dt = time.perf_counter() - t0
     nv = 0 if w.var is None else w.var.n_var
     keep = {k: r[k] for k in ("n0_max", "n1_max", "ovl", "worst_cont", "status", "n_island_cont")}
     keep["idx"] = np.asarray(idx, np.int64)
+    if w.var is None:
+        # the worst contingency under each form's tie band (the lowest position within
+        # band * max(best, 1) of the largest per-contingency maximum), as the CUDA path reports it
+        for name, eps in (("band_1e-4", 1e-4), ("band_1e-10", 1e-10)):
+            wc = -np.ones_like(r["worst_cont"])
+            for i in range(wc.shape[0]):
+                for t in range(wc.shape[1]):
+                    if r["status"][i] == 0 and (r["cmax"][i, t] >= 0).any():
+                        wc[i, t] = oracle.first_in_band(r["cmax"][i, t], eps)
+            keep["worst_cont_" + name] = wc
     return oracle.loadflow_count(r, w.inj.shape[0], nv), dt, keep
 
 
@@ -198,10 +208,11 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
                       f"{cores} spawn workers, 1 BLAS thread each, {wall:.1f} s wall"}, ref
 
 
-def _errors(host, ref):
+def _errors(host, ref, form=None):
     """Errors of one form against the oracle on the oracle's topology sample
     (loadings |x - x_ref| / max(x_ref, 1), overload sums likewise; integer
-    outputs as the fraction that agrees exactly)."""
+    outputs as the fraction that agrees exactly; the worst contingency against
+    the oracle's under the form's tie band when the sample has it)."""
     idx = ref["idx"]
     st = host["status"][idx]
     ok = ref["status"] == 0
@@ -211,7 +222,11 @@ def _errors(host, ref):
     for key, name in (("n0_max", "n0_max_loading"), ("n1_max", "n1_max_loading"), ("ovl", "overload_sum")):
         g, r = host[key][idx][ok], ref[key][ok]
         out[f"max_err_{name}"] = float((np.abs(g - r) / np.maximum(np.abs(r), 1.0)).max()) if ok.any() else 0.0
-    out["worst_cont_agree"] = float(np.mean(host["worst_cont"][idx][ok] == ref["worst_cont"][ok])) if ok.any() else 1.0
+    key = {"fp64": "worst_cont_band_1e-10", "fp32": "worst_cont_band_1e-4", "bf16x3": "worst_cont_band_1e-4"}.get(form)
+    wref = ref[key] if key in ref else ref["worst_cont"]
+    out["worst_cont_agree"] = float(np.mean(host["worst_cont"][idx][ok] == wref[ok])) if ok.any() else 1.0
+    if key in ref:
+        out["worst_cont_rule"] = "lowest position within " + key.split("_")[-1] + " x max(best, 1) of the best"
     return out
 
 
@@ -492,6 +507,29 @@ def run_ours(args):
             results[form]["kernels"] = {"name": "k_n1<double>", "ms_per_step": kern["n1_ms"] / steps,
                                         "entries_per_s_T": e64, "fp64_peak_T": fp64_peak, "frac": e64 / fp64_peak}
         solver.close()
+    configs = {}
+    run_cfgs = [c for c in args.configs.split(",") if c and c != "none"] if ws == 1 and args.workload == "grid500" \
+        else []
+    if run_cfgs:
+        import multiprocessing as mp
+        pool = None
+        if not args.no_cpu:
+            for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+                os.environ[k] = "1"
+            pool = mp.get_context("spawn").Pool(os.cpu_count() or 1)
+        if "grid10000" in run_cfgs:  # its oracle jobs start first (the longest; no GPU result needed)
+            configs["grid10000"] = run_cfg_grid10000(args, flush, peaks, pool)
+        if "cand" in run_cfgs:
+            configs["grid2000_cand256"] = run_cfg_candidates(args, flush, peaks, pool)
+        if "screen" in run_cfgs:
+            configs["grid2000_screen"] = run_cfg_screener(args, peaks)
+        if "grid10000" in configs and "_oracle" in configs["grid10000"]:
+            configs["grid10000"]["error_vs_oracle"] = _grid10000_errors(configs["grid10000"])
+        if "grid2000_cand256" in configs and "_oracle" in configs["grid2000_cand256"]:
+            configs["grid2000_cand256"]["error_vs_oracle"] = _cand_errors(configs["grid2000_cand256"])
+        if pool is not None:
+            pool.close()
+            pool.join()
     if rank != 0:
         if ws > 1:
             dist.barrier()
@@ -544,14 +582,284 @@ def run_ours(args):
         line["e2e"] = head["e2e"]
     if roof:
         line["roofline"] = roof
+    if configs:
+        line["configs"] = configs
     if ws == 1 and not args.no_cpu:
         line["cpu_baseline"], ref = cpu_baseline(args.workload, args.cpu_budget)
         if n_topo == WORKLOADS[args.workload][1]:  # the oracle's sample is of this very batch
-            line["error_vs_oracle"] = {f: _errors(h, ref) for f, h in hosts.items()}
+            line["error_vs_oracle"] = {f: _errors(h, ref, f) for f, h in hosts.items()}
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the other study shapes, one entry each under "configs" of the JSON line:
+# 2000-bus with 256 injection candidates (uneven k, autotuned schedule),
+# 10000-bus in the FP32 and BF16x3 forms, and the learned screener
+# ---------------------------------------------------------------------------
+
+def _device_limits(w):
+    """Limits 1.2 max_t |base flow| + 0.1 on the monitored branches, base PTDF rows on the device."""
+    from paper_2501_17529_b300.dcflow import Solver
+    base = Solver(w.grid, precision="fp64")
+    pt = base.base_ptdf(w.mon).cpu().numpy()
+    base.close()
+    lim = np.ones(w.grid.n_branch)
+    lim[w.mon] = 1.2 * np.abs(w.inj @ pt.T).max(axis=0) + 0.1
+    return lim
+
+
+def _cand_rows(w):
+    """[U, V] injection change of every candidate."""
+    var, U = w.var, w.var.n_var
+    D = np.zeros((U, w.grid.n_bus))
+    for u in range(U):
+        for k in range(var.var_ptr[u], var.var_ptr[u + 1]):
+            D[u, var.var_bus[k]] += var.var_delta[k]
+    return D
+
+
+def _cand_oracle_worker(job):
+    """Oracle rows of the 2000-bus candidate study for topologies idx: per timestep the
+    GPU's chosen candidate first, then `others` (a sample of the rest), each as its own
+    timestep of a plain refactorising evaluation."""
+    idx, picks, others = job
+    import oracle
+    from paper_2501_17529_b300 import synth
+    w = synth.workload(3, n_topo=max(idx) + 1)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    D = _cand_rows(w)
+    T = w.inj.shape[0]
+    out = []
+    for j, i in enumerate(idx):
+        rows = []
+        for t in range(T):
+            rows.append(w.inj[t] + (D[picks[j][t]] if picks[j][t] >= 0 else 0.0))
+            rows.extend(w.inj[t] + D[u] for u in others[j][t])
+        r = oracle.evaluate(w.grid, w.topo.subset([i]), np.array(rows), w.mon, w.cont, lim, tie_eps=1e-4)
+        out.append({k: r[k][0] for k in ("status", "n_island_cont", "n0_max", "n1_max", "ovl", "worst_cont")})
+    return out
+
+
+def _timed_solve(solver, db, res, steps, flush, stream):
+    """`steps` solves (L2 flushed before each) by CUDA events with the kernel timers on:
+    (seconds, N-1 kernel ms per step, launches per step, clocks)."""
+    import torch
+    lib = __import__("paper_2501_17529_b300.dcflow", fromlist=["x"])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    lib.dcflow_profile(solver.ctx, True)
+    launches = 0
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            solver.solve(db, results=res)
+            ev[k][1].record(stream)
+            launches += solver.last_launch_count()
+        torch.cuda.synchronize()
+    kp = lib.dcflow_profile_read(solver.ctx)
+    lib.dcflow_profile(solver.ctx, False)
+    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    return t, kp["n1_ms"] / steps, launches // steps, clk.summary()
+
+
+def run_cfg_candidates(args, flush, peaks, pool):
+    """2000 buses / 3000 branches, 100,000 topologies of uneven k (1-8 splits + 0-4 outages,
+    geometric), 8 timesteps x 256 injection candidates, N-1 over 1000 contingencies, every
+    branch monitored; schedule picked by the autotuner on a 512-topology prefix."""
+    import torch
+    from paper_2501_17529_b300 import synth
+    from paper_2501_17529_b300.dcflow import DeviceBatch, DeviceResults, Solver
+    n = args.cand_topologies
+    w = synth.workload(3, n_topo=n)
+    lim = _device_limits(w)
+    T, U, M = w.inj.shape[0], w.var.n_var, len(w.mon)
+    ocand = np.unique(np.asarray(w.topo.out_branch, np.int32))
+    ts = time.perf_counter()
+    s = Solver(w.grid, precision=args.cand_form)
+    s.set_study(w.mon, w.cont, lim, split_bus=w.subs, outage_cand=ocand)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - ts
+    ns = min(512, n)
+    sdb = DeviceBatch(w.topo.subset(np.arange(ns)), w.inj, w.var)
+    sres = DeviceResults(ns, T, M, want_var=True)
+    t0 = time.perf_counter()
+    pick, tried = s.autotune(sdb, sres)
+    tune_s = time.perf_counter() - t0
+    db = DeviceBatch(w.topo, w.inj, w.var)
+    res = DeviceResults(n, T, M, want_var=True)
+    s.solve(sdb, results=sres)  # warm-up on the prefix (the full batch allocates in its first chunk)
+    torch.cuda.synchronize()
+    t, n1_ms, launches, clk = _timed_solve(s, db, res, args.cand_steps, flush, torch.cuda.current_stream())
+    host = res.to_host()
+    lf = _loadflows(w.topo, host["status"], host["n_island_cont"], w.cont, T) * U
+    alu_peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    # N-1 entries: the screening pass evaluates every (timestep, candidate, contingency, monitored
+    # branch) once; the full pass of the chosen candidate adds 1/U of that
+    ach = lf * M * (1.0 + 1.0 / U) / (n1_ms / 1e3) / 1e12
+    entry = {"workload": "grid2000_splits1-8geo_outages0-4geo_T8_cand256_mon3000_cont1000", "form": args.cand_form,
+             "topologies": n, "timesteps": T, "candidates": U, "monitored": M, "contingencies": len(w.cont),
+             "value": lf * args.cand_steps / t, "unit": "loadflows/s", "ms_per_step": 1e3 * t / args.cand_steps,
+             "steps": args.cand_steps, "loadflows_per_step": lf, "launches_per_step": launches, "clocks": clk,
+             "setup_s": setup_s, "schedule": pick, "schedules_tried": tried, "tune_s": tune_s,
+             "roofline": {"bound": "alu", "kernel": "k_n1_reg (screening pass over every (timestep, candidate), "
+                                                  "then the full pass of the chosen one)",
+                          "achieved": ach, "peak": alu_peak, "unit": "T N-1 entries/s", "frac": ach / alu_peak,
+                          "n1_ms_per_step": n1_ms, "n1_share_of_step": n1_ms / (1e3 * t / args.cand_steps)},
+             "l2": "flushed before each step (256 MB write); the step's operands exceed L2"}
+    job = None
+    if pool is not None and args.cand_oracle > 0:
+        # oracle sample: the first topologies; per timestep the GPU's pick plus 8 random other candidates
+        k = min(args.cand_oracle, n)
+        rng = np.random.default_rng(12)
+        picks = host["best_var"][:k].astype(np.int64)
+        others = [[rng.choice(np.setdiff1d(np.arange(U), [picks[i][t]]), 8, replace=False).tolist()
+                   for t in range(T)] for i in range(k)]
+        chunks = [list(range(i, k, 16)) for i in range(min(16, k))]
+        job = pool.map_async(_cand_oracle_worker, [(c, [picks[i] for i in c], [others[i] for i in c])
+                                                   for c in chunks if c])
+        entry["_oracle"] = (job, chunks, {kk: host[kk][:k] for kk in ("status", "n_island_cont", "n0_max", "n1_max",
+                                                                       "ovl", "worst_cont", "best_var")})
+    s.close()
+    return entry
+
+
+def _cand_errors(entry, tol=1e-4):
+    job, chunks, g = entry.pop("_oracle")
+    rows = {}
+    for c, out in zip([c for c in chunks if c], job.get()):
+        for i, o in zip(c, out):
+            rows[i] = o
+    idx = sorted(rows)
+    T = g["n1_max"].shape[1]
+    K = 1 + 8
+    st = np.array([rows[i]["status"] for i in idx])
+    ok = st == 0
+    e = {"topologies": len(idx), "status_agree": float(np.mean(st == g["status"][idx]))}
+    errs_n1, errs_ovl, errs_n0, pick_ok, wc = [], [], [], [], []
+    for j, i in enumerate(idx):
+        if not ok[j]:
+            continue
+        r = rows[i]
+        for t in range(T):
+            ref_n1 = r["n1_max"][t * K]
+            errs_n1.append(abs(g["n1_max"][i, t] - ref_n1) / max(ref_n1, 1.0))
+            errs_ovl.append(abs(g["ovl"][i, t] - r["ovl"][t * K]) / max(r["ovl"][t * K], 1.0))
+            errs_n0.append(abs(g["n0_max"][i, t] - r["n0_max"][t * K]) / max(r["n0_max"][t * K], 1.0))
+            others = r["n1_max"][t * K + 1:(t + 1) * K]
+            pick_ok.append(bool(ref_n1 <= others.min() + 2 * tol * max(1.0, others.min())))
+            wc.append(int(g["worst_cont"][i, t]) == int(r["worst_cont"][t * K]))
+    e.update({"max_err_n1_max_loading": float(max(errs_n1, default=0.0)),
+              "max_err_overload_sum": float(max(errs_ovl, default=0.0)),
+              "max_err_n0_max_loading": float(max(errs_n0, default=0.0)),
+              "pick_not_beaten_by_8_random_candidates": float(np.mean(pick_ok)) if pick_ok else 1.0,
+              "worst_cont_agree": float(np.mean(wc)) if wc else 1.0,
+              "sample": f"first {len(idx)} topologies, every timestep: the oracle evaluated at the chosen "
+                        "candidate and at 8 random others (all 256 per topology take the oracle ~4 min)"})
+    return e
+
+
+def run_cfg_grid10000(args, flush, peaks, pool):
+    """10,000 buses / 15,000 branches, 5000 monitored x 2000 contingencies, 50,000 topologies
+    with 1-6 splits, 16 timesteps; the FP32 and the BF16x3 forms (FP64 denominators)."""
+    import torch
+    from paper_2501_17529_b300 import synth
+    from paper_2501_17529_b300.dcflow import DeviceBatch, DeviceResults, Solver
+    n = args.g10k_topologies
+    w = synth.workload(4, n_topo=n)
+    lim = _device_limits(w)
+    T, M = w.inj.shape[0], len(w.mon)
+    job = None
+    if pool is not None and args.g10k_oracle > 0:
+        k = min(args.g10k_oracle, n)
+        job = pool.map_async(_cpu_worker, [(4, list(range(i, k, 16))) for i in range(min(16, k))])
+    alu_peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    out = {"workload": "grid10000_splits1-6_T16_mon5000_cont2000", "topologies": n, "timesteps": T, "monitored": M,
+           "contingencies": len(w.cont), "l2": "flushed before each step (256 MB write)", "forms": {}}
+    hosts = {}
+    for form in args.g10k_forms.split(","):
+        ts = time.perf_counter()
+        s = Solver(w.grid, precision=form)
+        s.set_study(w.mon, w.cont, lim, split_bus=w.subs, outage_cand=np.zeros(0, np.int32))
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - ts
+        db = DeviceBatch(w.topo, w.inj)
+        res = DeviceResults(n, T, M)
+        s.solve(db, results=res)
+        torch.cuda.synchronize()
+        t, n1_ms, launches, clk = _timed_solve(s, db, res, args.g10k_steps, flush, torch.cuda.current_stream())
+        host = res.to_host()
+        hosts[form] = host
+        lf = _loadflows(w.topo, host["status"], host["n_island_cont"], w.cont, T)
+        ach = lf * M / (n1_ms / 1e3) / 1e12
+        out["forms"][form] = {"value": lf * args.g10k_steps / t, "unit": "loadflows/s",
+                              "ms_per_step": 1e3 * t / args.g10k_steps, "steps": args.g10k_steps,
+                              "loadflows_per_step": lf, "launches_per_step": launches, "setup_s": setup_s,
+                              "clocks": clk, "schedule": s.last_schedule(),
+                              "roofline": {"bound": "alu", "kernel": "k_n1_reg", "achieved": ach, "peak": alu_peak,
+                                           "unit": "T N-1 entries/s", "frac": ach / alu_peak, "n1_ms_per_step": n1_ms}}
+        s.close()
+    if "fp32" in out["forms"] and "bf16x3" in out["forms"]:
+        out["bf16x3_over_fp32_speedup"] = out["forms"]["bf16x3"]["value"] / out["forms"]["fp32"]["value"]
+    if job is not None:
+        out["_oracle"] = (job, hosts)
+    return out
+
+
+def _grid10000_errors(out):
+    job, hosts = out.pop("_oracle")
+    res = job.get()
+    ref = {k: np.concatenate([r[2][k] for r in res]) for k in res[0][2]}
+    e = {f: _errors(h, ref, f) for f, h in hosts.items()}
+    e["sample"] = f"first {ref['idx'].size} topologies (the oracle refactorises each: ~26 s per topology per core)"
+    return e
+
+
+def run_cfg_screener(args, peaks):
+    """The learned screener on the 2000-bus study: trained on solver-generated N-1 labels of
+    200,000 topologies (1-8 splits, 8 timesteps), evaluated on 100,000 held-out ones."""
+    import torch
+    from paper_2501_17529_b300 import screener as scr_mod
+    from paper_2501_17529_b300 import synth
+    from paper_2501_17529_b300.dcflow import Screener, Solver
+    w = synth.workload(5, n_topo=args.scr_train)
+    ev_topo = synth.make_topologies(w.grid, w.subs, args.scr_eval, 605, (1, 8), (0, 0))
+    lim = _device_limits(w)
+    s = Solver(w.grid, precision="fp32")
+    s.set_study(w.mon, w.cont, lim, split_bus=w.subs)
+    sc = Screener(s, max_rows=8192, seed=1)
+    t0 = time.perf_counter()
+    Xtr, Ytr, _, _, st_tr = scr_mod.dataset(s, sc, w.topo, w.inj, args.scr_top_k)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = scr_mod.train(sc, Xtr, Ytr, st_tr, w.inj.shape[0], args.scr_epochs, 8192, 2e-3, cosine=True)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    steps = args.scr_epochs * max(1, int((st_tr.repeat_interleave(w.inj.shape[0]) == 0).sum().item()) // 8192)
+    del Xtr, Ytr
+    Xev, Yev, cm_ev, n1_ev, st_ev = scr_mod.dataset(s, sc, ev_topo, w.inj, args.scr_top_k)
+    del Xev
+    rep = scr_mod.evaluate(s, sc, ev_topo, w.inj, Yev, cm_ev, n1_ev, st_ev, args.scr_top_k)
+    # training GEMM work per step: forward 2BH(F + H + C), backward twice that (B = 8192 rows)
+    F, H, C = sc.F, sc.H, s.n_cont
+    flop = 3 * 2 * 8192 * H * (F + H + C) * steps
+    tfs = flop / t_train / 1e12
+    rep.update({"workload": "grid2000_screen_train200k_eval100k_T8_cont1000_mlp256", "train_topologies": args.scr_train,
+                "eval_topologies": args.scr_eval, "epochs": args.scr_epochs, "train_steps": steps,
+                "loss_first_last": [hist[0], hist[-1]] if hist else None, "data_s": t_data, "train_s": t_train,
+                "features": F, "hidden": H,
+                "roofline": {"bound": "tensor", "kernel": "training (k_gemm_bf16 forward / backward + Adam)",
+                             "achieved": tfs, "peak": peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")),
+                             "unit": "TFLOP/s", "frac": tfs / peaks.get("bf16_tflops_sustained",
+                                                                         peaks.get("bf16_tflops", 1800.0))}})
+    sc.close()
+    s.close()
+    return rep
+
 
 
 def _e2e(solver, w, lim, steps, warmup, lf):
@@ -623,7 +931,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="fp32,fp64")
+    ap.add_argument("--forms", default="fp32,bf16x3,fp64")
     ap.add_argument("--fp64-steps", type=int, default=0, help="timed steps of the FP64 form (0 = --steps)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -646,6 +954,21 @@ def main():
                     help="also time the FP32 solve with this many multi-outage sets; 0 = skip")
     ap.add_argument("--top-k", type=int, default=8,
                     help="also time the FP32 solve with the k worst N-1 cases per (topology, timestep); 0 = skip")
+    ap.add_argument("--configs", default="grid10000,cand,screen",
+                    help="further study shapes timed after the 500-bus line (comma separated from grid10000, cand, "
+                         "screen; 'none' skips them)")
+    ap.add_argument("--cand-topologies", type=int, default=100000)
+    ap.add_argument("--cand-steps", type=int, default=1)
+    ap.add_argument("--cand-form", default="fp32")
+    ap.add_argument("--cand-oracle", type=int, default=32, help="oracle sample of the candidate study (topologies)")
+    ap.add_argument("--g10k-topologies", type=int, default=50000)
+    ap.add_argument("--g10k-steps", type=int, default=3)
+    ap.add_argument("--g10k-forms", default="fp32,bf16x3")
+    ap.add_argument("--g10k-oracle", type=int, default=64, help="oracle sample of the 10,000-bus study (topologies)")
+    ap.add_argument("--scr-train", type=int, default=200000)
+    ap.add_argument("--scr-eval", type=int, default=100000)
+    ap.add_argument("--scr-epochs", type=int, default=40)
+    ap.add_argument("--scr-top-k", type=int, default=64)
     ap.add_argument("--gemm", default="",
                     help="only time the screener's tensor-core GEMM on comma-separated MxNxK shapes")
     args = ap.parse_args()

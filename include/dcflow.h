@@ -71,10 +71,19 @@ typedef struct {
                             contingencies only (compacted per topology, columns gathered from
                             the transposed factors): pays when a topology's splits island many
                             contingencies, costs about a tenth per block otherwise */
+  int32_t autotune;      /* 1 = the first dcflow_solve_batch of every batch shape (timesteps,
+                            candidates, extra outputs) first tunes the schedule on a prefix of
+                            that batch (dcflow_autotune) and keeps the pick for the shape */
+  int32_t autotune_sample; /* topologies of that prefix; 0 = 2048 */
+  double tie_band;       /* worst_cont, worst_mon and best_var report the lowest position whose
+                            value lies within tie_band * max(|best|, 1) of the best value (an
+                            arg-max / arg-min up to the form's rounding); 0 = the form's
+                            tolerance (1e-10 FP64, 1e-4 FP32 and BF16x3), < 0 = none (exact
+                            ties only).  The screened solve reports the plain arg-max. */
 } dcflow_options;
 
 /* Fill `opt` with the defaults (FP32 form, current device, automatic chunk, 1e-9,
- * every contingency column). */
+ * every contingency column, no autotuning). */
 void dcflow_default_options(dcflow_options* opt);
 
 /*
@@ -297,6 +306,43 @@ int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* batch,
 
 /* Number of kernel launches issued by the last dcflow_solve_batch call. */
 int64_t dcflow_last_launch_count(const dcflow_ctx* ctx);
+
+/*
+ * Schedules.  The paper batches topologies of uneven depth by padding every
+ * topology to the deepest one (Sec. III-C); here the topologies of a batch are
+ * grouped by rank class (modifications per topology, padded to the class
+ * bound) and processed in chunks that alternate between two scratch sets, and
+ * the schedule below fixes how.  No choice changes the results beyond the
+ * rounding of the reduction order (the remainder choice) or the set of
+ * columns computed and then discarded (compact_n1).
+ */
+typedef struct {
+  int32_t budget_mb;      /* scratch per buffer set in MiB; sets the topologies per chunk
+                             (at most 8192; dcflow_options.chunk_topo > 0 overrides) */
+  int32_t rank_bounds[3]; /* rank classes: ascending upper bounds ending with 16, unused 0,
+                             e.g. {4, 8, 16}, {8, 16, 0} */
+  int32_t compact_n1;     /* FP32 / BF16x3 forms: as dcflow_options.compact_n1 */
+  int32_t remainder;      /* 1 = at most 4 contingencies beyond the last block of 64 are
+                             evaluated by the final pass instead of a block of their own */
+  float ms;               /* dcflow_autotune: measured time of one solve of the sample */
+} dcflow_schedule;
+
+/*
+ * Autotuner: time candidate schedules on `sample` (a batch the caller deems
+ * representative, e.g. a prefix of the real one) with CUDA events on `stream`
+ * (a warm-up and the best of two solves each, coordinate descent over the
+ * chunk budget, the rank classes, compact_n1 and the remainder), keep the
+ * fastest for batches of the sample's shape (timesteps, candidates, extra
+ * outputs), and report it in *pick (optional) and every schedule tried in
+ * tried[0 .. min(*n_tried, max_tried)) (optional).  `res` receives the
+ * sample's results (device buffers as for dcflow_solve_batch).  Synchronous.
+ */
+int dcflow_autotune(dcflow_ctx* ctx, const dcflow_batch* sample, const dcflow_results* res, void* stream,
+                    dcflow_schedule* tried, int32_t max_tried, int32_t* n_tried, dcflow_schedule* pick);
+/* Fix the schedule of every later solve (NULL: back to tuned / default schedules). */
+int dcflow_set_schedule(dcflow_ctx* ctx, const dcflow_schedule* s);
+/* The schedule the last dcflow_solve_batch used. */
+int dcflow_last_schedule(const dcflow_ctx* ctx, dcflow_schedule* out);
 
 /*
  * Kernel timing.  dcflow_profile(ctx, 1) resets the counters and makes every

@@ -355,6 +355,21 @@ def eligible_injections(inc, splits, inj_bus, cap=64):
     return el[:cap], buses
 
 
+def first_in_band(values, eps, lowest=False):
+    """The reported index of an arg-max (or, lowest=True, an arg-min) with a tie
+    band: the lowest index whose value lies within eps * max(|best|, 1) of the
+    best value.  eps = 0 is the plain arg-max / arg-min with ties to the lowest
+    index.  The band makes the reported index the same for two computations of
+    the same values that differ by less than the band (rounding of one
+    precision against another) whenever no value lies at the band's edge."""
+    v = np.asarray(values, np.float64)
+    if lowest:
+        best = v.min()
+        return int(np.nonzero(v <= best + eps * max(abs(best), 1.0))[0][0])
+    best = v.max()
+    return int(np.nonzero(v >= best - eps * max(abs(best), 1.0))[0][0])
+
+
 def classify_contingencies(cont, alive, br):
     """Which N-1 cases of one topology are solved (Def. 3 / Eq. (5) need
     1 - Phi[c, c] != 0): a contingency branch in service that is not a bridge
@@ -369,7 +384,7 @@ def classify_contingencies(cont, alive, br):
 
 def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
                       var=None, mode="lodf", want_flows=False, want_cmax=False, ti=None,
-                      split_bus=None, outage_cand=None):
+                      split_bus=None, outage_cand=None, tie_eps=0.0):
     """Outputs of one topology for every timestep (and variation).
 
     P: [T, V] injections.  var: (var_ptr, var_bus, var_delta) or None.
@@ -381,7 +396,12 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
     Returns a dict with per-timestep arrays: n0_max, n1_max, ovl, worst_cont,
     worst_mon, best_var, plus island status and n_island_cont (and n0 flows
     of the monitored branches if want_flows).  split_bus / outage_cand: the
-    study's switchable substations and outage candidates (build_topology)."""
+    study's switchable substations and outage candidates (build_topology).
+    tie_eps: the tie band of the reported indices (first_in_band): the worst
+    contingency is the lowest position whose maximum loading is within the
+    band of the largest, its worst monitored branch likewise within its
+    column, and the chosen candidate the lowest index within the band of the
+    smallest maximum loading."""
     V, f, t, b, slack = grid.n_bus, grid.f, grid.t, grid.b, grid.slack
     T = P.shape[0]
     M, C = len(mon), len(cont)
@@ -481,12 +501,13 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
         rho = np.abs(n1) / lim_mon[:, None]
         rho[diag_mask] = 0.0
         rho[~alive[mon], :] = 0.0
-        # ties: lowest contingency position, then lowest monitored position
-        flat = rho.T.reshape(-1)
-        k = int(np.argmax(flat))
-        jc, im = divmod(k, M)
+        # the worst contingency: the lowest position within the tie band of the largest
+        # per-contingency maximum, then its worst monitored branch within that column's band
+        cm = rho.max(axis=0)
+        jc = first_in_band(cm, tie_eps)
+        im = first_in_band(rho[:, jc], tie_eps)
         ovl = float(np.maximum(rho - 1.0, 0.0).sum())
-        return n0m, float(flat[k]), ovl, int(vj[jc]), int(im), (rho.max(axis=0), rho.argmax(axis=0))
+        return n0m, float(cm.max()), ovl, int(vj[jc]), int(im), (cm, rho.argmax(axis=0))
 
     for ti in range(T):
         if not nvar:
@@ -495,13 +516,13 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
             if want_flows:
                 res["n0_flow"][ti] = p[mon]
         else:
-            best = None
+            cand = []
             for u in range(nvar):
                 p = base_flows[:, ti] + dflow[:, ti, u]
-                r_u = metrics(p, Pn[:, ti] + dP[:, ti, u])
-                if best is None or r_u[1] < best[0][1]:
-                    best = (r_u, u, p)
-            r, u_best, p = best
+                cand.append((metrics(p, Pn[:, ti] + dP[:, ti, u]), p))
+            # Eq. (8): the candidate with the smallest maximum loading (lowest index within the tie band)
+            u_best = first_in_band([c[0][1] for c in cand], tie_eps, lowest=True)
+            r, p = cand[u_best]
             res["best_var"][ti] = u_best
             if want_flows:
                 res["n0_flow"][ti] = p[mon]
@@ -514,11 +535,12 @@ def evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
 
 
 def evaluate(grid, topo, P, mon, cont, limit, var=None, mode="lodf", idx=None,
-             want_flows=False, want_cmax=False, ti=None, split_bus=None, outage_cand=None):
+             want_flows=False, want_cmax=False, ti=None, split_bus=None, outage_cand=None, tie_eps=0.0):
     """Evaluate a batch of topologies (or the subset ``idx``); arrays per topology.
     ti: injection topologies as (ti_ptr [n_topo + 1], ti_mask, inj_bus, inj_p [T, n_inj]).
     split_bus / outage_cand: the study's switchable substations and outage
-    candidates (None: every bus / branch); a topology outside them is INVALID."""
+    candidates (None: every bus / branch); a topology outside them is INVALID.
+    tie_eps: the tie band of the reported indices (evaluate_topology)."""
     inc = incident_lists(grid.n_bus, grid.f, grid.t)
     sb = None if split_bus is None else {int(x) for x in split_bus}
     oc = None if outage_cand is None else {int(x) for x in outage_cand}
@@ -538,12 +560,13 @@ def evaluate(grid, topo, P, mon, cont, limit, var=None, mode="lodf", idx=None,
             tp, tm, ib, ip = ti
             tti = ([int(x) for x in tm[tp[i]:tp[i + 1]]], ib, ip)
         outs.append(evaluate_topology(grid, inc, splits, outages, P, mon, cont, limit,
-                                      vtuple, mode, want_flows, want_cmax, tti, sb, oc))
+                                      vtuple, mode, want_flows, want_cmax, tti, sb, oc, tie_eps))
     keys = ["n0_max", "n1_max", "ovl", "worst_cont", "worst_mon", "best_var"]
     r = {k: np.stack([o[k] for o in outs]) if outs else np.zeros((0, P.shape[0])) for k in keys}
     r["status"] = np.array([o["status"] for o in outs], np.int64)
     r["n_island_cont"] = np.array([o["n_island_cont"] for o in outs], np.int64)
     r["n_valid_cont"] = np.array([o["n_valid_cont"] for o in outs], np.int64)
+    r["tie_eps"] = float(tie_eps)
     if want_flows:
         r["n0_flow"] = np.stack([o["n0_flow"] for o in outs]) if outs else np.zeros((0, P.shape[0], len(mon)))
     if want_cmax:

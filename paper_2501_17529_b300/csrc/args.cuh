@@ -58,6 +58,11 @@ struct Args {
   int c_rem;  // first contingency of a short remainder [c_rem, C_eff) left to the final pass
               // instead of an almost empty N-1 block (C_eff when there is none)
   const int* best_u;  // chosen injection candidate per (slot, timestep), or null
+  // per (slot, timestep, internal contingency) maximum loading in the working
+  // precision, -1 where skipped (read by the final pass's tie band), or null
+  void* cmr;
+  double tie_eps;       // tie band of the reported indices: eps * max(best, 1)
+  const int* cont_inv;  // caller's position -> internal contingency
   int* err;  // set to 1 by a kernel whose bounded wait expired
   // outputs
   dcflow_results out;

@@ -50,7 +50,7 @@ struct DevBuf {
 struct ChunkBufs {
   DevBuf ent_n, ent_s, ent_w, mod_ptr, q_info;
   DevBuf Kinv, alpha, Vt64, VtR, Zs, Zbf, ptil, meta, s, valid, nisl;
-  DevBuf pmax, parg, povl;
+  DevBuf pmax, parg, povl, cmr;
   // injection candidates: per (timestep, candidate) operands and screening maxima,
   // the chosen candidate per timestep and its operands
   DevBuf ptv, svv, pmaxv, pargv, povlv, bestu, ptb, sb;
@@ -63,7 +63,7 @@ struct ChunkBufs {
   DevBuf zcd, tiel, tirow, nel;
   void release_all() {
     DevBuf* b[] = {&ent_n, &ent_s, &ent_w, &mod_ptr, &q_info, &Kinv, &alpha, &Vt64, &VtR, &Zs, &Zbf, &ptil, &meta,
-                   &s, &valid, &nisl, &pmax, &parg, &povl, &ptv, &svv, &pmaxv, &pargv, &povlv, &bestu, &ptb, &sb,
+                   &s, &valid, &nisl, &pmax, &parg, &povl, &cmr, &ptv, &svv, &pmaxv, &pargv, &povlv, &bestu, &ptb, &sb,
                    &selmask, &sfb, &csel, &nsel, &work, &nwork, &mvt, &mw, &mflag, &zcd, &tiel, &tirow, &nel};
     for (auto* x : b) x->release();
   }
@@ -107,6 +107,29 @@ struct DeviceGuard {
   }
   ~DeviceGuard() {
     if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// The schedule of dcflow_solve_batch: how the topologies are grouped by rank
+// and chunked, and which N-1 variant runs.  The autotuner searches over these.
+struct SchedPlan {
+  int budget_mb = 2048;           // scratch per buffer set (two sets alternate); sets the chunk size
+  int bounds[3] = {4, 8, 16};     // rank classes: ascending upper bounds, the last 16; unused 0
+  int compact = 0;                // FP32 forms: N-1 over each topology's compacted valid contingencies
+  int remainder = 1;              // a short contingency remainder goes to the final pass
+};
+inline bool operator==(const SchedPlan& a, const SchedPlan& b) {
+  return a.budget_mb == b.budget_mb && a.bounds[0] == b.bounds[0] && a.bounds[1] == b.bounds[1] &&
+         a.bounds[2] == b.bounds[2] && a.compact == b.compact && a.remainder == b.remainder;
+}
+
+// What a tuned schedule is keyed on: the shape of a batch as far as it changes
+// the work per topology (timesteps, candidates, the extra outputs).
+struct ShapeKey {
+  int T = 0, U = 0, ti = 0, top_k = 0, gen = 0, multi = 0, mode = 0;
+  bool operator==(const ShapeKey& o) const {
+    return T == o.T && U == o.U && ti == o.ti && top_k == o.top_k && gen == o.gen && multi == o.multi &&
+           mode == o.mode;
   }
 };
 
@@ -168,6 +191,15 @@ struct dcflow_ctx {
   dcf::DevBuf err;         // int: set by a kernel whose bounded wait expired
   int64_t launches = 0;
   int64_t chunk_cap = 0;
+  // schedule: fixed by dcflow_set_schedule, else tuned per batch shape
+  // (dcflow_autotune, or automatically with opt.autotune), else the defaults
+  bool sched_fixed = false;
+  dcf::SchedPlan sched;
+  std::vector<std::pair<dcf::ShapeKey, dcf::SchedPlan>> tuned;
+  bool tuning = false;  // inside the autotuner: the plan below is forced
+  dcf::SchedPlan tune_plan;
+  dcf::SchedPlan last_plan;  // the schedule of the last solve
+  int last_uc = 0;           // candidates per (topology, timestep) of the last solve
   // kernel timing (dcflow_profile)
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop) per timed launch

@@ -7,16 +7,17 @@
 //   build   every thread builds RB rows of one contingency's Phi_f column
 //           (FFMA2 over row pairs) into s_ph[row pair][contingency] and the
 //           block transposes p_f into s_pt[row pair][timestep] (float2 pairs);
-//   compute thread (cg, tg) owns contingencies cg + 16 i (i < 4) and
-//           timesteps TR tg .. TR tg + TR - 1: per row pair four LDS.64 of
-//           Phi_f pairs and the p_f pairs of its timesteps feed 4 TR packed
-//           FFMA2 (two rows each) and 4 TR three-input |max| (folding both
+//   compute thread (cg, tg) owns contingencies cg + CG i (i < CR; CR = 2 or 4,
+//           CG = 64 / CR) and timesteps TR tg .. TR tg + TR - 1: per row pair
+//           CR LDS.64 of Phi_f pairs and the p_f pairs of its timesteps (float4
+//           loads, two timesteps each, where TR is even) feed CR TR packed
+//           FFMA2 (two rows each) and CR TR three-input |max| (folding both
 //           rows), i.e. one FP32 issue slot per N-1 entry;
 //   overload the (contingency, timestep) items whose tile maximum exceeds 1
-//           are queued per warp, one ballot per item class (so the lanes of
-//           a serving round read consecutive contingencies: no bank
-//           conflicts), and their 16 entries recomputed with the
-//           saturating-FMA overload term.
+//           are marked in a bit mask per thread, queued per warp (a prefix sum
+//           of the mask counts over the lanes places each lane's items), and
+//           their 16 entries recomputed by all lanes with the saturating-FMA
+//           overload term.
 // SEL (a per-topology contingency list): block (cb, q) takes the cb-th 64
 // contingencies of topology q's list, either from a work list (the learned
 // screener's selection: one work item per block) or from the grid itself
@@ -72,8 +73,10 @@ template <int TT>
 struct RegTile {
   static constexpr int NTH = TT >= 24 ? 2 : 1;  // 64 NTH threads
   static constexpr int NT = kCB * NTH;
-  static constexpr int CR = 4;                  // contingencies per thread
-  static constexpr int CG = kCB / CR;           // 16 contingency groups
+  // contingencies per thread: 2 where it makes the timesteps per thread even
+  // (float4 loads of the transposed p_f cover two timesteps), else 4
+  static constexpr int CR = (TT == 24 || TT == 8) ? 2 : 4;
+  static constexpr int CG = kCB / CR;           // contingency groups
   static constexpr int TG = NT / CG;            // timestep groups
   static constexpr int TR = TT / TG;            // timesteps per thread
   static constexpr int RB = kLT / NTH;          // tile rows built per thread
@@ -167,7 +170,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
   const int bl = tid % kCB, bth = tid / kCB;
   const int bc = s_ci[bl];
   const int bdrow = bc >= 0 ? a.mpos[bc] : -1;  // monitored row of its own branch (LODF[c, c] = -1)
-  // compute role: contingencies c0 + cg + 16 i, timesteps TR tg + j
+  // compute role: contingencies c0 + cg + CG i, timesteps TR tg + j
   constexpr int TP = L::kTP, SP = L::kSP;
   const int cg = tid % R::CG, tg = tid / R::CG;
   if constexpr (!TC) {
@@ -415,21 +418,35 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
 #pragma unroll
         for (int j = 0; j < TR; ++j) mx[i][j] = fmaxf(mx[i][j], mt[i][j]);
       // overload sum only for the (contingency, timestep) items whose tile
-      // maximum exceeds 1: the warp queues them and serves the queue with all
-      // lanes (items of one tile are distinct (t, c) pairs: no write conflicts)
+      // maximum exceeds 1: every lane marks its items in a bit mask, a warp
+      // prefix sum of the mask counts places each lane's items in the warp's
+      // queue, and all lanes serve the queue (items of one tile are distinct
+      // (t, c) pairs: no write conflicts)
       const int lane = tid & 31;
-      const uint32_t lt = (1u << lane) - 1u;
       uint16_t* queue = reinterpret_cast<uint16_t*>(sm + L::kOffQ) + (tid >> 5) * 32 * CR * TR;
-      int n = 0;
+      static_assert(CR * TR <= 32, "item mask");
+      uint32_t hm = 0;
 #pragma unroll
       for (int i = 0; i < CR; ++i)
 #pragma unroll
-        for (int j = 0; j < TR; ++j) {
-          const bool hit = mt[i][j] > 1.0f;
-          const uint32_t m = __ballot_sync(0xffffffffu, hit);
-          if (hit) queue[n + __popc(m & lt)] = (uint16_t)((lane << 8) | (i * TR + j));
-          n += __popc(m);
+        for (int j = 0; j < TR; ++j) hm |= (mt[i][j] > 1.0f ? 1u : 0u) << (i * TR + j);
+      int n = 0;
+      if (__any_sync(0xffffffffu, hm != 0)) {
+        const int cnt = __popc(hm);
+        int incl = cnt;  // inclusive prefix over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += v;
         }
+        n = __shfl_sync(0xffffffffu, incl, 31);
+        int pos = incl - cnt;
+        while (hm) {
+          const int b = __ffs(hm) - 1;
+          queue[pos++] = (uint16_t)((lane << 8) | b);
+          hm &= hm - 1u;
+        }
+      }
       if (n) {
         __syncwarp();
         for (int jq = lane; jq < n; jq += 32) {
@@ -473,6 +490,13 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
       const int t = t0 + i / kCB, cl = i % kCB, c = s_ci[cl];
       if (t < T && c >= 0)
         a.out.n1_cont_max[((size_t)qi.tau * T + t) * C + a.cont_pos[c]] = okc[cl] ? s_s[(i / kCB) * SP + cl] : -1.f;
+    }
+  }
+  if (a.cmr) {  // the same in internal order for the final pass's tie band
+    for (int i = tid; i < TT * kCB; i += R::NT) {
+      const int t = t0 + i / kCB, cl = i % kCB, c = s_ci[cl];
+      if (t < T && c >= 0)
+        static_cast<float*>(a.cmr)[((size_t)q * T + t) * C + c] = okc[cl] ? s_s[(i / kCB) * SP + cl] : -1.f;
     }
   }
   for (int t = tid; t < TT; t += R::NT) {

@@ -298,6 +298,13 @@ __global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1
       if (t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t) * C + a.cont_pos[c]] = okv ? mx[tt] : -1.f;
     }
   }
+  if (a.cmr && cin) {  // the same for the final pass's tie band (internal order)
+#pragma unroll
+    for (int tt = 0; tt < TH; ++tt) {
+      const int t = t0 + th * TH + tt;
+      if (t < T) static_cast<float*>(a.cmr)[((size_t)q * T + t) * C + c] = okv ? mx[tt] : -1.f;
+    }
+  }
   __syncthreads();
   for (int t = tid; t < TT; t += kCB * NTH) {
     if (t0 + t >= T) continue;

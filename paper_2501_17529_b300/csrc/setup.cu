@@ -131,6 +131,9 @@ extern "C" void dcflow_default_options(dcflow_options* opt) {
   opt->chunk_topo = 0;
   opt->island_tol = 1e-9;
   opt->compact_n1 = 0;
+  opt->autotune = 0;
+  opt->autotune_sample = 0;
+  opt->tie_band = 0.0;
 }
 
 extern "C" int dcflow_setup(dcflow_ctx** out, int32_t n_bus, int32_t n_branch, const int32_t* from,
@@ -144,6 +147,7 @@ extern "C" int dcflow_setup(dcflow_ctx** out, int32_t n_bus, int32_t n_branch, c
   dcflow_default_options(&o);
   if (opt) o = *opt;
   if (o.island_tol <= 0) o.island_tol = 1e-9;
+  if (o.autotune_sample <= 0) o.autotune_sample = 2048;
   if (o.precision != DCFLOW_FP64 && o.precision != DCFLOW_FP32 && o.precision != DCFLOW_BF16X3) {
     set_error("dcflow_setup: unknown precision");
     return DCFLOW_ERR_INVALID_ARG;

@@ -708,6 +708,11 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
     for (int t = 0; t < TT; ++t)
       if (t0 + t < T) a.out.n1_cont_max[((size_t)qi.tau * T + t0 + t) * C + a.cont_pos[c]] = ok ? (float)mx[t] : -1.f;
   }
+  if (a.cmr && cin) {  // working-precision maxima for the final pass's tie band
+#pragma unroll
+    for (int t = 0; t < TT; ++t)
+      if (t0 + t < T) static_cast<Real*>(a.cmr)[((size_t)q * T + t0 + t) * C + c] = ok ? mx[t] : (Real)-1;
+  }
   __shared__ Real rv[2];  // maxima compared in the working precision (no FP64-pipe work in the FP32 form)
   __shared__ double ro[2];
   __shared__ int ra[2];
@@ -793,6 +798,25 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
   const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
   const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
   const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
+  // the short remainder of the contingency range (no N-1 block of its own): its
+  // Phi_f columns, built once with the N-1 kernels' arithmetic into shared memory
+  // ([column][monitored row]), then applied to every timestep below
+  extern __shared__ __align__(16) unsigned char fin_dyn[];
+  Real* s_rem = reinterpret_cast<Real*>(fin_dyn);
+  const int c_rem = nsel ? a.C_eff : a.c_rem, n_rem = a.C_eff - c_rem;
+  if (n_rem > 0) {
+    for (int i = tid; i < n_rem * M; i += blockDim.x) {
+      const int c = c_rem + i / M, l = i % M;
+      Real vt[RMAX], zr[RMAX];
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) {
+        vt[j] = VtR[(size_t)j * C + c];
+        zr[j] = Zs[(size_t)j * Mp + l];
+      }
+      s_rem[i] = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
+    }
+    __syncthreads();
+  }
   for (int t = tid >> 5; t < T; t += nw) {
     Real bv = (Real)-1;  // maxima compared in the working precision
     double ovl = 0.0;
@@ -817,23 +841,16 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
         ba = a2;
       }
     }
-    // the short remainder of the contingency range (no N-1 block of its own):
-    // each column over the monitored rows with the N-1 kernels' arithmetic
-    for (int c = nsel ? a.C_eff : a.c_rem; c < a.C_eff; ++c) {
+    // the remainder columns at this timestep
+    for (int c = c_rem; c < a.C_eff; ++c) {
       const bool okc = a.valid[(size_t)q * C + c];
       Real vr = (Real)0;
       double ov = 0.0;
       if (okc) {
-        Real vt[RMAX];
-#pragma unroll
-        for (int j = 0; j < RMAX; ++j) vt[j] = VtR[(size_t)j * C + c];
         const Real st = sv[(size_t)t * C + c];
+        const Real* ph = s_rem + (size_t)(c - c_rem) * M;
         for (int l = lane; l < M; l += 32) {
-          Real zr[RMAX];
-#pragma unroll
-          for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
-          const Real ph = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
-          const Real x = fabs(fma(ph, st, ptil[(size_t)t * Mp + l]));
+          const Real x = fabs(fma(ph[l], st, ptil[(size_t)t * Mp + l]));
           vr = fmax(vr, x);
           if (x > (Real)1) ov += (double)x - 1.0;
         }
@@ -849,8 +866,24 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       }
       if (lane == 0 && o.n1_cont_max)
         o.n1_cont_max[((size_t)tau * T + t) * C + a.cont_pos[c]] = okc ? (float)vr : -1.f;
+      if (lane == 0 && a.cmr) static_cast<Real*>(a.cmr)[((size_t)q * T + t) * C + c] = okc ? vr : (Real)-1;
     }
-    const int c = (ba == 0x7fffffff) ? -1 : ba;
+    int c = (ba == 0x7fffffff) ? -1 : ba;
+    if (c >= 0 && a.cmr && !nsel) {
+      // tie band: the lowest contingency position whose maximum loading lies within
+      // eps * max(best, 1) of the best (internal order is the caller's order up to
+      // the base-grid bridges, which are never valid)
+      __syncwarp();  // the remainder maxima written by lane 0 above
+      const Real* cr = static_cast<const Real*>(a.cmr) + ((size_t)q * T + t) * C;
+      const Real thr = bv - (Real)(a.tie_eps * fmax((double)bv, 1.0));
+      int pos = -1;
+      for (int p0 = 0; p0 < a.C_eff && pos < 0; p0 += 32) {
+        const int p = p0 + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, p < a.C_eff && cr[p] >= thr);
+        if (m) pos = p0 + __ffs(m) - 1;
+      }
+      if (pos >= 0) c = pos;  // the best itself lies in the band
+    }
     if (lane == 0) {
       const size_t k = (size_t)tau * T + t;
       o.n1_max_loading[k] = c >= 0 ? (double)bv : 0.0;
@@ -859,34 +892,31 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       if (o.best_var) o.best_var[k] = a.best_u ? a.best_u[(size_t)q * T + t] : -1;
     }
     if (o.worst_mon) {
-      Real v = (Real)-1;
+      // the worst contingency's column: its maximum, then the lowest monitored
+      // position within the tie band of that maximum
       int arg = 0x7fffffff;
       if (c >= 0) {
-        Real vr = (Real)-1;
         Real vt[RMAX];
 #pragma unroll
         for (int j = 0; j < RMAX; ++j) vt[j] = VtR[(size_t)j * C + c];
         const Real st = sv[(size_t)t * C + c];
-        for (int l = lane; l < M; l += 32) {
+        auto entry = [&](int l) {
           Real zr[RMAX];
 #pragma unroll
           for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
           const Real ph = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
-          const Real x = fabs(fma(ph, st, ptil[(size_t)t * Mp + l]));
-          if (x > vr) {
-            vr = x;
+          return fabs(fma(ph, st, ptil[(size_t)t * Mp + l]));
+        };
+        Real v = (Real)-1;
+        for (int l = lane; l < M; l += 32) v = fmax(v, entry(l));
+        for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+        const Real thr = v - (Real)(a.tie_eps * fmax((double)v, 1.0));
+        for (int l = lane; l < M; l += 32)
+          if (entry(l) >= thr) {
             arg = l;
+            break;
           }
-        }
-        v = vr;
-      }
-      for (int off = 16; off; off >>= 1) {
-        const Real v2 = __shfl_xor_sync(0xffffffffu, v, off);
-        const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
-        if (v2 > v || (v2 == v && a2 < arg)) {
-          v = v2;
-          arg = a2;
-        }
+        for (int off = 16; off; off >>= 1) arg = min(arg, __shfl_xor_sync(0xffffffffu, arg, off));
       }
       if (lane == 0) o.worst_mon[(size_t)tau * T + t] = (c >= 0) ? arg : -1;
     }
@@ -1077,28 +1107,26 @@ __global__ void k_var_select(Args av, int T, int U, int* __restrict__ best_u) {
     return;
   }
   const int TV = T * U;
-  Real bv = (Real)1e30;  // compared in the working precision
-  int bu = 0x7fffffff;
-  for (int u = lane; u < U; u += 32) {
+  auto cand_max = [&](int u) {  // the candidate's maximum loading over the contingency blocks
     Real v = (Real)-1;
     for (int b = 0; b < av.ncb; ++b) {
       const size_t k = ((size_t)q * TV + (size_t)t * U + u) * av.ncb + b;
       if (av.parg[k] >= 0) v = fmax(v, static_cast<const Real*>(av.pmax)[k]);
     }
-    if (v < (Real)0) v = (Real)0;  // no valid contingency: loading 0
-    if (v < bv || (v == bv && u < bu)) {
-      bv = v;
+    return v < (Real)0 ? (Real)0 : v;  // no valid contingency: loading 0
+  };
+  Real bv = (Real)1e30;  // compared in the working precision
+  for (int u = lane; u < U; u += 32) bv = fmin(bv, cand_max(u));
+  for (int off = 16; off; off >>= 1) bv = fmin(bv, __shfl_xor_sync(0xffffffffu, bv, off));
+  // Eq. (8): the lowest candidate index within the tie band of the smallest maximum
+  const Real thr = bv + (Real)(av.tie_eps * fmax((double)bv, 1.0));
+  int bu = 0x7fffffff;
+  for (int u = lane; u < U; u += 32)
+    if (cand_max(u) <= thr) {
       bu = u;
+      break;
     }
-  }
-  for (int off = 16; off; off >>= 1) {
-    const Real v2 = __shfl_xor_sync(0xffffffffu, bv, off);
-    const int u2 = __shfl_xor_sync(0xffffffffu, bu, off);
-    if (v2 < bv || (v2 == bv && u2 < bu)) {
-      bv = v2;
-      bu = u2;
-    }
-  }
+  for (int off = 16; off; off >>= 1) bu = min(bu, __shfl_xor_sync(0xffffffffu, bu, off));
   if (lane == 0) best_u[(size_t)q * T + t] = bu;
 }
 
@@ -1244,6 +1272,8 @@ __global__ void k_valid_compact(Args a, int* __restrict__ csel, int* __restrict_
     base += __popc(m);
     if (cm && c < a.C_eff && !v)
       for (int t = 0; t < T; ++t) cm[((size_t)qi.tau * T + t) * C + a.cont_pos[c]] = -1.f;
+    if (a.cmr && c < a.C_eff && !v)  // the tie band's maxima (FP32 forms): skipped
+      for (int t = 0; t < T; ++t) static_cast<float*>(a.cmr)[((size_t)q * T + t) * C + c] = -1.f;
   }
   if (lane == 0) nsel[q] = base;
 }
@@ -2155,11 +2185,24 @@ int launch_n1(const Args& a, int RMAX, int TT, dim3 grid, cudaStream_t st, int t
 }
 
 template <class Real>
-void launch_final(const Args& a, int RMAX, cudaStream_t st, const void* phicm, const int* nsel = nullptr) {
+int launch_final(const Args& a, int RMAX, cudaStream_t st, const void* phicm, const int* nsel = nullptr) {
   const Real* pc = static_cast<const Real*>(phicm);
-  if (RMAX == 4) k_final<Real, 4><<<a.nq, 128, 0, st>>>(a, nsel, pc);
-  else if (RMAX == 8) k_final<Real, 8><<<a.nq, 128, 0, st>>>(a, nsel, pc);
-  else k_final<Real, 16><<<a.nq, 128, 0, st>>>(a, nsel, pc);
+  // the remainder columns' Phi_f entries in shared memory (at most 4 x M)
+  const size_t dyn = nsel ? 0 : (size_t)(a.C_eff - a.c_rem) * a.M * sizeof(Real);
+  static uint64_t attr[3] = {0, 0, 0};
+  const int big = 200 * 1024;
+  if (dyn > (size_t)big) return DCFLOW_ERR_INVALID_ARG;
+  if (RMAX == 4) {
+    if (dyn > 48 * 1024 && smem_attr_once(k_final<Real, 4>, big, attr[0]) != cudaSuccess) return DCFLOW_ERR_CUDA;
+    k_final<Real, 4><<<a.nq, 128, dyn, st>>>(a, nsel, pc);
+  } else if (RMAX == 8) {
+    if (dyn > 48 * 1024 && smem_attr_once(k_final<Real, 8>, big, attr[1]) != cudaSuccess) return DCFLOW_ERR_CUDA;
+    k_final<Real, 8><<<a.nq, 128, dyn, st>>>(a, nsel, pc);
+  } else {
+    if (dyn > 48 * 1024 && smem_attr_once(k_final<Real, 16>, big, attr[2]) != cudaSuccess) return DCFLOW_ERR_CUDA;
+    k_final<Real, 16><<<a.nq, 128, dyn, st>>>(a, nsel, pc);
+  }
+  return 0;
 }
 
 template <class Real, int RMAX>
@@ -2216,8 +2259,6 @@ void launch_multi_rows(const Args& a, int RMAX, int n_multi, const int* mptr, co
   else if (RMAX == 8) k_multi_rows<Real, 8, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
   else k_multi_rows<Real, 16, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
 }
-
-int rank_class(int r) { return r <= 4 ? 4 : (r <= 8 ? 8 : 16); }
 
 // per-topology r x r systems and row operands of one chunk
 template <class Real>
@@ -2309,6 +2350,19 @@ uint32_t host_float_key(float f) {
 }
 
 }  // namespace
+
+static int autotune_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_results* res, void* stream,
+                         std::vector<dcflow_schedule>* tried, dcf::SchedPlan* pick, float* pick_ms);
+
+static dcflow_schedule to_schedule(const dcf::SchedPlan& P, float ms) {
+  dcflow_schedule o{};
+  o.budget_mb = P.budget_mb;
+  for (int i = 0; i < 3; ++i) o.rank_bounds[i] = P.bounds[i];
+  o.compact_n1 = P.compact;
+  o.remainder = P.remainder;
+  o.ms = ms;
+  return o;
+}
 
 static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_results* res, void* stream,
                       const ScreenCall* sc) {
@@ -2408,6 +2462,46 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     set_error("dcflow_solve_batch: the screener runs without injection candidates");
     return DCFLOW_ERR_INVALID_ARG;
   }
+  // the schedule: forced while tuning, fixed by the caller, tuned for this batch shape, or the defaults
+  SchedPlan plan;
+  plan.compact = ctx->opt.compact_n1 ? 1 : 0;
+  {
+    ShapeKey key;
+    key.T = T;
+    key.U = Uc;
+    key.ti = TI;
+    key.top_k = top_k;
+    key.gen = G;
+    key.multi = want_multi;
+    key.mode = mode;
+    bool found = false;
+    if (ctx->tuning) {
+      plan = ctx->tune_plan;
+      found = true;
+    } else if (ctx->sched_fixed) {
+      plan = ctx->sched;
+      found = true;
+    } else {
+      for (const auto& kv : ctx->tuned)
+        if (kv.first == key) {
+          plan = kv.second;
+          found = true;
+        }
+    }
+    if (!found && ctx->opt.autotune && mode == kModeFull) {
+      // tune on a prefix of this batch (the CSR prefixes are the first topologies' lists)
+      dcflow_batch pre = *bt;
+      pre.n_topo = std::min(N, std::max(1, ctx->opt.autotune_sample));
+      SchedPlan pk;
+      float ms = 0.f;
+      const int rc = autotune_impl(ctx, &pre, res, stream, nullptr, &pk, &ms);
+      if (rc) return rc;
+      plan = pk;  // autotune_impl stored it under this key
+    }
+  }
+  ctx->last_plan = plan;
+  ctx->last_uc = Uc;
+  ctx->launches = 0;
   int R = 0;
   if (U > 0) {
     if (!bt->var_ptr || !bt->var_bus || !bt->var_delta || (int64_t)T * U > (1 << 20)) {
@@ -2490,16 +2584,26 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   }
   std::vector<int> perm;
   perm.reserve(N);
-  std::vector<int> cls_start(4, 0);
-  const int classes[3] = {4, 8, 16};
-  for (int ci = 0; ci < 3; ++ci) {
+  // rank classes of the schedule (ascending bounds, the last 16): a topology of rank r
+  // goes to the first class whose bound is at least r
+  int classes[3] = {16, 16, 16};
+  int ncls = 0;
+  for (int i = 0; i < 3; ++i)
+    if (plan.bounds[i] > 0) classes[ncls++] = plan.bounds[i];
+  std::vector<int> cls_start(ncls + 1, 0);
+  auto class_of = [&](int r) {
+    for (int ci = 0; ci < ncls; ++ci)
+      if (r <= classes[ci]) return ci;
+    return ncls - 1;
+  };
+  for (int ci = 0; ci < ncls; ++ci) {
     cls_start[ci] = (int)perm.size();
     for (int i = 0; i < N; ++i) {
       const int r = hr[i] < 0 ? 0 : hr[i];
-      if (rank_class(r) == classes[ci]) perm.push_back(i);
+      if (class_of(r) == ci) perm.push_back(i);
     }
   }
-  cls_start[3] = N;
+  cls_start[ncls] = N;
   if (ctx->perm.ensure(sizeof(int) * N)) return DCFLOW_ERR_OOM;
   DCF_CUDA(cudaMemcpyAsync(ctx->perm.p, perm.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
   // chunk capacity from a scratch budget per buffer set (two sets alternate);
@@ -2508,12 +2612,13 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   // memory, so preparation kernels of the next chunk only run in its tail)
   const int C_eff = ctx->C_eff;       // contingencies that can be valid (base-grid bridges excluded)
   // FP32 full solve on request: the N-1 kernel runs over each topology's compacted valid contingencies
-  const bool cmp = !fp64 && mode == kModeFull && C_eff > 0 && ctx->opt.compact_n1;
+  const bool cmp = !fp64 && mode == kModeFull && C_eff > 0 && plan.compact;
   // a remainder of at most kRemCols contingencies beyond the last full block of 64
   // goes to the final pass (a column each over the monitored rows) instead of an
   // N-1 block that would compute 64 columns for it (plain full solves only)
   constexpr int kRemCols = 4;
-  const bool use_rem = mode == kModeFull && Uc == 0 && !cmp && C_eff > 64 && C_eff % 64 > 0 && C_eff % 64 <= kRemCols;
+  const bool use_rem = plan.remainder && mode == kModeFull && Uc == 0 && !cmp && C_eff > 64 && C_eff % 64 > 0 &&
+                       C_eff % 64 <= kRemCols && (size_t)(C_eff % 64) * M * rs <= 200 * 1024;
   const int ncb = use_rem ? C_eff / 64 : (C_eff + 63) / 64;  // 64-contingency blocks of the N-1 kernels
   const int Mp = (int)round_up(M, 16);
   const int TV = T * Uc;  // virtual timesteps: (timestep, candidate) pairs
@@ -2527,12 +2632,14 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                     (size_t)T * ncb * (rs + 4 + 8) + 64;
   if (TI) per_slot += (size_t)kRMax * C * rs + 64 * 8 + 4;
   if (tc) per_slot += (size_t)Mp * 16 * 4;  // BF16 hi / lo Z rows
+  if (mode == kModeFull) per_slot += (size_t)T * C * rs;  // per-contingency maxima (tie band)
   if (cmp) per_slot += (size_t)C * 4 + 4;
   if (Uc > 0)
     per_slot += (size_t)TV * (Mp + C) * rs + (size_t)TV * ncb * (rs + 4 + 8) + (size_t)T * 4 + (size_t)T * (Mp + C) * rs;
   const size_t SM_ = want_multi ? (size_t)ctx->n_multi : 0;
   per_slot += SM_ * ((4 * kRMax + 4 * (size_t)T) * rs + 4);
-  int64_t cap = ctx->opt.chunk_topo > 0 ? ctx->opt.chunk_topo : (int64_t)((size_t)2 << 30) / (int64_t)per_slot;
+  int64_t cap = ctx->opt.chunk_topo > 0 ? ctx->opt.chunk_topo
+                                         : (int64_t)(((size_t)std::max(plan.budget_mb, 1)) << 20) / (int64_t)per_slot;
   cap = std::max<int64_t>(1, std::min<int64_t>({cap, 8192, (int64_t)N}));
   for (int bi = 0; bi < 2; ++bi) {
     const size_t c = (size_t)cap;
@@ -2551,6 +2658,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     if (cmp && (B.csel.ensure(c * std::max(C, 1) * sizeof(int)) || B.nsel.ensure(c * sizeof(int))))
       return DCFLOW_ERR_OOM;
     if (tc && B.Zbf.ensure(c * Mp * 16 * 4)) return DCFLOW_ERR_OOM;
+    if (mode == kModeFull && B.cmr.ensure(c * T * std::max(C, 1) * rs)) return DCFLOW_ERR_OOM;
     if (TI && (B.zcd.ensure(c * kRMax * std::max(C, 1) * rs) || B.tiel.ensure(c * 64 * sizeof(int)) ||
                B.tirow.ensure(c * 64 * sizeof(int)) || B.nel.ensure(c * sizeof(int))))
       return DCFLOW_ERR_OOM;
@@ -2631,6 +2739,9 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   base.ncb = ncb;
   base.C_eff = C_eff;
   base.c_rem = use_rem ? ncb * 64 : C_eff;
+  // tie band of the reported indices: the form's tolerance unless the option sets one (negative: none)
+  base.tie_eps = ctx->opt.tie_band < 0 ? 0.0 : (ctx->opt.tie_band > 0 ? ctx->opt.tie_band : (fp64 ? 1e-10 : 1e-4));
+  base.cont_inv = ctx->cont_inv.as<int>();
   base.cont_pos = ctx->cont_pos.as<int>();
   base.Mpad = Mp;
   base.ldc = ctx->ldc;
@@ -2664,6 +2775,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     a.pmax = B.pmax.p;
     a.parg = B.parg.as<int>();
     a.povl = B.povl.as<double>();
+    a.cmr = mode == kModeFull ? B.cmr.p : nullptr;
     return a;
   };
   const int TT = pick_tt(T, fp64);
@@ -2730,18 +2842,18 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   struct Chunk {
     int cls, c0, nq;
   };
-  std::vector<Chunk> plan;
-  for (int ci = 0; ci < 3; ++ci)
+  std::vector<Chunk> chunks;
+  for (int ci = 0; ci < ncls; ++ci)
     for (int c0 = cls_start[ci]; c0 < cls_start[ci + 1]; c0 += (int)cap)
-      plan.push_back({ci, c0, std::min<int>((int)cap, cls_start[ci + 1] - c0)});
+      chunks.push_back({ci, c0, std::min<int>((int)cap, cls_start[ci + 1] - c0)});
   // two-stream pipeline: preparation of chunk i (decode, r x r systems, row
   // operands; FP64-heavy) on the side stream overlaps the N-1 and final
   // kernels of chunk i-1 (FP32) on the caller's stream
   cudaStream_t side = ctx->side;
   DCF_CUDA(cudaEventRecord(ctx->ev_ready, st));
   DCF_CUDA(cudaStreamWaitEvent(side, ctx->ev_ready, 0));
-  for (size_t i = 0; i < plan.size(); ++i) {
-    const Chunk& ch = plan[i];
+  for (size_t i = 0; i < chunks.size(); ++i) {
+    const Chunk& ch = chunks[i];
     const int bi = (int)(i & 1);
     ChunkBufs& B = ctx->bufs[bi];
     Args a = chunk_args(bi);
@@ -2813,6 +2925,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       Args av = a;
       av.T = TV;
       av.out.n1_cont_max = nullptr;
+      av.cmr = nullptr;  // the screening pass keeps no per-contingency maxima
       av.ptil = B.ptv.p;
       av.s = B.svv.p;
       av.pmax = B.pmaxv.p;
@@ -2913,8 +3026,14 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       int rc = run_n1(af, RMAX, T, true, cmp ? &B : nullptr);
       if (rc) return rc;
     }
-    if (fp64) launch_final<double>(af, RMAX, st, ctx->PhiCM.p, nsel_dev);
-    else launch_final<float>(af, RMAX, st, ctx->PhiCM.p, nsel_dev);
+    {
+      const int rcf = fp64 ? launch_final<double>(af, RMAX, st, ctx->PhiCM.p, nsel_dev)
+                           : launch_final<float>(af, RMAX, st, ctx->PhiCM.p, nsel_dev);
+      if (rcf) {
+        set_error("dcflow_solve_batch: final pass launch (remainder columns' shared memory)");
+        return rcf;
+      }
+    }
     ++ctx->launches;
     DCF_CHECK_LAUNCH();
     if (want_multi) {
@@ -2956,6 +3075,180 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
 
 extern "C" int dcflow_solve_batch(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_results* res, void* stream) {
   return solve_impl(ctx, bt, res, stream, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: coordinate descent over the schedule, each candidate timed on the
+// sample with CUDA events (a warm-up solve, then the best of two)
+// ---------------------------------------------------------------------------
+static int autotune_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_results* res, void* stream,
+                         std::vector<dcflow_schedule>* tried, SchedPlan* pick, float* pick_ms) {
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  DCF_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    set_error("dcflow_autotune: cudaEventCreate failed");
+    return DCFLOW_ERR_CUDA;
+  }
+  const bool prof = ctx->prof_on;
+  ctx->prof_on = false;  // tuning solves stay out of the kernel timers
+  const bool fp64 = ctx->opt.precision == DCFLOW_FP64;
+  int rc = 0;
+  auto time_plan = [&](const SchedPlan& P, float* ms) -> int {
+    ctx->tuning = true;
+    ctx->tune_plan = P;
+    int r = solve_impl(ctx, bt, res, stream, nullptr);  // warm-up: first-use allocations
+    float best = 3.4e38f;
+    for (int k = 0; k < 2 && !r; ++k) {
+      if (cudaEventRecord(e0, st) != cudaSuccess) r = DCFLOW_ERR_CUDA;
+      if (!r) r = solve_impl(ctx, bt, res, stream, nullptr);
+      if (!r && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        r = DCFLOW_ERR_CUDA;
+      float t = 0.f;
+      if (!r && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) r = DCFLOW_ERR_CUDA;
+      if (!r) best = std::min(best, t);
+    }
+    ctx->tuning = false;
+    *ms = best;
+    if (!r && tried) tried->push_back(to_schedule(P, best));
+    return r;
+  };
+  SchedPlan cur;
+  cur.compact = ctx->opt.compact_n1 ? 1 : 0;
+  float tcur = 0.f;
+  rc = time_plan(cur, &tcur);
+  // a candidate replaces the current schedule only when it is faster by more than 1 %
+  auto consider = [&](const SchedPlan& P) -> int {
+    if (P == cur) return 0;
+    float t = 0.f;
+    const int r = time_plan(P, &t);
+    if (!r && t < 0.99f * tcur) {
+      cur = P;
+      tcur = t;
+    }
+    return r;
+  };
+  // 1. scratch budget (chunk size): bounded by a third of the free device memory per set
+  size_t free_b = 0, total_b = 0;
+  if (!rc && cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) rc = DCFLOW_ERR_CUDA;
+  const int budgets[] = {512, 8192, 32768};
+  for (int b : budgets) {
+    if (rc) break;
+    if (((size_t)b << 20) * 3 > free_b) continue;
+    SchedPlan P = cur;
+    P.budget_mb = b;
+    rc = consider(P);
+  }
+  // 2. rank classes
+  const int bounds[][3] = {{8, 16, 0}, {4, 16, 0}, {16, 0, 0}};
+  for (const auto& bd : bounds) {
+    if (rc) break;
+    SchedPlan P = cur;
+    for (int i = 0; i < 3; ++i) P.bounds[i] = bd[i];
+    rc = consider(P);
+  }
+  // 3. dense or compacted N-1 (FP32 forms)
+  if (!rc && !fp64) {
+    SchedPlan P = cur;
+    P.compact = 1 - cur.compact;
+    rc = consider(P);
+  }
+  // 4. the contingency remainder in the final pass or in a block of its own (when there is one)
+  if (!rc && ctx->C_eff > 64 && ctx->C_eff % 64 > 0 && ctx->C_eff % 64 <= 4) {
+    SchedPlan P = cur;
+    P.remainder = 1 - cur.remainder;
+    rc = consider(P);
+  }
+  ctx->prof_on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  ShapeKey key;
+  key.T = bt->n_time;
+  key.U = bt->n_var;
+  key.ti = bt->ti_ptr != nullptr;
+  if (key.ti) key.U = ctx->last_uc;
+  key.top_k = res->top_k;
+  key.gen = bt->n_gen;
+  key.multi = res->multi_max_loading != nullptr;
+  key.mode = 0;
+  bool stored = false;
+  for (auto& kv : ctx->tuned)
+    if (kv.first == key) {
+      kv.second = cur;
+      stored = true;
+    }
+  if (!stored) ctx->tuned.push_back({key, cur});
+  if (pick) *pick = cur;
+  if (pick_ms) *pick_ms = tcur;
+  return DCFLOW_OK;
+}
+
+extern "C" int dcflow_autotune(dcflow_ctx* ctx, const dcflow_batch* sample, const dcflow_results* res, void* stream,
+                               dcflow_schedule* tried, int32_t max_tried, int32_t* n_tried, dcflow_schedule* pick) {
+  if (!ctx || !sample || !res || sample->n_topo < 1 || (tried && max_tried < 0)) {
+    set_error("dcflow_autotune: null argument or empty sample");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  if (ctx->tuning) {
+    set_error("dcflow_autotune: already tuning");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  std::vector<dcflow_schedule> all;
+  SchedPlan pk;
+  float ms = 0.f;
+  const int rc = autotune_impl(ctx, sample, res, stream, &all, &pk, &ms);
+  if (rc) return rc;
+  if (n_tried) *n_tried = (int32_t)all.size();
+  if (tried)
+    for (int i = 0; i < (int)all.size() && i < max_tried; ++i) tried[i] = all[i];
+  if (pick) *pick = to_schedule(pk, ms);
+  return DCFLOW_OK;
+}
+
+extern "C" int dcflow_set_schedule(dcflow_ctx* ctx, const dcflow_schedule* s) {
+  if (!ctx) {
+    set_error("dcflow_set_schedule: null context");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  if (!s) {
+    ctx->sched_fixed = false;
+    return DCFLOW_OK;
+  }
+  // bounds: ascending, from {4, 8, 16}, the last 16, then zeros
+  int prev = 0, last = 0;
+  bool ok = s->budget_mb > 0;
+  for (int i = 0; i < 3 && ok; ++i) {
+    const int b = s->rank_bounds[i];
+    if (b == 0) {
+      for (int j = i; j < 3; ++j) ok = ok && s->rank_bounds[j] == 0;
+      break;
+    }
+    ok = (b == 4 || b == 8 || b == 16) && b > prev;
+    prev = last = b;
+  }
+  if (!ok || last != 16) {
+    set_error("dcflow_set_schedule: budget_mb > 0 and rank_bounds ascending from {4, 8, 16} ending with 16");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  SchedPlan P;
+  P.budget_mb = s->budget_mb;
+  for (int i = 0; i < 3; ++i) P.bounds[i] = s->rank_bounds[i];
+  P.compact = s->compact_n1 ? 1 : 0;
+  P.remainder = s->remainder ? 1 : 0;
+  ctx->sched = P;
+  ctx->sched_fixed = true;
+  return DCFLOW_OK;
+}
+
+extern "C" int dcflow_last_schedule(const dcflow_ctx* ctx, dcflow_schedule* out) {
+  if (!ctx || !out) {
+    set_error("dcflow_last_schedule: null argument");
+    return DCFLOW_ERR_INVALID_ARG;
+  }
+  *out = to_schedule(ctx->last_plan, 0.f);
+  return DCFLOW_OK;
 }
 
 static int screen_matches(const dcflow_ctx* ctx, const dcflow_screen* s, const char* who) {

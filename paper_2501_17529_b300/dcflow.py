@@ -22,7 +22,18 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("device", c_int32), ("chunk_topo", c_int32),
-                ("island_tol", c_double), ("compact_n1", c_int32)]
+                ("island_tol", c_double), ("compact_n1", c_int32), ("autotune", c_int32),
+                ("autotune_sample", c_int32), ("tie_band", c_double)]
+
+
+class Schedule(ctypes.Structure):
+    """dcflow_schedule: chunk budget, rank classes, compacted N-1, remainder, measured ms."""
+    _fields_ = [("budget_mb", c_int32), ("rank_bounds", c_int32 * 3), ("compact_n1", c_int32),
+                ("remainder", c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"budget_mb": int(self.budget_mb), "rank_bounds": [int(x) for x in self.rank_bounds],
+                "compact_n1": int(self.compact_n1), "remainder": int(self.remainder), "ms": float(self.ms)}
 
 
 class Study(ctypes.Structure):
@@ -64,7 +75,8 @@ class ScreenReport(ctypes.Structure):
 
 EXPORTED = ["dcflow_default_options", "dcflow_setup", "dcflow_base_ptdf", "dcflow_base_ptdf_noalloc",
             "dcflow_set_study",
-            "dcflow_solve_batch", "dcflow_last_launch_count", "dcflow_profile", "dcflow_profile_read",
+            "dcflow_solve_batch", "dcflow_last_launch_count", "dcflow_autotune", "dcflow_set_schedule",
+            "dcflow_last_schedule", "dcflow_profile", "dcflow_profile_read",
             "dcflow_profile_read_kind",
             "dcflow_gemm_bf16",
             "dcflow_screen_create", "dcflow_screen_destroy", "dcflow_screen_dims", "dcflow_screen_features",
@@ -102,6 +114,13 @@ def load_library(path: str = LIB_PATH):
     lib.dcflow_solve_batch.restype = c_int32
     lib.dcflow_last_launch_count.argtypes = [c_void_p]
     lib.dcflow_last_launch_count.restype = c_int64
+    lib.dcflow_autotune.argtypes = [c_void_p, POINTER(Batch), POINTER(Results), c_void_p, POINTER(Schedule), c_int32,
+                                    POINTER(c_int32), POINTER(Schedule)]
+    lib.dcflow_autotune.restype = c_int32
+    lib.dcflow_set_schedule.argtypes = [c_void_p, POINTER(Schedule)]
+    lib.dcflow_set_schedule.restype = c_int32
+    lib.dcflow_last_schedule.argtypes = [c_void_p, POINTER(Schedule)]
+    lib.dcflow_last_schedule.restype = c_int32
     lib.dcflow_profile.argtypes = [c_void_p, c_int32]
     lib.dcflow_profile.restype = c_int32
     lib.dcflow_profile_read.argtypes = [c_void_p, POINTER(c_double), POINTER(c_int64)]
@@ -190,13 +209,16 @@ def dcflow_default_options() -> Options:
     return o
 
 
-def dcflow_setup(n_bus, f, t, b, slack, precision="fp32", device=-1, chunk_topo=0, island_tol=0.0, compact_n1=False):
+def dcflow_setup(n_bus, f, t, b, slack, precision="fp32", device=-1, chunk_topo=0, island_tol=0.0, compact_n1=False,
+                 autotune=False, autotune_sample=0):
     lib = load_library()
     o = dcflow_default_options()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.device = int(device)
     o.chunk_topo = int(chunk_topo)
     o.compact_n1 = int(bool(compact_n1))
+    o.autotune = int(bool(autotune))
+    o.autotune_sample = int(autotune_sample)
     if island_tol:
         o.island_tol = float(island_tol)
     fa, fp = _i32(f)
@@ -206,6 +228,37 @@ def dcflow_setup(n_bus, f, t, b, slack, precision="fp32", device=-1, chunk_topo=
     _check(lib.dcflow_setup(byref(ctx), int(n_bus), int(fa.size), fp, tp, bp, int(slack), byref(o)),
            "dcflow_setup")
     return ctx
+
+
+def dcflow_autotune(ctx, batch, results, stream=None, max_tried=32):
+    """Tune the schedule on `batch` (a Batch / Results pair of ctypes structs); returns (pick, tried) as dicts."""
+    tried = (Schedule * max_tried)()
+    n = c_int32(0)
+    pick = Schedule()
+    _check(load_library().dcflow_autotune(ctx, byref(batch), byref(results), _stream_ptr(stream), tried,
+                                          int(max_tried), byref(n), byref(pick)), "dcflow_autotune")
+    return pick.as_dict(), [tried[i].as_dict() for i in range(min(n.value, max_tried))]
+
+
+def dcflow_set_schedule(ctx, sched=None):
+    """Fix the schedule (a dict with budget_mb, rank_bounds, compact_n1, remainder) or, with None, release it."""
+    if sched is None:
+        _check(load_library().dcflow_set_schedule(ctx, None), "dcflow_set_schedule")
+        return
+    s = Schedule()
+    s.budget_mb = int(sched.get("budget_mb", 2048))
+    rb = list(sched.get("rank_bounds", [4, 8, 16])) + [0, 0, 0]
+    for i in range(3):
+        s.rank_bounds[i] = int(rb[i])
+    s.compact_n1 = int(sched.get("compact_n1", 0))
+    s.remainder = int(sched.get("remainder", 1))
+    _check(load_library().dcflow_set_schedule(ctx, byref(s)), "dcflow_set_schedule")
+
+
+def dcflow_last_schedule(ctx):
+    s = Schedule()
+    _check(load_library().dcflow_last_schedule(ctx, byref(s)), "dcflow_last_schedule")
+    return s.as_dict()
 
 
 def dcflow_base_ptdf(ctx, rows, out, stream=None):
@@ -511,10 +564,12 @@ class DeviceResults:
 class Solver:
     """One grid + study on the current CUDA device."""
 
-    def __init__(self, grid, precision="fp32", chunk_topo=0, island_tol=0.0, device=-1, compact_n1=False):
+    def __init__(self, grid, precision="fp32", chunk_topo=0, island_tol=0.0, device=-1, compact_n1=False,
+                 autotune=False, autotune_sample=0):
         self.grid = grid
         self.ctx = dcflow_setup(grid.n_bus, grid.f, grid.t, grid.b, grid.slack, precision=precision,
-                                device=device, chunk_topo=chunk_topo, island_tol=island_tol, compact_n1=compact_n1)
+                                device=device, chunk_topo=chunk_topo, island_tol=island_tol, compact_n1=compact_n1,
+                                autotune=autotune, autotune_sample=autotune_sample)
         self.n_mon = 0
         self.n_cont = 0
         self.n_multi = 0
@@ -544,6 +599,18 @@ class Solver:
                                        want_gen=dbatch.n_gen > 0, want_multi=want_multi)
         dcflow_solve_batch(self.ctx, dbatch.cstruct(), res.cstruct(), stream)
         return res
+
+    def autotune(self, dbatch: DeviceBatch, results: DeviceResults | None = None, stream=None):
+        """Tune the schedule on `dbatch` (kept for batches of its shape); returns (pick, tried)."""
+        res = results or DeviceResults(dbatch.n_topo, dbatch.n_time, self.n_mon, False,
+                                       dbatch.n_var > 0 or dbatch.has_ti, n_cont=self.n_cont)
+        return dcflow_autotune(self.ctx, dbatch.cstruct(), res.cstruct(), stream)
+
+    def set_schedule(self, sched=None):
+        dcflow_set_schedule(self.ctx, sched)
+
+    def last_schedule(self):
+        return dcflow_last_schedule(self.ctx)
 
     def solve_screened(self, dbatch: DeviceBatch, screener: "Screener", top_k=64, fallback_logit=float("inf"),
                        results: DeviceResults | None = None, want_pred=False, stream=None):

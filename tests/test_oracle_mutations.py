@@ -298,3 +298,29 @@ def test_loadflow_count_mutation_is_caught(monkeypatch, golden_dir, attr, fake):
     monkeypatch.setattr(ref, attr, fake)
     monkeypatch.setattr(oracle, attr, fake, raising=False)
     assert _fails(pins.test_loadflow_count_hand_counted, golden_dir)
+
+
+_orig_band = ref.first_in_band
+
+
+def _band_highest_index(values, eps, lowest=False):
+    v = np.asarray(values, np.float64)
+    best = v.min() if lowest else v.max()
+    ok = (v <= best + eps * max(abs(best), 1.0)) if lowest else (v >= best - eps * max(abs(best), 1.0))
+    return int(np.nonzero(ok)[0][-1])  # planted: the highest index inside the band
+
+
+def _band_without_scale(values, eps, lowest=False):
+    v = np.asarray(values, np.float64)
+    best = v.min() if lowest else v.max()
+    ok = (v <= best + eps) if lowest else (v >= best - eps)  # planted: band not scaled by max(|best|, 1)
+    return int(np.nonzero(ok)[0][0])
+
+
+@pytest.mark.parametrize("fake", [_band_highest_index, _band_without_scale])
+def test_tie_band_mutation_is_caught(monkeypatch, golden_dir, fake):
+    monkeypatch.setattr(ref, "first_in_band", fake)
+    monkeypatch.setattr(oracle, "first_in_band", fake)
+    caught = _fails(pins.test_first_in_band_hand_values) or \
+        _fails(pins.test_series_branches_tie_goes_to_the_lowest_position, golden_dir)
+    assert caught

@@ -766,3 +766,41 @@ def test_study_switching_sets_make_other_topologies_invalid(golden_dir):
     same = want != oracle.INVALID
     np.testing.assert_array_equal(r["n_valid_cont"][same], full["n_valid_cont"][same])
     np.testing.assert_array_equal(r["n1_max"][same], full["n1_max"][same])
+
+
+# --------------------------------------------------------------------------
+# tie band of the reported indices (worst contingency, worst branch, candidate)
+# --------------------------------------------------------------------------
+
+def test_first_in_band_hand_values():
+    f = oracle.first_in_band
+    assert f([0.5, 0.99999, 1.0], 1e-4) == 1
+    assert f([0.5, 0.99999, 1.0], 0.0) == 2
+    assert f([0.5, 1.0, 0.7, 1.0], 0.0) == 1          # exact ties: the lowest index
+    assert f([10.0, 9.9995, 3.0], 1e-4) == 0          # band scales with |best| above 1
+    assert f([9.9995, 10.0, 3.0], 1e-4) == 0
+    assert f([9.998, 10.0, 3.0], 1e-4) == 1
+    assert f([1.0, 0.5, 0.50001, 0.5], 1e-4, lowest=True) == 1
+    assert f([1.0, 0.50001, 0.5], 0.0, lowest=True) == 2
+
+
+def test_series_branches_tie_goes_to_the_lowest_position(golden_dir):
+    """On the 6-bus grid, branches 4 and 5 are in series through bus 4 (no
+    injection there): their outages give identical N-1 flows.  With a small
+    limit on the parallel branch 6, either outage is the worst case; inside the
+    tie band the reported contingency is the lower position in the caller's
+    contingency list, in either list order."""
+    d, g, _, _ = _count_case(golden_dir)
+    topo = synth.Topologies(np.array([0, 0], np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint64),
+                            np.array([0, 0], np.int32), np.zeros(0, np.int32))
+    P = np.zeros((1, 6))
+    P[0, 5], P[0, 1] = 1.0, -1.0
+    lim = np.full(7, 10.0)
+    lim[6] = 0.5
+    mon = np.arange(7, dtype=np.int32)
+    r = oracle.evaluate(g, topo, P, mon, np.arange(7, dtype=np.int32), lim, want_cmax=True, tie_eps=1e-9)
+    assert abs(r["cmax"][0, 0, 4] - r["cmax"][0, 0, 5]) < 1e-12 and r["cmax"][0, 0, 4] > r["cmax"][0, 0, 6]
+    assert r["worst_cont"][0, 0] == 4 and r["worst_mon"][0, 0] == 6
+    rev = np.arange(7, dtype=np.int32)[::-1].copy()
+    r2 = oracle.evaluate(g, topo, P, mon, rev, lim, tie_eps=1e-9)
+    assert r2["worst_cont"][0, 0] == 1  # branch 5 sits at position 1 of the reversed list
