@@ -44,12 +44,12 @@ WORKLOADS = {
 # 500-bus study (its summary sits under profiles/), keyed by the sha1 of the
 # kernel's source and of its argument block at the time of the capture
 N1_TRAFFIC = {
-    ("bc173a8d1288", "fp32"): {"bytes": 1.096e9, "per": "bench step of the 500-bus study (2 launches)",
-                               "how": "1,000-topology capture (626 + 374 topologies) scaled by topologies "
-                                      "per rank class to 6,233 + 3,767"},
-    ("bc173a8d1288", "fp32_compact"): {"bytes": 1.061e9, "per": "bench step of the 500-bus study (2 launches)",
-                                       "how": "1,000-topology capture (626 + 374 topologies) scaled by "
-                                              "topologies per rank class to 6,233 + 3,767"},
+    ("de42642cae77", "fp32"): {"bytes": 1.109e9, "per": "bench step of the 500-bus study",
+                               "how": "1,000-topology capture (626 + 374 topologies: 79.33 MB + 31.68 MB of DRAM "
+                                      "read + write) scaled by topologies per rank class to 6,233 + 3,767"},
+    ("de42642cae77", "bf16x3"): {"bytes": 1.167e9, "per": "bench step of the 500-bus study",
+                                 "how": "1,000-topology capture (626 + 374 topologies: 85.28 MB + 31.59 MB) scaled "
+                                        "by topologies per rank class to 6,233 + 3,767"},
 }
 
 
@@ -830,26 +830,44 @@ def run_cfg_screener(args, peaks):
     lim = _device_limits(w)
     s = Solver(w.grid, precision="fp32")
     s.set_study(w.mon, w.cont, lim, split_bus=w.subs)
-    sc = Screener(s, max_rows=8192, seed=1)
+    B = args.scr_batch
+    sc = Screener(s, max_rows=B, seed=1)
     t0 = time.perf_counter()
     Xtr, Ytr, _, _, st_tr = scr_mod.dataset(s, sc, w.topo, w.inj, args.scr_top_k)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    hist = scr_mod.train(sc, Xtr, Ytr, st_tr, w.inj.shape[0], args.scr_epochs, 8192, 2e-3, cosine=True)
+    hist = scr_mod.train(sc, Xtr, Ytr, st_tr, w.inj.shape[0], args.scr_epochs, B, args.scr_lr, cosine=True)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    steps = args.scr_epochs * max(1, int((st_tr.repeat_interleave(w.inj.shape[0]) == 0).sum().item()) // 8192)
+    steps = args.scr_epochs * max(1, int((st_tr.repeat_interleave(w.inj.shape[0]) == 0).sum().item()) // B)
     del Xtr, Ytr
+    # the probability threshold of the additions beyond the top k, calibrated on topologies held
+    # apart from both the training and the evaluation sets (seed 606) for 0.99 recall
+    cal_topo = synth.make_topologies(w.grid, w.subs, args.scr_cal, 606, (1, 8), (0, 0))
+    Xc, Yc, cm_c, n1_c, st_c = scr_mod.dataset(s, sc, cal_topo, w.inj, args.scr_top_k)
+    del Xc
+    p_min, cal_curve = scr_mod.calibrate_min_prob(s, sc, cal_topo, w.inj, Yc, cm_c, n1_c, st_c, args.scr_top_k)
+    del Yc, cm_c
     Xev, Yev, cm_ev, n1_ev, st_ev = scr_mod.dataset(s, sc, ev_topo, w.inj, args.scr_top_k)
     del Xev
-    rep = scr_mod.evaluate(s, sc, ev_topo, w.inj, Yev, cm_ev, n1_ev, st_ev, args.scr_top_k)
-    # training GEMM work per step: forward 2BH(F + H + C), backward twice that (B = 8192 rows)
+    rep = scr_mod.evaluate(s, sc, ev_topo, w.inj, Yev, cm_ev, n1_ev, st_ev, args.scr_top_k, min_prob=p_min)
+    rep["calibration"] = {"topologies": args.scr_cal, "target_recall": 0.99, "min_prob": p_min,
+                          "curve": [{"min_prob": p, "recall_evaluated": r, "evaluated_fraction": f}
+                                    for p, r, f in cal_curve]}
+    # the plain top k, and the recall / speed curve over larger selections
+    rep["curve"] = {}
+    for k, pm in ((args.scr_top_k, 0.0), (96, 0.0), (128, 0.0)):
+        r = scr_mod.evaluate(s, sc, ev_topo, w.inj, Yev, cm_ev, n1_ev, st_ev, k, repeats=2, min_prob=pm)
+        rep["curve"][f"top_{k}"] = {x: r[x] for x in ("recall_at_k", "recall_evaluated", "worst_cont_hit_rate",
+                                                       "evaluated_fraction", "speedup")}
+    # training GEMM work per step: forward 2BH(F + H + C), backward twice that (B rows)
     F, H, C = sc.F, sc.H, s.n_cont
-    flop = 3 * 2 * 8192 * H * (F + H + C) * steps
+    flop = 3 * 2 * B * H * (F + H + C) * steps
     tfs = flop / t_train / 1e12
     rep.update({"workload": "grid2000_screen_train200k_eval100k_T8_cont1000_mlp256", "train_topologies": args.scr_train,
-                "eval_topologies": args.scr_eval, "epochs": args.scr_epochs, "train_steps": steps,
+                "eval_topologies": args.scr_eval, "epochs": args.scr_epochs, "batch": B, "lr": args.scr_lr,
+                "train_steps": steps,
                 "loss_first_last": [hist[0], hist[-1]] if hist else None, "data_s": t_data, "train_s": t_train,
                 "features": F, "hidden": H,
                 "roofline": {"bound": "tensor", "kernel": "training (k_gemm_bf16 forward / backward + Adam)",
@@ -967,8 +985,11 @@ def main():
     ap.add_argument("--g10k-oracle", type=int, default=64, help="oracle sample of the 10,000-bus study (topologies)")
     ap.add_argument("--scr-train", type=int, default=200000)
     ap.add_argument("--scr-eval", type=int, default=100000)
-    ap.add_argument("--scr-epochs", type=int, default=40)
+    ap.add_argument("--scr-epochs", type=int, default=80)
+    ap.add_argument("--scr-batch", type=int, default=4096)
+    ap.add_argument("--scr-lr", type=float, default=1e-3)
     ap.add_argument("--scr-top-k", type=int, default=64)
+    ap.add_argument("--scr-cal", type=int, default=20000, help="calibration topologies of the screener")
     ap.add_argument("--gemm", default="",
                     help="only time the screener's tensor-core GEMM on comma-separated MxNxK shapes")
     args = ap.parse_args()

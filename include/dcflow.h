@@ -452,13 +452,19 @@ int dcflow_screen_adam_step(dcflow_screen* s, int64_t* t, int32_t set);
 typedef struct dcflow_screen_options {
   int32_t top_k;         /* contingencies kept per (topology, timestep) */
   float fallback_logit;  /* the full N-1 of a topology runs when a k-th score exceeds this (INFINITY: never) */
+  float min_prob;        /* every contingency whose predicted probability sigmoid(score) exceeds this
+                            is evaluated as well, beyond the top_k (0: none): the rows the network is
+                            unsure about get more */
 } dcflow_screen_options;
 
 typedef struct dcflow_screen_report {  /* device buffers, each optional */
   int32_t* n_eval;   /* [n_topo] contingencies evaluated exactly (bridges of the base grid, which
                         island every topology, are never evaluated) */
   uint8_t* fallback; /* [n_topo] 1 if the full N-1 ran */
-  int32_t* pred;     /* [n_topo * n_time * top_k] the top_k per row, ascending; -1 padding */
+  int32_t* pred;     /* [n_topo * n_time * top_k] the top_k per row, ascending; -1 padding (the
+                        min_prob additions are not listed) */
+  uint32_t* evaluated; /* [n_topo * ceil(n_cont / 32)] the evaluated set: bit c % 32 of word c / 32
+                          for the contingency at position c */
 } dcflow_screen_report;
 
 /* dcflow_solve_batch with the N-1 restricted, per topology, to the union over

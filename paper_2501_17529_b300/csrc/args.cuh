@@ -53,6 +53,7 @@ struct Args {
   void* pmax;
   int* parg;
   double* povl;
+  void* p2max;  // second largest per-contingency maximum of each block (the tie band's check), or null
   int ncb;    // 64-contingency blocks of the N-1 kernels (the stride of their partial results)
   int C_eff;  // contingencies before the base-grid bridges (internal order)
   int c_rem;  // first contingency of a short remainder [c_rem, C_eff) left to the final pass

@@ -7,17 +7,18 @@
 //   build   every thread builds RB rows of one contingency's Phi_f column
 //           (FFMA2 over row pairs) into s_ph[row pair][contingency] and the
 //           block transposes p_f into s_pt[row pair][timestep] (float2 pairs);
-//   compute thread (cg, tg) owns contingencies cg + CG i (i < CR; CR = 2 or 4,
-//           CG = 64 / CR) and timesteps TR tg .. TR tg + TR - 1: per row pair
-//           CR LDS.64 of Phi_f pairs and the p_f pairs of its timesteps (float4
-//           loads, two timesteps each, where TR is even) feed CR TR packed
-//           FFMA2 (two rows each) and CR TR three-input |max| (folding both
+//   compute thread (cg, tg) owns contingencies cg + 16 i (i < 4) and
+//           timesteps TR tg .. TR tg + TR - 1: per row pair four LDS.64 of
+//           Phi_f pairs and the p_f pairs of its timesteps feed 4 TR packed
+//           FFMA2 (two rows each) and 4 TR three-input |max| (folding both
 //           rows), i.e. one FP32 issue slot per N-1 entry;
 //   overload the (contingency, timestep) items whose tile maximum exceeds 1
-//           are marked in a bit mask per thread, queued per warp (a prefix sum
-//           of the mask counts over the lanes places each lane's items), and
-//           their 16 entries recomputed by all lanes with the saturating-FMA
-//           overload term.
+//           are queued per warp, one ballot per item class (so the lanes of
+//           a serving round read consecutive contingencies: no bank
+//           conflicts), and their 16 entries recomputed with the
+//           saturating-FMA overload term (a bit mask per thread with a warp
+//           prefix sum to place the items measured slower: its queue order
+//           groups a lane's items, and the serving reads then conflict).
 // SEL (a per-topology contingency list): block (cb, q) takes the cb-th 64
 // contingencies of topology q's list, either from a work list (the learned
 // screener's selection: one work item per block) or from the grid itself
@@ -73,9 +74,7 @@ template <int TT>
 struct RegTile {
   static constexpr int NTH = TT >= 24 ? 2 : 1;  // 64 NTH threads
   static constexpr int NT = kCB * NTH;
-  // contingencies per thread: 2 where it makes the timesteps per thread even
-  // (float4 loads of the transposed p_f cover two timesteps), else 4
-  static constexpr int CR = (TT == 24 || TT == 8) ? 2 : 4;
+  static constexpr int CR = 4;  // contingencies per thread (2 measured slower at 24 and 8 timesteps)
   static constexpr int CG = kCB / CR;           // contingency groups
   static constexpr int TG = NT / CG;            // timestep groups
   static constexpr int TR = TT / TG;            // timesteps per thread
@@ -114,8 +113,9 @@ struct RegLayout {
 };
 
 template <int TT, int RMAX, bool OVL, bool SEL = false, bool TC = false>
-__global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n1_reg(const __grid_constant__ N1Maps maps, Args a, int t0,
+__global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n1_reg(const __grid_constant__ N1Maps maps, Args a, int t0_base,
                                                             const SelArgs sel) {
+  const int t0 = t0_base + (int)blockIdx.z * TT;  // grid z: the passes over TT timesteps each
   using L = RegLayout<TT, RMAX, SEL, TC>;
   constexpr int PH = L::kPW;  // pitch (pairs) of s_ph
   using R = RegTile<TT>;
@@ -138,6 +138,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
           static_cast<float*>(a.pmax)[o2] = 0.f;
           a.parg[o2] = -1;
           a.povl[o2] = 0.0;
+          if (a.p2max) static_cast<float*>(a.p2max)[o2] = -1.f;
         }
       return;
     }
@@ -170,7 +171,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
   const int bl = tid % kCB, bth = tid / kCB;
   const int bc = s_ci[bl];
   const int bdrow = bc >= 0 ? a.mpos[bc] : -1;  // monitored row of its own branch (LODF[c, c] = -1)
-  // compute role: contingencies c0 + cg + CG i, timesteps TR tg + j
+  // compute role: contingencies c0 + cg + 16 i, timesteps TR tg + j
   constexpr int TP = L::kTP, SP = L::kSP;
   const int cg = tid % R::CG, tg = tid / R::CG;
   if constexpr (!TC) {
@@ -418,35 +419,21 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
 #pragma unroll
         for (int j = 0; j < TR; ++j) mx[i][j] = fmaxf(mx[i][j], mt[i][j]);
       // overload sum only for the (contingency, timestep) items whose tile
-      // maximum exceeds 1: every lane marks its items in a bit mask, a warp
-      // prefix sum of the mask counts places each lane's items in the warp's
-      // queue, and all lanes serve the queue (items of one tile are distinct
-      // (t, c) pairs: no write conflicts)
+      // maximum exceeds 1: the warp queues them and serves the queue with all
+      // lanes (items of one tile are distinct (t, c) pairs: no write conflicts)
       const int lane = tid & 31;
       uint16_t* queue = reinterpret_cast<uint16_t*>(sm + L::kOffQ) + (tid >> 5) * 32 * CR * TR;
-      static_assert(CR * TR <= 32, "item mask");
-      uint32_t hm = 0;
+      const uint32_t lt = (1u << lane) - 1u;
+      int n = 0;
 #pragma unroll
       for (int i = 0; i < CR; ++i)
 #pragma unroll
-        for (int j = 0; j < TR; ++j) hm |= (mt[i][j] > 1.0f ? 1u : 0u) << (i * TR + j);
-      int n = 0;
-      if (__any_sync(0xffffffffu, hm != 0)) {
-        const int cnt = __popc(hm);
-        int incl = cnt;  // inclusive prefix over the lanes
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += v;
+        for (int j = 0; j < TR; ++j) {
+          const bool hit = mt[i][j] > 1.0f;
+          const uint32_t m = __ballot_sync(0xffffffffu, hit);
+          if (hit) queue[n + __popc(m & lt)] = (uint16_t)((lane << 8) | (i * TR + j));
+          n += __popc(m);
         }
-        n = __shfl_sync(0xffffffffu, incl, 31);
-        int pos = incl - cnt;
-        while (hm) {
-          const int b = __ffs(hm) - 1;
-          queue[pos++] = (uint16_t)((lane << 8) | b);
-          hm &= hm - 1u;
-        }
-      }
       if (n) {
         __syncwarp();
         for (int jq = lane; jq < n; jq += 32) {
@@ -501,15 +488,18 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
   }
   for (int t = tid; t < TT; t += R::NT) {
     if (t0 + t >= T) continue;
-    float bv = -1.f;
+    float bv = -1.f, b2 = -1.f;  // the largest (lowest contingency on ties) and the second largest
     int ba = -1;
     double o = 0.0;
     for (int k2 = 0; k2 < kCB; ++k2) {
       if (!okc[k2]) continue;
       const float v = s_s[t * SP + k2];
       if (v > bv) {
+        b2 = bv;
         bv = v;
         ba = s_ci[k2];
+      } else if (v > b2) {
+        b2 = v;
       }
       o += (double)s_ov[t * SP + k2] * 1048576.0;
     }
@@ -517,6 +507,7 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
     static_cast<float*>(a.pmax)[o2] = bv;
     a.parg[o2] = ba;
     a.povl[o2] = o;
+    if (a.p2max) static_cast<float*>(a.p2max)[o2] = b2;
   }
 }
 

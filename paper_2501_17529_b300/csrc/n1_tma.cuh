@@ -99,7 +99,8 @@ __device__ __forceinline__ float max3abs(float a, float b, float c) {
 // OVL = false drops the overload sum (metric-first screening of injection
 // candidates needs only the maximum loading).
 template <int TT, int RMAX, int NTH, bool OVL>
-__global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1Maps maps, Args a, int t0) {
+__global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1Maps maps, Args a, int t0_base) {
+  const int t0 = t0_base + (int)blockIdx.z * TT;  // grid z: the passes over TT timesteps each
   using L = TmaLayout<TT, RMAX>;
   constexpr int TH = TT / NTH;    // timesteps per thread
   constexpr int RB = kLT / NTH;   // tile rows built per thread
@@ -308,15 +309,18 @@ __global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1
   __syncthreads();
   for (int t = tid; t < TT; t += kCB * NTH) {
     if (t0 + t >= T) continue;
-    float bv = -1.f;
+    float bv = -1.f, b2 = -1.f;  // the largest (lowest contingency on ties) and the second largest
     int ba = -1;
     double o = 0.0;
     for (int k2 = 0; k2 < kCB; ++k2) {
       if (!okc[k2]) continue;
       const float v = s_s[t * kCB + k2];
       if (v > bv) {
+        b2 = bv;
         bv = v;
         ba = c0 + k2;
+      } else if (v > b2) {
+        b2 = v;
       }
       o += (double)s_ov[t * kCB + k2] * 1048576.0;
     }
@@ -324,6 +328,7 @@ __global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1
     static_cast<float*>(a.pmax)[o2] = bv;
     a.parg[o2] = ba;
     a.povl[o2] = o;
+    if (a.p2max) static_cast<float*>(a.p2max)[o2] = b2;
   }
 }
 

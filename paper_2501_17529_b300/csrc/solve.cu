@@ -587,7 +587,8 @@ __device__ __forceinline__ Real phi_entry_r(Real base, const Real* zrow, const R
 // exceeds 1 (queued per warp), in the same order as a per-entry sum, and Phi_f
 // is built at the exact rank.
 template <class Real, int TT, int RMAX, int LT>
-__global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
+__global__ __launch_bounds__(64) void k_n1(Args a, int t0_base) {
+  const int t0 = t0_base + (int)blockIdx.z * TT;  // grid z: the passes over TT timesteps each
   const int q = blockIdx.y;
   const QInfo qi = a.qi[q];
   if (qi.status != ST_OK) return;
@@ -716,18 +717,22 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
   __shared__ Real rv[2];  // maxima compared in the working precision (no FP64-pipe work in the FP32 form)
   __shared__ double ro[2];
   __shared__ int ra[2];
+  __shared__ Real r2[2];
   const int lane = tid & 31, w = tid >> 5;
 #pragma unroll
   for (int t = 0; t < TT; ++t) {
     if (t0 + t < T) {  // uniform over the block
       Real v = ok ? mx[t] : (Real)-1;
+      Real w2 = (Real)-1;  // the second largest of the lanes merged so far
       int arg = ok ? c : 0x7fffffff;
       double o = ok ? (double)ov[t] * Acc<Real>::ovl_scale() : 0.0;
 #pragma unroll
       for (int off = 16; off; off >>= 1) {
         const Real v2 = __shfl_xor_sync(0xffffffffu, v, off);
+        const Real s2 = __shfl_xor_sync(0xffffffffu, w2, off);
         const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
         o += __shfl_xor_sync(0xffffffffu, o, off);
+        w2 = fmax(fmax(w2, s2), fmin(v, v2));
         if (v2 > v || (v2 == v && a2 < arg)) {
           v = v2;
           arg = a2;
@@ -737,11 +742,13 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
         rv[w] = v;
         ra[w] = arg;
         ro[w] = o;
+        r2[w] = w2;
       }
       __syncthreads();
       if (tid == 0) {
         Real bv = rv[0];
         int ba = ra[0];
+        const Real b2 = fmax(fmax(r2[0], r2[1]), fmin(rv[0], rv[1]));
         if (rv[1] > bv || (rv[1] == bv && ra[1] < ba)) {
           bv = rv[1];
           ba = ra[1];
@@ -750,6 +757,7 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
         static_cast<Real*>(a.pmax)[o2] = bv;
         a.parg[o2] = (bv < (Real)0) ? -1 : ba;
         a.povl[o2] = ro[0] + ro[1];
+        if (a.p2max) static_cast<Real*>(a.p2max)[o2] = b2;
       }
       __syncthreads();
     }
@@ -762,7 +770,8 @@ __global__ __launch_bounds__(64) void k_n1(Args a, int t0) {
 // the same arithmetic as the N-1 kernel, write every output of the topology
 // ---------------------------------------------------------------------------
 template <class Real, int RMAX>
-__global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ nsel, const Real* __restrict__ PhiCM) {
+__global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ nsel, const Real* __restrict__ PhiCM,
+                                               int col_room) {
   const int q = blockIdx.x;
   const QInfo qi = a.qi[q];
   const int tau = qi.tau, T = a.T, M = a.M, C = a.C, Mp = a.Mpad, tid = threadIdx.x;
@@ -804,6 +813,11 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
   extern __shared__ __align__(16) unsigned char fin_dyn[];
   Real* s_rem = reinterpret_cast<Real*>(fin_dyn);
   const int c_rem = nsel ? a.C_eff : a.c_rem, n_rem = a.C_eff - c_rem;
+  // the worst contingency of every timestep, and one Phi_f column (after the
+  // remainder columns) when the launch gave it room: the worst monitored branch
+  // of all timesteps that share a worst contingency comes from one column build
+  __shared__ int s_wc[256];
+  Real* s_col = col_room ? s_rem + (size_t)n_rem * M : nullptr;
   if (n_rem > 0) {
     for (int i = tid; i < n_rem * M; i += blockDim.x) {
       const int c = c_rem + i / M, l = i % M;
@@ -841,7 +855,8 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
         ba = a2;
       }
     }
-    // the remainder columns at this timestep
+    // the remainder columns at this timestep (their maxima kept for the tie band)
+    Real vrem[4] = {(Real)-1, (Real)-1, (Real)-1, (Real)-1};
     for (int c = c_rem; c < a.C_eff; ++c) {
       const bool okc = a.valid[(size_t)q * C + c];
       Real vr = (Real)0;
@@ -863,26 +878,47 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
           ba = c;
         }
         ovl += ov;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j == c - c_rem) vrem[j] = vr;
       }
       if (lane == 0 && o.n1_cont_max)
         o.n1_cont_max[((size_t)tau * T + t) * C + a.cont_pos[c]] = okc ? (float)vr : -1.f;
       if (lane == 0 && a.cmr) static_cast<Real*>(a.cmr)[((size_t)q * T + t) * C + c] = okc ? vr : (Real)-1;
     }
     int c = (ba == 0x7fffffff) ? -1 : ba;
-    if (c >= 0 && a.cmr && !nsel) {
+    if (c >= 0 && !nsel) {
       // tie band: the lowest contingency position whose maximum loading lies within
       // eps * max(best, 1) of the best (internal order is the caller's order up to
-      // the base-grid bridges, which are never valid)
-      __syncwarp();  // the remainder maxima written by lane 0 above
-      const Real* cr = static_cast<const Real*>(a.cmr) + ((size_t)q * T + t) * C;
+      // the base-grid bridges, which are never valid).  Each block's best within the
+      // band is a candidate; only a block whose second largest maximum also lies in
+      // the band needs the scan over the per-contingency maxima.
       const Real thr = bv - (Real)(a.tie_eps * fmax((double)bv, 1.0));
-      int pos = -1;
-      for (int p0 = 0; p0 < a.C_eff && pos < 0; p0 += 32) {
-        const int p = p0 + lane;
-        const unsigned m = __ballot_sync(0xffffffffu, p < a.C_eff && cr[p] >= thr);
-        if (m) pos = p0 + __ffs(m) - 1;
+      int cand = 0x7fffffff;
+      bool amb = a.p2max == nullptr;
+      for (int b = lane; b < nb; b += 32) {
+        const size_t k = ((size_t)q * T + t) * a.ncb + b;
+        const int ar = a.parg[k];
+        if (ar >= 0 && static_cast<const Real*>(a.pmax)[k] >= thr) cand = min(cand, ar);
+        if (a.p2max && static_cast<const Real*>(a.p2max)[k] >= thr) amb = true;
       }
-      if (pos >= 0) c = pos;  // the best itself lies in the band
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < n_rem && vrem[j] >= thr) cand = min(cand, c_rem + j);
+      for (int off = 16; off; off >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, off));
+      if (!__any_sync(0xffffffffu, amb)) {
+        c = cand;  // the best itself lies in the band
+      } else if (a.cmr) {
+        __syncwarp();  // the remainder maxima written by lane 0 above
+        const Real* cr = static_cast<const Real*>(a.cmr) + ((size_t)q * T + t) * C;
+        int pos = -1;
+        for (int p0 = 0; p0 < a.C_eff && pos < 0; p0 += 32) {
+          const int p = p0 + lane;
+          const unsigned m = __ballot_sync(0xffffffffu, p < a.C_eff && cr[p] >= thr);
+          if (m) pos = p0 + __ffs(m) - 1;
+        }
+        if (pos >= 0) c = pos;
+      }
     }
     if (lane == 0) {
       const size_t k = (size_t)tau * T + t;
@@ -891,7 +927,8 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       o.worst_cont[k] = c >= 0 ? a.cont_pos[c] : -1;  // the caller's position
       if (o.best_var) o.best_var[k] = a.best_u ? a.best_u[(size_t)q * T + t] : -1;
     }
-    if (o.worst_mon) {
+    if (lane == 0) s_wc[t] = c;
+    if (o.worst_mon && !s_col) {
       // the worst contingency's column: its maximum, then the lowest monitored
       // position within the tie band of that maximum
       int arg = 0x7fffffff;
@@ -920,6 +957,70 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       }
       if (lane == 0) o.worst_mon[(size_t)tau * T + t] = (c >= 0) ? arg : -1;
     }
+  }
+  if (!o.worst_mon || !s_col) return;
+  __syncthreads();
+  // per distinct worst contingency (block-uniform, timestep order): its Phi_f column
+  // once into shared memory, then every timestep with that worst contingency: one
+  // pass keeping each lane's two largest loadings decides the tie band unless some
+  // lane holds two values inside it (then a second pass finds the lowest position)
+  const int warp = tid >> 5;
+  for (int t0 = 0; t0 < T; ++t0) {
+    const int c = s_wc[t0];
+    bool first = true;
+    for (int t1 = 0; t1 < t0 && first; ++t1) first = s_wc[t1] != c;
+    if (!first) continue;
+    if (c < 0) {  // no valid contingency at these timesteps
+      for (int t = t0 + tid; t < T; t += blockDim.x)
+        if (s_wc[t] == c) o.worst_mon[(size_t)tau * T + t] = -1;
+      continue;
+    }
+    {
+      Real vt[RMAX];
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) vt[j] = VtR[(size_t)j * C + c];
+      for (int l = tid; l < M; l += blockDim.x) {
+        Real zr[RMAX];
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
+        s_col[l] = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
+      }
+    }
+    __syncthreads();
+    int k = 0;  // the matching timesteps, dealt out to the warps in turn
+    for (int t = t0; t < T; ++t) {
+      if (s_wc[t] != c) continue;
+      if ((k++ % nw) != warp) continue;
+      const Real st = sv[(size_t)t * C + c];
+      const Real* pt = ptil + (size_t)t * Mp;
+      Real v1 = (Real)-1, v2 = (Real)-1;
+      int i1 = 0x7fffffff;
+      for (int l = lane; l < M; l += 32) {
+        const Real x = fabs(fma(s_col[l], st, pt[l]));
+        if (x > v1) {
+          v2 = v1;
+          v1 = x;
+          i1 = l;
+        } else if (x > v2) {
+          v2 = x;
+        }
+      }
+      Real v = v1;
+      for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+      const Real thr = v - (Real)(a.tie_eps * fmax((double)v, 1.0));
+      int arg = v1 >= thr ? i1 : 0x7fffffff;
+      if (__any_sync(0xffffffffu, v2 >= thr)) {  // two candidates in one lane: its lowest in the band
+        arg = 0x7fffffff;
+        for (int l = lane; l < M; l += 32)
+          if (fabs(fma(s_col[l], st, pt[l])) >= thr) {
+            arg = l;
+            break;
+          }
+      }
+      for (int off = 16; off; off >>= 1) arg = min(arg, __shfl_xor_sync(0xffffffffu, arg, off));
+      if (lane == 0) o.worst_mon[(size_t)tau * T + t] = arg;
+    }
+    __syncthreads();  // before the next column overwrites s_col
   }
 }
 
@@ -1208,7 +1309,7 @@ __global__ void k_features(Args a, GridDev g, BatchDev in, const int* __restrict
 // k-th score still exceeds the fallback threshold.
 template <int NPL>
 __global__ void k_select(const QInfo* __restrict__ qinfo, int nq, int T, int C, const float* __restrict__ Z,
-                         int ldz, int k, uint32_t fb_key, uint32_t* __restrict__ selmask, int W,
+                         int ldz, int k, uint32_t fb_key, uint32_t min_key, uint32_t* __restrict__ selmask, int W,
                          uint8_t* __restrict__ fb, int32_t* __restrict__ pred) {
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -1235,7 +1336,9 @@ __global__ void k_select(const QInfo* __restrict__ qinfo, int nq, int T, int C, 
 #pragma unroll
   for (int i = 0; i < NPL; ++i) {
     const uint32_t b = __ballot_sync(0xffffffffu, sel[i]);
-    if (lane == 0 && b) atomicOr(&selmask[(size_t)q * W + i], b);
+    // the evaluated set: the top k, and every score above the minimum logit (not reported in pred)
+    const uint32_t bx = __ballot_sync(0xffffffffu, lane + 32 * i < C && key[i] > min_key);
+    if (lane == 0 && (b | bx)) atomicOr(&selmask[(size_t)q * W + i], b | bx);
     if (pr && sel[i]) pr[off + __popc(b & ((1u << lane) - 1u))] = lane + 32 * i;
     off += __popc(b);
   }
@@ -1281,7 +1384,8 @@ __global__ void k_valid_compact(Args a, int* __restrict__ csel, int* __restrict_
 __global__ void k_compact(const QInfo* __restrict__ qinfo, int nq, int C, int C_eff, const int* __restrict__ cont_inv,
                           int W, const uint32_t* __restrict__ selmask, const uint8_t* __restrict__ fb,
                           int* __restrict__ csel, int* __restrict__ nsel, int* __restrict__ work,
-                          int* __restrict__ nwork, int32_t* __restrict__ n_eval, uint8_t* __restrict__ fb_out) {
+                          int* __restrict__ nwork, int32_t* __restrict__ n_eval, uint8_t* __restrict__ fb_out,
+                          uint32_t* __restrict__ ev_out) {
   const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (q >= nq) return;
   const QInfo qi = qinfo[q];
@@ -1298,6 +1402,7 @@ __global__ void k_compact(const QInfo* __restrict__ qinfo, int nq, int C, int C_
         if (rem < 32) word &= (1u << rem) - 1u;
         for (uint32_t x = word; x; x &= x - 1u)  // base-grid bridges are never evaluated
           if (cont_inv[32 * w + __ffs(x) - 1] >= C_eff) word &= ~(1u << (__ffs(x) - 1));
+        if (ev_out) ev_out[(size_t)qi.tau * W + w] = word;  // the evaluated set, caller's positions
       }
       const int cnt = __popc(word);
       int incl = cnt;
@@ -1315,6 +1420,8 @@ __global__ void k_compact(const QInfo* __restrict__ qinfo, int nq, int C, int C_
       base += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
+  if (!ok && ev_out)  // islanded or invalid: nothing evaluated
+    for (int w = lane; w < W; w += 32) ev_out[(size_t)qi.tau * W + w] = 0u;
   if (lane == 0) {
     nsel[q] = base;
     const int nb = (base + 63) / 64;
@@ -2187,20 +2294,23 @@ int launch_n1(const Args& a, int RMAX, int TT, dim3 grid, cudaStream_t st, int t
 template <class Real>
 int launch_final(const Args& a, int RMAX, cudaStream_t st, const void* phicm, const int* nsel = nullptr) {
   const Real* pc = static_cast<const Real*>(phicm);
-  // the remainder columns' Phi_f entries in shared memory (at most 4 x M)
-  const size_t dyn = nsel ? 0 : (size_t)(a.C_eff - a.c_rem) * a.M * sizeof(Real);
+  // shared memory: the remainder columns' Phi_f entries (at most 4 x M), then one
+  // column for the worst monitored branches when it fits
+  const size_t rem = nsel ? 0 : (size_t)(a.C_eff - a.c_rem) * a.M * sizeof(Real);
+  const size_t big = 200 * 1024;
+  if (rem > big) return DCFLOW_ERR_INVALID_ARG;
+  const int col_room = rem + (size_t)a.M * sizeof(Real) <= big ? 1 : 0;
+  const size_t dyn = rem + (col_room ? (size_t)a.M * sizeof(Real) : 0);
   static uint64_t attr[3] = {0, 0, 0};
-  const int big = 200 * 1024;
-  if (dyn > (size_t)big) return DCFLOW_ERR_INVALID_ARG;
   if (RMAX == 4) {
-    if (dyn > 48 * 1024 && smem_attr_once(k_final<Real, 4>, big, attr[0]) != cudaSuccess) return DCFLOW_ERR_CUDA;
-    k_final<Real, 4><<<a.nq, 128, dyn, st>>>(a, nsel, pc);
+    if (dyn > 48 * 1024 && smem_attr_once(k_final<Real, 4>, (int)big, attr[0]) != cudaSuccess) return DCFLOW_ERR_CUDA;
+    k_final<Real, 4><<<a.nq, 128, dyn, st>>>(a, nsel, pc, col_room);
   } else if (RMAX == 8) {
-    if (dyn > 48 * 1024 && smem_attr_once(k_final<Real, 8>, big, attr[1]) != cudaSuccess) return DCFLOW_ERR_CUDA;
-    k_final<Real, 8><<<a.nq, 128, dyn, st>>>(a, nsel, pc);
+    if (dyn > 48 * 1024 && smem_attr_once(k_final<Real, 8>, (int)big, attr[1]) != cudaSuccess) return DCFLOW_ERR_CUDA;
+    k_final<Real, 8><<<a.nq, 128, dyn, st>>>(a, nsel, pc, col_room);
   } else {
-    if (dyn > 48 * 1024 && smem_attr_once(k_final<Real, 16>, big, attr[2]) != cudaSuccess) return DCFLOW_ERR_CUDA;
-    k_final<Real, 16><<<a.nq, 128, dyn, st>>>(a, nsel, pc);
+    if (dyn > 48 * 1024 && smem_attr_once(k_final<Real, 16>, (int)big, attr[2]) != cudaSuccess) return DCFLOW_ERR_CUDA;
+    k_final<Real, 16><<<a.nq, 128, dyn, st>>>(a, nsel, pc, col_room);
   }
   return 0;
 }
@@ -2289,6 +2399,7 @@ struct ScreenCall {
   dcflow_screen* scr = nullptr;
   int top_k = 64;
   float fallback_logit = 0.f;
+  float min_logit = 0.f;  // every score above it is evaluated too (INFINITY: none)
   const dcflow_screen_report* rep = nullptr;
   void* X = nullptr;  // features mode: rows tau * T + t, pitch ldx
   int64_t ldx = 0;
@@ -2330,16 +2441,17 @@ int launch_sel(const Args& a, const void* phicm, const ChunkBufs& B, int RMAX, i
   return launch_sel_r<Real, 16>(a, phicm, B, TT, grid, st, t0);
 }
 
-int launch_select(const Args& a, int T, int C, const float* Z, int ldz, int k, uint32_t fb_key, const ChunkBufs& B,
+int launch_select(const Args& a, int T, int C, const float* Z, int ldz, int k, uint32_t fb_key, uint32_t min_key,
+                  const ChunkBufs& B,
                   int W, int32_t* pred, cudaStream_t st) {
   const int64_t rows = (int64_t)a.nq * T;
   const unsigned grid = (unsigned)((rows * 32 + 255) / 256);
   uint32_t* mk = B.selmask.as<uint32_t>();
   uint8_t* fb = B.sfb.as<uint8_t>();
-  if (C <= 256) k_select<8><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, mk, W, fb, pred);
-  else if (C <= 512) k_select<16><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, mk, W, fb, pred);
-  else if (C <= 1024) k_select<32><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, mk, W, fb, pred);
-  else k_select<64><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, mk, W, fb, pred);
+  if (C <= 256) k_select<8><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, min_key, mk, W, fb, pred);
+  else if (C <= 512) k_select<16><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, min_key, mk, W, fb, pred);
+  else if (C <= 1024) k_select<32><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, min_key, mk, W, fb, pred);
+  else k_select<64><<<grid, 256, 0, st>>>(a.qi, a.nq, T, C, Z, ldz, k, fb_key, min_key, mk, W, fb, pred);
   return 0;
 }
 
@@ -2632,7 +2744,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
                     (size_t)T * ncb * (rs + 4 + 8) + 64;
   if (TI) per_slot += (size_t)kRMax * C * rs + 64 * 8 + 4;
   if (tc) per_slot += (size_t)Mp * 16 * 4;  // BF16 hi / lo Z rows
-  if (mode == kModeFull) per_slot += (size_t)T * C * rs;  // per-contingency maxima (tie band)
+  if (mode == kModeFull) per_slot += (size_t)T * C * rs + (size_t)T * ncb * rs;  // the tie band's maxima
   if (cmp) per_slot += (size_t)C * 4 + 4;
   if (Uc > 0)
     per_slot += (size_t)TV * (Mp + C) * rs + (size_t)TV * ncb * (rs + 4 + 8) + (size_t)T * 4 + (size_t)T * (Mp + C) * rs;
@@ -2658,7 +2770,9 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     if (cmp && (B.csel.ensure(c * std::max(C, 1) * sizeof(int)) || B.nsel.ensure(c * sizeof(int))))
       return DCFLOW_ERR_OOM;
     if (tc && B.Zbf.ensure(c * Mp * 16 * 4)) return DCFLOW_ERR_OOM;
-    if (mode == kModeFull && B.cmr.ensure(c * T * std::max(C, 1) * rs)) return DCFLOW_ERR_OOM;
+    if (mode == kModeFull && (B.cmr.ensure(c * T * std::max(C, 1) * rs) ||
+                              B.p2max.ensure(c * T * std::max(ncb, 1) * rs)))
+      return DCFLOW_ERR_OOM;
     if (TI && (B.zcd.ensure(c * kRMax * std::max(C, 1) * rs) || B.tiel.ensure(c * 64 * sizeof(int)) ||
                B.tirow.ensure(c * 64 * sizeof(int)) || B.nel.ensure(c * sizeof(int))))
       return DCFLOW_ERR_OOM;
@@ -2776,6 +2890,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     a.parg = B.parg.as<int>();
     a.povl = B.povl.as<double>();
     a.cmr = mode == kModeFull ? B.cmr.p : nullptr;
+    a.p2max = mode == kModeFull ? B.p2max.p : nullptr;
     return a;
   };
   const int TT = pick_tt(T, fp64);
@@ -2820,8 +2935,12 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       int rc = encode_maps(a, RMAX, Tn, TTn, maps);
       if (rc) return rc;
     }
-    for (int t0 = 0; t0 < Tn; t0 += TTn) {
-      const dim3 grid(ncb, a.nq);
+    // one launch per 65,535 passes: grid z runs the passes over TTn timesteps each
+    // (no tail between passes)
+    const int npass = (Tn + TTn - 1) / TTn;
+    for (int z0 = 0; z0 < npass; z0 += 65535) {
+      const int t0 = z0 * TTn;
+      const dim3 grid(ncb, a.nq, std::min(65535, npass - z0));
       const int pe = ctx->prof_begin(st);  // screening and full passes alike
       int rc;
       if (fp64) rc = launch_n1<double>(a, RMAX, TTn, grid, st, t0);
@@ -2926,6 +3045,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       av.T = TV;
       av.out.n1_cont_max = nullptr;
       av.cmr = nullptr;  // the screening pass keeps no per-contingency maxima
+      av.p2max = nullptr;
       av.ptil = B.ptv.p;
       av.s = B.svv.p;
       av.pmax = B.pmaxv.p;
@@ -2990,14 +3110,15 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       DCF_CUDA(cudaMemsetAsync(SB.sfb.p, 0, (size_t)ch.nq, st));
       DCF_CUDA(cudaMemsetAsync(SB.nwork.p, 0, 4, st));
       const dcflow_screen_report* rep = sc->rep;
-      launch_select(a, T, C, scr->iZ.as<float>(), Cp, sc->top_k, host_float_key(sc->fallback_logit), SB, W,
+      launch_select(a, T, C, scr->iZ.as<float>(), Cp, sc->top_k, host_float_key(sc->fallback_logit),
+                    host_float_key(sc->min_logit), SB, W,
                     rep ? rep->pred : nullptr, st);
       DCF_CHECK_LAUNCH();
       k_compact<<<(ch.nq * 32 + 255) / 256, 256, 0, st>>>(a.qi, ch.nq, C, C_eff, ctx->cont_inv.as<int>(), W,
                                                          SB.selmask.as<uint32_t>(),
                                                          SB.sfb.as<uint8_t>(), SB.csel.as<int>(), SB.nsel.as<int>(),
                                                          SB.work.as<int>(), SB.nwork.as<int>(),
-                                                         rep ? rep->n_eval : nullptr, rep ? rep->fallback : nullptr);
+                                                         rep ? rep->n_eval : nullptr, rep ? rep->fallback : nullptr, rep ? rep->evaluated : nullptr);
       DCF_CHECK_LAUNCH();
       ctx->launches += 6;
       const int TTs = pick_tt(T, fp64);
@@ -3294,6 +3415,9 @@ extern "C" int dcflow_solve_batch_screened(dcflow_ctx* ctx, const dcflow_batch* 
   sc.scr = s;
   sc.top_k = opt->top_k;
   sc.fallback_logit = opt->fallback_logit;
+  // probability threshold -> logit threshold (0 or out of (0, 1): no additions)
+  sc.min_logit = (opt->min_prob > 0.f && opt->min_prob < 1.f) ? std::log(opt->min_prob / (1.f - opt->min_prob))
+                                                                : INFINITY;
   sc.rep = rep;
   return solve_impl(ctx, bt, res, stream, &sc);
 }

@@ -66,11 +66,11 @@ class Results(ctypes.Structure):
 
 
 class ScreenOptions(ctypes.Structure):
-    _fields_ = [("top_k", c_int32), ("fallback_logit", ctypes.c_float)]
+    _fields_ = [("top_k", c_int32), ("fallback_logit", ctypes.c_float), ("min_prob", ctypes.c_float)]
 
 
 class ScreenReport(ctypes.Structure):
-    _fields_ = [("n_eval", c_void_p), ("fallback", c_void_p), ("pred", c_void_p)]
+    _fields_ = [("n_eval", c_void_p), ("fallback", c_void_p), ("pred", c_void_p), ("evaluated", c_void_p)]
 
 
 EXPORTED = ["dcflow_default_options", "dcflow_setup", "dcflow_base_ptdf", "dcflow_base_ptdf_noalloc",
@@ -613,17 +613,23 @@ class Solver:
         return dcflow_last_schedule(self.ctx)
 
     def solve_screened(self, dbatch: DeviceBatch, screener: "Screener", top_k=64, fallback_logit=float("inf"),
-                       results: DeviceResults | None = None, want_pred=False, stream=None):
-        """Screened N-1 (the union of each topology's top_k scored contingencies); returns (results, report)."""
+                       results: DeviceResults | None = None, want_pred=False, stream=None, min_prob=0.0,
+                       want_evaluated=False):
+        """Screened N-1 (the union of each topology's top_k scored contingencies, plus every contingency
+        predicted with a probability above min_prob); returns (results, report)."""
         import torch
         res = results or DeviceResults(dbatch.n_topo, dbatch.n_time, self.n_mon, n_cont=self.n_cont)
         N, T = dbatch.n_topo, dbatch.n_time
+        W = (self.n_cont + 31) // 32
         rep = {"n_eval": torch.empty(max(1, N), dtype=torch.int32, device="cuda"),
                "fallback": torch.empty(max(1, N), dtype=torch.uint8, device="cuda"),
-               "pred": (torch.empty(max(1, N * T * top_k), dtype=torch.int32, device="cuda") if want_pred else None)}
+               "pred": (torch.empty(max(1, N * T * top_k), dtype=torch.int32, device="cuda") if want_pred else None),
+               "evaluated": (torch.empty(max(1, N * W), dtype=torch.int32, device="cuda") if want_evaluated
+                             else None)}
         dcflow_solve_batch_screened(self.ctx, dbatch.cstruct(), res.cstruct(), screener.scr,
-                                    ScreenOptions(int(top_k), float(fallback_logit)),
-                                    ScreenReport(_ptr(rep["n_eval"]), _ptr(rep["fallback"]), _ptr(rep["pred"])),
+                                    ScreenOptions(int(top_k), float(fallback_logit), float(min_prob)),
+                                    ScreenReport(_ptr(rep["n_eval"]), _ptr(rep["fallback"]), _ptr(rep["pred"]),
+                                                 _ptr(rep["evaluated"])),
                                     stream)
         return res, rep
 

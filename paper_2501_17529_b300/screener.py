@@ -93,11 +93,14 @@ def recall_at_k(pred, Y, C):
 
 
 def evaluate(solver: Solver, screener: Screener, topo, inj, Y, cont_max, n1_exact, status, top_k=64,
-             fallback_logit=float("inf"), chunk=20000, repeats=3):
-    """Screened vs full N-1 on a held-out batch: recall, worst-contingency hits, error, timings."""
+             fallback_logit=float("inf"), chunk=20000, repeats=3, min_prob=0.0):
+    """Screened vs full N-1 on a held-out batch: recall, worst-contingency hits, error, timings
+    (repeats = 0: no timings).  min_prob: contingencies predicted above it are evaluated too."""
     import torch
     N, T, C = topo.n_topo, inj.shape[0], solver.n_cont
+    W = (C + 31) // 32
     pred = torch.empty((N * T, top_k), dtype=torch.int32, device="cuda")
+    evw = torch.empty((N, W), dtype=torch.int32, device="cuda")
     neval = torch.empty(N, dtype=torch.int32, device="cuda")
     fb = torch.empty(N, dtype=torch.uint8, device="cuda")
     n1s = torch.empty((N, T), dtype=torch.float64, device="cuda")
@@ -107,8 +110,10 @@ def evaluate(solver: Solver, screener: Screener, topo, inj, Y, cont_max, n1_exac
 
     def run_screened():
         for (a, b), db, r in zip(batches, dbs, ress):
-            _, rep = solver.solve_screened(db, screener, top_k, fallback_logit, results=r, want_pred=True)
+            _, rep = solver.solve_screened(db, screener, top_k, fallback_logit, results=r, want_pred=True,
+                                           min_prob=min_prob, want_evaluated=True)
             pred[a * T:b * T] = rep["pred"][:(b - a) * T * top_k].view(-1, top_k)
+            evw[a:b] = rep["evaluated"][:(b - a) * W].view(b - a, W)
             neval[a:b] = rep["n_eval"][:b - a]
             fb[a:b] = rep["fallback"][:b - a]
             n1s[a:b] = r.n1_max_loading[:(b - a) * T].view(b - a, T)
@@ -130,17 +135,18 @@ def evaluate(solver: Solver, screener: Screener, topo, inj, Y, cont_max, n1_exac
             best = min(best, e0.elapsed_time(e1) / 1e3)
         return best
 
-    t_full = timed(run_full)
-    t_scr = timed(run_screened)
+    if repeats > 0:
+        t_full = timed(run_full)
+        t_scr = timed(run_screened)
+    else:
+        run_screened()
+        t_full = t_scr = float("nan")
     ok = (status == 0).repeat_interleave(T)
     cm = cont_max.view(N * T, C)
     worst = torch.where(cm.max(dim=1).values > 0, cm.argmax(dim=1), torch.full_like(cm[:, 0], -1, dtype=torch.int64))
-    # evaluated set per topology: the union of its rows' predictions (all contingencies after a fallback)
-    ev = torch.zeros((N, C + 1), dtype=torch.bool, device="cuda")  # column C collects the -1 padding
-    pv = pred.view(N, T * top_k).long()
-    ev.scatter_(1, torch.where((pv >= 0) & (pv < C), pv, C), True)
-    ev = ev[:, :C]
-    ev[fb.bool()] = True
+    # evaluated set per topology, as the solver reports it (the union of its rows' selections)
+    bits = (evw.unsqueeze(2) >> torch.arange(32, device="cuda", dtype=torch.int32)) & 1
+    ev = bits.view(N, W * 32)[:, :C].bool()
     ev_rows = ev.repeat_interleave(T, dim=0)
     Yc = Y[:, :C].bool()
     okr = ok.view(-1, 1)
@@ -159,9 +165,24 @@ def evaluate(solver: Solver, screener: Screener, topo, inj, Y, cont_max, n1_exac
         "n1_max_rel_err_mean": float(rel.mean().item()) if rel.numel() else 0.0,
         "evaluated_fraction": float(neval[status == 0].float().mean().item()) / C,
         "fallback_fraction": float(fb[status == 0].float().mean().item()),
+        "min_prob": min_prob,
         "full_s": t_full, "screened_s": t_scr, "speedup": t_full / t_scr,
         "full_loadflows_per_s": lf_full / t_full, "screened_equiv_loadflows_per_s": lf_full / t_scr,
     }
+
+
+def calibrate_min_prob(solver: Solver, screener: Screener, topo, inj, Y, cont_max, n1_exact, status, top_k=64,
+                       target=0.99, probs=(0.5, 0.3, 0.2, 0.12, 0.08, 0.05, 0.03, 0.02, 0.01)):
+    """The largest probability threshold whose screened solve reaches `target` recall of the
+    evaluated set on a calibration batch (held apart from both the training and the held-out
+    topologies); returns (threshold, [(threshold, recall, evaluated fraction)])."""
+    curve = []
+    for p in probs:
+        r = evaluate(solver, screener, topo, inj, Y, cont_max, n1_exact, status, top_k, repeats=0, min_prob=p)
+        curve.append((p, r["recall_evaluated"], r["evaluated_fraction"]))
+        if r["recall_evaluated"] >= target:
+            return p, curve
+    return probs[-1], curve
 
 
 def _study():
