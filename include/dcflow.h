@@ -317,8 +317,8 @@ int64_t dcflow_last_launch_count(const dcflow_ctx* ctx);
  * columns computed and then discarded (compact_n1).
  */
 typedef struct {
-  int32_t budget_mb;      /* scratch per buffer set in MiB; sets the topologies per chunk
-                             (at most 8192; dcflow_options.chunk_topo > 0 overrides) */
+  int32_t budget_mb;      /* scratch per buffer set in MiB (default 8192); sets the topologies
+                             per chunk (at most 8192; dcflow_options.chunk_topo > 0 overrides) */
   int32_t rank_bounds[3]; /* rank classes: ascending upper bounds ending with 16, unused 0,
                              e.g. {4, 8, 16}, {8, 16, 0} */
   int32_t compact_n1;     /* FP32 / BF16x3 forms: as dcflow_options.compact_n1 */

@@ -113,7 +113,7 @@ struct DeviceGuard {
 // The schedule of dcflow_solve_batch: how the topologies are grouped by rank
 // and chunked, and which N-1 variant runs.  The autotuner searches over these.
 struct SchedPlan {
-  int budget_mb = 2048;           // scratch per buffer set (two sets alternate); sets the chunk size
+  int budget_mb = 8192;           // scratch per buffer set (two sets alternate); sets the chunk size
   int bounds[3] = {4, 8, 16};     // rank classes: ascending upper bounds, the last 16; unused 0
   int compact = 0;                // FP32 forms: N-1 over each topology's compacted valid contingencies
   int remainder = 1;              // a short contingency remainder goes to the final pass

@@ -3253,7 +3253,7 @@ static int autotune_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_r
   // 1. scratch budget (chunk size): bounded by a third of the free device memory per set
   size_t free_b = 0, total_b = 0;
   if (!rc && cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) rc = DCFLOW_ERR_CUDA;
-  const int budgets[] = {512, 8192, 32768};
+  const int budgets[] = {2048, 32768};
   for (int b : budgets) {
     if (rc) break;
     if (((size_t)b << 20) * 3 > free_b) continue;

@@ -246,7 +246,7 @@ def dcflow_set_schedule(ctx, sched=None):
         _check(load_library().dcflow_set_schedule(ctx, None), "dcflow_set_schedule")
         return
     s = Schedule()
-    s.budget_mb = int(sched.get("budget_mb", 2048))
+    s.budget_mb = int(sched.get("budget_mb", 8192))
     rb = list(sched.get("rank_bounds", [4, 8, 16])) + [0, 0, 0]
     for i in range(3):
         s.rank_bounds[i] = int(rb[i])
