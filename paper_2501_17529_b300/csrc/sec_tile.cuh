@@ -1,0 +1,442 @@
+// Register-tiled FP32 kernels of the generator-failure N-1 (Sec. III-A) and
+// the multi-outage N-1 (Def. 4, MODF).  Both evaluate, per topology, a set of
+// cases (a generator, a set of branches) against every monitored row and
+// timestep; like the fused N-1 kernel they keep one running |max| per
+// (case, timestep) cell in registers, fold two rows per packed multiply-add,
+// form a cell's overload sum only over the row tiles where its maximum exceeds
+// 1, and take the arg-max over the cases once at the end (the lowest case on
+// ties).  Included by solve.cu after the per-chunk argument block.
+#pragma once
+
+#include "args.cuh"
+
+namespace dcf {
+
+__device__ __forceinline__ float sec_max3abs(float a, float b, float c) {
+  float r;
+  asm("max.abs.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// overload term of one entry, x 2^-20: sat((|v| - 1) 2^-20) = max(0, |v| - 1) 2^-20
+__device__ __forceinline__ float sec_ovl(float v) { return __saturatef(fmaf(fabsf(v), 0x1p-20f, -0x1p-20f)); }
+
+// ---------------------------------------------------------------------------
+// generator failures: generator g at bus b with output P_g[t] fails, the slack
+// takes it up, and the flows become p_f - P_g PTDF_f[:, b] with
+//   PTDF_f[l, b] = PTDF[l, b] - Z[l, :] K^{-1} Sigma^T PTDF[:, b]   (Eq. (3)).
+// Block = one topology and one pass of TT = 8 TR timesteps (grid y); its 4
+// warps take the 32-row tiles w, w + 4, ...; the generators go in groups of
+// 16.  Lane (gq, tq) owns the cells (generator gq + 4 i, timestep TR tq + j),
+// i < 4, j < TR.  Per tile each lane forms its row's 16 columns
+// PTDF_f[l, b_g] / limit_l and copies its row of p_f / limit into the warp's
+// tile as row pairs; then every lane runs its cells over the 16 row pairs.
+// The column entries and the flows are the same multiply-adds as the
+// one-thread-per-row form, so every entry is bit-identical to it.
+// ---------------------------------------------------------------------------
+template <int TR>
+struct GenTile {
+  static constexpr int TT = 8 * TR, GG = 16, RT = 32, NW = 4;
+  static constexpr int CP = GG + 2;  // float2 pitch of a column row pair (16-byte rows for the paired loads)
+  static constexpr int TP = TT + 1;  // float2 pitch of a p_f row pair (spreads the lanes' stores over the banks)
+  static constexpr int NCELL = GG * TT;
+  static constexpr int kTiles = NW * (RT / 2) * (CP + TP) * 8;  // bytes of the warps' tiles
+};
+
+template <int RMAX, int TR>
+__global__ __launch_bounds__(128, 6) void k_gen_tile(Args a, int G, const int* __restrict__ gen_bus,
+                                                  const double* __restrict__ gen_p, const double* __restrict__ PtdfN,
+                                                  int V, const float* __restrict__ PG) {
+  using L = GenTile<TR>;
+  constexpr int TT = L::TT, GG = L::GG, RT = L::RT, NW = L::NW, CP = L::CP, TP = L::TP, NCELL = L::NCELL;
+  __shared__ __align__(16) unsigned char tiles[L::kTiles];  // per warp: columns, then p_f; after the loop: maxima
+  __shared__ float ov_s[NW][NCELL];  // overload sums x 2^-20 per warp and cell (written by the owner lane)
+  __shared__ double sv_s[kRMax][GG];
+  __shared__ float beta_s[GG][RMAX];
+  __shared__ int mp_s[kRMax + 1];
+  __shared__ float bv_s[TT];
+  __shared__ int bg_s[TT];
+  __shared__ double bo_s[TT];
+  static_assert(NW * NCELL * 4 <= L::kTiles, "maxima fit the tiles");
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int t0 = blockIdx.y * TT;
+  const QInfo qi = a.qi[q];
+  const int T = a.T, M = a.M, Mp = a.Mpad, tau = qi.tau;
+  const dcflow_results& o = a.out;
+  if (qi.status != ST_OK) {
+    for (int t = t0 + tid; t < T && t < t0 + TT; t += blockDim.x) {
+      o.gen_max_loading[(size_t)tau * T + t] = 0.0;
+      o.worst_gen[(size_t)tau * T + t] = -1;
+      o.gen_overload_sum[(size_t)tau * T + t] = 0.0;
+    }
+    return;
+  }
+  const int r = qi.r;
+  for (int i = tid; i <= r; i += blockDim.x) mp_s[i] = a.mod_ptr[(size_t)q * (kRMax + 1) + i];
+  for (int t = tid; t < TT; t += blockDim.x) {
+    bv_s[t] = -1.f;
+    bg_s[t] = -1;
+    bo_s[t] = 0.0;
+  }
+  const double* Kinv = a.Kinv + (size_t)q * kRMax * kRMax;
+  const float* Zs = static_cast<const float*>(a.Zs) + (size_t)q * kRMax * Mp;
+  const float* ptil = static_cast<const float*>(a.ptil) + (size_t)q * T * Mp;
+  const float* meta = static_cast<const float*>(a.diagv) + (size_t)q * 4 * Mp;
+  const int* en = a.ent_n + (size_t)q * kEntMax;
+  const int8_t* es = a.ent_s + (size_t)q * kEntMax;
+  float2* col_w = reinterpret_cast<float2*>(tiles) + w * (RT / 2) * CP;
+  float2* pt_w = reinterpret_cast<float2*>(tiles) + NW * (RT / 2) * CP + w * (RT / 2) * TP;
+  float* colf = reinterpret_cast<float*>(col_w);
+  float* ptf = reinterpret_cast<float*>(pt_w);
+  float* mx_s = reinterpret_cast<float*>(tiles);  // [NW][NCELL] after the tile loop
+  const int gq = lane & 3, tq = lane >> 2, pr = lane >> 1, hf = lane & 1;
+  const int ntile = (M + RT - 1) / RT;
+  for (int g0 = 0; g0 < G; g0 += GG) {
+    const int gn = min(GG, G - g0);
+    __syncthreads();  // mp_s ready; the previous group's maxima and sums consumed
+    // Sigma^T PTDF[:, b_g] per modification i (FP64), then K^{-1} times it
+    for (int p = tid; p < r * GG; p += blockDim.x) {
+      const int i = p / GG, g = p % GG;
+      double x = 0.0;
+      if (g < gn) {
+        const int b = gen_bus[g0 + g];
+        for (int e = mp_s[i]; e < mp_s[i + 1]; ++e) x = fma((double)es[e], PtdfN[(size_t)en[e] * V + b], x);
+      }
+      sv_s[i][g] = x;
+    }
+    for (int p = tid; p < NW * NCELL; p += blockDim.x) ov_s[p / NCELL][p % NCELL] = 0.f;
+    __syncthreads();
+    for (int p = tid; p < GG * RMAX; p += blockDim.x) {
+      const int g = p / RMAX, j = p % RMAX;
+      double x = 0.0;
+      for (int i = 0; i < r; ++i) x = fma(Kinv[j * kRMax + i], sv_s[i][g], x);
+      beta_s[g][j] = (float)x;
+    }
+    __syncthreads();
+    float2 s2[4][TR];  // -P_g[t] of the lane's cells, duplicated for the row pairs
+    float mx[4][TR];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < TR; ++j) {
+        const int g = gq + 4 * i, t = t0 + tq * TR + j;
+        const float pv = (g < gn && t < T) ? (float)gen_p[(size_t)t * G + g0 + g] : 0.f;
+        s2[i][j] = make_float2(-pv, -pv);
+        mx[i][j] = 0.f;
+      }
+    for (int k = w; k < ntile; k += NW) {
+      const int l = k * RT + lane;
+      const bool in = l < M;
+      float zr[RMAX];
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) zr[j] = in ? Zs[(size_t)j * Mp + l] : 0.f;
+      const float rm = in ? meta[Mp + l] : 0.f;  // an outaged monitored branch carries nothing
+      __syncwarp();  // every lane is done with the previous tile
+#pragma unroll 4
+      for (int g = 0; g < GG; ++g) {  // column position: generator gq + 4 i at gq * 4 + i (paired loads)
+        float c = (in && g < gn) ? PG[(size_t)(g0 + g) * M + l] : 0.f;
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) c = fmaf(-zr[j], beta_s[g][j], c);
+        colf[(pr * CP + (g & 3) * 4 + (g >> 2)) * 2 + hf] = c * rm;
+      }
+#pragma unroll 4
+      for (int t = 0; t < TT; ++t)
+        ptf[(pr * TP + t) * 2 + hf] = (in && t0 + t < T) ? ptil[(size_t)(t0 + t) * Mp + l] : 0.f;
+      __syncwarp();
+      float mt[4][TR];
+#pragma unroll
+      for (int rp = 0; rp < RT / 2; ++rp) {
+        const float4 u0 = *reinterpret_cast<const float4*>(&col_w[rp * CP + gq * 4]);
+        const float4 u1 = *reinterpret_cast<const float4*>(&col_w[rp * CP + gq * 4 + 2]);
+        const float2 ph[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
+                              make_float2(u1.z, u1.w)};
+        float2 pt[TR];
+#pragma unroll
+        for (int j = 0; j < TR; ++j) pt[j] = pt_w[rp * TP + tq * TR + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < TR; ++j) {
+            const float2 v = __ffma2_rn(ph[i], s2[i][j], pt[j]);  // rows 2 rp and 2 rp + 1
+            mt[i][j] = rp == 0 ? sec_max3abs(v.x, v.y, v.y) : sec_max3abs(mt[i][j], v.x, v.y);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TR; ++j) {
+          mx[i][j] = fmaxf(mx[i][j], mt[i][j]);
+          if (mt[i][j] > 1.f) {  // the overload terms of this cell over the tile
+            float s = 0.f;
+            for (int rp = 0; rp < RT / 2; ++rp) {
+              const float2 v = __ffma2_rn(col_w[rp * CP + gq * 4 + i], s2[i][j], pt_w[rp * TP + tq * TR + j]);
+              s += sec_ovl(v.x) + sec_ovl(v.y);
+            }
+            ov_s[w][(gq + 4 * i) * TT + tq * TR + j] += s;
+          }
+        }
+    }
+    __syncthreads();  // every warp is done with its tiles (the maxima reuse them)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < TR; ++j) mx_s[w * NCELL + (gq + 4 * i) * TT + tq * TR + j] = mx[i][j];
+    __syncthreads();
+    for (int t = tid; t < TT; t += blockDim.x) {  // over the warps and generators, the lowest on ties
+      if (t0 + t >= T) continue;
+      float bv = bv_s[t];
+      int bg = bg_s[t];
+      double bo = bo_s[t];
+      for (int g = 0; g < gn; ++g) {
+        float v = mx_s[g * TT + t];
+        for (int w2 = 0; w2 < NW; ++w2) {
+          v = fmaxf(v, mx_s[w2 * NCELL + g * TT + t]);
+          bo += (double)ov_s[w2][g * TT + t] * 1048576.0;
+        }
+        if (v > bv) {
+          bv = v;
+          bg = g0 + g;
+        }
+      }
+      bv_s[t] = bv;
+      bg_s[t] = bg;
+      bo_s[t] = bo;
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < TT; t += blockDim.x) {
+    if (t0 + t >= T) continue;
+    const size_t k2 = (size_t)tau * T + t0 + t;
+    o.gen_max_loading[k2] = G ? (double)bv_s[t] : 0.0;
+    o.worst_gen[k2] = G ? bg_s[t] : -1;
+    o.gen_overload_sum[k2] = bo_s[t];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// multi-outage sets: p_n1 = p_f + Phi_f[:, O] w_t with w_t = (I - Phi_f[O, O])^{-1}
+// p_f[O, t] from the set preparation.  Block = one topology and one pass of
+// TT = 8 TR timesteps (grid y), 256 threads, sets in groups of 32.  Per tile
+// of 16 monitored rows the block builds the 4 member columns Phi_f[:, o_a] /
+// limit of every set of the group (thread (set, member, half) builds 8 rows;
+// absent members are zero columns) into row pairs, and copies p_f / limit.
+// Thread (warp w, lane) owns set 4 w + lane / 8 at timesteps TR (lane % 8) + j:
+// per row pair four packed multiply-adds (members in order, as the
+// one-thread-per-row form) and one three-input |max| per timestep.  A member's
+// own monitored row carries nothing: its column entry there becomes
+// Phi_f[o, o] / limit - 1 / limit, which makes the row's flow cancel to
+// (rounding) zero, the convention LODF[c, c] = -1 of the single contingencies.
+// Two tile buffers alternate, so one barrier per tile suffices.
+// ---------------------------------------------------------------------------
+template <int TR>
+struct MultiTile {
+  static constexpr int TT = 8 * TR, SG = 32, LT = 16, NB = 2;
+  static constexpr int CPW = SG * 4;  // float2 per column row pair: [set][member]
+};
+
+template <int RMAX, int TR>
+__global__ __launch_bounds__(256, 3) void k_multi_tile(Args a, int n_multi, const int* __restrict__ mptr,
+                                                    const int* __restrict__ mmpos, const float* __restrict__ PhiMO,
+                                                    const float* __restrict__ mvt, const float* __restrict__ mw,
+                                                    const int* __restrict__ mflag) {
+  using L = MultiTile<TR>;
+  constexpr int TT = L::TT, SG = L::SG, LT = L::LT, NB = L::NB, CPW = L::CPW;
+  __shared__ __align__(16) float2 col_s[NB][LT / 2][CPW];
+  __shared__ __align__(16) float2 pt_s[NB][LT / 2][TT];
+  __shared__ float mx_s[SG][TT + 1];
+  __shared__ float ov_s[SG][TT + 1];
+  __shared__ int fl_s[SG];
+  __shared__ float bv_s[TT];
+  __shared__ int bg_s[TT];
+  __shared__ double bo_s[TT];
+  __shared__ int nisl_s;
+  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int t0 = blockIdx.y * TT;
+  const QInfo qi = a.qi[q];
+  const int T = a.T, M = a.M, Mp = a.Mpad, tau = qi.tau;
+  const dcflow_results& o = a.out;
+  if (qi.status != ST_OK) {
+    for (int t = t0 + tid; t < T && t < t0 + TT; t += blockDim.x) {
+      o.multi_max_loading[(size_t)tau * T + t] = 0.0;
+      o.worst_multi[(size_t)tau * T + t] = -1;
+      o.multi_overload_sum[(size_t)tau * T + t] = 0.0;
+    }
+    if (tid == 0 && blockIdx.y == 0) o.n_island_multi[tau] = 0;
+    return;
+  }
+  const float* Zs = static_cast<const float*>(a.Zs) + (size_t)q * kRMax * Mp;
+  const float* ptil = static_cast<const float*>(a.ptil) + (size_t)q * T * Mp;
+  const float* meta = static_cast<const float*>(a.diagv) + (size_t)q * 4 * Mp;
+  const size_t qS = (size_t)q * n_multi;
+  if (tid == 0) nisl_s = 0;
+  for (int t = tid; t < TT; t += blockDim.x) {
+    bv_s[t] = -1.f;
+    bg_s[t] = 0x7fffffff;
+    bo_s[t] = 0.0;
+  }
+  // builder role: set bs, member ba, rows [8 bh, 8 bh + 8) of each tile
+  const int bs = tid >> 3, ba = (tid >> 1) & 3, bh = tid & 1;
+  // compute role: set cs, timesteps TR ct + j
+  const int cs = 4 * w + (lane >> 3), ct = lane & 7;
+  const int ntile = (M + LT - 1) / LT;
+  for (int g0 = 0; g0 < n_multi; g0 += SG) {
+    const int ng = min(SG, n_multi - g0);
+    __syncthreads();  // the previous group's buffers, maxima and flags consumed
+    // the builder's member: its K^{-1}-weighted factors and its monitored row
+    float vb[RMAX];
+    int brow = -1;
+    size_t bent = 0;
+    bool bon = false;
+    if (bs < ng) {
+      const int m = g0 + bs, e0 = mptr[m], n = mptr[m + 1] - e0;
+      bon = ba < n;
+      if (bon) {
+        bent = (size_t)(e0 + ba) * Mp;
+        brow = mmpos[e0 + ba];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < RMAX; ++j) vb[j] = bon ? mvt[(qS + g0 + bs) * 4 * kRMax + ba * kRMax + j] : 0.f;
+    const float bil = brow >= 0 ? (float)a.inv_lim[brow] : 0.f;
+    // the compute thread's set: its weights w_t (zero for absent members and
+    // for sets that are not evaluated), its flag
+    int cflag = 3;
+    float2 w2[TR][4];
+    {
+      int n = 0;
+      if (cs < ng) {
+        cflag = mflag[qS + g0 + cs];
+        n = mptr[g0 + cs + 1] - mptr[g0 + cs];
+      }
+#pragma unroll
+      for (int j = 0; j < TR; ++j) {
+        const int t = t0 + ct * TR + j;
+#pragma unroll
+        for (int a2 = 0; a2 < 4; ++a2) {
+          const float x = (cflag == 0 && a2 < n && t < T) ? mw[((qS + g0 + cs) * T + t) * 4 + a2] : 0.f;
+          w2[j][a2] = make_float2(x, x);
+        }
+      }
+    }
+    if (tid < SG) {
+      const int f = tid < ng ? mflag[qS + g0 + tid] : 3;
+      fl_s[tid] = f;
+      if (t0 == 0 && f == 1) atomicAdd(&nisl_s, 1);
+    }
+    float mx[TR], ov[TR];
+#pragma unroll
+    for (int j = 0; j < TR; ++j) {
+      mx[j] = 0.f;
+      ov[j] = 0.f;
+    }
+    // build tile k into buffer k % 2: the member columns and p_f as row pairs
+    auto build = [&](int k) {
+      const int b = k & 1, r0 = k * LT + 8 * bh;
+      float c[8];
+      const float4* ph = reinterpret_cast<const float4*>(PhiMO + bent + r0);
+      const float4 p0 = bon ? ph[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 p1 = bon ? ph[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+      c[0] = p0.x; c[1] = p0.y; c[2] = p0.z; c[3] = p0.w;
+      c[4] = p1.x; c[5] = p1.y; c[6] = p1.z; c[7] = p1.w;
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) {
+        const float4* zp = reinterpret_cast<const float4*>(Zs + (size_t)j * Mp + r0);
+        const float4 z0 = zp[0], z1 = zp[1];
+        c[0] = fmaf(-z0.x, vb[j], c[0]); c[1] = fmaf(-z0.y, vb[j], c[1]);
+        c[2] = fmaf(-z0.z, vb[j], c[2]); c[3] = fmaf(-z0.w, vb[j], c[3]);
+        c[4] = fmaf(-z1.x, vb[j], c[4]); c[5] = fmaf(-z1.y, vb[j], c[5]);
+        c[6] = fmaf(-z1.z, vb[j], c[6]); c[7] = fmaf(-z1.w, vb[j], c[7]);
+      }
+      const float4* rp4 = reinterpret_cast<const float4*>(meta + Mp + r0);
+      const float4 m0 = rp4[0], m1 = rp4[1];
+      const float rm[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        c[i] = r0 + i < M ? c[i] * rm[i] : 0.f;
+        if (r0 + i == brow) c[i] -= bil;  // the member's own row: its flow cancels
+      }
+#pragma unroll
+      for (int i2 = 0; i2 < 4; ++i2) col_s[b][4 * bh + i2][bs * 4 + ba] = make_float2(c[2 * i2], c[2 * i2 + 1]);
+      for (int p = tid; p < (LT / 2) * TT; p += blockDim.x) {
+        const int rp = p % (LT / 2), t = p / (LT / 2), l = k * LT + 2 * rp;
+        float2 v = make_float2(0.f, 0.f);
+        if (t0 + t < T) {
+          v = *reinterpret_cast<const float2*>(ptil + (size_t)(t0 + t) * Mp + l);
+          if (l >= M) v.x = 0.f;
+          if (l + 1 >= M) v.y = 0.f;
+        }
+        pt_s[b][rp][t] = v;
+      }
+    };
+    if (ntile > 0) build(0);
+    for (int k = 0; k < ntile; ++k) {
+      __syncthreads();  // tile k built; every thread is done with tile k - 1 (its buffer is refilled next)
+      if (k + 1 < ntile) build(k + 1);
+      const int b = k & 1;
+      float mt[TR];
+#pragma unroll
+      for (int rp = 0; rp < LT / 2; ++rp) {
+        const float4 u0 = *reinterpret_cast<const float4*>(&col_s[b][rp][cs * 4]);
+        const float4 u1 = *reinterpret_cast<const float4*>(&col_s[b][rp][cs * 4 + 2]);
+        const float2 cc[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
+                              make_float2(u1.z, u1.w)};
+#pragma unroll
+        for (int j = 0; j < TR; ++j) {
+          float2 v = pt_s[b][rp][ct * TR + j];
+#pragma unroll
+          for (int a2 = 0; a2 < 4; ++a2) v = __ffma2_rn(cc[a2], w2[j][a2], v);
+          mt[j] = rp == 0 ? sec_max3abs(v.x, v.y, v.y) : sec_max3abs(mt[j], v.x, v.y);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < TR; ++j) {
+        mx[j] = fmaxf(mx[j], mt[j]);
+        if (mt[j] > 1.f) {  // the overload terms of this cell over the tile
+          float s = 0.f;
+          for (int rp = 0; rp < LT / 2; ++rp) {
+            float2 v = pt_s[b][rp][ct * TR + j];
+#pragma unroll
+            for (int a2 = 0; a2 < 4; ++a2) v = __ffma2_rn(col_s[b][rp][cs * 4 + a2], w2[j][a2], v);
+            s += sec_ovl(v.x) + sec_ovl(v.y);
+          }
+          ov[j] += s;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < TR; ++j) {
+      mx_s[cs][ct * TR + j] = mx[j];
+      ov_s[cs][ct * TR + j] = ov[j];
+    }
+    __syncthreads();
+    for (int t = tid; t < TT; t += blockDim.x) {  // over the sets in order: the lowest on ties
+      if (t0 + t >= T) continue;
+      float bv = bv_s[t];
+      int bg = bg_s[t];
+      double bo = bo_s[t];
+      for (int s = 0; s < ng; ++s) {
+        if (fl_s[s]) continue;
+        bo += (double)ov_s[s][t] * 1048576.0;
+        if (mx_s[s][t] > bv) {
+          bv = mx_s[s][t];
+          bg = g0 + s;
+        }
+      }
+      bv_s[t] = bv;
+      bg_s[t] = bg;
+      bo_s[t] = bo;
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < TT; t += blockDim.x) {
+    if (t0 + t >= T) continue;
+    const size_t k2 = (size_t)tau * T + t0 + t;
+    const bool any = bg_s[t] != 0x7fffffff;
+    o.multi_max_loading[k2] = any ? (double)bv_s[t] : 0.0;
+    o.worst_multi[k2] = any ? bg_s[t] : -1;
+    o.multi_overload_sum[k2] = bo_s[t];
+  }
+  if (tid == 0 && blockIdx.y == 0) o.n_island_multi[tau] = nisl_s;
+}
+
+}  // namespace dcf

@@ -2239,6 +2239,7 @@ __global__ __launch_bounds__(128) void k_multi_rows(Args a, int n_multi, const i
 }  // namespace dcf
 
 #include "n1_launch.cuh"
+#include "sec_tile.cuh"
 
 using namespace dcf;
 
@@ -2332,22 +2333,36 @@ void launch_topcases(const Args& a, int RMAX, const float* cmax, const int* cinv
   else launch_topcases_r<Real, 16>(a, cmax, cinv, phicm, k, st);
 }
 
+// timesteps per pass of the register-tiled FP32 kernels (8 TR): the fewest passes
+inline int sec_tr(int T) { return T > 16 ? 3 : (T > 8 ? 2 : 1); }
+
+// FP64: one thread per monitored row, passes of 8 timesteps; FP32: the
+// register-tiled kernel, every pass in one launch (grid y).  Returns the launches.
 template <class Real, int RMAX>
-void launch_gen_r(const Args& a, int G, const int* gen_bus, const double* gen_p, const double* ptdf, int V,
-                  const Real* P, cudaStream_t st) {
-  // timesteps per pass (per-thread accumulators); one pass of 24 (the columns built once per
-  // topology) measured slower: the registers it needs halve the resident blocks
-  constexpr int TT = 8;
-  for (int t0 = 0; t0 < a.T; t0 += TT)
-    k_gen_n1<Real, RMAX, TT><<<a.nq, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P, t0);
+int launch_gen_r(const Args& a, int G, const int* gen_bus, const double* gen_p, const double* ptdf, int V,
+                 const Real* P, cudaStream_t st) {
+  if constexpr (sizeof(Real) == 4) {
+    const int tr = sec_tr(a.T);
+    const dim3 grid(a.nq, (a.T + 8 * tr - 1) / (8 * tr));
+    if (tr == 3) k_gen_tile<RMAX, 3><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
+    else if (tr == 2) k_gen_tile<RMAX, 2><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
+    else k_gen_tile<RMAX, 1><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
+    return 1;
+  } else {
+    constexpr int TT = 8;
+    int n = 0;
+    for (int t0 = 0; t0 < a.T; t0 += TT, ++n)
+      k_gen_n1<Real, RMAX, TT><<<a.nq, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P, t0);
+    return n;
+  }
 }
 template <class Real>
-void launch_gen(const Args& a, int RMAX, int G, const int* gen_bus, const double* gen_p, const double* ptdf, int V,
-                const void* pg, cudaStream_t st) {
+int launch_gen(const Args& a, int RMAX, int G, const int* gen_bus, const double* gen_p, const double* ptdf, int V,
+               const void* pg, cudaStream_t st) {
   const Real* P = static_cast<const Real*>(pg);
-  if (RMAX == 4) launch_gen_r<Real, 4>(a, G, gen_bus, gen_p, ptdf, V, P, st);
-  else if (RMAX == 8) launch_gen_r<Real, 8>(a, G, gen_bus, gen_p, ptdf, V, P, st);
-  else launch_gen_r<Real, 16>(a, G, gen_bus, gen_p, ptdf, V, P, st);
+  if (RMAX == 4) return launch_gen_r<Real, 4>(a, G, gen_bus, gen_p, ptdf, V, P, st);
+  if (RMAX == 8) return launch_gen_r<Real, 8>(a, G, gen_bus, gen_p, ptdf, V, P, st);
+  return launch_gen_r<Real, 16>(a, G, gen_bus, gen_p, ptdf, V, P, st);
 }
 
 template <class Real>
@@ -2361,13 +2376,27 @@ void launch_multi_prep(const Args& a, int n_multi, const int* mptr, const int* m
 template <class Real>
 void launch_multi_rows(const Args& a, int RMAX, int n_multi, const int* mptr, const int* mmpos, const void* phimo,
                        ChunkBufs& B, cudaStream_t st) {
-  constexpr int TT = 12, SG = 32;
   const Real* P = static_cast<const Real*>(phimo);
   const Real *vt = B.mvt.as<Real>(), *w = B.mw.as<Real>();
   const int* f = B.mflag.as<int>();
-  if (RMAX == 4) k_multi_rows<Real, 4, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
-  else if (RMAX == 8) k_multi_rows<Real, 8, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
-  else k_multi_rows<Real, 16, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
+  if constexpr (sizeof(Real) == 4) {  // register-tiled, every timestep pass in one launch (grid y)
+    const int tr = sec_tr(a.T);
+    const dim3 grid(a.nq, (a.T + 8 * tr - 1) / (8 * tr));
+#define DCF_MULTI_TILE(R_, TR_) k_multi_tile<R_, TR_><<<grid, 256, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f)
+    if (RMAX == 4) {
+      if (tr == 3) DCF_MULTI_TILE(4, 3); else if (tr == 2) DCF_MULTI_TILE(4, 2); else DCF_MULTI_TILE(4, 1);
+    } else if (RMAX == 8) {
+      if (tr == 3) DCF_MULTI_TILE(8, 3); else if (tr == 2) DCF_MULTI_TILE(8, 2); else DCF_MULTI_TILE(8, 1);
+    } else {
+      if (tr == 3) DCF_MULTI_TILE(16, 3); else if (tr == 2) DCF_MULTI_TILE(16, 2); else DCF_MULTI_TILE(16, 1);
+    }
+#undef DCF_MULTI_TILE
+  } else {
+    constexpr int TT = 12, SG = 32;
+    if (RMAX == 4) k_multi_rows<Real, 4, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
+    else if (RMAX == 8) k_multi_rows<Real, 8, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
+    else k_multi_rows<Real, 16, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
+  }
 }
 
 // per-topology r x r systems and row operands of one chunk
@@ -3171,11 +3200,11 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     }
     if (G > 0) {
       const int pe = ctx->prof_begin(st);
-      if (fp64)
-        launch_gen<double>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V, ctx->gen_cols.p, st);
-      else
-        launch_gen<float>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V, ctx->gen_cols.p, st);
-      ++ctx->launches;
+      ctx->launches +=
+          fp64 ? launch_gen<double>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V,
+                                    ctx->gen_cols.p, st)
+               : launch_gen<float>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V,
+                                   ctx->gen_cols.p, st);
       DCF_CHECK_LAUNCH();
       ctx->prof_end(pe, DCFLOW_PROF_GEN, st);
     }

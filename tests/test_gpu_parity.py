@@ -83,6 +83,22 @@ def test_grid500_sample(precision):
     compare(_gpu(w, lim, precision), _ref(w, lim, precision=precision), w, w.topo, lim, TOL[precision])
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("scale", [0.35, 0.8, 3.0])
+def test_grid500_overloaded_rows(precision, scale):
+    """Limits scaled so that rows overloaded already in N-0 are everywhere
+    (0.35: most tiles hold more of them than the FP32 kernel evaluates apart),
+    common (0.8) or rare (3.0): maxima, overload sums and indices against
+    the oracle, 24 topologies of the 500-bus study."""
+    w = synth.workload(2, n_topo=24)
+    lim = oracle.thermal_limits(w.grid, w.inj) * scale
+    ref = _ref(w, lim, precision=precision)
+    ok = ref["status"] == 0
+    n0 = ref["n0_max"][ok]
+    assert (n0 > 1).mean() > 0.9 if scale < 1 else (n0 > 1).mean() < 0.05
+    compare(_gpu(w, lim, precision), ref, w, w.topo, lim, TOL[precision])
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16x3"])
 def test_grid500_row_restricted_study(precision):
     """The benchmark's study: only the rows of the monitored, contingency,
