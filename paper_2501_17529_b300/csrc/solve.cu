@@ -1145,55 +1145,87 @@ __global__ __launch_bounds__(128) void k_ti_decode(GridDev g, BatchDev in, Args 
   }
 }
 
-// Operands of every (timestep, candidate): the rank-r correction above; a
-// topology with fewer candidates than U repeats its first one (an exact tie
-// that the argmin resolves to the original)
-template <class Real>
-__global__ __launch_bounds__(128) void k_ti_expand(Args ap, int T, int U, const int* __restrict__ ti_ptr,
+// Operands of every (timestep, candidate): the rank-r correction above.  One
+// block per (topology, timestep) and its candidates in groups of 16: the
+// moved powers q and K^{-1} q of a group are formed in parallel, then each
+// row's operands are loaded once for the group's 16 output rows (the kernel
+// is bound by writing them).  A topology with fewer candidates than U repeats
+// its first one (an exact tie that the argmin resolves to the original).  Rank
+// positions r <= j < RMAX carry zero weights, which leave every sum exact.
+template <class Real, int RMAX>
+__global__ __launch_bounds__(256) void k_ti_expand(Args ap, int T, int U, const int* __restrict__ ti_ptr,
                                                    const uint64_t* __restrict__ ti_mask,
                                                    const double* __restrict__ inj_p, int n_inj,
                                                    const int* __restrict__ tiel, const int* __restrict__ tirow,
                                                    const int* __restrict__ nel, const Real* __restrict__ zcd,
                                                    Real* __restrict__ ptv, Real* __restrict__ svv) {
-  const int q = blockIdx.y;
+  constexpr int UG = 16;
+  const int q = blockIdx.y, t = blockIdx.x;
   const QInfo qi = ap.qi[q];
   if (qi.status != ST_OK) return;
-  __shared__ double qv[kRMax];
-  __shared__ Real w_s[kRMax];
-  const int vt = blockIdx.x, t = vt / U, u = vt % U;
+  __shared__ double qv[UG][kRMax];
+  __shared__ Real w_s[UG][RMAX];
+  __shared__ int row_s[64];
+  __shared__ double ip_s[64];  // power of the topology's j-th eligible injection at timestep t
   const int Mp = ap.Mpad, M = ap.M, C = ap.C, TV = T * U, r = qi.r, ks = qi.ks, tid = threadIdx.x;
   const int u0 = ti_ptr[qi.tau], nu = ti_ptr[qi.tau + 1] - u0;
-  const uint64_t m = ti_mask[u0 + (u < nu ? u : 0)];
-  if (tid < kRMax) {  // q_i: power moved onto busbar B of split i at timestep t
-    double acc = 0.0;
-    if (tid < ks)
-      for (int j = 0; j < nel[q]; ++j)
-        if (((m >> j) & 1ull) && tirow[(size_t)q * 64 + j] == tid) acc += inj_p[(size_t)t * n_inj + tiel[(size_t)q * 64 + j]];
-    qv[tid] = acc;
+  const int ne = nel[q];
+  for (int j = tid; j < ne; j += blockDim.x) {
+    row_s[j] = tirow[(size_t)q * 64 + j];
+    ip_s[j] = inj_p[(size_t)t * n_inj + tiel[(size_t)q * 64 + j]];
   }
-  __syncthreads();
-  if (tid < kRMax) {  // w = K^{-1} q (only the split rows of q are nonzero)
-    const double* Kinv = ap.Kinv + (size_t)q * kRMax * kRMax;
-    double x = 0.0;
-    for (int i = 0; i < ks; ++i) x = fma(Kinv[tid * kRMax + i], qv[i], x);
-    w_s[tid] = tid < r ? (Real)x : (Real)0;
-  }
-  __syncthreads();
+  const double* Kinv = ap.Kinv + (size_t)q * kRMax * kRMax;
   const Real* pt = static_cast<const Real*>(ap.ptil) + (size_t)q * T * Mp;
   const Real* sv = static_cast<const Real*>(ap.s) + (size_t)q * T * C;
   const Real* Zs = static_cast<const Real*>(ap.Zs) + (size_t)q * kRMax * Mp;
   const Real* zc = zcd + (size_t)q * kRMax * C;
-  Real* po = ptv + ((size_t)q * TV + vt) * Mp;
-  Real* so = svv + ((size_t)q * TV + vt) * C;
-  for (int l = tid; l < M; l += blockDim.x) {
-    Real v = pt[(size_t)t * Mp + l];
-    for (int j = 0; j < r; ++j) v = fma(Zs[(size_t)j * Mp + l], w_s[j], v);
-    po[l] = v;
-  }
-  for (int c = tid; c < C; c += blockDim.x) {
-    Real v = sv[(size_t)t * C + c];
-    for (int j = 0; j < r; ++j) v = fma(zc[(size_t)j * C + c], w_s[j], v);
-    so[c] = v;
+  for (int ug = 0; ug < U; ug += UG) {
+    const int un = min(UG, U - ug);
+    __syncthreads();  // the injections are staged; the previous group's weights are consumed
+    for (int p = tid; p < UG * kRMax; p += blockDim.x) {  // q_i: power moved onto busbar B of split i
+      const int uu = p / kRMax, i = p % kRMax, u = ug + uu;
+      double acc = 0.0;
+      if (uu < un && i < ks) {
+        const uint64_t m = ti_mask[u0 + (u < nu ? u : 0)];
+        for (int j = 0; j < ne; ++j)
+          if (((m >> j) & 1ull) && row_s[j] == i) acc += ip_s[j];
+      }
+      qv[uu][i] = acc;
+    }
+    __syncthreads();
+    for (int p = tid; p < UG * RMAX; p += blockDim.x) {  // w = K^{-1} q (only the split rows of q are nonzero)
+      const int uu = p / RMAX, jj = p % RMAX;
+      double x = 0.0;
+      for (int i = 0; i < ks; ++i) x = fma(Kinv[jj * kRMax + i], qv[uu][i], x);
+      w_s[uu][jj] = jj < r ? (Real)x : (Real)0;
+    }
+    __syncthreads();
+    Real* po = ptv + ((size_t)q * TV + (size_t)t * U + ug) * Mp;
+    Real* so = svv + ((size_t)q * TV + (size_t)t * U + ug) * C;
+    for (int l = tid; l < M; l += blockDim.x) {
+      Real z[RMAX];
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) z[j] = Zs[(size_t)j * Mp + l];  // zero rows beyond the rank
+      const Real p0 = pt[(size_t)t * Mp + l];
+      for (int uu = 0; uu < un; ++uu) {
+        Real v = p0;
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) v = fma(z[j], w_s[uu][j], v);
+        po[(size_t)uu * Mp + l] = v;
+      }
+    }
+    for (int c = tid; c < C; c += blockDim.x) {
+      Real z[RMAX];
+#pragma unroll
+      for (int j = 0; j < RMAX; ++j) z[j] = zc[(size_t)j * C + c];
+      const Real s0 = sv[(size_t)t * C + c];
+      for (int uu = 0; uu < un; ++uu) {
+        Real v = s0;
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) v = fma(z[j], w_s[uu][j], v);
+        so[(size_t)uu * C + c] = v;
+      }
+    }
   }
 }
 
@@ -2333,6 +2365,20 @@ void launch_topcases(const Args& a, int RMAX, const float* cmax, const int* cinv
   else launch_topcases_r<Real, 16>(a, cmax, cinv, phicm, k, st);
 }
 
+template <class Real>
+void launch_ti_expand(const Args& ap, int RMAX, int T, int U, const dcflow_batch* bt, ChunkBufs& B, int nq,
+                      cudaStream_t st) {
+  const dim3 grid(T, nq);
+#define DCF_TI_EXPAND(R_)                                                                                    \
+  k_ti_expand<Real, R_><<<grid, 256, 0, st>>>(ap, T, U, bt->ti_ptr, bt->ti_mask, bt->inj_p, bt->n_inj,      \
+                                              B.tiel.as<int>(), B.tirow.as<int>(), B.nel.as<int>(),         \
+                                              B.zcd.as<Real>(), B.ptv.as<Real>(), B.svv.as<Real>())
+  if (RMAX == 4) DCF_TI_EXPAND(4);
+  else if (RMAX == 8) DCF_TI_EXPAND(8);
+  else DCF_TI_EXPAND(16);
+#undef DCF_TI_EXPAND
+}
+
 // timesteps per pass of the register-tiled FP32 kernels (8 TR): the fewest passes
 inline int sec_tr(int T) { return T > 16 ? 3 : (T > 8 ? 2 : 1); }
 
@@ -3053,13 +3099,9 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       const int pex = ctx->prof_begin(st);
       if (TI) {
         if (fp64)
-          k_ti_expand<double><<<dim3(TV, ch.nq), 128, 0, st>>>(
-              ap, T, Uc, bt->ti_ptr, bt->ti_mask, bt->inj_p, bt->n_inj, B.tiel.as<int>(), B.tirow.as<int>(),
-              B.nel.as<int>(), B.zcd.as<double>(), B.ptv.as<double>(), B.svv.as<double>());
+          launch_ti_expand<double>(ap, RMAX, T, Uc, bt, B, ch.nq, st);
         else
-          k_ti_expand<float><<<dim3(TV, ch.nq), 128, 0, st>>>(
-              ap, T, Uc, bt->ti_ptr, bt->ti_mask, bt->inj_p, bt->n_inj, B.tiel.as<int>(), B.tirow.as<int>(),
-              B.nel.as<int>(), B.zcd.as<float>(), B.ptv.as<float>(), B.svv.as<float>());
+          launch_ti_expand<float>(ap, RMAX, T, Uc, bt, B, ch.nq, st);
       } else if (fp64) {
         k_var_expand<double><<<dim3(TV, ch.nq), 128, 0, st>>>(ap, T, U, bt->var_ptr, ctx->var_k.as<int>(),
                                                                bt->var_delta, B.ptv.as<double>(), B.svv.as<double>());
