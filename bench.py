@@ -426,7 +426,7 @@ def run_ours(args):
             rec = nok * T_STEPS * args.top_k * n_mon  # entries of the cases' recomputed columns
             results[f"fp32_top{args.top_k}"] = {"value": lf_all * steps / tk, "ms_per_step": 1e3 * tk / steps,
                                                 "loadflows_per_step": lf_all, "steps": steps,
-                                                "kernels": {"name": "k_topcases", "ms_per_step": kk["topcases_ms"],
+                                                "kernels": {"name": "k_topcols", "ms_per_step": kk["topcases_ms"],
                                                            "column_entries_per_s_T": rec / (kk["topcases_ms"] / 1e3) / 1e12
                                                            if kk["topcases_ms"] else None},
                                                 "note": f"fp32 solve plus the {args.top_k} worst N-1 cases "
@@ -445,7 +445,7 @@ def run_ours(args):
             results[f"fp32_gen{args.gens}"] = {"value": lf_all * steps / tg, "ms_per_step": 1e3 * tg / steps,
                                                "loadflows_per_step": lf_all,
                                                "generator_cases_per_step": ngen_cases, "steps": steps,
-                                               "kernels": {"name": "k_gen_n1", "ms_per_step": kg["gen_ms"],
+                                               "kernels": {"name": "k_gen_tile", "ms_per_step": kg["gen_ms"],
                                                           "entries_per_s_T": gen_rate, "alu_peak_T": alu_peak,
                                                           "frac": gen_rate / alu_peak if gen_rate else None},
                                                "note": f"fp32 solve plus {args.gens} generator-failure N-1 cases "
@@ -491,7 +491,7 @@ def run_ours(args):
             results[f"fp32_multi{args.multi}"] = {
                 "value": lf_all * steps / tm, "ms_per_step": 1e3 * tm / steps, "loadflows_per_step": lf_all,
                 "multi_cases_per_step": nm_cases, "steps": steps,
-                "kernels": {"name": "k_multi_rows", "ms_per_step": km["multi_ms"],
+                "kernels": {"name": "k_multi_tile", "ms_per_step": km["multi_ms"],
                            "entries_per_s_T": nm_cases / ws * n_mon / (km["multi_ms"] / 1e3) / 1e12 if km["multi_ms"] else None,
                            "alu_peak_T": alu_peak,
                            "frac": (nm_cases / ws * n_mon / (km["multi_ms"] / 1e3) / 1e12 / alu_peak) if km["multi_ms"] else None,

@@ -64,6 +64,9 @@ struct Args {
   void* cmr;
   double tie_eps;       // tie band of the reported indices: eps * max(best, 1)
   const int* cont_inv;  // caller's position -> internal contingency
+  // per (slot, timestep, internal contingency) below c_rem: the 16-row tile holding
+  // the maximum (written by the tracking N-1 pass for the top-k cases), or null
+  uint16_t* tile;
   int* err;  // set to 1 by a kernel whose bounded wait expired
   // outputs
   dcflow_results out;

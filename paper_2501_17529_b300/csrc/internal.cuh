@@ -50,7 +50,7 @@ struct DevBuf {
 struct ChunkBufs {
   DevBuf ent_n, ent_s, ent_w, mod_ptr, q_info;
   DevBuf Kinv, alpha, Vt64, VtR, Zs, Zbf, ptil, meta, s, valid, nisl;
-  DevBuf pmax, parg, povl, cmr, p2max;
+  DevBuf pmax, parg, povl, cmr, p2max, tile;
   // injection candidates: per (timestep, candidate) operands and screening maxima,
   // the chosen candidate per timestep and its operands
   DevBuf ptv, svv, pmaxv, pargv, povlv, bestu, ptb, sb;
@@ -63,7 +63,7 @@ struct ChunkBufs {
   DevBuf zcd, tiel, tirow, nel;
   void release_all() {
     DevBuf* b[] = {&ent_n, &ent_s, &ent_w, &mod_ptr, &q_info, &Kinv, &alpha, &Vt64, &VtR, &Zs, &Zbf, &ptil, &meta,
-                   &s, &valid, &nisl, &pmax, &parg, &povl, &cmr, &p2max, &ptv, &svv, &pmaxv, &pargv, &povlv, &bestu, &ptb, &sb,
+                   &s, &valid, &nisl, &pmax, &parg, &povl, &cmr, &p2max, &tile, &ptv, &svv, &pmaxv, &pargv, &povlv, &bestu, &ptb, &sb,
                    &selmask, &sfb, &csel, &nsel, &work, &nwork, &mvt, &mw, &mflag, &zcd, &tiel, &tirow, &nel};
     for (auto* x : b) x->release();
   }

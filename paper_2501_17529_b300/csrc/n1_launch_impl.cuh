@@ -14,6 +14,15 @@ int launch_tma_t(const N1Maps& maps, const Args& a, dim3 grid, cudaStream_t st, 
   static uint64_t attr = 0;
   if constexpr (TT >= 4) {  // register-tiled kernel
     using L = RegLayout<TT, RMAX, false, TC>;
+    if constexpr (OVL && !TC) {  // the tracking variant: each maximum's tile for the top-k cases
+      if (a.tile) {
+        static uint64_t attr_t = 0;
+        if (smem_attr_once(k_n1_reg<TT, RMAX, true, false, false, true>, L::kBytes, attr_t) != cudaSuccess)
+          return DCFLOW_ERR_CUDA;
+        k_n1_reg<TT, RMAX, true, false, false, true><<<grid, RegTile<TT>::NT, L::kBytes, st>>>(maps, a, t0, SelArgs{});
+        return 0;
+      }
+    }
     if (smem_attr_once(k_n1_reg<TT, RMAX, OVL, false, TC>, L::kBytes, attr) != cudaSuccess) return DCFLOW_ERR_CUDA;
     k_n1_reg<TT, RMAX, OVL, false, TC><<<grid, RegTile<TT>::NT, L::kBytes, st>>>(maps, a, t0, SelArgs{});
   } else {  // one timestep: one thread per contingency

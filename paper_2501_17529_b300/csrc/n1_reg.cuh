@@ -112,7 +112,7 @@ struct RegLayout {
   static constexpr int kBytes = kOffQ + (R::NT / 32) * 32 * R::CR * R::TR * 2;
 };
 
-template <int TT, int RMAX, bool OVL, bool SEL = false, bool TC = false>
+template <int TT, int RMAX, bool OVL, bool SEL = false, bool TC = false, bool TRK = false>
 __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n1_reg(const __grid_constant__ N1Maps maps, Args a, int t0_base,
                                                             const SelArgs sel) {
   const int t0 = t0_base + (int)blockIdx.z * TT;  // grid z: the passes over TT timesteps each
@@ -233,10 +233,14 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
     issue_phi(k);
   }
   float mx[CR][TR];
+  int tk[TRK ? CR : 1][TRK ? TR : 1];  // TRK: the tile of each maximum (the first on ties)
 #pragma unroll
   for (int i = 0; i < CR; ++i)
 #pragma unroll
-    for (int j = 0; j < TR; ++j) mx[i][j] = 0.f;
+    for (int j = 0; j < TR; ++j) {
+      mx[i][j] = 0.f;
+      if constexpr (TRK) tk[i][j] = 0;
+    }
   // the builder's K^{-1}-weighted factors of its contingency, fixed for the block
   constexpr bool kVtReg = RMAX <= 8 && !TC;
   float vb[kVtReg ? RMAX : 1];
@@ -417,7 +421,15 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
 #pragma unroll
       for (int i = 0; i < CR; ++i)
 #pragma unroll
-        for (int j = 0; j < TR; ++j) mx[i][j] = fmaxf(mx[i][j], mt[i][j]);
+        for (int j = 0; j < TR; ++j) {
+          if constexpr (TRK) {
+            const bool up = mt[i][j] > mx[i][j];
+            mx[i][j] = up ? mt[i][j] : mx[i][j];
+            tk[i][j] = up ? k : tk[i][j];
+          } else {
+            mx[i][j] = fmaxf(mx[i][j], mt[i][j]);
+          }
+        }
       // overload sum only for the (contingency, timestep) items whose tile
       // maximum exceeds 1: the warp queues them and serves the queue with all
       // lanes (items of one tile are distinct (t, c) pairs: no write conflicts)
@@ -477,6 +489,20 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
       const int t = t0 + i / kCB, cl = i % kCB, c = s_ci[cl];
       if (t < T && c >= 0)
         a.out.n1_cont_max[((size_t)qi.tau * T + t) * C + a.cont_pos[c]] = okc[cl] ? s_s[(i / kCB) * SP + cl] : -1.f;
+    }
+  }
+  if constexpr (TRK) {  // the tile of every maximum (internal order), through the idle stages
+    static_assert(TT * SP * 4 + TT * SP * 2 <= kRegStages * L::kStage, "tiles fit the stages");
+    uint16_t* s_tk = reinterpret_cast<uint16_t*>(sm + TT * SP * 4);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < CR; ++i)
+#pragma unroll
+      for (int j = 0; j < TR; ++j) s_tk[(tg * TR + j) * SP + cg + R::CG * i] = (uint16_t)tk[i][j];
+    __syncthreads();
+    for (int i = tid; i < TT * kCB; i += R::NT) {
+      const int t = t0 + i / kCB, cl = i % kCB, c = s_ci[cl];
+      if (t < T && c >= 0) a.tile[((size_t)q * T + t) * C + c] = s_tk[(i / kCB) * SP + cl];
     }
   }
   if (a.cmr) {  // the same in internal order for the final pass's tie band

@@ -1685,6 +1685,47 @@ __device__ __forceinline__ bool warp_top_few(const uint32_t (&key)[NPL], int kk,
   return true;
 }
 
+// The kk highest per-contingency maxima of one (topology, timestep) row (one
+// warp): their values and positions in ov / op, by descending loading with
+// ties to the lower position.  ck, cq, sp, sv: 64-entry scratch of the warp.
+template <int NPL>
+__device__ __forceinline__ void select_cases(const float* __restrict__ row, int C, int kk, uint32_t* ck, int* cq,
+                                             int* sp, float* sv, float* ov, int* op) {
+  const int lane = threadIdx.x & 31;
+  uint32_t key[NPL];
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {
+    const int p = lane + 32 * i;
+    key[i] = p < C ? float_key(row[p]) : 0u;
+  }
+  if (kk < 1 || kk > 32 || !warp_top_few<NPL>(key, kk, row, ck, cq, sp, sv)) {  // warp-uniform
+    bool sel[NPL];
+    uint32_t thr;
+    warp_top_k<NPL>(key, kk, sel, thr);
+    int off = 0;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {  // the selected cases in ascending position
+      const uint32_t b = __ballot_sync(0xffffffffu, sel[i]);
+      if (sel[i]) {
+        const int j = off + __popc(b & ((1u << lane) - 1u));
+        sp[j] = lane + 32 * i;
+        sv[j] = row[lane + 32 * i];
+      }
+      off += __popc(b);
+    }
+  }
+  __syncwarp();
+  for (int j = lane; j < kk; j += 32) {  // descending loading, ties to the lower position
+    const float v = sv[j];
+    const int p = sp[j];
+    int rank = 0;
+    for (int m = 0; m < kk; ++m) rank += sv[m] > v || (sv[m] == v && sp[m] < p);
+    ov[rank] = v;
+    op[rank] = p;
+  }
+  __syncwarp();
+}
+
 // 7 resident blocks per SM (72 registers, a few bytes spilled in the select):
 // the column pass waits on its loads, and more warps in flight hide them better
 // than 5 blocks with no spill (measured 2.04 against 2.64 ms on the 500-bus study)
@@ -1712,42 +1753,10 @@ __global__ __launch_bounds__(128, 7) void k_topcases(Args a, const float* __rest
     }
     return;
   }
-  const float* row = cmax + ((size_t)tau * T + t) * C;
-  uint32_t key[NPL];
-#pragma unroll
-  for (int i = 0; i < NPL; ++i) {
-    const int p = lane + 32 * i;
-    key[i] = p < C ? float_key(row[p]) : 0u;
-  }
   const int kk = k < C ? k : C;
   __shared__ uint32_t ck_[4][64];
   __shared__ int cq_[4][64];
-  if (kk < 1 || kk > 32 || !warp_top_few<NPL>(key, kk, row, ck_[w], cq_[w], sp_[w], sv_[w])) {  // warp-uniform
-    bool sel[NPL];
-    uint32_t thr;
-    warp_top_k<NPL>(key, kk, sel, thr);
-    int off = 0;
-#pragma unroll
-    for (int i = 0; i < NPL; ++i) {  // the selected cases in ascending position
-      const uint32_t b = __ballot_sync(0xffffffffu, sel[i]);
-      if (sel[i]) {
-        const int j = off + __popc(b & ((1u << lane) - 1u));
-        sp_[w][j] = lane + 32 * i;
-        sv_[w][j] = row[lane + 32 * i];
-      }
-      off += __popc(b);
-    }
-  }
-  __syncwarp();
-  for (int j = lane; j < kk; j += 32) {  // descending loading, ties to the lower position
-    const float v = sv_[w][j];
-    const int p = sp_[w][j];
-    int rank = 0;
-    for (int m = 0; m < kk; ++m) rank += sv_[w][m] > v || (sv_[w][m] == v && sp_[w][m] < p);
-    ov_[w][rank] = v;
-    op_[w][rank] = p;
-  }
-  __syncwarp();
+  select_cases<NPL>(cmax + ((size_t)tau * T + t) * C, C, kk, ck_[w], cq_[w], sp_[w], sv_[w], ov_[w], op_[w]);
   const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
   const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
   const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
@@ -1815,6 +1824,255 @@ __global__ __launch_bounds__(128, 7) void k_topcases(Args a, const float* __rest
   }
 }
 
+
+// The same per topology (one block of 8 warps): the top k of every timestep
+// (one warp per timestep), then the distinct selected contingencies' Phi_f
+// columns, up to `cbm` at a time, into shared memory ([column][monitored row],
+// the N-1 kernels' arithmetic), and every case of those contingencies against
+// them (the cases in turn over the warps: the most loaded monitored branch,
+// the lowest on ties).  The k cases of the timesteps of a topology share few
+// contingencies, so the column builds fall from one per case to one per
+// distinct contingency.  Timesteps in chunks of 32.
+template <class Real, int RMAX, int NPL>
+__global__ __launch_bounds__(256) void k_topcols(Args a, const float* __restrict__ cmax,
+                                                 const int* __restrict__ cont_inv, const Real* __restrict__ PhiCM,
+                                                 int k, int cbm) {
+  constexpr int NW = 8, TCH = 32, CBX = 16;
+  __shared__ float sv_[NW][64];
+  __shared__ int sp_[NW][64];
+  __shared__ uint32_t ck_[NW][64];
+  __shared__ int cq_[NW][64];
+  __shared__ float ov_[NW][64];
+  __shared__ int op_[NW][64];
+  __shared__ int16_t cc_s[TCH * 64];  // internal contingency of case (timestep of the chunk, rank), or -1
+  __shared__ int16_t rk_s[TCH * 64];  // its position among the chunk's distinct contingencies
+  __shared__ int16_t dl_s[2048];      // the chunk's distinct contingencies, ascending
+  __shared__ uint32_t cmask[64];      // at most 2048 contingencies
+  __shared__ int wpre[64];            // distinct contingencies below each mask word
+  __shared__ Real vt_s[CBX][RMAX];
+  __shared__ int nd_s;
+  extern __shared__ __align__(16) unsigned char tc_dyn[];
+  Real* s_col = reinterpret_cast<Real*>(tc_dyn);  // [cbm][M]
+  const int q = blockIdx.x, tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const QInfo qi = a.qi[q];
+  const int T = a.T, M = a.M, C = a.C, Mp = a.Mpad, tau = qi.tau;
+  const dcflow_results& o = a.out;
+  if (qi.status != ST_OK) {
+    for (size_t i = tid; i < (size_t)T * k; i += blockDim.x) {
+      o.top_cont[(size_t)tau * T * k + i] = -1;
+      o.top_mon[(size_t)tau * T * k + i] = -1;
+      o.top_loading[(size_t)tau * T * k + i] = 0.f;
+    }
+    return;
+  }
+  const int kk = k < C ? k : C;
+  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
+  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp;
+  const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
+  const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
+  const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
+  for (int t0 = 0; t0 < T; t0 += TCH) {
+    const int tn = min(TCH, T - t0), ne = tn * k;
+    __syncthreads();  // the previous chunk's lists and columns are consumed
+    if (tid < 64) cmask[tid] = 0u;
+    __syncthreads();
+    for (int tl = w; tl < tn; tl += NW) {
+      const int t = t0 + tl;
+      select_cases<NPL>(cmax + ((size_t)tau * T + t) * C, C, kk, ck_[w], cq_[w], sp_[w], sv_[w], ov_[w], op_[w]);
+      const size_t ob = ((size_t)tau * T + t) * k;
+      for (int j = lane; j < k; j += 32) {
+        const bool valid = j < kk && ov_[w][j] >= 0.f;
+        const int c = valid ? cont_inv[op_[w][j]] : -1;
+        cc_s[tl * 64 + j] = (int16_t)c;
+        o.top_cont[ob + j] = valid ? op_[w][j] : -1;
+        o.top_loading[ob + j] = valid ? ov_[w][j] : 0.f;
+        if (!valid) o.top_mon[ob + j] = -1;
+        if (c >= 0) atomicOr(&cmask[c >> 5], 1u << (c & 31));
+      }
+      __syncwarp();  // the next timestep's selection rewrites the warp's lists
+    }
+    __syncthreads();
+    if (w == 0) {  // the distinct contingencies in ascending order
+      int base = 0;
+      for (int w0 = 0; w0 < 64; w0 += 32) {
+        const uint32_t m = cmask[w0 + lane];
+        const int cnt = __popc(m);
+        int inc = cnt;
+        for (int off = 1; off < 32; off <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc, off);
+          if (lane >= off) inc += y;
+        }
+        int pos = base + inc - cnt;
+        wpre[w0 + lane] = pos;
+        for (uint32_t b = m; b; b &= b - 1u) dl_s[pos++] = (int16_t)((w0 + lane) * 32 + __ffs(b) - 1);
+        base += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) nd_s = base;
+    }
+    __syncthreads();
+    for (int e = tid; e < ne; e += blockDim.x) {
+      const int c = cc_s[(e / k) * 64 + e % k];
+      rk_s[e] = (int16_t)(c < 0 ? -1 : wpre[c >> 5] + __popc(cmask[c >> 5] & ((1u << (c & 31)) - 1u)));
+    }
+    const int nd = nd_s;
+    for (int d0 = 0; d0 < nd; d0 += cbm) {
+      const int dn = min(cbm, nd - d0);
+      __syncthreads();  // the previous batch's cases are evaluated (and the ranks written)
+      for (int i = tid; i < dn * RMAX; i += blockDim.x)
+        vt_s[i / RMAX][i % RMAX] = VtR[(size_t)(i % RMAX) * C + dl_s[d0 + i / RMAX]];
+      __syncthreads();
+      for (int i = tid; i < dn * M; i += blockDim.x) {
+        const int dd = i / M, l = i % M, c = dl_s[d0 + dd];
+        Real zr[RMAX];
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j) zr[j] = Zs[(size_t)j * Mp + l];
+        s_col[i] = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt_s[dd], meta[Mp + l], a.cpos[l], c, meta[l]);
+      }
+      __syncthreads();
+      int nm = 0;  // matches so far (warp-uniform): match i goes to warp i % NW
+      for (int e0 = 0; e0 < ne; e0 += 32) {
+        const int e = e0 + lane;
+        const int rk = e < ne ? rk_s[e] : -1;
+        const uint32_t bal = __ballot_sync(0xffffffffu, rk >= d0 && rk < d0 + dn);
+        for (uint32_t b = bal; b; b &= b - 1u, ++nm) {
+          if (nm % NW != w) continue;
+          const int ec = e0 + __ffs(b) - 1, tl = ec / k, j = ec % k, t = t0 + tl;
+          const int c = cc_s[tl * 64 + j];
+          const Real* col = s_col + (size_t)(rk_s[ec] - d0) * M;
+          const Real st = sv[(size_t)t * C + c];
+          Real v = (Real)-1;
+          int arg = 0x7fffffff;
+          for (int l = lane; l < M; l += 32) {
+            const Real x = fabs(fma(col[l], st, ptil[(size_t)t * Mp + l]));
+            if (x > v) {
+              v = x;
+              arg = l;
+            }
+          }
+          for (int off = 16; off; off >>= 1) {
+            const Real v2 = __shfl_xor_sync(0xffffffffu, v, off);
+            const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
+            if (v2 > v || (v2 == v && a2 < arg)) {
+              v = v2;
+              arg = a2;
+            }
+          }
+          if (lane == 0) o.top_mon[((size_t)tau * T + t) * k + j] = arg;
+        }
+      }
+    }
+  }
+}
+
+// The top-k pass after the tracking N-1 pass (one warp per timestep, as
+// k_topcases): each case's maximum lies in the 16-row tile that pass recorded,
+// so its most loaded monitored branch comes from those 16 rows (half a warp
+// per case, two cases at a time; the lowest row on ties).  A case of the short
+// contingency remainder (no N-1 block, no tile) rebuilds its whole column.
+template <class Real, int RMAX, int NPL>
+__global__ __launch_bounds__(128) void k_topcases_tile(Args a, const float* __restrict__ cmax,
+                                                       const int* __restrict__ cont_inv,
+                                                       const Real* __restrict__ PhiCM, int k) {
+  __shared__ float sv_[4][64];
+  __shared__ int sp_[4][64];
+  __shared__ uint32_t ck_[4][64];
+  __shared__ int cq_[4][64];
+  __shared__ float ov_[4][64];
+  __shared__ int op_[4][64];
+  const int q = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.y * 4 + w;
+  const QInfo qi = a.qi[q];
+  const int T = a.T, M = a.M, C = a.C, Mp = a.Mpad, tau = qi.tau;
+  if (t >= T) return;
+  const dcflow_results& o = a.out;
+  const size_t ob = ((size_t)tau * T + t) * k;
+  if (qi.status != ST_OK) {
+    for (int j = lane; j < k; j += 32) {
+      o.top_cont[ob + j] = -1;
+      o.top_mon[ob + j] = -1;
+      o.top_loading[ob + j] = 0.f;
+    }
+    return;
+  }
+  const int kk = k < C ? k : C;
+  select_cases<NPL>(cmax + ((size_t)tau * T + t) * C, C, kk, ck_[w], cq_[w], sp_[w], sv_[w], ov_[w], op_[w]);
+  const Real* Zs = static_cast<const Real*>(a.Zs) + (size_t)q * kRMax * Mp;
+  const Real* ptil = static_cast<const Real*>(a.ptil) + (size_t)q * T * Mp + (size_t)t * Mp;
+  const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
+  const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
+  const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C + (size_t)t * C;
+  const uint16_t* tile = a.tile + ((size_t)q * T + t) * C;
+  const int h = lane >> 4, r16 = lane & 15;
+  bool rem = false;  // some case lies in the remainder (warp-uniform after the ballot below)
+  for (int j0 = 0; j0 < k; j0 += 2) {
+    const int j = j0 + h;
+    const bool valid = j < kk && ov_[w][j] >= 0.f;
+    const int c = valid ? cont_inv[op_[w][j]] : -1;
+    const bool tiled = c >= 0 && c < a.c_rem;
+    rem |= c >= a.c_rem;
+    Real v = (Real)-1;
+    int arg = 0x7fffffff;
+    if (tiled) {
+      const int l = 16 * (int)tile[c] + r16;
+      if (l < M) {
+        Real vt[RMAX], zr[RMAX];
+#pragma unroll
+        for (int jj = 0; jj < RMAX; ++jj) {
+          vt[jj] = VtR[(size_t)jj * C + c];
+          zr[jj] = Zs[(size_t)jj * Mp + l];
+        }
+        const Real ph = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
+        v = fabs(fma(ph, sv[c], ptil[l]));
+        arg = l;
+      }
+    }
+    for (int off = 8; off; off >>= 1) {  // within the half warp
+      const Real v2 = __shfl_xor_sync(0xffffffffu, v, off);
+      const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
+      if (v2 > v || (v2 == v && a2 < arg)) {
+        v = v2;
+        arg = a2;
+      }
+    }
+    if (r16 == 0 && j < k) {
+      o.top_cont[ob + j] = valid ? op_[w][j] : -1;
+      o.top_mon[ob + j] = tiled ? arg : -1;
+      o.top_loading[ob + j] = valid ? ov_[w][j] : 0.f;
+    }
+  }
+  if (!__any_sync(0xffffffffu, rem)) return;
+  __syncwarp();  // the half-warps' writes above come first
+  for (int j = 0; j < kk; ++j) {  // the remainder's cases: the whole column
+    if (ov_[w][j] < 0.f) continue;
+    const int c = cont_inv[op_[w][j]];
+    if (c < a.c_rem) continue;
+    Real vt[RMAX];
+#pragma unroll
+    for (int jj = 0; jj < RMAX; ++jj) vt[jj] = VtR[(size_t)jj * C + c];
+    Real v = (Real)-1;
+    int arg = 0x7fffffff;
+    for (int l = lane; l < M; l += 32) {
+      Real zr[RMAX];
+#pragma unroll
+      for (int jj = 0; jj < RMAX; ++jj) zr[jj] = Zs[(size_t)jj * Mp + l];
+      const Real ph = phi_entry<Real, RMAX>(PhiCM[(size_t)c * Mp + l], zr, vt, meta[Mp + l], a.cpos[l], c, meta[l]);
+      const Real x = fabs(fma(ph, sv[c], ptil[l]));
+      if (x > v) {
+        v = x;
+        arg = l;
+      }
+    }
+    for (int off = 16; off; off >>= 1) {
+      const Real v2 = __shfl_xor_sync(0xffffffffu, v, off);
+      const int a2 = __shfl_xor_sync(0xffffffffu, arg, off);
+      if (v2 > v || (v2 == v && a2 < arg)) {
+        v = v2;
+        arg = a2;
+      }
+    }
+    if (lane == 0) o.top_mon[ob + j] = arg;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // generator-failure N-1 (the "N-1 generator" case of Sec. III-A): generator g
@@ -2349,20 +2607,48 @@ int launch_final(const Args& a, int RMAX, cudaStream_t st, const void* phicm, co
 }
 
 template <class Real, int RMAX>
-void launch_topcases_r(const Args& a, const float* cmax, const int* cinv, const void* phicm, int k, cudaStream_t st) {
-  const dim3 grid(a.nq, (a.T + 3) / 4);
+int launch_topcases_r(const Args& a, const float* cmax, const int* cinv, const void* phicm, int k, cudaStream_t st) {
   const Real* pc = static_cast<const Real*>(phicm);
+  if (a.tile) {  // after the tracking N-1 pass: 16 rows per case
+    const dim3 g(a.nq, (a.T + 3) / 4);
+    if (a.C <= 256) k_topcases_tile<Real, RMAX, 8><<<g, 128, 0, st>>>(a, cmax, cinv, pc, k);
+    else if (a.C <= 512) k_topcases_tile<Real, RMAX, 16><<<g, 128, 0, st>>>(a, cmax, cinv, pc, k);
+    else if (a.C <= 768) k_topcases_tile<Real, RMAX, 24><<<g, 128, 0, st>>>(a, cmax, cinv, pc, k);
+    else if (a.C <= 1024) k_topcases_tile<Real, RMAX, 32><<<g, 128, 0, st>>>(a, cmax, cinv, pc, k);
+    else k_topcases_tile<Real, RMAX, 64><<<g, 128, 0, st>>>(a, cmax, cinv, pc, k);
+    return 0;
+  }
+  // distinct columns per build phase: as many as 40 KB of shared memory hold (at most 16),
+  // at least one (up to 150 KB for the largest studies)
+  const size_t colb = (size_t)std::max(a.M, 1) * sizeof(Real);
+  const int cbm = (int)std::max<size_t>(1, std::min<size_t>(16, (40 * 1024) / colb));
+  const size_t dyn = (size_t)cbm * colb;
+  if (dyn <= 150 * 1024) {  // each distinct selected contingency's column built once per topology
+    static uint64_t attr[5] = {0, 0, 0, 0, 0};
+    auto go = [&](auto kern, int i) -> int {
+      if (smem_attr_once(kern, 150 * 1024, attr[i]) != cudaSuccess) return DCFLOW_ERR_CUDA;
+      kern<<<a.nq, 256, dyn, st>>>(a, cmax, cinv, pc, k, cbm);
+      return 0;
+    };
+    if (a.C <= 256) return go(k_topcols<Real, RMAX, 8>, 0);
+    if (a.C <= 512) return go(k_topcols<Real, RMAX, 16>, 1);
+    if (a.C <= 768) return go(k_topcols<Real, RMAX, 24>, 2);
+    if (a.C <= 1024) return go(k_topcols<Real, RMAX, 32>, 3);
+    return go(k_topcols<Real, RMAX, 64>, 4);
+  }
+  const dim3 grid(a.nq, (a.T + 3) / 4);
   if (a.C <= 256) k_topcases<Real, RMAX, 8><<<grid, 128, 0, st>>>(a, cmax, cinv, pc, k);
   else if (a.C <= 512) k_topcases<Real, RMAX, 16><<<grid, 128, 0, st>>>(a, cmax, cinv, pc, k);
   else if (a.C <= 1024) k_topcases<Real, RMAX, 32><<<grid, 128, 0, st>>>(a, cmax, cinv, pc, k);
   else k_topcases<Real, RMAX, 64><<<grid, 128, 0, st>>>(a, cmax, cinv, pc, k);
+  return 0;
 }
 template <class Real>
-void launch_topcases(const Args& a, int RMAX, const float* cmax, const int* cinv, const void* phicm, int k,
-                     cudaStream_t st) {
-  if (RMAX == 4) launch_topcases_r<Real, 4>(a, cmax, cinv, phicm, k, st);
-  else if (RMAX == 8) launch_topcases_r<Real, 8>(a, cmax, cinv, phicm, k, st);
-  else launch_topcases_r<Real, 16>(a, cmax, cinv, phicm, k, st);
+int launch_topcases(const Args& a, int RMAX, const float* cmax, const int* cinv, const void* phicm, int k,
+                    cudaStream_t st) {
+  if (RMAX == 4) return launch_topcases_r<Real, 4>(a, cmax, cinv, phicm, k, st);
+  if (RMAX == 8) return launch_topcases_r<Real, 8>(a, cmax, cinv, phicm, k, st);
+  return launch_topcases_r<Real, 16>(a, cmax, cinv, phicm, k, st);
 }
 
 template <class Real>
@@ -2800,6 +3086,10 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   const int C_eff = ctx->C_eff;       // contingencies that can be valid (base-grid bridges excluded)
   // FP32 full solve on request: the N-1 kernel runs over each topology's compacted valid contingencies
   const bool cmp = !fp64 && mode == kModeFull && C_eff > 0 && plan.compact;
+  // top-k cases after the dense FFMA-build N-1: its tracking variant records each maximum's
+  // 16-row tile, and the top-k pass evaluates only that tile per case
+  const bool use_tile = top_k > 0 && !fp64 && !tc && !cmp && mode == kModeFull && C_eff > 0 &&
+                        pick_tt(T, false) >= 4;
   // a remainder of at most kRemCols contingencies beyond the last full block of 64
   // goes to the final pass (a column each over the monitored rows) instead of an
   // N-1 block that would compute 64 columns for it (plain full solves only)
@@ -2848,6 +3138,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     if (mode == kModeFull && (B.cmr.ensure(c * T * std::max(C, 1) * rs) ||
                               B.p2max.ensure(c * T * std::max(ncb, 1) * rs)))
       return DCFLOW_ERR_OOM;
+    if (use_tile && B.tile.ensure(c * T * std::max(C, 1) * sizeof(uint16_t))) return DCFLOW_ERR_OOM;
     if (TI && (B.zcd.ensure(c * kRMax * std::max(C, 1) * rs) || B.tiel.ensure(c * 64 * sizeof(int)) ||
                B.tirow.ensure(c * 64 * sizeof(int)) || B.nel.ensure(c * sizeof(int))))
       return DCFLOW_ERR_OOM;
@@ -2931,6 +3222,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   // tie band of the reported indices: the form's tolerance unless the option sets one (negative: none)
   base.tie_eps = ctx->opt.tie_band < 0 ? 0.0 : (ctx->opt.tie_band > 0 ? ctx->opt.tie_band : (fp64 ? 1e-10 : 1e-4));
   base.cont_inv = ctx->cont_inv.as<int>();
+  base.tile = nullptr;
   base.cont_pos = ctx->cont_pos.as<int>();
   base.Mpad = Mp;
   base.ldc = ctx->ldc;
@@ -3215,6 +3507,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       }
       nsel_dev = SB.nsel.as<int>();
     } else if (C_eff > 0) {
+      if (use_tile) af.tile = B.tile.as<uint16_t>();
       int rc = run_n1(af, RMAX, T, true, cmp ? &B : nullptr);
       if (rc) return rc;
     }
@@ -3252,10 +3545,14 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     }
     if (top_k > 0) {
       const int pe = ctx->prof_begin(st);
-      if (fp64)
-        launch_topcases<double>(af, RMAX, af.out.n1_cont_max, ctx->cont_inv.as<int>(), ctx->PhiCM.p, top_k, st);
-      else
-        launch_topcases<float>(af, RMAX, af.out.n1_cont_max, ctx->cont_inv.as<int>(), ctx->PhiCM.p, top_k, st);
+      const int rct = fp64 ? launch_topcases<double>(af, RMAX, af.out.n1_cont_max, ctx->cont_inv.as<int>(),
+                                                     ctx->PhiCM.p, top_k, st)
+                           : launch_topcases<float>(af, RMAX, af.out.n1_cont_max, ctx->cont_inv.as<int>(),
+                                                    ctx->PhiCM.p, top_k, st);
+      if (rct) {
+        set_error("dcflow_solve_batch: top-k pass shared memory");
+        return rct;
+      }
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
       ctx->prof_end(pe, DCFLOW_PROF_TOPCASES, st);
