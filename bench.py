@@ -445,7 +445,7 @@ def run_ours(args):
             results[f"fp32_gen{args.gens}"] = {"value": lf_all * steps / tg, "ms_per_step": 1e3 * tg / steps,
                                                "loadflows_per_step": lf_all,
                                                "generator_cases_per_step": ngen_cases, "steps": steps,
-                                               "kernels": {"name": "k_gen_tile", "ms_per_step": kg["gen_ms"],
+                                               "kernels": {"name": "k_gen_tma", "ms_per_step": kg["gen_ms"],
                                                           "entries_per_s_T": gen_rate, "alu_peak_T": alu_peak,
                                                           "frac": gen_rate / alu_peak if gen_rate else None},
                                                "note": f"fp32 solve plus {args.gens} generator-failure N-1 cases "

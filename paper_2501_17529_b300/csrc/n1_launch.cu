@@ -25,7 +25,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }  // namespace
 
 int encode_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
-               const uint32_t* box) {
+               const uint32_t* box, bool swizzle128) {
   auto fn = tensor_map_encoder();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -40,7 +40,8 @@ int encode_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
     if (i + 1 < rank) s[i] = strides[i];
   }
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void*>(base), d, s, b, e,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");

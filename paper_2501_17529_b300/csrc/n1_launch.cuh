@@ -12,8 +12,11 @@
 namespace dcf {
 
 // Row-major FP32 tensor of `rank` dims (innermost first); strides in bytes for dims 1..rank-1.
+// swizzle128: the box lands with 128-byte swizzling (its inner extent is then
+// 128 bytes and the destination 1024-byte aligned): 16-byte chunk c of box
+// row y sits at chunk c ^ (y % 8).
 int encode_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
-               const uint32_t* box);
+               const uint32_t* box, bool swizzle128 = false);
 // tc: the Phi_f tile on the tensor cores (split BF16x3; the maps then carry
 // the BF16 Z rows and a Phi tile 68 columns wide) instead of FFMA2.
 // every contingency column, TT timesteps per pass (TT = 1: one thread per

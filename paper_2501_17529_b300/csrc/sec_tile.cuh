@@ -9,6 +9,7 @@
 #pragma once
 
 #include "args.cuh"
+#include "n1_tma.cuh"
 
 namespace dcf {
 
@@ -25,43 +26,53 @@ __device__ __forceinline__ float sec_ovl(float v) { return __saturatef(fmaf(fabs
 // generator failures: generator g at bus b with output P_g[t] fails, the slack
 // takes it up, and the flows become p_f - P_g PTDF_f[:, b] with
 //   PTDF_f[l, b] = PTDF[l, b] - Z[l, :] K^{-1} Sigma^T PTDF[:, b]   (Eq. (3)).
-// Block = one topology and one pass of TT = 8 TR timesteps (grid y); its 4
-// warps take the 32-row tiles w, w + 4, ...; the generators go in groups of
-// 16.  Lane (gq, tq) owns the cells (generator gq + 4 i, timestep TR tq + j),
-// i < 4, j < TR.  Per tile each lane forms its row's 16 columns
-// PTDF_f[l, b_g] / limit_l and copies its row of p_f / limit into the warp's
-// tile as row pairs; then every lane runs its cells over the 16 row pairs.
-// The column entries and the flows are the same multiply-adds as the
-// one-thread-per-row form, so every entry is bit-identical to it.
-// ---------------------------------------------------------------------------
-template <int TR>
-struct GenTile {
-  static constexpr int TT = 8 * TR, GG = 16, RT = 32, NW = 4;
-  static constexpr int CP = GG + 2;  // float2 pitch of a column row pair (16-byte rows for the paired loads)
-  static constexpr int TP = TT + 1;  // float2 pitch of a p_f row pair (spreads the lanes' stores over the banks)
-  static constexpr int NCELL = GG * TT;
-  static constexpr int kTiles = NW * (RT / 2) * (CP + TP) * 8;  // bytes of the warps' tiles
+// Block = one topology and one pass of TT = 8 TR timesteps (grid y), the
+// generators in groups of 16, fed like the fused N-1 kernel: a 2-stage TMA ring
+// of 32-row tiles holding the 16 generators' rows PTDF[l, b_g] / limit_l
+// [16][32], Z / limit [RMAX][32], the metadata rows [4][32] and p_f / limit
+// [TT][32], the last with 128-byte swizzling so that the compute threads read
+// its row pairs without bank conflicts and without a transposition.  Per tile
+// thread (g, tb) builds rows 4 tb .. 4 tb + 3 of generator g's column; thread
+// (g, tg) owns the cells of generator g at timesteps TR tg + j.  The column
+// entries and flows are the multiply-adds of the one-thread-per-row FP64 form.
+// Waits are bounded (error flag 1).
+struct GenMaps {
+  CUtensorMap pg, zt, meta, pt;
+};
+template <int TR, int RMAX>
+struct GenTmaLayout {
+  static constexpr int TT = 8 * TR, RT = 32, GG = 16;
+  static constexpr int a1k(int x) { return (x + 1023) / 1024 * 1024; }
+  static constexpr int kPt = TT * RT * 4;           // swizzled, first in the stage (1024-aligned)
+  static constexpr int kOffPg = kPt;
+  static constexpr int kOffZt = kOffPg + GG * RT * 4;
+  static constexpr int kOffMeta = kOffZt + RMAX * RT * 4;
+  static constexpr int kTx = kOffMeta + 4 * RT * 4;  // bytes landing per stage
+  static constexpr int kStage = a1k(kTx);
+  static constexpr int kCP = GG + 1;                 // float2 pitch of a column row pair
+  static constexpr int kOffCol = 2 * kStage;         // float2 [RT / 2][kCP]
+  static constexpr int kOffBar = kOffCol + (RT / 2) * kCP * 8;
+  static constexpr int kBytes = kOffBar + 64 + 1024;  // + alignment slack of the dynamic base
 };
 
 template <int RMAX, int TR>
-__global__ __launch_bounds__(128, 6) void k_gen_tile(Args a, int G, const int* __restrict__ gen_bus,
-                                                  const double* __restrict__ gen_p, const double* __restrict__ PtdfN,
-                                                  int V, const float* __restrict__ PG) {
-  using L = GenTile<TR>;
-  constexpr int TT = L::TT, GG = L::GG, RT = L::RT, NW = L::NW, CP = L::CP, TP = L::TP, NCELL = L::NCELL;
-  __shared__ __align__(16) unsigned char tiles[L::kTiles];  // per warp: columns, then p_f; after the loop: maxima
-  __shared__ float ov_s[NW][NCELL];  // overload sums x 2^-20 per warp and cell (written by the owner lane)
+__global__ __launch_bounds__(128) void k_gen_tma(const __grid_constant__ GenMaps maps, Args a, int G,
+                                                 const int* __restrict__ gen_bus, const double* __restrict__ gen_p,
+                                                 const double* __restrict__ PtdfN, int V) {
+  using L = GenTmaLayout<TR, RMAX>;
+  constexpr int TT = L::TT, RT = L::RT, GG = L::GG, CP = L::kCP;
+  extern __shared__ unsigned char gen_dyn[];
   __shared__ double sv_s[kRMax][GG];
   __shared__ float beta_s[GG][RMAX];
+  __shared__ float mx_s[TT][GG + 1], ov_s[TT][GG + 1];
   __shared__ int mp_s[kRMax + 1];
   __shared__ float bv_s[TT];
   __shared__ int bg_s[TT];
   __shared__ double bo_s[TT];
-  static_assert(NW * NCELL * 4 <= L::kTiles, "maxima fit the tiles");
-  const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int q = blockIdx.x, tid = threadIdx.x;
   const int t0 = blockIdx.y * TT;
   const QInfo qi = a.qi[q];
-  const int T = a.T, M = a.M, Mp = a.Mpad, tau = qi.tau;
+  const int T = a.T, M = a.M, tau = qi.tau;
   const dcflow_results& o = a.out;
   if (qi.status != ST_OK) {
     for (int t = t0 + tid; t < T && t < t0 + TT; t += blockDim.x) {
@@ -71,6 +82,10 @@ __global__ __launch_bounds__(128, 6) void k_gen_tile(Args a, int G, const int* _
     }
     return;
   }
+  const uint32_t raw = smem_u32(gen_dyn);
+  unsigned char* sm = gen_dyn + (((raw + 1023u) & ~1023u) - raw);  // 1024-aligned (the swizzled tiles)
+  float2* s_col = reinterpret_cast<float2*>(sm + L::kOffCol);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kOffBar);
   const int r = qi.r;
   for (int i = tid; i <= r; i += blockDim.x) mp_s[i] = a.mod_ptr[(size_t)q * (kRMax + 1) + i];
   for (int t = tid; t < TT; t += blockDim.x) {
@@ -78,24 +93,22 @@ __global__ __launch_bounds__(128, 6) void k_gen_tile(Args a, int G, const int* _
     bg_s[t] = -1;
     bo_s[t] = 0.0;
   }
+  if (tid == 0) {
+    for (int st = 0; st < 2; ++st) mbar_init(smem_u32(&bars[st]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   const double* Kinv = a.Kinv + (size_t)q * kRMax * kRMax;
-  const float* Zs = static_cast<const float*>(a.Zs) + (size_t)q * kRMax * Mp;
-  const float* ptil = static_cast<const float*>(a.ptil) + (size_t)q * T * Mp;
-  const float* meta = static_cast<const float*>(a.diagv) + (size_t)q * 4 * Mp;
   const int* en = a.ent_n + (size_t)q * kEntMax;
   const int8_t* es = a.ent_s + (size_t)q * kEntMax;
-  float2* col_w = reinterpret_cast<float2*>(tiles) + w * (RT / 2) * CP;
-  float2* pt_w = reinterpret_cast<float2*>(tiles) + NW * (RT / 2) * CP + w * (RT / 2) * TP;
-  float* colf = reinterpret_cast<float*>(col_w);
-  float* ptf = reinterpret_cast<float*>(pt_w);
-  float* mx_s = reinterpret_cast<float*>(tiles);  // [NW][NCELL] after the tile loop
-  const int gq = lane & 3, tq = lane >> 2, pr = lane >> 1, hf = lane & 1;
+  const int cg = tid & 15, tg = tid >> 4;  // compute role; build role: generator cg, rows 4 tg .. 4 tg + 3
   const int ntile = (M + RT - 1) / RT;
-  for (int g0 = 0; g0 < G; g0 += GG) {
+  int seq = 0;  // tiles issued so far over the generator groups (the ring's phase)
+  bool failed = false;
+  int fsq = 0;  // the tile whose wait expired (the only one in flight then)
+  for (int g0 = 0; g0 < G && !failed; g0 += GG) {
     const int gn = min(GG, G - g0);
-    __syncthreads();  // mp_s ready; the previous group's maxima and sums consumed
-    // Sigma^T PTDF[:, b_g] per modification i (FP64), then K^{-1} times it
-    for (int p = tid; p < r * GG; p += blockDim.x) {
+    __syncthreads();  // mp_s and the barriers ready; the previous group's maxima consumed
+    for (int p = tid; p < r * GG; p += blockDim.x) {  // Sigma^T PTDF[:, b_g] per modification (FP64)
       const int i = p / GG, g = p % GG;
       double x = 0.0;
       if (g < gn) {
@@ -104,97 +117,114 @@ __global__ __launch_bounds__(128, 6) void k_gen_tile(Args a, int G, const int* _
       }
       sv_s[i][g] = x;
     }
-    for (int p = tid; p < NW * NCELL; p += blockDim.x) ov_s[p / NCELL][p % NCELL] = 0.f;
     __syncthreads();
-    for (int p = tid; p < GG * RMAX; p += blockDim.x) {
+    for (int p = tid; p < GG * RMAX; p += blockDim.x) {  // K^{-1} times it
       const int g = p / RMAX, j = p % RMAX;
       double x = 0.0;
       for (int i = 0; i < r; ++i) x = fma(Kinv[j * kRMax + i], sv_s[i][g], x);
       beta_s[g][j] = (float)x;
     }
-    __syncthreads();
-    float2 s2[4][TR];  // -P_g[t] of the lane's cells, duplicated for the row pairs
-    float mx[4][TR];
+    float2 s2[TR];  // -P_g[t] of the thread's cells, duplicated for the row pairs
+    float mx[TR], ov[TR];
+    int tx[TR];  // the cells' timesteps within the pass: line index of the swizzled p_f tile
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < TR; ++j) {
-        const int g = gq + 4 * i, t = t0 + tq * TR + j;
-        const float pv = (g < gn && t < T) ? (float)gen_p[(size_t)t * G + g0 + g] : 0.f;
-        s2[i][j] = make_float2(-pv, -pv);
-        mx[i][j] = 0.f;
+    for (int j = 0; j < TR; ++j) {
+      const int t = tg * TR + j;
+      const float pv = (cg < gn && t0 + t < T) ? (float)gen_p[(size_t)(t0 + t) * G + g0 + cg] : 0.f;
+      s2[j] = make_float2(-pv, -pv);
+      mx[j] = 0.f;
+      ov[j] = 0.f;
+      tx[j] = t;
+    }
+    auto issue = [&](int k, int sq) {
+      const int st = sq & 1;
+      unsigned char* base = sm + st * L::kStage;
+      const uint32_t bar = smem_u32(&bars[st]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(bar, L::kTx);
+      tma_load_3d(smem_u32(base), &maps.pt, k * RT, t0, q, bar);
+      tma_load_2d(smem_u32(base + L::kOffPg), &maps.pg, k * RT, g0, bar);
+      tma_load_3d(smem_u32(base + L::kOffZt), &maps.zt, k * RT, 0, q, bar);
+      tma_load_3d(smem_u32(base + L::kOffMeta), &maps.meta, k * RT, 0, q, bar);
+    };
+    __syncthreads();  // beta ready; every thread is past the previous group's last tile
+    if (tid == 0 && ntile > 0) issue(0, seq);
+    for (int k = 0; k < ntile; ++k) {
+      const int sq = seq + k, st = sq & 1;
+      const bool got = mbar_wait(smem_u32(&bars[st]), (uint32_t)((sq >> 1) & 1));
+      if (__syncthreads_or(!got)) {  // also: every thread is done with tile k - 1 (s_col, the other stage)
+        failed = true;
+        fsq = sq;
+        break;
       }
-    for (int k = w; k < ntile; k += NW) {
-      const int l = k * RT + lane;
-      const bool in = l < M;
-      float zr[RMAX];
+      if (tid == 0 && k + 1 < ntile) issue(k + 1, sq + 1);
+      const unsigned char* base = sm + st * L::kStage;
+      const float* pg_t = reinterpret_cast<const float*>(base + L::kOffPg);
+      const float* zt_t = reinterpret_cast<const float*>(base + L::kOffZt);
+      const float* rm_t = reinterpret_cast<const float*>(base + L::kOffMeta) + RT;  // metadata row 1
+      {  // build rows 4 tg .. 4 tg + 3 of generator cg's column
+        const int r0 = 4 * tg;
+        const float4 pg4 = *reinterpret_cast<const float4*>(&pg_t[cg * RT + r0]);
+        float c[4] = {pg4.x, pg4.y, pg4.z, pg4.w};
 #pragma unroll
-      for (int j = 0; j < RMAX; ++j) zr[j] = in ? Zs[(size_t)j * Mp + l] : 0.f;
-      const float rm = in ? meta[Mp + l] : 0.f;  // an outaged monitored branch carries nothing
-      __syncwarp();  // every lane is done with the previous tile
-#pragma unroll 4
-      for (int g = 0; g < GG; ++g) {  // column position: generator gq + 4 i at gq * 4 + i (paired loads)
-        float c = (in && g < gn) ? PG[(size_t)(g0 + g) * M + l] : 0.f;
-#pragma unroll
-        for (int j = 0; j < RMAX; ++j) c = fmaf(-zr[j], beta_s[g][j], c);
-        colf[(pr * CP + (g & 3) * 4 + (g >> 2)) * 2 + hf] = c * rm;
+        for (int j = 0; j < RMAX; ++j) {
+          const float4 z = *reinterpret_cast<const float4*>(&zt_t[j * RT + r0]);
+          const float b = beta_s[cg][j];
+          c[0] = fmaf(-z.x, b, c[0]);
+          c[1] = fmaf(-z.y, b, c[1]);
+          c[2] = fmaf(-z.z, b, c[2]);
+          c[3] = fmaf(-z.w, b, c[3]);
+        }
+        const float4 rm = *reinterpret_cast<const float4*>(&rm_t[r0]);
+        s_col[(2 * tg) * CP + cg] = make_float2(c[0] * rm.x, c[1] * rm.y);
+        s_col[(2 * tg + 1) * CP + cg] = make_float2(c[2] * rm.z, c[3] * rm.w);
       }
-#pragma unroll 4
-      for (int t = 0; t < TT; ++t)
-        ptf[(pr * TP + t) * 2 + hf] = (in && t0 + t < T) ? ptil[(size_t)(t0 + t) * Mp + l] : 0.f;
-      __syncwarp();
-      float mt[4][TR];
+      __syncthreads();
+      float mt[TR];
 #pragma unroll
       for (int rp = 0; rp < RT / 2; ++rp) {
-        const float4 u0 = *reinterpret_cast<const float4*>(&col_w[rp * CP + gq * 4]);
-        const float4 u1 = *reinterpret_cast<const float4*>(&col_w[rp * CP + gq * 4 + 2]);
-        const float2 ph[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
-                              make_float2(u1.z, u1.w)};
-        float2 pt[TR];
-#pragma unroll
-        for (int j = 0; j < TR; ++j) pt[j] = pt_w[rp * TP + tq * TR + j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < TR; ++j) {
-            const float2 v = __ffma2_rn(ph[i], s2[i][j], pt[j]);  // rows 2 rp and 2 rp + 1
-            mt[i][j] = rp == 0 ? sec_max3abs(v.x, v.y, v.y) : sec_max3abs(mt[i][j], v.x, v.y);
-          }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
+        const float2 ph = s_col[rp * CP + cg];
 #pragma unroll
         for (int j = 0; j < TR; ++j) {
-          mx[i][j] = fmaxf(mx[i][j], mt[i][j]);
-          if (mt[i][j] > 1.f) {  // the overload terms of this cell over the tile
-            float s = 0.f;
-            for (int rp = 0; rp < RT / 2; ++rp) {
-              const float2 v = __ffma2_rn(col_w[rp * CP + gq * 4 + i], s2[i][j], pt_w[rp * TP + tq * TR + j]);
-              s += sec_ovl(v.x) + sec_ovl(v.y);
-            }
-            ov_s[w][(gq + 4 * i) * TT + tq * TR + j] += s;
-          }
+          // rows 2 rp, 2 rp + 1 of timestep tx[j]: 16-byte chunk rp / 2 of line tx[j], swizzled
+          const float2 pt = *reinterpret_cast<const float2*>(
+              base + tx[j] * 128 + ((((rp >> 1) ^ tx[j]) & 7) << 4) + ((rp & 1) << 3));
+          const float2 v = __ffma2_rn(ph, s2[j], pt);
+          mt[j] = rp == 0 ? sec_max3abs(v.x, v.y, v.y) : sec_max3abs(mt[j], v.x, v.y);
         }
+      }
+#pragma unroll
+      for (int j = 0; j < TR; ++j) {
+        mx[j] = fmaxf(mx[j], mt[j]);
+        if (mt[j] > 1.f) {  // the overload terms of this cell over the tile
+          float sum = 0.f;
+          for (int rp = 0; rp < RT / 2; ++rp) {
+            const float2 pt = *reinterpret_cast<const float2*>(
+                base + tx[j] * 128 + ((((rp >> 1) ^ tx[j]) & 7) << 4) + ((rp & 1) << 3));
+            const float2 v = __ffma2_rn(s_col[rp * CP + cg], s2[j], pt);
+            sum += sec_ovl(v.x) + sec_ovl(v.y);
+          }
+          ov[j] += sum;
+        }
+      }
     }
-    __syncthreads();  // every warp is done with its tiles (the maxima reuse them)
+    seq += ntile;
+    if (failed) break;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < TR; ++j) mx_s[w * NCELL + (gq + 4 * i) * TT + tq * TR + j] = mx[i][j];
+    for (int j = 0; j < TR; ++j) {
+      mx_s[tg * TR + j][cg] = mx[j];
+      ov_s[tg * TR + j][cg] = ov[j];
+    }
     __syncthreads();
-    for (int t = tid; t < TT; t += blockDim.x) {  // over the warps and generators, the lowest on ties
+    for (int t = tid; t < TT; t += blockDim.x) {  // over the generators, the lowest on ties
       if (t0 + t >= T) continue;
       float bv = bv_s[t];
       int bg = bg_s[t];
       double bo = bo_s[t];
       for (int g = 0; g < gn; ++g) {
-        float v = mx_s[g * TT + t];
-        for (int w2 = 0; w2 < NW; ++w2) {
-          v = fmaxf(v, mx_s[w2 * NCELL + g * TT + t]);
-          bo += (double)ov_s[w2][g * TT + t] * 1048576.0;
-        }
-        if (v > bv) {
-          bv = v;
+        bo += (double)ov_s[t][g] * 1048576.0;
+        if (mx_s[t][g] > bv) {
+          bv = mx_s[t][g];
           bg = g0 + g;
         }
       }
@@ -202,6 +232,13 @@ __global__ __launch_bounds__(128, 6) void k_gen_tile(Args a, int G, const int* _
       bg_s[t] = bg;
       bo_s[t] = bo;
     }
+  }
+  if (failed) {  // the tile in flight lands (bounded wait) before the block exits
+    if (tid == 0) {
+      mbar_wait(smem_u32(&bars[fsq & 1]), (uint32_t)((fsq >> 1) & 1));
+      atomicExch(a.err, 1);
+    }
+    return;
   }
   __syncthreads();
   for (int t = tid; t < TT; t += blockDim.x) {

@@ -2084,13 +2084,13 @@ __global__ __launch_bounds__(128) void k_topcases_tile(Args a, const float* __re
 // branches of |flow| / limit, the generator reaching it (lowest on ties), and
 // the overload sum.
 // ---------------------------------------------------------------------------
-// PTDF[mon, gen_bus] / limit, one row per generator (once per solve)
+// PTDF[mon, gen_bus] / limit, one row per generator, row stride ld (once per solve)
 template <class Real>
-__global__ void k_gen_cols(int G, int M, int V, const int* __restrict__ gen_bus, const int* __restrict__ monN,
+__global__ void k_gen_cols(int G, int M, int ld, int V, const int* __restrict__ gen_bus, const int* __restrict__ monN,
                            const double* __restrict__ PtdfN, const double* __restrict__ inv_lim, Real* __restrict__ PG) {
   const int g = blockIdx.y;
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M; l += gridDim.x * blockDim.x)
-    PG[(size_t)g * M + l] = (Real)(PtdfN[(size_t)monN[l] * V + gen_bus[g]] * inv_lim[l]);
+    PG[(size_t)g * ld + l] = (Real)(PtdfN[(size_t)monN[l] * V + gen_bus[g]] * inv_lim[l]);
 }
 
 // One block per topology; thread i owns monitored rows i, i + 128, ...: per
@@ -2160,7 +2160,7 @@ __global__ __launch_bounds__(128) void k_gen_n1(Args a, int G, const int* __rest
       for (int j = 0; j < TT; ++j) pt[j] = (t0 + j < T) ? ptil[(size_t)(t0 + j) * Mp + l] : (Real)0;
       const Real rm = meta[Mp + l];  // an outaged monitored branch carries nothing
       for (int g = 0; g < gn; ++g) {
-        Real col = PG[(size_t)(g0 + g) * M + l];
+        Real col = PG[(size_t)(g0 + g) * Mp + l];
 #pragma unroll
         for (int j = 0; j < RMAX; ++j) col = fma(-zr[j], beta_s[g][j], col);
         col *= rm;
@@ -2669,17 +2669,41 @@ void launch_ti_expand(const Args& ap, int RMAX, int T, int U, const dcflow_batch
 inline int sec_tr(int T) { return T > 16 ? 3 : (T > 8 ? 2 : 1); }
 
 // FP64: one thread per monitored row, passes of 8 timesteps; FP32: the
-// register-tiled kernel, every pass in one launch (grid y).  Returns the launches.
+// TMA-fed kernel, every pass in one launch (grid y).  Returns the launches, or
+// minus an error code.
 template <class Real, int RMAX>
 int launch_gen_r(const Args& a, int G, const int* gen_bus, const double* gen_p, const double* ptdf, int V,
                  const Real* P, cudaStream_t st) {
   if constexpr (sizeof(Real) == 4) {
-    const int tr = sec_tr(a.T);
-    const dim3 grid(a.nq, (a.T + 8 * tr - 1) / (8 * tr));
-    if (tr == 3) k_gen_tile<RMAX, 3><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
-    else if (tr == 2) k_gen_tile<RMAX, 2><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
-    else k_gen_tile<RMAX, 1><<<grid, 128, 0, st>>>(a, G, gen_bus, gen_p, ptdf, V, P);
-    return 1;
+    const int tr = sec_tr(a.T), TT = 8 * tr;
+    const dim3 grid(a.nq, (a.T + TT - 1) / TT);
+    const uint64_t M = (uint64_t)a.M, Mp = (uint64_t)a.Mpad, nq = (uint64_t)a.nq;
+    GenMaps maps;
+    const uint64_t d_pg[2] = {M, (uint64_t)G}, s_pg[1] = {Mp * 4};
+    const uint32_t b_pg[2] = {32, 16};
+    const uint64_t d_zt[3] = {M, (uint64_t)kRMax, nq}, s_zt[2] = {Mp * 4, Mp * kRMax * 4};
+    const uint32_t b_zt[3] = {32, (uint32_t)RMAX, 1};
+    const uint64_t d_me[3] = {M, 4, nq}, s_me[2] = {Mp * 4, Mp * 16};
+    const uint32_t b_me[3] = {32, 4, 1};
+    const uint64_t d_pt[3] = {M, (uint64_t)a.T, nq}, s_pt[2] = {Mp * 4, Mp * a.T * 4};
+    const uint32_t b_pt[3] = {32, (uint32_t)TT, 1};
+    int rc = encode_map(&maps.pg, P, 2, d_pg, s_pg, b_pg);
+    if (!rc) rc = encode_map(&maps.zt, a.Zs, 3, d_zt, s_zt, b_zt);
+    if (!rc) rc = encode_map(&maps.meta, a.diagv, 3, d_me, s_me, b_me);
+    if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt, true);
+    if (rc) return -rc;
+    static uint64_t attr[3] = {0, 0, 0};
+    auto go = [&](auto kern, int bytes, int i) -> int {
+      if (smem_attr_once(kern, bytes, attr[i]) != cudaSuccess) {
+        set_error("dcflow_solve_batch: generator pass shared memory");
+        return -DCFLOW_ERR_CUDA;
+      }
+      kern<<<grid, 128, bytes, st>>>(maps, a, G, gen_bus, gen_p, ptdf, V);
+      return 1;
+    };
+    if (tr == 3) return go(k_gen_tma<RMAX, 3>, GenTmaLayout<3, RMAX>::kBytes, 0);
+    if (tr == 2) return go(k_gen_tma<RMAX, 2>, GenTmaLayout<2, RMAX>::kBytes, 1);
+    return go(k_gen_tma<RMAX, 1>, GenTmaLayout<1, RMAX>::kBytes, 2);
   } else {
     constexpr int TT = 8;
     int n = 0;
@@ -3183,14 +3207,16 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
         set_error("dcflow_solve_batch: gen_bus out of range");
         return DCFLOW_ERR_INVALID_ARG;
       }
-    if (ctx->gen_cols.ensure((size_t)G * std::max(M, 1) * rs)) return DCFLOW_ERR_OOM;
+    if (ctx->gen_cols.ensure((size_t)G * Mp * rs)) return DCFLOW_ERR_OOM;  // rows of Mp: 16-byte pitch (TMA)
     const dim3 grd((M + 255) / 256, G);
     if (fp64)
-      k_gen_cols<double><<<grd, 256, 0, st>>>(G, M, ctx->V, bt->gen_bus, ctx->monN.as<int>(), ctx->PtdfN.as<double>(),
-                                              ctx->inv_lim.as<double>(), ctx->gen_cols.as<double>());
+      k_gen_cols<double><<<grd, 256, 0, st>>>(G, M, Mp, ctx->V, bt->gen_bus, ctx->monN.as<int>(),
+                                              ctx->PtdfN.as<double>(), ctx->inv_lim.as<double>(),
+                                              ctx->gen_cols.as<double>());
     else
-      k_gen_cols<float><<<grd, 256, 0, st>>>(G, M, ctx->V, bt->gen_bus, ctx->monN.as<int>(), ctx->PtdfN.as<double>(),
-                                             ctx->inv_lim.as<double>(), ctx->gen_cols.as<float>());
+      k_gen_cols<float><<<grd, 256, 0, st>>>(G, M, Mp, ctx->V, bt->gen_bus, ctx->monN.as<int>(),
+                                             ctx->PtdfN.as<double>(), ctx->inv_lim.as<double>(),
+                                             ctx->gen_cols.as<float>());
     DCF_CHECK_LAUNCH();
     ++ctx->launches;
   }
@@ -3535,11 +3561,12 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     }
     if (G > 0) {
       const int pe = ctx->prof_begin(st);
-      ctx->launches +=
-          fp64 ? launch_gen<double>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V,
-                                    ctx->gen_cols.p, st)
-               : launch_gen<float>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V,
-                                   ctx->gen_cols.p, st);
+      const int ng = fp64 ? launch_gen<double>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V,
+                                               ctx->gen_cols.p, st)
+                          : launch_gen<float>(af, RMAX, G, bt->gen_bus, bt->gen_p, ctx->PtdfN.as<double>(), ctx->V,
+                                              ctx->gen_cols.p, st);
+      if (ng < 0) return -ng;  // a tensor map the driver refused (the message is set)
+      ctx->launches += ng;
       DCF_CHECK_LAUNCH();
       ctx->prof_end(pe, DCFLOW_PROF_GEN, st);
     }
