@@ -426,7 +426,7 @@ def run_ours(args):
             rec = nok * T_STEPS * args.top_k * n_mon  # entries of the cases' recomputed columns
             results[f"fp32_top{args.top_k}"] = {"value": lf_all * steps / tk, "ms_per_step": 1e3 * tk / steps,
                                                 "loadflows_per_step": lf_all, "steps": steps,
-                                                "kernels": {"name": "k_topcols", "ms_per_step": kk["topcases_ms"],
+                                                "kernels": {"name": "k_topcases_tile", "ms_per_step": kk["topcases_ms"],
                                                            "column_entries_per_s_T": rec / (kk["topcases_ms"] / 1e3) / 1e12
                                                            if kk["topcases_ms"] else None},
                                                 "note": f"fp32 solve plus the {args.top_k} worst N-1 cases "
@@ -491,7 +491,7 @@ def run_ours(args):
             results[f"fp32_multi{args.multi}"] = {
                 "value": lf_all * steps / tm, "ms_per_step": 1e3 * tm / steps, "loadflows_per_step": lf_all,
                 "multi_cases_per_step": nm_cases, "steps": steps,
-                "kernels": {"name": "k_multi_tile", "ms_per_step": km["multi_ms"],
+                "kernels": {"name": "k_multi_tma", "ms_per_step": km["multi_ms"],
                            "entries_per_s_T": nm_cases / ws * n_mon / (km["multi_ms"] / 1e3) / 1e12 if km["multi_ms"] else None,
                            "alu_peak_T": alu_peak,
                            "frac": (nm_cases / ws * n_mon / (km["multi_ms"] / 1e3) / 1e12 / alu_peak) if km["multi_ms"] else None,

@@ -1,5 +1,5 @@
-// Register-tiled FP32 kernels of the generator-failure N-1 (Sec. III-A) and
-// the multi-outage N-1 (Def. 4, MODF).  Both evaluate, per topology, a set of
+// TMA-fed FP32 kernels of the generator-failure N-1 (Sec. III-A) and the
+// multi-outage N-1 (Def. 4, MODF).  Both evaluate, per topology, a set of
 // cases (a generator, a set of branches) against every monitored row and
 // timestep; like the fused N-1 kernel they keep one running |max| per
 // (case, timestep) cell in registers, fold two rows per packed multiply-add,
@@ -253,33 +253,45 @@ __global__ __launch_bounds__(128) void k_gen_tma(const __grid_constant__ GenMaps
 // ---------------------------------------------------------------------------
 // multi-outage sets: p_n1 = p_f + Phi_f[:, O] w_t with w_t = (I - Phi_f[O, O])^{-1}
 // p_f[O, t] from the set preparation.  Block = one topology and one pass of
-// TT = 8 TR timesteps (grid y), 256 threads, sets in groups of 32.  Per tile
-// of 16 monitored rows the block builds the 4 member columns Phi_f[:, o_a] /
-// limit of every set of the group (thread (set, member, half) builds 8 rows;
-// absent members are zero columns) into row pairs, and copies p_f / limit.
-// Thread (warp w, lane) owns set 4 w + lane / 8 at timesteps TR (lane % 8) + j:
-// per row pair four packed multiply-adds (members in order, as the
-// one-thread-per-row form) and one three-input |max| per timestep.  A member's
-// own monitored row carries nothing: its column entry there becomes
-// Phi_f[o, o] / limit - 1 / limit, which makes the row's flow cancel to
-// (rounding) zero, the convention LODF[c, c] = -1 of the single contingencies.
-// Two tile buffers alternate, so one barrier per tile suffices.
+// TT = 8 TR timesteps (grid y), 256 threads, sets in groups of 32, fed by a
+// 2-stage TMA ring of 32-row tiles: p_f / limit [TT][32] (128-byte swizzled),
+// the group's member rows Phi[mon, o] / limit [128][32] (the sets of a group
+// own consecutive entries, so one box covers them), Z / limit [RMAX][32] and
+// the metadata rows [4][32].  Per tile thread (set, member, half) builds 16
+// rows of its member column Phi_f[:, o_a] / limit into the column tile (absent
+// members are zero columns); thread (warp w, lane) owns set 4 w + lane / 8 at
+// timesteps TR (lane % 8) + j: per row pair four packed multiply-adds (members
+// in order, as the one-thread-per-row FP64 form) and one three-input |max|
+// per timestep.  A member's own monitored row carries nothing: its column entry
+// there becomes Phi_f[o, o] / limit - 1 / limit, which makes the row's flow
+// cancel to (rounding) zero, the convention LODF[c, c] = -1 of the single
+// contingencies.  Waits are bounded (error flag 1).
 // ---------------------------------------------------------------------------
-template <int TR>
-struct MultiTile {
-  static constexpr int TT = 8 * TR, SG = 32, LT = 16, NB = 2;
-  static constexpr int CPW = SG * 4;  // float2 per column row pair: [set][member]
+struct MultiMaps {
+  CUtensorMap phi, zt, meta, pt;
+};
+template <int TR, int RMAX>
+struct MultiTmaLayout {
+  static constexpr int TT = 8 * TR, SG = 32, RT = 32, NE = 4 * SG;
+  static constexpr int a1k(int x) { return (x + 1023) / 1024 * 1024; }
+  static constexpr int kOffPhi = TT * RT * 4;  // after the swizzled p_f box
+  static constexpr int kOffZt = kOffPhi + NE * RT * 4;
+  static constexpr int kOffMeta = kOffZt + RMAX * RT * 4;
+  static constexpr int kTx = kOffMeta + 4 * RT * 4;
+  static constexpr int kStage = a1k(kTx);
+  static constexpr int kOffCol = 2 * kStage;  // float2 [RT / 2][NE]: [row pair][set][member]
+  static constexpr int kOffBar = kOffCol + (RT / 2) * NE * 8;
+  static constexpr int kBytes = kOffBar + 64 + 1024;  // + alignment slack of the dynamic base
 };
 
 template <int RMAX, int TR>
-__global__ __launch_bounds__(256, 3) void k_multi_tile(Args a, int n_multi, const int* __restrict__ mptr,
-                                                    const int* __restrict__ mmpos, const float* __restrict__ PhiMO,
-                                                    const float* __restrict__ mvt, const float* __restrict__ mw,
-                                                    const int* __restrict__ mflag) {
-  using L = MultiTile<TR>;
-  constexpr int TT = L::TT, SG = L::SG, LT = L::LT, NB = L::NB, CPW = L::CPW;
-  __shared__ __align__(16) float2 col_s[NB][LT / 2][CPW];
-  __shared__ __align__(16) float2 pt_s[NB][LT / 2][TT];
+__global__ __launch_bounds__(256, 3) void k_multi_tma(const __grid_constant__ MultiMaps maps, Args a, int n_multi,
+                                                   const int* __restrict__ mptr, const int* __restrict__ mmpos,
+                                                   const float* __restrict__ mvt, const float* __restrict__ mw,
+                                                   const int* __restrict__ mflag) {
+  using L = MultiTmaLayout<TR, RMAX>;
+  constexpr int TT = L::TT, SG = L::SG, RT = L::RT, NE = L::NE;
+  extern __shared__ unsigned char mt_dyn[];
   __shared__ float mx_s[SG][TT + 1];
   __shared__ float ov_s[SG][TT + 1];
   __shared__ int fl_s[SG];
@@ -290,7 +302,7 @@ __global__ __launch_bounds__(256, 3) void k_multi_tile(Args a, int n_multi, cons
   const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int t0 = blockIdx.y * TT;
   const QInfo qi = a.qi[q];
-  const int T = a.T, M = a.M, Mp = a.Mpad, tau = qi.tau;
+  const int T = a.T, M = a.M, tau = qi.tau;
   const dcflow_results& o = a.out;
   if (qi.status != ST_OK) {
     for (int t = t0 + tid; t < T && t < t0 + TT; t += blockDim.x) {
@@ -301,46 +313,50 @@ __global__ __launch_bounds__(256, 3) void k_multi_tile(Args a, int n_multi, cons
     if (tid == 0 && blockIdx.y == 0) o.n_island_multi[tau] = 0;
     return;
   }
-  const float* Zs = static_cast<const float*>(a.Zs) + (size_t)q * kRMax * Mp;
-  const float* ptil = static_cast<const float*>(a.ptil) + (size_t)q * T * Mp;
-  const float* meta = static_cast<const float*>(a.diagv) + (size_t)q * 4 * Mp;
+  const uint32_t raw = smem_u32(mt_dyn);
+  unsigned char* sm = mt_dyn + (((raw + 1023u) & ~1023u) - raw);  // 1024-aligned (the swizzled tiles)
+  float2* col_s = reinterpret_cast<float2*>(sm + L::kOffCol);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kOffBar);
   const size_t qS = (size_t)q * n_multi;
-  if (tid == 0) nisl_s = 0;
+  if (tid == 0) {
+    nisl_s = 0;
+    for (int st = 0; st < 2; ++st) mbar_init(smem_u32(&bars[st]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   for (int t = tid; t < TT; t += blockDim.x) {
     bv_s[t] = -1.f;
     bg_s[t] = 0x7fffffff;
     bo_s[t] = 0.0;
   }
-  // builder role: set bs, member ba, rows [8 bh, 8 bh + 8) of each tile
+  // builder role: column (set bs, member ba), rows [16 bh, 16 bh + 16) of each tile
   const int bs = tid >> 3, ba = (tid >> 1) & 3, bh = tid & 1;
   // compute role: set cs, timesteps TR ct + j
   const int cs = 4 * w + (lane >> 3), ct = lane & 7;
-  const int ntile = (M + LT - 1) / LT;
-  for (int g0 = 0; g0 < n_multi; g0 += SG) {
+  const int ntile = (M + RT - 1) / RT;
+  int seq = 0;  // tiles issued so far over the set groups (the ring's phase)
+  bool failed = false;
+  int fsq = 0;  // the tile whose wait expired (the only one in flight then)
+  for (int g0 = 0; g0 < n_multi && !failed; g0 += SG) {
     const int ng = min(SG, n_multi - g0);
-    __syncthreads();  // the previous group's buffers, maxima and flags consumed
-    // the builder's member: its K^{-1}-weighted factors and its monitored row
+    __syncthreads();  // barriers ready; the previous group's maxima, flags and tiles consumed
+    const int ebase = mptr[g0];  // the group's first entry: the Phi box's row coordinate
+    // the builder's member: its K^{-1}-weighted factors, its monitored row
     float vb[RMAX];
-    int brow = -1;
-    size_t bent = 0;
-    bool bon = false;
+    int brow = -1, eloc = -1;
     if (bs < ng) {
       const int m = g0 + bs, e0 = mptr[m], n = mptr[m + 1] - e0;
-      bon = ba < n;
-      if (bon) {
-        bent = (size_t)(e0 + ba) * Mp;
+      if (ba < n) {
+        eloc = e0 + ba - ebase;
         brow = mmpos[e0 + ba];
       }
     }
 #pragma unroll
-    for (int j = 0; j < RMAX; ++j) vb[j] = bon ? mvt[(qS + g0 + bs) * 4 * kRMax + ba * kRMax + j] : 0.f;
+    for (int j = 0; j < RMAX; ++j) vb[j] = eloc >= 0 ? mvt[(qS + g0 + bs) * 4 * kRMax + ba * kRMax + j] : 0.f;
     const float bil = brow >= 0 ? (float)a.inv_lim[brow] : 0.f;
-    // the compute thread's set: its weights w_t (zero for absent members and
-    // for sets that are not evaluated), its flag
-    int cflag = 3;
+    // the compute thread's set: its weights w_t (zero for absent members and sets not evaluated)
     float2 w2[TR][4];
     {
-      int n = 0;
+      int cflag = 3, n = 0;
       if (cs < ng) {
         cflag = mflag[qS + g0 + cs];
         n = mptr[g0 + cs + 1] - mptr[g0 + cs];
@@ -366,80 +382,102 @@ __global__ __launch_bounds__(256, 3) void k_multi_tile(Args a, int n_multi, cons
       mx[j] = 0.f;
       ov[j] = 0.f;
     }
-    // build tile k into buffer k % 2: the member columns and p_f as row pairs
-    auto build = [&](int k) {
-      const int b = k & 1, r0 = k * LT + 8 * bh;
-      float c[8];
-      const float4* ph = reinterpret_cast<const float4*>(PhiMO + bent + r0);
-      const float4 p0 = bon ? ph[0] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 p1 = bon ? ph[1] : make_float4(0.f, 0.f, 0.f, 0.f);
-      c[0] = p0.x; c[1] = p0.y; c[2] = p0.z; c[3] = p0.w;
-      c[4] = p1.x; c[5] = p1.y; c[6] = p1.z; c[7] = p1.w;
-#pragma unroll
-      for (int j = 0; j < RMAX; ++j) {
-        const float4* zp = reinterpret_cast<const float4*>(Zs + (size_t)j * Mp + r0);
-        const float4 z0 = zp[0], z1 = zp[1];
-        c[0] = fmaf(-z0.x, vb[j], c[0]); c[1] = fmaf(-z0.y, vb[j], c[1]);
-        c[2] = fmaf(-z0.z, vb[j], c[2]); c[3] = fmaf(-z0.w, vb[j], c[3]);
-        c[4] = fmaf(-z1.x, vb[j], c[4]); c[5] = fmaf(-z1.y, vb[j], c[5]);
-        c[6] = fmaf(-z1.z, vb[j], c[6]); c[7] = fmaf(-z1.w, vb[j], c[7]);
-      }
-      const float4* rp4 = reinterpret_cast<const float4*>(meta + Mp + r0);
-      const float4 m0 = rp4[0], m1 = rp4[1];
-      const float rm[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        c[i] = r0 + i < M ? c[i] * rm[i] : 0.f;
-        if (r0 + i == brow) c[i] -= bil;  // the member's own row: its flow cancels
-      }
-#pragma unroll
-      for (int i2 = 0; i2 < 4; ++i2) col_s[b][4 * bh + i2][bs * 4 + ba] = make_float2(c[2 * i2], c[2 * i2 + 1]);
-      for (int p = tid; p < (LT / 2) * TT; p += blockDim.x) {
-        const int rp = p % (LT / 2), t = p / (LT / 2), l = k * LT + 2 * rp;
-        float2 v = make_float2(0.f, 0.f);
-        if (t0 + t < T) {
-          v = *reinterpret_cast<const float2*>(ptil + (size_t)(t0 + t) * Mp + l);
-          if (l >= M) v.x = 0.f;
-          if (l + 1 >= M) v.y = 0.f;
-        }
-        pt_s[b][rp][t] = v;
-      }
+    auto issue = [&](int k, int sq) {
+      unsigned char* base = sm + (sq & 1) * L::kStage;
+      const uint32_t bar = smem_u32(&bars[sq & 1]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(bar, L::kTx);
+      tma_load_3d(smem_u32(base), &maps.pt, k * RT, t0, q, bar);
+      tma_load_2d(smem_u32(base + L::kOffPhi), &maps.phi, k * RT, ebase, bar);
+      tma_load_3d(smem_u32(base + L::kOffZt), &maps.zt, k * RT, 0, q, bar);
+      tma_load_3d(smem_u32(base + L::kOffMeta), &maps.meta, k * RT, 0, q, bar);
     };
-    if (ntile > 0) build(0);
+    if (tid == 0 && ntile > 0) issue(0, seq);
     for (int k = 0; k < ntile; ++k) {
-      __syncthreads();  // tile k built; every thread is done with tile k - 1 (its buffer is refilled next)
-      if (k + 1 < ntile) build(k + 1);
-      const int b = k & 1;
+      const int sq = seq + k;
+      const bool got = mbar_wait(smem_u32(&bars[sq & 1]), (uint32_t)((sq >> 1) & 1));
+      if (__syncthreads_or(!got)) {  // also: every thread is done with tile k - 1 (the column tile, the other stage)
+        failed = true;
+        fsq = sq;
+        break;
+      }
+      if (tid == 0 && k + 1 < ntile) issue(k + 1, sq + 1);
+      const unsigned char* base = sm + (sq & 1) * L::kStage;
+      const float* phi_t = reinterpret_cast<const float*>(base + L::kOffPhi);
+      const float* zt_t = reinterpret_cast<const float*>(base + L::kOffZt);
+      const float* rm_t = reinterpret_cast<const float*>(base + L::kOffMeta) + RT;  // metadata row 1
+      {  // rows [16 bh, 16 bh + 16) of column (bs, ba): Phi_f[l, o] / limit_l
+        const int r0 = 16 * bh;
+        float c[16];
+#pragma unroll
+        for (int i4 = 0; i4 < 4; ++i4) {
+          const float4 p4 = eloc >= 0 ? *reinterpret_cast<const float4*>(&phi_t[eloc * RT + r0 + 4 * i4])
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+          c[4 * i4] = p4.x;
+          c[4 * i4 + 1] = p4.y;
+          c[4 * i4 + 2] = p4.z;
+          c[4 * i4 + 3] = p4.w;
+        }
+#pragma unroll
+        for (int j = 0; j < RMAX; ++j)
+#pragma unroll
+          for (int i4 = 0; i4 < 4; ++i4) {
+            const float4 z = *reinterpret_cast<const float4*>(&zt_t[j * RT + r0 + 4 * i4]);
+            c[4 * i4] = fmaf(-z.x, vb[j], c[4 * i4]);
+            c[4 * i4 + 1] = fmaf(-z.y, vb[j], c[4 * i4 + 1]);
+            c[4 * i4 + 2] = fmaf(-z.z, vb[j], c[4 * i4 + 2]);
+            c[4 * i4 + 3] = fmaf(-z.w, vb[j], c[4 * i4 + 3]);
+          }
+#pragma unroll
+        for (int i4 = 0; i4 < 4; ++i4) {
+          const float4 rm = *reinterpret_cast<const float4*>(&rm_t[r0 + 4 * i4]);
+          c[4 * i4] *= rm.x;
+          c[4 * i4 + 1] *= rm.y;
+          c[4 * i4 + 2] *= rm.z;
+          c[4 * i4 + 3] *= rm.w;
+        }
+#pragma unroll
+        for (int i2 = 0; i2 < 8; ++i2) col_s[(8 * bh + i2) * NE + bs * 4 + ba] = make_float2(c[2 * i2], c[2 * i2 + 1]);
+        const int dr = brow - k * RT - r0;  // the member's own row: its flow cancels (same thread wrote it)
+        if ((unsigned)dr < 16u) reinterpret_cast<float*>(&col_s[(8 * bh + dr / 2) * NE + bs * 4 + ba])[dr & 1] -= bil;
+      }
+      __syncthreads();
       float mt[TR];
 #pragma unroll
-      for (int rp = 0; rp < LT / 2; ++rp) {
-        const float4 u0 = *reinterpret_cast<const float4*>(&col_s[b][rp][cs * 4]);
-        const float4 u1 = *reinterpret_cast<const float4*>(&col_s[b][rp][cs * 4 + 2]);
+      for (int j = 0; j < TR; ++j) mt[j] = 0.f;
+#pragma unroll 2
+      for (int rp = 0; rp < RT / 2; ++rp) {
+        const float4 u0 = *reinterpret_cast<const float4*>(&col_s[rp * NE + cs * 4]);
+        const float4 u1 = *reinterpret_cast<const float4*>(&col_s[rp * NE + cs * 4 + 2]);
         const float2 cc[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
                               make_float2(u1.z, u1.w)};
 #pragma unroll
         for (int j = 0; j < TR; ++j) {
-          float2 v = pt_s[b][rp][ct * TR + j];
+          const int t = ct * TR + j;  // rows 2 rp, 2 rp + 1 of line t: chunk rp / 2, swizzled
+          float2 v = *reinterpret_cast<const float2*>(base + t * 128 + ((((rp >> 1) ^ t) & 7) << 4) + ((rp & 1) << 3));
 #pragma unroll
           for (int a2 = 0; a2 < 4; ++a2) v = __ffma2_rn(cc[a2], w2[j][a2], v);
-          mt[j] = rp == 0 ? sec_max3abs(v.x, v.y, v.y) : sec_max3abs(mt[j], v.x, v.y);
+          mt[j] = sec_max3abs(mt[j], v.x, v.y);
         }
       }
 #pragma unroll
       for (int j = 0; j < TR; ++j) {
         mx[j] = fmaxf(mx[j], mt[j]);
         if (mt[j] > 1.f) {  // the overload terms of this cell over the tile
-          float s = 0.f;
-          for (int rp = 0; rp < LT / 2; ++rp) {
-            float2 v = pt_s[b][rp][ct * TR + j];
+          const int t = ct * TR + j;
+          float sum = 0.f;
+          for (int rp = 0; rp < RT / 2; ++rp) {
+            float2 v = *reinterpret_cast<const float2*>(base + t * 128 + ((((rp >> 1) ^ t) & 7) << 4) + ((rp & 1) << 3));
 #pragma unroll
-            for (int a2 = 0; a2 < 4; ++a2) v = __ffma2_rn(col_s[b][rp][cs * 4 + a2], w2[j][a2], v);
-            s += sec_ovl(v.x) + sec_ovl(v.y);
+            for (int a2 = 0; a2 < 4; ++a2) v = __ffma2_rn(col_s[rp * NE + cs * 4 + a2], w2[j][a2], v);
+            sum += sec_ovl(v.x) + sec_ovl(v.y);
           }
-          ov[j] += s;
+          ov[j] += sum;
         }
       }
     }
+    seq += ntile;
+    if (failed) break;
 #pragma unroll
     for (int j = 0; j < TR; ++j) {
       mx_s[cs][ct * TR + j] = mx[j];
@@ -451,18 +489,25 @@ __global__ __launch_bounds__(256, 3) void k_multi_tile(Args a, int n_multi, cons
       float bv = bv_s[t];
       int bg = bg_s[t];
       double bo = bo_s[t];
-      for (int s = 0; s < ng; ++s) {
-        if (fl_s[s]) continue;
-        bo += (double)ov_s[s][t] * 1048576.0;
-        if (mx_s[s][t] > bv) {
-          bv = mx_s[s][t];
-          bg = g0 + s;
+      for (int s2 = 0; s2 < ng; ++s2) {
+        if (fl_s[s2]) continue;
+        bo += (double)ov_s[s2][t] * 1048576.0;
+        if (mx_s[s2][t] > bv) {
+          bv = mx_s[s2][t];
+          bg = g0 + s2;
         }
       }
       bv_s[t] = bv;
       bg_s[t] = bg;
       bo_s[t] = bo;
     }
+  }
+  if (failed) {  // the tile in flight lands (bounded wait) before the block exits
+    if (tid == 0) {
+      mbar_wait(smem_u32(&bars[fsq & 1]), (uint32_t)((fsq >> 1) & 1));
+      atomicExch(a.err, 1);
+    }
+    return;
   }
   __syncthreads();
   for (int t = tid; t < TT; t += blockDim.x) {

@@ -2730,28 +2730,51 @@ void launch_multi_prep(const Args& a, int n_multi, const int* mptr, const int* m
 }
 
 template <class Real>
-void launch_multi_rows(const Args& a, int RMAX, int n_multi, const int* mptr, const int* mmpos, const void* phimo,
-                       ChunkBufs& B, cudaStream_t st) {
+int launch_multi_rows(const Args& a, int RMAX, int n_multi, int n_ent, const int* mptr, const int* mmpos,
+                      const void* phimo, ChunkBufs& B, cudaStream_t st) {
   const Real* P = static_cast<const Real*>(phimo);
   const Real *vt = B.mvt.as<Real>(), *w = B.mw.as<Real>();
   const int* f = B.mflag.as<int>();
-  if constexpr (sizeof(Real) == 4) {  // register-tiled, every timestep pass in one launch (grid y)
-    const int tr = sec_tr(a.T);
-    const dim3 grid(a.nq, (a.T + 8 * tr - 1) / (8 * tr));
-#define DCF_MULTI_TILE(R_, TR_) k_multi_tile<R_, TR_><<<grid, 256, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f)
-    if (RMAX == 4) {
-      if (tr == 3) DCF_MULTI_TILE(4, 3); else if (tr == 2) DCF_MULTI_TILE(4, 2); else DCF_MULTI_TILE(4, 1);
-    } else if (RMAX == 8) {
-      if (tr == 3) DCF_MULTI_TILE(8, 3); else if (tr == 2) DCF_MULTI_TILE(8, 2); else DCF_MULTI_TILE(8, 1);
-    } else {
-      if (tr == 3) DCF_MULTI_TILE(16, 3); else if (tr == 2) DCF_MULTI_TILE(16, 2); else DCF_MULTI_TILE(16, 1);
-    }
-#undef DCF_MULTI_TILE
+  if constexpr (sizeof(Real) == 4) {  // TMA-fed, every timestep pass in one launch (grid y)
+    const int tr = sec_tr(a.T), TT = 8 * tr;
+    const dim3 grid(a.nq, (a.T + TT - 1) / TT);
+    const uint64_t M = (uint64_t)a.M, Mp = (uint64_t)a.Mpad, nq = (uint64_t)a.nq;
+    MultiMaps maps;
+    const uint64_t d_ph[2] = {M, (uint64_t)n_ent}, s_ph[1] = {Mp * 4};
+    const uint32_t b_ph[2] = {32, 128};
+    const uint64_t d_zt[3] = {M, (uint64_t)kRMax, nq}, s_zt[2] = {Mp * 4, Mp * kRMax * 4};
+    const uint32_t b_zt[3] = {32, (uint32_t)RMAX, 1};
+    const uint64_t d_me[3] = {M, 4, nq}, s_me[2] = {Mp * 4, Mp * 16};
+    const uint32_t b_me[3] = {32, 4, 1};
+    const uint64_t d_pt[3] = {M, (uint64_t)a.T, nq}, s_pt[2] = {Mp * 4, Mp * a.T * 4};
+    const uint32_t b_pt[3] = {32, (uint32_t)TT, 1};
+    int rc = encode_map(&maps.phi, P, 2, d_ph, s_ph, b_ph);
+    if (!rc) rc = encode_map(&maps.zt, a.Zs, 3, d_zt, s_zt, b_zt);
+    if (!rc) rc = encode_map(&maps.meta, a.diagv, 3, d_me, s_me, b_me);
+    if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt, true);
+    if (rc) return rc;
+    static uint64_t attr[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    auto go = [&](auto kern, int bytes, int i) -> int {
+      if (smem_attr_once(kern, bytes, attr[i]) != cudaSuccess) {
+        set_error("dcflow_solve_batch: multi-outage pass shared memory");
+        return DCFLOW_ERR_CUDA;
+      }
+      kern<<<grid, 256, bytes, st>>>(maps, a, n_multi, mptr, mmpos, vt, w, f);
+      return 0;
+    };
+#define DCF_MULTI_TMA(R_, TR_, I_) go(k_multi_tma<R_, TR_>, MultiTmaLayout<TR_, R_>::kBytes, I_)
+    const int ri = RMAX == 4 ? 0 : (RMAX == 8 ? 1 : 2);
+    if (ri == 0) return tr == 3 ? DCF_MULTI_TMA(4, 3, 0) : (tr == 2 ? DCF_MULTI_TMA(4, 2, 1) : DCF_MULTI_TMA(4, 1, 2));
+    if (ri == 1) return tr == 3 ? DCF_MULTI_TMA(8, 3, 3) : (tr == 2 ? DCF_MULTI_TMA(8, 2, 4) : DCF_MULTI_TMA(8, 1, 5));
+    return tr == 3 ? DCF_MULTI_TMA(16, 3, 6) : (tr == 2 ? DCF_MULTI_TMA(16, 2, 7) : DCF_MULTI_TMA(16, 1, 8));
+#undef DCF_MULTI_TMA
   } else {
     constexpr int TT = 12, SG = 32;
+    (void)n_ent;
     if (RMAX == 4) k_multi_rows<Real, 4, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
     else if (RMAX == 8) k_multi_rows<Real, 8, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
     else k_multi_rows<Real, 16, TT, SG><<<a.nq, 128, 0, st>>>(a, n_multi, mptr, mmpos, P, vt, w, f);
+    return 0;
   }
 }
 
@@ -3549,12 +3572,11 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
     DCF_CHECK_LAUNCH();
     if (want_multi) {
       const int pe = ctx->prof_begin(st);
-      if (fp64)
-        launch_multi_rows<double>(af, RMAX, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multi_mpos.as<int>(),
-                                  ctx->PhiMO.p, B, st);
-      else
-        launch_multi_rows<float>(af, RMAX, ctx->n_multi, ctx->multi_ptr.as<int>(), ctx->multi_mpos.as<int>(),
-                                 ctx->PhiMO.p, B, st);
+      const int rcm = fp64 ? launch_multi_rows<double>(af, RMAX, ctx->n_multi, ctx->n_multi_ent, ctx->multi_ptr.as<int>(),
+                                                       ctx->multi_mpos.as<int>(), ctx->PhiMO.p, B, st)
+                           : launch_multi_rows<float>(af, RMAX, ctx->n_multi, ctx->n_multi_ent, ctx->multi_ptr.as<int>(),
+                                                      ctx->multi_mpos.as<int>(), ctx->PhiMO.p, B, st);
+      if (rcm) return rcm;
       ++ctx->launches;
       DCF_CHECK_LAUNCH();
       ctx->prof_end(pe, DCFLOW_PROF_MULTI, st);
