@@ -44,11 +44,11 @@ WORKLOADS = {
 # 500-bus study (its summary sits under profiles/), keyed by the sha1 of the
 # kernel's source and of its argument block at the time of the capture
 N1_TRAFFIC = {
-    ("de42642cae77", "fp32"): {"bytes": 1.109e9, "per": "bench step of the 500-bus study",
-                               "how": "1,000-topology capture (626 + 374 topologies: 79.33 MB + 31.68 MB of DRAM "
+    ("4721d056a1ba", "fp32"): {"bytes": 1.0995e9, "per": "bench step of the 500-bus study",
+                               "how": "1,000-topology capture (626 + 374 topologies: 78.45 MB + 31.61 MB of DRAM "
                                       "read + write) scaled by topologies per rank class to 6,233 + 3,767"},
-    ("de42642cae77", "bf16x3"): {"bytes": 1.167e9, "per": "bench step of the 500-bus study",
-                                 "how": "1,000-topology capture (626 + 374 topologies: 85.28 MB + 31.59 MB) scaled "
+    ("4721d056a1ba", "bf16x3"): {"bytes": 1.1636e9, "per": "bench step of the 500-bus study",
+                                 "how": "1,000-topology capture (626 + 374 topologies: 84.93 MB + 31.56 MB) scaled "
                                         "by topologies per rank class to 6,233 + 3,767"},
 }
 
