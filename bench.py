@@ -477,6 +477,28 @@ def run_ours(args):
                 "note": f"injection topologies: {args.ti} busbar assignments of the injections at the split "
                         f"substations per topology ({nsub} topologies x {T_STEPS} timesteps), metric-first "
                         "brute force; loadflows count every (topology, timestep, assignment, contingency)"}
+            # the same with the top-k cases (agg_i): metric-first (the chosen assignment's cases only)
+            # against output-first (every assignment's cases inside the loop, the chosen one's kept)
+            if args.top_k > 0:
+                modes = {}
+                for of in (False, True):
+                    so = solver if not of else Solver(w.grid, precision=form, output_first=True)
+                    if of:
+                        so.set_study(w.mon, w.cont, lim, split_bus=w.subs, outage_cand=ocand)
+                    rk2 = DeviceResults(nsub, db.n_time, len(w.mon), want_var=True, top_k=args.top_k)
+                    tk2, kk2 = timed(so, dbt, rk2, steps, stream)
+                    modes["output_first" if of else "metric_first"] = {
+                        "value": lft * steps / tk2, "ms_per_step": 1e3 * tk2 / steps,
+                        "topcases_ms_per_step": kk2["topcases_ms"]}
+                    if of:
+                        so.close()
+                results[f"fp32_ti{args.ti}_top{args.top_k}"] = dict(
+                    modes, output_first_over_metric_first=modes["output_first"]["ms_per_step"]
+                    / modes["metric_first"]["ms_per_step"],
+                    note=f"the injection-topology form with the {args.top_k} worst N-1 cases per (topology, "
+                         "timestep): metric-first computes them for the chosen assignment only, output-first "
+                         "for every assignment inside the brute-force loop (the modes of Sec. III-A); both "
+                         "report the same outputs")
         # the same solve with multi-outage N-1 cases (sets of 2-4 branches that fail together)
         if form == "fp32" and args.multi > 0 and db.n_var == 0:
             rng = np.random.default_rng(800)

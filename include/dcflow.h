@@ -80,6 +80,14 @@ typedef struct {
                             arg-max / arg-min up to the form's rounding); 0 = the form's
                             tolerance (1e-10 FP64, 1e-4 FP32 and BF16x3), < 0 = none (exact
                             ties only).  The screened solve reports the plain arg-max. */
+  int32_t output_first;  /* injection candidates with top_k > 0 (Sec. III-A's injection module):
+                            0 = metric-first (default): the candidates are screened on agg_m
+                            alone and the top-k cases (agg_i) computed for the chosen one only;
+                            1 = output-first: agg_i of every (timestep, candidate) is computed
+                            inside the candidate loop and the chosen candidate's kept (needs
+                            n_topo * n_time * candidates * n_cont floats of device scratch;
+                            DCFLOW_ERR_OOM beyond what the device holds).  Every output is the
+                            same in both modes; they differ in time. */
 } dcflow_options;
 
 /* Fill `opt` with the defaults (FP32 form, current device, automatic chunk, 1e-9,

@@ -38,7 +38,7 @@ extern "C" void dcflow_destroy(dcflow_ctx* ctx) {
                          &ctx->nidx, &ctx->split_ok, &ctx->out_ok, &ctx->monN, &ctx->contN, &ctx->cpos_of_mon, &ctx->mpos_of_cont,
                          &ctx->inv_lim, &ctx->bN, &ctx->PhiN, &ctx->PhiNf, &ctx->bNf, &ctx->p0f, &ctx->PtdfN, &ctx->PhiMC, &ctx->Y, &ctx->p0, &ctx->dp,
                          &ctx->rank, &ctx->status, &ctx->perm, &ctx->hist, &ctx->hist_host, &ctx->err, &ctx->pool, &ctx->var_k, &ctx->PhiCM, &ctx->cont_pos, &ctx->cont_inv,
-                         &ctx->cm_scratch, &ctx->gen_cols,
+                         &ctx->cm_scratch, &ctx->of_cmax, &ctx->of_top, &ctx->gen_cols,
                          &ctx->multi_ptr, &ctx->multiN, &ctx->multi_mpos, &ctx->PhiMO};
   for (auto* b : bufs) b->release();
   ctx->bufs[0].release_all();

@@ -184,6 +184,9 @@ struct dcflow_ctx {
   dcf::DevBuf dp;          // double[NN*U] base flow change of each candidate
   dcf::DevBuf rank, status, perm, hist, hist_host;
   dcf::DevBuf cm_scratch;  // float[N*T*C] per-contingency maxima for the top-k pass when not requested
+  // output-first candidates: per (topology, timestep x candidate) the per-contingency maxima
+  // float[N*T*U*C] and the top-k cases int, int, float [N*T*U*k] of every candidate
+  dcf::DevBuf of_cmax, of_top;
   dcf::DevBuf gen_cols;    // Real[G*M] PTDF[mon, gen_bus] / limit of the batch's generators
   dcf::ChunkBufs bufs[2];
   cudaStream_t side = nullptr;           // preparation stream (created on first use)

@@ -134,6 +134,7 @@ extern "C" void dcflow_default_options(dcflow_options* opt) {
   opt->autotune = 0;
   opt->autotune_sample = 0;
   opt->tie_band = 0.0;
+  opt->output_first = 0;
 }
 
 extern "C" int dcflow_setup(dcflow_ctx** out, int32_t n_bus, int32_t n_branch, const int32_t* from,

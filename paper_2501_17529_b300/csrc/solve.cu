@@ -2074,6 +2074,35 @@ __global__ __launch_bounds__(128) void k_topcases_tile(Args a, const float* __re
   }
 }
 
+// Output-first candidates (Sec. III-A's injection module): the winner's top-k
+// cases, computed for every (timestep, candidate) in the loop, copied to the
+// outputs once Eq. (8) has chosen it.  One thread per (topology slot,
+// timestep, case); a topology without a choice gets -1 / -1 / 0.
+__global__ void k_top_gather(Args a, int U, int k, const int* __restrict__ ctop, const int* __restrict__ mtop,
+                             const float* __restrict__ ltop) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int T = a.T;
+  if (i >= (size_t)a.nq * T * k) return;
+  const int q = (int)(i / ((size_t)T * k)), t = (int)((i / k) % T), j = (int)(i % k);
+  const int tau = a.qi[q].tau;
+  const int u = a.qi[q].status == ST_OK ? a.best_u[(size_t)q * T + t] : -1;
+  const size_t o = ((size_t)tau * T + t) * k + j;
+  if (u < 0) {
+    a.out.top_cont[o] = -1;
+    a.out.top_mon[o] = -1;
+    a.out.top_loading[o] = 0.f;
+    return;
+  }
+  const size_t src = (((size_t)tau * T + t) * U + u) * k + j;
+  a.out.top_cont[o] = ctop[src];
+  a.out.top_mon[o] = mtop[src];
+  a.out.top_loading[o] = ltop[src];
+}
+
+__global__ void k_fill_f(float* __restrict__ p, size_t n, float v) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
 // ---------------------------------------------------------------------------
 // generator-failure N-1 (the "N-1 generator" case of Sec. III-A): generator g
 // at bus b with output P_g[t] fails, the slack takes it up, and the flows
@@ -3135,8 +3164,10 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   const bool cmp = !fp64 && mode == kModeFull && C_eff > 0 && plan.compact;
   // top-k cases after the dense FFMA-build N-1: its tracking variant records each maximum's
   // 16-row tile, and the top-k pass evaluates only that tile per case
+  // output-first candidates: the top-k cases of every (timestep, candidate) in the loop
+  const bool of = ctx->opt.output_first && Uc > 0 && top_k > 0 && mode == kModeFull;
   const bool use_tile = top_k > 0 && !fp64 && !tc && !cmp && mode == kModeFull && C_eff > 0 &&
-                        pick_tt(T, false) >= 4;
+                        pick_tt(T, false) >= 4 && !of;
   // a remainder of at most kRemCols contingencies beyond the last full block of 64
   // goes to the final pass (a column each over the monitored rows) instead of an
   // N-1 block that would compute 64 columns for it (plain full solves only)
@@ -3281,6 +3312,17 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
   if (top_k > 0 && !res->n1_cont_max) {  // the top-k pass reads the per-contingency maxima
     if (ctx->cm_scratch.ensure((size_t)N * T * std::max(C, 1) * sizeof(float))) return DCFLOW_ERR_OOM;
     base.out.n1_cont_max = ctx->cm_scratch.as<float>();
+  }
+  const size_t of_n = of ? (size_t)N * T * Uc : 0;  // (topology, timestep, candidate) triples
+  if (of) {
+    const size_t ncm = of_n * std::max(C, 1);
+    if (ctx->of_cmax.ensure(ncm * sizeof(float)) || ctx->of_top.ensure(of_n * top_k * 12)) {
+      set_error("dcflow_solve_batch: output-first scratch (n_topo * n_time * candidates * n_cont floats)");
+      return DCFLOW_ERR_OOM;
+    }
+    k_fill_f<<<4 * 148, 256, 0, st>>>(ctx->of_cmax.as<float>(), ncm, -1.f);  // bridges and skipped topologies
+    ++ctx->launches;
+    DCF_CHECK_LAUNCH();
   }
   auto chunk_args = [&](int bi) {
     Args a = base;
@@ -3455,7 +3497,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       ctx->prof_end(pex, DCFLOW_PROF_EXPAND, st);
       Args av = a;
       av.T = TV;
-      av.out.n1_cont_max = nullptr;
+      av.out.n1_cont_max = of ? ctx->of_cmax.as<float>() : nullptr;
       av.cmr = nullptr;  // the screening pass keeps no per-contingency maxima
       av.p2max = nullptr;
       av.ptil = B.ptv.p;
@@ -3469,6 +3511,28 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       } else {
         DCF_CUDA(cudaMemsetAsync(B.pargv.p, 0xff, (size_t)ch.nq * TV * sizeof(int), st));
       }
+      int* of_c = ctx->of_top.as<int>();
+      int* of_m = of_c + of_n * top_k;
+      float* of_l = reinterpret_cast<float*>(of_m + of_n * top_k);
+      if (of) {  // output-first: agg_i of every (timestep, candidate), inside the candidate loop
+        Args at = av;
+        at.tile = nullptr;
+        at.out.top_cont = of_c;
+        at.out.top_mon = of_m;
+        at.out.top_loading = of_l;
+        const int pet = ctx->prof_begin(st);
+        const int rct = fp64 ? launch_topcases<double>(at, RMAX, at.out.n1_cont_max, ctx->cont_inv.as<int>(),
+                                                       ctx->PhiCM.p, top_k, st)
+                             : launch_topcases<float>(at, RMAX, at.out.n1_cont_max, ctx->cont_inv.as<int>(),
+                                                      ctx->PhiCM.p, top_k, st);
+        if (rct) {
+          set_error("dcflow_solve_batch: top-k pass shared memory");
+          return rct;
+        }
+        ++ctx->launches;
+        DCF_CHECK_LAUNCH();
+        ctx->prof_end(pet, DCFLOW_PROF_TOPCASES, st);
+      }
       const dim3 gs(ch.nq, (T + 7) / 8);
       if (fp64) k_var_select<double><<<gs, 256, 0, st>>>(av, T, Uc, B.bestu.as<int>());
       else k_var_select<float><<<gs, 256, 0, st>>>(av, T, Uc, B.bestu.as<int>());
@@ -3479,6 +3543,12 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       else k_var_gather<float><<<dim3(T, ch.nq), 128, 0, st>>>(af, Uc, B.ptv.as<float>(), B.svv.as<float>());
       ctx->launches += 2;
       DCF_CHECK_LAUNCH();
+      if (of) {  // the chosen candidate's cases
+        const size_t nt = (size_t)ch.nq * T * top_k;
+        k_top_gather<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(af, Uc, top_k, of_c, of_m, of_l);
+        ++ctx->launches;
+        DCF_CHECK_LAUNCH();
+      }
     }
     if (mode == kModeFeatures) {
       if (fp64)
@@ -3592,7 +3662,7 @@ static int solve_impl(dcflow_ctx* ctx, const dcflow_batch* bt, const dcflow_resu
       DCF_CHECK_LAUNCH();
       ctx->prof_end(pe, DCFLOW_PROF_GEN, st);
     }
-    if (top_k > 0) {
+    if (top_k > 0 && !of) {  // metric-first: the chosen candidate's cases only
       const int pe = ctx->prof_begin(st);
       const int rct = fp64 ? launch_topcases<double>(af, RMAX, af.out.n1_cont_max, ctx->cont_inv.as<int>(),
                                                      ctx->PhiCM.p, top_k, st)

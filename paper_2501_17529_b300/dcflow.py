@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("device", c_int32), ("chunk_topo", c_int32),
                 ("island_tol", c_double), ("compact_n1", c_int32), ("autotune", c_int32),
-                ("autotune_sample", c_int32), ("tie_band", c_double)]
+                ("autotune_sample", c_int32), ("tie_band", c_double), ("output_first", c_int32)]
 
 
 class Schedule(ctypes.Structure):
@@ -210,7 +210,7 @@ def dcflow_default_options() -> Options:
 
 
 def dcflow_setup(n_bus, f, t, b, slack, precision="fp32", device=-1, chunk_topo=0, island_tol=0.0, compact_n1=False,
-                 autotune=False, autotune_sample=0):
+                 autotune=False, autotune_sample=0, output_first=False):
     lib = load_library()
     o = dcflow_default_options()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -218,6 +218,7 @@ def dcflow_setup(n_bus, f, t, b, slack, precision="fp32", device=-1, chunk_topo=
     o.chunk_topo = int(chunk_topo)
     o.compact_n1 = int(bool(compact_n1))
     o.autotune = int(bool(autotune))
+    o.output_first = int(bool(output_first))
     o.autotune_sample = int(autotune_sample)
     if island_tol:
         o.island_tol = float(island_tol)
@@ -565,11 +566,11 @@ class Solver:
     """One grid + study on the current CUDA device."""
 
     def __init__(self, grid, precision="fp32", chunk_topo=0, island_tol=0.0, device=-1, compact_n1=False,
-                 autotune=False, autotune_sample=0):
+                 autotune=False, autotune_sample=0, output_first=False):
         self.grid = grid
         self.ctx = dcflow_setup(grid.n_bus, grid.f, grid.t, grid.b, grid.slack, precision=precision,
                                 device=device, chunk_topo=chunk_topo, island_tol=island_tol, compact_n1=compact_n1,
-                                autotune=autotune, autotune_sample=autotune_sample)
+                                autotune=autotune, autotune_sample=autotune_sample, output_first=output_first)
         self.n_mon = 0
         self.n_cont = 0
         self.n_multi = 0

@@ -455,6 +455,56 @@ def test_top_cases_tracking_matches_full_columns():
             assert col[l] >= col.max() - 1e-6 * max(1.0, col.max())
 
 
+def _candidate_workloads(kind):
+    if kind == "ti":
+        w = synth.workload(2, n_topo=12, T=3)
+        return w, dict(ti=synth.make_injection_topologies(w.grid, w.subs, w.topo, w.inj, 5, 91))
+    g = synth.make_grid(150, 220, 71)
+    subs = synth.split_capable(g, 30, 71)
+    topo = synth.make_topologies(g, subs, 20, 72, (1, 3), (0, 2))
+    inj = synth.make_injections(g, 3, 73, daily=True)
+    var = synth.make_variations(g, 37, 9, 74)
+    rng = np.random.default_rng(75)
+    mon = np.arange(g.n_branch, dtype=np.int32)
+    cont = np.sort(rng.choice(g.n_branch, 90, replace=False)).astype(np.int32)
+    return synth.Workload("cand", g, topo, inj, mon, cont, subs, var), dict(var=var)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["ti", "var"])
+def test_output_first_matches_metric_first(precision, kind):
+    """Injection candidates with the top-k cases: output-first (agg_i of every
+    (timestep, candidate) inside the candidate loop, the chosen one's kept) and
+    metric-first (agg_i of the chosen candidate only) report the same outputs:
+    the same pick, maxima, overload sums, indices and cases.  The FP32
+    metric-first cases come from the tracking pass, so their most loaded branch
+    may differ from the output-first column rebuild on a near tie only."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch, Solver
+    w, extra = _candidate_workloads(kind)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    k = 5
+    out = []
+    for of in (False, True):
+        s = Solver(w.grid, precision=precision, output_first=of)
+        s.set_study(w.mon, w.cont, lim, split_bus=w.subs)
+        batch = DeviceBatch(w.topo, w.inj, **extra)
+        out.append(s.solve(batch, top_k=k).to_host())
+        torch.cuda.synchronize()
+        s.close()
+    mf, of_ = out
+    assert (mf["status"] == 0).sum() >= 8
+    for key in ("status", "n_island_cont", "best_var", "worst_cont", "worst_mon", "top_cont"):
+        np.testing.assert_array_equal(mf[key], of_[key], err_msg=key)
+    for key in ("n1_max", "ovl", "top_loading"):
+        np.testing.assert_array_equal(mf[key], of_[key], err_msg=key)
+    diff = mf["top_mon"] != of_["top_mon"]
+    if precision == "fp64":
+        assert not diff.any()
+    else:
+        assert diff.mean() < 0.01, diff.mean()
+        assert (mf["top_cont"][diff] >= 0).all()
+
+
 def _top_k_of(cmax, k):
     """Per (topology, timestep) the top k of the per-contingency maxima by
     (value descending, position ascending); -1 / 0 where the value is below 0."""
