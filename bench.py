@@ -499,6 +499,30 @@ def run_ours(args):
                          "timestep): metric-first computes them for the chosen assignment only, output-first "
                          "for every assignment inside the brute-force loop (the modes of Sec. III-A); both "
                          "report the same outputs")
+            # |T_i| sweep (the paper's injection-ratio figure): loadflows/s against the number of
+            # injection topologies per branch topology, both modes, with the top-k cases
+            if args.ti_sweep and args.top_k > 0:
+                sweep = {}
+                so_of = Solver(w.grid, precision=form, output_first=True)
+                so_of.set_study(w.mon, w.cont, lim, split_bus=w.subs, outage_cand=ocand)
+                for U_ in (int(x) for x in args.ti_sweep.split(",")):
+                    tis_ = synth.make_injection_topologies(w.grid, w.subs, tsub, w.inj, U_, 900)
+                    dbs = DeviceBatch(tsub, w.inj, ti=tis_)
+                    row = {}
+                    for of, so in ((False, solver), (True, so_of)):
+                        rks = DeviceResults(nsub, db.n_time, len(w.mon), want_var=True, top_k=args.top_k)
+                        tks, _ = timed(so, dbs, rks, steps, stream)
+                        st_s = rks.island_flag[:nsub].cpu().numpy()
+                        ni_s = rks.n_island_cont[:nsub].cpu().numpy()
+                        lfs = _loadflows(tsub, st_s, ni_s, w.cont, T_STEPS) * U_
+                        row["output_first" if of else "metric_first"] = {
+                            "loadflows_per_s": lfs * steps / tks, "ms_per_step": 1e3 * tks / steps}
+                    sweep[str(U_)] = row
+                so_of.close()
+                results[f"fp32_ti_sweep_top{args.top_k}"] = {
+                    "by_ti": sweep, "topologies": nsub,
+                    "note": "loadflows/s (every topology, timestep, assignment and contingency) against |T_i|, "
+                            "the busbar assignments per branch topology, in both injection-module modes"}
         # the same solve with multi-outage N-1 cases (sets of 2-4 branches that fail together)
         if form == "fp32" and args.multi > 0 and db.n_var == 0:
             rng = np.random.default_rng(800)
@@ -982,6 +1006,8 @@ def main():
                     help="also time the FP32 solve with this many generator-failure cases; 0 = skip")
     ap.add_argument("--ti", type=int, default=16,
                     help="also time the FP32 solve with this many injection topologies per topology; 0 = skip")
+    ap.add_argument("--ti-sweep", default="1,4,16,64",
+                    help="assignments per topology of the |T_i| sweep (both injection-module modes); '' = none")
     ap.add_argument("--ti-topologies", type=int, default=1000,
                     help="topologies of the injection-topology form")
     ap.add_argument("--rows", default="restricted", choices=["restricted", "full"],
