@@ -613,7 +613,10 @@ def run_ours(args):
                 "peak_note": f"1 FP32 issue slot per entry at the {peak_kind} max SM clock "
                              f"({peaks.get('sm_max_mhz', 2032.0):.0f} MHz), 148 SMs x 128 lanes",
                 "n1_ms_per_step": k["n1_ms"] / head["steps"],
-                "n1_share_of_step": k["n1_ms"] / (head["ms_per_step"] * head["steps"])}
+                "n1_share_of_step": k["n1_ms"] / (head["ms_per_step"] * head["steps"]),
+                # the same rate against the 5 FP32-pipe operations per entry of the method's
+                # per-entry accounting (flow FFMA, |.|, max, and the overload max + add)
+                "frac_at_5_ops_per_entry": ach * 5 / peak}
     line = {"metric": METRIC,
             "value": head["value"], "unit": "loadflows/s", "n_gpus": ws, "steps": head["steps"],
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
