@@ -2715,11 +2715,11 @@ int launch_gen_r(const Args& a, int G, const int* gen_bus, const double* gen_p, 
     const uint64_t d_me[3] = {M, 4, nq}, s_me[2] = {Mp * 4, Mp * 16};
     const uint32_t b_me[3] = {32, 4, 1};
     const uint64_t d_pt[3] = {M, (uint64_t)a.T, nq}, s_pt[2] = {Mp * 4, Mp * a.T * 4};
-    const uint32_t b_pt[3] = {32, (uint32_t)TT, 1};
-    int rc = encode_map(&maps.pg, P, 2, d_pg, s_pg, b_pg);
+    const uint32_t b_pt[3] = {GenTmaLayout<1, RMAX>::PL, (uint32_t)TT, 1};  // 36-float lines
+    int rc = encode_map(&maps.pg, P, 2, d_pg, s_pg, b_pg, true);  // 128-byte swizzled
     if (!rc) rc = encode_map(&maps.zt, a.Zs, 3, d_zt, s_zt, b_zt);
     if (!rc) rc = encode_map(&maps.meta, a.diagv, 3, d_me, s_me, b_me);
-    if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt, true);
+    if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt);
     if (rc) return -rc;
     static uint64_t attr[3] = {0, 0, 0};
     auto go = [&](auto kern, int bytes, int i) -> int {
@@ -2776,11 +2776,11 @@ int launch_multi_rows(const Args& a, int RMAX, int n_multi, int n_ent, const int
     const uint64_t d_me[3] = {M, 4, nq}, s_me[2] = {Mp * 4, Mp * 16};
     const uint32_t b_me[3] = {32, 4, 1};
     const uint64_t d_pt[3] = {M, (uint64_t)a.T, nq}, s_pt[2] = {Mp * 4, Mp * a.T * 4};
-    const uint32_t b_pt[3] = {32, (uint32_t)TT, 1};
-    int rc = encode_map(&maps.phi, P, 2, d_ph, s_ph, b_ph);
+    const uint32_t b_pt[3] = {MultiTmaLayout<1, 4>::PL, (uint32_t)TT, 1};  // 36-float lines
+    int rc = encode_map(&maps.phi, P, 2, d_ph, s_ph, b_ph, true);  // 128-byte swizzled
     if (!rc) rc = encode_map(&maps.zt, a.Zs, 3, d_zt, s_zt, b_zt);
     if (!rc) rc = encode_map(&maps.meta, a.diagv, 3, d_me, s_me, b_me);
-    if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt, true);
+    if (!rc) rc = encode_map(&maps.pt, a.ptil, 3, d_pt, s_pt, b_pt);
     if (rc) return rc;
     static uint64_t attr[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     auto go = [&](auto kern, int bytes, int i) -> int {
