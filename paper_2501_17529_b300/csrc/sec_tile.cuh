@@ -57,6 +57,8 @@ struct GenTmaLayout {
   static constexpr int kOffCol = NS * kStage;       // float2 [RT / 2][GG]: [row pair][generator]
   static constexpr int kOffBar = kOffCol + (RT / 2) * GG * 8;
   static constexpr int kBytes = kOffBar + 64 + 1024;  // + alignment slack of the dynamic base
+  // the halves' maxima and overload sums [2][TT][GG + 1] reuse stage 0 at the group's end
+  static_assert(2 * 2 * TT * (GG + 1) * 4 <= kStage, "group reduction does not fit a stage");
 };
 
 template <int RMAX, int TR>
@@ -68,7 +70,6 @@ __global__ __launch_bounds__(128, 7) void k_gen_tma(const __grid_constant__ GenM
   extern __shared__ unsigned char gen_dyn[];
   __shared__ double sv_s[kRMax][GG];
   __shared__ float beta_s[GG][RMAX];
-  __shared__ float mx_s[2][TT][GG + 1], ov_s[2][TT][GG + 1];
   __shared__ int mp_s[kRMax + 1];
   __shared__ float bv_s[TT];
   __shared__ int bg_s[TT];
@@ -90,6 +91,8 @@ __global__ __launch_bounds__(128, 7) void k_gen_tma(const __grid_constant__ GenM
   unsigned char* sm = gen_dyn + (((raw + 1023u) & ~1023u) - raw);  // 1024-aligned stages (the swizzled tile)
   float2* s_col = reinterpret_cast<float2*>(sm + L::kOffCol);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::kOffBar);
+  float(*mx_s)[TT][GG + 1] = reinterpret_cast<float(*)[TT][GG + 1]>(sm);  // [2][TT][GG + 1], group end only
+  float(*ov_s)[TT][GG + 1] = reinterpret_cast<float(*)[TT][GG + 1]>(sm + 2 * TT * (GG + 1) * 4);
   const int r = qi.r;
   for (int i = tid; i <= r; i += blockDim.x) mp_s[i] = a.mod_ptr[(size_t)q * (kRMax + 1) + i];
   for (int t = tid; t < TT; t += blockDim.x) {
@@ -232,6 +235,7 @@ __global__ __launch_bounds__(128, 7) void k_gen_tma(const __grid_constant__ GenM
     }
     seq += ntile;
     if (failed) break;
+    __syncthreads();  // every thread is done with the last tile: the reduction reuses stage 0
 #pragma unroll
     for (int u = 0; u < 2; ++u)
 #pragma unroll
