@@ -650,6 +650,51 @@ def test_multi_outages_match_oracle(precision):
     assert (g["n_island_multi"][~ok] == 0).all()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_generator_and_multi_groups_and_passes(precision):
+    """37 generators (groups of 16, 16 and 5) and 75 sets of 1-4 branches (groups of 32, 32 and
+    11) in one solve over 29 timesteps (two passes of the FP32 kernels, the second ragged): the
+    group and pass boundaries of the generator and multi-outage kernels against the oracle."""
+    from paper_2501_17529_b300.dcflow import DeviceBatch, Solver
+    T, G = 29, 37
+    w = synth.workload(2, n_topo=10, T=T)
+    lim = oracle.thermal_limits(w.grid, w.inj)
+    rng = np.random.default_rng(83)
+    gb = np.sort(rng.choice(np.arange(1, w.grid.n_bus), G, replace=False)).astype(np.int32)
+    gp = np.abs(rng.normal(1.0, 0.5, (T, G)))
+    E = len(w.grid.f)
+    pool = np.nonzero(~oracle.bridges(w.grid.n_bus, w.grid.f, w.grid.t, np.ones(E, bool)))[0]
+    sets = [[int(b) for b in rng.choice(pool, 1 + k % 4, replace=False)] for k in range(75)]
+    s = Solver(w.grid, precision=precision)
+    s.set_study(w.mon, w.cont, lim, split_bus=w.subs, multi=sets)
+    g = s.solve(DeviceBatch(w.topo, w.inj, gen_bus=gb, gen_p=gp)).to_host()
+    s.close()
+    tol = TOL[precision]
+    rg = oracle.generator_n1(w.grid, w.topo, w.inj, gb, gp, w.mon, lim)
+    rm = oracle.multi_outage_n1(w.grid, w.topo, w.inj, sets, w.mon, lim)
+    ok = rg["status"] == 0
+    assert ok.sum() >= 3
+    np.testing.assert_array_equal(g["status"], rg["status"])
+    np.testing.assert_allclose(g["gen_max"][ok], rg["gen_max"][ok], rtol=tol, atol=tol)
+    d = np.abs(g["gen_ovl"][ok] - rg["gen_ovl"][ok]) / np.maximum(rg["gen_ovl"][ok], 1.0)
+    assert d.max() <= tol
+    np.testing.assert_array_equal(g["n_island_multi"][ok], rm["n_island_multi"][ok])
+    np.testing.assert_allclose(g["multi_max"][ok], rm["multi_max"][ok], rtol=tol, atol=tol)
+    d = np.abs(g["multi_ovl"][ok] - rm["multi_ovl"][ok]) / np.maximum(rm["multi_ovl"][ok], 1.0)
+    assert d.max() <= tol
+    for i in np.nonzero(ok)[0]:
+        for t in range(T):
+            wg, wm = g["worst_gen"][i, t], g["worst_multi"][i, t]
+            assert wg == rg["worst_gen"][i, t] or \
+                rg["gen_each"][i, t, wg] >= rg["gen_max"][i, t] - 2 * tol * max(1.0, rg["gen_max"][i, t])
+            assert wm == rm["worst_multi"][i, t] or \
+                rm["multi_each"][i, t, wm] >= rm["multi_max"][i, t] - 2 * tol * max(1.0, rm["multi_max"][i, t])
+    assert (g["worst_gen"][~ok] == -1).all() and (g["worst_multi"][~ok] == -1).all()
+    # the last groups hold worst cases here (so a dropped or misplaced group fails above)
+    assert (rg["worst_gen"][ok] >= 32).any() and (rm["worst_multi"][ok] >= 64).any()
+    assert (g["worst_gen"][ok] >= 32).any() and (g["worst_multi"][ok] >= 64).any()
+
+
 def test_multi_outages_rejected_forms():
     """Multi-outage outputs need a study with sets, all four arrays and no injection candidates;
     a set has 1-4 distinct in-range branches."""
