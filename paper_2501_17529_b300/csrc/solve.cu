@@ -807,6 +807,7 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
   const Real* meta = static_cast<const Real*>(a.diagv) + (size_t)q * 4 * Mp;
   const Real* VtR = static_cast<const Real*>(a.VtR) + (size_t)q * kRMax * C;
   const Real* sv = static_cast<const Real*>(a.s) + (size_t)q * T * C;
+  const Real eps = (Real)a.tie_eps;  // the tie band, eps * max(best, 1), in the working precision
   // the short remainder of the contingency range (no N-1 block of its own): its
   // Phi_f columns, built once with the N-1 kernels' arithmetic into shared memory
   // ([column][monitored row]), then applied to every timestep below
@@ -855,19 +856,22 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
         ba = a2;
       }
     }
-    // the remainder columns at this timestep (their maxima kept for the tie band)
+    // the remainder columns at this timestep (their maxima kept for the tie band);
+    // their overload terms summed in the working precision, one conversion per
+    // column (B300 runs FP64 arithmetic and conversions at a small fraction of
+    // the FP32 rate)
     Real vrem[4] = {(Real)-1, (Real)-1, (Real)-1, (Real)-1};
     for (int c = c_rem; c < a.C_eff; ++c) {
       const bool okc = a.valid[(size_t)q * C + c];
       Real vr = (Real)0;
-      double ov = 0.0;
       if (okc) {
         const Real st = sv[(size_t)t * C + c];
         const Real* ph = s_rem + (size_t)(c - c_rem) * M;
+        Real ov = (Real)0;
         for (int l = lane; l < M; l += 32) {
           const Real x = fabs(fma(ph[l], st, ptil[(size_t)t * Mp + l]));
           vr = fmax(vr, x);
-          if (x > (Real)1) ov += (double)x - 1.0;
+          if (x > (Real)1) ov += x - (Real)1;
         }
         for (int off = 16; off; off >>= 1) {
           vr = fmax(vr, __shfl_xor_sync(0xffffffffu, vr, off));
@@ -877,7 +881,7 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
           bv = vr;
           ba = c;
         }
-        ovl += ov;
+        ovl += (double)ov;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if (j == c - c_rem) vrem[j] = vr;
@@ -893,7 +897,7 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       // the base-grid bridges, which are never valid).  Each block's best within the
       // band is a candidate; only a block whose second largest maximum also lies in
       // the band needs the scan over the per-contingency maxima.
-      const Real thr = bv - (Real)(a.tie_eps * fmax((double)bv, 1.0));
+      const Real thr = bv - eps * fmax(bv, (Real)1);
       int cand = 0x7fffffff;
       bool amb = a.p2max == nullptr;
       for (int b = lane; b < nb; b += 32) {
@@ -947,7 +951,7 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
         Real v = (Real)-1;
         for (int l = lane; l < M; l += 32) v = fmax(v, entry(l));
         for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-        const Real thr = v - (Real)(a.tie_eps * fmax((double)v, 1.0));
+        const Real thr = v - eps * fmax(v, (Real)1);
         for (int l = lane; l < M; l += 32)
           if (entry(l) >= thr) {
             arg = l;
@@ -1007,7 +1011,7 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       }
       Real v = v1;
       for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-      const Real thr = v - (Real)(a.tie_eps * fmax((double)v, 1.0));
+      const Real thr = v - eps * fmax(v, (Real)1);
       int arg = v1 >= thr ? i1 : 0x7fffffff;
       if (__any_sync(0xffffffffu, v2 >= thr)) {  // two candidates in one lane: its lowest in the band
         arg = 0x7fffffff;
