@@ -516,18 +516,27 @@ __global__ __launch_bounds__(RegTile<TT>::NT, (TC && TT == 24) ? 7 : 0) void k_n
     if (t0 + t >= T) continue;
     float bv = -1.f, b2 = -1.f;  // the largest (lowest contingency on ties) and the second largest
     int ba = -1;
+    // the overload sums of 8 consecutive contingencies in FP32, then one FP64
+    // add: the B300's FP64 pipe would otherwise hold the block's slot for a
+    // conversion and an add per contingency
     double o = 0.0;
+    float o8 = 0.f;
     for (int k2 = 0; k2 < kCB; ++k2) {
-      if (!okc[k2]) continue;
-      const float v = s_s[t * SP + k2];
-      if (v > bv) {
-        b2 = bv;
-        bv = v;
-        ba = s_ci[k2];
-      } else if (v > b2) {
-        b2 = v;
+      if (okc[k2]) {
+        const float v = s_s[t * SP + k2];
+        if (v > bv) {
+          b2 = bv;
+          bv = v;
+          ba = s_ci[k2];
+        } else if (v > b2) {
+          b2 = v;
+        }
+        o8 += s_ov[t * SP + k2];
       }
-      o += (double)s_ov[t * SP + k2] * 1048576.0;
+      if ((k2 & 7) == 7) {
+        o += (double)(o8 * 1048576.f);
+        o8 = 0.f;
+      }
     }
     const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + cb;
     static_cast<float*>(a.pmax)[o2] = bv;

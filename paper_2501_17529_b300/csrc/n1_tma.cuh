@@ -311,18 +311,24 @@ __global__ __launch_bounds__(kCB * NTH) void k_n1_tma(const __grid_constant__ N1
     if (t0 + t >= T) continue;
     float bv = -1.f, b2 = -1.f;  // the largest (lowest contingency on ties) and the second largest
     int ba = -1;
-    double o = 0.0;
+    double o = 0.0;  // 8 contingencies' overload sums in FP32, then one FP64 add (B300's FP64 rate)
+    float o8 = 0.f;
     for (int k2 = 0; k2 < kCB; ++k2) {
-      if (!okc[k2]) continue;
-      const float v = s_s[t * kCB + k2];
-      if (v > bv) {
-        b2 = bv;
-        bv = v;
-        ba = c0 + k2;
-      } else if (v > b2) {
-        b2 = v;
+      if (okc[k2]) {
+        const float v = s_s[t * kCB + k2];
+        if (v > bv) {
+          b2 = bv;
+          bv = v;
+          ba = c0 + k2;
+        } else if (v > b2) {
+          b2 = v;
+        }
+        o8 += s_ov[t * kCB + k2];
       }
-      o += (double)s_ov[t * kCB + k2] * 1048576.0;
+      if ((k2 & 7) == 7) {
+        o += (double)(o8 * 1048576.f);
+        o8 = 0.f;
+      }
     }
     const size_t o2 = ((size_t)q * T + t0 + t) * a.ncb + blockIdx.x;
     static_cast<float*>(a.pmax)[o2] = bv;

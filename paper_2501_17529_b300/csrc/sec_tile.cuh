@@ -248,9 +248,9 @@ __global__ __launch_bounds__(128, 7) void k_gen_tma(const __grid_constant__ GenM
       if (t0 + t >= T) continue;
       float bv = bv_s[t];
       int bgi = bg_s[t];
-      double bo = bo_s[t];
+      float of = 0.f;  // the group's overload sums in FP32, one FP64 add (B300's FP64 rate)
       for (int g = 0; g < gn; ++g) {
-        bo += (double)ov_s[0][t][g] * 1048576.0 + (double)ov_s[1][t][g] * 1048576.0;
+        of += ov_s[0][t][g] + ov_s[1][t][g];
         const float m = fmaxf(mx_s[0][t][g], mx_s[1][t][g]);
         if (m > bv) {
           bv = m;
@@ -259,7 +259,7 @@ __global__ __launch_bounds__(128, 7) void k_gen_tma(const __grid_constant__ GenM
       }
       bv_s[t] = bv;
       bg_s[t] = bgi;
-      bo_s[t] = bo;
+      bo_s[t] += (double)(of * 1048576.f);
     }
   }
   if (failed) {  // the tiles in flight land (bounded waits) before the block exits
@@ -550,10 +550,10 @@ __global__ __launch_bounds__(256, 3) void k_multi_tma(const __grid_constant__ Mu
       if (t0 + t >= T) continue;
       float bv = bv_s[t];
       int bg = bg_s[t];
-      double bo = bo_s[t];
+      float of = 0.f;  // the group's overload sums in FP32, one FP64 add (B300's FP64 rate)
       for (int s2 = 0; s2 < ng; ++s2) {
         if (fl_s[s2]) continue;
-        bo += (double)ov_s[0][s2][t] * 1048576.0 + (double)ov_s[1][s2][t] * 1048576.0;
+        of += ov_s[0][s2][t] + ov_s[1][s2][t];
         const float m = fmaxf(mx_s[0][s2][t], mx_s[1][s2][t]);
         if (m > bv) {
           bv = m;
@@ -562,7 +562,7 @@ __global__ __launch_bounds__(256, 3) void k_multi_tma(const __grid_constant__ Mu
       }
       bv_s[t] = bv;
       bg_s[t] = bg;
-      bo_s[t] = bo;
+      bo_s[t] += (double)(of * 1048576.f);
     }
   }
   if (failed) {  // the tile in flight lands (bounded wait) before the block exits
