@@ -44,11 +44,11 @@ WORKLOADS = {
 # 500-bus study (its summary sits under profiles/), keyed by the sha1 of the
 # kernel's source and of its argument block at the time of the capture
 N1_TRAFFIC = {
-    ("4721d056a1ba", "fp32"): {"bytes": 1.0995e9, "per": "bench step of the 500-bus study",
-                               "how": "1,000-topology capture (626 + 374 topologies: 78.45 MB + 31.61 MB of DRAM "
+    ("c1efdb0101c7", "fp32"): {"bytes": 1.1018e9, "per": "bench step of the 500-bus study",
+                               "how": "1,000-topology capture (626 + 374 topologies: 78.67 MB + 31.62 MB of DRAM "
                                       "read + write) scaled by topologies per rank class to 6,233 + 3,767"},
-    ("4721d056a1ba", "bf16x3"): {"bytes": 1.1636e9, "per": "bench step of the 500-bus study",
-                                 "how": "1,000-topology capture (626 + 374 topologies: 84.93 MB + 31.56 MB) scaled "
+    ("c1efdb0101c7", "bf16x3"): {"bytes": 1.1584e9, "per": "bench step of the 500-bus study",
+                                 "how": "1,000-topology capture (626 + 374 topologies: 84.42 MB + 31.55 MB) scaled "
                                         "by topologies per rank class to 6,233 + 3,767"},
 }
 
