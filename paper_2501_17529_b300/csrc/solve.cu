@@ -868,7 +868,8 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
         const Real st = sv[(size_t)t * C + c];
         const Real* ph = s_rem + (size_t)(c - c_rem) * M;
         Real ov = (Real)0;
-        for (int l = lane; l < M; l += 32) {
+#pragma unroll 4
+        for (int l = lane; l < M; l += 32) {  // 4 rows' loads in flight per lane
           const Real x = fabs(fma(ph[l], st, ptil[(size_t)t * Mp + l]));
           vr = fmax(vr, x);
           if (x > (Real)1) ov += x - (Real)1;
@@ -999,7 +1000,8 @@ __global__ __launch_bounds__(128) void k_final(Args a, const int* __restrict__ n
       const Real* pt = ptil + (size_t)t * Mp;
       Real v1 = (Real)-1, v2 = (Real)-1;
       int i1 = 0x7fffffff;
-      for (int l = lane; l < M; l += 32) {
+#pragma unroll 4
+      for (int l = lane; l < M; l += 32) {  // 4 rows' loads in flight per lane
         const Real x = fabs(fma(s_col[l], st, pt[l]));
         if (x > v1) {
           v2 = v1;
