@@ -2301,31 +2301,32 @@ __global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const i
     return;
   }
   const double* Kinv = a.Kinv + (size_t)q * kRMax * kRMax;
-  for (int p = lane; p < 4 * kRMax; p += 32) {  // Sigma^T Phi[:, o] - s_o and the Z row of member o
-    const int a2 = p / kRMax, i = p % kRMax;
-    double acc = 0.0, z = 0.0;
-    if (a2 < n && i < r) {
-      const int oN = mN[e0 + a2];
-      for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
-        const int mm = S.en[e];
-        acc = fma(S.esd[e], a.PhiN[(size_t)mm * NN + oN], acc);
-        if (i < ks && mm == oN) acc -= S.esd[e];
-      }
-      z = z_entry_col(S, a.PhiN, NN, a.bN, oN, i);
+  // the (member, modification) items packed to the topology's rank: n r <= 64 items
+  // over the warp's lanes (B300's FP64 pipe issues a whole warp for any active lane)
+  for (int p = lane; p < n * r; p += 32) {  // Sigma^T Phi[:, o] - s_o and the Z row of member o
+    const int a2 = p / r, i = p % r;
+    double acc = 0.0;
+    const int oN = mN[e0 + a2];
+    for (int e = S.mp[i]; e < S.mp[i + 1]; ++e) {
+      const int mm = S.en[e];
+      acc = fma(S.esd[e], a.PhiN[(size_t)mm * NN + oN], acc);
+      if (i < ks && mm == oN) acc -= S.esd[e];
     }
+    const double z = z_entry_col(S, a.PhiN, NN, a.bN, oN, i);
     bv_s[wp][a2][i] = acc;
     z_s[wp][a2][i] = z;
     zr_s[wp][a2][i] = (Real)z;  // the working-precision copy for the weights below
   }
   __syncwarp();
   Real* vt = mvt + qm * 4 * kRMax;
-  for (int p = lane; p < 4 * kRMax; p += 32) {  // K^{-1} is zero outside r x r
-    const int a2 = p / kRMax, j = p % kRMax;
+  for (int p = lane; p < 4 * kRMax; p += 32) vt[p] = (Real)0;  // rows past the rank and absent members
+  __syncwarp();
+  for (int p = lane; p < n * r; p += 32) {  // K^{-1} is zero outside r x r
+    const int a2 = p / r, j = p % r;
     double x = 0.0;
-    if (a2 < n)
-      for (int i = 0; i < r; ++i) x = fma(Kinv[j * kRMax + i], bv_s[wp][a2][i], x);
+    for (int i = 0; i < r; ++i) x = fma(Kinv[j * kRMax + i], bv_s[wp][a2][i], x);
     vt_s[wp][a2][j] = x;
-    vt[p] = (Real)x;
+    vt[a2 * kRMax + j] = (Real)x;
   }
   __syncwarp();
   if (lane < n * n) {  // A = I - Phi_f[O, O]
@@ -2335,20 +2336,25 @@ __global__ __launch_bounds__(128) void k_multi_prep(Args a, int n_multi, const i
     A_s[wp][a2][b2] = (a2 == b2 ? 1.0 : 0.0) - phi;
   }
   __syncwarp();
-  if (lane == 0) {  // natural-order LU
+  {  // natural-order LU, lane i owning row i (the same operations per entry as a row loop)
     int f = 0;
-    for (int k = 0; k < n && !f; ++k) {
-      if (!(A_s[wp][k][k] > a.tol)) {
+    for (int k = 0; k < n; ++k) {
+      const double piv = A_s[wp][k][k];  // warp-uniform
+      if (!(piv > a.tol)) {
         f = 1;
         break;
       }
-      for (int i = k + 1; i < n; ++i) {
-        A_s[wp][i][k] /= A_s[wp][k][k];
-        for (int j = k + 1; j < n; ++j) A_s[wp][i][j] = fma(-A_s[wp][i][k], A_s[wp][k][j], A_s[wp][i][j]);
+      if (lane > k && lane < n) {
+        const double fct = A_s[wp][lane][k] / piv;
+        A_s[wp][lane][k] = fct;
+        for (int j = k + 1; j < n; ++j) A_s[wp][lane][j] = fma(-fct, A_s[wp][k][j], A_s[wp][lane][j]);
       }
+      __syncwarp();
     }
-    flag_s[wp] = f;
-    mflag[qm] = f;
+    if (lane == 0) {
+      flag_s[wp] = f;
+      mflag[qm] = f;
+    }
   }
   __syncwarp();
   if (flag_s[wp]) return;
