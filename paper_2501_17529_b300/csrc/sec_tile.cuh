@@ -218,20 +218,23 @@ __global__ __launch_bounds__(128, 7) void k_gen_tma(const __grid_constant__ GenM
         }
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int j = 0; j < TR; ++j) {
-          mx[u][j] = fmaxf(mx[u][j], mt[u][j]);
-          if (mt[u][j] > 1.f) {  // the overload terms of this cell over the tile half
-            float sum = 0.f;
-            for (int i = 0; i < 8; ++i) {
-              const float2 pt = *reinterpret_cast<const float2*>(pt_h + 8 * j * PL + 2 * i);
-              const float2 v = __ffma2_rn(s_col[(8 * h + i) * GG + 2 * gp + u], s2[u][j], pt);
-              sum += sec_ovl(v.x) + sec_ovl(v.y);
-            }
-            ov[u][j] += sum;
+      for (int j = 0; j < TR; ++j) {
+        mx[0][j] = fmaxf(mx[0][j], mt[0][j]);
+        mx[1][j] = fmaxf(mx[1][j], mt[1][j]);
+        if (mt[0][j] > 1.f || mt[1][j] > 1.f) {  // the overload terms of both cells at this timestep
+          float s0 = 0.f, s1 = 0.f;  // (a cell whose maximum is at most 1 adds exact zeros)
+          for (int i = 0; i < 8; ++i) {
+            const float2 pt = *reinterpret_cast<const float2*>(pt_h + 8 * j * PL + 2 * i);
+            const float4 c4 = col_h[i * (GG / 2)];
+            const float2 v0 = __ffma2_rn(make_float2(c4.x, c4.y), s2[0][j], pt);
+            const float2 v1 = __ffma2_rn(make_float2(c4.z, c4.w), s2[1][j], pt);
+            s0 += sec_ovl(v0.x) + sec_ovl(v0.y);
+            s1 += sec_ovl(v1.x) + sec_ovl(v1.y);
           }
+          ov[0][j] += s0;
+          ov[1][j] += s1;
         }
+      }
     }
     seq += ntile;
     if (failed) break;
